@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark: brute-force dedispersion throughput on one GB300 (or N replicas).
+
+Default workload: the paper-scale 8-bit case -- 8192 channels x 262144
+samples of uint8 (16.8 s at 64 us), 4096 trial DMs 0..409.5 step 0.1,
+1670 MHz top of a 320 MHz band.  One step = one dd_run over the whole input
+(inputs resident in HBM; 2.1 GB in + 4.2 GB out, far larger than L2, so no
+flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  Metric: DM-trial x output-samples per second.
+Extra keys: channel-adds/s, real-time factor R = t_obs / t_step (Sec. 5.4),
+the ALU roofline of the dominant kernel, the oracle's CPU baseline and an
+end-to-end (host buffers through the C ABI) number.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference   # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DM-trials x samples / s"
+UNIT = "DM*samples/s"
+
+
+def _workload(name):
+    from synth import workloads
+    return {"paper_u8": workloads.paper_u8, "paper_u16": workloads.paper_u16,
+            "tiny_u8": workloads.tiny_u8, "diff_f32": workloads.diff_f32}[name]()
+
+
+def _describe(beam):
+    r = beam.ranges
+    plan = "; ".join(f"DM {lo:g}-{hi:g} step {st:g} bin {b}" for lo, hi, st, b in r)
+    return (f"{beam.name}: {beam.dtype} {beam.n_chan} ch x {beam.n_samp} samples, "
+            f"{beam.f_high:g} MHz top, {beam.bandwidth:g} MHz band, "
+            f"{beam.t_samp * 1e6:g} us; {plan}")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measure_alu_peak(torch, lib):
+    """Measured 3-input integer add rate (lane-ops/s) from the register microbenchmark."""
+    import ctypes
+    sms, clk = ctypes.c_int32(), ctypes.c_int32()
+    lib.dd_bench_device(ctypes.byref(sms), ctypes.byref(clk))
+    blocks, threads, iters = int(sms.value) * 4, 512, 4096
+    sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ops = ctypes.c_double()
+    res = {}
+    for kind, name in [(1, "iadd3"), (2, "iadd2"), (3, "fadd"), (4, "fadd2"), (5, "iadd3_imad"),
+                       (6, "lds128")]:
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lib.dd_bench_launch(kind, blocks, threads, iters, sink.data_ptr(), stream.cuda_stream,
+                                ctypes.byref(ops))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            best = max(best, blocks * threads * iters * ops.value / sec)
+        res[name] = best
+    res["sm_count"] = int(sms.value)
+    res["lds128_bytes_per_s"] = res["lds128"] * 16
+    return res
+
+
+def run_ours(args):
+    import torch
+    import paper_2311_05341_gb300 as dd
+    from paper_2311_05341_gb300 import _lib
+    from synth import workloads
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    lib = _lib.load()
+
+    beam = _workload(args.workload)
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype,
+                   device=f"cuda:{local}")
+    info = plan.info(beam.n_samp)
+    tables = {}
+
+    def shift_rows(r, d):
+        if r not in tables:
+            tables[r] = plan.shifts(r)
+        return tables[r][d]
+
+    x_host = workloads.make_input(beam, shift_rows, info["n_dm"], info["n_out"])
+    x = torch.from_numpy(x_host).cuda()
+    out = plan.empty_output(beam.n_samp)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step():
+        plan.run_raw(x.data_ptr(), x.stride(0), beam.n_samp, out.data_ptr(), sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    dm_samples = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
+    chan_adds = dm_samples * beam.n_chan
+    launches_per_step = len(beam.ranges)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
+    total = sum(per)
+    if ws > 1:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / args.steps * 1e3
+    value = dm_samples * args.steps * ws / total
+
+    # End to end through the C ABI: pinned host in -> device -> pinned host out.
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(x_host).pin_memory()
+        h_out = torch.empty(info["out_elems"], dtype=plan.out_dtype()).pin_memory()
+        plan.run_host(h_in, h_out, x, out, n_samp=beam.n_samp)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(k):
+            plan.run_host(h_in, h_out, x, out, n_samp=beam.n_samp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / k
+        e2e = {"value": dm_samples * ws / sec, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
+               "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
+               "ms_per_step": sec * 1e3}
+
+    peaks = measure_alu_peak(torch, lib)
+    if rank != 0:
+        return
+    # Roofline of the dominant (only) kernel: sample-adds per launch / mean launch time.
+    sample_adds_per_s = chan_adds / (total / args.steps)
+    per_lane = {"u8": 4, "u16": 2, "f32": 1}[beam.dtype]
+    peak_adds = peaks["iadd3"] * per_lane if beam.dtype != "f32" else peaks["fadd"]
+    roofline = {
+        "bound": "alu", "achieved": sample_adds_per_s / 1e12, "peak": peak_adds / 1e12,
+        "unit": "Tadd/s", "frac": sample_adds_per_s / peak_adds, "traffic": None,
+        "peak_source": ("measured 3-input int32 add rate x %d sample-adds per lane-op "
+                        "(16-bit packed lanes)" % per_lane) if beam.dtype != "f32"
+        else "measured float32 add rate",
+        "alu_microbench": {k: v for k, v in peaks.items()},
+    }
+    t_obs = beam.n_samp * beam.t_samp
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"u8": "int32", "u16": "int32", "f32": "f32"}[beam.dtype],
+        "data": "synthetic",
+        "config": {"workload": _describe(beam), "n_dm": info["n_dm_total"],
+                   "n_out": info["n_out"], "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{ws}"},
+        "channel_adds_per_s": chan_adds * args.steps * ws / total,
+        "real_time_factor": t_obs / (ms_per_step / 1e3),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps * launches_per_step,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(beam, x_host, info, args.cpu_rows)
+    print(json.dumps(line))
+
+
+def cpu_baseline(beam, x_host, info, n_rows):
+    """The oracle, as it stands, on a bounded sample: n_rows full-length DM rows."""
+    import oracle
+    rows = np.linspace(0, info["n_dm"][0] - 1, n_rows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.forward_rows(x_host, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
+    sec = time.perf_counter() - t0
+    units = n_rows * info["n_out"][0]
+    return {"value": units / sec, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n_rows} of {info['n_dm'][0]} DM rows, full length "
+                      f"({info['n_out'][0]} samples), range 0", "seconds": sec}
+
+
+def run_reference(args):
+    """The CPU oracle timed as it stands on a bounded sample of the workload."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from synth import workloads
+    import oracle
+    beam = _workload(args.workload)
+    tables = [oracle.shift_table(beam.freqs, beam.f_high, beam.t_samp, r) for r in beam.ranges]
+    n_dm = [t.shape[0] for t in tables]
+    n_out = [oracle.extent(beam.freqs, beam.f_high, beam.t_samp, r, beam.n_samp)[1]
+             for r in beam.ranges]
+    x = workloads.make_input(beam, lambda r, d: tables[r][d], n_dm, n_out)
+    info = {"n_dm": n_dm, "n_out": n_out}
+    n_rows = args.cpu_rows_reference
+    rows = np.linspace(0, n_dm[0] - 1, n_rows).astype(np.int64)
+
+    def step():
+        oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = time.perf_counter() - t0
+    value = n_rows * n_out[0] * args.steps / sec
+    sample = f"{n_rows} of {n_dm[0]} DM rows, full length ({n_out[0]} samples) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": _describe(beam), "n_dm": sum(n_dm), "n_out": n_out},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    del info
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_u8",
+                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32"])
+    ap.add_argument("--cpu-rows", type=int, default=24)
+    ap.add_argument("--cpu-rows-reference", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * dd.h -- C ABI of the GB300 brute-force incoherent dedispersion library.
+ *
+ * The operation (Sec. 2 of the paper, Eq. 3 and Algorithm 1): for every
+ * trial DM d of every DM range r and every output sample t,
+ *
+ *     Y_r[d][t] = sum_{c < n_chan} X_r[c][t + s_r(c, d)]
+ *
+ * where
+ *   - X is a channel-major filterbank X[c][t] (uint8, uint16 or float32),
+ *   - X_r is X decimated by the range's time bin b_r (the sum of b_r consecutive
+ *     raw samples; the paper's "time binning", Sec. 5.3),
+ *   - s_r(c, d) = floor(DM_d * k_c / (b_r * t_samp) + 0.5) is the integer delay
+ *     of channel c at trial DM_d = lo_r + d * step_r (fixed step per range,
+ *     Table 2), rounded half up, evaluated in FP64 on the host,
+ *   - k_c = 4148.808 * (1/f_c^2 - 1/f_ref^2) seconds per unit DM, the
+ *     cold-plasma delay law of Eq. 1 in the per-channel form of Eq. 7, with
+ *     frequencies in MHz.
+ * Outputs are the valid samples only: t in [0, N_out_r) with
+ * N_out_r = floor(n_samp / b_r) - S_max_r and S_max_r = max_{c,d} s_r(c, d).
+ * Sums are raw (no normalisation): int32 for integer inputs, float32 for float.
+ *
+ * Memory ownership: the library NEVER allocates device memory.  The caller
+ * owns every device buffer (inputs, outputs and the plan workspace); the plan
+ * handle itself is host memory owned by the library.  All device work is
+ * stream-ordered on the caller's stream, passed as an opaque `void*` holding a
+ * cudaStream_t (NULL = the legacy default stream).
+ *
+ * Errors: every call returns a dd_status; nothing aborts or throws across the
+ * boundary.  dd_last_error_detail() gives a thread-local human-readable reason
+ * for the last failing call on this thread.  CUDA launch/runtime failures are
+ * reported as DD_ERR_CUDA with the CUDA error text in the detail string.
+ *
+ * Thread safety: a plan is immutable once uploaded; any number of host
+ * threads may run it concurrently on different streams.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DD_OK = 0,
+  DD_ERR_INVALID_ARG = 1, /* null pointer, bad enum, non-positive size ... */
+  DD_ERR_UNSUPPORTED = 2, /* valid request the library does not implement */
+  DD_ERR_SHAPE = 3,       /* input too short, misaligned pointer or stride */
+  DD_ERR_BUDGET = 4,      /* workspace or a fixed-size table is too small */
+  DD_ERR_CUDA = 5,        /* a CUDA call failed; see dd_last_error_detail() */
+  DD_ERR_TIMEOUT = 6      /* a bounded device wait gave up */
+} dd_status;
+
+typedef enum { DD_U8 = 1, DD_U16 = 2, DD_F32 = 3 } dd_dtype;
+
+/* One DM range: trial DMs lo, lo+step, ... (n = llround((hi-lo)/step) of
+ * them, half-open like Table 2), dedispersed at time bin `bin` (>= 1). */
+typedef struct {
+  double dm_lo;
+  double dm_hi;
+  double dm_step;
+  int32_t bin;
+} dd_range;
+
+typedef struct dd_plan_s* dd_plan;
+
+#define DD_MAX_RANGES 16
+
+/* Sizes of a plan for a given number of raw input samples. */
+typedef struct {
+  int32_t n_chan;
+  int32_t n_ranges;
+  dd_dtype dtype;
+  int64_t n_samp;                     /* raw samples the query was made for */
+  int64_t n_dm_total;                 /* sum of n_dm over ranges */
+  int64_t n_dm[DD_MAX_RANGES];        /* trial DMs per range */
+  int64_t s_max[DD_MAX_RANGES];       /* largest shift per range (decimated samples) */
+  int64_t n_out[DD_MAX_RANGES];       /* output samples per range (<= 0: too short) */
+  int64_t out_offset[DD_MAX_RANGES];  /* element offset of each range in d_out */
+  int64_t out_elems;                  /* total output elements */
+  int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
+  size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
+} dd_plan_info;
+
+/*
+ * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
+ * centre frequencies, each in (0, f_ref_mhz]; conventionally channel 0 is the
+ * highest.  t_samp_s > 0 is the raw sampling time.  ranges[n_ranges]
+ * (1..DD_MAX_RANGES) each need step > 0, hi > lo >= 0 and bin >= 1.  The
+ * library copies what it needs; the caller keeps ownership of freqs and
+ * ranges.  On success *out holds a new plan to release with dd_plan_destroy.
+ * Errors: DD_ERR_INVALID_ARG for any violated condition above.
+ */
+dd_status dd_plan_create(const double* freqs_mhz, int32_t n_chan, double f_ref_mhz,
+                         double t_samp_s, const dd_range* ranges, int32_t n_ranges,
+                         dd_dtype dtype, dd_plan* out);
+
+/* Release a plan (NULL is a no-op).  Device workspace stays the caller's. */
+dd_status dd_plan_destroy(dd_plan plan);
+
+/* Fill *out with the plan's sizes for n_samp raw samples (n_samp >= 0). */
+dd_status dd_plan_query(dd_plan plan, int64_t n_samp, dd_plan_info* out);
+
+/* Copy the int32 shift table of range `range` to host memory host_out laid
+ * out [n_dm][n_chan] (s(c,d) at host_out[d*n_chan + c]). */
+dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out);
+
+/*
+ * Copy the plan's device tables into caller-owned device memory d_workspace
+ * of `bytes` >= workspace_bytes (16-byte aligned), asynchronously on
+ * `stream`, and bind that workspace to the plan.  The workspace must stay
+ * alive and unmodified while runs are in flight.  The host staging copy lives
+ * in the plan, so the plan must outlive the copy (synchronise the stream
+ * before destroying a plan whose upload may still be running).
+ * Errors: DD_ERR_BUDGET if bytes is too small, DD_ERR_SHAPE if misaligned,
+ * DD_ERR_CUDA if the copy cannot be enqueued.
+ */
+dd_status dd_plan_upload(dd_plan plan, void* d_workspace, size_t bytes, void* stream);
+
+/*
+ * Forward transform (Eq. 3) of every range.
+ *   d_in:  device, channel-major [n_chan][in_row_stride] elements of the plan
+ *          dtype; n_samp <= in_row_stride valid samples per row; 16-byte
+ *          aligned base and in_row_stride*elem_size a multiple of 16 bytes.
+ *   d_out: device, the concatenation over ranges of [n_dm_r][n_out_r]
+ *          (offsets from dd_plan_query), int32 for integer dtypes and float32
+ *          for DD_F32; overwritten.  16-byte aligned.
+ * Needs a bound workspace (dd_plan_upload).  Asynchronous on `stream`.
+ * Errors: DD_ERR_SHAPE if some range has n_out <= 0 or alignment/stride rules
+ * are broken, DD_ERR_INVALID_ARG for null pointers or no workspace,
+ * DD_ERR_CUDA on a launch failure.
+ */
+dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                 void* d_out, void* stream);
+
+/*
+ * Adjoint (transpose) of dd_run for float32 plans: re-dispersion
+ *   xbar[c][t] = sum_r sum_d ybar_r[d][floor(t/b_r) - s_r(c, d)]
+ * over terms with 0 <= floor(t/b_r) - s_r(c,d) < n_out_r, computed as a gather
+ * (no atomics).  d_ybar has dd_run's output layout; d_xbar is device
+ * [n_chan][xbar_row_stride] float32, fully overwritten for t < n_samp (samples
+ * no output reads get 0).  This operation is this library's own (the paper has
+ * no adjoint); it is the derivative of Eq. 3 with respect to X.
+ * Errors: DD_ERR_UNSUPPORTED for integer plans, otherwise as dd_run.
+ */
+dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
+                         int64_t xbar_row_stride, void* stream);
+
+/*
+ * End-to-end forward from HOST buffers: copies h_in (pinned host memory,
+ * [n_chan][in_row_stride]) to the caller's device staging buffer d_in_stage,
+ * runs dd_run into d_out_stage and copies the output plane back to h_out, all
+ * on `stream` (one cudaMemcpyAsync per copy).  Staging buffers have the same
+ * layout rules as dd_run.  Returns once the work is enqueued.
+ */
+dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
+                      void* h_out, void* d_in_stage, void* d_out_stage, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* dd_status_string(dd_status status);
+/* Thread-local detail of the last failing call on this thread ("" if none). */
+const char* dd_last_error_detail(void);
+/* Library version string. */
+const char* dd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

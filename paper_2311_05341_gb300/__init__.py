@@ -1,0 +1,179 @@
+"""GB300-native brute-force incoherent dedispersion (arxiv 2311.05341).
+
+Python binding of libdd (include/dd.h).  PyTorch supplies device memory and
+streams only; every step of the transform runs in the library's CUDA kernels.
+
+    plan = Plan(freqs_mhz, f_ref_mhz, t_samp_s, [(lo, hi, step, bin), ...], "u8")
+    planes = plan.run(x)          # x: cuda tensor [n_chan][n_samp]
+    # planes[r]: [n_dm_r][n_out_r] int32 (u8/u16) or float32 (f32)
+
+Y_r[d][t] = sum_c X_r[c][t + s_r(c, d)] with the shift law of Eq. 1 and the
+direct transform of Eq. 3 (Sec. 2 of the paper); see include/dd.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import DDError, check
+
+__all__ = ["Plan", "DDError", "build", "DTYPES"]
+
+DTYPES = {"u8": _lib.DD_U8, "u16": _lib.DD_U16, "f32": _lib.DD_F32}
+_TORCH_DTYPE_NAMES = {"u8": "uint8", "u16": "uint16", "f32": "float32"}
+
+
+def build(force: bool = False) -> str:
+    """Compile libdd.so for sm_103a (in-tree)."""
+    from . import builder
+    return builder.build(force=force)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A dedispersion plan: channel frequencies, sampling time and DM ranges.
+
+    ``ranges`` is a sequence of ``(dm_lo, dm_hi, dm_step, bin)``: trial DMs
+    lo, lo+step, ... (half-open, fixed step per range as in Table 2), each range
+    dedispersed at time bin ``bin``.  The device tables are uploaded into a
+    torch-owned workspace on ``device`` when ``upload`` is true.
+    """
+
+    def __init__(self, freqs_mhz, f_ref_mhz: float, t_samp_s: float, ranges, dtype: str = "u8",
+                 device=None, upload: bool = True):
+        self._lib = _lib.load()
+        if dtype not in DTYPES:
+            raise ValueError(f"dtype must be one of {list(DTYPES)}")
+        self.dtype = dtype
+        self.freqs = np.ascontiguousarray(np.asarray(freqs_mhz, dtype=np.float64))
+        self.f_ref = float(f_ref_mhz)
+        self.t_samp = float(t_samp_s)
+        self.ranges = [tuple(r) for r in ranges]
+        arr = (_lib.Range * len(self.ranges))(
+            *[_lib.Range(float(a), float(b), float(c), int(d)) for a, b, c, d in self.ranges])
+        handle = ctypes.c_void_p()
+        check(self._lib.dd_plan_create(
+            self.freqs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.freqs.size,
+            self.f_ref, self.t_samp, arr, len(self.ranges), DTYPES[dtype], ctypes.byref(handle)))
+        self._h = handle
+        self.workspace = None
+        if upload:
+            self.upload(device)
+
+    # -- host queries -----------------------------------------------------
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def n_chan(self) -> int:
+        return int(self.freqs.size)
+
+    def info(self, n_samp: int) -> dict:
+        inf = _lib.PlanInfo()
+        check(self._lib.dd_plan_query(self._h, int(n_samp), ctypes.byref(inf)))
+        n = inf.n_ranges
+        return {
+            "n_chan": inf.n_chan, "n_ranges": n, "n_samp": inf.n_samp,
+            "n_dm": [inf.n_dm[i] for i in range(n)], "s_max": [inf.s_max[i] for i in range(n)],
+            "n_out": [inf.n_out[i] for i in range(n)],
+            "out_offset": [inf.out_offset[i] for i in range(n)],
+            "out_elems": inf.out_elems, "n_dm_total": inf.n_dm_total,
+            "max_delay_raw": inf.max_delay_raw, "workspace_bytes": inf.workspace_bytes,
+        }
+
+    def shifts(self, r: int = 0) -> np.ndarray:
+        """int32 [n_dm][n_chan] shift table of range r (host copy)."""
+        n_dm = self.info(0)["n_dm"][r]
+        out = np.empty((n_dm, self.n_chan), dtype=np.int32)
+        check(self._lib.dd_plan_shifts(self._h, int(r), out.ctypes.data))
+        return out
+
+    # -- device -----------------------------------------------------------
+    def upload(self, device=None, stream=None):
+        import torch
+        dev = torch.device("cuda" if device is None else device)
+        nbytes = max(int(self.info(0)["workspace_bytes"]), 16)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        check(self._lib.dd_plan_upload(self._h, self.workspace.data_ptr(), nbytes,
+                                       _stream_ptr(stream)))
+        torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
+        return self
+
+    def out_dtype(self):
+        import torch
+        return torch.float32 if self.dtype == "f32" else torch.int32
+
+    def empty_output(self, n_samp: int, device=None):
+        import torch
+        inf = self.info(n_samp)
+        dev = self.workspace.device if device is None else device
+        return torch.empty(max(inf["out_elems"], 4), dtype=self.out_dtype(), device=dev)
+
+    def split(self, flat, n_samp: int):
+        """Views of a flat output buffer as per-range [n_dm][n_out] planes."""
+        inf = self.info(n_samp)
+        return [flat[o:o + nd * no].view(nd, no)
+                for o, nd, no in zip(inf["out_offset"], inf["n_dm"], inf["n_out"])]
+
+    def run(self, x, out=None, n_samp: int | None = None, stream=None):
+        """Forward transform of a cuda tensor x [n_chan][stride] -> list of planes."""
+        self._check_input(x)
+        n = x.shape[1] if n_samp is None else int(n_samp)
+        if out is None:
+            out = self.empty_output(n, x.device)
+        check(self._lib.dd_run(self._h, x.data_ptr(), x.stride(0), n, out.data_ptr(),
+                               _stream_ptr(stream)))
+        return self.split(out, n)
+
+    def run_raw(self, x_ptr: int, stride: int, n_samp: int, out_ptr: int, stream_ptr: int):
+        """Forward transform on raw device pointers (no checks beyond the library's)."""
+        check(self._lib.dd_run(self._h, x_ptr, stride, n_samp, out_ptr, stream_ptr))
+
+    def run_adjoint(self, ybar_flat, n_samp: int, xbar=None, stream=None):
+        """Adjoint of run() for f32 plans: flat cotangent -> [n_chan][n_samp] float32."""
+        import torch
+        if xbar is None:
+            stride = (n_samp + 3) // 4 * 4
+            xbar = torch.empty((self.n_chan, stride), dtype=torch.float32,
+                               device=ybar_flat.device)
+        check(self._lib.dd_run_adjoint(self._h, ybar_flat.data_ptr(), xbar.data_ptr(), int(n_samp),
+                                       xbar.stride(0), _stream_ptr(stream)))
+        return xbar[:, :n_samp]
+
+    def run_host(self, h_in, h_out, d_in_stage, d_out_stage, n_samp: int | None = None,
+                 stream=None):
+        """Host-to-host forward through pinned host buffers and device staging."""
+        n = h_in.shape[1] if n_samp is None else int(n_samp)
+        check(self._lib.dd_run_host(self._h, h_in.data_ptr(), h_in.stride(0), n,
+                                    h_out.data_ptr(), d_in_stage.data_ptr(),
+                                    d_out_stage.data_ptr(), _stream_ptr(stream)))
+
+    def _check_input(self, x):
+        import torch
+        want = getattr(torch, _TORCH_DTYPE_NAMES[self.dtype])
+        if x.dtype != want:
+            raise TypeError(f"plan dtype {self.dtype} needs {want}, got {x.dtype}")
+        if x.dim() != 2 or x.shape[0] != self.n_chan or x.stride(1) != 1:
+            raise ValueError("x must be [n_chan][n_samp] with a contiguous time axis")
+        if not x.is_cuda:
+            raise ValueError("x must be a cuda tensor")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

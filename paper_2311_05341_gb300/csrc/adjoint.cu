@@ -1,0 +1,153 @@
+// adjoint.cu -- transpose of the forward transform for float32 plans
+// (re-dispersion), written as a gather so that no atomics are needed:
+//
+//   xbar[c][t] = sum_r sum_d ybar_r[d][floor(t / b_r) - s_r(c, d)]
+//
+// over the terms with 0 <= floor(t/b_r) - s_r(c, d) < n_out_r.  Every input
+// sample X[c][t] enters output Y_r[d][floor(t/b_r) - s_r(c,d)] with weight 1
+// (Eq. 3 with time binning), so this is exactly the derivative of Eq. 3 with
+// respect to X.  The paper has no adjoint; this mirrors its forward tiling with
+// the roles of channel and DM swapped: a CTA owns 8 channels x 256 raw
+// samples, and for each chunk of DMs it stages the needed window of each DM's
+// output row in shared memory, then every thread gathers from it at its
+// channel's offset.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+constexpr int kAdjChan = 8;        // channels per CTA (one per warp row)
+constexpr int kAdjSampPerThread = 8;
+constexpr int kAdjTile = 32 * kAdjSampPerThread;  // raw samples per CTA
+constexpr int kAdjDmChunk = 32;
+
+struct AdjRange {
+  const int32_t* shifts;  // [n_dm][n_chan]
+  const float* ybar;      // this range's plane [n_dm][n_out]
+  int32_t n_dm;
+  int32_t bin;
+  int64_t n_out;
+  int32_t win;            // staged window length per DM
+};
+
+struct AdjParams {
+  AdjRange r[DD_MAX_RANGES];
+  int32_t n_ranges;
+  int32_t n_chan;
+  int64_t n_samp;
+  int64_t stride;
+  int32_t max_win;
+};
+
+__global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams prm, float* __restrict__ xbar) {
+  extern __shared__ unsigned char smem_raw[];
+  float* win_buf = reinterpret_cast<float*>(smem_raw);                      // [chunk][max_win]
+  int32_t* sh_buf = reinterpret_cast<int32_t*>(win_buf + kAdjDmChunk * prm.max_win);  // [chunk][8]
+  int32_t* hi_buf = sh_buf + kAdjDmChunk * kAdjChan;                        // [chunk]
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int32_t n_cblk = (prm.n_chan + kAdjChan - 1) / kAdjChan;
+  const int64_t tile = blockIdx.x / n_cblk;
+  const int32_t c_first = (blockIdx.x % n_cblk) * kAdjChan;
+  const int32_t c = min(c_first + ty, prm.n_chan - 1);
+  const int64_t t_raw0 = tile * kAdjTile;
+
+  float acc[kAdjSampPerThread];
+#pragma unroll
+  for (int k = 0; k < kAdjSampPerThread; ++k) acc[k] = 0.f;
+
+  for (int32_t ri = 0; ri < prm.n_ranges; ++ri) {
+    const AdjRange rr = prm.r[ri];
+    const int64_t u0 = t_raw0 / rr.bin;  // first decimated sample of the tile
+    int32_t rel[kAdjSampPerThread];      // decimated offset of each of my samples
+#pragma unroll
+    for (int k = 0; k < kAdjSampPerThread; ++k)
+      rel[k] = static_cast<int32_t>((t_raw0 + tx + 32 * k) / rr.bin - u0);
+
+    for (int32_t d0 = 0; d0 < rr.n_dm; d0 += kAdjDmChunk) {
+      const int32_t nd = min(kAdjDmChunk, rr.n_dm - d0);
+      __syncthreads();
+      // Shifts of the chunk's DMs for the CTA's channels and their maximum.
+      for (int32_t dd = ty; dd < nd; dd += 8) {
+        const int32_t d = d0 + dd;
+        int32_t s = -0x7fffffff;
+        if (tx < kAdjChan) {
+          const int32_t cc = min(c_first + tx, prm.n_chan - 1);
+          s = rr.shifts[static_cast<int64_t>(d) * prm.n_chan + cc];
+          sh_buf[dd * kAdjChan + tx] = s;
+        }
+        const int32_t hi = __reduce_max_sync(0xffffffffu, s);
+        if (tx == 0) hi_buf[dd] = hi;
+        // Window of output row d: ybar[d][u0 - hi + k], k < win (0 outside [0, n_out)).
+        const float* yrow = rr.ybar + static_cast<int64_t>(d) * rr.n_out;
+        for (int32_t k = tx; k < rr.win; k += 32) {
+          const int64_t u = u0 - hi + k;
+          win_buf[dd * prm.max_win + k] = (u >= 0 && u < rr.n_out) ? yrow[u] : 0.f;
+        }
+      }
+      __syncthreads();
+      for (int32_t dd = 0; dd < nd; ++dd) {
+        const int32_t off = hi_buf[dd] - sh_buf[dd * kAdjChan + ty];
+        const float* w = win_buf + dd * prm.max_win + off;
+#pragma unroll
+        for (int k = 0; k < kAdjSampPerThread; ++k) acc[k] += w[rel[k]];
+      }
+    }
+  }
+
+  if (c_first + ty < prm.n_chan) {
+    float* xrow = xbar + static_cast<int64_t>(c) * prm.stride;
+#pragma unroll
+    for (int k = 0; k < kAdjSampPerThread; ++k) {
+      const int64_t t = t_raw0 + tx + 32 * k;
+      if (t < prm.n_samp) xrow[t] = acc[k];
+    }
+  }
+}
+
+}  // namespace
+
+int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
+                   int64_t stride, const int64_t* n_out, const int64_t* out_off,
+                   void* stream) {
+  AdjParams prm{};
+  prm.n_ranges = static_cast<int32_t>(p->ranges.size());
+  prm.n_chan = p->n_chan;
+  prm.n_samp = n_samp;
+  prm.stride = stride;
+  int32_t max_win = 1;
+  for (int32_t i = 0; i < prm.n_ranges; ++i) {
+    const RangePlan& rp = p->ranges[i];
+    AdjRange& a = prm.r[i];
+    a.shifts = reinterpret_cast<const int32_t*>(static_cast<const unsigned char*>(p->d_ws) +
+                                                rp.off_shifts);
+    a.ybar = d_ybar + out_off[i];
+    a.n_dm = static_cast<int32_t>(rp.n_dm);
+    a.bin = rp.r.bin;
+    a.n_out = n_out[i];
+    // Decimated samples touched by one tile, plus the channel-block span.
+    a.win = kAdjTile / rp.r.bin + 2 + rp.adj_span;
+    max_win = std::max(max_win, a.win);
+  }
+  prm.max_win = max_win;
+  const size_t smem = static_cast<size_t>(kAdjDmChunk) * max_win * sizeof(float) +
+                      static_cast<size_t>(kAdjDmChunk) * (kAdjChan + 1) * sizeof(int32_t);
+  if (smem > 200 * 1024) return static_cast<int>(cudaErrorInvalidConfiguration);
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  const int32_t n_cblk = (p->n_chan + kAdjChan - 1) / kAdjChan;
+  const int64_t tiles = (n_samp + kAdjTile - 1) / kAdjTile;
+  const int64_t grid = tiles * n_cblk;
+  if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  adjoint_kernel<<<static_cast<unsigned>(grid), dim3(32, 8), smem,
+                   static_cast<cudaStream_t>(stream)>>>(prm, d_xbar);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace dd

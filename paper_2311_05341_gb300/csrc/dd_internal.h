@@ -1,0 +1,73 @@
+// dd_internal.h -- host-side plan representation and kernel launch interfaces
+// shared by the translation units of libdd (planner, kernels, C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dd.h"
+
+namespace dd {
+
+// Dispersion constant of the cold-plasma delay law (Eq. 1), MHz^2 s pc^-1 cm^3.
+constexpr double kDispersionConstant = 4148.808;
+
+// Tile of the generic forward kernel: DMs per CTA (8 warps x kGenDmPerThread).
+constexpr int kGenDmPerThread = 2;
+constexpr int kGenSampPerThread = 8;
+constexpr int kGenDmPerCta = 8 * kGenDmPerThread;
+constexpr int kGenSampPerCta = 32 * kGenSampPerThread;
+
+struct RangePlan {
+  dd_range r{};
+  int64_t n_dm = 0;
+  int32_t s_max = 0;
+  std::vector<int32_t> shifts;  // [n_dm][n_chan]
+
+  // Generic kernel blocking.
+  int32_t gen_n_blocks = 0;     // DM blocks of kGenDmPerCta
+  int32_t gen_span = 0;         // max over blocks/channels of in-block shift span
+
+  // Adjoint blocking: max over channel blocks and DMs of the in-block span.
+  int32_t adj_span = 0;
+
+  // Byte offsets of the device tables inside the workspace.
+  size_t off_shifts = 0;        // int32 [n_dm][n_chan]
+};
+
+}  // namespace dd
+
+struct dd_plan_s {
+  int32_t n_chan = 0;
+  double f_ref = 0.0;
+  double t_samp = 0.0;
+  dd_dtype dtype = DD_U8;
+  std::vector<double> freqs;
+  std::vector<double> k;  // delay coefficient per channel [s per unit DM]
+  std::vector<dd::RangePlan> ranges;
+  std::vector<unsigned char> host_ws;  // staged device tables
+  void* d_ws = nullptr;                // bound device workspace (caller-owned)
+  size_t ws_bytes = 0;
+};
+
+namespace dd {
+
+// Thread-local error detail helpers (api.cu).
+dd_status fail(dd_status st, const std::string& detail);
+dd_status cuda_fail(int err, const char* what);
+
+// Planner (plan.cpp).
+dd_status build_plan(dd_plan_s* p);
+int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
+
+// Kernel launchers (return a cudaError_t as int; 0 on success).
+int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
+                           int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
+                           void* stream);
+int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
+                   int64_t stride, const int64_t* n_out, const int64_t* out_off,
+                   void* stream);
+
+}  // namespace dd

@@ -1,0 +1,114 @@
+// plan.cpp -- host planner: per-channel delay coefficients and integer shift
+// tables in FP64, DM blocking and the device workspace layout.
+//
+// The shift of channel c at trial DM_d of a range with time bin b is
+//   s(c, d) = floor(DM_d * k_c / (b * t_samp) + 0.5),
+//   k_c     = C_DM * (1/f_c^2 - 1/f_ref^2)              (Eq. 1, Eq. 7 form),
+//   DM_d    = lo + d * step                             (fixed step, Table 2),
+// evaluated in exactly this order in FP64.  This file is compiled with
+// -ffp-contract=off so no multiply-add is fused: the table must not depend on
+// the host CPU.  The kernels never evaluate the delay law; they read the
+// precomputed integer shifts, like the paper's precomputed Delta t_pc array
+// (Sec. 4.1) but resolved to integers on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Delay of one (channel, DM) in decimated samples, before rounding.
+double delay_samples(double dm, double k_c, int32_t bin, double t_samp) {
+  double delay = dm * k_c;
+  double tick = static_cast<double>(bin) * t_samp;
+  return delay / tick;
+}
+
+// Max over DM blocks of `per_block` DMs and over channels of the in-block span
+// s(c, last DM of block) - s(c, first DM of block).
+int32_t block_span(const RangePlan& rp, int32_t n_chan, int32_t per_block) {
+  int32_t span = 0;
+  for (int64_t d0 = 0; d0 < rp.n_dm; d0 += per_block) {
+    int64_t d1 = std::min<int64_t>(d0 + per_block, rp.n_dm) - 1;
+    const int32_t* a = &rp.shifts[static_cast<size_t>(d0) * n_chan];
+    const int32_t* b = &rp.shifts[static_cast<size_t>(d1) * n_chan];
+    for (int32_t c = 0; c < n_chan; ++c) span = std::max(span, b[c] - a[c]);
+  }
+  return span;
+}
+
+}  // namespace
+
+int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp) {
+  (void)p;
+  return n_samp / rp.r.bin - rp.s_max;
+}
+
+dd_status build_plan(dd_plan_s* p) {
+  const int32_t n_chan = p->n_chan;
+  p->k.resize(n_chan);
+  const double inv_ref2 = 1.0 / (p->f_ref * p->f_ref);
+  for (int32_t c = 0; c < n_chan; ++c) {
+    double f = p->freqs[c];
+    double inv_f2 = 1.0 / (f * f);
+    p->k[c] = kDispersionConstant * (inv_f2 - inv_ref2);
+  }
+
+  size_t ws = 0;
+  for (auto& rp : p->ranges) {
+    rp.n_dm = std::llround((rp.r.dm_hi - rp.r.dm_lo) / rp.r.dm_step);
+    if (rp.n_dm <= 0 || rp.n_dm > (int64_t{1} << 24))
+      return fail(DD_ERR_INVALID_ARG, "range has no trial DMs or too many (max 2^24)");
+    rp.shifts.resize(static_cast<size_t>(rp.n_dm) * n_chan);
+    int32_t smax = 0;
+    for (int64_t d = 0; d < rp.n_dm; ++d) {
+      double dm = rp.r.dm_lo + static_cast<double>(d) * rp.r.dm_step;
+      int32_t* row = &rp.shifts[static_cast<size_t>(d) * n_chan];
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double x = delay_samples(dm, p->k[c], rp.r.bin, p->t_samp);
+        if (!(x < 1.0e9)) return fail(DD_ERR_INVALID_ARG, "shift exceeds 1e9 samples");
+        int32_t s = static_cast<int32_t>(std::floor(x + 0.5));  // round half up
+        row[c] = s;
+        smax = std::max(smax, s);
+      }
+    }
+    rp.s_max = smax;
+    rp.gen_n_blocks = static_cast<int32_t>((rp.n_dm + kGenDmPerCta - 1) / kGenDmPerCta);
+    rp.gen_span = block_span(rp, n_chan, kGenDmPerCta);
+
+    // Adjoint: channel blocks of 8 (one warp row each), span over the block for
+    // each DM: s(last channel) - s(first channel) with shifts non-decreasing
+    // towards lower frequency; take the true max/min to allow any order.
+    int32_t aspan = 0;
+    for (int64_t d = 0; d < rp.n_dm; ++d) {
+      const int32_t* row = &rp.shifts[static_cast<size_t>(d) * n_chan];
+      for (int32_t c0 = 0; c0 < n_chan; c0 += 8) {
+        int32_t lo = row[c0], hi = row[c0];
+        for (int32_t c = c0; c < std::min(c0 + 8, n_chan); ++c) {
+          lo = std::min(lo, row[c]);
+          hi = std::max(hi, row[c]);
+        }
+        aspan = std::max(aspan, hi - lo);
+      }
+    }
+    rp.adj_span = aspan;
+
+    ws = align_up(ws, 256);
+    rp.off_shifts = ws;
+    ws += rp.shifts.size() * sizeof(int32_t);
+  }
+  p->ws_bytes = align_up(ws, 256);
+  p->host_ws.assign(p->ws_bytes, 0);
+  for (auto& rp : p->ranges) {
+    std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
+                rp.shifts.size() * sizeof(int32_t));
+  }
+  return DD_OK;
+}
+
+}  // namespace dd

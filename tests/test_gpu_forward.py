@@ -1,0 +1,176 @@
+"""Parity of the CUDA forward transform (through the C ABI) with the oracle.
+
+Integer inputs: bit-exact.  Float inputs: |err| <= 1e-5 * sum_c |X| per
+output against the FP64 oracle.  Small cases compare every output (several
+CTA tiles, ragged tails, odd channel counts, bins, several ranges); the
+paper-scale workloads compare sampled rows and windows plus properties that
+hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2311_05341_gb300 as dd
+from synth import workloads, channel_freqs, filterbank
+
+from gpu_util import assert_float_parity, oracle_input
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu_planes(beam_like, x_np, ranges=None, dtype=None, row_stride=None):
+    b = beam_like
+    plan = dd.Plan(b.freqs, b.f_high, b.t_samp, ranges or b.ranges, dtype or b.dtype)
+    x = torch.from_numpy(x_np).cuda()
+    n = x_np.shape[1] if row_stride is None else b.n_samp
+    planes = plan.run(x, n_samp=n)
+    torch.cuda.synchronize()
+    return [p.cpu().numpy() for p in planes]
+
+
+def test_tiny_u8_full_plane():
+    beam = workloads.tiny_u8()
+    x, tables, n_dm, n_out = oracle_input(beam)
+    ref = oracle.forward(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges)
+    got = gpu_planes(beam, x)
+    assert got[0].dtype == np.int32
+    np.testing.assert_array_equal(got[0], ref[0])
+    # The injected DM = 30 pulse peaks at its trial.
+    d, t0 = 60, 3000
+    assert np.argmax(got[0][:, t0:t0 + 4].sum(1)) == d
+
+
+class _Beam:
+    def __init__(self, freqs, f_high, t_samp, ranges, dtype, n_samp):
+        self.freqs, self.f_high, self.t_samp = freqs, f_high, t_samp
+        self.ranges, self.dtype, self.n_samp = ranges, dtype, n_samp
+
+
+def _random_case(seed):
+    rng = np.random.default_rng(seed)
+    n_chan = int(rng.choice([1, 3, 31, 33, 64, 130, 257]))
+    f_high = float(rng.uniform(300, 1700))
+    bw = float(rng.uniform(0.05, 0.4)) * f_high
+    freqs = channel_freqs(f_high, bw, n_chan)
+    t_samp = float(rng.choice([64e-6, 128e-6, 327.68e-6, 1e-3]))
+    dtype = ["u8", "u16", "f32"][seed % 3]
+    ranges, lo = [], 0.0
+    for _ in range(int(rng.integers(1, 4))):
+        step = float(rng.choice([0.05, 0.1, 0.5, 2.0]))
+        n = int(rng.integers(1, 70))
+        ranges.append((lo, lo + n * step, step, int(rng.choice([1, 2, 3, 4, 8]))))
+        lo += n * step
+    smax = 0
+    for r in ranges:
+        s, _ = oracle.extent(freqs, f_high, t_samp, r, 10 ** 9)
+        smax = max(smax, (s + 1) * r[3])
+    n_samp = int(smax + rng.integers(1, 3000))
+    return _Beam(freqs, f_high, t_samp, ranges, dtype, n_samp), rng
+
+
+@pytest.mark.parametrize("seed", range(18))
+def test_random_cases_full_planes(seed):
+    b, rng = _random_case(seed)
+    npdt = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32}[b.dtype]
+    mean, sd = {"u8": (128, 40), "u16": (32768, 9000), "f32": (0.0, 1.0)}[b.dtype]
+    x = filterbank(npdt, len(b.freqs), b.n_samp, 7000 + seed, mean, sd)
+    ref = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges)
+    got = gpu_planes(b, x)
+    assert len(got) == len(ref)
+    for r, (g, o) in enumerate(zip(got, ref)):
+        assert g.shape == o.shape
+        if b.dtype == "f32":
+            ab = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges, take_abs=True)[r]
+            assert_float_parity(g, o, ab, f"range {r}")
+        else:
+            np.testing.assert_array_equal(g, o, err_msg=f"range {r}")
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_minimal_output_length(dtype):
+    """n_samp = S_max + 1: exactly one output sample per trial."""
+    freqs = channel_freqs(1400.0, 300.0, 40)
+    r = (0.0, 25.0, 0.5, 1)
+    s_max, _ = oracle.extent(freqs, 1400.0, 64e-6, r, 10 ** 6)
+    n_samp = s_max + 1
+    npdt = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32}[dtype]
+    x = filterbank(npdt, 40, n_samp, 11, 100, 30)
+    b = _Beam(freqs, 1400.0, 64e-6, [r], dtype, n_samp)
+    ref = oracle.forward(x, freqs, 1400.0, 64e-6, [r])[0]
+    got = gpu_planes(b, x)[0]
+    assert got.shape == (50, 1)
+    if dtype == "f32":
+        ab = oracle.forward(x, freqs, 1400.0, 64e-6, [r], take_abs=True)[0]
+        assert_float_parity(got, ref, ab)
+    else:
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_padded_row_stride_ignores_padding():
+    freqs = channel_freqs(1400.0, 300.0, 48)
+    r = (0.0, 30.0, 0.25, 2)
+    n_samp, stride = 3001, 3072
+    x = filterbank(np.uint8, 48, n_samp, 5, 128, 16, row_stride=stride)
+    x[:, n_samp:] = 255  # garbage the transform must never read
+    ref = oracle.forward(np.ascontiguousarray(x[:, :n_samp]), freqs, 1400.0, 64e-6, [r])[0]
+    plan = dd.Plan(freqs, 1400.0, 64e-6, [r], "u8")
+    xt = torch.from_numpy(x).cuda()
+    got = plan.run(xt, n_samp=n_samp)[0].cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_too_short_input_raises():
+    freqs = channel_freqs(1400.0, 300.0, 16)
+    plan = dd.Plan(freqs, 1400.0, 64e-6, [(0.0, 500.0, 1.0, 1)], "u8")
+    x = torch.zeros((16, 64), dtype=torch.uint8, device="cuda")
+    with pytest.raises(dd.DDError) as ei:
+        plan.run(x)
+    assert ei.value.status == 3  # DD_ERR_SHAPE
+
+
+def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
+    """Compare sampled full rows and windows of a large plane with the oracle."""
+    r = 0
+    rows_full = sorted(set(list(range(0, n_dm[r], 256)) + [n_dm[r] - 1] + pulse_rows))
+    got = planes_gpu[r][torch.tensor(rows_full, device="cuda")].cpu().numpy()
+    ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[r],
+                              rows_full)
+    np.testing.assert_array_equal(got, ref)
+    # Random rows on windows (including the ragged last tile).
+    rows = rng.integers(0, n_dm[r], 96)
+    for t_lo in [0, int(rng.integers(0, n_out[r] - 2048)), n_out[r] - 1500]:
+        t_hi = min(t_lo + 2048, n_out[r])
+        g = planes_gpu[r][torch.tensor(rows, device="cuda"), t_lo:t_hi].cpu().numpy()
+        o = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[r], rows,
+                                t_lo, t_hi)
+        np.testing.assert_array_equal(g, o)
+
+
+@pytest.mark.parametrize("make", [workloads.paper_u8, workloads.paper_u16],
+                         ids=["paper_u8", "paper_u16"])
+def test_paper_scale_sampled(make):
+    beam = make()
+    x, tables, n_dm, n_out = oracle_input(beam)
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
+    xt = torch.from_numpy(x).cuda()
+    planes = plan.run(xt)
+    torch.cuda.synchronize()
+    assert planes[0].shape == (n_dm[0], n_out[0])
+    pulses = workloads.resolve_pulses(beam, n_dm, n_out)
+    _sampled_parity(beam, x, planes, n_dm, n_out, [p[1] for p in pulses],
+                    np.random.default_rng(9))
+    # DM 0 is the plain channel sum at any size.
+    dm0 = xt.to(torch.int64).sum(0)[: n_out[0]].to(torch.int32)
+    assert torch.equal(planes[0][0], dm0)
+    # Every injected pulse peaks at its own trial among its neighbours.
+    for _, d, t0, w in pulses:
+        lo, hi = max(d - 20, 0), min(d + 21, n_dm[0])
+        seg = planes[0][lo:hi, t0:t0 + w].to(torch.int64).sum(1)
+        assert int(torch.argmax(seg)) + lo == d

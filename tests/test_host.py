@@ -1,0 +1,137 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load, export every entry point the public headers declare,
+plan exactly the oracle's shift tables for every workload, and reject bad
+arguments with the documented status codes.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2311_05341_gb300 as dd
+from paper_2311_05341_gb300 import _lib
+from synth import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(dd_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    declared = _declared_functions()
+    assert {"dd_plan_create", "dd_run", "dd_run_adjoint"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(_lib.SIGNATURES) >= declared
+
+
+def test_status_strings():
+    lib = _lib.load()
+    for code, name in [(0, "DD_OK"), (1, "DD_ERR_INVALID_ARG"), (2, "DD_ERR_UNSUPPORTED"),
+                       (3, "DD_ERR_SHAPE"), (4, "DD_ERR_BUDGET"), (5, "DD_ERR_CUDA"),
+                       (6, "DD_ERR_TIMEOUT")]:
+        assert lib.dd_status_string(code).decode() == name
+
+
+def _beams():
+    return [workloads.tiny_u8(), workloads.paper_u8(), workloads.diff_f32(),
+            workloads.batched()[0], workloads.batched()[24], workloads.batched()[32],
+            workloads.stream_beam(0, 65536 + 24632)]
+
+
+@pytest.mark.parametrize("beam", _beams(), ids=lambda b: b.name)
+def test_plan_tables_equal_oracle(oracle_mod, beam):
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype, upload=False)
+    info = plan.info(beam.n_samp)
+    for r, rng in enumerate(beam.ranges):
+        ref = oracle_mod.shift_table(beam.freqs, beam.f_high, beam.t_samp, rng)
+        got = plan.shifts(r)
+        assert got.shape == ref.shape
+        assert np.array_equal(got, ref), f"range {r}"
+        s_max, n_out = oracle_mod.extent(beam.freqs, beam.f_high, beam.t_samp, rng, beam.n_samp)
+        assert info["s_max"][r] == s_max
+        assert info["n_out"][r] == n_out
+        assert info["n_dm"][r] == oracle_mod.n_dm(rng)
+
+
+def test_plan_info_layout():
+    beam = workloads.stream_beam(0, 65536 + 24632)
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype, upload=False)
+    info = plan.info(beam.n_samp)
+    off = 0
+    for r in range(4):
+        assert info["out_offset"][r] == off
+        off += info["n_dm"][r] * info["n_out"][r]
+    assert info["out_elems"] == off
+    assert info["n_dm"] == [1500, 750, 1400, 1000]
+    raw = max((s + 1) * rr[3] - 1 for s, rr in zip(info["s_max"], beam.ranges))
+    assert info["max_delay_raw"] == raw
+
+
+def _create(freqs, f_ref, ts, ranges, dtype=_lib.DD_U8):
+    lib = _lib.load()
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    arr = (_lib.Range * max(len(ranges), 1))(*[_lib.Range(*r) for r in ranges])
+    h = ctypes.c_void_p()
+    st = lib.dd_plan_create(f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), f.size, f_ref, ts,
+                            arr, len(ranges), dtype, ctypes.byref(h))
+    if st == 0:
+        lib.dd_plan_destroy(h)
+    return st
+
+
+@pytest.mark.parametrize("args", [
+    ([1400.0, 1300.0], 1400.0, 0.0, [(0.0, 10.0, 1.0, 1)]),        # t_samp = 0
+    ([1400.0, 1500.0], 1400.0, 1e-4, [(0.0, 10.0, 1.0, 1)]),       # f > f_ref
+    ([1400.0, -1.0], 1400.0, 1e-4, [(0.0, 10.0, 1.0, 1)]),         # f <= 0
+    ([1400.0], 1400.0, 1e-4, [(0.0, 10.0, 0.0, 1)]),               # step 0
+    ([1400.0], 1400.0, 1e-4, [(10.0, 10.0, 1.0, 1)]),              # empty range
+    ([1400.0], 1400.0, 1e-4, [(0.0, 10.0, 1.0, 0)]),               # bin 0
+    ([1400.0], 1400.0, 1e-4, [(-5.0, 10.0, 1.0, 1)]),              # negative DM
+    ([1400.0], 1400.0, 1e-4, []),                                  # no ranges
+    ([1400.0], 1400.0, 1e-4, [(0.0, 1.0, 1.0, 1)] * 17),           # too many ranges
+])
+def test_plan_create_rejects_bad_arguments(args):
+    assert _create(*args) == _lib.DD_ERR_INVALID_ARG
+
+
+def test_plan_create_rejects_bad_dtype():
+    assert _create([1400.0], 1400.0, 1e-4, [(0.0, 1.0, 1.0, 1)], dtype=9) == _lib.DD_ERR_INVALID_ARG
+
+
+def test_null_and_shape_errors():
+    lib = _lib.load()
+    assert lib.dd_plan_query(None, 10, None) == _lib.DD_ERR_INVALID_ARG
+    assert lib.dd_run(None, None, 0, 0, None, None) == _lib.DD_ERR_INVALID_ARG
+    plan = dd.Plan([1400.0, 1300.0], 1400.0, 1e-4, [(0.0, 10.0, 1.0, 1)], "u8", upload=False)
+    # No workspace bound yet.
+    assert lib.dd_run(plan.handle, 16, 64, 64, 16, None) == _lib.DD_ERR_INVALID_ARG
+    # Workspace too small / misaligned (checked before any device call).
+    assert lib.dd_plan_upload(plan.handle, 16, 0, None) == _lib.DD_ERR_BUDGET
+    nb = plan.info(0)["workspace_bytes"]
+    assert lib.dd_plan_upload(plan.handle, 8, nb, None) == _lib.DD_ERR_SHAPE
+    assert lib.dd_plan_shifts(plan.handle, 3, None) == _lib.DD_ERR_INVALID_ARG
+    u16 = dd.Plan([1400.0], 1400.0, 1e-4, [(0.0, 10.0, 1.0, 1)], "u16", upload=False)
+    assert lib.dd_run_adjoint(u16.handle, 16, 16, 64, 64, None) == _lib.DD_ERR_UNSUPPORTED
+    msg = lib.dd_last_error_detail().decode()
+    assert "float32" in msg
+
+
+def test_too_short_input_is_reported():
+    plan = dd.Plan(workloads.tiny_u8().freqs, 1500.0, 64e-6, [(0.0, 64.0, 0.5, 1)], "u8",
+                   upload=False)
+    info = plan.info(100)
+    assert info["n_out"][0] <= 0
