@@ -83,7 +83,12 @@ typedef struct {
   int64_t out_elems;                  /* total output elements */
   int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
+  int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
 } dd_plan_info;
+
+/* Forward kernels a range can run on (dd_plan_info.kernel). */
+#define DD_KERNEL_GENERIC 1  /* shared-memory staged, any dtype and bin */
+#define DD_KERNEL_U8_TILED 2 /* uint8, bin 1: packed 16-bit lanes, register reuse */
 
 /*
  * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
@@ -148,6 +153,14 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
  */
 dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
                          int64_t xbar_row_stride, void* stream);
+
+/*
+ * Device status of a plan's earlier runs: synchronises `stream`, then returns
+ * DD_ERR_TIMEOUT (and clears the flag) if a kernel of this plan gave up a
+ * bounded wait since the last call, DD_OK otherwise.  Kernels never trap or
+ * spin forever; a timeout leaves that run's output undefined.
+ */
+dd_status dd_plan_device_status(dd_plan plan, void* stream);
 
 /*
  * End-to-end forward from HOST buffers: copies h_in (pinned host memory,

@@ -88,6 +88,7 @@ class Plan:
             "out_offset": [inf.out_offset[i] for i in range(n)],
             "out_elems": inf.out_elems, "n_dm_total": inf.n_dm_total,
             "max_delay_raw": inf.max_delay_raw, "workspace_bytes": inf.workspace_bytes,
+            "kernel": [{1: "generic", 2: "u8_tiled"}[inf.kernel[i]] for i in range(n)],
         }
 
     def shifts(self, r: int = 0) -> np.ndarray:

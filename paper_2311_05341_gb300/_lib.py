@@ -18,6 +18,7 @@ DD_OK, DD_ERR_INVALID_ARG, DD_ERR_UNSUPPORTED, DD_ERR_SHAPE = 0, 1, 2, 3
 DD_ERR_BUDGET, DD_ERR_CUDA, DD_ERR_TIMEOUT = 4, 5, 6
 DD_U8, DD_U16, DD_F32 = 1, 2, 3
 DD_MAX_RANGES = 16
+DD_KERNEL_GENERIC, DD_KERNEL_U8_TILED = 1, 2
 
 
 class DDError(RuntimeError):
@@ -43,7 +44,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_out", ctypes.c_int64 * DD_MAX_RANGES),
                 ("out_offset", ctypes.c_int64 * DD_MAX_RANGES),
                 ("out_elems", ctypes.c_int64), ("max_delay_raw", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t),
+                ("kernel", ctypes.c_int32 * DD_MAX_RANGES)]
 
 
 # name -> (restype, argtypes) for every exported entry point.
@@ -58,6 +60,7 @@ SIGNATURES = {
     "dd_plan_upload": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "dd_run": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP]),
+    "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
     "dd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dd_last_error_detail": (ctypes.c_char_p, []),

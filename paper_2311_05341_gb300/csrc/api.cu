@@ -47,6 +47,7 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     o->out_offset[i] = off;
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
+    o->kernel[i] = rp.u8_ok ? DD_KERNEL_U8_TILED : DD_KERNEL_GENERIC;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
     if (raw > o->max_delay_raw) o->max_delay_raw = raw;
   }
@@ -179,8 +180,11 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
   const size_t osz = 4;
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
     void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
-    int e = launch_forward_generic(plan, plan->ranges[i], d_in, in_row_stride, n_samp,
-                                   info.n_out[i], o, stream);
+    const RangePlan& rp = plan->ranges[i];
+    int e = rp.u8_ok ? launch_forward_u8(plan, rp, d_in, in_row_stride, n_samp, info.n_out[i], o,
+                                         stream)
+                     : launch_forward_generic(plan, rp, d_in, in_row_stride, n_samp,
+                                              info.n_out[i], o, stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
   return DD_OK;
@@ -195,6 +199,23 @@ dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64
   int e = launch_adjoint(plan, d_ybar, d_xbar, n_samp, xbar_row_stride, info.n_out,
                          info.out_offset, stream);
   if (e != 0) return cuda_fail(e, "dd_run_adjoint launch");
+  return DD_OK;
+}
+
+dd_status dd_plan_device_status(dd_plan plan, void* stream) {
+  if (!plan || !plan->d_ws) return fail(DD_ERR_INVALID_ARG, "plan has no uploaded workspace");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, plan->d_ws, sizeof(word), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_plan_device_status");
+  if (word != 0) {
+    const int32_t zero = 0;
+    e = cudaMemcpyAsync(plan->d_ws, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_plan_device_status reset");
+    return fail(DD_ERR_TIMEOUT, "a bounded device wait gave up during an earlier run");
+  }
   return DD_OK;
 }
 

@@ -33,8 +33,16 @@ struct RangePlan {
   // Adjoint blocking: max over channel blocks and DMs of the in-block span.
   int32_t adj_span = 0;
 
+  // Register-tiled uint8 kernel (fwd_u8.cu), used when u8_ok.
+  bool u8_ok = false;
+  int32_t u8_n_blocks = 0;      // DM blocks of u8k::kDmCta
+  int32_t u8_lp = 0;            // paired words per staged channel window
+  uint32_t u8_units_magic = 0;  // division by u8_lp / 4 (see fwd_u8.h)
+  int32_t u8_units_shift = 0;
+
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
+  size_t off_u8_recs = 0;       // u8k::Rec [u8_n_blocks][n_chan]
 };
 
 }  // namespace dd
@@ -66,6 +74,9 @@ int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
 int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                            int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
                            void* stream);
+int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
+                      int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
+                      void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);

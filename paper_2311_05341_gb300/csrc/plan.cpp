@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "dd_internal.h"
+#include "fwd_u8.h"
 
 namespace dd {
 
@@ -42,6 +43,64 @@ int32_t block_span(const RangePlan& rp, int32_t n_chan, int32_t per_block) {
   return span;
 }
 
+// Records of the register-tiled uint8 kernel.  For DM block b (first DM d0),
+// channel c and warp w (DMs d0 + 8w + i, i < 8, clamped to the last DM):
+//   base  = s(c, d0),  m = base mod 16 (the TMA copy starts 16-byte aligned),
+//   D_i   = s(c, d0 + 8w + i) - base + m   (word offset inside the staged window),
+//   a_w   = 4 * floor(D_0 / 4)              (16-byte aligned window start),
+//   off_i = D_i - a_w                        (must fit in 4 bits).
+// Returns false if some offset does not fit, leaving the plan on the generic kernel.
+bool build_u8_records(RangePlan& rp, int32_t n_chan, std::vector<u8k::Rec>& recs) {
+  using namespace u8k;
+  const int64_t n_blocks = (rp.n_dm + kDmCta - 1) / kDmCta;
+  recs.assign(static_cast<size_t>(n_blocks) * n_chan, u8k::Rec{});
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    const int64_t d0 = b * kDmCta;
+    for (int32_t c = 0; c < n_chan; ++c) {
+      u8k::Rec& r = recs[static_cast<size_t>(b) * n_chan + c];
+      const int32_t base = rp.shifts[static_cast<size_t>(d0) * n_chan + c];
+      const int32_t m = base & 15;
+      r.base = base;
+      for (int w = 0; w < kWarps; ++w) {
+        int32_t a_w = 0;
+        uint32_t packed = 0;
+        for (int i = 0; i < kDR; ++i) {
+          const int64_t d = std::min<int64_t>(d0 + w * kDR + i, rp.n_dm - 1);
+          const int32_t D = rp.shifts[static_cast<size_t>(d) * n_chan + c] - base + m;
+          if (i == 0) a_w = (D >> 2) << 2;
+          const int32_t off = D - a_w;
+          if (off < 0 || off > kMaxOff) return false;
+          packed |= static_cast<uint32_t>(off) << (4 * i);
+        }
+        if ((a_w >> 2) > 255) return false;
+        r.delta[w] = packed;
+        r.aq[w] = static_cast<uint8_t>(a_w >> 2);
+      }
+    }
+  }
+  rp.u8_n_blocks = static_cast<int32_t>(n_blocks);
+  return true;
+}
+
+// Multiply-high constants for exact u / d with u < limit (verified exhaustively).
+bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift) {
+  int32_t s = 0;
+  while ((2u << s) <= d) ++s;  // s = floor(log2(d))
+  for (; s < 32; ++s) {
+    const uint64_t m = ((uint64_t{1} << (32 + s)) + d - 1) / d;
+    if (m > 0xffffffffull) break;
+    bool ok = true;
+    for (uint32_t u = 0; u < limit && ok; ++u)
+      ok = ((static_cast<uint64_t>(u) * m) >> (32 + s)) == u / d;
+    if (ok) {
+      *magic = static_cast<uint32_t>(m);
+      *shift = s;
+      return true;
+    }
+  }
+  return false;
+}
+
 }  // namespace
 
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp) {
@@ -59,7 +118,9 @@ dd_status build_plan(dd_plan_s* p) {
     p->k[c] = kDispersionConstant * (inv_f2 - inv_ref2);
   }
 
-  size_t ws = 0;
+  size_t ws = u8k::kStatusBytes;  // device status word(s) first
+  std::vector<std::vector<u8k::Rec>> u8_recs(p->ranges.size());
+  size_t ri = 0;
   for (auto& rp : p->ranges) {
     rp.n_dm = std::llround((rp.r.dm_hi - rp.r.dm_lo) / rp.r.dm_step);
     if (rp.n_dm <= 0 || rp.n_dm > (int64_t{1} << 24))
@@ -101,12 +162,39 @@ dd_status build_plan(dd_plan_s* p) {
     ws = align_up(ws, 256);
     rp.off_shifts = ws;
     ws += rp.shifts.size() * sizeof(int32_t);
+
+    // Register-tiled uint8 kernel: 8-bit input at time bin 1 whose per-warp DM
+    // offsets fit its 4-bit fields and whose window fits shared memory.
+    rp.u8_ok = false;
+    if (p->dtype == DD_U8 && rp.r.bin == 1) {
+      const int32_t span = block_span(rp, n_chan, u8k::kDmCta);
+      const int32_t lp = u8k::window_words(span);
+      uint32_t magic = 0;
+      int32_t shift = 0;
+      if (u8k::smem_bytes(lp) <= 227 * 1024 &&
+          division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(u8k::kNC * lp / 4),
+                         &magic, &shift) &&
+          build_u8_records(rp, n_chan, u8_recs[ri])) {
+        rp.u8_ok = true;
+        rp.u8_lp = lp;
+        rp.u8_units_magic = magic;
+        rp.u8_units_shift = shift;
+        ws = align_up(ws, 256);
+        rp.off_u8_recs = ws;
+        ws += u8_recs[ri].size() * sizeof(u8k::Rec);
+      }
+    }
+    ++ri;
   }
   p->ws_bytes = align_up(ws, 256);
   p->host_ws.assign(p->ws_bytes, 0);
-  for (auto& rp : p->ranges) {
+  for (size_t i = 0; i < p->ranges.size(); ++i) {
+    const RangePlan& rp = p->ranges[i];
     std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
                 rp.shifts.size() * sizeof(int32_t));
+    if (rp.u8_ok)
+      std::memcpy(p->host_ws.data() + rp.off_u8_recs, u8_recs[i].data(),
+                  u8_recs[i].size() * sizeof(u8k::Rec));
   }
   return DD_OK;
 }

@@ -25,12 +25,20 @@ def _need_cuda():
         pytest.skip("no CUDA device")
 
 
-def gpu_planes(beam_like, x_np, ranges=None, dtype=None, row_stride=None):
+def padded_device(x_np):
+    """Copy to the device with the row stride rounded up to 16 bytes."""
+    per = 16 // x_np.itemsize
+    stride = (x_np.shape[1] + per - 1) // per * per
+    x = torch.zeros((x_np.shape[0], stride), dtype=getattr(torch, str(x_np.dtype)),
+                    device="cuda")
+    x[:, : x_np.shape[1]] = torch.from_numpy(x_np).cuda()
+    return x
+
+
+def gpu_planes(beam_like, x_np, ranges=None, dtype=None):
     b = beam_like
     plan = dd.Plan(b.freqs, b.f_high, b.t_samp, ranges or b.ranges, dtype or b.dtype)
-    x = torch.from_numpy(x_np).cuda()
-    n = x_np.shape[1] if row_stride is None else b.n_samp
-    planes = plan.run(x, n_samp=n)
+    planes = plan.run(padded_device(x_np), n_samp=x_np.shape[1])
     torch.cuda.synchronize()
     return [p.cpu().numpy() for p in planes]
 
@@ -91,6 +99,47 @@ def test_random_cases_full_planes(seed):
             assert_float_parity(g, o, ab, f"range {r}")
         else:
             np.testing.assert_array_equal(g, o, err_msg=f"range {r}")
+
+
+def _tiled_case(seed):
+    """uint8 plans on the register-tiled kernel: shallow DM steps, ragged sizes."""
+    rng = np.random.default_rng(seed)
+    n_chan = int(rng.choice([1, 15, 17, 255, 256, 257, 300, 513]))
+    f_high = float(rng.uniform(800, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    t_samp = 64e-6
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / t_samp  # samples per unit DM
+    step = float(rng.uniform(0.2, 1.7)) / max(k_low, 1e-9)  # <= 1.7 samples per step
+    n_dm = int(rng.choice([1, 7, 63, 64, 65, 130]))
+    lo = float(rng.uniform(0, 50)) * step
+    r = (lo, lo + n_dm * step, step, 1)
+    s_max, _ = oracle.extent(freqs, f_high, t_samp, r, 10 ** 9)
+    n_samp = int(s_max + rng.choice([1, 1279, 1280, 1281, 5000]))
+    return _Beam(freqs, f_high, t_samp, [r], "u8", n_samp), rng
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_u8_tiled_full_planes(seed):
+    b, rng = _tiled_case(seed)
+    plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, "u8")
+    assert plan.info(b.n_samp)["kernel"] == ["u8_tiled"]
+    # Values up to 255 in every channel exercise the 16-bit lane bound (256 channels).
+    x = filterbank(np.uint8, len(b.freqs), b.n_samp, 8000 + seed, 200, 80)
+    ref = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges)
+    got = gpu_planes(b, x)
+    np.testing.assert_array_equal(got[0], ref[0])
+
+
+def test_u8_tiled_saturated_input():
+    """All samples 255: every 16-bit lane reaches 255 * 256 before widening."""
+    freqs = channel_freqs(1670.0, 320.0, 1000)
+    r = (0.0, 12.8, 0.1, 1)
+    s_max, _ = oracle.extent(freqs, 1670.0, 64e-6, r, 10 ** 9)
+    n_samp = s_max + 3000
+    x = np.full((1000, n_samp), 255, np.uint8)
+    b = _Beam(freqs, 1670.0, 64e-6, [r], "u8", n_samp)
+    got = gpu_planes(b, x)[0]
+    assert np.all(got == 255 * 1000)
 
 
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])

@@ -135,3 +135,18 @@ def test_too_short_input_is_reported():
                    upload=False)
     info = plan.info(100)
     assert info["n_out"][0] <= 0
+
+
+def test_kernel_selection():
+    paper = workloads.paper_u8()
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
+    assert plan.info(paper.n_samp)["kernel"] == ["u8_tiled"]
+    stream = workloads.stream_beam(0, 90168)
+    plan = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, stream.ranges, "u8", upload=False)
+    assert plan.info(stream.n_samp)["kernel"][0] == "u8_tiled"
+    tiny = workloads.tiny_u8()  # 8 samples of delay per DM step: too steep for 4-bit offsets
+    plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
+    assert plan.info(tiny.n_samp)["kernel"] == ["generic"]
+    f32 = workloads.diff_f32()
+    plan = dd.Plan(f32.freqs, f32.f_high, f32.t_samp, f32.ranges, "f32", upload=False)
+    assert plan.info(f32.n_samp)["kernel"] == ["generic"]
