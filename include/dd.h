@@ -84,6 +84,7 @@ typedef struct {
   int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
+  int32_t tile_dms[DD_MAX_RANGES];    /* DMs per lane of the uint8 tiled kernel (0: other) */
 } dd_plan_info;
 
 /* Forward kernels a range can run on (dd_plan_info.kernel). */
@@ -112,6 +113,17 @@ dd_status dd_plan_query(dd_plan plan, int64_t n_samp, dd_plan_info* out);
 /* Copy the int32 shift table of range `range` to host memory host_out laid
  * out [n_dm][n_chan] (s(c,d) at host_out[d*n_chan + c]). */
 dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out);
+
+/*
+ * Choose the tile shape of range `range` of a uint8 plan: `dms_per_lane` is
+ * the register tile's DM count (8, 6 or 4; 0 = automatic).  Per-plan tile
+ * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
+ * Rebuilds the plan's device tables, so it must be followed by
+ * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
+ * Errors: DD_ERR_UNSUPPORTED if that shape cannot serve the range (non-uint8
+ * plan, bin > 1, or DM offsets too wide for it); the previous choice is kept.
+ */
+dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t dms_per_lane);
 
 /*
  * Copy the plan's device tables into caller-owned device memory d_workspace

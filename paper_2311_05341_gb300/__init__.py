@@ -89,6 +89,7 @@ class Plan:
             "out_elems": inf.out_elems, "n_dm_total": inf.n_dm_total,
             "max_delay_raw": inf.max_delay_raw, "workspace_bytes": inf.workspace_bytes,
             "kernel": [{1: "generic", 2: "u8_tiled"}[inf.kernel[i]] for i in range(n)],
+            "tile_dms": [inf.tile_dms[i] for i in range(n)],
         }
 
     def shifts(self, r: int = 0) -> np.ndarray:
@@ -97,6 +98,13 @@ class Plan:
         out = np.empty((n_dm, self.n_chan), dtype=np.int32)
         check(self._lib.dd_plan_shifts(self._h, int(r), out.ctypes.data))
         return out
+
+    def set_tile(self, r: int, dms_per_lane: int, device=None):
+        """Pick the uint8 register-tile shape of range r (8, 6, 4; 0 = auto) and re-upload."""
+        check(self._lib.dd_plan_set_tile(self._h, int(r), int(dms_per_lane)))
+        if self.workspace is not None:
+            self.upload(self.workspace.device if device is None else device)
+        return self
 
     # -- device -----------------------------------------------------------
     def upload(self, device=None, stream=None):

@@ -45,7 +45,8 @@ class PlanInfo(ctypes.Structure):
                 ("out_offset", ctypes.c_int64 * DD_MAX_RANGES),
                 ("out_elems", ctypes.c_int64), ("max_delay_raw", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_size_t),
-                ("kernel", ctypes.c_int32 * DD_MAX_RANGES)]
+                ("kernel", ctypes.c_int32 * DD_MAX_RANGES),
+                ("tile_dms", ctypes.c_int32 * DD_MAX_RANGES)]
 
 
 # name -> (restype, argtypes) for every exported entry point.
@@ -58,6 +59,7 @@ SIGNATURES = {
     "dd_plan_query": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(PlanInfo)]),
     "dd_plan_shifts": (ctypes.c_int, [_VP, _I32, _VP]),
     "dd_plan_upload": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
+    "dd_plan_set_tile": (ctypes.c_int, [_VP, _I32, _I32]),
     "dd_run": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),

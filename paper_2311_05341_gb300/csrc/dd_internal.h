@@ -35,7 +35,9 @@ struct RangePlan {
 
   // Register-tiled uint8 kernel (fwd_u8.cu), used when u8_ok.
   bool u8_ok = false;
-  int32_t u8_n_blocks = 0;      // DM blocks of u8k::kDmCta
+  int32_t u8_dr = 0;            // DMs per warp of the chosen tile shape
+  int32_t u8_request = 0;       // tile requested by dd_plan_set_tile (0 = automatic)
+  int32_t u8_n_blocks = 0;      // DM blocks of u8_dr * warps DMs
   int32_t u8_lp = 0;            // paired words per staged channel window
   uint32_t u8_units_magic = 0;  // division by u8_lp / 4 (see fwd_u8.h)
   int32_t u8_units_shift = 0;
@@ -43,6 +45,7 @@ struct RangePlan {
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
   size_t off_u8_recs = 0;       // u8k::Rec [u8_n_blocks][n_chan]
+  std::vector<unsigned char> u8_recs;  // host image of the records
 };
 
 }  // namespace dd
@@ -68,6 +71,9 @@ dd_status cuda_fail(int err, const char* what);
 
 // Planner (plan.cpp).
 dd_status build_plan(dd_plan_s* p);
+// (Re)choose the uint8 tile of one range (request 0 = automatic) and rebuild
+// the workspace image.  Returns false if the requested tile does not fit.
+bool retile_range(dd_plan_s* p, size_t range, int32_t request);
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
 
 // Kernel launchers (return a cudaError_t as int; 0 on success).

@@ -6,9 +6,10 @@
 // kernel (Sec. 4: a CTA owns D_dm x D_t outputs, threads keep accumulators in
 // registers, Algorithm 3) but organised for GB300's issue rate:
 //
-//  * CTA = 8 warps x 32 lanes.  The CTA owns 64 consecutive DMs and 1280 output
-//    samples.  Warp w owns DMs d0 + 8w .. d0 + 8w + 7; every lane owns the same
-//    8 DMs x 40 samples.
+//  * CTA = W warps x 32 lanes owning dr * W consecutive DMs and 1280 output
+//    samples.  Warp w owns DMs d0 + dr*w .. d0 + dr*w + dr - 1; every lane owns
+//    the same dr DMs x 40 samples (dr = 8, 6 or 4: the tile shapes of
+//    fwd_u8.h, picked per plan).
 //  * Samples are summed two per 32-bit word in 16-bit lanes (SIMD within a
 //    word, Sec. 4.1): word u of a channel's staged window packs samples u and
 //    u + 640 (the pairing distance is half the CTA tile, so lane l's 20 words
@@ -20,7 +21,7 @@
 //    (cp.async.bulk, 16-byte aligned, completion on an mbarrier), two stages
 //    in flight; all threads then re-pack them into paired 16-bit words.
 //  * Register reuse across DMs: each lane loads its 36-word window of a
-//    channel once (9 x 16-byte shared loads) and adds it into all 8 DMs.  The
+//    channel once (9 x 16-byte shared loads) and adds it into all dr DMs.  The
 //    offset of DM i inside the window is a per-(channel, warp) 4-bit value
 //    (the paper's T_diff * Delta t_pc of Eq. 6, resolved to an integer on the
 //    host); a warp-uniform switch selects the register slice, so the adds use
@@ -36,6 +37,7 @@
 
 #include "dd_internal.h"
 #include "fwd_u8.h"
+#include "fwd_u8_dispatch.inc"
 
 namespace dd {
 namespace u8k {
@@ -85,13 +87,14 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 
 struct Smem {
   uint32_t bar_base;   // 2 mbarriers
-  Rec* recs;           // [2][kNC]
-  uint8_t* raw;        // [2][kNC][lraw]
-  uint32_t* pw;        // [kNC][lp]
+  Rec* recs;           // [2][NC]
+  uint8_t* raw;        // [2][NC][lraw]
+  uint32_t* pw;        // [NC][lp]
 };
 
-// Issue the TMA copies of stage `st` into buffer `buf`.  Threads 0..kNC-1 copy
-// one channel each, thread kNC copies the stage's records.
+// Issue the TMA copies of stage `st` into buffer `buf`.  Threads 0..NC-1 copy
+// one channel each, thread NC copies the stage's records.
+template <int kNC>
 __device__ __forceinline__ void issue_stage(const U8Params& p, const Smem& sm, int st, int buf,
                                             int64_t t0, int32_t base, int tid) {
   const uint32_t bar = sm.bar_base + 8u * buf;
@@ -122,20 +125,41 @@ __device__ __forceinline__ void issue_stage(const U8Params& p, const Smem& sm, i
   }
 }
 
-// acc[i][j] += R[K + j] for j < kH.
-#define DD_U8_CASE(K)                                                     \
-  case K:                                                                 \
-    _Pragma("unroll") for (int j = 0; j < kH; ++j) acc[i][j] += R[K + j]; \
-    break;
+static_assert(kH == 20 && kWin == 36 && kMaxOff == 15,
+              "fwd_u8_dispatch.inc is generated for 20 words, a 36-word window and 16 offsets");
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
+// Adds the lane's window slices into its DR register tiles: one warp-uniform
+// indexed branch per DM (fwd_u8_dispatch.inc, generated by gen_u8_dispatch.py).
+template <int DR>
+__device__ __forceinline__ void dispatch_dms(uint32_t (&acc)[DR][kH], const uint32_t (&R)[kWin],
+                                             uint32_t dl) {
+  uint32_t ix[DR];
+#pragma unroll
+  for (int i = 0; i < DR; ++i) ix[i] = (dl >> (4 * i)) & 15u;
+  if constexpr (DR == 4) {
+    DD_U8_CHANNEL_4(acc, R, ix);
+  } else if constexpr (DR == 6) {
+    DD_U8_CHANNEL_6(acc, R, ix);
+  } else {
+    static_assert(DR == 8, "tile shapes are 4, 6 or 8 DMs per lane");
+    DD_U8_CHANNEL_8(acc, R, ix);
+  }
+}
+
+template <int DR, int NW, int MINB, int kNC>
+__global__ void __launch_bounds__(NW * 32, MINB) fwd_u8_kernel(const U8Params p) {
+  constexpr int kThreads = NW * 32;
+  constexpr int kDmCta = DR * NW;
+  constexpr int kDR = DR;
+  static_assert(NW * kFlushWords <= kNC * 672, "flush tile must fit the paired window buffer");
   extern __shared__ __align__(128) unsigned char smem[];
   Smem sm;
   sm.bar_base = smem_u32(smem);
-  sm.recs = reinterpret_cast<Rec*>(smem + 128);
-  sm.raw = smem + kRawOffset;
+  sm.recs = reinterpret_cast<Rec*>(smem + kRecOffset);
+  constexpr size_t kRawOff = raw_offset(kNC);
+  sm.raw = smem + kRawOff;
   sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * kNC * static_cast<size_t>(p.lraw));
 
   const int tid = threadIdx.x;
@@ -159,8 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
     return (tid < kNC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
   };
   if (tid <= kNC) {
-    issue_stage(p, sm, 0, 0, t0, base_of(0), tid);
-    if (n_st > 1) issue_stage(p, sm, 1, 1, t0, base_of(1), tid);
+    issue_stage<kNC>(p, sm, 0, 0, t0, base_of(0), tid);
+    if (n_st > 1) issue_stage<kNC>(p, sm, 1, 1, t0, base_of(1), tid);
   }
   int32_t next_base = base_of(2);
 
@@ -171,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
     for (int j = 0; j < kH; ++j) acc[i][j] = 0u;
 
   bool first_flush = true;
-  int chan_done = 0;
+  int since_flush = 0;  // channels added into the 16-bit lanes since the last widen
   const int units = p.lp >> 2;  // 4 paired words per conversion unit
 
   for (int st = 0; st < n_st; ++st) {
@@ -211,8 +235,12 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
     }
     __syncthreads();
 
-    // Shift-and-sum: every lane adds its window into its 8 DMs.
+    // Shift-and-sum: every lane adds its window into its DR DMs.  One indexed
+    // branch per DM selects the register slice R[off .. off + 20) (see
+    // gen_u8_dispatch.py); the loop is kept rolled so the dispatch block, and
+    // its PTX labels, appears once per kernel.
     const Rec* rs = sm.recs + buf * kNC;
+#pragma unroll 1
     for (int ch = 0; ch < nc; ++ch) {
       const uint32_t dl = rs[ch].delta[w];
       const int a = 4 * static_cast<int>(rs[ch].aq[w]);
@@ -227,28 +255,20 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
         R[4 * k + 2] = v.z;
         R[4 * k + 3] = v.w;
       }
-#pragma unroll
-      for (int i = 0; i < kDR; ++i) {
-        const uint32_t off = (dl >> (4 * i)) & 15u;
-        switch (off) {
-          DD_U8_CASE(0) DD_U8_CASE(1) DD_U8_CASE(2) DD_U8_CASE(3)
-          DD_U8_CASE(4) DD_U8_CASE(5) DD_U8_CASE(6) DD_U8_CASE(7)
-          DD_U8_CASE(8) DD_U8_CASE(9) DD_U8_CASE(10) DD_U8_CASE(11)
-          DD_U8_CASE(12) DD_U8_CASE(13) DD_U8_CASE(14) DD_U8_CASE(15)
-          default: __builtin_unreachable();
-        }
-      }
+      dispatch_dms<DR>(acc, R, dl);
     }
-    chan_done += nc;
+    since_flush += nc;
     __syncthreads();  // P, raw[buf] and recs[buf] are free
 
     if (tid <= kNC && st + 2 < n_st) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_stage(p, sm, st + 2, buf, t0, next_base, tid);
+      issue_stage<kNC>(p, sm, st + 2, buf, t0, next_base, tid);
       next_base = base_of(st + 3);
     }
 
-    if ((chan_done & (kFlushChannels - 1)) == 0 || st == n_st - 1) {
+    // Widen before the next stage could take a lane past kFlushChannels channels.
+    if (since_flush + kNC > kFlushChannels || st == n_st - 1) {
+      since_flush = 0;
       // Widen the 16-bit lanes into the int32 output through a transposed
       // shared-memory tile (index f(p) = p + p / 160 is conflict-free for both
       // the lane-major writes and the row-major reads).
@@ -267,13 +287,29 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
         if (d < p.n_dm) {
           int32_t* row = p.out + static_cast<int64_t>(d) * p.n_out + t0;
           const int64_t lim = p.n_out - t0;
-#pragma unroll 8
-          for (int k = 0; k < kTile / 32; ++k) {
-            const int pos = 32 * k + l;
-            if (pos < lim) {
-              int32_t v = static_cast<int32_t>(tr[pos + k / 5]);
-              if (!first_flush) v += row[pos];
-              row[pos] = v;
+          // Two halves of 20 positions: issue all loads of a half before any add.
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            int32_t v[kTile / 64];
+#pragma unroll
+            for (int k = 0; k < kTile / 64; ++k) {
+              const int kk = h * (kTile / 64) + k;
+              v[k] = static_cast<int32_t>(tr[32 * kk + l + kk / 5]);
+            }
+            if (!first_flush) {
+              int32_t g[kTile / 64];
+#pragma unroll
+              for (int k = 0; k < kTile / 64; ++k) {
+                const int pos = 32 * (h * (kTile / 64) + k) + l;
+                g[k] = pos < lim ? __ldcg(row + pos) : 0;
+              }
+#pragma unroll
+              for (int k = 0; k < kTile / 64; ++k) v[k] += g[k];
+            }
+#pragma unroll
+            for (int k = 0; k < kTile / 64; ++k) {
+              const int pos = 32 * (h * (kTile / 64) + k) + l;
+              if (pos < lim) row[pos] = v[k];
             }
           }
         }
@@ -284,9 +320,24 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_u8_kernel(const U8Params p) {
   }
 }
 
-#undef DD_U8_CASE
 
 }  // namespace u8k
+
+namespace {
+
+template <int DR, int NW, int MINB, int NC>
+int launch_shape(const u8k::U8Params& prm, int64_t grid, cudaStream_t st) {
+  const u8k::Shape* sh = u8k::shape_for(DR);
+  const size_t smem = u8k::smem_bytes(*sh, prm.lp);
+  auto kern = u8k::fwd_u8_kernel<DR, NW, MINB, NC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<static_cast<unsigned>(grid), NW * 32, smem, st>>>(prm);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace
 
 int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
                       int64_t n_samp, int64_t n_out, void* d_out, void* stream) {
@@ -307,16 +358,16 @@ int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
   prm.units_shift = rp.u8_units_shift;
   prm.out = static_cast<int32_t*>(d_out);
   prm.err = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) + kStatusOffset);
-  const size_t smem = smem_bytes(prm.lp);
-  cudaError_t e = cudaFuncSetAttribute(fwd_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return static_cast<int>(e);
   const int64_t tiles = (n_out + kTile - 1) / kTile;
   const int64_t grid = tiles * rp.u8_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
-  fwd_u8_kernel<<<static_cast<unsigned>(grid), kThreads, smem,
-                  static_cast<cudaStream_t>(stream)>>>(prm);
-  return static_cast<int>(cudaGetLastError());
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (rp.u8_dr) {
+    case 8: return launch_shape<8, 8, 1, 16>(prm, grid, st);
+    case 6: return launch_shape<6, 12, 1, 24>(prm, grid, st);
+    case 4: return launch_shape<4, 8, 2, 16>(prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
 }
 
 }  // namespace dd

@@ -43,29 +43,32 @@ int32_t block_span(const RangePlan& rp, int32_t n_chan, int32_t per_block) {
   return span;
 }
 
-// Records of the register-tiled uint8 kernel.  For DM block b (first DM d0),
-// channel c and warp w (DMs d0 + 8w + i, i < 8, clamped to the last DM):
+// Records of the register-tiled uint8 kernel for a tile shape with dr DMs per
+// warp and W warps.  For DM block b (first DM d0, dr * W DMs), channel c and
+// warp w (DMs d0 + dr*w + i, i < dr, clamped to the last DM):
 //   base  = s(c, d0),  m = base mod 16 (the TMA copy starts 16-byte aligned),
-//   D_i   = s(c, d0 + 8w + i) - base + m   (word offset inside the staged window),
-//   a_w   = 4 * floor(D_0 / 4)              (16-byte aligned window start),
-//   off_i = D_i - a_w                        (must fit in 4 bits).
-// Returns false if some offset does not fit, leaving the plan on the generic kernel.
-bool build_u8_records(RangePlan& rp, int32_t n_chan, std::vector<u8k::Rec>& recs) {
+//   D_i   = s(c, d0 + dr*w + i) - base + m   (word offset inside the staged window),
+//   a_w   = 4 * floor(D_0 / 4)                (16-byte aligned window start),
+//   off_i = D_i - a_w                          (must fit in 4 bits).
+// Returns false if some offset does not fit.
+bool build_u8_records(const RangePlan& rp, int32_t n_chan, const u8k::Shape& sh,
+                      std::vector<u8k::Rec>& recs, int32_t* n_blocks_out) {
   using namespace u8k;
-  const int64_t n_blocks = (rp.n_dm + kDmCta - 1) / kDmCta;
+  const int dm_cta = sh.dr * sh.warps;
+  const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   recs.assign(static_cast<size_t>(n_blocks) * n_chan, u8k::Rec{});
   for (int64_t b = 0; b < n_blocks; ++b) {
-    const int64_t d0 = b * kDmCta;
+    const int64_t d0 = b * dm_cta;
     for (int32_t c = 0; c < n_chan; ++c) {
       u8k::Rec& r = recs[static_cast<size_t>(b) * n_chan + c];
       const int32_t base = rp.shifts[static_cast<size_t>(d0) * n_chan + c];
       const int32_t m = base & 15;
       r.base = base;
-      for (int w = 0; w < kWarps; ++w) {
+      for (int w = 0; w < sh.warps; ++w) {
         int32_t a_w = 0;
         uint32_t packed = 0;
-        for (int i = 0; i < kDR; ++i) {
-          const int64_t d = std::min<int64_t>(d0 + w * kDR + i, rp.n_dm - 1);
+        for (int i = 0; i < sh.dr; ++i) {
+          const int64_t d = std::min<int64_t>(d0 + w * sh.dr + i, rp.n_dm - 1);
           const int32_t D = rp.shifts[static_cast<size_t>(d) * n_chan + c] - base + m;
           if (i == 0) a_w = (D >> 2) << 2;
           const int32_t off = D - a_w;
@@ -78,7 +81,7 @@ bool build_u8_records(RangePlan& rp, int32_t n_chan, std::vector<u8k::Rec>& recs
       }
     }
   }
-  rp.u8_n_blocks = static_cast<int32_t>(n_blocks);
+  *n_blocks_out = static_cast<int32_t>(n_blocks);
   return true;
 }
 
@@ -101,6 +104,71 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
   return false;
 }
 
+
+// Try one tile shape for a uint8 range; on success fill the range's u8 fields.
+bool try_u8_shape(RangePlan& rp, int32_t n_chan, const u8k::Shape& sh) {
+  const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
+  const int32_t lp = u8k::window_words(span);
+  if (u8k::smem_bytes(sh, lp) * sh.min_blocks > 227 * 1024) return false;
+  uint32_t magic = 0;
+  int32_t shift = 0;
+  if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(sh.nc * lp / 4), &magic,
+                      &shift))
+    return false;
+  std::vector<u8k::Rec> recs;
+  int32_t n_blocks = 0;
+  if (!build_u8_records(rp, n_chan, sh, recs, &n_blocks)) return false;
+  rp.u8_ok = true;
+  rp.u8_dr = sh.dr;
+  rp.u8_n_blocks = n_blocks;
+  rp.u8_lp = lp;
+  rp.u8_units_magic = magic;
+  rp.u8_units_shift = shift;
+  rp.u8_recs.resize(recs.size() * sizeof(u8k::Rec));
+  std::memcpy(rp.u8_recs.data(), recs.data(), rp.u8_recs.size());
+  return true;
+}
+
+// Register-tiled uint8 kernel: 8-bit input at time bin 1 whose per-warp DM
+// offsets fit the 4-bit fields and whose window fits shared memory.  The
+// automatic choice takes the first shape that fits in kAutoOrder.
+void choose_u8(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
+  static const int kAutoOrder[] = {6, 8, 4};
+  rp.u8_ok = false;
+  rp.u8_dr = 0;
+  rp.u8_recs.clear();
+  if (dtype != DD_U8 || rp.r.bin != 1) return;
+  if (rp.u8_request > 0) {
+    const u8k::Shape* sh = u8k::shape_for(rp.u8_request);
+    if (sh) try_u8_shape(rp, n_chan, *sh);
+    return;
+  }
+  for (int dr : kAutoOrder)
+    if (try_u8_shape(rp, n_chan, *u8k::shape_for(dr))) return;
+}
+
+void layout_workspace(dd_plan_s* p) {
+  size_t ws = u8k::kStatusBytes;  // device status word(s) first
+  for (auto& rp : p->ranges) {
+    ws = align_up(ws, 256);
+    rp.off_shifts = ws;
+    ws += rp.shifts.size() * sizeof(int32_t);
+    if (rp.u8_ok) {
+      ws = align_up(ws, 256);
+      rp.off_u8_recs = ws;
+      ws += rp.u8_recs.size();
+    }
+  }
+  p->ws_bytes = align_up(ws, 256);
+  p->host_ws.assign(p->ws_bytes, 0);
+  for (const auto& rp : p->ranges) {
+    std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
+                rp.shifts.size() * sizeof(int32_t));
+    if (rp.u8_ok)
+      std::memcpy(p->host_ws.data() + rp.off_u8_recs, rp.u8_recs.data(), rp.u8_recs.size());
+  }
+}
+
 }  // namespace
 
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp) {
@@ -118,9 +186,6 @@ dd_status build_plan(dd_plan_s* p) {
     p->k[c] = kDispersionConstant * (inv_f2 - inv_ref2);
   }
 
-  size_t ws = u8k::kStatusBytes;  // device status word(s) first
-  std::vector<std::vector<u8k::Rec>> u8_recs(p->ranges.size());
-  size_t ri = 0;
   for (auto& rp : p->ranges) {
     rp.n_dm = std::llround((rp.r.dm_hi - rp.r.dm_lo) / rp.r.dm_step);
     if (rp.n_dm <= 0 || rp.n_dm > (int64_t{1} << 24))
@@ -159,44 +224,25 @@ dd_status build_plan(dd_plan_s* p) {
     }
     rp.adj_span = aspan;
 
-    ws = align_up(ws, 256);
-    rp.off_shifts = ws;
-    ws += rp.shifts.size() * sizeof(int32_t);
-
-    // Register-tiled uint8 kernel: 8-bit input at time bin 1 whose per-warp DM
-    // offsets fit its 4-bit fields and whose window fits shared memory.
-    rp.u8_ok = false;
-    if (p->dtype == DD_U8 && rp.r.bin == 1) {
-      const int32_t span = block_span(rp, n_chan, u8k::kDmCta);
-      const int32_t lp = u8k::window_words(span);
-      uint32_t magic = 0;
-      int32_t shift = 0;
-      if (u8k::smem_bytes(lp) <= 227 * 1024 &&
-          division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(u8k::kNC * lp / 4),
-                         &magic, &shift) &&
-          build_u8_records(rp, n_chan, u8_recs[ri])) {
-        rp.u8_ok = true;
-        rp.u8_lp = lp;
-        rp.u8_units_magic = magic;
-        rp.u8_units_shift = shift;
-        ws = align_up(ws, 256);
-        rp.off_u8_recs = ws;
-        ws += u8_recs[ri].size() * sizeof(u8k::Rec);
-      }
-    }
-    ++ri;
+    choose_u8(rp, n_chan, p->dtype);
   }
-  p->ws_bytes = align_up(ws, 256);
-  p->host_ws.assign(p->ws_bytes, 0);
-  for (size_t i = 0; i < p->ranges.size(); ++i) {
-    const RangePlan& rp = p->ranges[i];
-    std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
-                rp.shifts.size() * sizeof(int32_t));
-    if (rp.u8_ok)
-      std::memcpy(p->host_ws.data() + rp.off_u8_recs, u8_recs[i].data(),
-                  u8_recs[i].size() * sizeof(u8k::Rec));
-  }
+  layout_workspace(p);
   return DD_OK;
+}
+
+bool retile_range(dd_plan_s* p, size_t range, int32_t request) {
+  RangePlan& rp = p->ranges[range];
+  const int32_t old = rp.u8_request;
+  rp.u8_request = request;
+  choose_u8(rp, p->n_chan, p->dtype);
+  if (request > 0 && !rp.u8_ok) {
+    rp.u8_request = old;
+    choose_u8(rp, p->n_chan, p->dtype);
+    layout_workspace(p);
+    return false;
+  }
+  layout_workspace(p);
+  return true;
 }
 
 }  // namespace dd

@@ -121,13 +121,17 @@ def _tiled_case(seed):
 @pytest.mark.parametrize("seed", range(16))
 def test_u8_tiled_full_planes(seed):
     b, rng = _tiled_case(seed)
-    plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, "u8")
-    assert plan.info(b.n_samp)["kernel"] == ["u8_tiled"]
     # Values up to 255 in every channel exercise the 16-bit lane bound (256 channels).
     x = filterbank(np.uint8, len(b.freqs), b.n_samp, 8000 + seed, 200, 80)
     ref = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges)
-    got = gpu_planes(b, x)
-    np.testing.assert_array_equal(got[0], ref[0])
+    xd = padded_device(x)
+    for dms in (8, 6, 4):
+        plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, "u8")
+        plan.set_tile(0, dms)
+        info = plan.info(b.n_samp)
+        assert info["kernel"] == ["u8_tiled"] and info["tile_dms"] == [dms]
+        got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
+        np.testing.assert_array_equal(got, ref[0], err_msg=f"tile {dms}")
 
 
 def test_u8_tiled_saturated_input():
