@@ -184,6 +184,32 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream);
 dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
                       void* h_out, void* d_in_stage, void* d_out_stage, void* stream);
 
+/*
+ * Forward transform of a uint8 plan without any caller-provided workspace, for
+ * callers that cannot allocate device memory (for example a real-time
+ * pipeline that must not call cudaMalloc while data streams in, or a plug-in
+ * whose host framework owns every device allocation).  The paper has no
+ * counterpart: it exists only for those callers.
+ *   - The plan's tables live in a fixed array of 8 MiB in this library's own
+ *     device memory (every GPU that loads the library reserves it until the
+ *     process exits).  Plans whose tables exceed it get DD_ERR_BUDGET.
+ *   - Every range must run on the uint8 tiled kernel (dd_plan_query's kernel
+ *     is DD_KERNEL_U8_TILED), otherwise DD_ERR_UNSUPPORTED.
+ *   - d_in / in_row_stride / n_samp / d_out follow dd_run; the plan needs no
+ *     dd_plan_upload.  The call allocates nothing and frees nothing.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any CUDA
+ *     stream capture.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     each call first clears the status word and copies its tables in, on
+ *     `stream`.  Calls that overlap on the GPU (different streams, or host
+ *     threads) race on the array and give undefined results: serialise them.
+ *   - A bounded device wait that gives up leaves this call's output undefined;
+ *     it is not reported here (dd_run with dd_plan_device_status reports it).
+ */
+dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t in_row_stride,
+                            int64_t n_samp, void* d_out, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* dd_status_string(dd_status status);
 /* Thread-local detail of the last failing call on this thread ("" if none). */

@@ -63,6 +63,7 @@ SIGNATURES = {
     "dd_run": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
+    "dd_run_u8_noalloc": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
     "dd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dd_last_error_detail": (ctypes.c_char_p, []),

@@ -83,6 +83,11 @@ int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* 
 int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                       int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
                       void* stream);
+// The uint8 tiled kernel with its record table and status word at explicit
+// device addresses (used by the no-allocation entry point).
+int launch_forward_u8_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                                  int32_t* err, const void* d_in, int64_t stride,
+                                  int64_t n_out, void* d_out, void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);

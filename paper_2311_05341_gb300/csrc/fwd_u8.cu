@@ -370,4 +370,34 @@ int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
   return static_cast<int>(cudaErrorInvalidValue);
 }
 
+int launch_forward_u8_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                                  int32_t* err, const void* d_in, int64_t stride,
+                                  int64_t n_out, void* d_out, void* stream) {
+  using namespace u8k;
+  U8Params prm{};
+  prm.x = static_cast<const uint8_t*>(d_in);
+  prm.stride = stride;
+  prm.n_chan = p->n_chan;
+  prm.recs = static_cast<const Rec*>(recs);
+  prm.n_dm = static_cast<int32_t>(rp.n_dm);
+  prm.n_blocks = rp.u8_n_blocks;
+  prm.n_out = n_out;
+  prm.lp = rp.u8_lp;
+  prm.lraw = rp.u8_lp + kPair;
+  prm.units_magic = rp.u8_units_magic;
+  prm.units_shift = rp.u8_units_shift;
+  prm.out = static_cast<int32_t*>(d_out);
+  prm.err = err;
+  const int64_t tiles = (n_out + kTile - 1) / kTile;
+  const int64_t grid = tiles * rp.u8_n_blocks;
+  if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (rp.u8_dr) {
+    case 8: return launch_shape<8, 8, 1, 16>(prm, grid, st);
+    case 6: return launch_shape<6, 12, 1, 24>(prm, grid, st);
+    case 4: return launch_shape<4, 8, 2, 16>(prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
 }  // namespace dd
