@@ -84,12 +84,12 @@ typedef struct {
   int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
-  int32_t tile_dms[DD_MAX_RANGES];    /* DMs per lane of the uint8 tiled kernel (0: other) */
+  int32_t tile_dms[DD_MAX_RANGES];    /* DMs per lane of the tiled kernel (0: generic) */
 } dd_plan_info;
 
 /* Forward kernels a range can run on (dd_plan_info.kernel). */
-#define DD_KERNEL_GENERIC 1  /* shared-memory staged, any dtype and bin */
-#define DD_KERNEL_U8_TILED 2 /* uint8, bin 1: packed 16-bit lanes, register reuse */
+#define DD_KERNEL_GENERIC 1 /* shared-memory staged, any dtype and bin */
+#define DD_KERNEL_TILED 2   /* bin 1: TMA-staged register tiles (uint8 in packed 16-bit lanes) */
 
 /*
  * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
@@ -115,13 +115,13 @@ dd_status dd_plan_query(dd_plan plan, int64_t n_samp, dd_plan_info* out);
 dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out);
 
 /*
- * Choose the tile shape of range `range` of a uint8 plan: `dms_per_lane` is
- * the register tile's DM count (8, 6 or 4; 0 = automatic).  Per-plan tile
+ * Choose the tile shape of range `range` (time bin 1): `dms_per_lane` is the
+ * register tile's DM count (8, 6, 4, 2 or 1; 0 = automatic).  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
  * Rebuilds the plan's device tables, so it must be followed by
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
- * Errors: DD_ERR_UNSUPPORTED if that shape cannot serve the range (non-uint8
- * plan, bin > 1, or DM offsets too wide for it); the previous choice is kept.
+ * Errors: DD_ERR_UNSUPPORTED if that shape cannot serve the range (bin > 1, or
+ * DM offsets too wide for it); the previous choice is kept.
  */
 dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t dms_per_lane);
 
@@ -193,8 +193,8 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
  *   - The plan's tables live in a fixed array of 8 MiB in this library's own
  *     device memory (every GPU that loads the library reserves it until the
  *     process exits).  Plans whose tables exceed it get DD_ERR_BUDGET.
- *   - Every range must run on the uint8 tiled kernel (dd_plan_query's kernel
- *     is DD_KERNEL_U8_TILED), otherwise DD_ERR_UNSUPPORTED.
+ *   - Every range must run on the tiled kernel (dd_plan_query's kernel is
+ *     DD_KERNEL_TILED), otherwise DD_ERR_UNSUPPORTED.
  *   - d_in / in_row_stride / n_samp / d_out follow dd_run; the plan needs no
  *     dd_plan_upload.  The call allocates nothing and frees nothing.
  *   - The first call on a device looks up the array's device address (once per
@@ -209,6 +209,44 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
  */
 dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t in_row_stride,
                             int64_t n_samp, void* d_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Persistent batches: many beams (plans of different channel counts, dtypes,
+ * sampling times and DM plans) dedispersed by ONE persistent launch of the
+ * tiled kernel, whose CTAs take (beam range, DM block, time tile) work items
+ * from a device counter, longest items first.  The paper tunes its tile
+ * parameters per telescope and plan (Sec. 4.1); here each plan's tile shape
+ * is chosen before the batch is built (dd_plan_set_tile), so the batch mixes
+ * shapes.  The batch keeps pointers to its plans, which must outlive it and
+ * stay uploaded.  Device memory is the caller's (dd_batch_workspace_bytes).
+ * ------------------------------------------------------------------------- */
+typedef struct dd_batch_s* dd_batch;
+
+/* Build the work list for n_plans plans and their raw sample counts.  Every
+ * range must be on the tiled kernel with 4, 2 or 1 DMs per lane (time bin 1),
+ * else DD_ERR_UNSUPPORTED; DD_ERR_SHAPE if an input is shorter than a range's
+ * maximum delay. */
+dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n_plans,
+                          dd_batch* out);
+dd_status dd_batch_destroy(dd_batch batch);
+/* Device workspace bytes the batch needs (work counter, job table, items). */
+dd_status dd_batch_workspace_bytes(dd_batch batch, size_t* bytes);
+/* Number of work items and jobs (plan ranges) of the batch. */
+dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs);
+/* Copy the work list into caller device memory (256-byte aligned, >= the
+ * workspace bytes) and bind it; synchronises `stream`. */
+dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void* stream);
+/* Bind the input/output buffers of every plan (d_in[i], in_row_stride[i],
+ * d_out[i] follow dd_run's rules for plan i) by uploading the job table;
+ * synchronises `stream`.  Rebind whenever a buffer address changes. */
+dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
+                        void* const* d_out, void* stream);
+/* One persistent launch over all items of a bound batch (a counter reset and a
+ * kernel launch on `stream`; both can be captured in a CUDA graph). */
+dd_status dd_batch_run(dd_batch batch, void* stream);
+/* DD_ERR_TIMEOUT if a bounded device wait of any batch plan gave up since the
+ * last check (clears the flags); synchronises `stream`. */
+dd_status dd_batch_status(dd_batch batch, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* dd_status_string(dd_status status);

@@ -88,7 +88,7 @@ class Plan:
             "out_offset": [inf.out_offset[i] for i in range(n)],
             "out_elems": inf.out_elems, "n_dm_total": inf.n_dm_total,
             "max_delay_raw": inf.max_delay_raw, "workspace_bytes": inf.workspace_bytes,
-            "kernel": [{1: "generic", 2: "u8_tiled"}[inf.kernel[i]] for i in range(n)],
+            "kernel": [{1: "generic", 2: "tiled"}[inf.kernel[i]] for i in range(n)],
             "tile_dms": [inf.tile_dms[i] for i in range(n)],
         }
 
@@ -100,7 +100,7 @@ class Plan:
         return out
 
     def set_tile(self, r: int, dms_per_lane: int, device=None):
-        """Pick the uint8 register-tile shape of range r (8, 6, 4; 0 = auto) and re-upload."""
+        """Pick the register-tile shape of range r (8, 6, 4, 2, 1; 0 = auto) and re-upload."""
         check(self._lib.dd_plan_set_tile(self._h, int(r), int(dms_per_lane)))
         if self.workspace is not None:
             self.upload(self.workspace.device if device is None else device)

@@ -18,7 +18,7 @@ DD_OK, DD_ERR_INVALID_ARG, DD_ERR_UNSUPPORTED, DD_ERR_SHAPE = 0, 1, 2, 3
 DD_ERR_BUDGET, DD_ERR_CUDA, DD_ERR_TIMEOUT = 4, 5, 6
 DD_U8, DD_U16, DD_F32 = 1, 2, 3
 DD_MAX_RANGES = 16
-DD_KERNEL_GENERIC, DD_KERNEL_U8_TILED = 1, 2
+DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 
 
 class DDError(RuntimeError):
@@ -65,6 +65,16 @@ SIGNATURES = {
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
     "dd_run_u8_noalloc": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
+    "dd_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_I64), _I32,
+                                       ctypes.POINTER(_VP)]),
+    "dd_batch_destroy": (ctypes.c_int, [_VP]),
+    "dd_batch_workspace_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_SZ)]),
+    "dd_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
+    "dd_batch_upload": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
+    "dd_batch_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I64),
+                                     ctypes.POINTER(_VP), _VP]),
+    "dd_batch_run": (ctypes.c_int, [_VP, _VP]),
+    "dd_batch_status": (ctypes.c_int, [_VP, _VP]),
     "dd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dd_last_error_detail": (ctypes.c_char_p, []),
     "dd_version": (ctypes.c_char_p, []),

@@ -1,0 +1,219 @@
+"""Batched dedispersion of many beams in one persistent launch (dd_batch_*).
+
+Beams may differ in channel count, dtype, sampling time and DM plan.  Each
+beam's plan gets a tile shape (DMs per lane of the register tile) chosen by
+the autotuner, which times the feasible shapes on the beam's own shapes and
+caches the winner by plan signature -- the per-telescope tuning of the paper's
+tile parameters (Sec. 4.1) done automatically.  The batch then runs as one
+persistent launch over a (beam range, DM block, time tile) work list,
+optionally captured once in a CUDA graph and replayed.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import json
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import Plan, _lib
+from ._lib import check
+
+BATCH_SHAPES = (4, 2, 1)  # DMs per lane the persistent kernel serves
+
+
+@dataclass
+class BeamSpec:
+    """One beam: channel frequencies, sampling, DM plan, dtype and length."""
+
+    freqs: np.ndarray
+    f_ref: float
+    t_samp: float
+    ranges: list
+    dtype: str
+    n_samp: int
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def plan_signature(plan: Plan, n_samp: int) -> str:
+    """Key of the autotune cache: everything that changes the tile's work."""
+    h = hashlib.sha1(plan.freqs.tobytes()).hexdigest()[:16]
+    return json.dumps([plan.dtype, plan.n_chan, h, plan.f_ref, plan.t_samp,
+                       [list(r) for r in plan.ranges], int(n_samp)])
+
+
+class Autotuner:
+    """Times every feasible tile shape of a plan and keeps the fastest."""
+
+    def __init__(self, shapes=BATCH_SHAPES, reps: int = 3, cache_path: str | None = None):
+        self.shapes = tuple(shapes)
+        self.reps = reps
+        self.cache_path = cache_path or os.environ.get("DD_AUTOTUNE_CACHE")
+        self.cache = {}
+        if self.cache_path and os.path.exists(self.cache_path):
+            with open(self.cache_path) as fh:
+                self.cache = json.load(fh)
+        self.log = []
+
+    def _feasible(self, plan: Plan, r: int):
+        ok = []
+        for dr in self.shapes:
+            try:
+                plan.set_tile(r, dr)
+                ok.append(dr)
+            except _lib.DDError:
+                pass
+        return ok
+
+    def choose(self, plan: Plan, n_samp: int, x, out):
+        """Pick and set a shape for every range of the plan; returns them."""
+        torch = _torch()
+        key = plan_signature(plan, n_samp)
+        if key in self.cache:
+            choice = self.cache[key]
+            for r, dr in enumerate(choice):
+                plan.set_tile(r, dr)
+            return choice
+        choice = []
+        for r in range(len(plan.ranges)):
+            feas = self._feasible(plan, r)
+            if not feas:
+                raise _lib.DDError(_lib.DD_ERR_UNSUPPORTED,
+                                   f"range {r} fits none of the batch tile shapes")
+            best, best_ms = feas[0], float("inf")
+            if len(feas) > 1:
+                for dr in feas:
+                    plan.set_tile(r, dr)
+                    plan.run(x, out=out, n_samp=n_samp)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(self.reps):
+                        plan.run(x, out=out, n_samp=n_samp)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / self.reps
+                    self.log.append((key, r, dr, ms))
+                    if ms < best_ms:
+                        best, best_ms = dr, ms
+            plan.set_tile(r, best)
+            choice.append(best)
+        self.cache[key] = choice
+        if self.cache_path:
+            tmp = self.cache_path + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(self.cache, fh)
+            os.replace(tmp, self.cache_path)
+        return choice
+
+
+class BatchRunner:
+    """Owns per-beam device buffers and runs all beams as one persistent launch."""
+
+    def __init__(self, beams, device="cuda", autotune: bool = True, graph: bool = True,
+                 tuner: Autotuner | None = None):
+        torch = _torch()
+        self.device = torch.device(device)
+        self.beams = list(beams)
+        self.plans, self.inputs, self.outputs = [], [], []
+        self.tuner = tuner or (Autotuner() if autotune else None)
+        self.shapes = []
+        for b in self.beams:
+            plan = Plan(b.freqs, b.f_ref, b.t_samp, b.ranges, b.dtype, device=self.device)
+            esz = {"u8": 1, "u16": 2, "f32": 4}[b.dtype]
+            per = 16 // esz
+            stride = (b.n_samp + per - 1) // per * per
+            raw = torch.zeros((plan.n_chan, stride * esz), dtype=torch.uint8, device=self.device)
+            x = raw.view({"u8": torch.uint8, "u16": torch.uint16, "f32": torch.float32}[b.dtype])
+            out = plan.empty_output(b.n_samp, self.device)
+            if self.tuner is not None:
+                self.shapes.append(self.tuner.choose(plan, b.n_samp, x, out))
+            else:
+                shp = []
+                for r in range(len(b.ranges)):
+                    for dr in BATCH_SHAPES:
+                        try:
+                            plan.set_tile(r, dr)
+                            shp.append(dr)
+                            break
+                        except _lib.DDError:
+                            continue
+                self.shapes.append(shp)
+            self.plans.append(plan)
+            self.inputs.append(x)
+            self.outputs.append(out)
+        lib = _lib.load()
+        n = len(self.plans)
+        handles = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        n_samp = (ctypes.c_int64 * n)(*[b.n_samp for b in self.beams])
+        h = ctypes.c_void_p()
+        check(lib.dd_batch_create(handles, n_samp, n, ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        nbytes = ctypes.c_size_t()
+        check(lib.dd_batch_workspace_bytes(h, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        check(lib.dd_batch_upload(h, self.workspace.data_ptr(), self.workspace.numel(), stream))
+        d_in = (ctypes.c_void_p * n)(*[x.data_ptr() for x in self.inputs])
+        strides = (ctypes.c_int64 * n)(*[x.stride(0) for x in self.inputs])
+        d_out = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outputs])
+        check(lib.dd_batch_bind(h, d_in, strides, d_out, stream))
+        n_items, n_jobs = ctypes.c_int64(), ctypes.c_int32()
+        check(lib.dd_batch_info(h, ctypes.byref(n_items), ctypes.byref(n_jobs)))
+        self.n_items, self.n_jobs = n_items.value, n_jobs.value
+        self.graph = None
+        if graph:
+            self._capture()
+
+    def _launch(self):
+        torch = _torch()
+        check(self._lib.dd_batch_run(self._h, torch.cuda.current_stream(self.device).cuda_stream))
+
+    def _capture(self):
+        torch = _torch()
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self._launch()  # warm-up outside the graph
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._launch()
+        self.graph = g
+
+    def run(self):
+        """One persistent launch over every beam (graph replay if captured)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._launch()
+
+    def status(self):
+        torch = _torch()
+        check(self._lib.dd_batch_status(self._h, torch.cuda.current_stream(self.device).cuda_stream))
+
+    def planes(self, i: int):
+        return self.plans[i].split(self.outputs[i], self.beams[i].n_samp)
+
+    def run_per_beam(self):
+        """The plain path: one dd_run per beam, in order, on the current stream."""
+        for p, x, o, b in zip(self.plans, self.inputs, self.outputs, self.beams):
+            p.run(x, out=o, n_samp=b.n_samp)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

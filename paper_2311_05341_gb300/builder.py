@@ -19,10 +19,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
+GEN = os.path.join(BUILD, "gen")
 LIB = os.path.join(BUILD, "libdd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-I", INCLUDE, "-I", CSRC,
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-I", INCLUDE, "-I", CSRC, "-I", GEN,
           "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math,-Wall"]
 
 
@@ -38,8 +39,18 @@ def sources():
 
 
 def _deps():
-    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.inc"))
+    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.py"))
             + glob.glob(os.path.join(INCLUDE, "*.h")))
+
+
+def _generate():
+    """Write the generated dispatch include (see csrc/gen_dispatch.py)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("dd_gen_dispatch",
+                                                  os.path.join(CSRC, "gen_dispatch.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.generate(os.path.join(GEN, "fwd_tiled_dispatch.inc"))
 
 
 def _compile(src: str, verbose_ptxas: bool) -> str:
@@ -65,6 +76,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         newest = max(os.path.getmtime(p) for p in _deps())
         if newest <= os.path.getmtime(LIB):
             return LIB
+    _generate()
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))

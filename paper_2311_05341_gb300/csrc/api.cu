@@ -8,7 +8,6 @@
 #include <string>
 
 #include "dd_internal.h"
-#include "fwd_u8.h"
 
 namespace dd {
 
@@ -48,8 +47,8 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     o->out_offset[i] = off;
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
-    o->kernel[i] = rp.u8_ok ? DD_KERNEL_U8_TILED : DD_KERNEL_GENERIC;
-    o->tile_dms[i] = rp.u8_ok ? rp.u8_dr : 0;
+    o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
+    o->tile_dms[i] = rp.tile_ok ? rp.tile_dr : 0;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
     if (raw > o->max_delay_raw) o->max_delay_raw = raw;
   }
@@ -153,8 +152,8 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t dms_per_lane) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
     return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
-  if (dms_per_lane != 0 && !u8k::shape_for(dms_per_lane))
-    return fail(DD_ERR_INVALID_ARG, "dms_per_lane must be 0, 4, 6 or 8");
+  if (dms_per_lane != 0 && !tk::shape_for(dms_per_lane))
+    return fail(DD_ERR_INVALID_ARG, "dms_per_lane must be 0, 1, 2, 4, 6 or 8");
   bool ok;
   try {
     ok = retile_range(plan, static_cast<size_t>(range), dms_per_lane);
@@ -200,10 +199,10 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
     void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
     const RangePlan& rp = plan->ranges[i];
-    int e = rp.u8_ok ? launch_forward_u8(plan, rp, d_in, in_row_stride, n_samp, info.n_out[i], o,
-                                         stream)
-                     : launch_forward_generic(plan, rp, d_in, in_row_stride, n_samp,
-                                              info.n_out[i], o, stream);
+    int e = rp.tile_ok ? launch_forward_tiled(plan, rp, d_in, in_row_stride, n_samp,
+                                              info.n_out[i], o, stream)
+                       : launch_forward_generic(plan, rp, d_in, in_row_stride, n_samp,
+                                                info.n_out[i], o, stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
   return DD_OK;

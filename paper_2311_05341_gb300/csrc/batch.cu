@@ -1,0 +1,250 @@
+// batch.cu -- C ABI of the persistent batch runtime (include/dd.h, dd_batch_*).
+//
+// Many beams -- plans of different channel counts, dtypes, sampling times and
+// DM plans -- are dedispersed by one persistent launch of the tiled kernel
+// (fwd_tiled.cu): its CTAs take (job, DM block, time tile) items from a
+// device counter until the list is exhausted.  Items are ordered longest
+// first (largest channel count x tile work), DM blocks of a time tile
+// consecutive so their shared input window stays in L2.  dd_batch_bind
+// uploads the per-job pointers once; dd_batch_run is then a counter reset and
+// one launch, which a CUDA graph can capture and replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dd_internal.h"
+#include "fwd_tiled.h"
+
+struct dd_batch_s {
+  std::vector<dd_plan> plans;
+  std::vector<int64_t> n_samp;
+  struct JobRef {
+    int32_t plan;
+    int32_t range;
+    int64_t n_out;
+    int64_t out_offset;  // elements into the plan's output
+  };
+  std::vector<JobRef> jobs;
+  std::vector<dd::tk::BatchItem> items;
+  std::vector<dd::tk::BatchJob> host_jobs;
+  int32_t max_lraw = 0;
+  int32_t max_lp = 0;
+  size_t off_jobs = 0, off_items = 0, ws_bytes = 0;
+  unsigned char* d_ws = nullptr;
+  bool bound = false;
+  int32_t sm_count = 0;
+};
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+bool batch_shape(int32_t dr) {
+  for (const dd::tk::Shape& s : dd::tk::kBatchShapes)
+    if (s.dr == dr) return true;
+  return false;
+}
+
+}  // namespace
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n_plans,
+                          dd_batch* out) {
+  if (!out) return fail(DD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!plans || !n_samp || n_plans <= 0) return fail(DD_ERR_INVALID_ARG, "no plans");
+  dd_batch_s* b = new (std::nothrow) dd_batch_s();
+  if (!b) return fail(DD_ERR_INVALID_ARG, "host allocation failed");
+  try {
+    struct Cost {
+      double per_item;
+      int32_t job;
+    };
+    std::vector<Cost> order;
+    for (int32_t i = 0; i < n_plans; ++i) {
+      const dd_plan p = plans[i];
+      if (!p) {
+        delete b;
+        return fail(DD_ERR_INVALID_ARG, "NULL plan in batch");
+      }
+      b->plans.push_back(p);
+      b->n_samp.push_back(n_samp[i]);
+      int64_t out_off = 0;
+      for (size_t r = 0; r < p->ranges.size(); ++r) {
+        const RangePlan& rp = p->ranges[r];
+        if (!rp.tile_ok || !batch_shape(rp.tile_dr)) {
+          delete b;
+          return fail(DD_ERR_UNSUPPORTED,
+                      "batch plan " + std::to_string(i) + " range " + std::to_string(r) +
+                          " is not on a batch tile shape (time bin 1, 4/2/1 DMs per lane; see "
+                          "dd_plan_set_tile)");
+        }
+        const int64_t n_out = range_n_out(p, rp, n_samp[i]);
+        if (n_out <= 0) {
+          delete b;
+          return fail(DD_ERR_SHAPE, "batch plan " + std::to_string(i) + " input too short");
+        }
+        const int32_t job = static_cast<int32_t>(b->jobs.size());
+        b->jobs.push_back({i, static_cast<int32_t>(r), n_out, out_off});
+        out_off += rp.n_dm * n_out;
+        b->max_lraw = std::max(b->max_lraw, tk::raw_bytes(p->dtype, rp.tile_lp));
+        b->max_lp = std::max(b->max_lp, rp.tile_lp);
+        const double dms = static_cast<double>(tk::shape_for(rp.tile_dr)->warps) * rp.tile_dr;
+        order.push_back({static_cast<double>(p->n_chan) * dms * tk::tile_samples(p->dtype), job});
+      }
+    }
+    // Longest items first; within a job, DM blocks of a time tile together.
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Cost& a, const Cost& c) { return a.per_item > c.per_item; });
+    for (const Cost& c : order) {
+      const auto& j = b->jobs[c.job];
+      const dd_plan p = b->plans[j.plan];
+      const RangePlan& rp = p->ranges[j.range];
+      const int64_t tiles = (j.n_out + tk::tile_samples(p->dtype) - 1) / tk::tile_samples(p->dtype);
+      for (int64_t t = 0; t < tiles; ++t)
+        for (int32_t blk = 0; blk < rp.tile_n_blocks; ++blk)
+          b->items.push_back({c.job, blk, static_cast<int32_t>(t), 0});
+    }
+    if (b->items.size() > 0x7fffffffu) {
+      delete b;
+      return fail(DD_ERR_BUDGET, "too many batch items");
+    }
+    size_t ws = tk::kStatusBytes;  // work counter
+    ws = align256(ws);
+    b->off_jobs = ws;
+    ws += b->jobs.size() * sizeof(tk::BatchJob);
+    ws = align256(ws);
+    b->off_items = ws;
+    ws += b->items.size() * sizeof(tk::BatchItem);
+    b->ws_bytes = align256(ws);
+    b->host_jobs.resize(b->jobs.size());
+    const size_t smem = tk::batch_smem_bytes(tk::kBatchShapes[0], b->max_lraw, b->max_lp);
+    if (smem > 227 * 1024) {
+      delete b;
+      return fail(DD_ERR_BUDGET, "batch shared-memory layout exceeds 227 KB");
+    }
+  } catch (const std::bad_alloc&) {
+    delete b;
+    return fail(DD_ERR_INVALID_ARG, "host allocation failed while building the batch");
+  }
+  *out = b;
+  return DD_OK;
+}
+
+dd_status dd_batch_destroy(dd_batch batch) {
+  delete batch;
+  return DD_OK;
+}
+
+dd_status dd_batch_workspace_bytes(dd_batch batch, size_t* bytes) {
+  if (!batch || !bytes) return fail(DD_ERR_INVALID_ARG, "batch or bytes is NULL");
+  *bytes = batch->ws_bytes;
+  return DD_OK;
+}
+
+dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs) {
+  if (!batch || !n_items || !n_jobs) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+  *n_items = static_cast<int64_t>(batch->items.size());
+  *n_jobs = static_cast<int32_t>(batch->jobs.size());
+  return DD_OK;
+}
+
+dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void* stream) {
+  if (!batch || !d_workspace) return fail(DD_ERR_INVALID_ARG, "batch or workspace is NULL");
+  if (bytes < batch->ws_bytes) return fail(DD_ERR_BUDGET, "workspace smaller than needed");
+  if (reinterpret_cast<uintptr_t>(d_workspace) & 255u)
+    return fail(DD_ERR_SHAPE, "batch workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  cudaError_t e = cudaMemcpyAsync(ws + batch->off_items, batch->items.data(),
+                                  batch->items.size() * sizeof(tk::BatchItem),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_batch_upload");
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_batch_upload device query");
+  batch->sm_count = sms;
+  batch->d_ws = ws;
+  batch->bound = false;
+  return DD_OK;
+}
+
+dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
+                        void* const* d_out, void* stream) {
+  if (!batch || !d_in || !in_row_stride || !d_out)
+    return fail(DD_ERR_INVALID_ARG, "NULL argument");
+  if (!batch->d_ws) return fail(DD_ERR_INVALID_ARG, "batch has no uploaded workspace");
+  for (size_t j = 0; j < batch->jobs.size(); ++j) {
+    const auto& jr = batch->jobs[j];
+    const dd_plan p = batch->plans[jr.plan];
+    if (!p->d_ws) return fail(DD_ERR_INVALID_ARG, "a batch plan has no uploaded workspace");
+    const void* x = d_in[jr.plan];
+    void* o = d_out[jr.plan];
+    const int64_t stride = in_row_stride[jr.plan];
+    const int64_t n = batch->n_samp[jr.plan];
+    const size_t esz = p->dtype == DD_U8 ? 1 : (p->dtype == DD_U16 ? 2 : 4);
+    if (!x || !o) return fail(DD_ERR_INVALID_ARG, "NULL input or output pointer");
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(o) & 15u) ||
+        stride < n || (stride * static_cast<int64_t>(esz)) % 16 != 0)
+      return fail(DD_ERR_SHAPE, "batch input/output alignment or stride");
+    const RangePlan& rp = p->ranges[jr.range];
+    tk::BatchJob& bj = batch->host_jobs[j];
+    bj.p = tiled_params(p, rp, static_cast<unsigned char*>(p->d_ws) + rp.off_tile_recs,
+                        reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) +
+                                                   tk::kStatusOffset),
+                        x, stride, jr.n_out, static_cast<char*>(o) + jr.out_offset * 4);
+    bj.kind = p->dtype;
+    bj.dr = rp.tile_dr;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(batch->d_ws + batch->off_jobs, batch->host_jobs.data(),
+                                  batch->host_jobs.size() * sizeof(tk::BatchJob),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_batch_bind");
+  batch->bound = true;
+  return DD_OK;
+}
+
+dd_status dd_batch_run(dd_batch batch, void* stream) {
+  if (!batch) return fail(DD_ERR_INVALID_ARG, "batch is NULL");
+  if (!batch->bound) return fail(DD_ERR_INVALID_ARG, "batch is not bound (dd_batch_bind)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(batch->d_ws, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run counter reset");
+  tk::BatchArgs args{};
+  args.jobs = reinterpret_cast<const tk::BatchJob*>(batch->d_ws + batch->off_jobs);
+  args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + batch->off_items);
+  args.n_items = static_cast<int32_t>(batch->items.size());
+  args.counter = reinterpret_cast<uint32_t*>(batch->d_ws);
+  args.max_lraw = batch->max_lraw;
+  const tk::Shape& sh = tk::kBatchShapes[0];
+  const size_t smem = tk::batch_smem_bytes(sh, batch->max_lraw, batch->max_lp);
+  const int per_sm = smem * 2 <= 227 * 1024 ? sh.min_blocks : 1;
+  const int64_t grid = std::min<int64_t>(static_cast<int64_t>(batch->items.size()),
+                                         static_cast<int64_t>(batch->sm_count) * per_sm);
+  int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, stream);
+  if (le != 0) return cuda_fail(le, "dd_batch_run launch");
+  return DD_OK;
+}
+
+dd_status dd_batch_status(dd_batch batch, void* stream) {
+  if (!batch) return fail(DD_ERR_INVALID_ARG, "batch is NULL");
+  dd_status worst = DD_OK;
+  for (const dd_plan p : batch->plans) {
+    dd_status st = dd_plan_device_status(p, stream);
+    if (st != DD_OK) worst = st;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "dd.h"
+#include "fwd_tiled.h"
 
 namespace dd {
 
@@ -33,20 +34,25 @@ struct RangePlan {
   // Adjoint blocking: max over channel blocks and DMs of the in-block span.
   int32_t adj_span = 0;
 
-  // Register-tiled uint8 kernel (fwd_u8.cu), used when u8_ok.
-  bool u8_ok = false;
-  int32_t u8_dr = 0;            // DMs per warp of the chosen tile shape
-  int32_t u8_request = 0;       // tile requested by dd_plan_set_tile (0 = automatic)
-  int32_t u8_n_blocks = 0;      // DM blocks of u8_dr * warps DMs
-  int32_t u8_lp = 0;            // paired words per staged channel window
-  uint32_t u8_units_magic = 0;  // division by u8_lp / 4 (see fwd_u8.h)
-  int32_t u8_units_shift = 0;
+  // Register-tiled kernel (fwd_tiled.cu), used when tile_ok (time bin 1).
+  bool tile_ok = false;
+  int32_t tile_dr = 0;          // DMs per lane of the chosen tile shape
+  int32_t tile_request = 0;     // shape requested by dd_plan_set_tile (0 = automatic)
+  int32_t tile_n_blocks = 0;    // DM blocks of tile_dr * warps DMs
+  int32_t tile_lp = 0;          // window words per staged channel
+  uint32_t tile_units_magic = 0;  // division by tile_lp / 4 (see fwd_tiled.h)
+  int32_t tile_units_shift = 0;
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
-  size_t off_u8_recs = 0;       // u8k::Rec [u8_n_blocks][n_chan]
-  std::vector<unsigned char> u8_recs;  // host image of the records
+  size_t off_tile_recs = 0;     // tk::Rec [tile_n_blocks][n_chan]
+  std::vector<unsigned char> tile_recs;  // host image of the records
 };
+
+tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
+                            void* d_out);
+int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
 
 }  // namespace dd
 
@@ -80,16 +86,21 @@ int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
 int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                            int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
                            void* stream);
-int launch_forward_u8(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
-                      int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
-                      void* stream);
-// The uint8 tiled kernel with its record table and status word at explicit
-// device addresses (used by the no-allocation entry point).
-int launch_forward_u8_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
-                                  int32_t* err, const void* d_in, int64_t stride,
-                                  int64_t n_out, void* d_out, void* stream);
+int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
+                         int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
+                         void* stream);
+// The tiled kernel with its record table and status word at explicit device
+// addresses (used by the no-allocation entry point and the batch runtime).
+int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                                     int32_t* err, const void* d_in, int64_t stride,
+                                     int64_t n_out, void* d_out, void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);
+
+tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
+                            void* d_out);
+int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
 
 }  // namespace dd

@@ -1,0 +1,503 @@
+// fwd_tiled.cu -- register-tiled forward dedispersion kernels for sm_103a
+// (uint8, uint16 and float32 input at time bin 1), standalone and persistent.
+//
+// Computes Eq. 3 (Algorithm 1): Y[d][t] = sum_c X[c][t + s(c, d)], with the
+// output partition of the paper's GPU kernel (Sec. 4: a CTA owns D_dm x D_t
+// outputs and threads keep accumulators in registers, Algorithm 3), organised
+// for GB300's issue rate:
+//
+//  * CTA = W warps x 32 lanes owning dr * W consecutive DMs and one time tile.
+//    Warp w owns DMs d0 + dr*w .. d0 + dr*w + dr - 1; every lane owns the same
+//    dr DMs x 20 window words (uint8: 40 samples, two per word in 16-bit lanes
+//    as in Sec. 4.1's SIMD-within-a-word, pairing samples u and u + 640;
+//    uint16 / float32: 20 samples).
+//  * Staging (Algorithm 3's B_loc): per channel, the raw bytes of the window
+//    starting at t0 + s(c, d0) are fetched with one TMA bulk copy
+//    (cp.async.bulk, 16-byte aligned, completion on an mbarrier), two stages
+//    in flight; all threads then unpack them into 32-bit window words.
+//  * Register reuse across DMs: each lane loads its 36-word window of a
+//    channel once (9 x 16-byte shared loads, conflict-free with a 20-word lane
+//    stride) and adds it into all dr DMs.  DM i's offset inside the window is
+//    a per-(channel, warp) 4-bit value (the paper's T_diff * Delta t_pc of
+//    Eq. 6, resolved to an integer on the host); a warp-uniform indexed branch
+//    per DM selects the register slice (generated by gen_dispatch.py).
+//  * Accumulators are widened (uint8: every 256 channels) or stored through a
+//    transposed shared tile into the output rows with coalesced accesses.
+//
+// The persistent batch kernel runs the same tile body over a work list of
+// (job, DM block, time tile) items taken from a device counter.  Every wait
+// on an mbarrier is bounded; on timeout the kernel records kErrTimeout in the
+// status word and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "dd_internal.h"
+#include "fwd_tiled.h"
+#include "fwd_tiled_dispatch.inc"
+
+namespace dd {
+namespace tk {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitIters; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int KIND>
+using AccT = std::conditional_t<KIND == kF32, float, uint32_t>;
+template <int KIND>
+using OutT = std::conditional_t<KIND == kF32, float, int32_t>;
+
+struct Smem {
+  uint32_t bar_base;  // 2 mbarriers
+  Rec* recs;          // [2][NC]
+  uint8_t* raw;       // [2][NC][lraw]
+  uint32_t* pw;       // [NC][lp] window words
+};
+
+template <int NC>
+__device__ __forceinline__ Smem smem_layout(unsigned char* smem, int32_t lraw) {
+  constexpr size_t kRawOff = raw_offset(NC);
+  Smem sm;
+  sm.bar_base = smem_u32(smem);
+  sm.recs = reinterpret_cast<Rec*>(smem + kRecOffset);
+  sm.raw = smem + kRawOff;
+  sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
+  return sm;
+}
+
+// Issue the TMA copies of stage `st` into buffer `buf`.  Threads 0..NC-1 copy
+// one channel each, thread NC copies the stage's records.
+template <int KIND, int NC>
+__device__ __forceinline__ void issue_stage(const TileParams& p, const Smem& sm, int blk, int st,
+                                            int buf, int64_t t0, int32_t base, int tid) {
+  constexpr int kE = elem_bytes(KIND);
+  const uint32_t bar = sm.bar_base + 8u * buf;
+  const int c0 = st * NC;
+  if (tid < NC) {
+    const int c = c0 + tid;
+    uint32_t bytes = 0;
+    const uint8_t* src = nullptr;
+    if (c < p.n_chan) {
+      const int64_t ua = (t0 + base) & ~int64_t(align_samples(KIND) - 1);  // elements
+      if (ua < p.stride) {
+        const int64_t room = (p.stride - ua) * kE;
+        bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
+        src = static_cast<const uint8_t*>(p.x) + (static_cast<int64_t>(c) * p.stride + ua) * kE;
+      }
+    }
+    mbar_arrive_expect(bar, bytes);
+    if (bytes) {
+      uint8_t* dst = sm.raw + (static_cast<size_t>(buf) * NC + tid) * p.lraw;
+      bulk_copy(smem_u32(dst), src, bytes, bar);
+    }
+  } else if (tid == NC) {
+    const int nc = min(NC, p.n_chan - c0);
+    const uint32_t bytes = static_cast<uint32_t>(nc) * sizeof(Rec);
+    mbar_arrive_expect(bar, bytes);
+    const Rec* src = p.recs + static_cast<int64_t>(blk) * p.n_chan + c0;
+    bulk_copy(smem_u32(sm.recs + buf * NC), src, bytes, bar);
+  }
+}
+
+// Unpack raw bytes into four window words (unit q of one channel).
+template <int KIND>
+__device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q) {
+  uint4 v;
+  if constexpr (KIND == kU8) {
+    // Word k packs X[k] and X[k + kPair] in its 16-bit lanes.
+    const uint32_t a = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q);
+    const uint32_t b = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q + kPair);
+    const uint32_t t01 = __byte_perm(a, b, 0x5140);
+    const uint32_t t23 = __byte_perm(a, b, 0x7362);
+    v.x = __byte_perm(t01, 0u, 0x4140);
+    v.y = __byte_perm(t01, 0u, 0x4342);
+    v.z = __byte_perm(t23, 0u, 0x4140);
+    v.w = __byte_perm(t23, 0u, 0x4342);
+  } else if constexpr (KIND == kU16) {
+    const uint2 a = *reinterpret_cast<const uint2*>(raw_ch + 8 * q);
+    v.x = __byte_perm(a.x, 0u, 0x4410);
+    v.y = __byte_perm(a.x, 0u, 0x4432);
+    v.z = __byte_perm(a.y, 0u, 0x4410);
+    v.w = __byte_perm(a.y, 0u, 0x4432);
+  } else {
+    v = *reinterpret_cast<const uint4*>(raw_ch + 16 * q);
+  }
+  return v;
+}
+
+template <int KIND, int DR>
+__device__ __forceinline__ void dispatch(AccT<KIND> (&acc)[DR][kH], const AccT<KIND> (&R)[kWin],
+                                         uint32_t dl) {
+  uint32_t ix[DR];
+#pragma unroll
+  for (int i = 0; i < DR; ++i) ix[i] = (dl >> (4 * i)) & 15u;
+  if constexpr (KIND == kF32) {
+    if constexpr (DR == 1) DD_TILE_CHANNEL_F32_1(acc, R, ix);
+    else if constexpr (DR == 2) DD_TILE_CHANNEL_F32_2(acc, R, ix);
+    else if constexpr (DR == 4) DD_TILE_CHANNEL_F32_4(acc, R, ix);
+    else if constexpr (DR == 6) DD_TILE_CHANNEL_F32_6(acc, R, ix);
+    else DD_TILE_CHANNEL_F32_8(acc, R, ix);
+  } else {
+    if constexpr (DR == 1) DD_TILE_CHANNEL_U32_1(acc, R, ix);
+    else if constexpr (DR == 2) DD_TILE_CHANNEL_U32_2(acc, R, ix);
+    else if constexpr (DR == 4) DD_TILE_CHANNEL_U32_4(acc, R, ix);
+    else if constexpr (DR == 6) DD_TILE_CHANNEL_U32_6(acc, R, ix);
+    else DD_TILE_CHANNEL_U32_8(acc, R, ix);
+  }
+}
+
+// Store (first) or add (later) the accumulators into the output rows through
+// the warp's transposed shared tile.  Index f(p) = p + p / 160 is
+// conflict-free for the lane-major writes (p = 20 l + j) and the row-major
+// reads (p = 32 k + l).
+template <int KIND, int DR, int NW>
+__device__ __forceinline__ void widen_store(const TileParams& p, const Smem& sm,
+                                            AccT<KIND> (&acc)[DR][kH], int blk, int64_t t0,
+                                            bool first) {
+  constexpr int kTileS = tile_samples(KIND);
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  uint32_t* tr = sm.pw + w * kFlushWords;
+  const int wbase = kH * l + (l >> 3);
+  const int64_t lim = p.n_out - t0;
+#pragma unroll
+  for (int i = 0; i < DR; ++i) {
+    const int d = blk * (DR * NW) + w * DR + i;
+#pragma unroll
+    for (int j = 0; j < kH; ++j) {
+      if constexpr (KIND == kU8) {
+        const uint32_t v = acc[i][j];
+        tr[wbase + j] = v & 0xffffu;
+        tr[wbase + j + kPair + 4] = v >> 16;
+        acc[i][j] = 0u;
+      } else if constexpr (KIND == kU16) {
+        tr[wbase + j] = acc[i][j];
+        acc[i][j] = 0u;
+      } else {
+        tr[wbase + j] = __float_as_uint(acc[i][j]);
+        acc[i][j] = 0.f;
+      }
+    }
+    __syncwarp();
+    if (d < p.n_dm) {
+      OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+      constexpr int kHalf = kTileS / 64;  // two halves of kTileS / 64 positions per lane
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        OutT<KIND> v[kHalf];
+#pragma unroll
+        for (int k = 0; k < kHalf; ++k) {
+          const int kk = h * kHalf + k;
+          const uint32_t bits = tr[32 * kk + l + kk / 5];
+          if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
+          else v[k] = static_cast<int32_t>(bits);
+        }
+        if (!first) {
+          OutT<KIND> g[kHalf];
+#pragma unroll
+          for (int k = 0; k < kHalf; ++k) {
+            const int pos = 32 * (h * kHalf + k) + l;
+            g[k] = pos < lim ? __ldcg(row + pos) : OutT<KIND>(0);
+          }
+#pragma unroll
+          for (int k = 0; k < kHalf; ++k) v[k] += g[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kHalf; ++k) {
+          const int pos = 32 * (h * kHalf + k) + l;
+          if (pos < lim) row[pos] = v[k];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// One (DM block, time tile) work unit.  gstage counts pipeline stages across
+// the work units a CTA runs, so mbarrier phases continue from unit to unit.
+// Returns false after a bounded wait gave up (the status word is set).
+template <int KIND, int DR, int NW, int NC>
+__device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, int blk,
+                                          int64_t tile, uint32_t& gstage) {
+  constexpr int kThreads = NW * 32;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int64_t t0 = tile * tile_samples(KIND);
+  const int n_st = (p.n_chan + NC - 1) / NC;
+
+  const Rec* my_recs = p.recs + static_cast<int64_t>(blk) * p.n_chan;
+  auto base_of = [&](int st) -> int32_t {
+    const int c = st * NC + tid;
+    return (tid < NC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
+  };
+  if (tid <= NC) {
+    issue_stage<KIND, NC>(p, sm, blk, 0, gstage & 1, t0, base_of(0), tid);
+    if (n_st > 1) issue_stage<KIND, NC>(p, sm, blk, 1, (gstage + 1) & 1, t0, base_of(1), tid);
+  }
+  int32_t next_base = base_of(2);
+
+  AccT<KIND> acc[DR][kH];
+#pragma unroll
+  for (int i = 0; i < DR; ++i)
+#pragma unroll
+    for (int j = 0; j < kH; ++j) acc[i][j] = AccT<KIND>(0);
+
+  bool first = true;
+  int since = 0;  // channels accumulated since the last widen
+  const int units = p.lp >> 2;
+
+  for (int st = 0; st < n_st; ++st) {
+    const uint32_t g = gstage + st;
+    const int buf = g & 1;
+    const uint32_t parity = (g >> 1) & 1;
+    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(p.err, kErrTimeout);
+        // Let copies still in flight land before the CTA exits (bounded).
+        mbar_wait(sm.bar_base + 8u * buf, parity);
+        if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((g + 1) >> 1) & 1);
+      }
+      return false;
+    }
+    const int nc = min(NC, p.n_chan - st * NC);
+
+    {  // Unpack raw bytes into window words.
+      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
+      const int total = nc * units;
+      for (int u = tid; u < total; u += kThreads) {
+        const int ch =
+            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
+        const int q = u - ch * units;
+        const uint4 v = unpack_unit<KIND>(rawb + static_cast<size_t>(ch) * p.lraw, q);
+        *reinterpret_cast<uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
+      }
+    }
+    __syncthreads();
+
+    // Shift-and-sum.  The loop stays rolled so the dispatch block, and its PTX
+    // labels, appear once per instantiation.
+    const Rec* rs = sm.recs + buf * NC;
+#pragma unroll 1
+    for (int ch = 0; ch < nc; ++ch) {
+      const uint32_t dl = rs[ch].delta[w];
+      const int a = 4 * static_cast<int>(rs[ch].aq[w]);
+      const uint4* src = reinterpret_cast<const uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp +
+                                                         kH * l + a);
+      AccT<KIND> R[kWin];
+#pragma unroll
+      for (int k = 0; k < kWin / 4; ++k) {
+        const uint4 v = src[k];
+        if constexpr (KIND == kF32) {
+          R[4 * k] = __uint_as_float(v.x);
+          R[4 * k + 1] = __uint_as_float(v.y);
+          R[4 * k + 2] = __uint_as_float(v.z);
+          R[4 * k + 3] = __uint_as_float(v.w);
+        } else {
+          R[4 * k] = v.x;
+          R[4 * k + 1] = v.y;
+          R[4 * k + 2] = v.z;
+          R[4 * k + 3] = v.w;
+        }
+      }
+      dispatch<KIND, DR>(acc, R, dl);
+    }
+    since += nc;
+    __syncthreads();  // window words, raw[buf] and recs[buf] are free
+
+    if (tid <= NC && st + 2 < n_st) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_stage<KIND, NC>(p, sm, blk, st + 2, buf, t0, next_base, tid);
+      next_base = base_of(st + 3);
+    }
+    if (since + NC > flush_channels(KIND) || st == n_st - 1) {
+      widen_store<KIND, DR, NW>(p, sm, acc, blk, t0, first);
+      first = false;
+      since = 0;
+    }
+  }
+  gstage += n_st;
+  __syncthreads();  // the transpose tile (window buffer) is free for the next unit
+  return true;
+}
+
+template <int NC>
+__device__ __forceinline__ void init_barriers(const Smem& sm) {
+  if (threadIdx.x == 0) {
+    mbar_init(sm.bar_base, NC + 1);
+    mbar_init(sm.bar_base + 8, NC + 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+template <int KIND, int DR, int NW, int MINB, int NC>
+__global__ void __launch_bounds__(NW * 32, MINB) fwd_tiled_kernel(const TileParams p) {
+  static_assert(NW * kFlushWords <= NC * 672, "transpose tiles must fit the window buffer");
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Smem sm = smem_layout<NC>(smem, p.lraw);
+  init_barriers<NC>(sm);
+  uint32_t gstage = 0;
+  tile_body<KIND, DR, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks, gstage);
+}
+
+template <int NW, int MINB, int NC>
+__global__ void __launch_bounds__(NW * 32, MINB) fwd_batch_kernel(const BatchArgs b) {
+  static_assert(NW * kFlushWords <= NC * 672, "transpose tiles must fit the window buffer");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int item_slot;
+  const Smem sm = smem_layout<NC>(smem, b.max_lraw);
+  init_barriers<NC>(sm);
+  uint32_t gstage = 0;
+  for (;;) {
+    if (threadIdx.x == 0) item_slot = static_cast<int>(atomicAdd(b.counter, 1u));
+    __syncthreads();
+    const int it = item_slot;
+    if (it >= b.n_items) break;
+    const BatchItem item = b.items[it];
+    const BatchJob& job = b.jobs[item.job];
+    // The shared-memory layout is sized for the largest raw window and window
+    // of any job; a job indexes the raw buffers with its own (smaller) lraw.
+    const Smem& jsm = sm;
+    const TileParams p = job.p;
+    bool ok = true;
+    switch (job.kind * 16 + job.dr) {
+      case kU8 * 16 + 4: ok = tile_body<kU8, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kU8 * 16 + 2: ok = tile_body<kU8, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kU8 * 16 + 1: ok = tile_body<kU8, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kU16 * 16 + 4: ok = tile_body<kU16, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kU16 * 16 + 2: ok = tile_body<kU16, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kU16 * 16 + 1: ok = tile_body<kU16, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kF32 * 16 + 4: ok = tile_body<kF32, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kF32 * 16 + 2: ok = tile_body<kF32, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      case kF32 * 16 + 1: ok = tile_body<kF32, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
+      default: ok = true; break;
+    }
+    if (!ok) break;
+  }
+}
+
+}  // namespace tk
+
+namespace {
+
+template <int KIND, int DR, int NW, int MINB, int NC>
+int launch_tiled_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  const tk::Shape* sh = tk::shape_for(DR);
+  const size_t smem = tk::smem_bytes(KIND, *sh, prm.lp);
+  auto kern = tk::fwd_tiled_kernel<KIND, DR, NW, MINB, NC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<static_cast<unsigned>(grid), NW * 32, smem, st>>>(prm);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <int KIND>
+int launch_kind(int dr, const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  switch (dr) {
+    case 8: return launch_tiled_shape<KIND, 8, 8, 1, 16>(prm, grid, st);
+    case 6: return launch_tiled_shape<KIND, 6, 12, 1, 24>(prm, grid, st);
+    case 4: return launch_tiled_shape<KIND, 4, 8, 2, 16>(prm, grid, st);
+    case 2: return launch_tiled_shape<KIND, 2, 8, 2, 16>(prm, grid, st);
+    case 1: return launch_tiled_shape<KIND, 1, 8, 2, 16>(prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+}  // namespace
+
+tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
+                            void* d_out) {
+  tk::TileParams prm{};
+  prm.x = d_in;
+  prm.stride = stride;
+  prm.n_chan = p->n_chan;
+  prm.recs = static_cast<const tk::Rec*>(recs);
+  prm.n_dm = static_cast<int32_t>(rp.n_dm);
+  prm.n_blocks = rp.tile_n_blocks;
+  prm.n_out = n_out;
+  prm.lp = rp.tile_lp;
+  prm.lraw = tk::raw_bytes(p->dtype, rp.tile_lp);
+  prm.units_magic = rp.tile_units_magic;
+  prm.units_shift = rp.tile_units_shift;
+  prm.out = d_out;
+  prm.err = err;
+  return prm;
+}
+
+int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                                     int32_t* err, const void* d_in, int64_t stride,
+                                     int64_t n_out, void* d_out, void* stream) {
+  const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
+  const int64_t tiles = (n_out + tk::tile_samples(p->dtype) - 1) / tk::tile_samples(p->dtype);
+  const int64_t grid = tiles * rp.tile_n_blocks;
+  if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (p->dtype) {
+    case DD_U8: return launch_kind<tk::kU8>(rp.tile_dr, prm, grid, st);
+    case DD_U16: return launch_kind<tk::kU16>(rp.tile_dr, prm, grid, st);
+    case DD_F32: return launch_kind<tk::kF32>(rp.tile_dr, prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
+                         int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
+                         void* stream) {
+  (void)n_samp;
+  const unsigned char* ws = static_cast<const unsigned char*>(p->d_ws);
+  return launch_forward_tiled_with_tables(
+      p, rp, ws + rp.off_tile_recs,
+      reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) + tk::kStatusOffset), d_in,
+      stride, n_out, d_out, stream);
+}
+
+int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream) {
+  auto kern = tk::fwd_batch_kernel<8, 2, 16>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<grid, 8 * 32, smem, static_cast<cudaStream_t>(stream)>>>(args);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace dd

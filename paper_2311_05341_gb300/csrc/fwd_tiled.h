@@ -1,0 +1,143 @@
+// fwd_tiled.h -- geometry, device table record and launch parameters of the
+// register-tiled forward kernels (fwd_tiled.cu), shared with the planner and
+// the batch runtime.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define DD_HOST_DEVICE __host__ __device__
+#else
+#define DD_HOST_DEVICE
+#endif
+
+namespace dd {
+namespace tk {
+
+// Sample kinds of the tiled kernels (values equal dd_dtype).
+enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3 };
+
+constexpr int kH = 20;               // window words per lane per DM (the register tile width)
+constexpr int kMaxOff = 15;          // largest in-window DM offset (4-bit field)
+constexpr int kWin = 36;             // window words per lane (>= kH + kMaxOff, multiple of 4)
+constexpr int kPair = 32 * kH;       // uint8: word u packs samples u and u + kPair
+constexpr int kFlushWords = 1288;    // per-warp transpose tile (1280 + 1280/160 pad)
+constexpr int kMaxWarps = 12;
+constexpr int kWaitIters = 1 << 22;  // bound on every mbarrier wait loop
+constexpr int kErrTimeout = 1;       // device status bit: a bounded wait gave up
+constexpr size_t kStatusOffset = 0;  // status word at the start of the plan workspace
+constexpr size_t kStatusBytes = 256;
+
+// Samples held by one 32-bit window word: uint8 packs two (16-bit lanes).
+DD_HOST_DEVICE constexpr int samples_per_word(int kind) { return kind == kU8 ? 2 : 1; }
+// Output samples per CTA tile: 32 lanes x kH words x samples per word.
+DD_HOST_DEVICE constexpr int tile_samples(int kind) { return 32 * kH * samples_per_word(kind); }
+DD_HOST_DEVICE constexpr int elem_bytes(int kind) { return kind == kU8 ? 1 : (kind == kU16 ? 2 : 4); }
+// Samples in 16 bytes: TMA copies start 16-byte aligned, so a window starts up
+// to align_samples - 1 samples before the block's base shift.
+DD_HOST_DEVICE constexpr int align_samples(int kind) { return 16 / elem_bytes(kind); }
+// Channels between widenings of the accumulators: uint8 lanes hold 16 bits
+// (255 * 256 < 2^16); uint16 sums stay below 2^31 for 32768 channels; float
+// never needs one.
+DD_HOST_DEVICE constexpr int flush_channels(int kind) {
+  return kind == kU8 ? 256 : (kind == kU16 ? 32768 : (1 << 30));
+}
+
+// Tile shapes: DMs per lane (the register tile is dr DMs x kH words), warps
+// per CTA, CTAs per SM and channels per pipeline stage.  Fewer DMs per lane
+// free registers for more resident warps and admit steeper plans (a wider
+// per-warp shift span) at the cost of more shared-memory traffic per add.
+struct Shape {
+  int dr;
+  int warps;
+  int min_blocks;
+  int nc;
+};
+constexpr Shape kShapes[] = {{8, 8, 1, 16}, {6, 12, 1, 24}, {4, 8, 2, 16}, {2, 8, 2, 16},
+                             {1, 8, 2, 16}};
+// The persistent batch kernel serves every plan with one resource footprint.
+constexpr Shape kBatchShapes[] = {{4, 8, 2, 16}, {2, 8, 2, 16}, {1, 8, 2, 16}};
+
+inline const Shape* shape_for(int dr) {
+  for (const Shape& s : kShapes)
+    if (s.dr == dr) return &s;
+  return nullptr;
+}
+
+// Per (DM block of dr * warps DMs, channel) record, 64 bytes (TMA-copyable).
+struct Rec {
+  int32_t base;               // s(c, first DM of the block)
+  uint32_t delta[kMaxWarps];  // dr x 4-bit in-window offsets of warp w's DMs
+  uint8_t aq[kMaxWarps];      // warp w's window start, in 16-byte units
+};
+static_assert(sizeof(Rec) == 64, "Rec must stay 64 bytes");
+
+constexpr size_t kRecOffset = 128;
+DD_HOST_DEVICE constexpr size_t raw_offset(int nc) {
+  return (kRecOffset + 2 * static_cast<size_t>(nc) * sizeof(Rec) + 127) / 128 * 128;
+}
+
+// Words of a channel's staged window for a given DM-block shift span.
+inline int32_t window_words(int kind, int32_t span) {
+  const int32_t need = kH * 31 + span + (align_samples(kind) - 1) + kWin;
+  return (need + 15) / 16 * 16;
+}
+
+// Raw bytes fetched per channel and stage for lp window words.
+DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int32_t lp) {
+  return kind == kU8 ? lp + kPair : lp * elem_bytes(kind);
+}
+
+inline size_t smem_bytes(int kind, const Shape& s, int32_t lp) {
+  return raw_offset(s.nc) + 2 * static_cast<size_t>(s.nc) * raw_bytes(kind, lp) +
+         static_cast<size_t>(s.nc) * lp * 4;
+}
+
+// One (DM block, time tile) work unit of one range.
+struct TileParams {
+  const void* x;        // channel-major input rows
+  int64_t stride;       // elements between channel rows
+  int32_t n_chan;
+  const Rec* recs;      // [n_blocks][n_chan]
+  int32_t n_dm;
+  int32_t n_blocks;
+  int64_t n_out;
+  int32_t lp;           // window words per staged channel
+  int32_t lraw;         // raw bytes per staged channel
+  uint32_t units_magic; // u / (lp/4) == (u * magic) >> (32 + shift)
+  int32_t units_shift;
+  void* out;            // [n_dm][n_out] int32 or float32
+  int32_t* err;
+};
+
+// Persistent batch execution: one work list of (job, DM block, time tile)
+// items over many jobs (plan ranges with their input/output pointers).
+struct BatchJob {
+  TileParams p;
+  int32_t kind;  // kU8 / kU16 / kF32
+  int32_t dr;    // DMs per lane (a kBatchShapes entry)
+};
+
+struct BatchItem {
+  int32_t job;
+  int32_t blk;
+  int32_t tile;
+  int32_t pad;
+};
+
+struct BatchArgs {
+  const BatchJob* jobs;    // device
+  const BatchItem* items;  // device, in execution order
+  int32_t n_items;
+  uint32_t* counter;       // device, zero before the launch
+  int32_t max_lraw;        // largest raw window of any job (shared-memory layout)
+};
+
+inline size_t batch_smem_bytes(const Shape& s, int32_t max_lraw, int32_t max_lp) {
+  return raw_offset(s.nc) + 2 * static_cast<size_t>(s.nc) * max_lraw +
+         static_cast<size_t>(s.nc) * max_lp * 4;
+}
+
+}  // namespace tk
+}  // namespace dd

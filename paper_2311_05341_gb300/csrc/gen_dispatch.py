@@ -1,0 +1,69 @@
+#!/usr/bin/env python3
+"""Generates the per-channel DM-offset dispatch used by fwd_tiled.cu.
+
+For a register tile of DR DMs per lane, DD_TILE_CHANNEL_<OP>_<DR>(A, R, IX)
+adds, for every DM i < DR, the 20-word register slice R[IX[i] .. IX[i] + 20)
+of the lane's 36-word window into the accumulators A[i][0 .. 20), with IX[i]
+in [0, 16).  OP is U32 (packed 16-bit lanes or uint16 samples in 32-bit words)
+or F32 (float samples).
+
+Each macro is one inline-PTX block laid out as a chain of indexed branches:
+block (i, k) does the 20 adds of DM i at offset k and then jumps straight to
+block (i + 1, IX[i + 1]) with a warp-uniform brx.idx, so each DM costs one
+indexed branch and no join branch.  (A C++ switch over the same cases became
+a chain of compares and branches.)  The build writes the result into the
+build directory; nothing generated is committed.
+"""
+import os
+import sys
+
+H, CASES, WIN = 20, 16, 36
+SHAPES = (1, 2, 4, 6, 8)
+OPS = {"U32": ("add.u32", "r"), "F32": ("add.f32", "f")}
+
+
+def macro(op, dr):
+    instr, cons = OPS[op]
+    tag = f"ddt{op.lower()}{dr}"
+    nacc = dr * H
+    lines = ['"{\\n\\t"']
+    for i in range(dr):
+        targets = ", ".join(f"{tag}_d{i}_k{k}" for k in range(CASES))
+        lines.append(f'"{tag}_t{i}: .branchtargets {targets};\\n\\t"')
+    lines.append(f'"brx.idx.uni %{nacc + WIN}, {tag}_t0;\\n\\t"')
+    for i in range(dr):
+        for k in range(CASES):
+            lines.append(f'"{tag}_d{i}_k{k}:\\n\\t"')
+            for j in range(H):
+                lines.append(f'"{instr} %{i * H + j}, %{i * H + j}, %{nacc + k + j};\\n\\t"')
+            if i + 1 < dr:
+                lines.append(f'"brx.idx.uni %{nacc + WIN + i + 1}, {tag}_t{i + 1};\\n\\t"')
+            elif k != CASES - 1:
+                lines.append(f'"bra.uni {tag}_end;\\n\\t"')
+    lines.append(f'"{tag}_end:\\n\\t}}"')
+    outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(dr) for j in range(H))
+    ins = ", ".join(f'"{cons}"(R[{j}])' for j in range(WIN))
+    ins += ", " + ", ".join(f'"r"(IX[{i}])' for i in range(dr))
+    out = [f"#define DD_TILE_CHANNEL_{op}_{dr}(A, R, IX) \\", "  asm volatile( \\"]
+    out += [f"      {ln} \\" for ln in lines]
+    out.append(f"      : {outs} \\")
+    out.append(f"      : {ins})")
+    return out
+
+
+def generate(path):
+    out = ["// Generated by gen_dispatch.py at build time.", "#pragma once"]
+    for op in OPS:
+        for dr in SHAPES:
+            out += macro(op, dr)
+            out.append("")
+    text = "\n".join(out) + "\n"
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    return path
+
+
+if __name__ == "__main__":
+    print(generate(sys.argv[1] if len(sys.argv) > 1 else "fwd_tiled_dispatch.inc"))

@@ -15,7 +15,7 @@
 #include <cstring>
 
 #include "dd_internal.h"
-#include "fwd_u8.h"
+#include "fwd_tiled.h"
 
 namespace dd {
 
@@ -43,26 +43,28 @@ int32_t block_span(const RangePlan& rp, int32_t n_chan, int32_t per_block) {
   return span;
 }
 
-// Records of the register-tiled uint8 kernel for a tile shape with dr DMs per
-// warp and W warps.  For DM block b (first DM d0, dr * W DMs), channel c and
-// warp w (DMs d0 + dr*w + i, i < dr, clamped to the last DM):
-//   base  = s(c, d0),  m = base mod 16 (the TMA copy starts 16-byte aligned),
+// Records of the register-tiled kernel for a tile shape with dr DMs per lane
+// and W warps.  For DM block b (first DM d0, dr * W DMs), channel c and warp w
+// (DMs d0 + dr*w + i, i < dr, clamped to the last DM):
+//   base  = s(c, d0),  m = base mod A (A samples in 16 bytes: the TMA copy of
+//           the channel's window starts 16-byte aligned),
 //   D_i   = s(c, d0 + dr*w + i) - base + m   (word offset inside the staged window),
 //   a_w   = 4 * floor(D_0 / 4)                (16-byte aligned window start),
 //   off_i = D_i - a_w                          (must fit in 4 bits).
 // Returns false if some offset does not fit.
-bool build_u8_records(const RangePlan& rp, int32_t n_chan, const u8k::Shape& sh,
-                      std::vector<u8k::Rec>& recs, int32_t* n_blocks_out) {
-  using namespace u8k;
+bool build_tile_records(const RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh,
+                        std::vector<tk::Rec>& recs, int32_t* n_blocks_out) {
+  using namespace tk;
   const int dm_cta = sh.dr * sh.warps;
+  const int32_t align = align_samples(kind);
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
-  recs.assign(static_cast<size_t>(n_blocks) * n_chan, u8k::Rec{});
+  recs.assign(static_cast<size_t>(n_blocks) * n_chan, tk::Rec{});
   for (int64_t b = 0; b < n_blocks; ++b) {
     const int64_t d0 = b * dm_cta;
     for (int32_t c = 0; c < n_chan; ++c) {
-      u8k::Rec& r = recs[static_cast<size_t>(b) * n_chan + c];
+      tk::Rec& r = recs[static_cast<size_t>(b) * n_chan + c];
       const int32_t base = rp.shifts[static_cast<size_t>(d0) * n_chan + c];
-      const int32_t m = base & 15;
+      const int32_t m = base % align;
       r.base = base;
       for (int w = 0; w < sh.warps; ++w) {
         int32_t a_w = 0;
@@ -105,58 +107,59 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
 }
 
 
-// Try one tile shape for a uint8 range; on success fill the range's u8 fields.
-bool try_u8_shape(RangePlan& rp, int32_t n_chan, const u8k::Shape& sh) {
+// Try one tile shape for a range; on success fill the range's tile fields.
+bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh) {
   const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
-  const int32_t lp = u8k::window_words(span);
-  if (u8k::smem_bytes(sh, lp) * sh.min_blocks > 227 * 1024) return false;
+  const int32_t lp = tk::window_words(kind, span);
+  if (tk::smem_bytes(kind, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
   uint32_t magic = 0;
   int32_t shift = 0;
   if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(sh.nc * lp / 4), &magic,
                       &shift))
     return false;
-  std::vector<u8k::Rec> recs;
+  std::vector<tk::Rec> recs;
   int32_t n_blocks = 0;
-  if (!build_u8_records(rp, n_chan, sh, recs, &n_blocks)) return false;
-  rp.u8_ok = true;
-  rp.u8_dr = sh.dr;
-  rp.u8_n_blocks = n_blocks;
-  rp.u8_lp = lp;
-  rp.u8_units_magic = magic;
-  rp.u8_units_shift = shift;
-  rp.u8_recs.resize(recs.size() * sizeof(u8k::Rec));
-  std::memcpy(rp.u8_recs.data(), recs.data(), rp.u8_recs.size());
+  if (!build_tile_records(rp, n_chan, kind, sh, recs, &n_blocks)) return false;
+  rp.tile_ok = true;
+  rp.tile_dr = sh.dr;
+  rp.tile_n_blocks = n_blocks;
+  rp.tile_lp = lp;
+  rp.tile_units_magic = magic;
+  rp.tile_units_shift = shift;
+  rp.tile_recs.resize(recs.size() * sizeof(tk::Rec));
+  std::memcpy(rp.tile_recs.data(), recs.data(), rp.tile_recs.size());
   return true;
 }
 
-// Register-tiled uint8 kernel: 8-bit input at time bin 1 whose per-warp DM
+// Register-tiled kernel: time bin 1 and a tile shape whose per-warp DM
 // offsets fit the 4-bit fields and whose window fits shared memory.  The
-// automatic choice takes the first shape that fits in kAutoOrder.
-void choose_u8(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
-  static const int kAutoOrder[] = {6, 8, 4};
-  rp.u8_ok = false;
-  rp.u8_dr = 0;
-  rp.u8_recs.clear();
-  if (dtype != DD_U8 || rp.r.bin != 1) return;
-  if (rp.u8_request > 0) {
-    const u8k::Shape* sh = u8k::shape_for(rp.u8_request);
-    if (sh) try_u8_shape(rp, n_chan, *sh);
+// automatic choice takes the first shape that fits in kAutoOrder (fewer DMs
+// per lane serve steeper plans).
+void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
+  static const int kAutoOrder[] = {6, 4, 2, 1};
+  rp.tile_ok = false;
+  rp.tile_dr = 0;
+  rp.tile_recs.clear();
+  if (rp.r.bin != 1) return;
+  if (rp.tile_request > 0) {
+    const tk::Shape* sh = tk::shape_for(rp.tile_request);
+    if (sh) try_tile_shape(rp, n_chan, dtype, *sh);
     return;
   }
   for (int dr : kAutoOrder)
-    if (try_u8_shape(rp, n_chan, *u8k::shape_for(dr))) return;
+    if (try_tile_shape(rp, n_chan, dtype, *tk::shape_for(dr))) return;
 }
 
 void layout_workspace(dd_plan_s* p) {
-  size_t ws = u8k::kStatusBytes;  // device status word(s) first
+  size_t ws = tk::kStatusBytes;  // device status word(s) first
   for (auto& rp : p->ranges) {
     ws = align_up(ws, 256);
     rp.off_shifts = ws;
     ws += rp.shifts.size() * sizeof(int32_t);
-    if (rp.u8_ok) {
+    if (rp.tile_ok) {
       ws = align_up(ws, 256);
-      rp.off_u8_recs = ws;
-      ws += rp.u8_recs.size();
+      rp.off_tile_recs = ws;
+      ws += rp.tile_recs.size();
     }
   }
   p->ws_bytes = align_up(ws, 256);
@@ -164,8 +167,8 @@ void layout_workspace(dd_plan_s* p) {
   for (const auto& rp : p->ranges) {
     std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
                 rp.shifts.size() * sizeof(int32_t));
-    if (rp.u8_ok)
-      std::memcpy(p->host_ws.data() + rp.off_u8_recs, rp.u8_recs.data(), rp.u8_recs.size());
+    if (rp.tile_ok)
+      std::memcpy(p->host_ws.data() + rp.off_tile_recs, rp.tile_recs.data(), rp.tile_recs.size());
   }
 }
 
@@ -224,7 +227,7 @@ dd_status build_plan(dd_plan_s* p) {
     }
     rp.adj_span = aspan;
 
-    choose_u8(rp, n_chan, p->dtype);
+    choose_tile(rp, n_chan, p->dtype);
   }
   layout_workspace(p);
   return DD_OK;
@@ -232,12 +235,12 @@ dd_status build_plan(dd_plan_s* p) {
 
 bool retile_range(dd_plan_s* p, size_t range, int32_t request) {
   RangePlan& rp = p->ranges[range];
-  const int32_t old = rp.u8_request;
-  rp.u8_request = request;
-  choose_u8(rp, p->n_chan, p->dtype);
-  if (request > 0 && !rp.u8_ok) {
-    rp.u8_request = old;
-    choose_u8(rp, p->n_chan, p->dtype);
+  const int32_t old = rp.tile_request;
+  rp.tile_request = request;
+  choose_tile(rp, p->n_chan, p->dtype);
+  if (request > 0 && !rp.tile_ok) {
+    rp.tile_request = old;
+    choose_tile(rp, p->n_chan, p->dtype);
     layout_workspace(p);
     return false;
   }

@@ -16,12 +16,12 @@
 #include <string>
 
 #include "dd_internal.h"
-#include "fwd_u8.h"
+#include "fwd_tiled.h"
 
 namespace dd {
 namespace {
 
-// Status word (u8k::kStatusBytes) followed by each range's record table.
+// Status word (tk::kStatusBytes) followed by each range's record table.
 constexpr size_t kStaticScratchBytes = size_t{8} << 20;  // 8 MiB
 static_assert(kStaticScratchBytes % 256 == 0, "scratch size must keep 256-byte alignment");
 
@@ -67,13 +67,13 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
   if (in_row_stride % 16 != 0) return fail(DD_ERR_SHAPE, "row stride must be a multiple of 16 bytes");
 
   // Every range must run on the tiled kernel, and all tables must fit.
-  size_t need = u8k::kStatusBytes;
+  size_t need = tk::kStatusBytes;
   for (const RangePlan& rp : plan->ranges) {
-    if (!rp.u8_ok)
-      return fail(DD_ERR_UNSUPPORTED, "dd_run_u8_noalloc needs every range on the uint8 tiled kernel");
+    if (!rp.tile_ok)
+      return fail(DD_ERR_UNSUPPORTED, "dd_run_u8_noalloc needs every range on the tiled kernel");
     if (range_n_out(plan, rp, n_samp) <= 0)
       return fail(DD_ERR_SHAPE, "input shorter than a range's maximum delay");
-    need = align256(need) + rp.u8_recs.size();
+    need = align256(need) + rp.tile_recs.size();
   }
   if (align256(need) > kStaticScratchBytes)
     return fail(DD_ERR_BUDGET, "plan tables need " + std::to_string(align256(need)) +
@@ -85,22 +85,22 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
   if (st != DD_OK) return st;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int32_t* err = reinterpret_cast<int32_t*>(scratch + u8k::kStatusOffset);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, u8k::kStatusBytes, s);
+  int32_t* err = reinterpret_cast<int32_t*>(scratch + tk::kStatusOffset);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, tk::kStatusBytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc: clear status");
-  size_t off = u8k::kStatusBytes;
+  size_t off = tk::kStatusBytes;
   int64_t out_off = 0;
   for (const RangePlan& rp : plan->ranges) {
     off = align256(off);
-    e = cudaMemcpyAsync(scratch + off, rp.u8_recs.data(), rp.u8_recs.size(),
+    e = cudaMemcpyAsync(scratch + off, rp.tile_recs.data(), rp.tile_recs.size(),
                         cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc: copy tables");
     const int64_t n_out = range_n_out(plan, rp, n_samp);
     int32_t* o = static_cast<int32_t*>(d_out) + out_off;
-    int le = launch_forward_u8_with_tables(plan, rp, scratch + off, err, d_in, in_row_stride,
-                                           n_out, o, stream);
+    int le = launch_forward_tiled_with_tables(plan, rp, scratch + off, err, d_in, in_row_stride,
+                                              n_out, o, stream);
     if (le != 0) return cuda_fail(le, "dd_run_u8_noalloc launch");
-    off += rp.u8_recs.size();
+    off += rp.tile_recs.size();
     out_off += rp.n_dm * n_out;
   }
   return DD_OK;

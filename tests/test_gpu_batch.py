@@ -1,0 +1,97 @@
+"""The persistent batch (one launch over many uneven beams, CUDA graph).
+
+Each beam's output in the batch must equal its output alone (bit for bit: the
+same tile arithmetic runs in both), the alone output must match the oracle,
+and a replayed graph must follow new input contents.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_05341_gb300 import batch as ddb
+from synth import channel_freqs, filterbank
+
+from gpu_util import assert_float_parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _beams():
+    """Uneven beams: channel counts, dtypes, sampling times and DM plans differ."""
+    out = []
+    f = channel_freqs(1520.0, 310.0, 256)
+    out.append(ddb.BeamSpec(f, 1520.0, 64e-6, [(0.0, 25.6, 0.1, 1)], "u8", 9000))
+    f = channel_freqs(1400.0, 300.0, 300)
+    out.append(ddb.BeamSpec(f, 1400.0, 64e-6, [(0.0, 6.4, 0.05, 1), (6.4, 12.8, 0.1, 1)], "u8",
+                            7001))
+    f = channel_freqs(1670.0, 320.0, 512)
+    out.append(ddb.BeamSpec(f, 1670.0, 54.6e-6, [(0.0, 19.2, 0.2, 1)], "u16", 6000))
+    f = channel_freqs(400.0, 100.0, 96)
+    out.append(ddb.BeamSpec(f, 400.0, 327.68e-6, [(0.0, 6.4, 0.2, 1)], "f32", 5000))
+    f = channel_freqs(1500.0, 300.0, 130)
+    out.append(ddb.BeamSpec(f, 1500.0, 128e-6, [(0.0, 12.0, 0.2, 1)], "f32", 4001))
+    return out
+
+
+_NOISE = {"u8": (np.uint8, 128, 40), "u16": (np.uint16, 32768, 9000),
+          "f32": (np.float32, 0.0, 1.0)}
+
+
+def _fill(runner, seed0):
+    hosts = []
+    for i, (b, x) in enumerate(zip(runner.beams, runner.inputs)):
+        npdt, mean, sd = _NOISE[b.dtype]
+        h = filterbank(npdt, len(b.freqs), b.n_samp, seed0 + i, mean, sd)
+        x[:, : b.n_samp].copy_(torch.from_numpy(h).to(x.device))
+        hosts.append(h)
+    torch.cuda.synchronize()
+    return hosts
+
+
+def _check_oracle(b, host, planes):
+    ref = oracle.forward(host, b.freqs, b.f_ref, b.t_samp, b.ranges)
+    for r, (g, o) in enumerate(zip(planes, ref)):
+        g = g.cpu().numpy()
+        if b.dtype == "f32":
+            ab = oracle.forward(host, b.freqs, b.f_ref, b.t_samp, b.ranges, take_abs=True)[r]
+            assert_float_parity(g, o, ab, f"range {r}")
+        else:
+            np.testing.assert_array_equal(g, o)
+
+
+def test_batch_equals_alone_and_oracle():
+    runner = ddb.BatchRunner(_beams(), autotune=True, graph=True)
+    assert runner.n_jobs == 6
+    assert all(dr in (4, 2, 1) for shp in runner.shapes for dr in shp)
+    hosts = _fill(runner, 600)
+    runner.run()
+    torch.cuda.synchronize()
+    runner.status()
+    batched = [o.clone() for o in runner.outputs]
+    runner.run_per_beam()
+    torch.cuda.synchronize()
+    for i, (bo, o) in enumerate(zip(batched, runner.outputs)):
+        assert torch.equal(bo, o), f"beam {i} differs between batch and alone"
+    for i, b in enumerate(runner.beams):
+        _check_oracle(b, hosts[i], runner.planes(i))
+
+
+def test_graph_replay_follows_new_inputs():
+    runner = ddb.BatchRunner(_beams()[:3], autotune=False, graph=True)
+    _fill(runner, 700)
+    runner.run()
+    hosts = _fill(runner, 800)
+    for o in runner.outputs:
+        o.fill_(-1)
+    runner.run()
+    runner.run()
+    torch.cuda.synchronize()
+    for i, b in enumerate(runner.beams):
+        _check_oracle(b, hosts[i], runner.planes(i))

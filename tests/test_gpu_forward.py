@@ -101,8 +101,8 @@ def test_random_cases_full_planes(seed):
             np.testing.assert_array_equal(g, o, err_msg=f"range {r}")
 
 
-def _tiled_case(seed):
-    """uint8 plans on the register-tiled kernel: shallow DM steps, ragged sizes."""
+def _tiled_case(seed, dtype="u8"):
+    """Plans on the register-tiled kernel: shallow DM steps, ragged sizes."""
     rng = np.random.default_rng(seed)
     n_chan = int(rng.choice([1, 15, 17, 255, 256, 257, 300, 513]))
     f_high = float(rng.uniform(800, 1700))
@@ -114,24 +114,33 @@ def _tiled_case(seed):
     lo = float(rng.uniform(0, 50)) * step
     r = (lo, lo + n_dm * step, step, 1)
     s_max, _ = oracle.extent(freqs, f_high, t_samp, r, 10 ** 9)
-    n_samp = int(s_max + rng.choice([1, 1279, 1280, 1281, 5000]))
-    return _Beam(freqs, f_high, t_samp, [r], "u8", n_samp), rng
+    n_samp = int(s_max + rng.choice([1, 639, 640, 1279, 1280, 1281, 5000]))
+    return _Beam(freqs, f_high, t_samp, [r], dtype, n_samp), rng
 
 
-@pytest.mark.parametrize("seed", range(16))
-def test_u8_tiled_full_planes(seed):
-    b, rng = _tiled_case(seed)
-    # Values up to 255 in every channel exercise the 16-bit lane bound (256 channels).
-    x = filterbank(np.uint8, len(b.freqs), b.n_samp, 8000 + seed, 200, 80)
+_NOISE = {"u8": (np.uint8, 200, 80), "u16": (np.uint16, 40000, 12000), "f32": (np.float32, 0.0, 1.0)}
+
+
+@pytest.mark.parametrize("dtype,seed", [("u8", s) for s in range(16)] +
+                         [("u16", s) for s in range(8)] + [("f32", s) for s in range(8)])
+def test_tiled_full_planes_every_shape(dtype, seed):
+    b, rng = _tiled_case(seed, dtype)
+    npdt, mean, sd = _NOISE[dtype]
+    # uint8 values up to 255 in every channel exercise the 16-bit lane bound.
+    x = filterbank(npdt, len(b.freqs), b.n_samp, 8000 + seed, mean, sd)
     ref = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges)
+    ref_abs = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges, take_abs=True)
     xd = padded_device(x)
-    for dms in (8, 6, 4):
-        plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, "u8")
+    for dms in (8, 6, 4, 2, 1):
+        plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
         info = plan.info(b.n_samp)
-        assert info["kernel"] == ["u8_tiled"] and info["tile_dms"] == [dms]
+        assert info["kernel"] == ["tiled"] and info["tile_dms"] == [dms]
         got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
-        np.testing.assert_array_equal(got, ref[0], err_msg=f"tile {dms}")
+        if dtype == "f32":
+            assert_float_parity(got, ref[0], ref_abs[0], f"tile {dms}")
+        else:
+            np.testing.assert_array_equal(got, ref[0], err_msg=f"tile {dms}")
 
 
 def test_u8_tiled_saturated_input():

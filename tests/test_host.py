@@ -140,13 +140,26 @@ def test_too_short_input_is_reported():
 def test_kernel_selection():
     paper = workloads.paper_u8()
     plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
-    assert plan.info(paper.n_samp)["kernel"] == ["u8_tiled"]
+    info = plan.info(paper.n_samp)
+    assert info["kernel"] == ["tiled"] and info["tile_dms"] == [6]
+    # Binned ranges run on the generic kernel.
     stream = workloads.stream_beam(0, 90168)
     plan = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, stream.ranges, "u8", upload=False)
-    assert plan.info(stream.n_samp)["kernel"][0] == "u8_tiled"
-    tiny = workloads.tiny_u8()  # 8 samples of delay per DM step: too steep for 4-bit offsets
+    assert plan.info(stream.n_samp)["kernel"] == ["tiled", "generic", "generic", "generic"]
+    # 8 samples of delay per DM step: only 2 DMs per lane fit the 4-bit offsets.
+    tiny = workloads.tiny_u8()
     plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
-    assert plan.info(tiny.n_samp)["kernel"] == ["generic"]
+    assert plan.info(tiny.n_samp)["tile_dms"] == [2]
+    with pytest.raises(dd.DDError) as ei:
+        plan.set_tile(0, 4)
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    assert plan.info(tiny.n_samp)["tile_dms"] == [2]
     f32 = workloads.diff_f32()
     plan = dd.Plan(f32.freqs, f32.f_high, f32.t_samp, f32.ranges, "f32", upload=False)
-    assert plan.info(f32.n_samp)["kernel"] == ["generic"]
+    assert plan.info(f32.n_samp)["kernel"] == ["tiled"]
+    u16 = workloads.batched()[24]  # 2.9 samples of delay per DM step
+    plan = dd.Plan(u16.freqs, u16.f_high, u16.t_samp, u16.ranges, "u16", upload=False)
+    assert plan.info(u16.n_samp)["tile_dms"] == [4]
+    fb = workloads.batched()[32]  # 12.3 samples of delay per DM step
+    plan = dd.Plan(fb.freqs, fb.f_high, fb.t_samp, fb.ranges, "f32", upload=False)
+    assert plan.info(fb.n_samp)["tile_dms"] == [1]

@@ -35,7 +35,7 @@ def test_noalloc_matches_dd_run_twice():
     beam = workloads.batched()[0]  # 1024 ch x 131072 samples, 2048 DMs, uint8
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, "u8")
     info = plan.info(beam.n_samp)
-    assert info["kernel"] == ["u8_tiled"]
+    assert info["kernel"] == ["tiled"]
     x_np = filterbank(np.uint8, beam.n_chan, beam.n_samp, beam.seed, 200, 80)
     x = torch.from_numpy(x_np).cuda()
     ref = plan.empty_output(beam.n_samp)
@@ -61,7 +61,11 @@ def test_noalloc_rejects_plans_it_cannot_serve():
     big = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
     assert _noalloc(big, x, paper.n_samp, out, stride=paper.n_samp) == _lib.DD_ERR_BUDGET
     assert "at most" in _lib.load().dd_last_error_detail().decode()
-    # A plan on the generic kernel (8 samples of delay per DM step) is refused.
+    # A plan with binned ranges (generic kernel) and a float32 plan are refused.
+    stream = workloads.stream_beam(0, 90168)
+    binned = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, stream.ranges, "u8", upload=False)
+    assert _noalloc(binned, x, stream.n_samp, out, stride=stream.n_samp + 8) == \
+        _lib.DD_ERR_UNSUPPORTED
     tiny = workloads.tiny_u8()
-    steep = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
-    assert _noalloc(steep, x, 4096, out) == _lib.DD_ERR_UNSUPPORTED
+    f32 = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "f32", upload=False)
+    assert _noalloc(f32, x, 4096, out) == _lib.DD_ERR_UNSUPPORTED
