@@ -314,6 +314,160 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """Config 3: 24 u8 + 8 u16 + 4 f32 beams, one persistent launch (CUDA graph)
+    against the plain path (one dd_run per beam, each plan's own best tile)."""
+    import torch
+    import paper_2311_05341_gb300 as dd
+    from paper_2311_05341_gb300 import batch as ddb
+    from synth import workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    beams = workloads.batched()
+    specs = [ddb.BeamSpec(b.freqs, b.f_high, b.t_samp, b.ranges, b.dtype, b.n_samp) for b in beams]
+    runner = ddb.BatchRunner(specs, autotune=True, graph=True)
+    for b, x in zip(beams, runner.inputs):
+        h = workloads.make_input(b, lambda r, d, b=b: _plan_shifts_cache(b)[r][d], *_sizes(b))
+        x[:, : b.n_samp].copy_(torch.from_numpy(h).to(x.device))
+    torch.cuda.synchronize()
+    plain = [dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, b.dtype) for b in beams]
+    plain_out = [p.empty_output(b.n_samp) for p, b in zip(plain, beams)]
+    units = sum(sum(a * c for a, c in zip(p.info(b.n_samp)["n_dm"], p.info(b.n_samp)["n_out"]))
+                for p, b in zip(plain, beams))
+    adds = sum(sum(a * c for a, c in zip(p.info(b.n_samp)["n_dm"], p.info(b.n_samp)["n_out"]))
+               * b.n_chan for p, b in zip(plain, beams))
+
+    def plain_step():
+        for p, x, o, b in zip(plain, runner.inputs, plain_out, beams):
+            p.run(x, out=o, n_samp=b.n_samp)
+
+    def time(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps / 1e3
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_plain = time(plain_step)
+    t_batch = time(runner.run)
+    clk = clocks.stop()
+    runner.status()
+    same = all(torch.equal(a, c) for a, c in zip(plain_out, runner.outputs))
+    line = {
+        "metric": METRIC, "value": units / t_batch, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+        "data": "synthetic",
+        "config": {"workload": "batched: 24 x u8 1024 ch x 131072 (2048 DMs step 0.1), "
+                               "8 x u16 4096 ch x 65536 at 54.6 us (3072 DMs step 0.2), "
+                               "4 x f32 336 ch x 32768 at 327.68 us (1024 DMs step 0.2)",
+                   "beams": len(beams), "work_items": runner.n_items,
+                   "tiles_dms_per_lane": runner.shapes[0] + runner.shapes[24] + runner.shapes[32]},
+        "channel_adds_per_s": adds / t_batch,
+        "plain_per_beam": {"value": units / t_plain, "ms_per_step": t_plain * 1e3},
+        "batched_over_plain": t_plain / t_batch,
+        "outputs_identical_to_plain": bool(same),
+        "gpu_launches": 1, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+def run_stream(args):
+    """Config 5: 64 u8 beams of 4096 channels, chunks of 65536 samples, Poisson
+    arrivals at m x real time, 4-range decimated plan, HBM-budget admission."""
+    import torch
+    from paper_2311_05341_gb300 import stream as dds
+    from synth import poisson_arrivals, workloads, filterbank
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    chunk, n_beams = 65536, 64
+    beam0 = workloads.stream_beam(0, chunk)
+    spec = dds.StreamSpec(beam0.freqs, beam0.f_high, beam0.t_samp, beam0.ranges, "u8")
+    pool = [torch.from_numpy(filterbank(np.uint8, beam0.n_chan, chunk, 5000 + i, 128, 16))
+            .pin_memory() for i in range(4)]
+    chunk_s = chunk * beam0.t_samp
+    results = []
+    plan_cache = {}
+    for m in args.stream_rates:
+        srv = dds.StreamServer(chunk, int(args.hbm_budget_gb * 2**30), plan_cache=plan_cache)
+        need = srv.beam_bytes(spec)
+        rng = np.random.default_rng(int(m * 1000))
+        n_chunks = rng.integers(2, 6, n_beams)
+        sched = []
+        for b in range(n_beams):
+            ts = poisson_arrivals(7000 + b + int(m * 100), m / chunk_s, int(n_chunks[b]))
+            sched += [(float(t), b) for t in ts]
+        sched.sort()
+        for b in range(n_beams):
+            srv.request(b, spec)
+        sent = {b: 0 for b in range(n_beams)}
+        pending_release = set()
+        t0 = time.perf_counter()
+        i = 0
+        while True:
+            now = time.perf_counter() - t0
+            if now > args.stream_seconds:
+                break
+            while i < len(sched) and sched[i][0] <= now:
+                _, b = sched[i]
+                srv.submit(b, pool[(b + sent[b]) % len(pool)], arrival=t0 + sched[i][0])
+                sent[b] += 1
+                if sent[b] == n_chunks[b]:
+                    pending_release.add(b)
+                i += 1
+            srv.pump()
+            for b in list(pending_release):
+                if srv.is_admitted(b) and not any(j.beam == b for j in list(srv.queue) +
+                                                  srv.inflight):
+                    srv.release(b)
+                    pending_release.discard(b)
+            if i >= len(sched) and not srv.queue and not srv.inflight and not pending_release:
+                break
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        st = srv.stats()
+        dm_samples_per_chunk = sum(
+            n * (chunk // r[3]) for n, r in zip(srv._plan(spec).info(0)["n_dm"], spec.ranges))
+        results.append({"rate_x_realtime": m, "wall_s": wall, **st,
+                        "beam_bytes": need,
+                        "data_seconds_done": st["chunks"] * chunk_s,
+                        "real_time_factor_aggregate": st["chunks"] * chunk_s / wall,
+                        "dm_samples_per_s": st["chunks"] * dm_samples_per_chunk / wall})
+    print(json.dumps({"metric": "p50/p99 chunk latency, real-time factor",
+                      "workload": "stream: 64 beams u8 4096 ch, 1670 MHz top, 320 MHz band, "
+                                  "64 us, chunks 65536 + overlap; DM 0-150/0.1 b1, 150-300/0.2 b2, "
+                                  "300-1000/0.5 b4, 1000-2000/1.0 b8",
+                      "hbm_budget_gb": args.hbm_budget_gb, "results": results}))
+
+
+_SHIFT_CACHE = {}
+
+
+def _plan_shifts_cache(beam):
+    import paper_2311_05341_gb300 as dd
+    key = beam.name.rsplit("_", 1)[0]
+    if key not in _SHIFT_CACHE:
+        p = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype, upload=False)
+        _SHIFT_CACHE[key] = ([p.shifts(r) for r in range(len(beam.ranges))], p.info(beam.n_samp))
+    return _SHIFT_CACHE[key][0]
+
+
+def _sizes(beam):
+    _plan_shifts_cache(beam)
+    inf = _SHIFT_CACHE[beam.name.rsplit("_", 1)[0]][1]
+    return inf["n_dm"], inf["n_out"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,7 +475,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_u8",
-                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32"])
+                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32", "batched", "stream"])
+    ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
+    ap.add_argument("--stream-seconds", type=float, default=15.0)
+    ap.add_argument("--hbm-budget-gb", type=float, default=60.0)
     ap.add_argument("--cpu-rows", type=int, default=24)
     ap.add_argument("--cpu-rows-reference", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
@@ -329,6 +486,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "stream":
+        run_stream(args)
     else:
         run_ours(args)
 

@@ -223,9 +223,10 @@ dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t in_row_strid
 typedef struct dd_batch_s* dd_batch;
 
 /* Build the work list for n_plans plans and their raw sample counts.  Every
- * range must be on the tiled kernel with 4, 2 or 1 DMs per lane (time bin 1),
- * else DD_ERR_UNSUPPORTED; DD_ERR_SHAPE if an input is shorter than a range's
- * maximum delay. */
+ * range must be on the tiled kernel with 4, 2 or 1 DMs per lane, else
+ * DD_ERR_UNSUPPORTED; DD_ERR_BUDGET if the plans' windows together exceed the
+ * persistent kernel's shared memory; DD_ERR_SHAPE if an input is shorter than
+ * a range's maximum delay. */
 dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n_plans,
                           dd_batch* out);
 dd_status dd_batch_destroy(dd_batch batch);

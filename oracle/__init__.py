@@ -87,6 +87,10 @@ def _load():
             lib.oracle_adjoint.argtypes = [
                 c_double_p, ctypes.c_int32, ctypes.c_int64, c_double_p, ctypes.c_double,
                 ctypes.c_double, ctypes.POINTER(Range), ctypes.c_int32, c_double_p]
+            lib.oracle_adjoint_channels.argtypes = [
+                c_double_p, ctypes.c_int32, ctypes.c_int64, c_double_p, ctypes.c_double,
+                ctypes.c_double, ctypes.POINTER(Range), ctypes.c_int32,
+                ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, c_double_p]
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -221,6 +225,24 @@ def adjoint(ybar_planes, n_chan: int, n_samp: int, freqs, f_ref: float, t_samp: 
                                 float(t_samp), arr, len(rs), _dp(out))
     if rc != 0:
         raise ValueError(f"oracle_adjoint failed ({rc})")
+    return out
+
+
+def adjoint_channels(ybar_planes, n_chan: int, n_samp: int, freqs, f_ref: float, t_samp: float,
+                     ranges, chans) -> np.ndarray:
+    """FP64 [len(chans)][n_samp]: the transpose's rows for the listed channels."""
+    f = _f64(freqs)
+    rs = [_range(r) for r in ranges]
+    flat = np.ascontiguousarray(np.concatenate([_f64(p).ravel() for p in ybar_planes]))
+    ch = np.ascontiguousarray(np.asarray(chans, dtype=np.int32))
+    out = np.zeros((ch.size, n_samp), dtype=np.float64)
+    arr = (Range * len(rs))(*rs)
+    rc = _load().oracle_adjoint_channels(_dp(flat), int(n_chan), int(n_samp), _dp(f),
+                                         float(f_ref), float(t_samp), arr, len(rs),
+                                         ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         ch.size, _dp(out))
+    if rc != 0:
+        raise ValueError(f"oracle_adjoint_channels failed ({rc})")
     return out
 
 

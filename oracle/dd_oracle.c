@@ -189,10 +189,12 @@ int oracle_forward(int dtype, const void* x, int32_t n_chan, int64_t n_samp,
   return 0;
 }
 
-int oracle_adjoint(const double* ybar, int32_t n_chan, int64_t n_samp,
-                   const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
-                   const oracle_range* ranges, int32_t n_ranges, double* xbar) {
-  if (!ybar || !xbar || !ranges || n_ranges <= 0 || n_samp <= 0) return -1;
+/* Transpose for a list of channels (all channels when chans is NULL). */
+static int adjoint_impl(const double* ybar, int32_t n_chan, int64_t n_samp,
+                        const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
+                        const oracle_range* ranges, int32_t n_ranges, const int32_t* chans,
+                        int32_t n_sel, double* xbar) {
+  if (!ybar || !xbar || !ranges || n_ranges <= 0 || n_samp <= 0 || n_sel < 0) return -1;
   int64_t* n_outs = (int64_t*)malloc((size_t)n_ranges * sizeof(int64_t));
   int64_t* offsets = (int64_t*)malloc((size_t)n_ranges * sizeof(int64_t));
   if (!n_outs || !offsets) { free(n_outs); free(offsets); return -3; }
@@ -208,13 +210,17 @@ int oracle_adjoint(const double* ybar, int32_t n_chan, int64_t n_samp,
     offsets[k] = offset;
     offset += oracle_range_ndm(ranges[k]) * n_out;
   }
-  memset(xbar, 0, (size_t)n_chan * (size_t)n_samp * sizeof(double));
+  for (int32_t i = 0; i < n_sel; ++i) {
+    if (chans && (chans[i] < 0 || chans[i] >= n_chan)) { free(n_outs); free(offsets); return -1; }
+  }
+  memset(xbar, 0, (size_t)n_sel * (size_t)n_samp * sizeof(double));
 
   /* Each output Y_r[d][t] read X[c][b*(t+s)+j] for j < b: send its cotangent
    * back to exactly those inputs.  Channels are independent. */
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int32_t c = 0; c < n_chan; ++c) {
-    double* xc = xbar + (int64_t)c * n_samp;
+  for (int32_t i = 0; i < n_sel; ++i) {
+    const int32_t c = chans ? chans[i] : i;
+    double* xc = xbar + (int64_t)i * n_samp;
     for (int32_t k = 0; k < n_ranges; ++k) {
       oracle_range r = ranges[k];
       int64_t n_dm = oracle_range_ndm(r);
@@ -231,6 +237,22 @@ int oracle_adjoint(const double* ybar, int32_t n_chan, int64_t n_samp,
   free(n_outs);
   free(offsets);
   return 0;
+}
+
+int oracle_adjoint(const double* ybar, int32_t n_chan, int64_t n_samp,
+                   const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
+                   const oracle_range* ranges, int32_t n_ranges, double* xbar) {
+  return adjoint_impl(ybar, n_chan, n_samp, freqs_mhz, f_ref_mhz, t_samp_s, ranges, n_ranges,
+                      NULL, n_chan, xbar);
+}
+
+int oracle_adjoint_channels(const double* ybar, int32_t n_chan, int64_t n_samp,
+                            const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
+                            const oracle_range* ranges, int32_t n_ranges, const int32_t* chans,
+                            int32_t n_sel, double* xbar) {
+  if (!chans) return -1;
+  return adjoint_impl(ybar, n_chan, n_samp, freqs_mhz, f_ref_mhz, t_samp_s, ranges, n_ranges,
+                      chans, n_sel, xbar);
 }
 
 int oracle_threads(void) {

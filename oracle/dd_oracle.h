@@ -100,6 +100,14 @@ int oracle_adjoint(const double* ybar, int32_t n_chan, int64_t n_samp,
                    const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
                    const oracle_range* ranges, int32_t n_ranges, double* xbar);
 
+/* The same transpose for the channels listed in chans[n_sel] only:
+ * xbar[i][t] is channel chans[i] of the full result (the plan's extents still
+ * come from all n_chan channels). */
+int oracle_adjoint_channels(const double* ybar, int32_t n_chan, int64_t n_samp,
+                            const double* freqs_mhz, double f_ref_mhz, double t_samp_s,
+                            const oracle_range* ranges, int32_t n_ranges, const int32_t* chans,
+                            int32_t n_sel, double* xbar);
+
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int oracle_threads(void);
 

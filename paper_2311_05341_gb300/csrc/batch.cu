@@ -44,8 +44,8 @@ namespace {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 bool batch_shape(int32_t dr) {
-  for (const dd::tk::Shape& s : dd::tk::kBatchShapes)
-    if (s.dr == dr) return true;
+  for (int d : dd::tk::kBatchDr)
+    if (d == dr && dd::tk::shape_for(dr)->warps == dd::tk::kBatchWarps) return true;
   return false;
 }
 
@@ -83,7 +83,7 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
           delete b;
           return fail(DD_ERR_UNSUPPORTED,
                       "batch plan " + std::to_string(i) + " range " + std::to_string(r) +
-                          " is not on a batch tile shape (time bin 1, 4/2/1 DMs per lane; see "
+                          " is not on a batch tile shape (a tiled bin, 4/2/1 DMs per lane; see "
                           "dd_plan_set_tile)");
         }
         const int64_t n_out = range_n_out(p, rp, n_samp[i]);
@@ -94,10 +94,11 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
         const int32_t job = static_cast<int32_t>(b->jobs.size());
         b->jobs.push_back({i, static_cast<int32_t>(r), n_out, out_off});
         out_off += rp.n_dm * n_out;
-        b->max_lraw = std::max(b->max_lraw, tk::raw_bytes(p->dtype, rp.tile_lp));
+        b->max_lraw = std::max(b->max_lraw, tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp));
         b->max_lp = std::max(b->max_lp, rp.tile_lp);
         const double dms = static_cast<double>(tk::shape_for(rp.tile_dr)->warps) * rp.tile_dr;
-        order.push_back({static_cast<double>(p->n_chan) * dms * tk::tile_samples(p->dtype), job});
+        order.push_back({static_cast<double>(p->n_chan) * dms * tk::tile_samples(rp.tile_kind) *
+                             rp.r.bin, job});
       }
     }
     // Longest items first; within a job, DM blocks of a time tile together.
@@ -107,7 +108,8 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       const auto& j = b->jobs[c.job];
       const dd_plan p = b->plans[j.plan];
       const RangePlan& rp = p->ranges[j.range];
-      const int64_t tiles = (j.n_out + tk::tile_samples(p->dtype) - 1) / tk::tile_samples(p->dtype);
+      const int64_t tiles =
+          (j.n_out + tk::tile_samples(rp.tile_kind) - 1) / tk::tile_samples(rp.tile_kind);
       for (int64_t t = 0; t < tiles; ++t)
         for (int32_t blk = 0; blk < rp.tile_n_blocks; ++blk)
           b->items.push_back({c.job, blk, static_cast<int32_t>(t), 0});
@@ -125,7 +127,7 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
     ws += b->items.size() * sizeof(tk::BatchItem);
     b->ws_bytes = align256(ws);
     b->host_jobs.resize(b->jobs.size());
-    const size_t smem = tk::batch_smem_bytes(tk::kBatchShapes[0], b->max_lraw, b->max_lp);
+    const size_t smem = tk::batch_smem_bytes(b->max_lraw, b->max_lp);
     if (smem > 227 * 1024) {
       delete b;
       return fail(DD_ERR_BUDGET, "batch shared-memory layout exceeds 227 KB");
@@ -202,7 +204,7 @@ dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* 
                         reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) +
                                                    tk::kStatusOffset),
                         x, stride, jr.n_out, static_cast<char*>(o) + jr.out_offset * 4);
-    bj.kind = p->dtype;
+    bj.kind = rp.tile_kind;
     bj.dr = rp.tile_dr;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -227,11 +229,9 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
   args.n_items = static_cast<int32_t>(batch->items.size());
   args.counter = reinterpret_cast<uint32_t*>(batch->d_ws);
   args.max_lraw = batch->max_lraw;
-  const tk::Shape& sh = tk::kBatchShapes[0];
-  const size_t smem = tk::batch_smem_bytes(sh, batch->max_lraw, batch->max_lp);
-  const int per_sm = smem * 2 <= 227 * 1024 ? sh.min_blocks : 1;
+  const size_t smem = tk::batch_smem_bytes(batch->max_lraw, batch->max_lp);
   const int64_t grid = std::min<int64_t>(static_cast<int64_t>(batch->items.size()),
-                                         static_cast<int64_t>(batch->sm_count) * per_sm);
+                                         static_cast<int64_t>(batch->sm_count));
   int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, stream);
   if (le != 0) return cuda_fail(le, "dd_batch_run launch");
   return DD_OK;

@@ -37,6 +37,7 @@ struct RangePlan {
   // Register-tiled kernel (fwd_tiled.cu), used when tile_ok (time bin 1).
   bool tile_ok = false;
   int32_t tile_dr = 0;          // DMs per lane of the chosen tile shape
+  int32_t tile_kind = 0;        // window-word kind (tk::Kind)
   int32_t tile_request = 0;     // shape requested by dd_plan_set_tile (0 = automatic)
   int32_t tile_n_blocks = 0;    // DM blocks of tile_dr * warps DMs
   int32_t tile_lp = 0;          // window words per staged channel

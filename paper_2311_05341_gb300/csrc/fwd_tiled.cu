@@ -21,8 +21,12 @@
 //    a per-(channel, warp) 4-bit value (the paper's T_diff * Delta t_pc of
 //    Eq. 6, resolved to an integer on the host); a warp-uniform indexed branch
 //    per DM selects the register slice (generated by gen_dispatch.py).
-//  * Accumulators are widened (uint8: every 256 channels) or stored through a
-//    transposed shared tile into the output rows with coalesced accesses.
+//  * Time binning (Sec. 5.3) is fused into the unpacking: at bin b a window
+//    word is the sum of b consecutive raw samples (uint8 then uses one
+//    decimated sample per word).
+//  * Accumulators are widened (uint8 pairs: every 256 channels) or stored
+//    through a transposed shared tile into the output rows with coalesced
+//    accesses.
 //
 // The persistent batch kernel runs the same tile body over a work list of
 // (job, DM block, time tile) items taken from a device counter.  Every wait
@@ -81,6 +85,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 template <int KIND>
 using AccT = std::conditional_t<KIND == kF32, float, uint32_t>;
+// Input element of a kind (one raw sample).
 template <int KIND>
 using OutT = std::conditional_t<KIND == kF32, float, int32_t>;
 
@@ -115,7 +120,8 @@ __device__ __forceinline__ void issue_stage(const TileParams& p, const Smem& sm,
     uint32_t bytes = 0;
     const uint8_t* src = nullptr;
     if (c < p.n_chan) {
-      const int64_t ua = (t0 + base) & ~int64_t(align_samples(KIND) - 1);  // elements
+      const int64_t align = 16 / (kE * p.bin);                       // decimated samples, 2^k
+      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw elements
       if (ua < p.stride) {
         const int64_t room = (p.stride - ua) * kE;
         bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
@@ -136,12 +142,16 @@ __device__ __forceinline__ void issue_stage(const TileParams& p, const Smem& sm,
   }
 }
 
-// Unpack raw bytes into four window words (unit q of one channel).
+__device__ __forceinline__ uint32_t byte_sum4(uint32_t w) { return __dp4a(w, 0x01010101u, 0u); }
+__device__ __forceinline__ uint32_t half_sum2(uint32_t w) { return (w & 0xffffu) + (w >> 16); }
+
+// Unpack raw bytes into four window words (unit q of one channel).  At bin b
+// each word is the sum of b consecutive raw samples (the decimated sample).
 template <int KIND>
-__device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q) {
+__device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int bin) {
   uint4 v;
   if constexpr (KIND == kU8) {
-    // Word k packs X[k] and X[k + kPair] in its 16-bit lanes.
+    // Word k packs X[k] and X[k + kPair] in its 16-bit lanes (bin 1 only).
     const uint32_t a = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q);
     const uint32_t b = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q + kPair);
     const uint32_t t01 = __byte_perm(a, b, 0x5140);
@@ -150,14 +160,65 @@ __device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q) {
     v.y = __byte_perm(t01, 0u, 0x4342);
     v.z = __byte_perm(t23, 0u, 0x4140);
     v.w = __byte_perm(t23, 0u, 0x4342);
+  } else if constexpr (KIND == kU8W) {
+    const uint8_t* r = raw_ch + 4 * q * bin;
+    if (bin == 2) {
+      const uint2 a = *reinterpret_cast<const uint2*>(r);
+      const uint32_t s0 = (a.x & 0x00ff00ffu) + ((a.x >> 8) & 0x00ff00ffu);
+      const uint32_t s1 = (a.y & 0x00ff00ffu) + ((a.y >> 8) & 0x00ff00ffu);
+      v = make_uint4(s0 & 0xffffu, s0 >> 16, s1 & 0xffffu, s1 >> 16);
+    } else if (bin == 4) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      v = make_uint4(byte_sum4(a.x), byte_sum4(a.y), byte_sum4(a.z), byte_sum4(a.w));
+    } else if (bin == 8) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      const uint4 b = *reinterpret_cast<const uint4*>(r + 16);
+      v = make_uint4(byte_sum4(a.x) + byte_sum4(a.y), byte_sum4(a.z) + byte_sum4(a.w),
+                     byte_sum4(b.x) + byte_sum4(b.y), byte_sum4(b.z) + byte_sum4(b.w));
+    } else {  // bin 16
+      uint32_t o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint4 a = *reinterpret_cast<const uint4*>(r + 16 * k);
+        o[k] = byte_sum4(a.x) + byte_sum4(a.y) + byte_sum4(a.z) + byte_sum4(a.w);
+      }
+      v = make_uint4(o[0], o[1], o[2], o[3]);
+    }
   } else if constexpr (KIND == kU16) {
-    const uint2 a = *reinterpret_cast<const uint2*>(raw_ch + 8 * q);
-    v.x = __byte_perm(a.x, 0u, 0x4410);
-    v.y = __byte_perm(a.x, 0u, 0x4432);
-    v.z = __byte_perm(a.y, 0u, 0x4410);
-    v.w = __byte_perm(a.y, 0u, 0x4432);
-  } else {
-    v = *reinterpret_cast<const uint4*>(raw_ch + 16 * q);
+    const uint8_t* r = raw_ch + 8 * q * bin;
+    if (bin == 1) {
+      const uint2 a = *reinterpret_cast<const uint2*>(r);
+      v = make_uint4(a.x & 0xffffu, a.x >> 16, a.y & 0xffffu, a.y >> 16);
+    } else if (bin == 2) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      v = make_uint4(half_sum2(a.x), half_sum2(a.y), half_sum2(a.z), half_sum2(a.w));
+    } else {  // bin 4 or 8: bin / 2 words of two samples per output word
+      uint32_t o[4];
+      const int words = bin / 2;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t acc = 0;
+        for (int j = 0; j < words; ++j)
+          acc += half_sum2(*reinterpret_cast<const uint32_t*>(r + 4 * (k * words + j)));
+        o[k] = acc;
+      }
+      v = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  } else {  // kF32
+    const float* r = reinterpret_cast<const float*>(raw_ch + 16 * q * bin);
+    if (bin == 1) {
+      v = *reinterpret_cast<const uint4*>(r);
+    } else {
+      float o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float acc = 0.f;
+        for (int j = 0; j < bin; ++j) acc += r[k * bin + j];
+        o[k] = acc;
+      }
+      v = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                     __float_as_uint(o[3]));
+    }
   }
   return v;
 }
@@ -186,66 +247,78 @@ __device__ __forceinline__ void dispatch(AccT<KIND> (&acc)[DR][kH], const AccT<K
 // Store (first) or add (later) the accumulators into the output rows through
 // the warp's transposed shared tile.  Index f(p) = p + p / 160 is
 // conflict-free for the lane-major writes (p = 20 l + j) and the row-major
-// reads (p = 32 k + l).
-template <int KIND, int DR, int NW>
+// reads (p = 32 k + l).  The tiles live in the window buffer; when it cannot
+// hold one per warp, the warps take turns in `groups` rounds.  Called by every
+// thread of the CTA.
+template <int KIND, int DR, int NW, int NC>
 __device__ __forceinline__ void widen_store(const TileParams& p, const Smem& sm,
                                             AccT<KIND> (&acc)[DR][kH], int blk, int64_t t0,
                                             bool first) {
   constexpr int kTileS = tile_samples(KIND);
+  constexpr int kFw = flush_words(KIND);
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-  uint32_t* tr = sm.pw + w * kFlushWords;
+  // Window buffers are at least 672 words per channel, so many shapes fit one
+  // tile per warp at compile time.
+  constexpr bool kAllFit = NC * 672 >= NW * kFw;
+  const int fit = (NC * p.lp) / kFw;  // tiles that fit the window buffer
+  const int groups = kAllFit ? 1 : (NW + fit - 1) / fit;
+  uint32_t* tr = sm.pw + (w / groups) * kFw;
   const int wbase = kH * l + (l >> 3);
   const int64_t lim = p.n_out - t0;
+  for (int gi = 0; gi < groups; ++gi) {
+    if (gi > 0) __syncthreads();
+    if (w % groups != gi) continue;
 #pragma unroll
-  for (int i = 0; i < DR; ++i) {
-    const int d = blk * (DR * NW) + w * DR + i;
+    for (int i = 0; i < DR; ++i) {
+      const int d = blk * (DR * NW) + w * DR + i;
 #pragma unroll
-    for (int j = 0; j < kH; ++j) {
-      if constexpr (KIND == kU8) {
-        const uint32_t v = acc[i][j];
-        tr[wbase + j] = v & 0xffffu;
-        tr[wbase + j + kPair + 4] = v >> 16;
-        acc[i][j] = 0u;
-      } else if constexpr (KIND == kU16) {
-        tr[wbase + j] = acc[i][j];
-        acc[i][j] = 0u;
-      } else {
-        tr[wbase + j] = __float_as_uint(acc[i][j]);
-        acc[i][j] = 0.f;
-      }
-    }
-    __syncwarp();
-    if (d < p.n_dm) {
-      OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
-      constexpr int kHalf = kTileS / 64;  // two halves of kTileS / 64 positions per lane
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        OutT<KIND> v[kHalf];
-#pragma unroll
-        for (int k = 0; k < kHalf; ++k) {
-          const int kk = h * kHalf + k;
-          const uint32_t bits = tr[32 * kk + l + kk / 5];
-          if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
-          else v[k] = static_cast<int32_t>(bits);
+      for (int j = 0; j < kH; ++j) {
+        if constexpr (KIND == kU8) {
+          const uint32_t v = acc[i][j];
+          tr[wbase + j] = v & 0xffffu;
+          tr[wbase + j + kPair + 4] = v >> 16;
+          acc[i][j] = 0u;
+        } else if constexpr (KIND == kU16 || KIND == kU8W) {
+          tr[wbase + j] = acc[i][j];
+          acc[i][j] = 0u;
+        } else {
+          tr[wbase + j] = __float_as_uint(acc[i][j]);
+          acc[i][j] = 0.f;
         }
-        if (!first) {
-          OutT<KIND> g[kHalf];
+      }
+      __syncwarp();
+      if (d < p.n_dm) {
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        constexpr int kHalf = kTileS / 64;  // two halves of kTileS / 64 positions per lane
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          OutT<KIND> v[kHalf];
+#pragma unroll
+          for (int k = 0; k < kHalf; ++k) {
+            const int kk = h * kHalf + k;
+            const uint32_t bits = tr[32 * kk + l + kk / 5];
+            if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
+            else v[k] = static_cast<int32_t>(bits);
+          }
+          if (!first) {
+            OutT<KIND> g[kHalf];
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) {
+              const int pos = 32 * (h * kHalf + k) + l;
+              g[k] = pos < lim ? __ldcg(row + pos) : OutT<KIND>(0);
+            }
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) v[k] += g[k];
+          }
 #pragma unroll
           for (int k = 0; k < kHalf; ++k) {
             const int pos = 32 * (h * kHalf + k) + l;
-            g[k] = pos < lim ? __ldcg(row + pos) : OutT<KIND>(0);
+            if (pos < lim) row[pos] = v[k];
           }
-#pragma unroll
-          for (int k = 0; k < kHalf; ++k) v[k] += g[k];
-        }
-#pragma unroll
-        for (int k = 0; k < kHalf; ++k) {
-          const int pos = 32 * (h * kHalf + k) + l;
-          if (pos < lim) row[pos] = v[k];
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -304,7 +377,7 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
         const int ch =
             static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
         const int q = u - ch * units;
-        const uint4 v = unpack_unit<KIND>(rawb + static_cast<size_t>(ch) * p.lraw, q);
+        const uint4 v = unpack_unit<KIND>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
         *reinterpret_cast<uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
       }
     }
@@ -345,8 +418,8 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
       issue_stage<KIND, NC>(p, sm, blk, st + 2, buf, t0, next_base, tid);
       next_base = base_of(st + 3);
     }
-    if (since + NC > flush_channels(KIND) || st == n_st - 1) {
-      widen_store<KIND, DR, NW>(p, sm, acc, blk, t0, first);
+    if (since + NC > p.flush || st == n_st - 1) {
+      widen_store<KIND, DR, NW, NC>(p, sm, acc, blk, t0, first);
       first = false;
       since = 0;
     }
@@ -370,7 +443,6 @@ __device__ __forceinline__ void init_barriers(const Smem& sm) {
 
 template <int KIND, int DR, int NW, int MINB, int NC>
 __global__ void __launch_bounds__(NW * 32, MINB) fwd_tiled_kernel(const TileParams p) {
-  static_assert(NW * kFlushWords <= NC * 672, "transpose tiles must fit the window buffer");
   extern __shared__ __align__(128) unsigned char smem[];
   const Smem sm = smem_layout<NC>(smem, p.lraw);
   init_barriers<NC>(sm);
@@ -378,39 +450,51 @@ __global__ void __launch_bounds__(NW * 32, MINB) fwd_tiled_kernel(const TilePara
   tile_body<KIND, DR, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks, gstage);
 }
 
+// One batch item of one variant.  Returns the continued stage count, or
+// kStageError after a timeout.
+constexpr uint32_t kStageError = 0xffffffffu;
+
+template <int KIND, int DR, int NW, int NC>
+__device__ __forceinline__ uint32_t batch_item(const BatchJob* job, int blk, int tile,
+                                            uint32_t gstage, unsigned char* smem,
+                                            int32_t max_lraw) {
+  const Smem sm = smem_layout<NC>(smem, max_lraw);
+  const TileParams p = job->p;
+  uint32_t g = gstage;
+  return tile_body<KIND, DR, NW, NC>(p, sm, blk, tile, g) ? g : kStageError;
+}
+
 template <int NW, int MINB, int NC>
 __global__ void __launch_bounds__(NW * 32, MINB) fwd_batch_kernel(const BatchArgs b) {
-  static_assert(NW * kFlushWords <= NC * 672, "transpose tiles must fit the window buffer");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int item_slot;
-  const Smem sm = smem_layout<NC>(smem, b.max_lraw);
-  init_barriers<NC>(sm);
-  uint32_t gstage = 0;
+  init_barriers<NC>(smem_layout<NC>(smem, b.max_lraw));
+  uint32_t g = 0;
   for (;;) {
     if (threadIdx.x == 0) item_slot = static_cast<int>(atomicAdd(b.counter, 1u));
     __syncthreads();
     const int it = item_slot;
     if (it >= b.n_items) break;
     const BatchItem item = b.items[it];
-    const BatchJob& job = b.jobs[item.job];
+    const BatchJob* job = b.jobs + item.job;
     // The shared-memory layout is sized for the largest raw window and window
     // of any job; a job indexes the raw buffers with its own (smaller) lraw.
-    const Smem& jsm = sm;
-    const TileParams p = job.p;
-    bool ok = true;
-    switch (job.kind * 16 + job.dr) {
-      case kU8 * 16 + 4: ok = tile_body<kU8, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kU8 * 16 + 2: ok = tile_body<kU8, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kU8 * 16 + 1: ok = tile_body<kU8, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kU16 * 16 + 4: ok = tile_body<kU16, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kU16 * 16 + 2: ok = tile_body<kU16, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kU16 * 16 + 1: ok = tile_body<kU16, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kF32 * 16 + 4: ok = tile_body<kF32, 4, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kF32 * 16 + 2: ok = tile_body<kF32, 2, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      case kF32 * 16 + 1: ok = tile_body<kF32, 1, NW, NC>(p, jsm, item.blk, item.tile, gstage); break;
-      default: ok = true; break;
+    switch (job->kind * 16 + job->dr) {
+      case kU8 * 16 + 4: g = batch_item<kU8, 4, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU8 * 16 + 2: g = batch_item<kU8, 2, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU8 * 16 + 1: g = batch_item<kU8, 1, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU8W * 16 + 4: g = batch_item<kU8W, 4, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU8W * 16 + 2: g = batch_item<kU8W, 2, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU8W * 16 + 1: g = batch_item<kU8W, 1, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU16 * 16 + 4: g = batch_item<kU16, 4, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU16 * 16 + 2: g = batch_item<kU16, 2, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kU16 * 16 + 1: g = batch_item<kU16, 1, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kF32 * 16 + 4: g = batch_item<kF32, 4, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kF32 * 16 + 2: g = batch_item<kF32, 2, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      case kF32 * 16 + 1: g = batch_item<kF32, 1, NW, NC>(job, item.blk, item.tile, g, smem, b.max_lraw); break;
+      default: break;
     }
-    if (!ok) break;
+    if (g == kStageError) break;
   }
 }
 
@@ -421,7 +505,7 @@ namespace {
 template <int KIND, int DR, int NW, int MINB, int NC>
 int launch_tiled_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   const tk::Shape* sh = tk::shape_for(DR);
-  const size_t smem = tk::smem_bytes(KIND, *sh, prm.lp);
+  const size_t smem = tk::smem_bytes(KIND, prm.bin, *sh, prm.lp);
   auto kern = tk::fwd_tiled_kernel<KIND, DR, NW, MINB, NC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
@@ -435,9 +519,9 @@ int launch_kind(int dr, const tk::TileParams& prm, int64_t grid, cudaStream_t st
   switch (dr) {
     case 8: return launch_tiled_shape<KIND, 8, 8, 1, 16>(prm, grid, st);
     case 6: return launch_tiled_shape<KIND, 6, 12, 1, 24>(prm, grid, st);
-    case 4: return launch_tiled_shape<KIND, 4, 8, 2, 16>(prm, grid, st);
-    case 2: return launch_tiled_shape<KIND, 2, 8, 2, 16>(prm, grid, st);
-    case 1: return launch_tiled_shape<KIND, 1, 8, 2, 16>(prm, grid, st);
+    case 4: return launch_tiled_shape<KIND, 4, 12, 1, 24>(prm, grid, st);
+    case 2: return launch_tiled_shape<KIND, 2, 12, 1, 16>(prm, grid, st);
+    case 1: return launch_tiled_shape<KIND, 1, 12, 1, 16>(prm, grid, st);
   }
   return static_cast<int>(cudaErrorInvalidValue);
 }
@@ -456,9 +540,11 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.n_blocks = rp.tile_n_blocks;
   prm.n_out = n_out;
   prm.lp = rp.tile_lp;
-  prm.lraw = tk::raw_bytes(p->dtype, rp.tile_lp);
+  prm.lraw = tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp);
   prm.units_magic = rp.tile_units_magic;
   prm.units_shift = rp.tile_units_shift;
+  prm.bin = rp.r.bin;
+  prm.flush = tk::flush_channels(rp.tile_kind, rp.r.bin);
   prm.out = d_out;
   prm.err = err;
   return prm;
@@ -468,14 +554,16 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, void* stream) {
   const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
-  const int64_t tiles = (n_out + tk::tile_samples(p->dtype) - 1) / tk::tile_samples(p->dtype);
+  const int ts = tk::tile_samples(rp.tile_kind);
+  const int64_t tiles = (n_out + ts - 1) / ts;
   const int64_t grid = tiles * rp.tile_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  switch (p->dtype) {
-    case DD_U8: return launch_kind<tk::kU8>(rp.tile_dr, prm, grid, st);
-    case DD_U16: return launch_kind<tk::kU16>(rp.tile_dr, prm, grid, st);
-    case DD_F32: return launch_kind<tk::kF32>(rp.tile_dr, prm, grid, st);
+  switch (rp.tile_kind) {
+    case tk::kU8: return launch_kind<tk::kU8>(rp.tile_dr, prm, grid, st);
+    case tk::kU8W: return launch_kind<tk::kU8W>(rp.tile_dr, prm, grid, st);
+    case tk::kU16: return launch_kind<tk::kU16>(rp.tile_dr, prm, grid, st);
+    case tk::kF32: return launch_kind<tk::kF32>(rp.tile_dr, prm, grid, st);
   }
   return static_cast<int>(cudaErrorInvalidValue);
 }
@@ -492,11 +580,11 @@ int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_
 }
 
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream) {
-  auto kern = tk::fwd_batch_kernel<8, 2, 16>;
+  auto kern = tk::fwd_batch_kernel<tk::kBatchWarps, 1, tk::kBatchNc>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
-  kern<<<grid, 8 * 32, smem, static_cast<cudaStream_t>(stream)>>>(args);
+  kern<<<grid, 12 * 32, smem, static_cast<cudaStream_t>(stream)>>>(args);
   return static_cast<int>(cudaGetLastError());
 }
 

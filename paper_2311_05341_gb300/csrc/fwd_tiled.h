@@ -15,14 +15,18 @@
 namespace dd {
 namespace tk {
 
-// Sample kinds of the tiled kernels (values equal dd_dtype).
-enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3 };
+// Window-word kinds of the tiled kernels: uint8 at time bin 1 packs two samples
+// per 32-bit word (16-bit lanes); uint8 at a larger bin (kU8W), uint16 and
+// float32 keep one (decimated) sample per word.  Values 1-3 equal dd_dtype.
+enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4 };
 
 constexpr int kH = 20;               // window words per lane per DM (the register tile width)
 constexpr int kMaxOff = 15;          // largest in-window DM offset (4-bit field)
 constexpr int kWin = 36;             // window words per lane (>= kH + kMaxOff, multiple of 4)
 constexpr int kPair = 32 * kH;       // uint8: word u packs samples u and u + kPair
-constexpr int kFlushWords = 1288;    // per-warp transpose tile (1280 + 1280/160 pad)
+// Per-warp transpose tile of the widen/store: 1280 (uint8 pairs) or 640
+// positions plus the p / 160 padding, rounded up.
+DD_HOST_DEVICE constexpr int flush_words(int kind) { return kind == 1 ? 1288 : 648; }
 constexpr int kMaxWarps = 12;
 constexpr int kWaitIters = 1 << 22;  // bound on every mbarrier wait loop
 constexpr int kErrTimeout = 1;       // device status bit: a bounded wait gave up
@@ -33,15 +37,26 @@ constexpr size_t kStatusBytes = 256;
 DD_HOST_DEVICE constexpr int samples_per_word(int kind) { return kind == kU8 ? 2 : 1; }
 // Output samples per CTA tile: 32 lanes x kH words x samples per word.
 DD_HOST_DEVICE constexpr int tile_samples(int kind) { return 32 * kH * samples_per_word(kind); }
-DD_HOST_DEVICE constexpr int elem_bytes(int kind) { return kind == kU8 ? 1 : (kind == kU16 ? 2 : 4); }
-// Samples in 16 bytes: TMA copies start 16-byte aligned, so a window starts up
-// to align_samples - 1 samples before the block's base shift.
-DD_HOST_DEVICE constexpr int align_samples(int kind) { return 16 / elem_bytes(kind); }
-// Channels between widenings of the accumulators: uint8 lanes hold 16 bits
-// (255 * 256 < 2^16); uint16 sums stay below 2^31 for 32768 channels; float
-// never needs one.
-DD_HOST_DEVICE constexpr int flush_channels(int kind) {
-  return kind == kU8 ? 256 : (kind == kU16 ? 32768 : (1 << 30));
+DD_HOST_DEVICE constexpr int elem_bytes(int kind) {
+  return (kind == kU8 || kind == kU8W) ? 1 : (kind == kU16 ? 2 : 4);
+}
+// Decimated samples in 16 raw bytes: TMA copies start 16-byte aligned, so a
+// window starts up to align_samples - 1 decimated samples before the block's
+// base shift.  The tiled kernels take bins with bin * elem_bytes dividing 16.
+DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) { return 16 / (elem_bytes(kind) * bin); }
+inline bool bin_supported(int kind, int bin) {
+  const int eb = elem_bytes(kind) * bin;
+  return bin >= 1 && eb <= 16 && 16 % eb == 0 && (kind != kU8 || bin == 1);
+}
+// Channels between widenings of the accumulators: uint8 pairs in 16-bit lanes
+// hold 255 * 256 < 2^16; one-sample words stay below 2^31 for
+// floor((2^31 - 1) / (max sample * bin)) channels; float never needs one.
+inline int flush_channels(int kind, int bin) {
+  if (kind == kU8) return 256;
+  if (kind == kF32) return 1 << 30;
+  const double max_sample = (kind == kU8W ? 255.0 : 65535.0) * bin;
+  const double n = 2147483647.0 / max_sample;
+  return n > (1 << 30) ? (1 << 30) : static_cast<int>(n);
 }
 
 // Tile shapes: DMs per lane (the register tile is dr DMs x kH words), warps
@@ -54,10 +69,14 @@ struct Shape {
   int min_blocks;
   int nc;
 };
-constexpr Shape kShapes[] = {{8, 8, 1, 16}, {6, 12, 1, 24}, {4, 8, 2, 16}, {2, 8, 2, 16},
-                             {1, 8, 2, 16}};
-// The persistent batch kernel serves every plan with one resource footprint.
-constexpr Shape kBatchShapes[] = {{4, 8, 2, 16}, {2, 8, 2, 16}, {1, 8, 2, 16}};
+constexpr Shape kShapes[] = {{8, 8, 1, 16}, {6, 12, 1, 24}, {4, 12, 1, 24}, {2, 12, 1, 16},
+                             {1, 12, 1, 16}};
+// The persistent batch kernel serves these DMs-per-lane with one resource
+// footprint (12 warps, one CTA per SM, 16 channels per stage); the DM blocks
+// (records) only depend on DMs per lane and warps, so any 12-warp plan fits.
+constexpr int kBatchWarps = 12;
+constexpr int kBatchNc = 16;
+constexpr int kBatchDr[] = {4, 2, 1};
 
 inline const Shape* shape_for(int dr) {
   for (const Shape& s : kShapes)
@@ -79,18 +98,18 @@ DD_HOST_DEVICE constexpr size_t raw_offset(int nc) {
 }
 
 // Words of a channel's staged window for a given DM-block shift span.
-inline int32_t window_words(int kind, int32_t span) {
-  const int32_t need = kH * 31 + span + (align_samples(kind) - 1) + kWin;
+inline int32_t window_words(int kind, int bin, int32_t span) {
+  const int32_t need = kH * 31 + span + (align_samples(kind, bin) - 1) + kWin;
   return (need + 15) / 16 * 16;
 }
 
 // Raw bytes fetched per channel and stage for lp window words.
-DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int32_t lp) {
-  return kind == kU8 ? lp + kPair : lp * elem_bytes(kind);
+DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int bin, int32_t lp) {
+  return kind == kU8 ? lp + kPair : lp * elem_bytes(kind) * bin;
 }
 
-inline size_t smem_bytes(int kind, const Shape& s, int32_t lp) {
-  return raw_offset(s.nc) + 2 * static_cast<size_t>(s.nc) * raw_bytes(kind, lp) +
+inline size_t smem_bytes(int kind, int bin, const Shape& s, int32_t lp) {
+  return raw_offset(s.nc) + 2 * static_cast<size_t>(s.nc) * raw_bytes(kind, bin, lp) +
          static_cast<size_t>(s.nc) * lp * 4;
 }
 
@@ -107,6 +126,8 @@ struct TileParams {
   int32_t lraw;         // raw bytes per staged channel
   uint32_t units_magic; // u / (lp/4) == (u * magic) >> (32 + shift)
   int32_t units_shift;
+  int32_t bin;          // time decimation of the range (raw samples per window word)
+  int32_t flush;        // channels between accumulator widenings
   void* out;            // [n_dm][n_out] int32 or float32
   int32_t* err;
 };
@@ -115,7 +136,7 @@ struct TileParams {
 // items over many jobs (plan ranges with their input/output pointers).
 struct BatchJob {
   TileParams p;
-  int32_t kind;  // kU8 / kU16 / kF32
+  int32_t kind;  // kU8 / kU8W / kU16 / kF32
   int32_t dr;    // DMs per lane (a kBatchShapes entry)
 };
 
@@ -134,9 +155,9 @@ struct BatchArgs {
   int32_t max_lraw;        // largest raw window of any job (shared-memory layout)
 };
 
-inline size_t batch_smem_bytes(const Shape& s, int32_t max_lraw, int32_t max_lp) {
-  return raw_offset(s.nc) + 2 * static_cast<size_t>(s.nc) * max_lraw +
-         static_cast<size_t>(s.nc) * max_lp * 4;
+inline size_t batch_smem_bytes(int32_t max_lraw, int32_t max_lp) {
+  return raw_offset(kBatchNc) + 2 * static_cast<size_t>(kBatchNc) * max_lraw +
+         static_cast<size_t>(kBatchNc) * max_lp * 4;
 }
 
 }  // namespace tk

@@ -56,7 +56,7 @@ bool build_tile_records(const RangePlan& rp, int32_t n_chan, int kind, const tk:
                         std::vector<tk::Rec>& recs, int32_t* n_blocks_out) {
   using namespace tk;
   const int dm_cta = sh.dr * sh.warps;
-  const int32_t align = align_samples(kind);
+  const int32_t align = align_samples(kind, rp.r.bin);
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   recs.assign(static_cast<size_t>(n_blocks) * n_chan, tk::Rec{});
   for (int64_t b = 0; b < n_blocks; ++b) {
@@ -110,8 +110,8 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
 // Try one tile shape for a range; on success fill the range's tile fields.
 bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh) {
   const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
-  const int32_t lp = tk::window_words(kind, span);
-  if (tk::smem_bytes(kind, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
+  const int32_t lp = tk::window_words(kind, rp.r.bin, span);
+  if (tk::smem_bytes(kind, rp.r.bin, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
   uint32_t magic = 0;
   int32_t shift = 0;
   if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(sh.nc * lp / 4), &magic,
@@ -122,6 +122,7 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
   if (!build_tile_records(rp, n_chan, kind, sh, recs, &n_blocks)) return false;
   rp.tile_ok = true;
   rp.tile_dr = sh.dr;
+  rp.tile_kind = kind;
   rp.tile_n_blocks = n_blocks;
   rp.tile_lp = lp;
   rp.tile_units_magic = magic;
@@ -131,23 +132,28 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
   return true;
 }
 
-// Register-tiled kernel: time bin 1 and a tile shape whose per-warp DM
-// offsets fit the 4-bit fields and whose window fits shared memory.  The
-// automatic choice takes the first shape that fits in kAutoOrder (fewer DMs
-// per lane serve steeper plans).
+// Register-tiled kernel: a supported time bin (bin * sample bytes divides 16)
+// and a tile shape whose per-warp DM offsets fit the 4-bit fields and whose
+// window fits shared memory.  uint8 at bin 1 packs two samples per word; at a
+// larger bin it keeps one decimated sample per word.  The automatic choice
+// takes the first shape that fits in kAutoOrder (fewer DMs per lane serve
+// steeper plans; 8 DMs per lane stages 16 channels, fitting the widest raw
+// windows of large bins).
 void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
-  static const int kAutoOrder[] = {6, 4, 2, 1};
+  static const int kAutoOrder[] = {6, 4, 2, 1, 8};
   rp.tile_ok = false;
   rp.tile_dr = 0;
+  rp.tile_kind = 0;
   rp.tile_recs.clear();
-  if (rp.r.bin != 1) return;
+  const int kind = (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W : static_cast<int>(dtype);
+  if (!tk::bin_supported(kind, rp.r.bin)) return;
   if (rp.tile_request > 0) {
     const tk::Shape* sh = tk::shape_for(rp.tile_request);
-    if (sh) try_tile_shape(rp, n_chan, dtype, *sh);
+    if (sh) try_tile_shape(rp, n_chan, kind, *sh);
     return;
   }
   for (int dr : kAutoOrder)
-    if (try_tile_shape(rp, n_chan, dtype, *tk::shape_for(dr))) return;
+    if (try_tile_shape(rp, n_chan, kind, *tk::shape_for(dr))) return;
 }
 
 void layout_workspace(dd_plan_s* p) {

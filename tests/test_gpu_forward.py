@@ -143,6 +143,37 @@ def test_tiled_full_planes_every_shape(dtype, seed):
             np.testing.assert_array_equal(got, ref[0], err_msg=f"tile {dms}")
 
 
+@pytest.mark.parametrize("dtype,b", [("u8", 2), ("u8", 4), ("u8", 8), ("u16", 2), ("u16", 4),
+                                     ("f32", 2)])
+def test_tiled_decimation_every_shape(dtype, b):
+    """Time binning fused into the tiled kernel's staging, every feasible shape."""
+    rng = np.random.default_rng(900 + b)
+    n_chan = 77
+    freqs = channel_freqs(1400.0, 300.0, n_chan)
+    r = (2.0, 2.0 + 33 * 0.05 * b, 0.05 * b, b)
+    s_max, _ = oracle.extent(freqs, 1400.0, 64e-6, r, 10 ** 9)
+    n_samp = int((s_max + 700) * b + rng.integers(0, b))  # ragged tail of the bin
+    npdt, mean, sd = _NOISE[dtype]
+    x = filterbank(npdt, n_chan, n_samp, 9000 + b, mean, sd)
+    ref = oracle.forward(x, freqs, 1400.0, 64e-6, [r])[0]
+    ref_abs = oracle.forward(x, freqs, 1400.0, 64e-6, [r], take_abs=True)[0]
+    xd = padded_device(x)
+    ran = 0
+    for dms in (8, 6, 4, 2, 1):
+        plan = dd.Plan(freqs, 1400.0, 64e-6, [r], dtype)
+        try:
+            plan.set_tile(0, dms)
+        except dd.DDError:
+            continue  # this shape's staging does not fit shared memory at this bin
+        ran += 1
+        got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
+        if dtype == "f32":
+            assert_float_parity(got, ref, ref_abs, f"tile {dms}")
+        else:
+            np.testing.assert_array_equal(got, ref, err_msg=f"tile {dms}")
+    assert ran >= 1
+
+
 def test_u8_tiled_saturated_input():
     """All samples 255: every 16-bit lane reaches 255 * 256 before widening."""
     freqs = channel_freqs(1670.0, 320.0, 1000)

@@ -142,10 +142,18 @@ def test_kernel_selection():
     plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
     info = plan.info(paper.n_samp)
     assert info["kernel"] == ["tiled"] and info["tile_dms"] == [6]
-    # Binned ranges run on the generic kernel.
+    # Bins with bin * sample bytes dividing 16 are tiled (decimation fused)
+    # while their raw windows fit shared memory; other bins run on the generic
+    # kernel.
     stream = workloads.stream_beam(0, 90168)
     plan = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, stream.ranges, "u8", upload=False)
-    assert plan.info(stream.n_samp)["kernel"] == ["tiled", "generic", "generic", "generic"]
+    assert plan.info(stream.n_samp)["kernel"] == ["tiled"] * 4
+    odd = [(0.0, 10.0, 0.5, 3), (10.0, 20.0, 1.0, 4)]
+    plan = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, odd, "u8", upload=False)
+    assert plan.info(stream.n_samp)["kernel"] == ["generic", "tiled"]
+    plan = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, [(0.0, 10.0, 0.5, 8)], "f32",
+                   upload=False)
+    assert plan.info(stream.n_samp)["kernel"] == ["generic"]  # 8 * 4 bytes > 16
     # 8 samples of delay per DM step: only 2 DMs per lane fit the 4-bit offsets.
     tiny = workloads.tiny_u8()
     plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)

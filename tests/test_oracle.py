@@ -420,3 +420,14 @@ def test_generator_reference_vectors(synth_mod):
     assert synth_mod.splitmix64(0, 1) == 0xE220A8397B1DCDAF
     zs = np.array([synth_mod.normal(123, i) for i in range(20000)])
     assert abs(zs.mean()) < 0.03 and abs(zs.std() - 1) < 0.03
+
+
+def test_adjoint_channels_are_rows_of_full_adjoint(oracle_mod, synth_mod):
+    freqs, f_ref, ts, ranges = _tiny_plan(synth_mod)
+    rng = np.random.default_rng(8)
+    planes = oracle_mod.forward(rng.standard_normal((5, 60)).astype(np.float32), freqs, f_ref, ts,
+                                ranges)
+    ys = [rng.standard_normal(p.shape) for p in planes]
+    full = oracle_mod.adjoint(ys, 5, 60, freqs, f_ref, ts, ranges)
+    part = oracle_mod.adjoint_channels(ys, 5, 60, freqs, f_ref, ts, ranges, [4, 0, 2])
+    np.testing.assert_array_equal(part, full[[4, 0, 2]])

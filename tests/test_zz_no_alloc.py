@@ -61,11 +61,11 @@ def test_noalloc_rejects_plans_it_cannot_serve():
     big = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
     assert _noalloc(big, x, paper.n_samp, out, stride=paper.n_samp) == _lib.DD_ERR_BUDGET
     assert "at most" in _lib.load().dd_last_error_detail().decode()
-    # A plan with binned ranges (generic kernel) and a float32 plan are refused.
-    stream = workloads.stream_beam(0, 90168)
-    binned = dd.Plan(stream.freqs, stream.f_high, stream.t_samp, stream.ranges, "u8", upload=False)
-    assert _noalloc(binned, x, stream.n_samp, out, stride=stream.n_samp + 8) == \
-        _lib.DD_ERR_UNSUPPORTED
+    # A plan with a range on the generic kernel (time bin 3) and a float32
+    # plan are refused.
     tiny = workloads.tiny_u8()
+    binned = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, [(0.0, 8.0, 0.5, 3)], "u8",
+                     upload=False)
+    assert _noalloc(binned, x, 8192, out, stride=8192) == _lib.DD_ERR_UNSUPPORTED
     f32 = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "f32", upload=False)
     assert _noalloc(f32, x, 4096, out) == _lib.DD_ERR_UNSUPPORTED
