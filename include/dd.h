@@ -84,12 +84,20 @@ typedef struct {
   int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
-  int32_t tile_dms[DD_MAX_RANGES];    /* DMs per lane of the tiled kernel (0: generic) */
+  int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane, or
+                                          DD_TILE_PATTERN (0: generic kernel) */
 } dd_plan_info;
 
 /* Forward kernels a range can run on (dd_plan_info.kernel). */
 #define DD_KERNEL_GENERIC 1 /* shared-memory staged, any dtype and bin */
-#define DD_KERNEL_TILED 2   /* bin 1: TMA-staged register tiles (uint8 in packed 16-bit lanes) */
+#define DD_KERNEL_TILED 2   /* TMA-staged register tiles (uint8 at bin 1 in packed 16-bit
+                               lanes); bins with bin * sample bytes dividing 16 */
+
+/* Tile code of the pattern family (dd_plan_set_tile, dd_plan_info.tile_dms):
+ * 4 DMs per lane, one indexed branch per channel over the 27 patterns of
+ * per-DM shift increments in {0, 1, 2}.  Plans whose shift of some channel
+ * grows by more than 2 between consecutive trial DMs cannot use it. */
+#define DD_TILE_PATTERN 0x104
 
 /*
  * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
@@ -115,15 +123,17 @@ dd_status dd_plan_query(dd_plan plan, int64_t n_samp, dd_plan_info* out);
 dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out);
 
 /*
- * Choose the tile shape of range `range` (time bin 1): `dms_per_lane` is the
- * register tile's DM count (8, 6, 4, 2 or 1; 0 = automatic).  Per-plan tile
+ * Choose the tile of range `range`: `tile` is the offset tile's DM count per
+ * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, or 0 = automatic.  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
  * Rebuilds the plan's device tables, so it must be followed by
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
- * Errors: DD_ERR_UNSUPPORTED if that shape cannot serve the range (bin > 1, or
- * DM offsets too wide for it); the previous choice is kept.
+ * Errors: DD_ERR_INVALID_ARG for another code; DD_ERR_UNSUPPORTED if that
+ * tile cannot serve the range (unsupported bin, DM offsets or increments too
+ * wide for it, window too large for shared memory); the previous choice is
+ * kept.
  */
-dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t dms_per_lane);
+dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile);
 
 /*
  * Copy the plan's device tables into caller-owned device memory d_workspace

@@ -99,9 +99,14 @@ class Plan:
         check(self._lib.dd_plan_shifts(self._h, int(r), out.ctypes.data))
         return out
 
-    def set_tile(self, r: int, dms_per_lane: int, device=None):
-        """Pick the register-tile shape of range r (8, 6, 4, 2, 1; 0 = auto) and re-upload."""
-        check(self._lib.dd_plan_set_tile(self._h, int(r), int(dms_per_lane)))
+    def set_tile(self, r: int, tile, device=None):
+        """Pick the register tile of range r and re-upload.
+
+        tile: DMs per lane of the offset tile (8, 6, 4, 2, 1), "pattern"
+        (DD_TILE_PATTERN), or 0 for the automatic choice.
+        """
+        code = _lib.DD_TILE_PATTERN if tile == "pattern" else int(tile)
+        check(self._lib.dd_plan_set_tile(self._h, int(r), code))
         if self.workspace is not None:
             self.upload(self.workspace.device if device is None else device)
         return self

@@ -39,7 +39,8 @@ def sources():
 
 
 def _deps():
-    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.py"))
+    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + glob.glob(os.path.join(CSRC, "*.py"))
             + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 

@@ -48,7 +48,7 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
-    o->tile_dms[i] = rp.tile_ok ? rp.tile_dr : 0;
+    o->tile_dms[i] = !rp.tile_ok ? 0 : (rp.tile_pattern ? DD_TILE_PATTERN : rp.tile_dr);
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
     if (raw > o->max_delay_raw) o->max_delay_raw = raw;
   }
@@ -148,20 +148,20 @@ dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out) {
   return DD_OK;
 }
 
-dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t dms_per_lane) {
+dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
     return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
-  if (dms_per_lane != 0 && !tk::shape_for(dms_per_lane))
-    return fail(DD_ERR_INVALID_ARG, "dms_per_lane must be 0, 1, 2, 4, 6 or 8");
+  if (tile != 0 && tile != DD_TILE_PATTERN && !tk::shape_for(tile))
+    return fail(DD_ERR_INVALID_ARG, "tile must be 0, 1, 2, 4, 6, 8 or DD_TILE_PATTERN");
   bool ok;
   try {
-    ok = retile_range(plan, static_cast<size_t>(range), dms_per_lane);
+    ok = retile_range(plan, static_cast<size_t>(range), tile);
   } catch (const std::bad_alloc&) {
     return fail(DD_ERR_INVALID_ARG, "host allocation failed while retiling");
   }
   plan->d_ws = nullptr;  // tables changed: upload again
-  if (!ok) return fail(DD_ERR_UNSUPPORTED, "tile shape cannot serve this range");
+  if (!ok) return fail(DD_ERR_UNSUPPORTED, "tile cannot serve this range");
   return DD_OK;
 }
 

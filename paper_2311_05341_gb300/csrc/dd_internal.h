@@ -36,9 +36,12 @@ struct RangePlan {
 
   // Register-tiled kernel (fwd_tiled.cu), used when tile_ok (time bin 1).
   bool tile_ok = false;
+  bool tile_pattern = false;    // pattern tile (fwd_pattern.cu) instead of offset tile
   int32_t tile_dr = 0;          // DMs per lane of the chosen tile shape
+  int32_t tile_h = 0;           // window words per lane per DM (kH, or the pattern H)
+  int32_t tile_shape = 0;       // index into tk::kPatShapes (pattern tiles)
   int32_t tile_kind = 0;        // window-word kind (tk::Kind)
-  int32_t tile_request = 0;     // shape requested by dd_plan_set_tile (0 = automatic)
+  int32_t tile_request = 0;     // tile requested by dd_plan_set_tile (0 = automatic)
   int32_t tile_n_blocks = 0;    // DM blocks of tile_dr * warps DMs
   int32_t tile_lp = 0;          // window words per staged channel
   uint32_t tile_units_magic = 0;  // division by tile_lp / 4 (see fwd_tiled.h)
@@ -46,7 +49,7 @@ struct RangePlan {
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
-  size_t off_tile_recs = 0;     // tk::Rec [tile_n_blocks][n_chan]
+  size_t off_tile_recs = 0;     // tk::Rec or tk::PRec [tile_n_blocks][n_chan]
   std::vector<unsigned char> tile_recs;  // host image of the records
 };
 
@@ -95,6 +98,10 @@ int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, void* stream);
+// The pattern kernel (fwd_pattern.cu), same arguments.
+int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                           int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
+                           void* d_out, void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);

@@ -1,0 +1,225 @@
+// fwd_pattern.cu -- register-tiled forward dedispersion with one increment-
+// pattern branch per channel (sm_103a; uint8, uint16 and float32 input).
+//
+// Computes Eq. 3 (Algorithm 1) with the output partition, staging, binning and
+// widen/store of the offset tiles (fwd_tiled.cu); only the register tile and
+// its per-channel dispatch differ:
+//
+//  * Every lane owns kPatDr = 4 consecutive DMs x H window words, H odd
+//    (uint8: 2H samples, pairing samples u and u + 32H in 16-bit lanes).
+//  * Eq. 1 is linear in DM, so from one trial DM to the next the shift of a
+//    channel grows by the floor or the ceiling of step * k_c / (bin * t_samp).
+//    When every such increment of the plan is 0, 1 or 2, the offsets of a
+//    warp's four DMs relative to its first DM form one of 27 patterns.  The
+//    host stores, per (DM block, channel, warp), the window offset of the
+//    warp's first DM and the pattern number in 16 bits.
+//  * Per channel a lane loads H + 6 window words with scalar shared loads at
+//    that exact offset (conflict-free at any offset because the lane stride
+//    H is odd, so no 16-byte alignment term enters the offsets), then takes
+//    one warp-uniform indexed branch into the pattern's unrolled block of 4H
+//    adds (generated by gen_dispatch.py).
+//
+// Against the 4-bit-offset tiles this is one indexed branch per four DMs
+// instead of one per DM.  Every mbarrier wait is bounded; on timeout the
+// kernel records kErrTimeout in the status word and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd_internal.h"
+#include "fwd_tiled.h"
+#include "fwd_tiled_dispatch.inc"
+#include "tile_common.cuh"
+
+namespace dd {
+namespace tk {
+
+namespace {
+
+struct PSmem {
+  uint32_t bar_base;  // 2 mbarriers
+  PRec* recs;         // [2][NC]
+  uint8_t* raw;       // [2][NC][lraw]
+  uint32_t* pw;       // [NC][lp] window words
+};
+
+template <int NC>
+__device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
+  constexpr size_t kRawOff = raw_offset(NC, static_cast<int>(sizeof(PRec)));
+  PSmem sm;
+  sm.bar_base = smem_u32(smem);
+  sm.recs = reinterpret_cast<PRec*>(smem + kRecOffset);
+  sm.raw = smem + kRawOff;
+  sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
+  return sm;
+}
+
+template <int KIND, int H>
+__device__ __forceinline__ void pat_dispatch(AccT<KIND> (&acc)[kPatDr][H],
+                                             const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
+                                             uint32_t ix) {
+  static_assert(H == 21, "pattern dispatch generated for H = 21 only");
+  if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_21(acc, R, ix);
+  else DD_PAT_CHANNEL_U32_21(acc, R, ix);
+}
+
+// One (DM block, time tile) work unit.  Returns false after a bounded wait
+// gave up (the status word is set).
+template <int KIND, int H, int NW, int NC>
+__device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
+                                         int64_t tile) {
+  constexpr int kThreads = NW * 32;
+  constexpr int kR = H + 2 * (kPatDr - 1);
+  constexpr int kPairW = 32 * H;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int64_t t0 = tile * pat_tile_samples(KIND, H);
+  const int n_st = (p.n_chan + NC - 1) / NC;
+
+  const PRec* my_recs = static_cast<const PRec*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan;
+  auto base_of = [&](int st) -> int32_t {
+    const int c = st * NC + tid;
+    return (tid < NC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
+  };
+  if (tid <= NC) {
+    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 0, 0, t0, base_of(0), tid);
+    if (n_st > 1)
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 1, 1, t0, base_of(1), tid);
+  }
+  int32_t next_base = base_of(2);
+
+  AccT<KIND> acc[kPatDr][H];
+#pragma unroll
+  for (int i = 0; i < kPatDr; ++i)
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc[i][j] = AccT<KIND>(0);
+
+  bool first = true;
+  int since = 0;  // channels accumulated since the last widen
+  const int units = p.lp >> 2;
+
+  for (int st = 0; st < n_st; ++st) {
+    const int buf = st & 1;
+    const uint32_t parity = (st >> 1) & 1;
+    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(p.err, kErrTimeout);
+        // Let copies still in flight land before the CTA exits (bounded).
+        mbar_wait(sm.bar_base + 8u * buf, parity);
+        if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
+      }
+      return false;
+    }
+    const int nc = min(NC, p.n_chan - st * NC);
+
+    {  // Unpack raw bytes into window words.
+      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
+      const int total = nc * units;
+      for (int u = tid; u < total; u += kThreads) {
+        const int ch =
+            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
+        const int q = u - ch * units;
+        const uint4 v =
+            unpack_unit<KIND, kPairW>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
+        *reinterpret_cast<uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
+      }
+    }
+    __syncthreads();
+
+    // Shift-and-sum.  The loop stays rolled so the dispatch block, and its PTX
+    // labels, appear once per instantiation.
+    const PRec* rs = sm.recs + buf * NC;
+    const uint32_t* lane_pw = sm.pw + H * l;
+#pragma unroll 1
+    for (int ch = 0; ch < nc; ++ch) {
+      const uint32_t e = rs[ch].w[w];
+      const uint32_t* src = lane_pw + static_cast<size_t>(ch) * p.lp + (e & kPatOffMask);
+      AccT<KIND> R[kR];
+#pragma unroll
+      for (int k = 0; k < kR; ++k) {
+        if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
+        else R[k] = src[k];
+      }
+      pat_dispatch<KIND, H>(acc, R, e >> kPatOffBits);
+    }
+    since += nc;
+    __syncthreads();  // window words, raw[buf] and recs[buf] are free
+
+    if (tid <= NC && st + 2 < n_st) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, st + 2, buf, t0, next_base, tid);
+      next_base = base_of(st + 3);
+    }
+    if (since + NC > p.flush || st == n_st - 1) {
+      widen_store<KIND, kPatDr, NW, NC, H>(p, sm.pw, acc, blk, t0, first);
+      first = false;
+      since = 0;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+template <int KIND, int H, int NW, int NC>
+__global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const PSmem sm = pat_layout<NC>(smem, p.lraw);
+  if (threadIdx.x == 0) {
+    mbar_init(sm.bar_base, NC + 1);
+    mbar_init(sm.bar_base + 8, NC + 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pat_body<KIND, H, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks);
+}
+
+}  // namespace tk
+
+namespace {
+
+template <int KIND, int H, int NW, int NC>
+int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  const size_t smem = tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC}, prm.lp);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<static_cast<unsigned>(grid), NW * 32, smem, st>>>(prm);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <int KIND>
+int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  static_assert(tk::kPatShapes[0].h == 21 && tk::kPatShapes[0].warps == 16 &&
+                    tk::kPatShapes[0].nc == 32 && tk::kPatShapes[1].h == 21 &&
+                    tk::kPatShapes[1].warps == 16 && tk::kPatShapes[1].nc == 12,
+                "pattern launch table out of date");
+  switch (shape) {
+    case 0: return launch_pattern_shape<KIND, 21, 16, 32>(prm, grid, st);
+    case 1: return launch_pattern_shape<KIND, 21, 16, 12>(prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+}  // namespace
+
+int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
+                           int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
+                           void* d_out, void* stream) {
+  const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
+  const int ts = tk::pat_tile_samples(rp.tile_kind, rp.tile_h);
+  const int64_t tiles = (n_out + ts - 1) / ts;
+  const int64_t grid = tiles * rp.tile_n_blocks;
+  if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (rp.tile_kind) {
+    case tk::kU8: return launch_pattern_kind<tk::kU8>(rp.tile_shape, prm, grid, st);
+    case tk::kU8W: return launch_pattern_kind<tk::kU8W>(rp.tile_shape, prm, grid, st);
+    case tk::kU16: return launch_pattern_kind<tk::kU16>(rp.tile_shape, prm, grid, st);
+    case tk::kF32: return launch_pattern_kind<tk::kF32>(rp.tile_shape, prm, grid, st);
+  }
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+}  // namespace dd

@@ -40,54 +40,12 @@
 #include "dd_internal.h"
 #include "fwd_tiled.h"
 #include "fwd_tiled_dispatch.inc"
+#include "tile_common.cuh"
 
 namespace dd {
 namespace tk {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-// Bounded wait for phase `parity` of an mbarrier.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitIters; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-template <int KIND>
-using AccT = std::conditional_t<KIND == kF32, float, uint32_t>;
-// Input element of a kind (one raw sample).
-template <int KIND>
-using OutT = std::conditional_t<KIND == kF32, float, int32_t>;
 
 struct Smem {
   uint32_t bar_base;  // 2 mbarriers
@@ -105,122 +63,6 @@ __device__ __forceinline__ Smem smem_layout(unsigned char* smem, int32_t lraw) {
   sm.raw = smem + kRawOff;
   sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
   return sm;
-}
-
-// Issue the TMA copies of stage `st` into buffer `buf`.  Threads 0..NC-1 copy
-// one channel each, thread NC copies the stage's records.
-template <int KIND, int NC>
-__device__ __forceinline__ void issue_stage(const TileParams& p, const Smem& sm, int blk, int st,
-                                            int buf, int64_t t0, int32_t base, int tid) {
-  constexpr int kE = elem_bytes(KIND);
-  const uint32_t bar = sm.bar_base + 8u * buf;
-  const int c0 = st * NC;
-  if (tid < NC) {
-    const int c = c0 + tid;
-    uint32_t bytes = 0;
-    const uint8_t* src = nullptr;
-    if (c < p.n_chan) {
-      const int64_t align = 16 / (kE * p.bin);                       // decimated samples, 2^k
-      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw elements
-      if (ua < p.stride) {
-        const int64_t room = (p.stride - ua) * kE;
-        bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
-        src = static_cast<const uint8_t*>(p.x) + (static_cast<int64_t>(c) * p.stride + ua) * kE;
-      }
-    }
-    mbar_arrive_expect(bar, bytes);
-    if (bytes) {
-      uint8_t* dst = sm.raw + (static_cast<size_t>(buf) * NC + tid) * p.lraw;
-      bulk_copy(smem_u32(dst), src, bytes, bar);
-    }
-  } else if (tid == NC) {
-    const int nc = min(NC, p.n_chan - c0);
-    const uint32_t bytes = static_cast<uint32_t>(nc) * sizeof(Rec);
-    mbar_arrive_expect(bar, bytes);
-    const Rec* src = p.recs + static_cast<int64_t>(blk) * p.n_chan + c0;
-    bulk_copy(smem_u32(sm.recs + buf * NC), src, bytes, bar);
-  }
-}
-
-__device__ __forceinline__ uint32_t byte_sum4(uint32_t w) { return __dp4a(w, 0x01010101u, 0u); }
-__device__ __forceinline__ uint32_t half_sum2(uint32_t w) { return (w & 0xffffu) + (w >> 16); }
-
-// Unpack raw bytes into four window words (unit q of one channel).  At bin b
-// each word is the sum of b consecutive raw samples (the decimated sample).
-template <int KIND>
-__device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int bin) {
-  uint4 v;
-  if constexpr (KIND == kU8) {
-    // Word k packs X[k] and X[k + kPair] in its 16-bit lanes (bin 1 only).
-    const uint32_t a = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q);
-    const uint32_t b = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q + kPair);
-    const uint32_t t01 = __byte_perm(a, b, 0x5140);
-    const uint32_t t23 = __byte_perm(a, b, 0x7362);
-    v.x = __byte_perm(t01, 0u, 0x4140);
-    v.y = __byte_perm(t01, 0u, 0x4342);
-    v.z = __byte_perm(t23, 0u, 0x4140);
-    v.w = __byte_perm(t23, 0u, 0x4342);
-  } else if constexpr (KIND == kU8W) {
-    const uint8_t* r = raw_ch + 4 * q * bin;
-    if (bin == 2) {
-      const uint2 a = *reinterpret_cast<const uint2*>(r);
-      const uint32_t s0 = (a.x & 0x00ff00ffu) + ((a.x >> 8) & 0x00ff00ffu);
-      const uint32_t s1 = (a.y & 0x00ff00ffu) + ((a.y >> 8) & 0x00ff00ffu);
-      v = make_uint4(s0 & 0xffffu, s0 >> 16, s1 & 0xffffu, s1 >> 16);
-    } else if (bin == 4) {
-      const uint4 a = *reinterpret_cast<const uint4*>(r);
-      v = make_uint4(byte_sum4(a.x), byte_sum4(a.y), byte_sum4(a.z), byte_sum4(a.w));
-    } else if (bin == 8) {
-      const uint4 a = *reinterpret_cast<const uint4*>(r);
-      const uint4 b = *reinterpret_cast<const uint4*>(r + 16);
-      v = make_uint4(byte_sum4(a.x) + byte_sum4(a.y), byte_sum4(a.z) + byte_sum4(a.w),
-                     byte_sum4(b.x) + byte_sum4(b.y), byte_sum4(b.z) + byte_sum4(b.w));
-    } else {  // bin 16
-      uint32_t o[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint4 a = *reinterpret_cast<const uint4*>(r + 16 * k);
-        o[k] = byte_sum4(a.x) + byte_sum4(a.y) + byte_sum4(a.z) + byte_sum4(a.w);
-      }
-      v = make_uint4(o[0], o[1], o[2], o[3]);
-    }
-  } else if constexpr (KIND == kU16) {
-    const uint8_t* r = raw_ch + 8 * q * bin;
-    if (bin == 1) {
-      const uint2 a = *reinterpret_cast<const uint2*>(r);
-      v = make_uint4(a.x & 0xffffu, a.x >> 16, a.y & 0xffffu, a.y >> 16);
-    } else if (bin == 2) {
-      const uint4 a = *reinterpret_cast<const uint4*>(r);
-      v = make_uint4(half_sum2(a.x), half_sum2(a.y), half_sum2(a.z), half_sum2(a.w));
-    } else {  // bin 4 or 8: bin / 2 words of two samples per output word
-      uint32_t o[4];
-      const int words = bin / 2;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        uint32_t acc = 0;
-        for (int j = 0; j < words; ++j)
-          acc += half_sum2(*reinterpret_cast<const uint32_t*>(r + 4 * (k * words + j)));
-        o[k] = acc;
-      }
-      v = make_uint4(o[0], o[1], o[2], o[3]);
-    }
-  } else {  // kF32
-    const float* r = reinterpret_cast<const float*>(raw_ch + 16 * q * bin);
-    if (bin == 1) {
-      v = *reinterpret_cast<const uint4*>(r);
-    } else {
-      float o[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float acc = 0.f;
-        for (int j = 0; j < bin; ++j) acc += r[k * bin + j];
-        o[k] = acc;
-      }
-      v = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
-                     __float_as_uint(o[3]));
-    }
-  }
-  return v;
 }
 
 template <int KIND, int DR>
@@ -244,84 +86,6 @@ __device__ __forceinline__ void dispatch(AccT<KIND> (&acc)[DR][kH], const AccT<K
   }
 }
 
-// Store (first) or add (later) the accumulators into the output rows through
-// the warp's transposed shared tile.  Index f(p) = p + p / 160 is
-// conflict-free for the lane-major writes (p = 20 l + j) and the row-major
-// reads (p = 32 k + l).  The tiles live in the window buffer; when it cannot
-// hold one per warp, the warps take turns in `groups` rounds.  Called by every
-// thread of the CTA.
-template <int KIND, int DR, int NW, int NC>
-__device__ __forceinline__ void widen_store(const TileParams& p, const Smem& sm,
-                                            AccT<KIND> (&acc)[DR][kH], int blk, int64_t t0,
-                                            bool first) {
-  constexpr int kTileS = tile_samples(KIND);
-  constexpr int kFw = flush_words(KIND);
-  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-  // Window buffers are at least 672 words per channel, so many shapes fit one
-  // tile per warp at compile time.
-  constexpr bool kAllFit = NC * 672 >= NW * kFw;
-  const int fit = (NC * p.lp) / kFw;  // tiles that fit the window buffer
-  const int groups = kAllFit ? 1 : (NW + fit - 1) / fit;
-  uint32_t* tr = sm.pw + (w / groups) * kFw;
-  const int wbase = kH * l + (l >> 3);
-  const int64_t lim = p.n_out - t0;
-  for (int gi = 0; gi < groups; ++gi) {
-    if (gi > 0) __syncthreads();
-    if (w % groups != gi) continue;
-#pragma unroll
-    for (int i = 0; i < DR; ++i) {
-      const int d = blk * (DR * NW) + w * DR + i;
-#pragma unroll
-      for (int j = 0; j < kH; ++j) {
-        if constexpr (KIND == kU8) {
-          const uint32_t v = acc[i][j];
-          tr[wbase + j] = v & 0xffffu;
-          tr[wbase + j + kPair + 4] = v >> 16;
-          acc[i][j] = 0u;
-        } else if constexpr (KIND == kU16 || KIND == kU8W) {
-          tr[wbase + j] = acc[i][j];
-          acc[i][j] = 0u;
-        } else {
-          tr[wbase + j] = __float_as_uint(acc[i][j]);
-          acc[i][j] = 0.f;
-        }
-      }
-      __syncwarp();
-      if (d < p.n_dm) {
-        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
-        constexpr int kHalf = kTileS / 64;  // two halves of kTileS / 64 positions per lane
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          OutT<KIND> v[kHalf];
-#pragma unroll
-          for (int k = 0; k < kHalf; ++k) {
-            const int kk = h * kHalf + k;
-            const uint32_t bits = tr[32 * kk + l + kk / 5];
-            if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
-            else v[k] = static_cast<int32_t>(bits);
-          }
-          if (!first) {
-            OutT<KIND> g[kHalf];
-#pragma unroll
-            for (int k = 0; k < kHalf; ++k) {
-              const int pos = 32 * (h * kHalf + k) + l;
-              g[k] = pos < lim ? __ldcg(row + pos) : OutT<KIND>(0);
-            }
-#pragma unroll
-            for (int k = 0; k < kHalf; ++k) v[k] += g[k];
-          }
-#pragma unroll
-          for (int k = 0; k < kHalf; ++k) {
-            const int pos = 32 * (h * kHalf + k) + l;
-            if (pos < lim) row[pos] = v[k];
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 // One (DM block, time tile) work unit.  gstage counts pipeline stages across
 // the work units a CTA runs, so mbarrier phases continue from unit to unit.
 // Returns false after a bounded wait gave up (the status word is set).
@@ -333,14 +97,16 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
   const int64_t t0 = tile * tile_samples(KIND);
   const int n_st = (p.n_chan + NC - 1) / NC;
 
-  const Rec* my_recs = p.recs + static_cast<int64_t>(blk) * p.n_chan;
+  const Rec* my_recs = static_cast<const Rec*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan;
   auto base_of = [&](int st) -> int32_t {
     const int c = st * NC + tid;
     return (tid < NC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
   };
   if (tid <= NC) {
-    issue_stage<KIND, NC>(p, sm, blk, 0, gstage & 1, t0, base_of(0), tid);
-    if (n_st > 1) issue_stage<KIND, NC>(p, sm, blk, 1, (gstage + 1) & 1, t0, base_of(1), tid);
+    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 0, gstage & 1, t0, base_of(0), tid);
+    if (n_st > 1)
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 1, (gstage + 1) & 1, t0,
+                            base_of(1), tid);
   }
   int32_t next_base = base_of(2);
 
@@ -377,7 +143,7 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
         const int ch =
             static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
         const int q = u - ch * units;
-        const uint4 v = unpack_unit<KIND>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
+        const uint4 v = unpack_unit<KIND, kPair>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
         *reinterpret_cast<uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
       }
     }
@@ -415,11 +181,12 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
 
     if (tid <= NC && st + 2 < n_st) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_stage<KIND, NC>(p, sm, blk, st + 2, buf, t0, next_base, tid);
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, st + 2, buf, t0, next_base,
+                            tid);
       next_base = base_of(st + 3);
     }
     if (since + NC > p.flush || st == n_st - 1) {
-      widen_store<KIND, DR, NW, NC>(p, sm, acc, blk, t0, first);
+      widen_store<KIND, DR, NW, NC, kH>(p, sm.pw, acc, blk, t0, first);
       first = false;
       since = 0;
     }
@@ -535,12 +302,12 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.x = d_in;
   prm.stride = stride;
   prm.n_chan = p->n_chan;
-  prm.recs = static_cast<const tk::Rec*>(recs);
+  prm.recs = recs;
   prm.n_dm = static_cast<int32_t>(rp.n_dm);
   prm.n_blocks = rp.tile_n_blocks;
   prm.n_out = n_out;
   prm.lp = rp.tile_lp;
-  prm.lraw = tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp);
+  prm.lraw = tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp, 32 * rp.tile_h);
   prm.units_magic = rp.tile_units_magic;
   prm.units_shift = rp.tile_units_shift;
   prm.bin = rp.r.bin;
@@ -553,6 +320,8 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, void* stream) {
+  if (rp.tile_pattern)
+    return launch_forward_pattern(p, rp, recs, err, d_in, stride, n_out, d_out, stream);
   const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
   const int ts = tk::tile_samples(rp.tile_kind);
   const int64_t tiles = (n_out + ts - 1) / ts;

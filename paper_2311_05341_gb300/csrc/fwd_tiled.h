@@ -92,9 +92,38 @@ struct Rec {
 };
 static_assert(sizeof(Rec) == 64, "Rec must stay 64 bytes");
 
+// Pattern tiles (fwd_pattern.cu): every lane owns kPatDr consecutive DMs x H
+// window words, H odd.  When the shift of every channel grows by 0, 1 or 2
+// from one trial DM to the next, the offsets of a warp's DMs relative to its
+// first DM are (0, i1, i1 + i2, i1 + i2 + i3) with i_k in {0, 1, 2}: one of
+// kPatterns patterns, numbered i1 + 3 i2 + 9 i3.
+constexpr int kPatDr = 4;
+constexpr int kPatterns = 27;
+constexpr int kPatMaxInc = 2;
+constexpr int kPatMaxWarps = 16;
+constexpr int kPatOffBits = 11;      // window offset field of a pattern record entry
+constexpr uint32_t kPatOffMask = (1u << kPatOffBits) - 1;
+
+// Per (DM block of kPatDr * warps DMs, channel) record, 48 bytes.
+struct PRec {
+  int32_t base;                 // s(c, first DM of the block)
+  int32_t pad[3];
+  uint16_t w[kPatMaxWarps];     // warp w: window offset | pattern << kPatOffBits
+};
+static_assert(sizeof(PRec) == 48, "PRec must stay 48 bytes");
+
+// Pattern tile shapes: window words per lane (odd), warps per CTA, channels
+// per pipeline stage.
+struct PatShape {
+  int h;
+  int warps;
+  int nc;
+};
+constexpr PatShape kPatShapes[] = {{21, 16, 32}, {21, 16, 12}};
+
 constexpr size_t kRecOffset = 128;
-DD_HOST_DEVICE constexpr size_t raw_offset(int nc) {
-  return (kRecOffset + 2 * static_cast<size_t>(nc) * sizeof(Rec) + 127) / 128 * 128;
+DD_HOST_DEVICE constexpr size_t raw_offset(int nc, int rec_bytes = static_cast<int>(sizeof(Rec))) {
+  return (kRecOffset + 2 * static_cast<size_t>(nc) * rec_bytes + 127) / 128 * 128;
 }
 
 // Words of a channel's staged window for a given DM-block shift span.
@@ -103,9 +132,26 @@ inline int32_t window_words(int kind, int bin, int32_t span) {
   return (need + 15) / 16 * 16;
 }
 
-// Raw bytes fetched per channel and stage for lp window words.
-DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int bin, int32_t lp) {
-  return kind == kU8 ? lp + kPair : lp * elem_bytes(kind) * bin;
+// Raw bytes fetched per channel and stage for lp window words (uint8 at bin 1
+// also fetches the paired samples, `pair` words further).
+DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int bin, int32_t lp, int pair = kPair) {
+  return kind == kU8 ? lp + pair : lp * elem_bytes(kind) * bin;
+}
+
+// Pattern tiles: output samples per CTA tile, staged window words per channel
+// for a DM-block shift span, and shared memory.
+DD_HOST_DEVICE constexpr int pat_tile_samples(int kind, int h) {
+  return 32 * h * samples_per_word(kind);
+}
+inline int32_t pat_window_words(int kind, int bin, int h, int32_t span) {
+  // Lane 31 reads words up to 31h + (span + align - 1) + (h + 2 (kPatDr - 1)) - 1.
+  const int32_t need = 32 * h + span + (align_samples(kind, bin) - 1) + 2 * (kPatDr - 1);
+  return (need + 15) / 16 * 16;
+}
+inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp) {
+  return raw_offset(s.nc, static_cast<int>(sizeof(PRec))) +
+         2 * static_cast<size_t>(s.nc) * raw_bytes(kind, bin, lp, 32 * s.h) +
+         static_cast<size_t>(s.nc) * lp * 4;
 }
 
 inline size_t smem_bytes(int kind, int bin, const Shape& s, int32_t lp) {
@@ -118,7 +164,7 @@ struct TileParams {
   const void* x;        // channel-major input rows
   int64_t stride;       // elements between channel rows
   int32_t n_chan;
-  const Rec* recs;      // [n_blocks][n_chan]
+  const void* recs;     // [n_blocks][n_chan] Rec or PRec
   int32_t n_dm;
   int32_t n_blocks;
   int64_t n_out;

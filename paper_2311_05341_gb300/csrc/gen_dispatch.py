@@ -51,11 +51,52 @@ def macro(op, dr):
     return out
 
 
+PATTERN_H = (21,)  # odd window words per lane of the pattern tiles
+PATTERN_DR = 4
+
+
+def pattern_macro(op, h):
+    """DD_PAT_CHANNEL_<OP>_<H>(A, R, IX): 4 DMs of one lane, one indexed branch.
+
+    DM 0 adds R[0 .. h), DM i adds R[o_i .. o_i + h) with o_i the sum of the
+    first i increments; the 27 targets enumerate the increments (inc1, inc2,
+    inc3) in {0, 1, 2}^3 as IX = inc1 + 3 inc2 + 9 inc3.  R holds h + 6 words.
+    """
+    instr, cons = OPS[op]
+    tag = f"ddp{op.lower()}{h}"
+    nacc = PATTERN_DR * h
+    win = h + 2 * (PATTERN_DR - 1)
+    lines = ['"{\\n\\t"']
+    targets = ", ".join(f"{tag}_p{p}" for p in range(27))
+    lines.append(f'"{tag}_t: .branchtargets {targets};\\n\\t"')
+    lines.append(f'"brx.idx.uni %{nacc + win}, {tag}_t;\\n\\t"')
+    for p in range(27):
+        inc = (p % 3, (p // 3) % 3, p // 9)
+        offs = [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
+        lines.append(f'"{tag}_p{p}:\\n\\t"')
+        for i in range(PATTERN_DR):
+            for j in range(h):
+                lines.append(f'"{instr} %{i * h + j}, %{i * h + j}, %{nacc + offs[i] + j};\\n\\t"')
+        if p != 26:
+            lines.append(f'"bra.uni {tag}_end;\\n\\t"')
+    lines.append(f'"{tag}_end:\\n\\t}}"')
+    outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
+    ins = ", ".join(f'"{cons}"(R[{j}])' for j in range(win)) + ', "r"(IX)'
+    out = [f"#define DD_PAT_CHANNEL_{op}_{h}(A, R, IX) \\", "  asm volatile( \\"]
+    out += [f"      {ln} \\" for ln in lines]
+    out.append(f"      : {outs} \\")
+    out.append(f"      : {ins})")
+    return out
+
+
 def generate(path):
     out = ["// Generated by gen_dispatch.py at build time.", "#pragma once"]
     for op in OPS:
         for dr in SHAPES:
             out += macro(op, dr)
+            out.append("")
+        for h in PATTERN_H:
+            out += pattern_macro(op, h)
             out.append("")
     text = "\n".join(out) + "\n"
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <iterator>
 
 #include "dd_internal.h"
 #include "fwd_tiled.h"
@@ -87,6 +88,50 @@ bool build_tile_records(const RangePlan& rp, int32_t n_chan, int kind, const tk:
   return true;
 }
 
+// Records of the pattern kernel for shape ps (kPatDr DMs per lane, ps.warps
+// warps).  For DM block b (first DM d0), channel c and warp w (DMs
+// d0 + kPatDr w + i, clamped to the last DM):
+//   base = s(c, d0),  m = base mod A (as for the offset tiles),
+//   off  = s(c, d0 + kPatDr w) - base + m     (window offset, kPatOffBits bits),
+//   i_k  = s(c, d_k) - s(c, d_{k-1})            (k = 1..3, each in 0..kPatMaxInc),
+//   entry = off | (i_1 + 3 i_2 + 9 i_3) << kPatOffBits.
+// Returns false if some offset or increment does not fit.
+bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const tk::PatShape& ps,
+                           std::vector<tk::PRec>& recs, int32_t* n_blocks_out) {
+  using namespace tk;
+  const int dm_cta = kPatDr * ps.warps;
+  const int32_t align = align_samples(kind, rp.r.bin);
+  const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
+  recs.assign(static_cast<size_t>(n_blocks) * n_chan, tk::PRec{});
+  auto shift = [&](int64_t d, int32_t c) {
+    d = std::min<int64_t>(d, rp.n_dm - 1);
+    return rp.shifts[static_cast<size_t>(d) * n_chan + c];
+  };
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    const int64_t d0 = b * dm_cta;
+    for (int32_t c = 0; c < n_chan; ++c) {
+      tk::PRec& r = recs[static_cast<size_t>(b) * n_chan + c];
+      const int32_t base = shift(d0, c);
+      const int32_t m = base % align;
+      r.base = base;
+      for (int w = 0; w < ps.warps; ++w) {
+        const int64_t dw = d0 + static_cast<int64_t>(kPatDr) * w;
+        const int32_t off = shift(dw, c) - base + m;
+        if (off < 0 || off > static_cast<int32_t>(kPatOffMask)) return false;
+        uint32_t pat = 0, weight = 1;
+        for (int i = 1; i < kPatDr; ++i, weight *= 3) {
+          const int32_t inc = shift(dw + i, c) - shift(dw + i - 1, c);
+          if (inc < 0 || inc > kPatMaxInc) return false;
+          pat += weight * static_cast<uint32_t>(inc);
+        }
+        r.w[w] = static_cast<uint16_t>(static_cast<uint32_t>(off) | pat << kPatOffBits);
+      }
+    }
+  }
+  *n_blocks_out = static_cast<int32_t>(n_blocks);
+  return true;
+}
+
 // Multiply-high constants for exact u / d with u < limit (verified exhaustively).
 bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift) {
   int32_t s = 0;
@@ -121,13 +166,45 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
   int32_t n_blocks = 0;
   if (!build_tile_records(rp, n_chan, kind, sh, recs, &n_blocks)) return false;
   rp.tile_ok = true;
+  rp.tile_pattern = false;
   rp.tile_dr = sh.dr;
+  rp.tile_h = tk::kH;
+  rp.tile_shape = 0;
   rp.tile_kind = kind;
   rp.tile_n_blocks = n_blocks;
   rp.tile_lp = lp;
   rp.tile_units_magic = magic;
   rp.tile_units_shift = shift;
   rp.tile_recs.resize(recs.size() * sizeof(tk::Rec));
+  std::memcpy(rp.tile_recs.data(), recs.data(), rp.tile_recs.size());
+  return true;
+}
+
+// Try one pattern shape (index `shape` of tk::kPatShapes).
+bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
+  const tk::PatShape& ps = tk::kPatShapes[shape];
+  const int32_t span = block_span(rp, n_chan, tk::kPatDr * ps.warps);
+  const int32_t lp = tk::pat_window_words(kind, rp.r.bin, ps.h, span);
+  if (tk::pat_smem_bytes(kind, rp.r.bin, ps, lp) > 227 * 1024) return false;
+  uint32_t magic = 0;
+  int32_t shift = 0;
+  if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(ps.nc * lp / 4), &magic,
+                      &shift))
+    return false;
+  std::vector<tk::PRec> recs;
+  int32_t n_blocks = 0;
+  if (!build_pattern_records(rp, n_chan, kind, ps, recs, &n_blocks)) return false;
+  rp.tile_ok = true;
+  rp.tile_pattern = true;
+  rp.tile_dr = tk::kPatDr;
+  rp.tile_h = ps.h;
+  rp.tile_shape = shape;
+  rp.tile_kind = kind;
+  rp.tile_n_blocks = n_blocks;
+  rp.tile_lp = lp;
+  rp.tile_units_magic = magic;
+  rp.tile_units_shift = shift;
+  rp.tile_recs.resize(recs.size() * sizeof(tk::PRec));
   std::memcpy(rp.tile_recs.data(), recs.data(), rp.tile_recs.size());
   return true;
 }
@@ -142,11 +219,18 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
 void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   static const int kAutoOrder[] = {6, 4, 2, 1, 8};
   rp.tile_ok = false;
+  rp.tile_pattern = false;
   rp.tile_dr = 0;
+  rp.tile_h = 0;
   rp.tile_kind = 0;
   rp.tile_recs.clear();
   const int kind = (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W : static_cast<int>(dtype);
   if (!tk::bin_supported(kind, rp.r.bin)) return;
+  if (rp.tile_request == DD_TILE_PATTERN) {
+    for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
+      if (try_pattern_shape(rp, n_chan, kind, i)) return;
+    return;
+  }
   if (rp.tile_request > 0) {
     const tk::Shape* sh = tk::shape_for(rp.tile_request);
     if (sh) try_tile_shape(rp, n_chan, kind, *sh);

@@ -1,0 +1,278 @@
+// tile_common.cuh -- device helpers shared by the register-tiled forward
+// kernels (fwd_tiled.cu, fwd_pattern.cu): TMA bulk copies completing on
+// mbarriers, bounded mbarrier waits, accumulator/output types and the
+// unpacking of staged raw bytes into 32-bit window words (time binning fused).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "fwd_tiled.h"
+
+namespace dd {
+namespace tk {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitIters; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Accumulator (window word) and output element of a kind.
+template <int KIND>
+using AccT = std::conditional_t<KIND == kF32, float, uint32_t>;
+template <int KIND>
+using OutT = std::conditional_t<KIND == kF32, float, int32_t>;
+
+__device__ __forceinline__ uint32_t byte_sum4(uint32_t w) { return __dp4a(w, 0x01010101u, 0u); }
+__device__ __forceinline__ uint32_t half_sum2(uint32_t w) { return (w & 0xffffu) + (w >> 16); }
+
+// Unpack raw bytes into four window words (unit q of one channel).  At bin b
+// each word is the sum of b consecutive raw samples (the decimated sample).
+template <int KIND, int PAIR>
+__device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int bin) {
+  uint4 v;
+  if constexpr (KIND == kU8) {
+    // Word k packs X[k] and X[k + PAIR] in its 16-bit lanes (bin 1 only).
+    const uint32_t a = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q);
+    const uint32_t b = *reinterpret_cast<const uint32_t*>(raw_ch + 4 * q + PAIR);
+    const uint32_t t01 = __byte_perm(a, b, 0x5140);
+    const uint32_t t23 = __byte_perm(a, b, 0x7362);
+    v.x = __byte_perm(t01, 0u, 0x4140);
+    v.y = __byte_perm(t01, 0u, 0x4342);
+    v.z = __byte_perm(t23, 0u, 0x4140);
+    v.w = __byte_perm(t23, 0u, 0x4342);
+  } else if constexpr (KIND == kU8W) {
+    const uint8_t* r = raw_ch + 4 * q * bin;
+    if (bin == 2) {
+      const uint2 a = *reinterpret_cast<const uint2*>(r);
+      const uint32_t s0 = (a.x & 0x00ff00ffu) + ((a.x >> 8) & 0x00ff00ffu);
+      const uint32_t s1 = (a.y & 0x00ff00ffu) + ((a.y >> 8) & 0x00ff00ffu);
+      v = make_uint4(s0 & 0xffffu, s0 >> 16, s1 & 0xffffu, s1 >> 16);
+    } else if (bin == 4) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      v = make_uint4(byte_sum4(a.x), byte_sum4(a.y), byte_sum4(a.z), byte_sum4(a.w));
+    } else if (bin == 8) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      const uint4 b = *reinterpret_cast<const uint4*>(r + 16);
+      v = make_uint4(byte_sum4(a.x) + byte_sum4(a.y), byte_sum4(a.z) + byte_sum4(a.w),
+                     byte_sum4(b.x) + byte_sum4(b.y), byte_sum4(b.z) + byte_sum4(b.w));
+    } else {  // bin 16
+      uint32_t o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint4 a = *reinterpret_cast<const uint4*>(r + 16 * k);
+        o[k] = byte_sum4(a.x) + byte_sum4(a.y) + byte_sum4(a.z) + byte_sum4(a.w);
+      }
+      v = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  } else if constexpr (KIND == kU16) {
+    const uint8_t* r = raw_ch + 8 * q * bin;
+    if (bin == 1) {
+      const uint2 a = *reinterpret_cast<const uint2*>(r);
+      v = make_uint4(a.x & 0xffffu, a.x >> 16, a.y & 0xffffu, a.y >> 16);
+    } else if (bin == 2) {
+      const uint4 a = *reinterpret_cast<const uint4*>(r);
+      v = make_uint4(half_sum2(a.x), half_sum2(a.y), half_sum2(a.z), half_sum2(a.w));
+    } else {  // bin 4 or 8: bin / 2 words of two samples per output word
+      uint32_t o[4];
+      const int words = bin / 2;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t acc = 0;
+        for (int j = 0; j < words; ++j)
+          acc += half_sum2(*reinterpret_cast<const uint32_t*>(r + 4 * (k * words + j)));
+        o[k] = acc;
+      }
+      v = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  } else {  // kF32
+    const float* r = reinterpret_cast<const float*>(raw_ch + 16 * q * bin);
+    if (bin == 1) {
+      v = *reinterpret_cast<const uint4*>(r);
+    } else {
+      float o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float acc = 0.f;
+        for (int j = 0; j < bin; ++j) acc += r[k * bin + j];
+        o[k] = acc;
+      }
+      v = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                     __float_as_uint(o[3]));
+    }
+  }
+  return v;
+}
+
+// Issue the TMA copies of channel stage `st` into buffer `buf` (mbarrier at
+// bar_base + 8 buf).  Threads 0..NC-1 copy one channel's raw window each: it
+// starts at the 16-byte aligned decimated sample at or before t0 + base and is
+// clipped at the end of the row.  Thread NC copies the stage's records.
+template <int KIND, int NC, typename RecT>
+__device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_base, uint8_t* raw,
+                                            RecT* recs_sm, int blk, int st, int buf, int64_t t0,
+                                            int32_t base, int tid) {
+  constexpr int kE = elem_bytes(KIND);
+  const uint32_t bar = bar_base + 8u * buf;
+  const int c0 = st * NC;
+  if (tid < NC) {
+    const int c = c0 + tid;
+    uint32_t bytes = 0;
+    const uint8_t* src = nullptr;
+    if (c < p.n_chan) {
+      const int64_t align = 16 / (kE * p.bin);                       // decimated samples, 2^k
+      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw elements
+      if (ua < p.stride) {
+        const int64_t room = (p.stride - ua) * kE;
+        bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
+        src = static_cast<const uint8_t*>(p.x) + (static_cast<int64_t>(c) * p.stride + ua) * kE;
+      }
+    }
+    mbar_arrive_expect(bar, bytes);
+    if (bytes) {
+      uint8_t* dst = raw + (static_cast<size_t>(buf) * NC + tid) * p.lraw;
+      bulk_copy(smem_u32(dst), src, bytes, bar);
+    }
+  } else if (tid == NC) {
+    const int nc = min(NC, p.n_chan - c0);
+    const uint32_t bytes = static_cast<uint32_t>(nc) * sizeof(RecT);
+    mbar_arrive_expect(bar, bytes);
+    const RecT* src = static_cast<const RecT*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan + c0;
+    bulk_copy(smem_u32(recs_sm + buf * NC), src, bytes, bar);
+  }
+}
+
+// Transposed store tile of a register tile with H window words per lane.
+// Lane l holds positions p = H l + j (j < H); uint8 at bin 1 also holds
+// p + 32 H in the upper 16-bit halves.  The tile is read back row by row
+// (p = 32 k + l).  With H odd the identity index is conflict-free for both;
+// with H = 20 the index f(p) = p + p / 160 is.
+template <int KIND, int H>
+struct StoreTile {
+  static_assert(H % 2 == 1 || H == 20, "transpose index defined for odd H and H = 20");
+  static constexpr bool kPad = H % 2 == 0;
+  static constexpr int kRows = H * samples_per_word(KIND);  // rows of 32 positions
+  static constexpr int kPairW = 32 * H;                      // uint8 pair distance
+  static constexpr int kWords =                              // per-warp tile
+      kPad ? flush_words(KIND) : 32 * kRows;
+  __device__ static constexpr int row(int k) { return 32 * k + (kPad ? k / 5 : 0); }
+};
+
+// Store (first) or add (later) the accumulators of DR DMs x H words per lane
+// into the output rows through the warp's transposed shared tile.  The tiles
+// live in the window buffer pw; when it cannot hold one per warp, the warps
+// take turns in `groups` rounds.  Called by every thread of the CTA.
+template <int KIND, int DR, int NW, int NC, int H>
+__device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
+                                            AccT<KIND> (&acc)[DR][H], int blk, int64_t t0,
+                                            bool first) {
+  using ST = StoreTile<KIND, H>;
+  constexpr int kFw = ST::kWords;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  // Window buffers hold at least 32 H + 16 words per channel.
+  constexpr bool kAllFit = NC * (32 * H + 16) >= NW * kFw;
+  const int fit = (NC * p.lp) / kFw;  // tiles that fit the window buffer
+  const int groups = kAllFit ? 1 : (NW + fit - 1) / fit;
+  uint32_t* tr = pw + (w / groups) * kFw;
+  const int wbase = H * l + (ST::kPad ? (l >> 3) : 0);
+  constexpr int kHiOff = ST::kPairW + (ST::kPad ? ST::kPairW / 160 : 0);
+  const int64_t lim = p.n_out - t0;
+  for (int gi = 0; gi < groups; ++gi) {
+    if (gi > 0) __syncthreads();
+    if (w % groups != gi) continue;
+#pragma unroll
+    for (int i = 0; i < DR; ++i) {
+      const int d = blk * (DR * NW) + w * DR + i;
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        if constexpr (KIND == kU8) {
+          const uint32_t v = acc[i][j];
+          tr[wbase + j] = v & 0xffffu;
+          tr[wbase + j + kHiOff] = v >> 16;
+          acc[i][j] = 0u;
+        } else if constexpr (KIND == kU16 || KIND == kU8W) {
+          tr[wbase + j] = acc[i][j];
+          acc[i][j] = 0u;
+        } else {
+          tr[wbase + j] = __float_as_uint(acc[i][j]);
+          acc[i][j] = 0.f;
+        }
+      }
+      __syncwarp();
+      if (d < p.n_dm) {
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        constexpr int kCh = (ST::kRows + 1) / 2;  // rows per half
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          OutT<KIND> v[kCh];
+#pragma unroll
+          for (int k = 0; k < kCh; ++k) {
+            const int kk = h * kCh + k;
+            if (kk < ST::kRows) {
+              const uint32_t bits = tr[ST::row(kk) + l];
+              if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
+              else v[k] = static_cast<int32_t>(bits);
+            } else {
+              v[k] = OutT<KIND>(0);
+            }
+          }
+          if (!first) {
+            OutT<KIND> g[kCh];
+#pragma unroll
+            for (int k = 0; k < kCh; ++k) {
+              const int kk = h * kCh + k;
+              const int pos = 32 * kk + l;
+              g[k] = (kk < ST::kRows && pos < lim) ? __ldcg(row + pos) : OutT<KIND>(0);
+            }
+#pragma unroll
+            for (int k = 0; k < kCh; ++k) v[k] += g[k];
+          }
+#pragma unroll
+          for (int k = 0; k < kCh; ++k) {
+            const int kk = h * kCh + k;
+            const int pos = 32 * kk + l;
+            if (kk < ST::kRows && pos < lim) row[pos] = v[k];
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace tk
+}  // namespace dd

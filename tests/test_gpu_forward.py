@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import paper_2311_05341_gb300 as dd
+from paper_2311_05341_gb300._lib import DD_TILE_PATTERN as TILE_PATTERN
 from synth import workloads, channel_freqs, filterbank
 
 from gpu_util import assert_float_parity, oracle_input
@@ -131,11 +132,14 @@ def test_tiled_full_planes_every_shape(dtype, seed):
     ref = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges)
     ref_abs = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges, take_abs=True)
     xd = padded_device(x)
-    for dms in (8, 6, 4, 2, 1):
+    # Steps of at most 1.7 samples keep every per-DM increment in {0, 1, 2}:
+    # the pattern tile serves all these plans too.
+    for dms in (8, 6, 4, 2, 1, "pattern"):
         plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
         info = plan.info(b.n_samp)
-        assert info["kernel"] == ["tiled"] and info["tile_dms"] == [dms]
+        code = TILE_PATTERN if dms == "pattern" else dms
+        assert info["kernel"] == ["tiled"] and info["tile_dms"] == [code]
         got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
         if dtype == "f32":
             assert_float_parity(got, ref[0], ref_abs[0], f"tile {dms}")
@@ -159,7 +163,7 @@ def test_tiled_decimation_every_shape(dtype, b):
     ref_abs = oracle.forward(x, freqs, 1400.0, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
     ran = 0
-    for dms in (8, 6, 4, 2, 1):
+    for dms in (8, 6, 4, 2, 1, "pattern"):
         plan = dd.Plan(freqs, 1400.0, 64e-6, [r], dtype)
         try:
             plan.set_tile(0, dms)
@@ -246,12 +250,15 @@ def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
         np.testing.assert_array_equal(g, o)
 
 
-@pytest.mark.parametrize("make", [workloads.paper_u8, workloads.paper_u16],
-                         ids=["paper_u8", "paper_u16"])
-def test_paper_scale_sampled(make):
+@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, "pattern"),
+                                       (workloads.paper_u16, 0)],
+                         ids=["paper_u8", "paper_u8_pattern", "paper_u16"])
+def test_paper_scale_sampled(make, tile):
     beam = make()
     x, tables, n_dm, n_out = oracle_input(beam)
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
+    if tile:
+        plan.set_tile(0, tile)
     xt = torch.from_numpy(x).cuda()
     planes = plan.run(xt)
     torch.cuda.synchronize()

@@ -171,3 +171,26 @@ def test_kernel_selection():
     fb = workloads.batched()[32]  # 12.3 samples of delay per DM step
     plan = dd.Plan(fb.freqs, fb.f_high, fb.t_samp, fb.ranges, "f32", upload=False)
     assert plan.info(fb.n_samp)["tile_dms"] == [1]
+
+
+def test_pattern_tile_selection():
+    """The pattern tile serves plans whose per-DM shift increments are 0, 1 or 2."""
+    paper = workloads.paper_u8()  # at most 1.23 samples per DM step
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
+    ws_offset = plan.info(paper.n_samp)["workspace_bytes"]
+    plan.set_tile(0, "pattern")
+    info = plan.info(paper.n_samp)
+    assert info["kernel"] == ["tiled"] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
+    # 48-byte records for 64-DM blocks against 64-byte records for 72-DM blocks.
+    assert info["workspace_bytes"] != ws_offset
+    plan.set_tile(0, 0)
+    assert plan.info(paper.n_samp)["tile_dms"] == [6]
+    tiny = workloads.tiny_u8()  # 8 samples per DM step at the lowest channel
+    plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
+    with pytest.raises(dd.DDError) as ei:
+        plan.set_tile(0, "pattern")
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    assert plan.info(tiny.n_samp)["tile_dms"] == [2]
+    with pytest.raises(dd.DDError) as ei:
+        plan.set_tile(0, 3)
+    assert ei.value.status == _lib.DD_ERR_INVALID_ARG
