@@ -46,6 +46,8 @@ struct RangePlan {
   int32_t tile_lp = 0;          // window words per staged channel
   uint32_t tile_units_magic = 0;  // division by tile_lp / 4 (see fwd_tiled.h)
   int32_t tile_units_shift = 0;
+  size_t tile_chunk_off = 0;    // pair tiles: byte offset of the pair chunks in tile_recs
+  int32_t tile_chunk_bytes = 0; // pair tiles: bytes per (DM block, stage) chunk
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <iterator>
+#include <utility>
 
 #include "dd_internal.h"
 #include "fwd_tiled.h"
@@ -38,36 +40,66 @@ namespace {
 
 struct PSmem {
   uint32_t bar_base;  // 2 mbarriers
-  PRec* recs;         // [2][NC]
+  unsigned char* recs;  // [2][NC] PRec, or [2] pair chunks
   uint8_t* raw;       // [2][NC][lraw]
-  uint32_t* pw;       // [NC][lp] window words
+  uint32_t* pw;       // [NC][lp] window words (+ the zero window of the pair tiles)
 };
 
-template <int NC>
+template <int NW, int NC, bool PAIRS>
 __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
-  constexpr size_t kRawOff = raw_offset(NC, static_cast<int>(sizeof(PRec)));
+  constexpr size_t kRawOff = pat_raw_offset(NW, NC, PAIRS);
   PSmem sm;
   sm.bar_base = smem_u32(smem);
-  sm.recs = reinterpret_cast<PRec*>(smem + kRecOffset);
+  sm.recs = smem + kRecOffset;
   sm.raw = smem + kRawOff;
   sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
   return sm;
 }
 
+// The generated blocks exist for the window widths gen_dispatch.py lists.
+#define DD_PAT_CASE(HH)                                  \
+  if constexpr (H == HH) {                               \
+    if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
+    else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);            \
+    return;                                              \
+  }
+
 template <int KIND, int H>
 __device__ __forceinline__ void pat_dispatch(AccT<KIND> (&acc)[kPatDr][H],
                                              const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
                                              uint32_t ix) {
-  static_assert(H == 21, "pattern dispatch generated for H = 21 only");
-  if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_21(acc, R, ix);
-  else DD_PAT_CHANNEL_U32_21(acc, R, ix);
+  static_assert(H == 19 || H == 21 || H == 23 || H == 25, "no generated pattern blocks for H");
+  DD_PAT_CASE(19)
+  DD_PAT_CASE(21)
+  DD_PAT_CASE(23)
+  DD_PAT_CASE(25)
+}
+#undef DD_PAT_CASE
+
+template <int H>
+__device__ __forceinline__ void pair_dispatch(uint32_t (&acc)[kPatDr][H],
+                                              const uint32_t (&R1)[H + 2 * (kPatDr - 1)],
+                                              const uint32_t (&R2)[H + 2 * (kPatDr - 1)],
+                                              uint32_t ix) {
+  static_assert(H == 17 || H == 19 || H == 21, "no generated pair blocks for H");
+  if constexpr (H == 17) DD_PAT2_CHANNEL_U32_17(acc, R1, R2, ix);
+  else if constexpr (H == 19) DD_PAT2_CHANNEL_U32_19(acc, R1, R2, ix);
+  else DD_PAT2_CHANNEL_U32_21(acc, R1, R2, ix);
+}
+
+// Pair chunk of one (DM block, stage) in global memory.
+__device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, int blk, int n_st,
+                                                           int st) {
+  return static_cast<const unsigned char*>(p.recs) +
+         (static_cast<int64_t>(blk) * n_st + st) * p.chunk_bytes;
 }
 
 // One (DM block, time tile) work unit.  Returns false after a bounded wait
 // gave up (the status word is set).
-template <int KIND, int H, int NW, int NC>
+template <int KIND, int H, int NW, int NC, bool PAIRS>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
+  static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
   constexpr int kThreads = NW * 32;
   constexpr int kR = H + 2 * (kPatDr - 1);
   constexpr int kPairW = 32 * H;
@@ -76,14 +108,29 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   const int n_st = (p.n_chan + NC - 1) / NC;
 
   const PRec* my_recs = static_cast<const PRec*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan;
+  const int32_t* my_bases = p.bases + static_cast<int64_t>(blk) * p.n_chan;
   auto base_of = [&](int st) -> int32_t {
     const int c = st * NC + tid;
-    return (tid < NC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
+    if (!(tid < NC && st < n_st && c < p.n_chan)) return 0;
+    if constexpr (PAIRS) return my_bases[c];
+    else return my_recs[c].base;
+  };
+  const ChannelRecs<NC, PRec> cr{my_recs, reinterpret_cast<PRec*>(sm.recs), p.n_chan};
+  auto issue = [&](int st, int buf, int32_t base) {
+    if constexpr (PAIRS)
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, buf, t0, base, tid,
+                            pair_chunk(p, blk, n_st, st), p.chunk_bytes,
+                            sm.recs + buf * p.chunk_bytes);
+    else
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, buf, t0, base, tid, cr.src(st),
+                            cr.bytes(st), cr.dst(buf));
   };
   if (tid <= NC) {
-    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 0, 0, t0, base_of(0), tid);
-    if (n_st > 1)
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 1, 1, t0, base_of(1), tid);
+    issue(0, 0, base_of(0));
+    if (n_st > 1) issue(1, 1, base_of(1));
+  }
+  if constexpr (PAIRS) {  // the zero window pairs a channel left without a partner
+    for (int k = tid; k < pair_zero_words(H); k += kThreads) sm.pw[NC * p.lp + k] = 0u;
   }
   int32_t next_base = base_of(2);
 
@@ -128,26 +175,45 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
     // Shift-and-sum.  The loop stays rolled so the dispatch block, and its PTX
     // labels, appear once per instantiation.
-    const PRec* rs = sm.recs + buf * NC;
     const uint32_t* lane_pw = sm.pw + H * l;
+    if constexpr (PAIRS) {
+      const unsigned char* ck = sm.recs + buf * p.chunk_bytes;
+      const int n_items = ck[w];
+      const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
 #pragma unroll 1
-    for (int ch = 0; ch < nc; ++ch) {
-      const uint32_t e = rs[ch].w[w];
-      const uint32_t* src = lane_pw + static_cast<size_t>(ch) * p.lp + (e & kPatOffMask);
-      AccT<KIND> R[kR];
+      for (int k = 0; k < n_items; ++k) {
+        const PairItem it = items[k];
+        const uint32_t* s1 = lane_pw + (it.a & 0xffffu);
+        const uint32_t* s2 = lane_pw + (it.a >> 16);
+        uint32_t R1[kR], R2[kR];
 #pragma unroll
-      for (int k = 0; k < kR; ++k) {
-        if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
-        else R[k] = src[k];
+        for (int j = 0; j < kR; ++j) {
+          R1[j] = s1[j];
+          R2[j] = s2[j];
+        }
+        pair_dispatch<H>(acc, R1, R2, it.pat);
       }
-      pat_dispatch<KIND, H>(acc, R, e >> kPatOffBits);
+    } else {
+      const PRec* rs = reinterpret_cast<const PRec*>(sm.recs) + buf * NC;
+#pragma unroll 1
+      for (int ch = 0; ch < nc; ++ch) {
+        const uint32_t e = rs[ch].w[w];
+        const uint32_t* src = lane_pw + static_cast<size_t>(ch) * p.lp + (e & kPatOffMask);
+        AccT<KIND> R[kR];
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+          if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
+          else R[k] = src[k];
+        }
+        pat_dispatch<KIND, H>(acc, R, e >> kPatOffBits);
+      }
     }
     since += nc;
     __syncthreads();  // window words, raw[buf] and recs[buf] are free
 
     if (tid <= NC && st + 2 < n_st) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, st + 2, buf, t0, next_base, tid);
+      issue(st + 2, buf, next_base);
       next_base = base_of(st + 3);
     }
     if (since + NC > p.flush || st == n_st - 1) {
@@ -161,27 +227,27 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
 }  // namespace
 
-template <int KIND, int H, int NW, int NC>
+template <int KIND, int H, int NW, int NC, bool PAIRS>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const PSmem sm = pat_layout<NC>(smem, p.lraw);
+  const PSmem sm = pat_layout<NW, NC, PAIRS>(smem, p.lraw);
   if (threadIdx.x == 0) {
     mbar_init(sm.bar_base, NC + 1);
     mbar_init(sm.bar_base + 8, NC + 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pat_body<KIND, H, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks);
+  pat_body<KIND, H, NW, NC, PAIRS>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks);
 }
 
 }  // namespace tk
 
 namespace {
 
-template <int KIND, int H, int NW, int NC>
+template <int KIND, int H, int NW, int NC, bool PAIRS>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
-  const size_t smem = tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC}, prm.lp);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC>;
+  const size_t smem = tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS}, prm.lp);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -189,17 +255,29 @@ int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t s
   return static_cast<int>(cudaGetLastError());
 }
 
+template <int KIND, int I>
+int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  constexpr tk::PatShape s = tk::kPatShapes[I];
+  if constexpr (s.pairs && KIND == tk::kF32) {
+    return static_cast<int>(cudaErrorInvalidValue);  // the planner never pairs float channels
+  } else {
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs>(prm, grid, st);
+  }
+}
+
+template <int KIND, size_t... I>
+int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cudaStream_t st,
+                        std::index_sequence<I...>) {
+  int rc = static_cast<int>(cudaErrorInvalidValue);
+  ((shape == static_cast<int>(I) ? (rc = launch_pattern_index<KIND, I>(prm, grid, st), 0) : 0),
+   ...);
+  return rc;
+}
+
 template <int KIND>
 int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
-  static_assert(tk::kPatShapes[0].h == 21 && tk::kPatShapes[0].warps == 16 &&
-                    tk::kPatShapes[0].nc == 32 && tk::kPatShapes[1].h == 21 &&
-                    tk::kPatShapes[1].warps == 16 && tk::kPatShapes[1].nc == 12,
-                "pattern launch table out of date");
-  switch (shape) {
-    case 0: return launch_pattern_shape<KIND, 21, 16, 32>(prm, grid, st);
-    case 1: return launch_pattern_shape<KIND, 21, 16, 12>(prm, grid, st);
-  }
-  return static_cast<int>(cudaErrorInvalidValue);
+  return launch_pattern_kind<KIND>(
+      shape, prm, grid, st, std::make_index_sequence<std::size(tk::kPatShapes)>{});
 }
 
 }  // namespace

@@ -102,11 +102,14 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
     const int c = st * NC + tid;
     return (tid < NC && st < n_st && c < p.n_chan) ? my_recs[c].base : 0;
   };
+  const ChannelRecs<NC, Rec> cr{my_recs, sm.recs, p.n_chan};
+  auto issue = [&](int st, int buf, int32_t base) {
+    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, buf, t0, base, tid, cr.src(st),
+                          cr.bytes(st), cr.dst(buf));
+  };
   if (tid <= NC) {
-    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 0, gstage & 1, t0, base_of(0), tid);
-    if (n_st > 1)
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, 1, (gstage + 1) & 1, t0,
-                            base_of(1), tid);
+    issue(0, gstage & 1, base_of(0));
+    if (n_st > 1) issue(1, (gstage + 1) & 1, base_of(1));
   }
   int32_t next_base = base_of(2);
 
@@ -181,8 +184,7 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
 
     if (tid <= NC && st + 2 < n_st) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, sm.recs, blk, st + 2, buf, t0, next_base,
-                            tid);
+      issue(st + 2, buf, next_base);
       next_base = base_of(st + 3);
     }
     if (since + NC > p.flush || st == n_st - 1) {
@@ -303,6 +305,11 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.stride = stride;
   prm.n_chan = p->n_chan;
   prm.recs = recs;
+  if (rp.tile_pattern && rp.tile_chunk_bytes > 0) {  // pair tiles: base table, then chunks
+    prm.bases = static_cast<const int32_t*>(recs);
+    prm.recs = static_cast<const unsigned char*>(recs) + rp.tile_chunk_off;
+    prm.chunk_bytes = rp.tile_chunk_bytes;
+  }
   prm.n_dm = static_cast<int32_t>(rp.n_dm);
   prm.n_blocks = rp.tile_n_blocks;
   prm.n_out = n_out;

@@ -51,7 +51,7 @@ def macro(op, dr):
     return out
 
 
-PATTERN_H = (21,)  # odd window words per lane of the pattern tiles
+PATTERN_H = (19, 21, 23, 25)  # odd window words per lane of the pattern tiles
 PATTERN_DR = 4
 
 
@@ -89,6 +89,46 @@ def pattern_macro(op, h):
     return out
 
 
+PAIR_H = (17, 19, 21)  # window words per lane of the channel-pair pattern tiles
+
+
+def pair_macro(h):
+    """DD_PAT2_CHANNEL_U32_<H>(A, R1, R2, IX): two channels with one pattern.
+
+    Like DD_PAT_CHANNEL_U32_<H> for two windows R1, R2 (h + 6 words each)
+    whose channels share the increment pattern IX: every accumulator takes
+    both samples in two consecutive adds, which the assembler can merge into
+    one three-input add.
+    """
+    tag = f"ddq{h}"
+    nacc = PATTERN_DR * h
+    win = h + 2 * (PATTERN_DR - 1)
+    lines = ['"{\\n\\t"']
+    targets = ", ".join(f"{tag}_p{p}" for p in range(27))
+    lines.append(f'"{tag}_t: .branchtargets {targets};\\n\\t"')
+    lines.append(f'"brx.idx.uni %{nacc + 2 * win}, {tag}_t;\\n\\t"')
+    for p in range(27):
+        inc = (p % 3, (p // 3) % 3, p // 9)
+        offs = [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
+        lines.append(f'"{tag}_p{p}:\\n\\t"')
+        for i in range(PATTERN_DR):
+            for j in range(h):
+                a = i * h + j
+                lines.append(f'"add.u32 %{a}, %{a}, %{nacc + offs[i] + j};\\n\\t"')
+                lines.append(f'"add.u32 %{a}, %{a}, %{nacc + win + offs[i] + j};\\n\\t"')
+        if p != 26:
+            lines.append(f'"bra.uni {tag}_end;\\n\\t"')
+    lines.append(f'"{tag}_end:\\n\\t}}"')
+    outs = ", ".join(f'"+r"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
+    ins = ", ".join(f'"r"(R1[{j}])' for j in range(win)) + ", "
+    ins += ", ".join(f'"r"(R2[{j}])' for j in range(win)) + ', "r"(IX)'
+    out = [f"#define DD_PAT2_CHANNEL_U32_{h}(A, R1, R2, IX) \\", "  asm volatile( \\"]
+    out += [f"      {ln} \\" for ln in lines]
+    out.append(f"      : {outs} \\")
+    out.append(f"      : {ins})")
+    return out
+
+
 def generate(path):
     out = ["// Generated by gen_dispatch.py at build time.", "#pragma once"]
     for op in OPS:
@@ -98,6 +138,9 @@ def generate(path):
         for h in PATTERN_H:
             out += pattern_macro(op, h)
             out.append("")
+    for h in PAIR_H:
+        out += pair_macro(h)
+        out.append("")
     text = "\n".join(out) + "\n"
     os.makedirs(os.path.dirname(path), exist_ok=True)
     if not os.path.exists(path) or open(path).read() != text:

@@ -132,6 +132,75 @@ bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const 
   return true;
 }
 
+// Channel-pair tables of the pattern kernel for shape ps (ps.pairs): the base
+// shifts s(c, d0) of every (DM block, channel) as int32, padded to 256 bytes,
+// then one chunk per (DM block, stage of ps.nc channels).  In a chunk, warp w
+// lists the stage's channels as pairs of equal pattern (entries as in
+// build_pattern_records), grouped by pattern; a channel left alone is paired
+// with the zero window.  Item word offsets a = staged channel * lp + off must
+// stay below 2^16.  Returns false if some offset or increment does not fit.
+bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::PatShape& ps,
+                       int32_t lp, std::vector<unsigned char>& out, size_t* chunk_off,
+                       int32_t* n_blocks_out) {
+  using namespace tk;
+  const int dm_cta = kPatDr * ps.warps;
+  const int32_t align = align_samples(kind, rp.r.bin);
+  const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
+  const int n_st = (n_chan + ps.nc - 1) / ps.nc;
+  const uint32_t zero = static_cast<uint32_t>(ps.nc) * static_cast<uint32_t>(lp);
+  if (zero > 0xffffu) return false;
+  const size_t cb = static_cast<size_t>(pair_chunk_bytes(ps.warps, ps.nc));
+  const size_t bases_bytes = align_up(static_cast<size_t>(n_blocks) * n_chan * 4, 256);
+  out.assign(bases_bytes + static_cast<size_t>(n_blocks) * n_st * cb, 0);
+  auto shift = [&](int64_t d, int32_t c) {
+    d = std::min<int64_t>(d, rp.n_dm - 1);
+    return rp.shifts[static_cast<size_t>(d) * n_chan + c];
+  };
+  std::vector<std::vector<uint32_t>> by_pat(kPatterns);
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    const int64_t d0 = b * dm_cta;
+    int32_t* bases = reinterpret_cast<int32_t*>(out.data()) + b * n_chan;
+    for (int32_t c = 0; c < n_chan; ++c) bases[c] = shift(d0, c);
+    for (int st = 0; st < n_st; ++st) {
+      unsigned char* chunk = out.data() + bases_bytes + (static_cast<size_t>(b) * n_st + st) * cb;
+      PairItem* items = reinterpret_cast<PairItem*>(chunk + kPairCountBytes);
+      const int c0 = st * ps.nc, nc = std::min(ps.nc, n_chan - c0);
+      for (int w = 0; w < ps.warps; ++w) {
+        for (auto& v : by_pat) v.clear();
+        const int64_t dw = d0 + static_cast<int64_t>(kPatDr) * w;
+        for (int k = 0; k < nc; ++k) {
+          const int32_t c = c0 + k;
+          const int32_t base = bases[c];
+          const int32_t off = shift(dw, c) - base + base % align;
+          if (off < 0 || off > static_cast<int32_t>(kPatOffMask)) return false;
+          uint32_t pat = 0, weight = 1;
+          for (int i = 1; i < kPatDr; ++i, weight *= 3) {
+            const int32_t inc = shift(dw + i, c) - shift(dw + i - 1, c);
+            if (inc < 0 || inc > kPatMaxInc) return false;
+            pat += weight * static_cast<uint32_t>(inc);
+          }
+          const uint32_t a = static_cast<uint32_t>(k) * lp + static_cast<uint32_t>(off);
+          if (a > 0xffffu) return false;
+          by_pat[pat].push_back(a);
+        }
+        int n = 0;
+        for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat) {
+          const auto& v = by_pat[pat];
+          for (size_t i = 0; i < v.size(); i += 2) {
+            const uint32_t a2 = i + 1 < v.size() ? v[i + 1] : zero;
+            items[w * ps.nc + n] = PairItem{v[i] | a2 << 16, pat};
+            ++n;
+          }
+        }
+        chunk[w] = static_cast<unsigned char>(n);
+      }
+    }
+  }
+  *chunk_off = bases_bytes;
+  *n_blocks_out = static_cast<int32_t>(n_blocks);
+  return true;
+}
+
 // Multiply-high constants for exact u / d with u < limit (verified exhaustively).
 bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift) {
   int32_t s = 0;
@@ -170,6 +239,8 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
   rp.tile_dr = sh.dr;
   rp.tile_h = tk::kH;
   rp.tile_shape = 0;
+  rp.tile_chunk_off = 0;
+  rp.tile_chunk_bytes = 0;
   rp.tile_kind = kind;
   rp.tile_n_blocks = n_blocks;
   rp.tile_lp = lp;
@@ -191,9 +262,18 @@ bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(ps.nc * lp / 4), &magic,
                       &shift))
     return false;
-  std::vector<tk::PRec> recs;
+  std::vector<unsigned char> tables;
   int32_t n_blocks = 0;
-  if (!build_pattern_records(rp, n_chan, kind, ps, recs, &n_blocks)) return false;
+  size_t chunk_off = 0;
+  if (ps.pairs) {
+    if (kind == tk::kF32) return false;  // a float add takes two inputs only
+    if (!build_pair_tables(rp, n_chan, kind, ps, lp, tables, &chunk_off, &n_blocks)) return false;
+  } else {
+    std::vector<tk::PRec> recs;
+    if (!build_pattern_records(rp, n_chan, kind, ps, recs, &n_blocks)) return false;
+    tables.resize(recs.size() * sizeof(tk::PRec));
+    std::memcpy(tables.data(), recs.data(), tables.size());
+  }
   rp.tile_ok = true;
   rp.tile_pattern = true;
   rp.tile_dr = tk::kPatDr;
@@ -204,8 +284,9 @@ bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   rp.tile_lp = lp;
   rp.tile_units_magic = magic;
   rp.tile_units_shift = shift;
-  rp.tile_recs.resize(recs.size() * sizeof(tk::PRec));
-  std::memcpy(rp.tile_recs.data(), recs.data(), rp.tile_recs.size());
+  rp.tile_chunk_off = chunk_off;
+  rp.tile_chunk_bytes = ps.pairs ? tk::pair_chunk_bytes(ps.warps, ps.nc) : 0;
+  rp.tile_recs = std::move(tables);
   return true;
 }
 
@@ -223,6 +304,8 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_dr = 0;
   rp.tile_h = 0;
   rp.tile_kind = 0;
+  rp.tile_chunk_off = 0;
+  rp.tile_chunk_bytes = 0;
   rp.tile_recs.clear();
   const int kind = (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W : static_cast<int>(dtype);
   if (!tk::bin_supported(kind, rp.r.bin)) return;

@@ -141,16 +141,17 @@ __device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int b
 // Issue the TMA copies of channel stage `st` into buffer `buf` (mbarrier at
 // bar_base + 8 buf).  Threads 0..NC-1 copy one channel's raw window each: it
 // starts at the 16-byte aligned decimated sample at or before t0 + base and is
-// clipped at the end of the row.  Thread NC copies the stage's records.
-template <int KIND, int NC, typename RecT>
+// clipped at the end of the row.  Thread NC copies rec_bytes of the stage's
+// records from rec_src to rec_dst.
+template <int KIND, int NC>
 __device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_base, uint8_t* raw,
-                                            RecT* recs_sm, int blk, int st, int buf, int64_t t0,
-                                            int32_t base, int tid) {
+                                            int st, int buf, int64_t t0, int32_t base, int tid,
+                                            const void* rec_src, uint32_t rec_bytes,
+                                            void* rec_dst) {
   constexpr int kE = elem_bytes(KIND);
   const uint32_t bar = bar_base + 8u * buf;
-  const int c0 = st * NC;
   if (tid < NC) {
-    const int c = c0 + tid;
+    const int c = st * NC + tid;
     uint32_t bytes = 0;
     const uint8_t* src = nullptr;
     if (c < p.n_chan) {
@@ -168,13 +169,24 @@ __device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_ba
       bulk_copy(smem_u32(dst), src, bytes, bar);
     }
   } else if (tid == NC) {
-    const int nc = min(NC, p.n_chan - c0);
-    const uint32_t bytes = static_cast<uint32_t>(nc) * sizeof(RecT);
-    mbar_arrive_expect(bar, bytes);
-    const RecT* src = static_cast<const RecT*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan + c0;
-    bulk_copy(smem_u32(recs_sm + buf * NC), src, bytes, bar);
+    mbar_arrive_expect(bar, rec_bytes);
+    bulk_copy(smem_u32(rec_dst), rec_src, rec_bytes, bar);
   }
 }
+
+// Per-channel records of stage st (Rec or PRec, base shift first): the copy
+// arguments of issue_stage.
+template <int NC, typename RecT>
+struct ChannelRecs {
+  const RecT* blk_recs;  // the block's records in global memory
+  RecT* sm;              // [2][NC] in shared memory
+  int n_chan;
+  __device__ const void* src(int st) const { return blk_recs + st * NC; }
+  __device__ uint32_t bytes(int st) const {
+    return static_cast<uint32_t>(min(NC, n_chan - st * NC)) * sizeof(RecT);
+  }
+  __device__ void* dst(int buf) const { return sm + buf * NC; }
+};
 
 // Transposed store tile of a register tile with H window words per lane.
 // Lane l holds positions p = H l + j (j < H); uint8 at bin 1 also holds
