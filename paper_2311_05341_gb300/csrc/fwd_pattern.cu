@@ -40,14 +40,14 @@ namespace {
 
 struct PSmem {
   uint32_t bar_base;  // 2 mbarriers
-  unsigned char* recs;  // [2][NC] PRec, or [2] pair chunks
+  unsigned char* recs;  // [2 or 3][NC] PRec, or [2 or 3] pair chunks
   uint8_t* raw;       // [2][NC][lraw]
-  uint32_t* pw;       // [NC][lp] window words (+ the zero window of the pair tiles)
+  uint32_t* pw;       // [1 or 2][NC][lp] window words
 };
 
-template <int NW, int NC, bool PAIRS>
+template <int NW, int NC, bool PAIRS, bool DBUF>
 __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
-  constexpr size_t kRawOff = pat_raw_offset(NW, NC, PAIRS);
+  constexpr size_t kRawOff = pat_raw_offset(NW, NC, PAIRS, DBUF);
   PSmem sm;
   sm.bar_base = smem_u32(smem);
   sm.recs = smem + kRecOffset;
@@ -68,7 +68,9 @@ template <int KIND, int H>
 __device__ __forceinline__ void pat_dispatch(AccT<KIND> (&acc)[kPatDr][H],
                                              const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
                                              uint32_t ix) {
-  static_assert(H == 19 || H == 21 || H == 23 || H == 25, "no generated pattern blocks for H");
+  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+                "no generated pattern blocks for H");
+  DD_PAT_CASE(17)
   DD_PAT_CASE(19)
   DD_PAT_CASE(21)
   DD_PAT_CASE(23)
@@ -96,13 +98,22 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 
 // One (DM block, time tile) work unit.  Returns false after a bounded wait
 // gave up (the status word is set).
-template <int KIND, int H, int NW, int NC, bool PAIRS>
+//
+// Stage st uses raw buffer st % 2 and record buffer st % kRecBufs.  With
+// DBUF the window words are double-buffered too (stage st in window buffer
+// st % 2) and one barrier per stage suffices: the barrier after unpacking
+// stage st also certifies that every warp finished computing stage st - 1,
+// so the copies of stage st + 2 (raw buffer st % 2, record buffer
+// (st + 2) % 3) and the unpacking of stage st + 1 may start while warps still
+// compute stage st.  Without DBUF a second barrier ends each stage.
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
   constexpr int kThreads = NW * 32;
   constexpr int kR = H + 2 * (kPatDr - 1);
   constexpr int kPairW = 32 * H;
+  constexpr int kRecBufs = DBUF ? 3 : 2;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int64_t t0 = tile * pat_tile_samples(KIND, H);
   const int n_st = (p.n_chan + NC - 1) / NC;
@@ -115,24 +126,32 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     if constexpr (PAIRS) return my_bases[c];
     else return my_recs[c].base;
   };
+  auto rec_buf = [&](int rb) -> unsigned char* {
+    if constexpr (PAIRS) return sm.recs + rb * p.chunk_bytes;
+    else return sm.recs + rb * NC * static_cast<int>(sizeof(PRec));
+  };
   const ChannelRecs<NC, PRec> cr{my_recs, reinterpret_cast<PRec*>(sm.recs), p.n_chan};
-  auto issue = [&](int st, int buf, int32_t base) {
+  auto issue = [&](int st, int32_t base) {
+    unsigned char* dst = rec_buf(st % kRecBufs);
     if constexpr (PAIRS)
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, buf, t0, base, tid,
-                            pair_chunk(p, blk, n_st, st), p.chunk_bytes,
-                            sm.recs + buf * p.chunk_bytes);
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid,
+                            pair_chunk(p, blk, n_st, st), p.chunk_bytes, dst);
     else
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, buf, t0, base, tid, cr.src(st),
-                            cr.bytes(st), cr.dst(buf));
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid, cr.src(st),
+                            cr.bytes(st), dst);
   };
   if (tid <= NC) {
-    issue(0, 0, base_of(0));
-    if (n_st > 1) issue(1, 1, base_of(1));
-  }
-  if constexpr (PAIRS) {  // the zero window pairs a channel left without a partner
-    for (int k = tid; k < pair_zero_words(H); k += kThreads) sm.pw[NC * p.lp + k] = 0u;
+    issue(0, base_of(0));
+    if (n_st > 1) issue(1, base_of(1));
   }
   int32_t next_base = base_of(2);
+  auto issue_next = [&](int st) {  // copies of stage st + 2 into the buffers stage st freed
+    if (tid <= NC && st + 2 < n_st) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(st + 2, next_base);
+      next_base = base_of(st + 3);
+    }
+  };
 
   AccT<KIND> acc[kPatDr][H];
 #pragma unroll
@@ -143,11 +162,27 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   bool first = true;
   int since = 0;  // channels accumulated since the last widen
   const int units = p.lp >> 2;
+  int rb = 0;     // st % kRecBufs
 
   for (int st = 0; st < n_st; ++st) {
     const int buf = st & 1;
     const uint32_t parity = (st >> 1) & 1;
+    const int nc = min(NC, p.n_chan - st * NC);
+    uint32_t* pwb = sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
+    auto unpack = [&]() {  // raw bytes of stage st into window words
+      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
+      const int total = nc * units;
+      for (int u = tid; u < total; u += kThreads) {
+        const int ch =
+            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
+        const int q = u - ch * units;
+        const uint4 v =
+            unpack_unit<KIND, kPairW>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
+        *reinterpret_cast<uint4*>(pwb + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
+      }
+    };
     const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
+    if (DBUF && ok) unpack();
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.err, kErrTimeout);
@@ -157,31 +192,22 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       }
       return false;
     }
-    const int nc = min(NC, p.n_chan - st * NC);
-
-    {  // Unpack raw bytes into window words.
-      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
-      const int total = nc * units;
-      for (int u = tid; u < total; u += kThreads) {
-        const int ch =
-            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
-        const int q = u - ch * units;
-        const uint4 v =
-            unpack_unit<KIND, kPairW>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
-        *reinterpret_cast<uint4*>(sm.pw + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
-      }
+    if constexpr (DBUF) {
+      issue_next(st);
+    } else {
+      unpack();
+      __syncthreads();
     }
-    __syncthreads();
 
-    // Shift-and-sum.  The loop stays rolled so the dispatch block, and its PTX
-    // labels, appear once per instantiation.
-    const uint32_t* lane_pw = sm.pw + H * l;
+    // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
+    // PTX labels, appear once per instantiation.
+    const uint32_t* lane_pw = pwb + H * l;
     if constexpr (PAIRS) {
-      const unsigned char* ck = sm.recs + buf * p.chunk_bytes;
-      const int n_items = ck[w];
+      const unsigned char* ck = rec_buf(rb);
+      const int n_pairs = ck[w], n_items = n_pairs + ck[16 + w];
       const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
 #pragma unroll 1
-      for (int k = 0; k < n_items; ++k) {
+      for (int k = 0; k < n_pairs; ++k) {
         const PairItem it = items[k];
         const uint32_t* s1 = lane_pw + (it.a & 0xffffu);
         const uint32_t* s2 = lane_pw + (it.a >> 16);
@@ -193,8 +219,17 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
         }
         pair_dispatch<H>(acc, R1, R2, it.pat);
       }
+#pragma unroll 1
+      for (int k = n_pairs; k < n_items; ++k) {
+        const PairItem it = items[k];
+        const uint32_t* s1 = lane_pw + it.a;
+        uint32_t R1[kR];
+#pragma unroll
+        for (int j = 0; j < kR; ++j) R1[j] = s1[j];
+        pat_dispatch<KIND, H>(acc, R1, it.pat);
+      }
     } else {
-      const PRec* rs = reinterpret_cast<const PRec*>(sm.recs) + buf * NC;
+      const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
 #pragma unroll 1
       for (int ch = 0; ch < nc; ++ch) {
         const uint32_t e = rs[ch].w[w];
@@ -209,15 +244,16 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       }
     }
     since += nc;
-    __syncthreads();  // window words, raw[buf] and recs[buf] are free
-
-    if (tid <= NC && st + 2 < n_st) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(st + 2, buf, next_base);
-      next_base = base_of(st + 3);
+    rb = rb + 1 == kRecBufs ? 0 : rb + 1;
+    if constexpr (!DBUF) {
+      __syncthreads();  // window words, raw[buf] and recs[buf] are free
+      issue_next(st);
     }
     if (since + NC > p.flush || st == n_st - 1) {
-      widen_store<KIND, kPatDr, NW, NC, H>(p, sm.pw, acc, blk, t0, first);
+      // The transpose tiles reuse this stage's window buffer: wait until every
+      // warp has finished reading it.
+      if constexpr (DBUF) __syncthreads();
+      widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
       first = false;
       since = 0;
     }
@@ -227,27 +263,29 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
 }  // namespace
 
-template <int KIND, int H, int NW, int NC, bool PAIRS>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const PSmem sm = pat_layout<NW, NC, PAIRS>(smem, p.lraw);
+  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF>(smem, p.lraw);
   if (threadIdx.x == 0) {
     mbar_init(sm.bar_base, NC + 1);
     mbar_init(sm.bar_base + 8, NC + 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pat_body<KIND, H, NW, NC, PAIRS>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks);
+  pat_body<KIND, H, NW, NC, PAIRS, DBUF>(p, sm, blockIdx.x % p.n_blocks,
+                                         blockIdx.x / p.n_blocks);
 }
 
 }  // namespace tk
 
 namespace {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
-  const size_t smem = tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS}, prm.lp);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS>;
+  const size_t smem =
+      tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF}, prm.lp);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -261,7 +299,7 @@ int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t s
   if constexpr (s.pairs && KIND == tk::kF32) {
     return static_cast<int>(cudaErrorInvalidValue);  // the planner never pairs float channels
   } else {
-    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs>(prm, grid, st);
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf>(prm, grid, st);
   }
 }
 

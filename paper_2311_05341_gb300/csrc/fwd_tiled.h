@@ -114,11 +114,12 @@ static_assert(sizeof(PRec) == 48, "PRec must stay 48 bytes");
 
 // Channel pairs: with `pairs`, each warp runs the channels of a stage as
 // pairs that share its increment pattern, two samples per accumulator update
-// (a three-input integer add).  Per (DM block, stage) the host writes a chunk
-// of per-warp pair lists: 16 count bytes, then warps x nc items
-// {a1 | a2 << 16, pattern}, a = staged channel * lp + window offset; a
-// channel left without a partner is paired with a zero window (a = nc * lp).
-constexpr int kPairCountBytes = 16;
+// (a three-input integer add), and the channels left without a partner one by
+// one.  Per (DM block, stage) the host writes a chunk of per-warp lists: pair
+// counts (16 bytes), single counts (16 bytes), then warps x nc items
+// {a1 | a2 << 16, pattern}, pairs first, a = staged channel * lp + window
+// offset.
+constexpr int kPairCountBytes = 32;
 struct PairItem {
   uint32_t a;    // a1 | a2 << 16 (word offsets into the window buffer)
   uint32_t pat;  // pattern number
@@ -126,20 +127,22 @@ struct PairItem {
 static_assert(sizeof(PairItem) == 8, "PairItem must stay 8 bytes");
 
 // Pattern tile shapes: window words per lane (odd), warps per CTA, channels
-// per pipeline stage, channel pairs (integer kinds only).
+// per pipeline stage, channel pairs (integer kinds only), double-buffered
+// window words (one barrier per stage).
 struct PatShape {
   int h;
   int warps;
   int nc;
   bool pairs;
+  bool dbuf;
 };
-constexpr PatShape kPatShapes[] = {{21, 12, 32, true}, {19, 16, 32, false}, {19, 16, 12, false}};
+constexpr PatShape kPatShapes[] = {
+    {21, 12, 24, true, true}, {19, 16, 16, false, true}, {19, 16, 12, false, false}};
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
   return kPairCountBytes + warps * nc * static_cast<int>(sizeof(PairItem));
 }
-// Zero window of the channel-pair tiles: lane 31 reads up to word 32 h + 5.
-DD_HOST_DEVICE constexpr int pair_zero_words(int h) { return (32 * h + 6 + 3) / 4 * 4; }
+
 
 constexpr size_t kRecOffset = 128;
 DD_HOST_DEVICE constexpr size_t raw_offset(int nc, int rec_bytes = static_cast<int>(sizeof(Rec))) {
@@ -168,16 +171,19 @@ inline int32_t pat_window_words(int kind, int bin, int h, int32_t span) {
   const int32_t need = 32 * h + span + (align_samples(kind, bin) - 1) + 2 * (kPatDr - 1);
   return (need + 15) / 16 * 16;
 }
-// Start of the raw buffers: 128 bytes of barriers, then the two record
-// buffers (PRec per channel, or one pair chunk per stage).
-DD_HOST_DEVICE constexpr size_t pat_raw_offset(int warps, int nc, bool pairs) {
-  return pairs ? (kRecOffset + 2 * static_cast<size_t>(pair_chunk_bytes(warps, nc)) + 127) / 128 * 128
-               : raw_offset(nc, static_cast<int>(sizeof(PRec)));
+// Start of the raw buffers: 128 bytes of barriers, then two (three with
+// double-buffered windows) record buffers of PRec per channel or one pair
+// chunk per stage.
+DD_HOST_DEVICE constexpr size_t pat_raw_offset(int warps, int nc, bool pairs, bool dbuf) {
+  return (kRecOffset +
+          (dbuf ? 3 : 2) * static_cast<size_t>(pairs ? pair_chunk_bytes(warps, nc)
+                                                     : nc * static_cast<int>(sizeof(PRec))) +
+          127) / 128 * 128;
 }
 inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp) {
-  return pat_raw_offset(s.warps, s.nc, s.pairs) +
+  return pat_raw_offset(s.warps, s.nc, s.pairs, s.dbuf) +
          2 * static_cast<size_t>(s.nc) * raw_bytes(kind, bin, lp, 32 * s.h) +
-         (static_cast<size_t>(s.nc) * lp + (s.pairs ? pair_zero_words(s.h) : 0)) * 4;
+         (s.dbuf ? 2 : 1) * static_cast<size_t>(s.nc) * lp * 4;
 }
 
 inline size_t smem_bytes(int kind, int bin, const Shape& s, int32_t lp) {

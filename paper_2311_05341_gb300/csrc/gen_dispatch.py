@@ -51,7 +51,7 @@ def macro(op, dr):
     return out
 
 
-PATTERN_H = (19, 21, 23, 25)  # odd window words per lane of the pattern tiles
+PATTERN_H = (17, 19, 21, 23, 25)  # odd window words per lane of the pattern tiles
 PATTERN_DR = 4
 
 

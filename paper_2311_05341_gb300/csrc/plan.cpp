@@ -136,9 +136,8 @@ bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const 
 // shifts s(c, d0) of every (DM block, channel) as int32, padded to 256 bytes,
 // then one chunk per (DM block, stage of ps.nc channels).  In a chunk, warp w
 // lists the stage's channels as pairs of equal pattern (entries as in
-// build_pattern_records), grouped by pattern; a channel left alone is paired
-// with the zero window.  Item word offsets a = staged channel * lp + off must
-// stay below 2^16.  Returns false if some offset or increment does not fit.
+// build_pattern_records), grouped by pattern, then the channels left alone.
+// Item word offsets a = staged channel * lp + off must stay below 2^16.  Returns false if some offset or increment does not fit.
 bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::PatShape& ps,
                        int32_t lp, std::vector<unsigned char>& out, size_t* chunk_off,
                        int32_t* n_blocks_out) {
@@ -147,8 +146,6 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
   const int32_t align = align_samples(kind, rp.r.bin);
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   const int n_st = (n_chan + ps.nc - 1) / ps.nc;
-  const uint32_t zero = static_cast<uint32_t>(ps.nc) * static_cast<uint32_t>(lp);
-  if (zero > 0xffffu) return false;
   const size_t cb = static_cast<size_t>(pair_chunk_bytes(ps.warps, ps.nc));
   const size_t bases_bytes = align_up(static_cast<size_t>(n_blocks) * n_chan * 4, 256);
   out.assign(bases_bytes + static_cast<size_t>(n_blocks) * n_st * cb, 0);
@@ -186,13 +183,14 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
         int n = 0;
         for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat) {
           const auto& v = by_pat[pat];
-          for (size_t i = 0; i < v.size(); i += 2) {
-            const uint32_t a2 = i + 1 < v.size() ? v[i + 1] : zero;
-            items[w * ps.nc + n] = PairItem{v[i] | a2 << 16, pat};
-            ++n;
-          }
+          for (size_t i = 0; i + 1 < v.size(); i += 2)
+            items[w * ps.nc + n++] = PairItem{v[i] | v[i + 1] << 16, pat};
         }
         chunk[w] = static_cast<unsigned char>(n);
+        const int n_pairs = n;
+        for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat)
+          if (by_pat[pat].size() % 2) items[w * ps.nc + n++] = PairItem{by_pat[pat].back(), pat};
+        chunk[16 + w] = static_cast<unsigned char>(n - n_pairs);
       }
     }
   }
