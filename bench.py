@@ -34,10 +34,14 @@ METRIC = "DM-trials x samples / s"
 UNIT = "DM*samples/s"
 
 
-def _workload(name):
+def _workload(name, n_samp=None):
+    import dataclasses
     from synth import workloads
-    return {"paper_u8": workloads.paper_u8, "paper_u16": workloads.paper_u16,
+    beam = {"paper_u8": workloads.paper_u8, "paper_u16": workloads.paper_u16,
             "tiny_u8": workloads.tiny_u8, "diff_f32": workloads.diff_f32}[name]()
+    if n_samp:  # a shorter observation of the same plan (profiler captures)
+        beam = dataclasses.replace(beam, n_samp=int(n_samp))
+    return beam
 
 
 def _describe(beam):
@@ -151,9 +155,12 @@ def run_ours(args):
     torch.cuda.set_device(local)
     lib = _lib.load()
 
-    beam = _workload(args.workload)
+    beam = _workload(args.workload, args.n_samp)
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype,
                    device=f"cuda:{local}")
+    if args.tile != "auto":
+        for r in range(len(beam.ranges)):
+            plan.set_tile(r, args.tile if args.tile == "pattern" else int(args.tile))
     info = plan.info(beam.n_samp)
     tables = {}
 
@@ -162,7 +169,10 @@ def run_ours(args):
             tables[r] = plan.shifts(r)
         return tables[r][d]
 
-    x_host = workloads.make_input(beam, shift_rows, info["n_dm"], info["n_out"])
+    per = 16 // np.dtype(beam.np_dtype).itemsize  # rows start 16-byte aligned
+    row_stride = (beam.n_samp + per - 1) // per * per
+    x_host = workloads.make_input(beam, shift_rows, info["n_dm"], info["n_out"],
+                                  row_stride=row_stride)
     x = torch.from_numpy(x_host).cuda()
     out = plan.empty_output(beam.n_samp)
     stream = torch.cuda.current_stream()
@@ -245,7 +255,10 @@ def run_ours(args):
         "dtype": {"u8": "int32", "u16": "int32", "f32": "f32"}[beam.dtype],
         "data": "synthetic",
         "config": {"workload": _describe(beam), "n_dm": info["n_dm_total"],
-                   "n_out": info["n_out"], "l2": "inputs larger than L2 (no flush)",
+                   "n_out": info["n_out"],
+                   "tile": ["pattern" if t == _lib.DD_TILE_PATTERN else t
+                            for t in info["tile_dms"]],
+                   "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
         "channel_adds_per_s": chan_adds * args.steps * ws / total,
         "real_time_factor": t_obs / (ms_per_step / 1e3),
@@ -481,6 +494,12 @@ def main():
     ap.add_argument("--hbm-budget-gb", type=float, default=60.0)
     ap.add_argument("--cpu-rows", type=int, default=24)
     ap.add_argument("--cpu-rows-reference", type=int, default=4)
+    ap.add_argument("--n-samp", type=int, default=None,
+                    help="raw samples per channel instead of the workload's (smaller "
+                         "cases for profiler captures)")
+    ap.add_argument("--tile", default="auto",
+                    help="register tile of every range: auto, pattern or the offset tile's "
+                         "DMs per lane (8, 6, 4, 2, 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -56,37 +56,54 @@ __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
   return sm;
 }
 
-// The generated blocks exist for the window widths gen_dispatch.py lists.
-#define DD_PAT_CASE(HH)                                  \
-  if constexpr (H == HH) {                               \
-    if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
-    else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);            \
-    return;                                              \
-  }
-
+// One channel (or a pair of channels of one pattern) into the lane's
+// accumulators: `win` (`win2`) is the shared-memory address of the lane's
+// window; the generated block of pattern `ix` loads the window words it needs
+// and adds them.  The blocks exist for the window widths gen_dispatch.py lists.
 template <int KIND, int H>
-__device__ __forceinline__ void pat_dispatch(AccT<KIND> (&acc)[kPatDr][H],
-                                             const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
-                                             uint32_t ix) {
+__device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
+                                            uint32_t ix) {
   static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pattern blocks for H");
+#define DD_PAT_CASE(HH)                                                  \
+  if constexpr (H == HH) {                                               \
+    if constexpr (KIND == kF32) DD_PATL_CHANNEL_F32_##HH(acc, win, ix);  \
+    else DD_PATL_CHANNEL_U32_##HH(acc, win, ix);                         \
+  }
   DD_PAT_CASE(17)
   DD_PAT_CASE(19)
   DD_PAT_CASE(21)
   DD_PAT_CASE(23)
   DD_PAT_CASE(25)
-}
 #undef DD_PAT_CASE
+}
+
+// The same with the window words already in registers R (H + 6 of them): the
+// loads are scheduled before the branch.  Single-channel tiles run faster so.
+template <int KIND, int H>
+__device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
+                                                 const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
+                                                 uint32_t ix) {
+#define DD_PAT_CASE(HH)                                           \
+  if constexpr (H == HH) {                                        \
+    if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
+    else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);                     \
+  }
+  DD_PAT_CASE(17)
+  DD_PAT_CASE(19)
+  DD_PAT_CASE(21)
+  DD_PAT_CASE(23)
+  DD_PAT_CASE(25)
+#undef DD_PAT_CASE
+}
 
 template <int H>
-__device__ __forceinline__ void pair_dispatch(uint32_t (&acc)[kPatDr][H],
-                                              const uint32_t (&R1)[H + 2 * (kPatDr - 1)],
-                                              const uint32_t (&R2)[H + 2 * (kPatDr - 1)],
-                                              uint32_t ix) {
+__device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t win, uint32_t win2,
+                                         uint32_t ix) {
   static_assert(H == 17 || H == 19 || H == 21, "no generated pair blocks for H");
-  if constexpr (H == 17) DD_PAT2_CHANNEL_U32_17(acc, R1, R2, ix);
-  else if constexpr (H == 19) DD_PAT2_CHANNEL_U32_19(acc, R1, R2, ix);
-  else DD_PAT2_CHANNEL_U32_21(acc, R1, R2, ix);
+  if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
+  else if constexpr (H == 19) DD_PATL2_CHANNEL_U32_19(acc, win, win2, ix);
+  else DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
 }
 
 // Pair chunk of one (DM block, stage) in global memory.
@@ -111,7 +128,6 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
   constexpr int kThreads = NW * 32;
-  constexpr int kR = H + 2 * (kPatDr - 1);
   constexpr int kPairW = 32 * H;
   constexpr int kRecBufs = DBUF ? 3 : 2;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -201,35 +217,25 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
     // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
     // PTX labels, appear once per instantiation.
-    const uint32_t* lane_pw = pwb + H * l;
     if constexpr (PAIRS) {
+      const uint32_t lane_win = smem_u32(pwb + H * l);
       const unsigned char* ck = rec_buf(rb);
       const int n_pairs = ck[w], n_items = n_pairs + ck[16 + w];
       const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
 #pragma unroll 1
       for (int k = 0; k < n_pairs; ++k) {
         const PairItem it = items[k];
-        const uint32_t* s1 = lane_pw + (it.a & 0xffffu);
-        const uint32_t* s2 = lane_pw + (it.a >> 16);
-        uint32_t R1[kR], R2[kR];
-#pragma unroll
-        for (int j = 0; j < kR; ++j) {
-          R1[j] = s1[j];
-          R2[j] = s2[j];
-        }
-        pair_dispatch<H>(acc, R1, R2, it.pat);
+        pat_pair<H>(acc, lane_win + 4u * (it.a & 0xffffu), lane_win + 4u * (it.a >> 16), it.pat);
       }
 #pragma unroll 1
       for (int k = n_pairs; k < n_items; ++k) {
         const PairItem it = items[k];
-        const uint32_t* s1 = lane_pw + it.a;
-        uint32_t R1[kR];
-#pragma unroll
-        for (int j = 0; j < kR; ++j) R1[j] = s1[j];
-        pat_dispatch<KIND, H>(acc, R1, it.pat);
+        pat_channel<KIND, H>(acc, lane_win + 4u * it.a, it.pat);
       }
     } else {
+      constexpr int kR = H + 2 * (kPatDr - 1);
       const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
+      const uint32_t* lane_pw = pwb + H * l;
 #pragma unroll 1
       for (int ch = 0; ch < nc; ++ch) {
         const uint32_t e = rs[ch].w[w];
@@ -240,7 +246,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
           if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
           else R[k] = src[k];
         }
-        pat_dispatch<KIND, H>(acc, R, e >> kPatOffBits);
+        pat_channel_regs<KIND, H>(acc, R, e >> kPatOffBits);
       }
     }
     since += nc;

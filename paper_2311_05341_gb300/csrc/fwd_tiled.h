@@ -137,7 +137,7 @@ struct PatShape {
   bool dbuf;
 };
 constexpr PatShape kPatShapes[] = {
-    {21, 12, 24, true, true}, {19, 16, 16, false, true}, {19, 16, 12, false, false}};
+    {21, 12, 24, true, true}, {19, 16, 32, false, false}, {19, 16, 12, false, false}};
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
   return kPairCountBytes + warps * nc * static_cast<int>(sizeof(PairItem));

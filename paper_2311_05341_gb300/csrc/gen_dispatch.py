@@ -92,40 +92,61 @@ def pattern_macro(op, h):
 PAIR_H = (17, 19, 21)  # window words per lane of the channel-pair pattern tiles
 
 
-def pair_macro(h):
-    """DD_PAT2_CHANNEL_U32_<H>(A, R1, R2, IX): two channels with one pattern.
+LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32")}
 
-    Like DD_PAT_CHANNEL_U32_<H> for two windows R1, R2 (h + 6 words each)
-    whose channels share the increment pattern IX: every accumulator takes
-    both samples in two consecutive adds, which the assembler can merge into
-    one three-input add.
+
+def _pattern_offsets(p):
+    inc = (p % 3, (p // 3) % 3, p // 9)
+    return [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
+
+
+def pattern_load_macro(op, h, pair):
+    """Pattern blocks that load their own window words.
+
+    DD_PATL_CHANNEL_<OP>_<H>(A, S, IX) and, for two channels of one pattern,
+    DD_PATL2_CHANNEL_U32_<H>(A, S, S2, IX): S (S2) is the shared-memory
+    address of the lane's window.  Block p loads only the h + o_3 words its
+    offsets (0, o_1, o_2, o_3) touch, then DM i adds words o_i .. o_i + h
+    into A[i][0 .. h).
     """
-    tag = f"ddq{h}"
+    instr = OPS[op][0]
+    ld, ty = LOAD[op]
+    cons = OPS[op][1]
+    tag = f"ddl{'q' if pair else op.lower()}{h}"
     nacc = PATTERN_DR * h
     win = h + 2 * (PATTERN_DR - 1)
-    lines = ['"{\\n\\t"']
+    s1 = nacc
+    s2 = nacc + 1
+    ix = nacc + (2 if pair else 1)
+    regs = f".reg {ty} t<{win}>;" + (f" .reg {ty} u<{win}>;" if pair else "")
+    lines = ['"{\\n\\t"', f'"{regs}\\n\\t"']
     targets = ", ".join(f"{tag}_p{p}" for p in range(27))
     lines.append(f'"{tag}_t: .branchtargets {targets};\\n\\t"')
-    lines.append(f'"brx.idx.uni %{nacc + 2 * win}, {tag}_t;\\n\\t"')
+    lines.append(f'"brx.idx.uni %{ix}, {tag}_t;\\n\\t"')
     for p in range(27):
-        inc = (p % 3, (p // 3) % 3, p // 9)
-        offs = [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
+        offs = _pattern_offsets(p)
         lines.append(f'"{tag}_p{p}:\\n\\t"')
+        for k in range(h + offs[3]):
+            lines.append(f'"{ld} t{k}, [%{s1}+{4 * k}];\\n\\t"')
+            if pair:
+                lines.append(f'"{ld} u{k}, [%{s2}+{4 * k}];\\n\\t"')
         for i in range(PATTERN_DR):
             for j in range(h):
                 a = i * h + j
-                lines.append(f'"add.u32 %{a}, %{a}, %{nacc + offs[i] + j};\\n\\t"')
-                lines.append(f'"add.u32 %{a}, %{a}, %{nacc + win + offs[i] + j};\\n\\t"')
+                lines.append(f'"{instr} %{a}, %{a}, t{offs[i] + j};\\n\\t"')
+                if pair:
+                    lines.append(f'"{instr} %{a}, %{a}, u{offs[i] + j};\\n\\t"')
         if p != 26:
             lines.append(f'"bra.uni {tag}_end;\\n\\t"')
     lines.append(f'"{tag}_end:\\n\\t}}"')
-    outs = ", ".join(f'"+r"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
-    ins = ", ".join(f'"r"(R1[{j}])' for j in range(win)) + ", "
-    ins += ", ".join(f'"r"(R2[{j}])' for j in range(win)) + ', "r"(IX)'
-    out = [f"#define DD_PAT2_CHANNEL_U32_{h}(A, R1, R2, IX) \\", "  asm volatile( \\"]
+    outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
+    ins = '"r"(S), "r"(S2), "r"(IX)' if pair else '"r"(S), "r"(IX)'
+    name = f"DD_PATL2_CHANNEL_U32_{h}(A, S, S2, IX)" if pair else f"DD_PATL_CHANNEL_{op}_{h}(A, S, IX)"
+    out = [f"#define {name} \\", "  asm volatile( \\"]
     out += [f"      {ln} \\" for ln in lines]
     out.append(f"      : {outs} \\")
-    out.append(f"      : {ins})")
+    out.append(f"      : {ins} \\")
+    out.append('      : "memory")')
     return out
 
 
@@ -138,8 +159,12 @@ def generate(path):
         for h in PATTERN_H:
             out += pattern_macro(op, h)
             out.append("")
+    for h in PATTERN_H:
+        for op in OPS:
+            out += pattern_load_macro(op, h, False)
+            out.append("")
     for h in PAIR_H:
-        out += pair_macro(h)
+        out += pattern_load_macro("U32", h, True)
         out.append("")
     text = "\n".join(out) + "\n"
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -188,6 +188,12 @@ struct ChannelRecs {
   __device__ void* dst(int buf) const { return sm + buf * NC; }
 };
 
+// Fire-and-forget integer add into global memory (performed at L2).
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
+
 // Transposed store tile of a register tile with H window words per lane.
 // Lane l holds positions p = H l + j (j < H); uint8 at bin 1 also holds
 // p + 32 H in the upper 16-bit halves.  The tile is read back row by row
@@ -261,6 +267,17 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
             } else {
               v[k] = OutT<KIND>(0);
             }
+          }
+          if (!first && KIND != kF32) {
+            // Later widenings of integer sums: reductions at L2 (exact, any
+            // order), so the warp does not wait for the row to come back.
+#pragma unroll
+            for (int k = 0; k < kCh; ++k) {
+              const int kk = h * kCh + k;
+              const int pos = 32 * kk + l;
+              if (kk < ST::kRows && pos < lim) red_add(row + pos, v[k]);
+            }
+            continue;
           }
           if (!first) {
             OutT<KIND> g[kCh];

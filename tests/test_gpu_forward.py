@@ -250,9 +250,9 @@ def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
         np.testing.assert_array_equal(g, o)
 
 
-@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, "pattern"),
+@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, 6),
                                        (workloads.paper_u16, 0)],
-                         ids=["paper_u8", "paper_u8_pattern", "paper_u16"])
+                         ids=["paper_u8", "paper_u8_offset6", "paper_u16"])
 def test_paper_scale_sampled(make, tile):
     beam = make()
     x, tables, n_dm, n_out = oracle_input(beam)

@@ -141,7 +141,8 @@ def test_kernel_selection():
     paper = workloads.paper_u8()
     plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
     info = plan.info(paper.n_samp)
-    assert info["kernel"] == ["tiled"] and info["tile_dms"] == [6]
+    # At most 1.23 samples of delay per DM step: the pattern tile.
+    assert info["kernel"] == ["tiled"] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
     # Bins with bin * sample bytes dividing 16 are tiled (decimation fused)
     # while their raw windows fit shared memory; other bins run on the generic
     # kernel.
@@ -177,14 +178,17 @@ def test_pattern_tile_selection():
     """The pattern tile serves plans whose per-DM shift increments are 0, 1 or 2."""
     paper = workloads.paper_u8()  # at most 1.23 samples per DM step
     plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
+    plan.set_tile(0, 6)
     ws_offset = plan.info(paper.n_samp)["workspace_bytes"]
+    assert plan.info(paper.n_samp)["tile_dms"] == [6]
     plan.set_tile(0, "pattern")
     info = plan.info(paper.n_samp)
     assert info["kernel"] == ["tiled"] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
-    # 48-byte records for 64-DM blocks against 64-byte records for 72-DM blocks.
+    # Per-warp pair lists against 64-byte offset records: other table sizes.
     assert info["workspace_bytes"] != ws_offset
-    plan.set_tile(0, 0)
-    assert plan.info(paper.n_samp)["tile_dms"] == [6]
+    plan.set_tile(0, 6)
+    plan.set_tile(0, 0)  # automatic: the pattern tile again
+    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
     tiny = workloads.tiny_u8()  # 8 samples per DM step at the lowest channel
     plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
     with pytest.raises(dd.DDError) as ei:
