@@ -100,10 +100,13 @@ __device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
 template <int H>
 __device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t win, uint32_t win2,
                                          uint32_t ix) {
-  static_assert(H == 17 || H == 19 || H == 21, "no generated pair blocks for H");
+  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+                "no generated pair blocks for H");
   if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
   else if constexpr (H == 19) DD_PATL2_CHANNEL_U32_19(acc, win, win2, ix);
-  else DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
+  else if constexpr (H == 21) DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
+  else if constexpr (H == 23) DD_PATL2_CHANNEL_U32_23(acc, win, win2, ix);
+  else DD_PATL2_CHANNEL_U32_25(acc, win, win2, ix);
 }
 
 // Pair chunk of one (DM block, stage) in global memory.

@@ -136,8 +136,11 @@ struct PatShape {
   bool pairs;
   bool dbuf;
 };
-constexpr PatShape kPatShapes[] = {
-    {21, 12, 24, true, true}, {19, 16, 32, false, false}, {19, 16, 12, false, false}};
+// The channel-pair shapes come first (integer kinds), then single-channel
+// ones; fewer channels per stage fit the wider raw windows of larger bins.
+constexpr PatShape kPatShapes[] = {{23, 16, 32, true, false}, {23, 16, 12, true, false},
+                                   {23, 16, 6, true, false},  {19, 16, 32, false, false},
+                                   {19, 16, 12, false, false}, {19, 16, 6, false, false}};
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
   return kPairCountBytes + warps * nc * static_cast<int>(sizeof(PairItem));

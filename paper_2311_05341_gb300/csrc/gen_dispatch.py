@@ -89,7 +89,10 @@ def pattern_macro(op, h):
     return out
 
 
-PAIR_H = (17, 19, 21)  # window words per lane of the channel-pair pattern tiles
+PAIR_H = (17, 19, 21, 23, 25)  # window words per lane of the channel-pair pattern tiles
+# In-block loads run this many words ahead of the adds that consume them, so a
+# word's register dies after its last use (None: all loads first).
+LOAD_AHEAD = 4
 
 
 LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32")}
@@ -125,17 +128,35 @@ def pattern_load_macro(op, h, pair):
     lines.append(f'"brx.idx.uni %{ix}, {tag}_t;\\n\\t"')
     for p in range(27):
         offs = _pattern_offsets(p)
+        n = h + offs[3]
         lines.append(f'"{tag}_p{p}:\\n\\t"')
-        for k in range(h + offs[3]):
+
+        def load(k):
             lines.append(f'"{ld} t{k}, [%{s1}+{4 * k}];\\n\\t"')
             if pair:
                 lines.append(f'"{ld} u{k}, [%{s2}+{4 * k}];\\n\\t"')
-        for i in range(PATTERN_DR):
-            for j in range(h):
-                a = i * h + j
-                lines.append(f'"{instr} %{a}, %{a}, t{offs[i] + j};\\n\\t"')
-                if pair:
-                    lines.append(f'"{instr} %{a}, %{a}, u{offs[i] + j};\\n\\t"')
+
+        def add(i, j):
+            a = i * h + j
+            lines.append(f'"{instr} %{a}, %{a}, t{offs[i] + j};\\n\\t"')
+            if pair:
+                lines.append(f'"{instr} %{a}, %{a}, u{offs[i] + j};\\n\\t"')
+
+        if LOAD_AHEAD is None:
+            for k in range(n):
+                load(k)
+            for i in range(PATTERN_DR):
+                for j in range(h):
+                    add(i, j)
+        else:
+            for k in range(min(LOAD_AHEAD, n)):
+                load(k)
+            for k in range(n):  # adds consuming word k, then the next load
+                for i in range(PATTERN_DR):
+                    if 0 <= k - offs[i] < h:
+                        add(i, k - offs[i])
+                if k + LOAD_AHEAD < n:
+                    load(k + LOAD_AHEAD)
         if p != 26:
             lines.append(f'"bra.uni {tag}_end;\\n\\t"')
     lines.append(f'"{tag}_end:\\n\\t}}"')
