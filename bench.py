@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "DM-trials x samples / s"
+SM_MAX_MHZ = 2070.0   # GB300 maximum SM clock
+HBM_GBS = 6644.1      # measured copy bandwidth of the GB300s
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu), keyed by
+# workload, raw samples and tile; valid only for the kernel build it was taken
+# on (profiles/fwd_pattern_u8_8192ch.md).
+TRAFFIC = {("paper_u8", 262144, (0x104,)): 10.80e9 + 68.03e9}
 UNIT = "DM*samples/s"
 
 
@@ -57,6 +63,20 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def replica_throughput(units: float, seconds: float, device) -> tuple:
+    """Whole-job throughput of independent replicas: every rank processed
+    `units` in `seconds`; the job took the slowest rank's time, so value =
+    world_size * units / max(seconds).  Returns (value, max seconds)."""
+    import torch
+    ws = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        t = torch.tensor([seconds], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        seconds = float(t.item())
+    return units * ws / seconds, seconds
 
 
 class ClockSampler:
@@ -204,13 +224,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
-    total = sum(per)
-    if ws > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    value, total = replica_throughput(dm_samples * args.steps, sum(per), "cuda")
     ms_per_step = total / args.steps * 1e3
-    value = dm_samples * args.steps * ws / total
 
     # End to end through the C ABI: pinned host in -> device -> pinned host out.
     e2e = None
@@ -235,17 +250,30 @@ def run_ours(args):
     peaks = measure_alu_peak(torch, lib)
     if rank != 0:
         return
-    # Roofline of the dominant (only) kernel: sample-adds per launch / mean launch time.
+    # Roofline of the dominant (only) kernel: sample-adds per launch / mean launch time,
+    # against the add rate derived from the SM's integer units and clock (a
+    # three-input add retires on the 16-lane integer pipe of each of the 4 SM
+    # sub-partitions; float adds on both 16-lane float pipes).
     sample_adds_per_s = chan_adds / (total / args.steps)
+    sms = peaks["sm_count"]
     per_lane = {"u8": 4, "u16": 2, "f32": 1}[beam.dtype]
-    peak_adds = peaks["iadd3"] * per_lane if beam.dtype != "f32" else peaks["fadd"]
+    lanes = 128 if beam.dtype == "f32" else 64  # lane-ops per clock per SM
+    peak_adds = lanes * sms * SM_MAX_MHZ * 1e6 * per_lane
+    algo_bytes = (beam.n_chan * beam.n_samp * np.dtype(beam.np_dtype).itemsize
+                  + info["out_elems"] * 4)
+    traffic = TRAFFIC.get((args.workload, beam.n_samp, tuple(info["tile_dms"])))
     roofline = {
         "bound": "alu", "achieved": sample_adds_per_s / 1e12, "peak": peak_adds / 1e12,
-        "unit": "Tadd/s", "frac": sample_adds_per_s / peak_adds, "traffic": None,
-        "peak_source": ("measured 3-input int32 add rate x %d sample-adds per lane-op "
-                        "(16-bit packed lanes)" % per_lane) if beam.dtype != "f32"
-        else "measured float32 add rate",
+        "unit": "Tadd/s", "frac": sample_adds_per_s / peak_adds,
+        "traffic": traffic,
+        "peak_source": ("%d lane-ops/clk/SM x %d SMs x %g MHz x %d sample-adds per lane-op"
+                        % (lanes, sms, SM_MAX_MHZ, per_lane)),
         "alu_microbench": {k: v for k, v in peaks.items()},
+        "frac_of_microbench": sample_adds_per_s / (
+            peaks["iadd3"] * per_lane if beam.dtype != "f32" else peaks["fadd"]),
+        "hbm": {"algorithmic_bytes": algo_bytes,
+                "achieved_gbs": algo_bytes / (total / args.steps) / 1e9,
+                "frac_of_measured": algo_bytes / (total / args.steps) / 1e9 / HBM_GBS},
     }
     t_obs = beam.n_samp * beam.t_samp
     line = {
@@ -492,7 +520,7 @@ def main():
     ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
     ap.add_argument("--stream-seconds", type=float, default=15.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=60.0)
-    ap.add_argument("--cpu-rows", type=int, default=24)
+    ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-rows-reference", type=int, default=4)
     ap.add_argument("--n-samp", type=int, default=None,
                     help="raw samples per channel instead of the workload's (smaller "
