@@ -126,7 +126,7 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 // so the copies of stage st + 2 (raw buffer st % 2, record buffer
 // (st + 2) % 3) and the unpacking of stage st + 1 may start while warps still
 // compute stage st.  Without DBUF a second barrier ends each stage.
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
@@ -235,7 +235,9 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
         const PairItem it = items[k];
         pat_channel<KIND, H>(acc, lane_win + 4u * it.a, it.pat);
       }
-    } else {
+    } else if constexpr (AMAX <= 1) {
+      // Base increments 0 and 1 only: the lane's H + 6 window words are loaded
+      // before the branch.
       constexpr int kR = H + 2 * (kPatDr - 1);
       const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
       const uint32_t* lane_pw = pwb + H * l;
@@ -250,6 +252,15 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
           else R[k] = src[k];
         }
         pat_channel_regs<KIND, H>(acc, R, e >> kPatOffBits);
+      }
+    } else {
+      const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
+      const uint32_t lane_win = smem_u32(pwb + H * l);
+#pragma unroll 1
+      for (int ch = 0; ch < nc; ++ch) {
+        const uint32_t e = rs[ch].w[w];
+        pat_channel<KIND, H>(acc, lane_win + 4u * (ch * p.lp + (e & kPatOffMask)),
+                             e >> kPatOffBits);
       }
     }
     since += nc;
@@ -272,7 +283,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
 }  // namespace
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF>(smem, p.lraw);
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pat_body<KIND, H, NW, NC, PAIRS, DBUF>(p, sm, blockIdx.x % p.n_blocks,
+  pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blockIdx.x % p.n_blocks,
                                          blockIdx.x / p.n_blocks);
 }
 
@@ -290,11 +301,11 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
 
 namespace {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   const size_t smem =
-      tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF}, prm.lp);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF>;
+      tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX}, prm.lp);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -305,10 +316,11 @@ int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t s
 template <int KIND, int I>
 int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   constexpr tk::PatShape s = tk::kPatShapes[I];
-  if constexpr (s.pairs && KIND == tk::kF32) {
-    return static_cast<int>(cudaErrorInvalidValue);  // the planner never pairs float channels
+  if constexpr (!tk::pat_shape_serves(s, KIND)) {
+    return static_cast<int>(cudaErrorInvalidValue);  // the planner never picks it
   } else {
-    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf>(prm, grid, st);
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(prm, grid,
+                                                                                  st);
   }
 }
 

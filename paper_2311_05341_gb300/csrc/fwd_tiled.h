@@ -93,13 +93,15 @@ struct Rec {
 static_assert(sizeof(Rec) == 64, "Rec must stay 64 bytes");
 
 // Pattern tiles (fwd_pattern.cu): every lane owns kPatDr consecutive DMs x H
-// window words, H odd.  When the shift of every channel grows by 0, 1 or 2
-// from one trial DM to the next, the offsets of a warp's DMs relative to its
-// first DM are (0, i1, i1 + i2, i1 + i2 + i3) with i_k in {0, 1, 2}: one of
-// kPatterns patterns, numbered i1 + 3 i2 + 9 i3.
+// window words, H odd.  From one trial DM to the next the shift of channel c
+// grows by the floor or the ceiling of step k_c / (bin t_samp) (Eq. 1 is
+// linear in DM), so the increments i1, i2, i3 between a warp's four DMs are
+// a or a + 1 for a = min(i1, i2, i3).  With a < kPatBases the offsets of the
+// four DMs from the first, (0, i1, i1 + i2, i1 + i2 + i3), are one of
+// kPatterns patterns, numbered 8 a + (i1 - a) + 2 (i2 - a) + 4 (i3 - a).
 constexpr int kPatDr = 4;
-constexpr int kPatterns = 27;
-constexpr int kPatMaxInc = 2;
+constexpr int kPatBases = 4;
+constexpr int kPatterns = 8 * kPatBases;
 constexpr int kPatMaxWarps = 16;
 constexpr int kPatOffBits = 11;      // window offset field of a pattern record entry
 constexpr uint32_t kPatOffMask = (1u << kPatOffBits) - 1;
@@ -127,20 +129,28 @@ struct PairItem {
 static_assert(sizeof(PairItem) == 8, "PairItem must stay 8 bytes");
 
 // Pattern tile shapes: window words per lane (odd), warps per CTA, channels
-// per pipeline stage, channel pairs (integer kinds only), double-buffered
-// window words (one barrier per stage).
+// per pipeline stage, channel pairs (integer kinds) or single channels (float
+// kind), double-buffered window words (one barrier per stage), and the
+// largest base increment a served.  Single-channel shapes with amax 1 load
+// the lane's H + 6 window words before the pattern branch; the others load
+// inside each pattern's block only the words its offsets touch.
 struct PatShape {
   int h;
   int warps;
   int nc;
   bool pairs;
   bool dbuf;
+  int amax;
 };
-// The channel-pair shapes come first (integer kinds), then single-channel
-// ones; fewer channels per stage fit the wider raw windows of larger bins.
-constexpr PatShape kPatShapes[] = {{23, 16, 32, true, false}, {23, 16, 12, true, false},
-                                   {23, 16, 6, true, false},  {19, 16, 32, false, false},
-                                   {19, 16, 12, false, false}, {19, 16, 6, false, false}};
+// Fewer channels per stage fit the wider raw windows of larger bins.
+constexpr PatShape kPatShapes[] = {
+    {23, 16, 32, true, false, 3},  {23, 16, 12, true, false, 3}, {23, 16, 6, true, false, 3},
+    {19, 16, 32, false, false, 1}, {19, 16, 12, false, false, 1}, {19, 16, 6, false, false, 1},
+    {19, 16, 12, false, false, 3}, {19, 16, 6, false, false, 3}};
+// The shape serves a kind: pairs take integer window words, single channels float.
+DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
+  return s.pairs == (kind != kF32);
+}
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
   return kPairCountBytes + warps * nc * static_cast<int>(sizeof(PairItem));
@@ -170,8 +180,10 @@ DD_HOST_DEVICE constexpr int pat_tile_samples(int kind, int h) {
   return 32 * h * samples_per_word(kind);
 }
 inline int32_t pat_window_words(int kind, int bin, int h, int32_t span) {
-  // Lane 31 reads words up to 31h + (span + align - 1) + (h + 2 (kPatDr - 1)) - 1.
-  const int32_t need = 32 * h + span + (align_samples(kind, bin) - 1) + 2 * (kPatDr - 1);
+  // A lane reads at most h + 6 words from its first DM's offset (the loads
+  // before the branch) or, inside a pattern block, up to its last DM's shift
+  // plus h: lane 31 stays below 31h + (span + align - 1) + h + 6.
+  const int32_t need = 32 * h + span + (align_samples(kind, bin) - 1) + 6;
   return (need + 15) / 16 * 16;
 }
 // Start of the raw buffers: 128 bytes of barriers, then two (three with

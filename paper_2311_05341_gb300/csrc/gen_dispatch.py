@@ -58,26 +58,26 @@ PATTERN_DR = 4
 def pattern_macro(op, h):
     """DD_PAT_CHANNEL_<OP>_<H>(A, R, IX): 4 DMs of one lane, one indexed branch.
 
-    DM 0 adds R[0 .. h), DM i adds R[o_i .. o_i + h) with o_i the sum of the
-    first i increments; the 27 targets enumerate the increments (inc1, inc2,
-    inc3) in {0, 1, 2}^3 as IX = inc1 + 3 inc2 + 9 inc3.  R holds h + 6 words.
+    R holds the lane's h + 6 window words, loaded before the branch; block IX
+    (a pattern with base increment a <= 1, see _pattern_offsets) adds
+    R[o_i .. o_i + h) into A[i][0 .. h) for the four DMs i.
     """
     instr, cons = OPS[op]
     tag = f"ddp{op.lower()}{h}"
     nacc = PATTERN_DR * h
     win = h + 2 * (PATTERN_DR - 1)
+    npat = 16
     lines = ['"{\\n\\t"']
-    targets = ", ".join(f"{tag}_p{p}" for p in range(27))
+    targets = ", ".join(f"{tag}_p{p}" for p in range(npat))
     lines.append(f'"{tag}_t: .branchtargets {targets};\\n\\t"')
     lines.append(f'"brx.idx.uni %{nacc + win}, {tag}_t;\\n\\t"')
-    for p in range(27):
-        inc = (p % 3, (p // 3) % 3, p // 9)
-        offs = [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
+    for p in range(npat):
+        offs = _pattern_offsets(p)
         lines.append(f'"{tag}_p{p}:\\n\\t"')
         for i in range(PATTERN_DR):
             for j in range(h):
                 lines.append(f'"{instr} %{i * h + j}, %{i * h + j}, %{nacc + offs[i] + j};\\n\\t"')
-        if p != 26:
+        if p != npat - 1:
             lines.append(f'"bra.uni {tag}_end;\\n\\t"')
     lines.append(f'"{tag}_end:\\n\\t}}"')
     outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
@@ -98,8 +98,14 @@ LOAD_AHEAD = 4
 LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32")}
 
 
+PATTERNS = 32  # 8 base increments a = 0..3 x the 8 patterns of +0/+1 on top
+
+
 def _pattern_offsets(p):
-    inc = (p % 3, (p // 3) % 3, p // 9)
+    """Offsets of a warp's 4 DMs for pattern p = 8 a + b: increment k is
+    a + bit k of b."""
+    a, b = divmod(p, 8)
+    inc = [a + ((b >> k) & 1) for k in range(3)]
     return [0, inc[0], inc[0] + inc[1], inc[0] + inc[1] + inc[2]]
 
 
@@ -117,16 +123,16 @@ def pattern_load_macro(op, h, pair):
     cons = OPS[op][1]
     tag = f"ddl{'q' if pair else op.lower()}{h}"
     nacc = PATTERN_DR * h
-    win = h + 2 * (PATTERN_DR - 1)
+    win = h + max(_pattern_offsets(p)[3] for p in range(PATTERNS))
     s1 = nacc
     s2 = nacc + 1
     ix = nacc + (2 if pair else 1)
     regs = f".reg {ty} t<{win}>;" + (f" .reg {ty} u<{win}>;" if pair else "")
     lines = ['"{\\n\\t"', f'"{regs}\\n\\t"']
-    targets = ", ".join(f"{tag}_p{p}" for p in range(27))
+    targets = ", ".join(f"{tag}_p{p}" for p in range(PATTERNS))
     lines.append(f'"{tag}_t: .branchtargets {targets};\\n\\t"')
     lines.append(f'"brx.idx.uni %{ix}, {tag}_t;\\n\\t"')
-    for p in range(27):
+    for p in range(PATTERNS):
         offs = _pattern_offsets(p)
         n = h + offs[3]
         lines.append(f'"{tag}_p{p}:\\n\\t"')
@@ -157,7 +163,7 @@ def pattern_load_macro(op, h, pair):
                         add(i, k - offs[i])
                 if k + LOAD_AHEAD < n:
                     load(k + LOAD_AHEAD)
-        if p != 26:
+        if p != PATTERNS - 1:
             lines.append(f'"bra.uni {tag}_end;\\n\\t"')
     lines.append(f'"{tag}_end:\\n\\t}}"')
     outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))

@@ -88,13 +88,38 @@ bool build_tile_records(const RangePlan& rp, int32_t n_chan, int kind, const tk:
   return true;
 }
 
+// Pattern number of the increments i_k = s(c, d_k) - s(c, d_{k-1}) (k = 1..3)
+// of a warp's DMs d_0..d_3, of which the first n_real are trial DMs of the
+// range: 8 a + sum_k (i_k - a) 2^(k-1), a = min_k i_k.  False unless every
+// i_k is a or a + 1 and 0 <= a <= amax.  DMs past the end of the range are
+// never stored: they take increment a (at most 6 samples past the last DM,
+// inside the window's slack).
+bool pattern_of(const int32_t* s_dm, int n_real, int amax, uint32_t* pat) {
+  using tk::kPatDr;
+  *pat = 0;
+  if (n_real <= 1) return true;
+  int32_t inc[kPatDr - 1];
+  int32_t a = s_dm[1] - s_dm[0];
+  for (int k = 1; k < n_real; ++k) {
+    inc[k - 1] = s_dm[k] - s_dm[k - 1];
+    a = std::min(a, inc[k - 1]);
+  }
+  if (a < 0 || a > amax) return false;
+  uint32_t bits = 0;
+  for (int k = 0; k + 1 < n_real; ++k) {
+    if (inc[k] - a > 1) return false;
+    bits |= static_cast<uint32_t>(inc[k] - a) << k;
+  }
+  *pat = 8u * static_cast<uint32_t>(a) + bits;
+  return true;
+}
+
 // Records of the pattern kernel for shape ps (kPatDr DMs per lane, ps.warps
 // warps).  For DM block b (first DM d0), channel c and warp w (DMs
-// d0 + kPatDr w + i, clamped to the last DM):
+// d_i = d0 + kPatDr w + i, clamped to the last DM):
 //   base = s(c, d0),  m = base mod A (as for the offset tiles),
-//   off  = s(c, d0 + kPatDr w) - base + m     (window offset, kPatOffBits bits),
-//   i_k  = s(c, d_k) - s(c, d_{k-1})            (k = 1..3, each in 0..kPatMaxInc),
-//   entry = off | (i_1 + 3 i_2 + 9 i_3) << kPatOffBits.
+//   off  = s(c, d_0) - base + m     (window offset, kPatOffBits bits),
+//   entry = off | pattern_of(s(c, d_0..d_3)) << kPatOffBits.
 // Returns false if some offset or increment does not fit.
 bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const tk::PatShape& ps,
                            std::vector<tk::PRec>& recs, int32_t* n_blocks_out) {
@@ -118,12 +143,11 @@ bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const 
         const int64_t dw = d0 + static_cast<int64_t>(kPatDr) * w;
         const int32_t off = shift(dw, c) - base + m;
         if (off < 0 || off > static_cast<int32_t>(kPatOffMask)) return false;
-        uint32_t pat = 0, weight = 1;
-        for (int i = 1; i < kPatDr; ++i, weight *= 3) {
-          const int32_t inc = shift(dw + i, c) - shift(dw + i - 1, c);
-          if (inc < 0 || inc > kPatMaxInc) return false;
-          pat += weight * static_cast<uint32_t>(inc);
-        }
+        int32_t s_dm[kPatDr];
+        for (int i = 0; i < kPatDr; ++i) s_dm[i] = shift(dw + i, c);
+        const int n_real = static_cast<int>(std::min<int64_t>(kPatDr, rp.n_dm - dw));
+        uint32_t pat = 0;
+        if (!pattern_of(s_dm, n_real, ps.amax, &pat)) return false;
         r.w[w] = static_cast<uint16_t>(static_cast<uint32_t>(off) | pat << kPatOffBits);
       }
     }
@@ -170,12 +194,11 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
           const int32_t base = bases[c];
           const int32_t off = shift(dw, c) - base + base % align;
           if (off < 0 || off > static_cast<int32_t>(kPatOffMask)) return false;
-          uint32_t pat = 0, weight = 1;
-          for (int i = 1; i < kPatDr; ++i, weight *= 3) {
-            const int32_t inc = shift(dw + i, c) - shift(dw + i - 1, c);
-            if (inc < 0 || inc > kPatMaxInc) return false;
-            pat += weight * static_cast<uint32_t>(inc);
-          }
+          int32_t s_dm[kPatDr];
+          for (int i = 0; i < kPatDr; ++i) s_dm[i] = shift(dw + i, c);
+          const int n_real = static_cast<int>(std::min<int64_t>(kPatDr, rp.n_dm - dw));
+          uint32_t pat = 0;
+          if (!pattern_of(s_dm, n_real, ps.amax, &pat)) return false;
           const uint32_t a = static_cast<uint32_t>(k) * lp + static_cast<uint32_t>(off);
           if (a > 0xffffu) return false;
           by_pat[pat].push_back(a);
@@ -252,6 +275,7 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
 // Try one pattern shape (index `shape` of tk::kPatShapes).
 bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   const tk::PatShape& ps = tk::kPatShapes[shape];
+  if (!tk::pat_shape_serves(ps, kind)) return false;
   const int32_t span = block_span(rp, n_chan, tk::kPatDr * ps.warps);
   const int32_t lp = tk::pat_window_words(kind, rp.r.bin, ps.h, span);
   if (tk::pat_smem_bytes(kind, rp.r.bin, ps, lp) > 227 * 1024) return false;
@@ -264,7 +288,6 @@ bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   int32_t n_blocks = 0;
   size_t chunk_off = 0;
   if (ps.pairs) {
-    if (kind == tk::kF32) return false;  // a float add takes two inputs only
     if (!build_pair_tables(rp, n_chan, kind, ps, lp, tables, &chunk_off, &n_blocks)) return false;
   } else {
     std::vector<tk::PRec> recs;

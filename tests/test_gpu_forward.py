@@ -147,6 +147,37 @@ def test_tiled_full_planes_every_shape(dtype, seed):
             np.testing.assert_array_equal(got, ref[0], err_msg=f"tile {dms}")
 
 
+@pytest.mark.parametrize("dtype,seed", [("u8", s) for s in range(6)] +
+                         [("u16", s) for s in range(4)] + [("f32", s) for s in range(4)])
+def test_pattern_steep_plans(dtype, seed):
+    """Pattern tile on plans with 1.7 to 3.9 samples of delay per DM step (base
+    increments 1 to 3), against the oracle and the 1-DM offset tile."""
+    rng = np.random.default_rng(7000 + seed)
+    n_chan = int(rng.choice([15, 96, 257, 300]))
+    f_high = float(rng.uniform(800, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / 64e-6
+    step = float(rng.uniform(1.7, 3.9)) / k_low
+    n_dm = int(rng.choice([5, 64, 67, 129]))
+    r = (float(rng.uniform(0, 20)) * step, 0.0, step, 1)
+    r = (r[0], r[0] + n_dm * step, step, 1)
+    s_max, _ = oracle.extent(freqs, f_high, 64e-6, r, 10 ** 9)
+    n_samp = int(s_max + rng.choice([1, 735, 1472, 3001]))
+    npdt, mean, sd = _NOISE[dtype]
+    x = filterbank(npdt, n_chan, n_samp, 7100 + seed, mean, sd)
+    ref = oracle.forward(x, freqs, f_high, 64e-6, [r])[0]
+    ref_abs = oracle.forward(x, freqs, f_high, 64e-6, [r], take_abs=True)[0]
+    xd = padded_device(x)
+    for tile in ("pattern", 1):
+        plan = dd.Plan(freqs, f_high, 64e-6, [r], dtype)
+        plan.set_tile(0, tile)
+        got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
+        if dtype == "f32":
+            assert_float_parity(got, ref, ref_abs, f"tile {tile}")
+        else:
+            np.testing.assert_array_equal(got, ref, err_msg=f"tile {tile}")
+
+
 @pytest.mark.parametrize("dtype,b", [("u8", 2), ("u8", 4), ("u8", 8), ("u16", 2), ("u16", 4),
                                      ("f32", 2)])
 def test_tiled_decimation_every_shape(dtype, b):

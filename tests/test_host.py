@@ -166,8 +166,13 @@ def test_kernel_selection():
     f32 = workloads.diff_f32()
     plan = dd.Plan(f32.freqs, f32.f_high, f32.t_samp, f32.ranges, "f32", upload=False)
     assert plan.info(f32.n_samp)["kernel"] == ["tiled"]
-    u16 = workloads.batched()[24]  # 2.9 samples of delay per DM step
+    # 2.9 samples of delay per DM step: increments 2 or 3, base increment 2 of
+    # the pattern tile (0..3).
+    u16 = workloads.batched()[24]
     plan = dd.Plan(u16.freqs, u16.f_high, u16.t_samp, u16.ranges, "u16", upload=False)
+    assert plan.info(u16.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
+    plan.set_tile(0, 0)
+    plan.set_tile(0, 4)
     assert plan.info(u16.n_samp)["tile_dms"] == [4]
     fb = workloads.batched()[32]  # 12.3 samples of delay per DM step
     plan = dd.Plan(fb.freqs, fb.f_high, fb.t_samp, fb.ranges, "f32", upload=False)
