@@ -356,8 +356,9 @@ def run_reference(args):
 
 
 def run_batched(args):
-    """Config 3: 24 u8 + 8 u16 + 4 f32 beams, one persistent launch (CUDA graph)
-    against the plain path (one dd_run per beam, each plan's own best tile)."""
+    """Config 3: 24 u8 + 8 u16 + 4 f32 beams, persistent launches (one per tile
+    family, CUDA graph) against the plain path (one dd_run per beam, each
+    plan's automatic tile)."""
     import torch
     import paper_2311_05341_gb300 as dd
     from paper_2311_05341_gb300 import batch as ddb
@@ -411,12 +412,13 @@ def run_batched(args):
                                "8 x u16 4096 ch x 65536 at 54.6 us (3072 DMs step 0.2), "
                                "4 x f32 336 ch x 32768 at 327.68 us (1024 DMs step 0.2)",
                    "beams": len(beams), "work_items": runner.n_items,
-                   "tiles_dms_per_lane": runner.shapes[0] + runner.shapes[24] + runner.shapes[32]},
+                   "tiles": runner.shapes[0] + runner.shapes[24] + runner.shapes[32]},
         "channel_adds_per_s": adds / t_batch,
         "plain_per_beam": {"value": units / t_plain, "ms_per_step": t_plain * 1e3},
         "batched_over_plain": t_plain / t_batch,
         "outputs_identical_to_plain": bool(same),
-        "gpu_launches": 1, "clocks": clk,
+        "gpu_launches": args.steps * runner.n_launches,
+        "clocks": clk,
     }
     print(json.dumps(line))
 
@@ -519,7 +521,7 @@ def main():
                     choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32", "batched", "stream"])
     ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
     ap.add_argument("--stream-seconds", type=float, default=15.0)
-    ap.add_argument("--hbm-budget-gb", type=float, default=60.0)
+    ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-rows-reference", type=int, default=4)
     ap.add_argument("--n-samp", type=int, default=None,

@@ -222,19 +222,20 @@ dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t in_row_strid
 
 /* ---------------------------------------------------------------------------
  * Persistent batches: many beams (plans of different channel counts, dtypes,
- * sampling times and DM plans) dedispersed by ONE persistent launch of the
- * tiled kernel, whose CTAs take (beam range, DM block, time tile) work items
+ * sampling times and DM plans) dedispersed by persistent launches of the
+ * tiled kernels -- one for the ranges on the pattern tile, one for those on
+ * offset tiles -- whose CTAs take (beam range, DM block, time tile) work items
  * from a device counter, longest items first.  The paper tunes its tile
- * parameters per telescope and plan (Sec. 4.1); here each plan's tile shape
- * is chosen before the batch is built (dd_plan_set_tile), so the batch mixes
- * shapes.  The batch keeps pointers to its plans, which must outlive it and
+ * parameters per telescope and plan (Sec. 4.1); here each plan's tile is
+ * chosen before the batch is built (dd_plan_set_tile), so the batch mixes
+ * tiles.  The batch keeps pointers to its plans, which must outlive it and
  * stay uploaded.  Device memory is the caller's (dd_batch_workspace_bytes).
  * ------------------------------------------------------------------------- */
 typedef struct dd_batch_s* dd_batch;
 
-/* Build the work list for n_plans plans and their raw sample counts.  Every
- * range must be on the tiled kernel with 4, 2 or 1 DMs per lane, else
- * DD_ERR_UNSUPPORTED; DD_ERR_BUDGET if the plans' windows together exceed the
+/* Build the work lists for n_plans plans and their raw sample counts.  Every
+ * range must be on the tiled kernel, on the pattern tile or an offset tile
+ * with 4, 2 or 1 DMs per lane, else DD_ERR_UNSUPPORTED; DD_ERR_BUDGET if the plans' windows together exceed the
  * persistent kernel's shared memory; DD_ERR_SHAPE if an input is shorter than
  * a range's maximum delay. */
 dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n_plans,
@@ -244,6 +245,9 @@ dd_status dd_batch_destroy(dd_batch batch);
 dd_status dd_batch_workspace_bytes(dd_batch batch, size_t* bytes);
 /* Number of work items and jobs (plan ranges) of the batch. */
 dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs);
+/* Kernel launches one dd_batch_run makes (one per pattern-tile variant present,
+ * plus one if any range is on an offset tile). */
+dd_status dd_batch_launches(dd_batch batch, int32_t* n_launches);
 /* Copy the work list into caller device memory (256-byte aligned, >= the
  * workspace bytes) and bind it; synchronises `stream`. */
 dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void* stream);
@@ -252,8 +256,9 @@ dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void*
  * synchronises `stream`.  Rebind whenever a buffer address changes. */
 dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
                         void* const* d_out, void* stream);
-/* One persistent launch over all items of a bound batch (a counter reset and a
- * kernel launch on `stream`; both can be captured in a CUDA graph). */
+/* Persistent launches over all items of a bound batch (a counter reset and one
+ * kernel launch per tile family present, in order on `stream`; all can be
+ * captured in a CUDA graph). */
 dd_status dd_batch_run(dd_batch batch, void* stream);
 /* DD_ERR_TIMEOUT if a bounded device wait of any batch plan gave up since the
  * last check (clears the flags); synchronises `stream`. */

@@ -71,6 +71,7 @@ SIGNATURES = {
     "dd_batch_destroy": (ctypes.c_int, [_VP]),
     "dd_batch_workspace_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_SZ)]),
     "dd_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
+    "dd_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "dd_batch_upload": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "dd_batch_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I64),
                                      ctypes.POINTER(_VP), _VP]),

@@ -1,12 +1,13 @@
 """Batched dedispersion of many beams in one persistent launch (dd_batch_*).
 
 Beams may differ in channel count, dtype, sampling time and DM plan.  Each
-beam's plan gets a tile shape (DMs per lane of the register tile) chosen by
-the autotuner, which times the feasible shapes on the beam's own shapes and
-caches the winner by plan signature -- the per-telescope tuning of the paper's
-tile parameters (Sec. 4.1) done automatically.  The batch then runs as one
-persistent launch over a (beam range, DM block, time tile) work list,
-optionally captured once in a CUDA graph and replayed.
+beam's plan gets a register tile (the pattern tile, or the offset tile with
+4, 2 or 1 DMs per lane) chosen by the autotuner, which times the feasible
+tiles on the beam's own shapes and caches the winner by plan signature -- the
+per-telescope tuning of the paper's tile parameters (Sec. 4.1) done
+automatically.  The batch then runs as persistent launches (one per tile
+family) over (beam range, DM block, time tile) work lists, optionally
+captured once in a CUDA graph and replayed.
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ import numpy as np
 from . import Plan, _lib
 from ._lib import check
 
-BATCH_SHAPES = (4, 2, 1)  # DMs per lane the persistent kernel serves
+BATCH_SHAPES = ("pattern", 4, 2, 1)  # tiles the persistent kernels serve
 
 
 @dataclass
@@ -168,6 +169,9 @@ class BatchRunner:
         n_items, n_jobs = ctypes.c_int64(), ctypes.c_int32()
         check(lib.dd_batch_info(h, ctypes.byref(n_items), ctypes.byref(n_jobs)))
         self.n_items, self.n_jobs = n_items.value, n_jobs.value
+        n_launch = ctypes.c_int32()
+        check(lib.dd_batch_launches(h, ctypes.byref(n_launch)))
+        self.n_launches = n_launch.value  # kernel launches per run
         self.graph = None
         if graph:
             self._capture()

@@ -1,13 +1,16 @@
 // batch.cu -- C ABI of the persistent batch runtime (include/dd.h, dd_batch_*).
 //
 // Many beams -- plans of different channel counts, dtypes, sampling times and
-// DM plans -- are dedispersed by one persistent launch of the tiled kernel
-// (fwd_tiled.cu): its CTAs take (job, DM block, time tile) items from a
-// device counter until the list is exhausted.  Items are ordered longest
-// first (largest channel count x tile work), DM blocks of a time tile
-// consecutive so their shared input window stays in L2.  dd_batch_bind
-// uploads the per-job pointers once; dd_batch_run is then a counter reset and
-// one launch, which a CUDA graph can capture and replay.
+// DM plans -- are dedispersed by persistent launches whose CTAs take (job, DM
+// block, time tile) items from a device counter until the list is exhausted:
+// one launch of the pattern-tile kernel (fwd_pattern_batch.cu) for the ranges
+// on pattern tiles and one of the offset-tile kernel (fwd_tiled.cu) for the
+// others (the two register footprints differ: 16 warps x 128 registers
+// against 12 x 168).  Items are ordered longest first (largest channel count
+// x tile work), DM blocks of a time tile consecutive so their shared input
+// window stays in L2.  dd_batch_bind uploads the per-job pointers once;
+// dd_batch_run is then a counter reset and up to two launches, which a CUDA
+// graph can capture and replay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,13 +30,26 @@ struct dd_batch_s {
     int32_t range;
     int64_t n_out;
     int64_t out_offset;  // elements into the plan's output
+    bool pattern;        // on a pattern tile (else an offset tile)
+    int32_t index;       // job number within its family
   };
   std::vector<JobRef> jobs;
-  std::vector<dd::tk::BatchItem> items;
+  std::vector<dd::tk::BatchItem> items;    // offset-tile family
   std::vector<dd::tk::BatchJob> host_jobs;
+  std::vector<dd::tk::PatBatchJob> host_pjobs;
+  // Pattern-tile jobs grouped by variant (kind, shape): one launch each.
+  struct PatGroup {
+    int32_t kind;
+    int32_t shape;
+    size_t smem = 0;
+    size_t off_items = 0;
+    std::vector<dd::tk::BatchItem> items;
+  };
+  std::vector<PatGroup> groups;
+  std::vector<int32_t> pjob_group;  // group of each pattern job
   int32_t max_lraw = 0;
   int32_t max_lp = 0;
-  size_t off_jobs = 0, off_items = 0, ws_bytes = 0;
+  size_t off_jobs = 0, off_items = 0, off_pjobs = 0, ws_bytes = 0;
   unsigned char* d_ws = nullptr;
   bool bound = false;
   int32_t sm_count = 0;
@@ -79,12 +95,13 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       int64_t out_off = 0;
       for (size_t r = 0; r < p->ranges.size(); ++r) {
         const RangePlan& rp = p->ranges[r];
-        if (!rp.tile_ok || rp.tile_pattern || !batch_shape(rp.tile_dr)) {
+        const bool pat = rp.tile_ok && rp.tile_pattern;
+        if (!rp.tile_ok || (!pat && (rp.tile_pattern || !batch_shape(rp.tile_dr)))) {
           delete b;
           return fail(DD_ERR_UNSUPPORTED,
                       "batch plan " + std::to_string(i) + " range " + std::to_string(r) +
-                          " is not on a batch tile shape (a tiled bin, 4/2/1 DMs per lane; see "
-                          "dd_plan_set_tile)");
+                          " is not on a batch tile (the pattern tile, or the offset tile with "
+                          "4/2/1 DMs per lane; see dd_plan_set_tile)");
         }
         const int64_t n_out = range_n_out(p, rp, n_samp[i]);
         if (n_out <= 0) {
@@ -92,13 +109,34 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
           return fail(DD_ERR_SHAPE, "batch plan " + std::to_string(i) + " input too short");
         }
         const int32_t job = static_cast<int32_t>(b->jobs.size());
-        b->jobs.push_back({i, static_cast<int32_t>(r), n_out, out_off});
+        int32_t index;
+        int ts;
+        double dms;
+        if (pat) {
+          const tk::PatShape& ps = tk::kPatShapes[rp.tile_shape];
+          index = static_cast<int32_t>(b->host_pjobs.size());
+          b->host_pjobs.emplace_back();
+          size_t g = 0;
+          while (g < b->groups.size() &&
+                 !(b->groups[g].kind == rp.tile_kind && b->groups[g].shape == rp.tile_shape))
+            ++g;
+          if (g == b->groups.size()) b->groups.push_back({rp.tile_kind, rp.tile_shape});
+          b->pjob_group.push_back(static_cast<int32_t>(g));
+          b->groups[g].smem = std::max(
+              b->groups[g].smem, tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp));
+          ts = tk::pat_tile_samples(rp.tile_kind, ps.h);
+          dms = static_cast<double>(ps.warps) * tk::kPatDr;
+        } else {
+          index = static_cast<int32_t>(b->host_jobs.size());
+          b->host_jobs.emplace_back();
+          b->max_lraw = std::max(b->max_lraw, tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp));
+          b->max_lp = std::max(b->max_lp, rp.tile_lp);
+          ts = tk::tile_samples(rp.tile_kind);
+          dms = static_cast<double>(tk::shape_for(rp.tile_dr)->warps) * rp.tile_dr;
+        }
+        b->jobs.push_back({i, static_cast<int32_t>(r), n_out, out_off, pat, index});
         out_off += rp.n_dm * n_out;
-        b->max_lraw = std::max(b->max_lraw, tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp));
-        b->max_lp = std::max(b->max_lp, rp.tile_lp);
-        const double dms = static_cast<double>(tk::shape_for(rp.tile_dr)->warps) * rp.tile_dr;
-        order.push_back({static_cast<double>(p->n_chan) * dms * tk::tile_samples(rp.tile_kind) *
-                             rp.r.bin, job});
+        order.push_back({static_cast<double>(p->n_chan) * dms * ts * rp.r.bin, job});
       }
     }
     // Longest items first; within a job, DM blocks of a time tile together.
@@ -108,27 +146,41 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       const auto& j = b->jobs[c.job];
       const dd_plan p = b->plans[j.plan];
       const RangePlan& rp = p->ranges[j.range];
-      const int64_t tiles =
-          (j.n_out + tk::tile_samples(rp.tile_kind) - 1) / tk::tile_samples(rp.tile_kind);
+      const int ts = j.pattern ? tk::pat_tile_samples(rp.tile_kind, rp.tile_h)
+                               : tk::tile_samples(rp.tile_kind);
+      const int64_t tiles = (j.n_out + ts - 1) / ts;
+      auto& list = j.pattern ? b->groups[b->pjob_group[j.index]].items : b->items;
       for (int64_t t = 0; t < tiles; ++t)
         for (int32_t blk = 0; blk < rp.tile_n_blocks; ++blk)
-          b->items.push_back({c.job, blk, static_cast<int32_t>(t), 0});
+          list.push_back({j.index, blk, static_cast<int32_t>(t), 0});
     }
-    if (b->items.size() > 0x7fffffffu) {
+    size_t n_pitems = 0;
+    for (const auto& g : b->groups) n_pitems += g.items.size();
+    if (b->items.size() > 0x7fffffffu || n_pitems > 0x7fffffffu ||
+        b->groups.size() + 1 > tk::kStatusBytes / sizeof(uint32_t)) {
       delete b;
       return fail(DD_ERR_BUDGET, "too many batch items");
     }
-    size_t ws = tk::kStatusBytes;  // work counter
+    size_t ws = tk::kStatusBytes;  // work counters of the two launches
     ws = align256(ws);
     b->off_jobs = ws;
-    ws += b->jobs.size() * sizeof(tk::BatchJob);
+    ws += b->host_jobs.size() * sizeof(tk::BatchJob);
+    ws = align256(ws);
+    b->off_pjobs = ws;
+    ws += b->host_pjobs.size() * sizeof(tk::PatBatchJob);
     ws = align256(ws);
     b->off_items = ws;
     ws += b->items.size() * sizeof(tk::BatchItem);
+    for (auto& g : b->groups) {
+      ws = align256(ws);
+      g.off_items = ws;
+      ws += g.items.size() * sizeof(tk::BatchItem);
+    }
     b->ws_bytes = align256(ws);
-    b->host_jobs.resize(b->jobs.size());
     const size_t smem = tk::batch_smem_bytes(b->max_lraw, b->max_lp);
-    if (smem > 227 * 1024) {
+    bool too_big = !b->items.empty() && smem > 227 * 1024;
+    for (const auto& g : b->groups) too_big = too_big || g.smem > 227 * 1024;
+    if (too_big) {
       delete b;
       return fail(DD_ERR_BUDGET, "batch shared-memory layout exceeds 227 KB");
     }
@@ -153,8 +205,18 @@ dd_status dd_batch_workspace_bytes(dd_batch batch, size_t* bytes) {
 
 dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs) {
   if (!batch || !n_items || !n_jobs) return fail(DD_ERR_INVALID_ARG, "NULL argument");
-  *n_items = static_cast<int64_t>(batch->items.size());
+  int64_t n = static_cast<int64_t>(batch->items.size());
+  for (const auto& g : batch->groups) n += static_cast<int64_t>(g.items.size());
+  *n_items = n;
   *n_jobs = static_cast<int32_t>(batch->jobs.size());
+  return DD_OK;
+}
+
+dd_status dd_batch_launches(dd_batch batch, int32_t* n_launches) {
+  if (!batch || !n_launches) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+  int32_t n = batch->items.empty() ? 0 : 1;
+  for (const auto& g : batch->groups) n += g.items.empty() ? 0 : 1;
+  *n_launches = n;
   return DD_OK;
 }
 
@@ -165,9 +227,14 @@ dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void*
     return fail(DD_ERR_SHAPE, "batch workspace must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
-  cudaError_t e = cudaMemcpyAsync(ws + batch->off_items, batch->items.data(),
-                                  batch->items.size() * sizeof(tk::BatchItem),
-                                  cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
+  if (!batch->items.empty())
+    e = cudaMemcpyAsync(ws + batch->off_items, batch->items.data(),
+                        batch->items.size() * sizeof(tk::BatchItem), cudaMemcpyHostToDevice, s);
+  for (const auto& g : batch->groups)
+    if (e == cudaSuccess && !g.items.empty())
+      e = cudaMemcpyAsync(ws + g.off_items, g.items.data(), g.items.size() * sizeof(tk::BatchItem),
+                          cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_batch_upload");
   int dev = 0, sms = 0;
@@ -199,18 +266,33 @@ dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* 
         stride < n || (stride * static_cast<int64_t>(esz)) % 16 != 0)
       return fail(DD_ERR_SHAPE, "batch input/output alignment or stride");
     const RangePlan& rp = p->ranges[jr.range];
-    tk::BatchJob& bj = batch->host_jobs[j];
-    bj.p = tiled_params(p, rp, static_cast<unsigned char*>(p->d_ws) + rp.off_tile_recs,
-                        reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) +
-                                                   tk::kStatusOffset),
-                        x, stride, jr.n_out, static_cast<char*>(o) + jr.out_offset * 4);
-    bj.kind = rp.tile_kind;
-    bj.dr = rp.tile_dr;
+    const tk::TileParams prm =
+        tiled_params(p, rp, static_cast<unsigned char*>(p->d_ws) + rp.off_tile_recs,
+                     reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) +
+                                                tk::kStatusOffset),
+                     x, stride, jr.n_out, static_cast<char*>(o) + jr.out_offset * 4);
+    if (jr.pattern) {
+      tk::PatBatchJob& bj = batch->host_pjobs[jr.index];
+      bj.p = prm;
+      bj.kind = rp.tile_kind;
+      bj.shape = rp.tile_shape;
+    } else {
+      tk::BatchJob& bj = batch->host_jobs[jr.index];
+      bj.p = prm;
+      bj.kind = rp.tile_kind;
+      bj.dr = rp.tile_dr;
+    }
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(batch->d_ws + batch->off_jobs, batch->host_jobs.data(),
-                                  batch->host_jobs.size() * sizeof(tk::BatchJob),
-                                  cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
+  if (!batch->host_jobs.empty())
+    e = cudaMemcpyAsync(batch->d_ws + batch->off_jobs, batch->host_jobs.data(),
+                        batch->host_jobs.size() * sizeof(tk::BatchJob), cudaMemcpyHostToDevice,
+                        s);
+  if (e == cudaSuccess && !batch->host_pjobs.empty())
+    e = cudaMemcpyAsync(batch->d_ws + batch->off_pjobs, batch->host_pjobs.data(),
+                        batch->host_pjobs.size() * sizeof(tk::PatBatchJob),
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_batch_bind");
   batch->bound = true;
@@ -221,19 +303,36 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
   if (!batch) return fail(DD_ERR_INVALID_ARG, "batch is NULL");
   if (!batch->bound) return fail(DD_ERR_INVALID_ARG, "batch is not bound (dd_batch_bind)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(batch->d_ws, 0, sizeof(uint32_t), s);
+  cudaError_t e =
+      cudaMemsetAsync(batch->d_ws, 0, (1 + batch->groups.size()) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run counter reset");
-  tk::BatchArgs args{};
-  args.jobs = reinterpret_cast<const tk::BatchJob*>(batch->d_ws + batch->off_jobs);
-  args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + batch->off_items);
-  args.n_items = static_cast<int32_t>(batch->items.size());
-  args.counter = reinterpret_cast<uint32_t*>(batch->d_ws);
-  args.max_lraw = batch->max_lraw;
-  const size_t smem = tk::batch_smem_bytes(batch->max_lraw, batch->max_lp);
-  const int64_t grid = std::min<int64_t>(static_cast<int64_t>(batch->items.size()),
-                                         static_cast<int64_t>(batch->sm_count));
-  int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, stream);
-  if (le != 0) return cuda_fail(le, "dd_batch_run launch");
+  for (size_t gi = 0; gi < batch->groups.size(); ++gi) {
+    const auto& g = batch->groups[gi];
+    if (g.items.empty()) continue;
+    tk::PatBatchArgs args{};
+    args.jobs = reinterpret_cast<const tk::PatBatchJob*>(batch->d_ws + batch->off_pjobs);
+    args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + g.off_items);
+    args.n_items = static_cast<int32_t>(g.items.size());
+    args.counter = reinterpret_cast<uint32_t*>(batch->d_ws) + 1 + gi;
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(g.items.size()),
+                                           static_cast<int64_t>(batch->sm_count));
+    int le = launch_pattern_batch(g.kind, g.shape, args,
+                                  static_cast<int32_t>(std::max<int64_t>(grid, 1)), g.smem, stream);
+    if (le != 0) return cuda_fail(le, "dd_batch_run pattern launch");
+  }
+  if (!batch->items.empty()) {
+    tk::BatchArgs args{};
+    args.jobs = reinterpret_cast<const tk::BatchJob*>(batch->d_ws + batch->off_jobs);
+    args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + batch->off_items);
+    args.n_items = static_cast<int32_t>(batch->items.size());
+    args.counter = reinterpret_cast<uint32_t*>(batch->d_ws);
+    args.max_lraw = batch->max_lraw;
+    const size_t smem = tk::batch_smem_bytes(batch->max_lraw, batch->max_lp);
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(batch->items.size()),
+                                           static_cast<int64_t>(batch->sm_count));
+    int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, stream);
+    if (le != 0) return cuda_fail(le, "dd_batch_run launch");
+  }
   return DD_OK;
 }
 

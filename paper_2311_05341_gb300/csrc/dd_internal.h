@@ -55,10 +55,6 @@ struct RangePlan {
   std::vector<unsigned char> tile_recs;  // host image of the records
 };
 
-tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
-                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                            void* d_out);
-int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
 
 }  // namespace dd
 
@@ -112,5 +108,8 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                             void* d_out);
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
+// Persistent pattern-tile launch of one variant (kind, tk::kPatShapes index).
+int launch_pattern_batch(int kind, int shape, const tk::PatBatchArgs& args, int32_t grid,
+                         size_t smem, void* stream);
 
 }  // namespace dd

@@ -108,6 +108,9 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
                           cr.bytes(st), cr.dst(buf));
   };
   if (tid <= NC) {
+    // Shared memory read by an earlier unit of a persistent CTA is rewritten
+    // by the copies: order those generic-proxy reads before them.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     issue(0, gstage & 1, base_of(0));
     if (n_st > 1) issue(1, (gstage + 1) & 1, base_of(1));
   }

@@ -147,6 +147,7 @@ constexpr PatShape kPatShapes[] = {
     {23, 16, 32, true, false, 3},  {23, 16, 12, true, false, 3}, {23, 16, 6, true, false, 3},
     {19, 16, 32, false, false, 1}, {19, 16, 12, false, false, 1}, {19, 16, 6, false, false, 1},
     {19, 16, 12, false, false, 3}, {19, 16, 6, false, false, 3}};
+constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
 // The shape serves a kind: pairs take integer window words, single channels float.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
   return s.pairs == (kind != kF32);
@@ -248,6 +249,21 @@ struct BatchArgs {
   int32_t n_items;
   uint32_t* counter;       // device, zero before the launch
   int32_t max_lraw;        // largest raw window of any job (shared-memory layout)
+};
+
+// Persistent batch execution of pattern-tile jobs (fwd_pattern_batch.cu):
+// every job names its kind and its tk::kPatShapes entry.
+struct PatBatchJob {
+  TileParams p;
+  int32_t kind;
+  int32_t shape;
+};
+
+struct PatBatchArgs {
+  const PatBatchJob* jobs;  // device
+  const BatchItem* items;   // device, in execution order
+  int32_t n_items;
+  uint32_t* counter;        // device, zero before the launch
 };
 
 inline size_t batch_smem_bytes(int32_t max_lraw, int32_t max_lp) {

@@ -1,0 +1,289 @@
+// pattern_body.cuh -- device code of the pattern tiles (fwd_pattern.cu): the
+// shared-memory layout, the generated pattern blocks and the (DM block, time
+// tile) work unit, shared by the one-unit-per-CTA kernel and the persistent
+// batch kernel (fwd_pattern_batch.cu).
+//
+// Computes Eq. 3 (Algorithm 1) with the output partition, staging, binning and
+// widen/store of the offset tiles (fwd_tiled.cu); only the register tile and
+// its per-channel dispatch differ:
+//
+//  * Every lane owns kPatDr = 4 consecutive DMs x H window words, H odd
+//    (uint8: 2H samples, pairing samples u and u + 32H in 16-bit lanes).
+//  * Eq. 1 is linear in DM, so from one trial DM to the next the shift of a
+//    channel grows by the floor or the ceiling of step * k_c / (bin * t_samp):
+//    the increments between a warp's four DMs are a or a + 1.  The host
+//    stores, per (DM block, channel, warp), the window offset of the warp's
+//    first DM and the pattern 8 a + bits (fwd_tiled.h).
+//  * Integer kinds: each warp walks its own list of channel pairs that share
+//    a pattern; per pair one warp-uniform indexed branch enters a generated
+//    block (gen_dispatch.py) that loads the window words its offsets touch
+//    (scalar shared loads, conflict-free at any offset because the lane
+//    stride H is odd) and adds both channels' samples with three-input adds.
+//    Float: one channel per branch.
+//
+// Against the 4-bit-offset tiles this is one indexed branch per four DMs and
+// two channels instead of one per DM.  Every mbarrier wait is bounded; on
+// timeout the unit records kErrTimeout in the status word and returns false.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fwd_tiled.h"
+#include "fwd_tiled_dispatch.inc"
+#include "tile_common.cuh"
+
+namespace dd {
+namespace tk {
+namespace pattern {
+
+struct PSmem {
+  uint32_t bar_base;  // 2 mbarriers
+  unsigned char* recs;  // [2 or 3][NC] PRec, or [2 or 3] pair chunks
+  uint8_t* raw;       // [2][NC][lraw]
+  uint32_t* pw;       // [1 or 2][NC][lp] window words
+};
+
+template <int NW, int NC, bool PAIRS, bool DBUF>
+__device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
+  constexpr size_t kRawOff = pat_raw_offset(NW, NC, PAIRS, DBUF);
+  PSmem sm;
+  sm.bar_base = smem_u32(smem);
+  sm.recs = smem + kRecOffset;
+  sm.raw = smem + kRawOff;
+  sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
+  return sm;
+}
+
+// One channel (or a pair of channels of one pattern) into the lane's
+// accumulators: `win` (`win2`) is the shared-memory address of the lane's
+// window; the generated block of pattern `ix` loads the window words it needs
+// and adds them.  The blocks exist for the window widths gen_dispatch.py lists.
+template <int KIND, int H>
+__device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
+                                            uint32_t ix) {
+  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+                "no generated pattern blocks for H");
+#define DD_PAT_CASE(HH)                                                  \
+  if constexpr (H == HH) {                                               \
+    if constexpr (KIND == kF32) DD_PATL_CHANNEL_F32_##HH(acc, win, ix);  \
+    else DD_PATL_CHANNEL_U32_##HH(acc, win, ix);                         \
+  }
+  DD_PAT_CASE(17)
+  DD_PAT_CASE(19)
+  DD_PAT_CASE(21)
+  DD_PAT_CASE(23)
+  DD_PAT_CASE(25)
+#undef DD_PAT_CASE
+}
+
+// The same with the window words already in registers R (H + 6 of them): the
+// loads are scheduled before the branch.  Single-channel tiles run faster so.
+template <int KIND, int H>
+__device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
+                                                 const AccT<KIND> (&R)[H + 2 * (kPatDr - 1)],
+                                                 uint32_t ix) {
+#define DD_PAT_CASE(HH)                                           \
+  if constexpr (H == HH) {                                        \
+    if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
+    else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);                     \
+  }
+  DD_PAT_CASE(17)
+  DD_PAT_CASE(19)
+  DD_PAT_CASE(21)
+  DD_PAT_CASE(23)
+  DD_PAT_CASE(25)
+#undef DD_PAT_CASE
+}
+
+template <int H>
+__device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t win, uint32_t win2,
+                                         uint32_t ix) {
+  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+                "no generated pair blocks for H");
+  if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
+  else if constexpr (H == 19) DD_PATL2_CHANNEL_U32_19(acc, win, win2, ix);
+  else if constexpr (H == 21) DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
+  else if constexpr (H == 23) DD_PATL2_CHANNEL_U32_23(acc, win, win2, ix);
+  else DD_PATL2_CHANNEL_U32_25(acc, win, win2, ix);
+}
+
+// Pair chunk of one (DM block, stage) in global memory.
+__device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, int blk, int n_st,
+                                                           int st) {
+  return static_cast<const unsigned char*>(p.recs) +
+         (static_cast<int64_t>(blk) * n_st + st) * p.chunk_bytes;
+}
+
+// One (DM block, time tile) work unit.  Returns false after a bounded wait
+// gave up (the status word is set).
+//
+// Stage st uses raw buffer st % 2 and record buffer st % kRecBufs.  With
+// DBUF the window words are double-buffered too (stage st in window buffer
+// st % 2) and one barrier per stage suffices: the barrier after unpacking
+// stage st also certifies that every warp finished computing stage st - 1,
+// so the copies of stage st + 2 (raw buffer st % 2, record buffer
+// (st + 2) % 3) and the unpacking of stage st + 1 may start while warps still
+// compute stage st.  Without DBUF a second barrier ends each stage.
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+__device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
+                                         int64_t tile) {
+  static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
+  constexpr int kThreads = NW * 32;
+  constexpr int kPairW = 32 * H;
+  constexpr int kRecBufs = DBUF ? 3 : 2;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int64_t t0 = tile * pat_tile_samples(KIND, H);
+  const int n_st = (p.n_chan + NC - 1) / NC;
+
+  const PRec* my_recs = static_cast<const PRec*>(p.recs) + static_cast<int64_t>(blk) * p.n_chan;
+  const int32_t* my_bases = p.bases + static_cast<int64_t>(blk) * p.n_chan;
+  auto base_of = [&](int st) -> int32_t {
+    const int c = st * NC + tid;
+    if (!(tid < NC && st < n_st && c < p.n_chan)) return 0;
+    if constexpr (PAIRS) return my_bases[c];
+    else return my_recs[c].base;
+  };
+  auto rec_buf = [&](int rb) -> unsigned char* {
+    if constexpr (PAIRS) return sm.recs + rb * p.chunk_bytes;
+    else return sm.recs + rb * NC * static_cast<int>(sizeof(PRec));
+  };
+  const ChannelRecs<NC, PRec> cr{my_recs, reinterpret_cast<PRec*>(sm.recs), p.n_chan};
+  auto issue = [&](int st, int32_t base) {
+    unsigned char* dst = rec_buf(st % kRecBufs);
+    if constexpr (PAIRS)
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid,
+                            pair_chunk(p, blk, n_st, st), p.chunk_bytes, dst);
+    else
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid, cr.src(st),
+                            cr.bytes(st), dst);
+  };
+  if (tid <= NC) {
+    // Shared memory read by an earlier unit of a persistent CTA is rewritten
+    // by the copies: order those generic-proxy reads before them.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(0, base_of(0));
+    if (n_st > 1) issue(1, base_of(1));
+  }
+  int32_t next_base = base_of(2);
+  auto issue_next = [&](int st) {  // copies of stage st + 2 into the buffers stage st freed
+    if (tid <= NC && st + 2 < n_st) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(st + 2, next_base);
+      next_base = base_of(st + 3);
+    }
+  };
+
+  AccT<KIND> acc[kPatDr][H];
+#pragma unroll
+  for (int i = 0; i < kPatDr; ++i)
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc[i][j] = AccT<KIND>(0);
+
+  bool first = true;
+  int since = 0;  // channels accumulated since the last widen
+  const int units = p.lp >> 2;
+  int rb = 0;     // st % kRecBufs
+
+  for (int st = 0; st < n_st; ++st) {
+    const int buf = st & 1;
+    const uint32_t parity = (st >> 1) & 1;
+    const int nc = min(NC, p.n_chan - st * NC);
+    uint32_t* pwb = sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
+    auto unpack = [&]() {  // raw bytes of stage st into window words
+      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
+      const int total = nc * units;
+      for (int u = tid; u < total; u += kThreads) {
+        const int ch =
+            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
+        const int q = u - ch * units;
+        const uint4 v =
+            unpack_unit<KIND, kPairW>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
+        *reinterpret_cast<uint4*>(pwb + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
+      }
+    };
+    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
+    if (DBUF && ok) unpack();
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(p.err, kErrTimeout);
+        // Let copies still in flight land before the CTA exits (bounded).
+        mbar_wait(sm.bar_base + 8u * buf, parity);
+        if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
+      }
+      return false;
+    }
+    if constexpr (DBUF) {
+      issue_next(st);
+    } else {
+      unpack();
+      __syncthreads();
+    }
+
+    // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
+    // PTX labels, appear once per instantiation.
+    if constexpr (PAIRS) {
+      const uint32_t lane_win = smem_u32(pwb + H * l);
+      const unsigned char* ck = rec_buf(rb);
+      const int n_pairs = ck[w], n_items = n_pairs + ck[16 + w];
+      const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
+#pragma unroll 1
+      for (int k = 0; k < n_pairs; ++k) {
+        const PairItem it = items[k];
+        pat_pair<H>(acc, lane_win + 4u * (it.a & 0xffffu), lane_win + 4u * (it.a >> 16), it.pat);
+      }
+#pragma unroll 1
+      for (int k = n_pairs; k < n_items; ++k) {
+        const PairItem it = items[k];
+        pat_channel<KIND, H>(acc, lane_win + 4u * it.a, it.pat);
+      }
+    } else if constexpr (AMAX <= 1) {
+      // Base increments 0 and 1 only: the lane's H + 6 window words are loaded
+      // before the branch.
+      constexpr int kR = H + 2 * (kPatDr - 1);
+      const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
+      const uint32_t* lane_pw = pwb + H * l;
+#pragma unroll 1
+      for (int ch = 0; ch < nc; ++ch) {
+        const uint32_t e = rs[ch].w[w];
+        const uint32_t* src = lane_pw + static_cast<size_t>(ch) * p.lp + (e & kPatOffMask);
+        AccT<KIND> R[kR];
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+          if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
+          else R[k] = src[k];
+        }
+        pat_channel_regs<KIND, H>(acc, R, e >> kPatOffBits);
+      }
+    } else {
+      const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
+      const uint32_t lane_win = smem_u32(pwb + H * l);
+#pragma unroll 1
+      for (int ch = 0; ch < nc; ++ch) {
+        const uint32_t e = rs[ch].w[w];
+        pat_channel<KIND, H>(acc, lane_win + 4u * (ch * p.lp + (e & kPatOffMask)),
+                             e >> kPatOffBits);
+      }
+    }
+    since += nc;
+    rb = rb + 1 == kRecBufs ? 0 : rb + 1;
+    if constexpr (!DBUF) {
+      __syncthreads();  // window words, raw[buf] and recs[buf] are free
+      issue_next(st);
+    }
+    if (since + NC > p.flush || st == n_st - 1) {
+      // The transpose tiles reuse this stage's window buffer: wait until every
+      // warp has finished reading it.
+      if constexpr (DBUF) __syncthreads();
+      widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
+      first = false;
+      since = 0;
+    }
+  }
+  return true;
+}
+
+}  // namespace pattern
+}  // namespace tk
+}  // namespace dd

@@ -66,10 +66,18 @@ def _check_oracle(b, host, planes):
             np.testing.assert_array_equal(g, o)
 
 
-def test_batch_equals_alone_and_oracle():
-    runner = ddb.BatchRunner(_beams(), autotune=True, graph=True)
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_equals_alone_and_oracle(autotune):
+    runner = ddb.BatchRunner(_beams(), autotune=autotune, graph=True)
     assert runner.n_jobs == 6
-    assert all(dr in (4, 2, 1) for shp in runner.shapes for dr in shp)
+    assert all(dr in ddb.BATCH_SHAPES for shp in runner.shapes for dr in shp)
+    if not autotune:
+        # The first feasible tile: the pattern tile, except for the steep
+        # 96-channel float beam (offset tile): both persistent families run.
+        assert [shp[0] for shp in runner.shapes] == ["pattern", "pattern", "pattern", 1,
+                                                     "pattern"]
+        # At least the u8, u16 and f32 pattern variants plus the offset family.
+        assert runner.n_launches >= 4
     hosts = _fill(runner, 600)
     runner.run()
     torch.cuda.synchronize()
