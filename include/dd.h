@@ -187,8 +187,14 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream);
 /*
  * End-to-end forward from HOST buffers: copies h_in (pinned host memory,
  * [n_chan][in_row_stride]) to the caller's device staging buffer d_in_stage,
- * runs dd_run into d_out_stage and copies the output plane back to h_out, all
- * on `stream` (one cudaMemcpyAsync per copy).  Staging buffers have the same
+ * computes the transform into d_out_stage and copies the output planes back to
+ * h_out (pinned, the dd_run output layout).  The raw time axis is split into
+ * 16 segments: segment k's copy in, the outputs whose dispersion tracks end in
+ * segments 0..k, and their copy out run on internal copy streams and on
+ * `stream` alternating with an internal compute stream, so copies overlap the
+ * kernels.  The internal streams and events
+ * are created on the first call (per device) and released by dd_plan_destroy.
+ * When `stream` completes, h_out is written.  Staging buffers have the same
  * layout rules as dd_run.  Returns once the work is enqueued.
  */
 dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,

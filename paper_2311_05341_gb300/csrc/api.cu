@@ -2,6 +2,7 @@
 // error reporting and kernel dispatch.  No device memory is allocated here.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -14,6 +15,8 @@ namespace dd {
 namespace {
 thread_local std::string g_detail;
 }
+
+void free_host_pipe(dd_plan_s* p);
 
 dd_status fail(dd_status st, const std::string& detail) {
   g_detail = detail;
@@ -55,6 +58,85 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
   o->out_elems = off;
   o->workspace_bytes = p->ws_bytes;
   return DD_OK;
+}
+
+// dd_run_host splits the raw time axis into this many segments: segment k's
+// host-to-device copy, the outputs it completes and their device-to-host copy
+// run on separate streams, overlapping segment k+1's copy in and k-1's copy
+// out.  Segments alternate between two compute streams (the caller's and an
+// internal one) so that one segment's last CTAs overlap the next one's first.
+constexpr int kHostSegments = 16;
+
+struct HostPipe {
+  int device = -1;
+  cudaStream_t s_in = nullptr, s_out = nullptr, s_comp = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t in[kHostSegments] = {}, comp[kHostSegments] = {};
+};
+
+void destroy_pipe(HostPipe* hp) {
+  if (hp->s_in) cudaStreamDestroy(hp->s_in);
+  if (hp->s_out) cudaStreamDestroy(hp->s_out);
+  if (hp->s_comp) cudaStreamDestroy(hp->s_comp);
+  for (cudaEvent_t e : {hp->start, hp->done})
+    if (e) cudaEventDestroy(e);
+  for (int k = 0; k < kHostSegments; ++k) {
+    if (hp->in[k]) cudaEventDestroy(hp->in[k]);
+    if (hp->comp[k]) cudaEventDestroy(hp->comp[k]);
+  }
+  delete hp;
+}
+
+// The plan's copy streams and events on the current device (created once).
+cudaError_t host_pipe(dd_plan_s* p, HostPipe** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  HostPipe* hp = static_cast<HostPipe*>(p->host_pipe);
+  if (hp && hp->device == dev) {
+    *out = hp;
+    return cudaSuccess;
+  }
+  if (hp) destroy_pipe(hp);
+  p->host_pipe = nullptr;
+  hp = new (std::nothrow) HostPipe();
+  if (!hp) return cudaErrorMemoryAllocation;
+  hp->device = dev;
+  e = cudaStreamCreateWithFlags(&hp->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->done, cudaEventDisableTiming);
+  for (int k = 0; k < kHostSegments && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&hp->in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->comp[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    destroy_pipe(hp);
+    return e;
+  }
+  p->host_pipe = hp;
+  *out = hp;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+void free_host_pipe(dd_plan_s* p) {
+  if (p->host_pipe) destroy_pipe(static_cast<HostPipe*>(p->host_pipe));
+  p->host_pipe = nullptr;
+}
+
+namespace {
+
+// Outputs [t_begin, t_end) of one range on its kernel.
+int launch_range(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
+                 int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
+                 void* stream) {
+  return rp.tile_ok ? launch_forward_tiled(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
+                                           t_end, stream)
+                    : launch_forward_generic(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
+                                             t_end, stream);
 }
 
 }  // namespace
@@ -129,6 +211,7 @@ dd_status dd_plan_create(const double* freqs_mhz, int32_t n_chan, double f_ref_m
 }
 
 dd_status dd_plan_destroy(dd_plan plan) {
+  if (plan) free_host_pipe(plan);
   delete plan;
   return DD_OK;
 }
@@ -199,10 +282,8 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
     void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
     const RangePlan& rp = plan->ranges[i];
-    int e = rp.tile_ok ? launch_forward_tiled(plan, rp, d_in, in_row_stride, n_samp,
-                                              info.n_out[i], o, stream)
-                       : launch_forward_generic(plan, rp, d_in, in_row_stride, n_samp,
-                                                info.n_out[i], o, stream);
+    int e = launch_range(plan, rp, d_in, in_row_stride, n_samp, info.n_out[i], o, 0,
+                         info.n_out[i], stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
   return DD_OK;
@@ -243,15 +324,80 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
   dd_plan_info info;
   dd_status st = check_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, &info);
   if (st != DD_OK) return st;
+  HostPipe* hp = nullptr;
+  cudaError_t e = host_pipe(plan, &hp);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host streams");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t in_bytes = static_cast<size_t>(plan->n_chan) * in_row_stride * elem_size(plan->dtype);
-  cudaError_t e = cudaMemcpyAsync(d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host input copy");
-  st = dd_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, stream);
-  if (st != DD_OK) return st;
-  e = cudaMemcpyAsync(h_out, d_out_stage, static_cast<size_t>(info.out_elems) * 4,
-                      cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host output copy");
+  const size_t esz = elem_size(plan->dtype);
+  const size_t pitch_in = static_cast<size_t>(in_row_stride) * esz;
+  const unsigned char* hin = static_cast<const unsigned char*>(h_in);
+  unsigned char* din = static_cast<unsigned char*>(d_in_stage);
+  unsigned char* hout = static_cast<unsigned char*>(h_out);
+  unsigned char* dout = static_cast<unsigned char*>(d_out_stage);
+  // The copy streams start after the caller's earlier work on `stream`.
+  e = cudaEventRecord(hp->start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_in, hp->start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_out, hp->start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_comp, hp->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+  const int64_t seg = (n_samp + kHostSegments - 1) / kHostSegments;
+  const int64_t seg_len = (seg + 255) / 256 * 256;
+  int64_t raw_done = 0;
+  int64_t done[DD_MAX_RANGES] = {};
+  for (int k = 0; k < kHostSegments; ++k) {
+    const bool last = k == kHostSegments - 1;
+    cudaStream_t sc = (k & 1) ? hp->s_comp : s;
+    const int64_t raw_end = last ? n_samp : std::min<int64_t>(n_samp, (k + 1) * seg_len);
+    // Segment k of the raw samples, every channel (a strided 2-D copy).
+    if (raw_end > raw_done) {
+      e = cudaMemcpy2DAsync(din + raw_done * esz, pitch_in, hin + raw_done * esz, pitch_in,
+                            static_cast<size_t>(raw_end - raw_done) * esz, plan->n_chan,
+                            cudaMemcpyHostToDevice, hp->s_in);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host input copy");
+      raw_done = raw_end;
+    }
+    e = cudaEventRecord(hp->in[k], hp->s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, hp->in[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    // Every output whose dispersion track ends inside the samples copied so
+    // far: t + S_max < raw_end / bin, whole time tiles except at the end.
+    int64_t lim[DD_MAX_RANGES];
+    for (size_t r = 0; r < plan->ranges.size(); ++r) {
+      const RangePlan& rp = plan->ranges[r];
+      const int64_t n_out = info.n_out[r];
+      int64_t l = n_out;
+      if (!last) {
+        const int64_t ts = range_tile_samples(rp);
+        l = std::min<int64_t>(n_out, raw_end / rp.r.bin - rp.s_max);
+        l = l < 0 ? 0 : l / ts * ts;
+      }
+      lim[r] = l;
+      if (l > done[r]) {
+        const int le = launch_range(plan, rp, din, in_row_stride, n_samp, n_out,
+                                    dout + info.out_offset[r] * 4, done[r], l, sc);
+        if (le != 0) return cuda_fail(le, "dd_run_host forward launch");
+      }
+    }
+    e = cudaEventRecord(hp->comp[k], sc);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_out, hp->comp[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    for (size_t r = 0; r < plan->ranges.size(); ++r) {
+      if (lim[r] <= done[r]) continue;
+      const size_t pitch_out = static_cast<size_t>(info.n_out[r]) * 4;
+      const size_t off = static_cast<size_t>(info.out_offset[r] + done[r]) * 4;
+      e = cudaMemcpy2DAsync(hout + off, pitch_out, dout + off, pitch_out,
+                            static_cast<size_t>(lim[r] - done[r]) * 4,
+                            static_cast<size_t>(info.n_dm[r]), cudaMemcpyDeviceToHost,
+                            hp->s_out);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host output copy");
+      done[r] = lim[r];
+    }
+  }
+  // The caller's stream completes after the last output copy, which follows
+  // every segment's kernels on both compute streams.
+  e = cudaEventRecord(hp->done, hp->s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
   return DD_OK;
 }
 

@@ -69,6 +69,7 @@ struct dd_plan_s {
   std::vector<unsigned char> host_ws;  // staged device tables
   void* d_ws = nullptr;                // bound device workspace (caller-owned)
   size_t ws_bytes = 0;
+  void* host_pipe = nullptr;           // streams/events of dd_run_host (api.cu)
 };
 
 namespace dd {
@@ -84,22 +85,26 @@ dd_status build_plan(dd_plan_s* p);
 bool retile_range(dd_plan_s* p, size_t range, int32_t request);
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
 
-// Kernel launchers (return a cudaError_t as int; 0 on success).
+// Kernel launchers (return a cudaError_t as int; 0 on success).  Each writes
+// the outputs t in [t_begin, t_end) of rows of n_out samples; t_begin is a
+// multiple of range_tile_samples(rp).
+int64_t range_tile_samples(const RangePlan& rp);
 int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                            int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
-                           void* stream);
+                           int64_t t_begin, int64_t t_end, void* stream);
 int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                          int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
-                         void* stream);
+                         int64_t t_begin, int64_t t_end, void* stream);
 // The tiled kernel with its record table and status word at explicit device
 // addresses (used by the no-allocation entry point and the batch runtime).
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
-                                     int64_t n_out, void* d_out, void* stream);
+                                     int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
+                                     void* stream);
 // The pattern kernel (fwd_pattern.cu), same arguments.
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                           void* d_out, void* stream);
+                           void* d_out, int64_t t_begin, int64_t t_end, void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);

@@ -26,14 +26,14 @@ template <typename TIn, typename TAcc>
 __global__ void __launch_bounds__(256)
 fwd_generic_kernel(const TIn* __restrict__ x, int64_t stride, int32_t n_chan, int32_t bin,
                    int64_t n_dec, const int32_t* __restrict__ shifts, int32_t n_dm,
-                   int32_t n_dm_blocks, int64_t n_out, int32_t win, int32_t chunk,
-                   TAcc* __restrict__ out) {
+                   int32_t n_dm_blocks, int64_t n_out, int64_t tile0, int64_t t_end,
+                   int32_t win, int32_t chunk, TAcc* __restrict__ out) {
   extern __shared__ unsigned char smem_raw[];
   TAcc* win_buf = reinterpret_cast<TAcc*>(smem_raw);              // [chunk][win]
   int32_t* base_buf = reinterpret_cast<int32_t*>(win_buf + chunk * win);  // [chunk]
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t tile = blockIdx.x / n_dm_blocks;
+  const int64_t tile = blockIdx.x / n_dm_blocks + tile0;
   const int32_t dblk = blockIdx.x % n_dm_blocks;
   const int32_t d_first = dblk * kGenDmPerCta;
   const int64_t t0 = tile * kGenSampPerCta;
@@ -90,14 +90,17 @@ fwd_generic_kernel(const TIn* __restrict__ x, int64_t stride, int32_t n_chan, in
 #pragma unroll
     for (int k = 0; k < kGenSampPerThread; ++k) {
       const int64_t t = t0 + tx + 32 * k;
-      if (t < n_out) orow[t] = acc[i][k];
+      if (t < t_end) orow[t] = acc[i][k];
     }
   }
 }
 
 template <typename TIn, typename TAcc>
 int launch_typed(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
-                 int64_t n_samp, int64_t n_out, void* d_out, cudaStream_t st) {
+                 int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
+                 cudaStream_t st) {
+  if (t_begin % kGenSampPerCta != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)
+    return static_cast<int>(cudaErrorInvalidValue);
   const int32_t win = kGenSampPerCta + rp.gen_span;
   const size_t per_chan = static_cast<size_t>(win) * sizeof(TAcc) + sizeof(int32_t);
   int32_t chunk = static_cast<int32_t>(std::min<size_t>(32, (96 * 1024) / per_chan));
@@ -108,14 +111,15 @@ int launch_typed(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int6
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
-  const int64_t tiles = (n_out + kGenSampPerCta - 1) / kGenSampPerCta;
+  const int64_t tile0 = t_begin / kGenSampPerCta;
+  const int64_t tiles = (t_end + kGenSampPerCta - 1) / kGenSampPerCta - tile0;
   const int64_t grid = tiles * rp.gen_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
   const int32_t* shifts = reinterpret_cast<const int32_t*>(
       static_cast<const unsigned char*>(p->d_ws) + rp.off_shifts);
   kern<<<static_cast<unsigned>(grid), dim3(32, 8), smem, st>>>(
       static_cast<const TIn*>(d_in), stride, p->n_chan, rp.r.bin, n_samp / rp.r.bin, shifts,
-      static_cast<int32_t>(rp.n_dm), rp.gen_n_blocks, n_out, win, chunk,
+      static_cast<int32_t>(rp.n_dm), rp.gen_n_blocks, n_out, tile0, t_end, win, chunk,
       static_cast<TAcc*>(d_out));
   return static_cast<int>(cudaGetLastError());
 }
@@ -124,15 +128,18 @@ int launch_typed(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int6
 
 int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                            int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
-                           void* stream) {
+                           int64_t t_begin, int64_t t_end, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (p->dtype) {
     case DD_U8:
-      return launch_typed<uint8_t, int32_t>(p, rp, d_in, stride, n_samp, n_out, d_out, st);
+      return launch_typed<uint8_t, int32_t>(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
+                                            t_end, st);
     case DD_U16:
-      return launch_typed<uint16_t, int32_t>(p, rp, d_in, stride, n_samp, n_out, d_out, st);
+      return launch_typed<uint16_t, int32_t>(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
+                                             t_end, st);
     case DD_F32:
-      return launch_typed<float, float>(p, rp, d_in, stride, n_samp, n_out, d_out, st);
+      return launch_typed<float, float>(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin, t_end,
+                                        st);
   }
   return static_cast<int>(cudaErrorInvalidValue);
 }

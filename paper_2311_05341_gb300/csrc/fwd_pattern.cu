@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
   }
   __syncthreads();
   pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blockIdx.x % p.n_blocks,
-                                         blockIdx.x / p.n_blocks);
+                                               blockIdx.x / p.n_blocks + p.tile0);
 }
 
 }  // namespace tk
@@ -74,10 +74,14 @@ int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cuda
 
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                           void* d_out, void* stream) {
-  const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
+                           void* d_out, int64_t t_begin, int64_t t_end, void* stream) {
+  tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
   const int ts = tk::pat_tile_samples(rp.tile_kind, rp.tile_h);
-  const int64_t tiles = (n_out + ts - 1) / ts;
+  if (t_begin % ts != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)
+    return static_cast<int>(cudaErrorInvalidValue);
+  prm.tile0 = t_begin / ts;
+  prm.t_end = t_end;
+  const int64_t tiles = (t_end + ts - 1) / ts - prm.tile0;
   const int64_t grid = tiles * rp.tile_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) fwd_tiled_kernel(const TilePara
   const Smem sm = smem_layout<NC>(smem, p.lraw);
   init_barriers<NC>(sm);
   uint32_t gstage = 0;
-  tile_body<KIND, DR, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks, gstage);
+  tile_body<KIND, DR, NW, NC>(p, sm, blockIdx.x % p.n_blocks, blockIdx.x / p.n_blocks + p.tile0,
+                              gstage);
 }
 
 // One batch item of one variant.  Returns the continued stage count, or
@@ -316,6 +317,8 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.n_dm = static_cast<int32_t>(rp.n_dm);
   prm.n_blocks = rp.tile_n_blocks;
   prm.n_out = n_out;
+  prm.tile0 = 0;
+  prm.t_end = n_out;
   prm.lp = rp.tile_lp;
   prm.lraw = tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp, 32 * rp.tile_h);
   prm.units_magic = rp.tile_units_magic;
@@ -327,14 +330,26 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   return prm;
 }
 
+int64_t range_tile_samples(const RangePlan& rp) {
+  if (!rp.tile_ok) return kGenSampPerCta;
+  return rp.tile_pattern ? tk::pat_tile_samples(rp.tile_kind, rp.tile_h)
+                         : tk::tile_samples(rp.tile_kind);
+}
+
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
-                                     int64_t n_out, void* d_out, void* stream) {
+                                     int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
+                                     void* stream) {
   if (rp.tile_pattern)
-    return launch_forward_pattern(p, rp, recs, err, d_in, stride, n_out, d_out, stream);
-  const tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
+    return launch_forward_pattern(p, rp, recs, err, d_in, stride, n_out, d_out, t_begin, t_end,
+                                  stream);
+  tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
   const int ts = tk::tile_samples(rp.tile_kind);
-  const int64_t tiles = (n_out + ts - 1) / ts;
+  if (t_begin % ts != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)
+    return static_cast<int>(cudaErrorInvalidValue);
+  prm.tile0 = t_begin / ts;
+  prm.t_end = t_end;
+  const int64_t tiles = (t_end + ts - 1) / ts - prm.tile0;
   const int64_t grid = tiles * rp.tile_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -349,13 +364,13 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
 
 int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_in,
                          int64_t stride, int64_t n_samp, int64_t n_out, void* d_out,
-                         void* stream) {
+                         int64_t t_begin, int64_t t_end, void* stream) {
   (void)n_samp;
   const unsigned char* ws = static_cast<const unsigned char*>(p->d_ws);
   return launch_forward_tiled_with_tables(
       p, rp, ws + rp.off_tile_recs,
       reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) + tk::kStatusOffset), d_in,
-      stride, n_out, d_out, stream);
+      stride, n_out, d_out, t_begin, t_end, stream);
 }
 
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream) {

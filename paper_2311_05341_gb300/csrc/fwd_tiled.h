@@ -217,7 +217,9 @@ struct TileParams {
   int32_t chunk_bytes;  // pair tiles: bytes per (DM block, stage) chunk
   int32_t n_dm;
   int32_t n_blocks;
-  int64_t n_out;
+  int64_t n_out;        // output row length
+  int64_t tile0;        // first time tile of the launch
+  int64_t t_end;        // outputs t >= t_end are not written (<= n_out)
   int32_t lp;           // window words per staged channel
   int32_t lraw;         // raw bytes per staged channel
   uint32_t units_magic; // u / (lp/4) == (u * magic) >> (32 + shift)

@@ -228,7 +228,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
   uint32_t* tr = pw + (w / groups) * kFw;
   const int wbase = H * l + (ST::kPad ? (l >> 3) : 0);
   constexpr int kHiOff = ST::kPairW + (ST::kPad ? ST::kPairW / 160 : 0);
-  const int64_t lim = p.n_out - t0;
+  const int64_t lim = p.t_end - t0;
   for (int gi = 0; gi < groups; ++gi) {
     if (gi > 0) __syncthreads();
     if (w % groups != gi) continue;
