@@ -271,6 +271,8 @@ def run_ours(args):
         "alu_microbench": {k: v for k, v in peaks.items()},
         "frac_of_microbench": sample_adds_per_s / (
             peaks["iadd3"] * per_lane if beam.dtype != "f32" else peaks["fadd"]),
+        # Against one sample per two-input add on both 16-lane pipes (no packing).
+        "frac_unpacked": sample_adds_per_s / (128 * sms * SM_MAX_MHZ * 1e6),
         "hbm": {"algorithmic_bytes": algo_bytes,
                 "achieved_gbs": algo_bytes / (total / args.steps) / 1e9,
                 "frac_of_measured": algo_bytes / (total / args.steps) / 1e9 / HBM_GBS},
