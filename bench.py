@@ -495,6 +495,70 @@ def run_stream(args):
                       "hbm_budget_gb": args.hbm_budget_gb, "results": results}))
 
 
+def run_frontend(args):
+    """Time-major (receiver / SIGPROC order) input of the paper-scale uint8
+    workload: the transpose kernel alone against HBM bandwidth, and the whole
+    host-to-host pipeline (copy in, transpose, dedisperse, copy out)."""
+    import torch
+    import paper_2311_05341_gb300 as dd
+    from synth import workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    beam = _workload("paper_u8", args.n_samp)
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
+    info = plan.info(beam.n_samp)
+    x_cm = workloads.make_input(beam, lambda r, d: plan.shifts(r)[d], info["n_dm"], info["n_out"])
+    x_tm = np.ascontiguousarray(x_cm[:, : beam.n_samp].T)
+    h_in = torch.from_numpy(x_tm).pin_memory()
+    h_out = torch.empty(info["out_elems"], dtype=torch.int32).pin_memory()
+    d_tm = h_in.to("cuda")
+    d_cm = torch.empty((beam.n_chan, (beam.n_samp + 15) // 16 * 16), dtype=torch.uint8,
+                       device="cuda")
+    out = plan.empty_output(beam.n_samp)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / args.steps
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_tr = timed(lambda: dd.transpose(d_tm, out=d_cm))
+    t_e2e = timed(lambda: plan.run_host_tmajor(h_in, h_out, d_tm, d_cm, out,
+                                               n_samp=beam.n_samp))
+    clk = clocks.stop()
+    # Parity of the transposed input on sampled rows.
+    same = all(np.array_equal(d_cm[c, : beam.n_samp].cpu().numpy(), x_cm[c, : beam.n_samp])
+               for c in (0, beam.n_chan // 2, beam.n_chan - 1))
+    units = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
+    tr_bytes = 2 * beam.n_chan * beam.n_samp
+    line = {
+        "metric": METRIC, "value": units / t_e2e, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_e2e * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "frontend: " + _describe(beam) + "; time-major host input",
+                   "path": "pinned host -> device, transpose, dedisperse, device -> pinned host"},
+        "transpose": {"ms": t_tr * 1e3, "bytes": tr_bytes,
+                      "roofline": {"bound": "hbm", "achieved": tr_bytes / t_tr / 1e9,
+                                   "peak": HBM_GBS, "unit": "GB/s",
+                                   "frac": tr_bytes / t_tr / 1e9 / HBM_GBS,
+                                   "traffic": None},
+                      "rows_equal_definition": bool(same)},
+        "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 _SHIFT_CACHE = {}
 
 
@@ -520,7 +584,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_u8",
-                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32", "batched", "stream"])
+                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32", "batched", "stream",
+                             "frontend"])
     ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
     ap.add_argument("--stream-seconds", type=float, default=15.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
@@ -541,6 +606,8 @@ def main():
         run_batched(args)
     elif args.workload == "stream":
         run_stream(args)
+    elif args.workload == "frontend":
+        run_frontend(args)
     else:
         run_ours(args)
 

@@ -185,6 +185,32 @@ dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64
 dd_status dd_plan_device_status(dd_plan plan, void* stream);
 
 /*
+ * Front end: time-major samples d_in[t][c] (the order a receiver or a SIGPROC
+ * filterbank delivers; row stride in_row_stride >= n_chan elements) to the
+ * channel-major rows d_out[c][t] the transform reads (row stride
+ * out_row_stride elements), for t in [t_begin, t_end) and c < n_chan; other
+ * elements of d_out are not written.  Both buffers 16-byte aligned with
+ * 16-byte multiple row strides, t_begin a multiple of 4 / sample bytes,
+ * t_end <= out_row_stride.  Exact (a permutation); asynchronous on `stream`.
+ * The paper's pipeline transposes its input before dedispersion (Sec. 5.4).
+ * Errors: DD_ERR_INVALID_ARG, DD_ERR_SHAPE.
+ */
+dd_status dd_transpose(dd_dtype dtype, const void* d_in, int64_t in_row_stride, int32_t n_chan,
+                       void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
+                       void* stream);
+
+/*
+ * dd_run_host for time-major host input h_in[t][c] (row stride in_row_stride
+ * >= n_chan): each segment is copied to the time-major staging buffer
+ * d_tm_stage (same layout as h_in), transposed into the channel-major staging
+ * buffer d_cm_stage (row stride cm_row_stride >= n_samp) and dedispersed, with
+ * the same overlap of copies and kernels as dd_run_host.
+ */
+dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stride,
+                             int64_t n_samp, void* h_out, void* d_tm_stage, void* d_cm_stage,
+                             int64_t cm_row_stride, void* d_out_stage, void* stream);
+
+/*
  * End-to-end forward from HOST buffers: copies h_in (pinned host memory,
  * [n_chan][in_row_stride]) to the caller's device staging buffer d_in_stage,
  * computes the transform into d_out_stage and copies the output planes back to
@@ -193,8 +219,9 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream);
  * segments 0..k, and their copy out run on internal copy streams and on
  * `stream` alternating with an internal compute stream, so copies overlap the
  * kernels.  The internal streams and events
- * are created on the first call (per device) and released by dd_plan_destroy.
- * When `stream` completes, h_out is written.  Staging buffers have the same
+ * are created on the first call (per device) and released by dd_plan_destroy;
+ * concurrent calls enqueue one after the other.  When `stream` completes,
+ * h_out is written.  Staging buffers have the same
  * layout rules as dd_run.  Returns once the work is enqueued.
  */
 dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,

@@ -246,5 +246,16 @@ def adjoint_channels(ybar_planes, n_chan: int, n_samp: int, freqs, f_ref: float,
     return out
 
 
+def transpose(x_tm: np.ndarray) -> np.ndarray:
+    """Front end of the paper's pipeline (Sec. 5.4): time-major samples
+    x_tm[t][c] to channel-major rows x[c][t], the order Eq. 3 sums along.
+    The definition written out: element (c, t) of the result is x_tm[t, c]."""
+    n_samp, n_chan = x_tm.shape
+    out = np.empty((n_chan, n_samp), dtype=x_tm.dtype)
+    for c in range(n_chan):
+        out[c, :] = x_tm[:, c]
+    return out
+
+
 def threads() -> int:
     return int(_load().oracle_threads())

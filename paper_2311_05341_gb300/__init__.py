@@ -31,6 +31,26 @@ def build(force: bool = False) -> str:
     return builder.build(force=force)
 
 
+def transpose(x_tm, n_chan: int | None = None, out=None, t_begin: int = 0,
+              t_end: int | None = None, stream=None):
+    """Time-major cuda tensor x_tm [n_samp][stride >= n_chan] -> channel-major
+    [n_chan][stride' >= n_samp] (dd_transpose); rows of `out` padded to 16 bytes."""
+    import torch
+    names = {v: k for k, v in _TORCH_DTYPE_NAMES.items()}
+    dt = names[str(x_tm.dtype).replace("torch.", "")]
+    n_samp = x_tm.shape[0]
+    nc = x_tm.shape[1] if n_chan is None else int(n_chan)
+    if out is None:
+        per = 16 // x_tm.element_size()
+        out = torch.zeros((nc, (n_samp + per - 1) // per * per), dtype=x_tm.dtype,
+                          device=x_tm.device)
+    te = n_samp if t_end is None else int(t_end)
+    check(_lib.load().dd_transpose(DTYPES[dt], x_tm.data_ptr(), x_tm.stride(0), nc,
+                                   out.data_ptr(), out.stride(0), int(t_begin), te,
+                                   _stream_ptr(stream)))
+    return out
+
+
 def _stream_ptr(stream) -> int:
     import torch
     if stream is None:
@@ -162,6 +182,17 @@ class Plan:
         check(self._lib.dd_run_adjoint(self._h, ybar_flat.data_ptr(), xbar.data_ptr(), int(n_samp),
                                        xbar.stride(0), _stream_ptr(stream)))
         return xbar[:, :n_samp]
+
+    def run_host_tmajor(self, h_in, h_out, d_tm_stage, d_cm_stage, d_out_stage,
+                        n_samp: int | None = None, stream=None):
+        """Host-to-host forward from time-major input h_in [n_samp][stride >= n_chan]
+        (pinned), staged in d_tm_stage (same shape) and transposed into d_cm_stage
+        [n_chan][stride >= n_samp]."""
+        n = h_in.shape[0] if n_samp is None else int(n_samp)
+        check(self._lib.dd_run_host_tmajor(self._h, h_in.data_ptr(), h_in.stride(0), n,
+                                           h_out.data_ptr(), d_tm_stage.data_ptr(),
+                                           d_cm_stage.data_ptr(), d_cm_stage.stride(0),
+                                           d_out_stage.data_ptr(), _stream_ptr(stream)))
 
     def run_host(self, h_in, h_out, d_in_stage, d_out_stage, n_samp: int | None = None,
                  stream=None):

@@ -66,6 +66,8 @@ SIGNATURES = {
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
     "dd_run_u8_noalloc": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
+    "dd_run_host_tmajor": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _I64, _VP, _VP]),
+    "dd_transpose": (ctypes.c_int, [ctypes.c_int, _VP, _I64, _I32, _VP, _I64, _I64, _I64, _VP]),
     "dd_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_I64), _I32,
                                        ctypes.POINTER(_VP)]),
     "dd_batch_destroy": (ctypes.c_int, [_VP]),

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -69,20 +70,22 @@ constexpr int kHostSegments = 16;
 
 struct HostPipe {
   int device = -1;
-  cudaStream_t s_in = nullptr, s_out = nullptr, s_comp = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr, s_comp = nullptr, s_tr = nullptr;
   cudaEvent_t start = nullptr, done = nullptr;
-  cudaEvent_t in[kHostSegments] = {}, comp[kHostSegments] = {};
+  cudaEvent_t in[kHostSegments] = {}, comp[kHostSegments] = {}, tr[kHostSegments] = {};
 };
 
 void destroy_pipe(HostPipe* hp) {
   if (hp->s_in) cudaStreamDestroy(hp->s_in);
   if (hp->s_out) cudaStreamDestroy(hp->s_out);
   if (hp->s_comp) cudaStreamDestroy(hp->s_comp);
+  if (hp->s_tr) cudaStreamDestroy(hp->s_tr);
   for (cudaEvent_t e : {hp->start, hp->done})
     if (e) cudaEventDestroy(e);
   for (int k = 0; k < kHostSegments; ++k) {
     if (hp->in[k]) cudaEventDestroy(hp->in[k]);
     if (hp->comp[k]) cudaEventDestroy(hp->comp[k]);
+    if (hp->tr[k]) cudaEventDestroy(hp->tr[k]);
   }
   delete hp;
 }
@@ -105,11 +108,13 @@ cudaError_t host_pipe(dd_plan_s* p, HostPipe** out) {
   e = cudaStreamCreateWithFlags(&hp->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_tr, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->done, cudaEventDisableTiming);
   for (int k = 0; k < kHostSegments && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&hp->in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->comp[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->tr[k], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     destroy_pipe(hp);
@@ -318,27 +323,33 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream) {
   return DD_OK;
 }
 
-dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
-                      void* h_out, void* d_in_stage, void* d_out_stage, void* stream) {
-  if (!h_in || !h_out) return fail(DD_ERR_INVALID_ARG, "h_in or h_out is NULL");
-  dd_plan_info info;
-  dd_status st = check_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, &info);
-  if (st != DD_OK) return st;
+// The segmented host pipeline of dd_run_host (tm == nullptr: h_in is
+// channel-major with row stride cm_stride, copied straight into d_cm) and
+// dd_run_host_tmajor (h_in is time-major with row stride tm_stride, copied
+// into d_tm and transposed into d_cm on its own stream).
+static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const void* h_in,
+                                   int64_t tm_stride, void* d_tm, int64_t n_samp, void* h_out,
+                                   void* d_cm, int64_t cm_stride, void* d_out_stage,
+                                   void* stream) {
+  // The plan's copy streams and events are shared: calls from several host
+  // threads enqueue one after the other (each wait captures its own record).
+  static std::mutex host_mu;
+  std::lock_guard<std::mutex> lock(host_mu);
   HostPipe* hp = nullptr;
   cudaError_t e = host_pipe(plan, &hp);
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_host streams");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t esz = elem_size(plan->dtype);
-  const size_t pitch_in = static_cast<size_t>(in_row_stride) * esz;
+  const bool tmajor = d_tm != nullptr;
   const unsigned char* hin = static_cast<const unsigned char*>(h_in);
-  unsigned char* din = static_cast<unsigned char*>(d_in_stage);
+  unsigned char* dtm = static_cast<unsigned char*>(d_tm);
+  unsigned char* dcm = static_cast<unsigned char*>(d_cm);
   unsigned char* hout = static_cast<unsigned char*>(h_out);
   unsigned char* dout = static_cast<unsigned char*>(d_out_stage);
-  // The copy streams start after the caller's earlier work on `stream`.
+  // The other streams start after the caller's earlier work on `stream`.
   e = cudaEventRecord(hp->start, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_in, hp->start, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_out, hp->start, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_comp, hp->start, 0);
+  for (cudaStream_t o : {hp->s_in, hp->s_out, hp->s_comp, hp->s_tr})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(o, hp->start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
   const int64_t seg = (n_samp + kHostSegments - 1) / kHostSegments;
   const int64_t seg_len = (seg + 255) / 256 * 256;
@@ -348,16 +359,38 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
     const bool last = k == kHostSegments - 1;
     cudaStream_t sc = (k & 1) ? hp->s_comp : s;
     const int64_t raw_end = last ? n_samp : std::min<int64_t>(n_samp, (k + 1) * seg_len);
-    // Segment k of the raw samples, every channel (a strided 2-D copy).
+    // Segment k of the raw samples, every channel.
+    cudaEvent_t ready = hp->in[k];
     if (raw_end > raw_done) {
-      e = cudaMemcpy2DAsync(din + raw_done * esz, pitch_in, hin + raw_done * esz, pitch_in,
-                            static_cast<size_t>(raw_end - raw_done) * esz, plan->n_chan,
+      if (tmajor) {  // whole time rows: one contiguous block
+        const size_t pitch = static_cast<size_t>(tm_stride) * esz;
+        e = cudaMemcpyAsync(dtm + raw_done * pitch, hin + raw_done * pitch,
+                            static_cast<size_t>(raw_end - raw_done) * pitch,
                             cudaMemcpyHostToDevice, hp->s_in);
+      } else {       // a column block of every channel row (a strided 2-D copy)
+        const size_t pitch = static_cast<size_t>(cm_stride) * esz;
+        e = cudaMemcpy2DAsync(dcm + raw_done * esz, pitch, hin + raw_done * esz, pitch,
+                              static_cast<size_t>(raw_end - raw_done) * esz, plan->n_chan,
+                              cudaMemcpyHostToDevice, hp->s_in);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "dd_run_host input copy");
-      raw_done = raw_end;
     }
     e = cudaEventRecord(hp->in[k], hp->s_in);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, hp->in[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    if (tmajor) {  // transposes run in order on one stream
+      e = cudaStreamWaitEvent(hp->s_tr, hp->in[k], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      if (raw_end > raw_done) {
+        const int le = launch_transpose(static_cast<int>(esz), dtm, tm_stride, plan->n_chan, dcm,
+                                        cm_stride, raw_done, raw_end, hp->s_tr);
+        if (le != 0) return cuda_fail(le, "dd_run_host transpose");
+      }
+      e = cudaEventRecord(hp->tr[k], hp->s_tr);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      ready = hp->tr[k];
+    }
+    raw_done = std::max(raw_done, raw_end);
+    e = cudaStreamWaitEvent(sc, ready, 0);
     if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
     // Every output whose dispersion track ends inside the samples copied so
     // far: t + S_max < raw_end / bin, whole time tiles except at the end.
@@ -373,7 +406,7 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
       }
       lim[r] = l;
       if (l > done[r]) {
-        const int le = launch_range(plan, rp, din, in_row_stride, n_samp, n_out,
+        const int le = launch_range(plan, rp, dcm, cm_stride, n_samp, n_out,
                                     dout + info.out_offset[r] * 4, done[r], l, sc);
         if (le != 0) return cuda_fail(le, "dd_run_host forward launch");
       }
@@ -399,6 +432,62 @@ dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
   return DD_OK;
+}
+
+dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
+                      void* h_out, void* d_in_stage, void* d_out_stage, void* stream) {
+  if (!h_in || !h_out) return fail(DD_ERR_INVALID_ARG, "h_in or h_out is NULL");
+  dd_plan_info info;
+  dd_status st = check_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, &info);
+  if (st != DD_OK) return st;
+  return run_host_pipeline(plan, info, h_in, 0, nullptr, n_samp, h_out, d_in_stage,
+                           in_row_stride, d_out_stage, stream);
+}
+
+static dd_status check_transpose(size_t esz, const void* d_in, int64_t in_row_stride,
+                                 int32_t n_chan, const void* d_out, int64_t out_row_stride,
+                                 int64_t t_begin, int64_t t_end) {
+  if (!d_in || !d_out) return fail(DD_ERR_INVALID_ARG, "d_in or d_out is NULL");
+  if (n_chan <= 0 || in_row_stride < n_chan || t_begin < 0 || t_end < t_begin ||
+      t_end > out_row_stride)
+    return fail(DD_ERR_SHAPE, "need n_chan <= in_row_stride and 0 <= t_begin <= t_end <= "
+                              "out_row_stride");
+  if (!aligned16(d_in) || !aligned16(d_out) ||
+      (in_row_stride * static_cast<int64_t>(esz)) % 16 != 0 ||
+      (out_row_stride * static_cast<int64_t>(esz)) % 16 != 0)
+    return fail(DD_ERR_SHAPE, "buffers and row strides must be 16-byte aligned");
+  if (t_begin % static_cast<int64_t>(4 / esz) != 0)
+    return fail(DD_ERR_SHAPE, "t_begin must be a multiple of 4 / sample bytes");
+  return DD_OK;
+}
+
+dd_status dd_transpose(dd_dtype dtype, const void* d_in, int64_t in_row_stride, int32_t n_chan,
+                       void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
+                       void* stream) {
+  if (dtype != DD_U8 && dtype != DD_U16 && dtype != DD_F32)
+    return fail(DD_ERR_INVALID_ARG, "unknown dtype");
+  const size_t esz = elem_size(dtype);
+  dd_status st = check_transpose(esz, d_in, in_row_stride, n_chan, d_out, out_row_stride,
+                                 t_begin, t_end);
+  if (st != DD_OK) return st;
+  const int e = launch_transpose(static_cast<int>(esz), d_in, in_row_stride, n_chan, d_out,
+                                 out_row_stride, t_begin, t_end, stream);
+  if (e != 0) return cuda_fail(e, "dd_transpose launch");
+  return DD_OK;
+}
+
+dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stride,
+                             int64_t n_samp, void* h_out, void* d_tm_stage, void* d_cm_stage,
+                             int64_t cm_row_stride, void* d_out_stage, void* stream) {
+  if (!h_in || !h_out || !d_tm_stage) return fail(DD_ERR_INVALID_ARG, "NULL buffer");
+  dd_plan_info info;
+  dd_status st = check_run(plan, d_cm_stage, cm_row_stride, n_samp, d_out_stage, &info);
+  if (st != DD_OK) return st;
+  st = check_transpose(elem_size(plan->dtype), d_tm_stage, in_row_stride, plan->n_chan,
+                       d_cm_stage, cm_row_stride, 0, n_samp);
+  if (st != DD_OK) return st;
+  return run_host_pipeline(plan, info, h_in, in_row_stride, d_tm_stage, n_samp, h_out,
+                           d_cm_stage, cm_row_stride, d_out_stage, stream);
 }
 
 }  // extern "C"

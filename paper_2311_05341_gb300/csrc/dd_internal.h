@@ -105,6 +105,10 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                            void* d_out, int64_t t_begin, int64_t t_end, void* stream);
+// Time-major [t][c] to channel-major [c][t] for t in [t_begin, t_end) (transpose.cu).
+int launch_transpose(int elem_bytes, const void* d_in, int64_t in_row_stride, int32_t n_chan,
+                     void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
+                     void* stream);
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream);

@@ -431,3 +431,15 @@ def test_adjoint_channels_are_rows_of_full_adjoint(oracle_mod, synth_mod):
     full = oracle_mod.adjoint(ys, 5, 60, freqs, f_ref, ts, ranges)
     part = oracle_mod.adjoint_channels(ys, 5, 60, freqs, f_ref, ts, ranges, [4, 0, 2])
     np.testing.assert_array_equal(part, full[[4, 0, 2]])
+
+
+def test_transpose_pins(oracle_mod):
+    """The front-end transpose: a hand-written 2 x 3 case, the involution, and
+    a channel row equal to the strided column of the time-major array."""
+    x = np.array([[1, 2, 3], [4, 5, 6]], dtype=np.uint8)  # 2 times x 3 channels
+    np.testing.assert_array_equal(oracle_mod.transpose(x), [[1, 4], [2, 5], [3, 6]])
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((37, 11)).astype(np.float32)
+    np.testing.assert_array_equal(oracle_mod.transpose(oracle_mod.transpose(y)), y)
+    z = rng.integers(0, 65536, (50, 9)).astype(np.uint16)
+    assert list(oracle_mod.transpose(z)[4]) == [int(z[t, 4]) for t in range(50)]
