@@ -24,9 +24,27 @@ _SRC = os.path.join(_HERE, "dd_oracle.c")
 _HDR = os.path.join(_HERE, "dd_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-DTYPE_U8, DTYPE_U16, DTYPE_F32 = 1, 2, 3
+DTYPE_U8, DTYPE_U16, DTYPE_F32, DTYPE_U4 = 1, 2, 3, 4
 _NP_DTYPE = {np.dtype(np.uint8): DTYPE_U8, np.dtype(np.uint16): DTYPE_U16,
              np.dtype(np.float32): DTYPE_F32}
+
+
+class Packed4:
+    """4-bit samples packed two per byte: sample 2k of a row in the low nibble
+    of byte k, sample 2k + 1 in the high nibble.  data is uint8
+    [n_chan][row_bytes] (time contiguous); each row holds n_samp samples."""
+
+    def __init__(self, data: np.ndarray, n_samp: int):
+        if data.dtype != np.uint8 or data.ndim != 2 or data.strides[1] != 1:
+            raise ValueError("packed 4-bit data must be uint8 [n_chan][row_bytes]")
+        if n_samp > 2 * data.shape[1]:
+            raise ValueError("n_samp exceeds the packed row")
+        self.data = data
+        self.shape = (data.shape[0], int(n_samp))
+
+    @property
+    def ctypes(self):
+        return self.data.ctypes
 
 _lock = threading.Lock()
 _lib = None
@@ -158,7 +176,11 @@ def extent(freqs, f_ref: float, t_samp: float, r, n_samp: int):
     return int(smax[0]), int(nout[0])
 
 
-def _input(x: np.ndarray):
+def _input(x):
+    if isinstance(x, Packed4):
+        d = x.data
+        row_bytes = d.strides[0] if d.shape[0] > 1 else d.shape[1]
+        return DTYPE_U4, 2 * row_bytes
     if x.ndim != 2:
         raise ValueError("x must be [n_chan][n_samp]")
     if x.dtype not in _NP_DTYPE:

@@ -97,9 +97,14 @@ int oracle_range_extent(const double* freqs_mhz, int32_t n_chan, double f_ref_mh
   return 0;
 }
 
-/* One raw sample as int64 / FP64. */
+/* One raw sample as int64.  idx counts samples; 4-bit samples are packed two
+ * per byte, sample 2k in the low nibble of byte k and 2k+1 in the high one. */
 static inline int64_t load_int(int dtype, const void* x, int64_t idx) {
   if (dtype == ORACLE_DTYPE_U8) return (int64_t)((const uint8_t*)x)[idx];
+  if (dtype == ORACLE_DTYPE_U4) {
+    const uint8_t byte = ((const uint8_t*)x)[idx / 2];
+    return (int64_t)((idx % 2 == 0) ? (byte & 0x0f) : (byte >> 4));
+  }
   return (int64_t)((const uint16_t*)x)[idx];
 }
 
@@ -108,9 +113,11 @@ int oracle_forward_rows(int dtype, const void* x, int32_t n_chan, int64_t n_samp
                         double t_samp_s, oracle_range r, const int64_t* rows,
                         int64_t n_rows, int64_t t_begin, int64_t t_end, int take_abs,
                         double* out) {
-  if (dtype != ORACLE_DTYPE_U8 && dtype != ORACLE_DTYPE_U16 && dtype != ORACLE_DTYPE_F32)
+  if (dtype != ORACLE_DTYPE_U8 && dtype != ORACLE_DTYPE_U16 && dtype != ORACLE_DTYPE_F32 &&
+      dtype != ORACLE_DTYPE_U4)
     return -1;
   if (!x || !rows || !out || n_rows < 0 || row_stride < n_samp) return -1;
+  if (dtype == ORACLE_DTYPE_U4 && row_stride % 2 != 0) return -1;
   int64_t s_max = 0, n_out = 0;
   if (oracle_range_extent(freqs_mhz, n_chan, f_ref_mhz, t_samp_s, r, n_samp, &s_max,
                           &n_out) != 0)

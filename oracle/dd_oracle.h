@@ -34,6 +34,7 @@ extern "C" {
 #define ORACLE_DTYPE_U8 1
 #define ORACLE_DTYPE_U16 2
 #define ORACLE_DTYPE_F32 3
+#define ORACLE_DTYPE_U4 4  /* two samples per byte, the earlier one in the low nibble */
 
 typedef struct {
   double dm_lo;   /* first trial DM, pc cm^-3 */
@@ -71,7 +72,8 @@ int oracle_range_extent(const double* freqs_mhz, int32_t n_chan, double f_ref_mh
  * Direct transform (Eq. 3, Algorithm 1) of one range on selected DM rows and a
  * time window [t_begin, t_end) of output samples:
  *   out[i][t - t_begin] = sum_c X_b[c][t + s(c, rows[i])]
- * x is channel-major [n_chan][row_stride] of the given dtype.  Integer inputs
+ * x is channel-major [n_chan][row_stride] of the given dtype (row_stride and
+ * n_samp count samples; 4-bit rows are row_stride / 2 bytes).  Integer inputs
  * are summed in int64, float inputs in FP64; out is FP64 in both cases (every
  * integer sum here is far below 2^53).  If take_abs is non-zero, |X| is summed
  * instead (used for the float tolerance bound).  OpenMP over rows.

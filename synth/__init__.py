@@ -127,3 +127,28 @@ def pick_pulses(seed: int, n_pulses: int, n_dm: int, n_out: int, w_lo: int = 1,
         w = int(rng.integers(w_lo, w_hi + 1))
         out.append((d, t0, w))
     return out
+
+
+def pack4(x: np.ndarray) -> np.ndarray:
+    """Pack 4-bit samples (uint8 values 0..15, [n_chan][n], n even) two per
+    byte: sample 2k in the low nibble of byte k, 2k + 1 in the high nibble."""
+    if x.shape[1] % 2:
+        raise ValueError("pack4 needs an even number of samples per row")
+    lo = x[:, 0::2].astype(np.uint8) & 0x0F
+    hi = x[:, 1::2].astype(np.uint8) & 0x0F
+    return np.ascontiguousarray(lo | (hi << 4))
+
+
+def filterbank4(n_chan: int, n_samp: int, seed: int, mean: float, sd: float, pulses=(),
+                row_bytes: int | None = None) -> np.ndarray:
+    """Packed 4-bit filterbank: the uint8 generator's samples clamped to 0..15,
+    packed by pack4 into [n_chan][row_bytes] bytes (row_bytes >= n_samp / 2)."""
+    n_even = n_samp + (n_samp % 2)
+    x = filterbank(np.uint8, n_chan, n_even, seed, mean, sd, pulses=pulses)
+    x = np.minimum(x, 15).astype(np.uint8)
+    packed = pack4(x)
+    if row_bytes is not None and row_bytes != packed.shape[1]:
+        out = np.zeros((n_chan, row_bytes), np.uint8)
+        out[:, : packed.shape[1]] = packed
+        packed = out
+    return packed
