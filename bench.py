@@ -44,7 +44,8 @@ def _workload(name, n_samp=None):
     import dataclasses
     from synth import workloads
     beam = {"paper_u8": workloads.paper_u8, "paper_u16": workloads.paper_u16,
-            "tiny_u8": workloads.tiny_u8, "diff_f32": workloads.diff_f32}[name]()
+            "paper_u4": workloads.paper_u4, "tiny_u8": workloads.tiny_u8,
+            "diff_f32": workloads.diff_f32}[name]()
     if n_samp:  # a shorter observation of the same plan (profiler captures)
         beam = dataclasses.replace(beam, n_samp=int(n_samp))
     return beam
@@ -189,8 +190,10 @@ def run_ours(args):
             tables[r] = plan.shifts(r)
         return tables[r][d]
 
-    per = 16 // np.dtype(beam.np_dtype).itemsize  # rows start 16-byte aligned
+    # Rows start 16-byte aligned; strides count samples (two per byte for "u4").
+    per = 32 if beam.dtype == "u4" else 16 // np.dtype(beam.np_dtype).itemsize
     row_stride = (beam.n_samp + per - 1) // per * per
+    spe = 2 if beam.dtype == "u4" else 1  # samples per buffer element
     x_host = workloads.make_input(beam, shift_rows, info["n_dm"], info["n_out"],
                                   row_stride=row_stride)
     x = torch.from_numpy(x_host).cuda()
@@ -199,7 +202,7 @@ def run_ours(args):
     sp = stream.cuda_stream
 
     def step():
-        plan.run_raw(x.data_ptr(), x.stride(0), beam.n_samp, out.data_ptr(), sp)
+        plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp)
 
     for _ in range(args.warmup):
         step()
@@ -256,10 +259,10 @@ def run_ours(args):
     # sub-partitions; float adds on both 16-lane float pipes).
     sample_adds_per_s = chan_adds / (total / args.steps)
     sms = peaks["sm_count"]
-    per_lane = {"u8": 4, "u16": 2, "f32": 1}[beam.dtype]
+    per_lane = {"u8": 4, "u4": 4, "u16": 2, "f32": 1}[beam.dtype]
     lanes = 128 if beam.dtype == "f32" else 64  # lane-ops per clock per SM
     peak_adds = lanes * sms * SM_MAX_MHZ * 1e6 * per_lane
-    algo_bytes = (beam.n_chan * beam.n_samp * np.dtype(beam.np_dtype).itemsize
+    algo_bytes = (beam.n_chan * beam.n_samp * np.dtype(beam.np_dtype).itemsize // spe
                   + info["out_elems"] * 4)
     traffic = TRAFFIC.get((args.workload, beam.n_samp, tuple(info["tile_dms"])))
     roofline = {
@@ -282,7 +285,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"u8": "int32", "u16": "int32", "f32": "f32"}[beam.dtype],
+        "dtype": {"u8": "int32", "u4": "int32", "u16": "int32", "f32": "f32"}[beam.dtype],
         "data": "synthetic",
         "config": {"workload": _describe(beam), "n_dm": info["n_dm_total"],
                    "n_out": info["n_out"],
@@ -307,7 +310,8 @@ def cpu_baseline(beam, x_host, info, n_rows):
     import oracle
     rows = np.linspace(0, info["n_dm"][0] - 1, n_rows).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.forward_rows(x_host, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
+    x = oracle.Packed4(x_host, beam.n_samp) if beam.dtype == "u4" else x_host
+    oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
     sec = time.perf_counter() - t0
     units = n_rows * info["n_out"][0]
     return {"value": units / sec, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
@@ -328,6 +332,8 @@ def run_reference(args):
     n_out = [oracle.extent(beam.freqs, beam.f_high, beam.t_samp, r, beam.n_samp)[1]
              for r in beam.ranges]
     x = workloads.make_input(beam, lambda r, d: tables[r][d], n_dm, n_out)
+    if beam.dtype == "u4":
+        x = oracle.Packed4(x, beam.n_samp)
     info = {"n_dm": n_dm, "n_out": n_out}
     n_rows = args.cpu_rows_reference
     rows = np.linspace(0, n_dm[0] - 1, n_rows).astype(np.int64)
@@ -584,8 +590,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_u8",
-                    choices=["paper_u8", "paper_u16", "tiny_u8", "diff_f32", "batched", "stream",
-                             "frontend"])
+                    choices=["paper_u8", "paper_u16", "paper_u4", "tiny_u8", "diff_f32", "batched",
+                             "stream", "frontend"])
     ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
     ap.add_argument("--stream-seconds", type=float, default=15.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=100.0)

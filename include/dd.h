@@ -54,7 +54,10 @@ typedef enum {
   DD_ERR_TIMEOUT = 6      /* a bounded device wait gave up */
 } dd_status;
 
-typedef enum { DD_U8 = 1, DD_U16 = 2, DD_F32 = 3 } dd_dtype;
+/* Sample types.  DD_U4: 4-bit unsigned samples packed two per byte, the
+ * earlier sample in the low nibble; row strides and n_samp still count
+ * samples (a row is row_stride / 2 bytes, row_stride a multiple of 32). */
+typedef enum { DD_U8 = 1, DD_U16 = 2, DD_F32 = 3, DD_U4 = 4 } dd_dtype;
 
 /* One DM range: trial DMs lo, lo+step, ... (n = llround((hi-lo)/step) of
  * them, half-open like Table 2), dedispersed at time bin `bin` (>= 1). */

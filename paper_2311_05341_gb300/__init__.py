@@ -21,8 +21,13 @@ from ._lib import DDError, check
 
 __all__ = ["Plan", "DDError", "build", "DTYPES"]
 
-DTYPES = {"u8": _lib.DD_U8, "u16": _lib.DD_U16, "f32": _lib.DD_F32}
-_TORCH_DTYPE_NAMES = {"u8": "uint8", "u16": "uint16", "f32": "float32"}
+DTYPES = {"u8": _lib.DD_U8, "u16": _lib.DD_U16, "f32": _lib.DD_F32, "u4": _lib.DD_U4}
+# Torch element type of each dtype's buffers ("u4": packed bytes, two samples each).
+_TORCH_DTYPE_NAMES = {"u8": "uint8", "u16": "uint16", "f32": "float32", "u4": "uint8"}
+
+
+def _samples_per_elem(dtype: str) -> int:
+    return 2 if dtype == "u4" else 1
 
 
 def build(force: bool = False) -> str:
@@ -36,7 +41,7 @@ def transpose(x_tm, n_chan: int | None = None, out=None, t_begin: int = 0,
     """Time-major cuda tensor x_tm [n_samp][stride >= n_chan] -> channel-major
     [n_chan][stride' >= n_samp] (dd_transpose); rows of `out` padded to 16 bytes."""
     import torch
-    names = {v: k for k, v in _TORCH_DTYPE_NAMES.items()}
+    names = {"uint8": "u8", "uint16": "u16", "float32": "f32"}
     dt = names[str(x_tm.dtype).replace("torch.", "")]
     n_samp = x_tm.shape[0]
     nc = x_tm.shape[1] if n_chan is None else int(n_chan)
@@ -159,12 +164,15 @@ class Plan:
                 for o, nd, no in zip(inf["out_offset"], inf["n_dm"], inf["n_out"])]
 
     def run(self, x, out=None, n_samp: int | None = None, stream=None):
-        """Forward transform of a cuda tensor x [n_chan][stride] -> list of planes."""
+        """Forward transform of a cuda tensor x [n_chan][stride] -> list of planes.
+
+        For "u4" plans x holds packed bytes [n_chan][stride / 2]."""
         self._check_input(x)
-        n = x.shape[1] if n_samp is None else int(n_samp)
+        per = _samples_per_elem(self.dtype)
+        n = x.shape[1] * per if n_samp is None else int(n_samp)
         if out is None:
             out = self.empty_output(n, x.device)
-        check(self._lib.dd_run(self._h, x.data_ptr(), x.stride(0), n, out.data_ptr(),
+        check(self._lib.dd_run(self._h, x.data_ptr(), x.stride(0) * per, n, out.data_ptr(),
                                _stream_ptr(stream)))
         return self.split(out, n)
 
@@ -197,8 +205,9 @@ class Plan:
     def run_host(self, h_in, h_out, d_in_stage, d_out_stage, n_samp: int | None = None,
                  stream=None):
         """Host-to-host forward through pinned host buffers and device staging."""
-        n = h_in.shape[1] if n_samp is None else int(n_samp)
-        check(self._lib.dd_run_host(self._h, h_in.data_ptr(), h_in.stride(0), n,
+        per = _samples_per_elem(self.dtype)
+        n = h_in.shape[1] * per if n_samp is None else int(n_samp)
+        check(self._lib.dd_run_host(self._h, h_in.data_ptr(), h_in.stride(0) * per, n,
                                     h_out.data_ptr(), d_in_stage.data_ptr(),
                                     d_out_stage.data_ptr(), _stream_ptr(stream)))
 

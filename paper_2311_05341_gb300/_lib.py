@@ -16,7 +16,7 @@ _lib = None
 
 DD_OK, DD_ERR_INVALID_ARG, DD_ERR_UNSUPPORTED, DD_ERR_SHAPE = 0, 1, 2, 3
 DD_ERR_BUDGET, DD_ERR_CUDA, DD_ERR_TIMEOUT = 4, 5, 6
-DD_U8, DD_U16, DD_F32 = 1, 2, 3
+DD_U8, DD_U16, DD_F32, DD_U4 = 1, 2, 3, 4
 DD_MAX_RANGES = 16
 DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 DD_TILE_PATTERN = 0x104

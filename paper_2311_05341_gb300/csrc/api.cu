@@ -32,7 +32,11 @@ dd_status cuda_fail(int err, const char* what) {
 
 namespace {
 
-size_t elem_size(dd_dtype t) { return t == DD_U8 ? 1 : (t == DD_U16 ? 2 : 4); }
+size_t elem_size(dd_dtype t) { return (t == DD_U8 || t == DD_U4) ? 1 : (t == DD_U16 ? 2 : 4); }
+// Bytes of n samples of a dtype (4-bit: two per byte, rounded up).
+size_t row_bytes(dd_dtype t, int64_t n) {
+  return t == DD_U4 ? static_cast<size_t>((n + 1) / 2) : static_cast<size_t>(n) * elem_size(t);
+}
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -178,7 +182,7 @@ dd_status dd_plan_create(const double* freqs_mhz, int32_t n_chan, double f_ref_m
   if (n_chan <= 0 || n_chan > (1 << 20)) return fail(DD_ERR_INVALID_ARG, "n_chan out of range");
   if (n_ranges <= 0 || n_ranges > DD_MAX_RANGES)
     return fail(DD_ERR_INVALID_ARG, "n_ranges must be in [1, DD_MAX_RANGES]");
-  if (dtype != DD_U8 && dtype != DD_U16 && dtype != DD_F32)
+  if (dtype != DD_U8 && dtype != DD_U16 && dtype != DD_F32 && dtype != DD_U4)
     return fail(DD_ERR_INVALID_ARG, "unknown dtype");
   if (!(t_samp_s > 0.0) || !std::isfinite(t_samp_s)) return fail(DD_ERR_INVALID_ARG, "t_samp must be > 0");
   if (!(f_ref_mhz > 0.0) || !std::isfinite(f_ref_mhz)) return fail(DD_ERR_INVALID_ARG, "f_ref must be > 0");
@@ -270,7 +274,8 @@ static dd_status check_run(dd_plan plan, const void* d_in, int64_t stride, int64
   if (!plan->d_ws) return fail(DD_ERR_INVALID_ARG, "plan has no uploaded workspace");
   if (n_samp <= 0 || stride < n_samp) return fail(DD_ERR_SHAPE, "need 0 < n_samp <= row stride");
   if (!aligned16(d_in) || !aligned16(d_out)) return fail(DD_ERR_SHAPE, "d_in/d_out must be 16-byte aligned");
-  if ((stride * static_cast<int64_t>(elem_size(plan->dtype))) % 16 != 0)
+  if (plan->dtype == DD_U4 ? stride % 32 != 0
+                            : (stride * static_cast<int64_t>(elem_size(plan->dtype))) % 16 != 0)
     return fail(DD_ERR_SHAPE, "row stride must be a multiple of 16 bytes");
   fill_info(plan, n_samp, info);
   for (int32_t i = 0; i < info->n_ranges; ++i)
@@ -368,9 +373,10 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
                             static_cast<size_t>(raw_end - raw_done) * pitch,
                             cudaMemcpyHostToDevice, hp->s_in);
       } else {       // a column block of every channel row (a strided 2-D copy)
-        const size_t pitch = static_cast<size_t>(cm_stride) * esz;
-        e = cudaMemcpy2DAsync(dcm + raw_done * esz, pitch, hin + raw_done * esz, pitch,
-                              static_cast<size_t>(raw_end - raw_done) * esz, plan->n_chan,
+        const size_t pitch = row_bytes(plan->dtype, cm_stride);
+        const size_t b0 = row_bytes(plan->dtype, raw_done);  // raw_done is even
+        e = cudaMemcpy2DAsync(dcm + b0, pitch, hin + b0, pitch,
+                              row_bytes(plan->dtype, raw_end) - b0, plan->n_chan,
                               cudaMemcpyHostToDevice, hp->s_in);
       }
       if (e != cudaSuccess) return cuda_fail(e, "dd_run_host input copy");
@@ -465,7 +471,8 @@ dd_status dd_transpose(dd_dtype dtype, const void* d_in, int64_t in_row_stride, 
                        void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
                        void* stream) {
   if (dtype != DD_U8 && dtype != DD_U16 && dtype != DD_F32)
-    return fail(DD_ERR_INVALID_ARG, "unknown dtype");
+    return fail(dtype == DD_U4 ? DD_ERR_UNSUPPORTED : DD_ERR_INVALID_ARG,
+                "dd_transpose takes uint8, uint16 or float32 samples");
   const size_t esz = elem_size(dtype);
   dd_status st = check_transpose(esz, d_in, in_row_stride, n_chan, d_out, out_row_stride,
                                  t_begin, t_end);
@@ -480,6 +487,8 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
                              int64_t n_samp, void* h_out, void* d_tm_stage, void* d_cm_stage,
                              int64_t cm_row_stride, void* d_out_stage, void* stream) {
   if (!h_in || !h_out || !d_tm_stage) return fail(DD_ERR_INVALID_ARG, "NULL buffer");
+  if (plan && plan->dtype == DD_U4)
+    return fail(DD_ERR_UNSUPPORTED, "time-major input takes uint8, uint16 or float32 samples");
   dd_plan_info info;
   dd_status st = check_run(plan, d_cm_stage, cm_row_stride, n_samp, d_out_stage, &info);
   if (st != DD_OK) return st;

@@ -260,10 +260,11 @@ dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* 
     void* o = d_out[jr.plan];
     const int64_t stride = in_row_stride[jr.plan];
     const int64_t n = batch->n_samp[jr.plan];
-    const size_t esz = p->dtype == DD_U8 ? 1 : (p->dtype == DD_U16 ? 2 : 4);
+    const int64_t stride_bytes = p->dtype == DD_U4 ? stride / 2
+                                 : stride * (p->dtype == DD_U8 ? 1 : (p->dtype == DD_U16 ? 2 : 4));
     if (!x || !o) return fail(DD_ERR_INVALID_ARG, "NULL input or output pointer");
     if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(o) & 15u) ||
-        stride < n || (stride * static_cast<int64_t>(esz)) % 16 != 0)
+        stride < n || stride_bytes % 16 != 0 || (p->dtype == DD_U4 && stride % 2 != 0))
       return fail(DD_ERR_SHAPE, "batch input/output alignment or stride");
     const RangePlan& rp = p->ranges[jr.range];
     const tk::TileParams prm =

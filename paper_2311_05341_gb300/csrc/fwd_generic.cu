@@ -1,5 +1,5 @@
 // fwd_generic.cu -- shared-memory forward dedispersion kernel for every input
-// dtype (uint8, uint16, float32) and every time bin.
+// dtype (uint8, uint16, float32, packed 4-bit) and every time bin.
 //
 // Eq. 3 / Algorithm 1: Y[d][t] = sum_c X_b[c][t + s(c, d)].  The output
 // (DM, t) plane is cut into CTA tiles of kGenDmPerCta DMs x kGenSampPerCta
@@ -22,7 +22,15 @@ namespace dd {
 
 namespace {
 
-template <typename TIn, typename TAcc>
+// Raw sample i of a channel row: 4-bit rows (NIB) hold two samples per byte,
+// the earlier in the low nibble.
+template <typename TIn, typename TAcc, bool NIB>
+__device__ __forceinline__ TAcc raw_sample(const TIn* row, int64_t i) {
+  if constexpr (NIB) return static_cast<TAcc>((row[i >> 1] >> (4 * (i & 1))) & 15);
+  else return static_cast<TAcc>(row[i]);
+}
+
+template <typename TIn, typename TAcc, bool NIB>
 __global__ void __launch_bounds__(256)
 fwd_generic_kernel(const TIn* __restrict__ x, int64_t stride, int32_t n_chan, int32_t bin,
                    int64_t n_dec, const int32_t* __restrict__ shifts, int32_t n_dm,
@@ -57,13 +65,13 @@ fwd_generic_kernel(const TIn* __restrict__ x, int64_t stride, int32_t n_chan, in
       const int32_t c = c0 + cc;
       const int32_t base = shifts[static_cast<int64_t>(d_first) * n_chan + c];
       if (tx == 0) base_buf[cc] = base;
-      const TIn* row = x + static_cast<int64_t>(c) * stride;
+      const TIn* row = x + static_cast<int64_t>(c) * (NIB ? stride / 2 : stride);
       for (int32_t k = tx; k < win; k += 32) {
         const int64_t u = t0 + base + k;  // decimated sample index
         TAcc v = TAcc(0);
         if (u < n_dec) {
           const int64_t raw = u * bin;
-          for (int32_t j = 0; j < bin; ++j) v += static_cast<TAcc>(row[raw + j]);
+          for (int32_t j = 0; j < bin; ++j) v += raw_sample<TIn, TAcc, NIB>(row, raw + j);
         }
         win_buf[cc * win + k] = v;
       }
@@ -95,7 +103,7 @@ fwd_generic_kernel(const TIn* __restrict__ x, int64_t stride, int32_t n_chan, in
   }
 }
 
-template <typename TIn, typename TAcc>
+template <typename TIn, typename TAcc, bool NIB = false>
 int launch_typed(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
                  int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
                  cudaStream_t st) {
@@ -107,7 +115,7 @@ int launch_typed(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int6
   if (chunk < 1) return static_cast<int>(cudaErrorInvalidConfiguration);
   chunk = std::min(chunk, p->n_chan);
   const size_t smem = per_chan * chunk + 16;
-  auto kern = fwd_generic_kernel<TIn, TAcc>;
+  auto kern = fwd_generic_kernel<TIn, TAcc, NIB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -137,6 +145,9 @@ int launch_forward_generic(const dd_plan_s* p, const RangePlan& rp, const void* 
     case DD_U16:
       return launch_typed<uint16_t, int32_t>(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
                                              t_end, st);
+    case DD_U4:
+      return launch_typed<uint8_t, int32_t, true>(p, rp, d_in, stride, n_samp, n_out, d_out,
+                                                  t_begin, t_end, st);
     case DD_F32:
       return launch_typed<float, float>(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin, t_end,
                                         st);

@@ -15,10 +15,14 @@
 namespace dd {
 namespace tk {
 
-// Window-word kinds of the tiled kernels: uint8 at time bin 1 packs two samples
-// per 32-bit word (16-bit lanes); uint8 at a larger bin (kU8W), uint16 and
-// float32 keep one (decimated) sample per word.  Values 1-3 equal dd_dtype.
-enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4 };
+// Window-word kinds of the tiled kernels: uint8 at time bin 1 and 4-bit input
+// at any bin pack two (decimated) samples per 32-bit word (16-bit lanes);
+// uint8 at a larger bin (kU8W), uint16 and float32 keep one (decimated) sample
+// per word.  Values 1-3 equal dd_dtype.
+enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5 };
+
+// Window words pair samples u and u + pair in their 16-bit halves.
+DD_HOST_DEVICE constexpr bool packed_pairs(int kind) { return kind == kU8 || kind == kU4; }
 
 constexpr int kH = 20;               // window words per lane per DM (the register tile width)
 constexpr int kMaxOff = 15;          // largest in-window DM offset (4-bit field)
@@ -33,26 +37,39 @@ constexpr int kErrTimeout = 1;       // device status bit: a bounded wait gave u
 constexpr size_t kStatusOffset = 0;  // status word at the start of the plan workspace
 constexpr size_t kStatusBytes = 256;
 
-// Samples held by one 32-bit window word: uint8 packs two (16-bit lanes).
-DD_HOST_DEVICE constexpr int samples_per_word(int kind) { return kind == kU8 ? 2 : 1; }
+// Samples held by one 32-bit window word: two for the packed-pair kinds.
+DD_HOST_DEVICE constexpr int samples_per_word(int kind) { return packed_pairs(kind) ? 2 : 1; }
 // Output samples per CTA tile: 32 lanes x kH words x samples per word.
 DD_HOST_DEVICE constexpr int tile_samples(int kind) { return 32 * kH * samples_per_word(kind); }
 DD_HOST_DEVICE constexpr int elem_bytes(int kind) {
-  return (kind == kU8 || kind == kU8W) ? 1 : (kind == kU16 ? 2 : 4);
+  return (kind == kU8 || kind == kU8W || kind == kU4) ? 1 : (kind == kU16 ? 2 : 4);
+}
+// Raw samples per 16 bytes (4-bit samples: two per byte).
+DD_HOST_DEVICE constexpr int samples_per_16b(int kind) {
+  return kind == kU4 ? 32 : 16 / elem_bytes(kind);
+}
+// Bytes of n raw samples (4-bit: rounded up to whole bytes).
+DD_HOST_DEVICE constexpr int64_t sample_bytes(int kind, int64_t n) {
+  return kind == kU4 ? (n + 1) / 2 : n * elem_bytes(kind);
 }
 // Decimated samples in 16 raw bytes: TMA copies start 16-byte aligned, so a
 // window starts up to align_samples - 1 decimated samples before the block's
-// base shift.  The tiled kernels take bins with bin * elem_bytes dividing 16.
-DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) { return 16 / (elem_bytes(kind) * bin); }
+// base shift.  The tiled kernels take bins dividing the samples in 16 bytes.
+DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) {
+  return samples_per_16b(kind) / bin;
+}
 inline bool bin_supported(int kind, int bin) {
-  const int eb = elem_bytes(kind) * bin;
-  return bin >= 1 && eb <= 16 && 16 % eb == 0 && (kind != kU8 || bin == 1);
+  const int per = samples_per_16b(kind);
+  return bin >= 1 && bin <= per && per % bin == 0 && (kind != kU8 || bin == 1) &&
+         (kind != kU4 || bin <= 16);
 }
 // Channels between widenings of the accumulators: uint8 pairs in 16-bit lanes
-// hold 255 * 256 < 2^16; one-sample words stay below 2^31 for
-// floor((2^31 - 1) / (max sample * bin)) channels; float never needs one.
+// hold 255 * 256 < 2^16, 4-bit pairs 15 * bin per channel; one-sample words
+// stay below 2^31 for floor((2^31 - 1) / (max sample * bin)) channels; float
+// never needs one.
 inline int flush_channels(int kind, int bin) {
   if (kind == kU8) return 256;
+  if (kind == kU4) return 65535 / (15 * bin);
   if (kind == kF32) return 1 << 30;
   const double max_sample = (kind == kU8W ? 255.0 : 65535.0) * bin;
   const double n = 2147483647.0 / max_sample;
@@ -172,7 +189,9 @@ inline int32_t window_words(int kind, int bin, int32_t span) {
 // Raw bytes fetched per channel and stage for lp window words (uint8 at bin 1
 // also fetches the paired samples, `pair` words further).
 DD_HOST_DEVICE constexpr int32_t raw_bytes(int kind, int bin, int32_t lp, int pair = kPair) {
-  return kind == kU8 ? lp + pair : lp * elem_bytes(kind) * bin;
+  return kind == kU8   ? lp + pair
+         : kind == kU4 ? (lp + pair) * bin / 2
+                       : lp * elem_bytes(kind) * bin;
 }
 
 // Pattern tiles: output samples per CTA tile, staged window words per channel
@@ -185,7 +204,9 @@ inline int32_t pat_window_words(int kind, int bin, int h, int32_t span) {
   // before the branch) or, inside a pattern block, up to its last DM's shift
   // plus h: lane 31 stays below 31h + (span + align - 1) + h + 6.
   const int32_t need = 32 * h + span + (align_samples(kind, bin) - 1) + 6;
-  return (need + 15) / 16 * 16;
+  // Whole 16-byte raw windows: 4-bit pairs need lp + 32h to be even in 16s.
+  const int32_t mult = kind == kU4 ? 32 : 16;
+  return (need + mult - 1) / mult * mult;
 }
 // Start of the raw buffers: 128 bytes of barriers, then two (three with
 // double-buffered windows) record buffers of PRec per channel or one pair

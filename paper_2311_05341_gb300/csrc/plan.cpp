@@ -244,6 +244,7 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
 
 // Try one tile shape for a range; on success fill the range's tile fields.
 bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh) {
+  if (kind == tk::kU4) return false;  // 4-bit input runs on the pattern tiles only
   const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
   const int32_t lp = tk::window_words(kind, rp.r.bin, span);
   if (tk::smem_bytes(kind, rp.r.bin, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
@@ -330,7 +331,9 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_chunk_off = 0;
   rp.tile_chunk_bytes = 0;
   rp.tile_recs.clear();
-  const int kind = (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W : static_cast<int>(dtype);
+  const int kind = dtype == DD_U4                      ? tk::kU4
+                   : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
+                                                      : static_cast<int>(dtype);
   if (!tk::bin_supported(kind, rp.r.bin)) return;
   if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == 0) {
     for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)

@@ -75,6 +75,49 @@ __device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int b
     v.y = __byte_perm(t01, 0u, 0x4342);
     v.z = __byte_perm(t23, 0u, 0x4140);
     v.w = __byte_perm(t23, 0u, 0x4342);
+  } else if constexpr (KIND == kU4) {
+    // 4-bit samples, two per byte (the earlier in the low nibble).  Word k
+    // packs decimated samples k and k + PAIR in its 16-bit lanes; at bin b a
+    // decimated sample is the sum of b nibbles (at most 15 * 16 = 240).
+    auto nib2 = [](uint32_t w) { return (w & 0x0f0f0f0fu) + ((w >> 4) & 0x0f0f0f0fu); };
+    const uint8_t* lo = raw_ch + 2 * q * bin;
+    const uint8_t* hi = lo + PAIR * bin / 2;
+    if (bin == 1) {
+      const uint32_t c = *reinterpret_cast<const uint16_t*>(lo) |
+                         (static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(hi)) << 16);
+      v = make_uint4(c & 0x000f000fu, (c >> 4) & 0x000f000fu, (c >> 8) & 0x000f000fu,
+                     (c >> 12) & 0x000f000fu);
+    } else if (bin == 2) {  // one byte per decimated sample
+      const uint32_t a = nib2(*reinterpret_cast<const uint32_t*>(lo));
+      const uint32_t b = nib2(*reinterpret_cast<const uint32_t*>(hi));
+      const uint32_t t01 = __byte_perm(a, b, 0x5140);
+      const uint32_t t23 = __byte_perm(a, b, 0x7362);
+      v = make_uint4(__byte_perm(t01, 0u, 0x4140), __byte_perm(t01, 0u, 0x4342),
+                     __byte_perm(t23, 0u, 0x4140), __byte_perm(t23, 0u, 0x4342));
+    } else if (bin == 4) {  // two bytes per decimated sample
+      auto half = [&](uint32_t w) {
+        const uint32_t s2 = nib2(w);
+        return (s2 & 0x00ff00ffu) + ((s2 >> 8) & 0x00ff00ffu);
+      };
+      const uint2 a = *reinterpret_cast<const uint2*>(lo);
+      const uint2 b = *reinterpret_cast<const uint2*>(hi);
+      const uint32_t l0 = half(a.x), l1 = half(a.y), h0 = half(b.x), h1 = half(b.y);
+      v = make_uint4(__byte_perm(l0, h0, 0x5410), __byte_perm(l0, h0, 0x7632),
+                     __byte_perm(l1, h1, 0x5410), __byte_perm(l1, h1, 0x7632));
+    } else {  // bin 8 or 16: bin / 2 bytes per decimated sample
+      const int words = bin / 8;
+      uint32_t o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t sl = 0, sh = 0;
+        for (int j = 0; j < words; ++j) {
+          sl += byte_sum4(nib2(reinterpret_cast<const uint32_t*>(lo)[k * words + j]));
+          sh += byte_sum4(nib2(reinterpret_cast<const uint32_t*>(hi)[k * words + j]));
+        }
+        o[k] = sl | (sh << 16);
+      }
+      v = make_uint4(o[0], o[1], o[2], o[3]);
+    }
   } else if constexpr (KIND == kU8W) {
     const uint8_t* r = raw_ch + 4 * q * bin;
     if (bin == 2) {
@@ -148,19 +191,19 @@ __device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_ba
                                             int st, int buf, int64_t t0, int32_t base, int tid,
                                             const void* rec_src, uint32_t rec_bytes,
                                             void* rec_dst) {
-  constexpr int kE = elem_bytes(KIND);
   const uint32_t bar = bar_base + 8u * buf;
   if (tid < NC) {
     const int c = st * NC + tid;
     uint32_t bytes = 0;
     const uint8_t* src = nullptr;
     if (c < p.n_chan) {
-      const int64_t align = 16 / (kE * p.bin);                       // decimated samples, 2^k
-      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw elements
+      const int64_t align = align_samples(KIND, p.bin);              // decimated samples, 2^k
+      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw samples
       if (ua < p.stride) {
-        const int64_t room = (p.stride - ua) * kE;
+        const int64_t room = sample_bytes(KIND, p.stride - ua);
         bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
-        src = static_cast<const uint8_t*>(p.x) + (static_cast<int64_t>(c) * p.stride + ua) * kE;
+        src = static_cast<const uint8_t*>(p.x) +
+              sample_bytes(KIND, static_cast<int64_t>(c) * p.stride + ua);
       }
     }
     mbar_arrive_expect(bar, bytes);
@@ -237,7 +280,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
       const int d = blk * (DR * NW) + w * DR + i;
 #pragma unroll
       for (int j = 0; j < H; ++j) {
-        if constexpr (KIND == kU8) {
+        if constexpr (packed_pairs(KIND)) {
           const uint32_t v = acc[i][j];
           tr[wbase + j] = v & 0xffffu;
           tr[wbase + j + kHiOff] = v >> 16;

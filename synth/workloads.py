@@ -54,7 +54,8 @@ class Beam:
 
     @property
     def np_dtype(self):
-        return {"u8": np.uint8, "u16": np.uint16, "f32": np.float32}[self.dtype]
+        """Element type of the sample buffer (packed bytes for "u4")."""
+        return {"u8": np.uint8, "u16": np.uint16, "f32": np.float32, "u4": np.uint8}[self.dtype]
 
 
 def tiny_u8() -> Beam:
@@ -65,6 +66,12 @@ def tiny_u8() -> Beam:
 def paper_u8() -> Beam:
     return Beam("paper_u8", "u8", 8192, 262144, 1670.0, 320.0, 64e-6,
                 [(0.0, 409.6, 0.1, 1)], 128.0, 16.0, 2000, 40.0, n_random_pulses=3)
+
+
+def paper_u4() -> Beam:
+    """The paper-scale plan on 4-bit samples (N(8, 2) clamped to 0..15)."""
+    return Beam("paper_u4", "u4", 8192, 262144, 1670.0, 320.0, 64e-6,
+                [(0.0, 409.6, 0.1, 1)], 8.0, 2.0, 2002, 5.0, n_random_pulses=3)
 
 
 def paper_u16() -> Beam:
@@ -124,5 +131,15 @@ def make_input(beam: Beam, shift_rows, n_dm, n_out, out=None, row_stride=None):
         b = beam.ranges[r][3]
         s = np.asarray(shift_rows(r, d), dtype=np.int64)
         tracks.append(((t0 + s) * b, w * b, beam.pulse_amp))
+    if beam.dtype == "u4":  # 4-bit: 8-bit draws clamped to 0..15, packed two per byte
+        from . import pack4
+        n_even = beam.n_samp + (beam.n_samp % 2)
+        x = filterbank(np.uint8, beam.n_chan, n_even, beam.seed, beam.mean, beam.sd,
+                       pulses=tracks)
+        packed = pack4(np.minimum(x, 15).astype(np.uint8))
+        stride = n_even if row_stride is None else int(row_stride)
+        res = np.zeros((beam.n_chan, stride // 2), np.uint8) if out is None else out
+        res[:, : packed.shape[1]] = packed
+        return res
     return filterbank(beam.np_dtype, beam.n_chan, beam.n_samp, beam.seed, beam.mean, beam.sd,
                       pulses=tracks, out=out, row_stride=row_stride)

@@ -203,3 +203,17 @@ def test_pattern_tile_selection():
     with pytest.raises(dd.DDError) as ei:
         plan.set_tile(0, 3)
     assert ei.value.status == _lib.DD_ERR_INVALID_ARG
+
+
+def test_u4_plan_selection_and_refusals():
+    """4-bit plans take the pattern tile or the generic kernel (no offset
+    tiles); the transpose front end refuses them."""
+    paper = workloads.paper_u8()
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u4", upload=False)
+    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
+    with pytest.raises(dd.DDError) as ei:
+        plan.set_tile(0, 6)
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    lib = _lib.load()
+    st = lib.dd_transpose(_lib.DD_U4, 16, 32, 1, 16, 32, 0, 1, None)
+    assert st == _lib.DD_ERR_UNSUPPORTED
