@@ -126,6 +126,30 @@ dd_status dd_plan_query(dd_plan plan, int64_t n_samp, dd_plan_info* out);
 dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out);
 
 /*
+ * DM plan from a smearing tolerance: the discrete counterpart (fixed step and
+ * time bin per range) of an adaptive DM list, as the paper builds for its
+ * comparison with adaptive plans (Sec. 5.2).  With the band's lowest and
+ * highest channel centres f_lo, f_hi (MHz), channel width df and centre f_c,
+ *   t_chan(DM) = 8297.4e3 * DM * df / f_c^3 ms        (Eq. 4, intra-channel smear)
+ *   W_b(DM)    = sqrt((b t_samp)^2 + t_chan(DM)^2 + width^2)
+ *   k_band     = 4148.808 * (1/f_lo^2 - 1/f_hi^2) s per unit DM   (Eq. 1)
+ *   step_b(DM) = 2 W_b(DM) sqrt(tol^2 - 1) / k_band
+ * so that a pulse at any DM, at most step/2 from a trial, is broadened by at
+ * most a factor tol.  Range r starts at the previous range's end with bin b_r
+ * and step step_b(lo_r) (W grows with DM, so the step holds over the range)
+ * and ends where the continuous step has doubled, where t_chan reaches 2 b_r
+ * t_samp (the next range then bins by 2 b_r, up to max_bin), or at dm_max;
+ * its end is rounded up to a whole number of steps (the last range's to half a
+ * step past dm_max, so every DM up to dm_max has a trial within step / 2).  The last of max_ranges
+ * ranges runs to dm_max.  Writes *n_ranges <= max_ranges (<= DD_MAX_RANGES)
+ * ranges.  Errors: DD_ERR_INVALID_ARG (n_chan < 2, tol <= 1, dm_max <= 0,
+ * t_samp <= 0, width < 0, max_bin < 1, max_ranges < 1).
+ */
+dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_samp_s,
+                            double dm_max, double tol, double width_s, int32_t max_bin,
+                            int32_t max_ranges, dd_range* out, int32_t* n_ranges);
+
+/*
  * Choose the tile of range `range`: `tile` is the offset tile's DM count per
  * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, or 0 = automatic.  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).

@@ -56,6 +56,18 @@ def transpose(x_tm, n_chan: int | None = None, out=None, t_begin: int = 0,
     return out
 
 
+def dm_ranges(freqs, t_samp: float, dm_max: float, tol: float = 1.25, width: float = 0.0,
+              max_bin: int = 16, max_ranges: int = 16) -> list:
+    """DM ranges [(lo, hi, step, bin)] from a smearing tolerance (dd_plan_dm_ranges)."""
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    arr = (_lib.Range * _lib.DD_MAX_RANGES)()
+    n = ctypes.c_int32()
+    check(_lib.load().dd_plan_dm_ranges(f.ctypes.data, f.size, float(t_samp), float(dm_max),
+                                        float(tol), float(width), int(max_bin), int(max_ranges),
+                                        ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(n)))
+    return [(arr[i].dm_lo, arr[i].dm_hi, arr[i].dm_step, arr[i].bin) for i in range(n.value)]
+
+
 def _stream_ptr(stream) -> int:
     import torch
     if stream is None:

@@ -72,6 +72,9 @@ SIGNATURES = {
                                        ctypes.POINTER(_VP)]),
     "dd_batch_destroy": (ctypes.c_int, [_VP]),
     "dd_batch_workspace_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_SZ)]),
+    "dd_plan_dm_ranges": (ctypes.c_int, [_VP, _I32, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, _I32, _I32, _VP,
+                                          ctypes.POINTER(_I32)]),
     "dd_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
     "dd_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "dd_batch_upload": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),

@@ -240,6 +240,27 @@ dd_status dd_plan_shifts(dd_plan plan, int32_t range, int32_t* host_out) {
   return DD_OK;
 }
 
+dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_samp_s,
+                            double dm_max, double tol, double width_s, int32_t max_bin,
+                            int32_t max_ranges, dd_range* out, int32_t* n_ranges) {
+  if (!freqs_mhz || !out || !n_ranges) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+  if (n_chan < 2 || !(tol > 1.0) || !(dm_max > 0.0) || !(t_samp_s > 0.0) || !(width_s >= 0.0) ||
+      max_bin < 1 || max_ranges < 1)
+    return fail(DD_ERR_INVALID_ARG, "need n_chan >= 2, tol > 1, dm_max > 0, t_samp > 0, "
+                                    "width >= 0, max_bin >= 1, max_ranges >= 1");
+  for (int32_t c = 0; c < n_chan; ++c)
+    if (!(freqs_mhz[c] > 0.0)) return fail(DD_ERR_INVALID_ARG, "frequencies must be positive");
+  double f_lo = freqs_mhz[0], f_hi = freqs_mhz[0];
+  for (int32_t c = 1; c < n_chan; ++c) {
+    f_lo = std::min(f_lo, freqs_mhz[c]);
+    f_hi = std::max(f_hi, freqs_mhz[c]);
+  }
+  if (!(f_hi > f_lo)) return fail(DD_ERR_INVALID_ARG, "the band has no width");
+  *n_ranges = dm_plan_ranges(freqs_mhz, n_chan, t_samp_s, dm_max, tol, width_s, max_bin,
+                             std::min(max_ranges, DD_MAX_RANGES), out);
+  return DD_OK;
+}
+
 dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))

@@ -84,6 +84,10 @@ dd_status build_plan(dd_plan_s* p);
 // the workspace image.  Returns false if the requested tile does not fit.
 bool retile_range(dd_plan_s* p, size_t range, int32_t request);
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
+// DM ranges from a smearing tolerance (dd_plan_dm_ranges); returns their count.
+int32_t dm_plan_ranges(const double* freqs, int32_t n_chan, double t_samp, double dm_max,
+                       double tol, double width, int32_t max_bin, int32_t max_ranges,
+                       dd_range* out);
 
 // Kernel launchers (return a cudaError_t as int; 0 on success).  Each writes
 // the outputs t in [t_begin, t_end) of rows of n_out samples; t_begin is a

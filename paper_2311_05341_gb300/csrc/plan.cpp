@@ -373,6 +373,51 @@ void layout_workspace(dd_plan_s* p) {
 
 }  // namespace
 
+int32_t dm_plan_ranges(const double* freqs, int32_t n_chan, double t_samp, double dm_max,
+                       double tol, double width, int32_t max_bin, int32_t max_ranges,
+                       dd_range* out) {
+  double f_lo = freqs[0], f_hi = freqs[0];
+  for (int32_t c = 1; c < n_chan; ++c) {
+    f_lo = std::min(f_lo, freqs[c]);
+    f_hi = std::max(f_hi, freqs[c]);
+  }
+  const double df = (f_hi - f_lo) / (n_chan - 1);
+  const double f_c = 0.5 * (f_lo + f_hi);
+  const double chan_per_dm = 8297.4e3 * df / (f_c * f_c * f_c) * 1e-3;  // s per unit DM (Eq. 4)
+  const double k_band = kDispersionConstant * (1.0 / (f_lo * f_lo) - 1.0 / (f_hi * f_hi));
+  const double q = 2.0 * std::sqrt(tol * tol - 1.0) / k_band;
+  auto width_at = [&](double dm, int32_t b) {
+    const double ts = b * t_samp, tc = chan_per_dm * dm;
+    return std::sqrt(ts * ts + tc * tc + width * width);
+  };
+  int32_t n = 0;
+  double lo = 0.0;
+  int32_t bin = 1;
+  while (lo < dm_max && n < max_ranges) {
+    const double w0 = width_at(lo, bin);
+    const double step = q * w0;
+    double hi = dm_max;
+    if (n + 1 < max_ranges) {
+      // Where the continuous step has doubled: W_b(DM) = 2 W_b(lo).
+      const double rest = 4.0 * w0 * w0 - (bin * t_samp) * (bin * t_samp) - width * width;
+      if (chan_per_dm > 0.0) hi = std::min(hi, std::sqrt(std::max(rest, 0.0)) / chan_per_dm);
+      // Where binning by 2 b costs little: t_chan = 2 b t_samp.
+      if (2 * bin <= max_bin && chan_per_dm > 0.0)
+        hi = std::min(hi, 2.0 * bin * t_samp / chan_per_dm);
+    }
+    // Trials lo + k step, k < n; the next range's first trial is hi.  The last
+    // range keeps dm_max within half a step of its last trial.
+    const bool last = hi >= dm_max;
+    const double n_steps =
+        std::max(1.0, std::ceil((hi - lo) / step + (last ? 0.5 : 0.0) - 1e-9));
+    hi = lo + n_steps * step;
+    out[n++] = dd_range{lo, hi, step, bin};
+    if (2 * bin <= max_bin && chan_per_dm * hi >= 2.0 * bin * t_samp) bin *= 2;
+    lo = hi;
+  }
+  return n;
+}
+
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp) {
   (void)p;
   return n_samp / rp.r.bin - rp.s_max;
