@@ -302,6 +302,9 @@ def run_ours(args):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(beam, x_host, info, args.cpu_rows)
+        if beam.dtype in ("u8", "u16", "f32") and len(beam.ranges) == 1 and beam.ranges[0][3] == 1:
+            line["cpu_baseline_tiled"] = cpu_tiled_baseline(beam, x_host, plan.shifts(0), info,
+                                                            args.cpu_tiled_rows)
     print(json.dumps(line))
 
 
@@ -317,6 +320,23 @@ def cpu_baseline(beam, x_host, info, n_rows):
     return {"value": units / sec, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{n_rows} of {info['n_dm'][0]} DM rows, full length "
                       f"({info['n_out'][0]} samples), range 0", "seconds": sec}
+
+
+def cpu_tiled_baseline(beam, x_host, shifts, info, n_rows):
+    """The tiled CPU scheme (cpu_baseline/, the paper's Algorithm 2) on a
+    bounded sample: n_rows consecutive DM rows from the middle, full length."""
+    import cpu_baseline
+    d0 = max(0, info["n_dm"][0] // 2 - n_rows // 2)
+    rows = shifts[d0:d0 + n_rows]
+    cpu_baseline.forward(x_host, rows[:16], 4096)  # build / warm
+    t0 = time.perf_counter()
+    cpu_baseline.forward(x_host, rows, info["n_out"][0])
+    sec = time.perf_counter() - t0
+    import oracle
+    return {"value": rows.shape[0] * info["n_out"][0] / sec, "unit": UNIT,
+            "cores": oracle.threads(), "kind": "tiled CPU (Algorithm 2 scheme)",
+            "sample": f"DM rows {d0}..{d0 + rows.shape[0] - 1} of {info['n_dm'][0]}, full length "
+                      f"({info['n_out'][0]} samples)", "seconds": sec}
 
 
 def run_reference(args):
@@ -597,6 +617,7 @@ def main():
     ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-rows-reference", type=int, default=4)
+    ap.add_argument("--cpu-tiled-rows", type=int, default=256)
     ap.add_argument("--n-samp", type=int, default=None,
                     help="raw samples per channel instead of the workload's (smaller "
                          "cases for profiler captures)")
