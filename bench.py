@@ -616,7 +616,7 @@ def main():
     ap.add_argument("--stream-seconds", type=float, default=15.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
     ap.add_argument("--cpu-rows", type=int, default=96)
-    ap.add_argument("--cpu-rows-reference", type=int, default=4)
+    ap.add_argument("--cpu-rows-reference", type=int, default=16)
     ap.add_argument("--cpu-tiled-rows", type=int, default=256)
     ap.add_argument("--n-samp", type=int, default=None,
                     help="raw samples per channel instead of the workload's (smaller "
