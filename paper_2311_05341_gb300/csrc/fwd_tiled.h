@@ -135,10 +135,12 @@ static_assert(sizeof(PRec) == 48, "PRec must stay 48 bytes");
 // pairs that share its increment pattern, two samples per accumulator update
 // (a three-input integer add), and the channels left without a partner one by
 // one.  Per (DM block, stage) the host writes a chunk of per-warp lists: pair
-// counts (16 bytes), single counts (16 bytes), then warps x nc items
+// counts (kPairMaxWarps bytes), single counts (kPairMaxWarps bytes), then
+// warps x nc items
 // {a1 | a2 << 16, pattern}, pairs first, a = staged channel * lp + window
 // offset.
-constexpr int kPairCountBytes = 32;
+constexpr int kPairMaxWarps = 32;
+constexpr int kPairCountBytes = 2 * kPairMaxWarps;
 struct PairItem {
   uint32_t a;    // a1 | a2 << 16 (word offsets into the window buffer)
   uint32_t pat;  // pattern number
@@ -165,6 +167,12 @@ constexpr PatShape kPatShapes[] = {
     {19, 16, 32, false, false, 1}, {19, 16, 12, false, false, 1}, {19, 16, 6, false, false, 1},
     {19, 16, 12, false, false, 3}, {19, 16, 6, false, false, 3}};
 constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
+constexpr bool pat_shapes_fit_records() {
+  for (const PatShape& s : kPatShapes)
+    if (s.warps > (s.pairs ? kPairMaxWarps : kPatMaxWarps)) return false;
+  return true;
+}
+static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its records hold");
 // The shape serves a kind: pairs take integer window words, single channels float.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
   return s.pairs == (kind != kF32);

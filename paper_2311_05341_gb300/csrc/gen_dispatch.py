@@ -51,7 +51,7 @@ def macro(op, dr):
     return out
 
 
-PATTERN_H = (17, 19, 21, 23, 25)  # odd window words per lane of the pattern tiles
+PATTERN_H = (15, 17, 19, 21, 23, 25)  # odd window words per lane of the pattern tiles
 PATTERN_DR = 4
 
 
@@ -89,7 +89,7 @@ def pattern_macro(op, h):
     return out
 
 
-PAIR_H = (17, 19, 21, 23, 25)  # window words per lane of the channel-pair pattern tiles
+PAIR_H = (15, 17, 19, 21, 23, 25)  # window words per lane of the channel-pair pattern tiles
 # In-block loads run this many words ahead of the adds that consume them, so a
 # word's register dies after its last use (None: all loads first).
 LOAD_AHEAD = 4

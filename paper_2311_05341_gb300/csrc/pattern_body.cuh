@@ -63,13 +63,14 @@ __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
 template <int KIND, int H>
 __device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
                                             uint32_t ix) {
-  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+  static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pattern blocks for H");
 #define DD_PAT_CASE(HH)                                                  \
   if constexpr (H == HH) {                                               \
     if constexpr (KIND == kF32) DD_PATL_CHANNEL_F32_##HH(acc, win, ix);  \
     else DD_PATL_CHANNEL_U32_##HH(acc, win, ix);                         \
   }
+  DD_PAT_CASE(15)
   DD_PAT_CASE(17)
   DD_PAT_CASE(19)
   DD_PAT_CASE(21)
@@ -89,6 +90,7 @@ __device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
     if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
     else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);                     \
   }
+  DD_PAT_CASE(15)
   DD_PAT_CASE(17)
   DD_PAT_CASE(19)
   DD_PAT_CASE(21)
@@ -100,9 +102,10 @@ __device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
 template <int H>
 __device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t win, uint32_t win2,
                                          uint32_t ix) {
-  static_assert(H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
+  static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pair blocks for H");
-  if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
+  if constexpr (H == 15) DD_PATL2_CHANNEL_U32_15(acc, win, win2, ix);
+  else if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
   else if constexpr (H == 19) DD_PATL2_CHANNEL_U32_19(acc, win, win2, ix);
   else if constexpr (H == 21) DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
   else if constexpr (H == 23) DD_PATL2_CHANNEL_U32_23(acc, win, win2, ix);
@@ -130,7 +133,6 @@ template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
-  constexpr int kThreads = NW * 32;
   constexpr int kPairW = 32 * H;
   constexpr int kRecBufs = DBUF ? 3 : 2;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -192,15 +194,14 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     const int nc = min(NC, p.n_chan - st * NC);
     uint32_t* pwb = sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
     auto unpack = [&]() {  // raw bytes of stage st into window words
+      // Warp w takes channels w, w + NW, ...; its lanes take consecutive units
+      // (conflict-free 16-byte stores).
       const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
-      const int total = nc * units;
-      for (int u = tid; u < total; u += kThreads) {
-        const int ch =
-            static_cast<int>((static_cast<uint64_t>(u) * p.units_magic) >> (32 + p.units_shift));
-        const int q = u - ch * units;
-        const uint4 v =
-            unpack_unit<KIND, kPairW>(rawb + static_cast<size_t>(ch) * p.lraw, q, p.bin);
-        *reinterpret_cast<uint4*>(pwb + static_cast<size_t>(ch) * p.lp + 4 * q) = v;
+      for (int ch = w; ch < nc; ch += NW) {
+        const uint8_t* raw_ch = rawb + static_cast<size_t>(ch) * p.lraw;
+        uint32_t* dst = pwb + static_cast<size_t>(ch) * p.lp;
+        for (int q = l; q < units; q += 32)
+          *reinterpret_cast<uint4*>(dst + 4 * q) = unpack_unit<KIND, kPairW>(raw_ch, q, p.bin);
       }
     };
     const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
@@ -226,7 +227,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     if constexpr (PAIRS) {
       const uint32_t lane_win = smem_u32(pwb + H * l);
       const unsigned char* ck = rec_buf(rb);
-      const int n_pairs = ck[w], n_items = n_pairs + ck[16 + w];
+      const int n_pairs = ck[w], n_items = n_pairs + ck[kPairMaxWarps + w];
       const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
 #pragma unroll 1
       for (int k = 0; k < n_pairs; ++k) {

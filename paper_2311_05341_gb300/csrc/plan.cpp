@@ -213,7 +213,7 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
         const int n_pairs = n;
         for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat)
           if (by_pat[pat].size() % 2) items[w * ps.nc + n++] = PairItem{by_pat[pat].back(), pat};
-        chunk[16 + w] = static_cast<unsigned char>(n - n_pairs);
+        chunk[kPairMaxWarps + w] = static_cast<unsigned char>(n - n_pairs);
       }
     }
   }
