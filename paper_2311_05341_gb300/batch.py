@@ -42,6 +42,21 @@ def _torch():
     return torch
 
 
+def input_buffer(dtype: str, n_chan: int, n_samp: int, device, n_cols: int | None = None):
+    """Zeroed device input [n_chan][row] with 16-byte rows for n_samp samples
+    (n_cols: samples per row instead).  "u4" rows hold packed bytes, two
+    samples each (row stride in samples a multiple of 32)."""
+    torch = _torch()
+    esz = {"u8": 1, "u16": 2, "f32": 4, "u4": 1}[dtype]
+    per = 32 if dtype == "u4" else 16 // esz
+    n = n_samp if n_cols is None else n_cols
+    stride = (n + per - 1) // per * per
+    row_bytes = stride // 2 if dtype == "u4" else stride * esz
+    raw = torch.zeros((n_chan, row_bytes), dtype=torch.uint8, device=device)
+    return raw.view({"u8": torch.uint8, "u16": torch.uint16, "f32": torch.float32,
+                     "u4": torch.uint8}[dtype])
+
+
 def plan_signature(plan: Plan, n_samp: int) -> str:
     """Key of the autotune cache: everything that changes the tile's work."""
     h = hashlib.sha1(plan.freqs.tobytes()).hexdigest()[:16]
@@ -127,11 +142,7 @@ class BatchRunner:
         self.shapes = []
         for b in self.beams:
             plan = Plan(b.freqs, b.f_ref, b.t_samp, b.ranges, b.dtype, device=self.device)
-            esz = {"u8": 1, "u16": 2, "f32": 4}[b.dtype]
-            per = 16 // esz
-            stride = (b.n_samp + per - 1) // per * per
-            raw = torch.zeros((plan.n_chan, stride * esz), dtype=torch.uint8, device=self.device)
-            x = raw.view({"u8": torch.uint8, "u16": torch.uint16, "f32": torch.float32}[b.dtype])
+            x = input_buffer(b.dtype, plan.n_chan, b.n_samp, self.device)
             out = plan.empty_output(b.n_samp, self.device)
             if self.tuner is not None:
                 self.shapes.append(self.tuner.choose(plan, b.n_samp, x, out))
@@ -163,7 +174,8 @@ class BatchRunner:
         stream = torch.cuda.current_stream(self.device).cuda_stream
         check(lib.dd_batch_upload(h, self.workspace.data_ptr(), self.workspace.numel(), stream))
         d_in = (ctypes.c_void_p * n)(*[x.data_ptr() for x in self.inputs])
-        strides = (ctypes.c_int64 * n)(*[x.stride(0) for x in self.inputs])
+        strides = (ctypes.c_int64 * n)(*[x.stride(0) * (2 if b.dtype == "u4" else 1)
+                                         for x, b in zip(self.inputs, self.beams)])
         d_out = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outputs])
         check(lib.dd_batch_bind(h, d_in, strides, d_out, stream))
         n_items, n_jobs = ctypes.c_int64(), ctypes.c_int32()

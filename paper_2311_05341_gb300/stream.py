@@ -105,9 +105,9 @@ class StreamServer:
     def beam_bytes(self, spec: StreamSpec) -> int:
         plan = self._plan(spec)
         ov = overlap_for(plan, spec.ranges)
-        esz = {"u8": 1, "u16": 2, "f32": 4}[spec.dtype]
         n = ov + self.chunk
-        return len(spec.freqs) * n * esz + plan.info(n)["out_elems"] * 4
+        in_bytes = (n + 1) // 2 if spec.dtype == "u4" else n * {"u8": 1, "u16": 2, "f32": 4}[spec.dtype]
+        return len(spec.freqs) * in_bytes + plan.info(n)["out_elems"] * 4
 
     def request(self, beam_id: int, spec: StreamSpec) -> bool:
         """Admit a beam now if its memory fits the budget, else queue it."""
@@ -125,14 +125,11 @@ class StreamServer:
 
     def _admit(self, beam_id: int, spec: StreamSpec, need: int):
         torch = _torch()
+        from .batch import input_buffer
         plan = self._plan(spec)
         ov = overlap_for(plan, spec.ranges)
-        dt = {"u8": torch.uint8, "u16": torch.uint16, "f32": torch.float32}[spec.dtype]
-        esz = {"u8": 1, "u16": 2, "f32": 4}[spec.dtype]
         n = ov + self.chunk
-        stride = (n * esz + 15) // 16 * 16 // esz
-        raw = torch.zeros((len(spec.freqs), stride * esz), dtype=torch.uint8, device=self.device)
-        window = raw.view(dt)
+        window = input_buffer(spec.dtype, len(spec.freqs), n, self.device)
         out = plan.empty_output(n, self.device)
         self.beams[beam_id] = _Beam(spec, plan, window, out, torch.cuda.Stream(self.device),
                                     bytes=need)
@@ -166,14 +163,17 @@ class StreamServer:
         beam = self.beams[job.beam]
         plan, ov = beam.plan, overlap_for(beam.plan, beam.spec.ranges)
         n = ov + self.chunk
+        # Column indices of the window buffer ("u4" packs two samples per byte;
+        # the overlap and the chunk are even).
+        spe = 2 if beam.spec.dtype == "u4" else 1
         with torch.cuda.stream(beam.stream):
-            beam.window[:, ov:n].copy_(job.chunk, non_blocking=True)
+            beam.window[:, ov // spe:n // spe].copy_(job.chunk, non_blocking=True)
             plan.run(beam.window, out=beam.out, n_samp=n, stream=beam.stream)
             if self.keep_outputs:
                 beam.kept.append(self._kept(beam, n, ov))
             # The tail of this window is the next step's overlap.
-            tail = beam.window[:, self.chunk:n]
-            beam.window[:, :ov].copy_(tail.clone() if ov > self.chunk else tail)
+            tail = beam.window[:, self.chunk // spe:n // spe]
+            beam.window[:, :ov // spe].copy_(tail.clone() if ov > self.chunk else tail)
             ev = torch.cuda.Event()
             ev.record(beam.stream)
         job.event = ev

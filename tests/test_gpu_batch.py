@@ -103,3 +103,36 @@ def test_graph_replay_follows_new_inputs():
     torch.cuda.synchronize()
     for i, b in enumerate(runner.beams):
         _check_oracle(b, hosts[i], runner.planes(i))
+
+
+def test_batch_with_4bit_beams():
+    """Packed 4-bit beams in a batch with an 8-bit one: batch == alone == oracle."""
+    from synth import filterbank4
+    beams = [ddb.BeamSpec(channel_freqs(1520.0, 310.0, 200), 1520.0, 64e-6,
+                          [(0.0, 25.6, 0.1, 1)], "u4", 9000),
+             ddb.BeamSpec(channel_freqs(1400.0, 300.0, 96), 1400.0, 64e-6,
+                          [(0.0, 12.8, 0.1, 1), (12.8, 25.6, 0.2, 2)], "u4", 7001),
+             ddb.BeamSpec(channel_freqs(1670.0, 320.0, 128), 1670.0, 64e-6,
+                          [(0.0, 12.8, 0.1, 1)], "u8", 6000)]
+    runner = ddb.BatchRunner(beams, autotune=False, graph=True)
+    hosts = []
+    for i, (b, x) in enumerate(zip(runner.beams, runner.inputs)):
+        if b.dtype == "u4":
+            h = filterbank4(len(b.freqs), b.n_samp, 900 + i, 8, 4, row_bytes=x.shape[1])
+            x.copy_(torch.from_numpy(h).to(x.device))
+            hosts.append(oracle.Packed4(h, b.n_samp))
+        else:
+            h = filterbank(np.uint8, len(b.freqs), b.n_samp, 900 + i, 128, 40)
+            x[:, : b.n_samp].copy_(torch.from_numpy(h).to(x.device))
+            hosts.append(h)
+    torch.cuda.synchronize()
+    runner.run()
+    torch.cuda.synchronize()
+    runner.status()
+    batched = [o.clone() for o in runner.outputs]
+    runner.run_per_beam()
+    torch.cuda.synchronize()
+    for i, (bo, o) in enumerate(zip(batched, runner.outputs)):
+        assert torch.equal(bo, o), f"beam {i} differs between batch and alone"
+    for i, b in enumerate(runner.beams):
+        _check_oracle(b, hosts[i], runner.planes(i))

@@ -110,3 +110,25 @@ def test_alone_equals_mixed_with_admission():
         np.testing.assert_array_equal(g, o[:, : g.shape[1]])
     st = srv2.stats()
     assert st["chunks"] == 3 * N_CHUNKS and st["rejected"] == 0
+
+
+def test_chunked_4bit_equals_one_shot():
+    """Packed 4-bit chunks (two samples per byte) through the server equal one
+    dd_run over the concatenated packed stream and the oracle's 4-bit path."""
+    from synth import filterbank4
+    spec = dds.StreamSpec(channel_freqs(1670.0, 320.0, 192), 1670.0, 64e-6, RANGES, "u4")
+    x = filterbank4(192, CHUNK * N_CHUNKS, 700, 8, 4)  # [192][CHUNK * N_CHUNKS / 2] bytes
+    half = CHUNK // 2
+    chunks = [torch.from_numpy(np.ascontiguousarray(x[:, k * half:(k + 1) * half])).pin_memory()
+              for k in range(N_CHUNKS)]
+    done, srv = _run_server({0: (spec, chunks)}, 1 << 34, [0] * N_CHUNKS)
+    plan = dd.Plan(spec.freqs, spec.f_ref, spec.t_samp, spec.ranges, "u4")
+    ref = [p.cpu().numpy() for p in plan.run(torch.from_numpy(x).cuda(),
+                                              n_samp=CHUNK * N_CHUNKS)]
+    got = done[0]
+    for r, (g, o) in enumerate(zip(got, ref)):
+        np.testing.assert_array_equal(g, o[:, : g.shape[1]], err_msg=f"range {r}")
+    rows = [0, got[0].shape[0] - 1]
+    o = oracle.forward_rows(oracle.Packed4(x, CHUNK * N_CHUNKS), spec.freqs, spec.f_ref,
+                            spec.t_samp, RANGES[0], rows, 0, got[0].shape[1])
+    np.testing.assert_array_equal(got[0][rows], o)
