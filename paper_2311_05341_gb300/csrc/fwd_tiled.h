@@ -216,18 +216,19 @@ inline int32_t pat_window_words(int kind, int bin, int h, int32_t span) {
   const int32_t mult = kind == kU4 ? 32 : 16;
   return (need + mult - 1) / mult * mult;
 }
-// Start of the raw buffers: 128 bytes of barriers, then two (three with
-// double-buffered windows) record buffers of PRec per channel or one pair
-// chunk per stage.
+// Pattern tiles' shared memory: 128 bytes of barriers, two record buffers
+// (PRec per channel, or one pair chunk per stage), one raw buffer of nc
+// channels, and one window buffer (two with dbuf).
 DD_HOST_DEVICE constexpr size_t pat_raw_offset(int warps, int nc, bool pairs, bool dbuf) {
-  return (kRecOffset +
-          (dbuf ? 3 : 2) * static_cast<size_t>(pairs ? pair_chunk_bytes(warps, nc)
-                                                     : nc * static_cast<int>(sizeof(PRec))) +
+  return (void)dbuf,
+         (kRecOffset +
+          2 * static_cast<size_t>(pairs ? pair_chunk_bytes(warps, nc)
+                                        : nc * static_cast<int>(sizeof(PRec))) +
           127) / 128 * 128;
 }
 inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp) {
   return pat_raw_offset(s.warps, s.nc, s.pairs, s.dbuf) +
-         2 * static_cast<size_t>(s.nc) * raw_bytes(kind, bin, lp, 32 * s.h) +
+         static_cast<size_t>(s.nc) * raw_bytes(kind, bin, lp, 32 * s.h) +
          (s.dbuf ? 2 : 1) * static_cast<size_t>(s.nc) * lp * 4;
 }
 

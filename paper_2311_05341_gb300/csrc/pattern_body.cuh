@@ -40,8 +40,8 @@ namespace pattern {
 
 struct PSmem {
   uint32_t bar_base;  // 2 mbarriers
-  unsigned char* recs;  // [2 or 3][NC] PRec, or [2 or 3] pair chunks
-  uint8_t* raw;       // [2][NC][lraw]
+  unsigned char* recs;  // [2][NC] PRec, or [2] pair chunks
+  uint8_t* raw;       // [NC][lraw]
   uint32_t* pw;       // [1 or 2][NC][lp] window words
 };
 
@@ -52,7 +52,7 @@ __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
   sm.bar_base = smem_u32(smem);
   sm.recs = smem + kRecOffset;
   sm.raw = smem + kRawOff;
-  sm.pw = reinterpret_cast<uint32_t*>(sm.raw + 2 * NC * static_cast<size_t>(lraw));
+  sm.pw = reinterpret_cast<uint32_t*>(sm.raw + NC * static_cast<size_t>(lraw));
   return sm;
 }
 
@@ -122,19 +122,20 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 // One (DM block, time tile) work unit.  Returns false after a bounded wait
 // gave up (the status word is set).
 //
-// Stage st uses raw buffer st % 2 and record buffer st % kRecBufs.  With
-// DBUF the window words are double-buffered too (stage st in window buffer
-// st % 2) and one barrier per stage suffices: the barrier after unpacking
-// stage st also certifies that every warp finished computing stage st - 1,
-// so the copies of stage st + 2 (raw buffer st % 2, record buffer
-// (st + 2) % 3) and the unpacking of stage st + 1 may start while warps still
-// compute stage st.  Without DBUF a second barrier ends each stage.
+// One raw buffer: the copies of stage st + 1 are issued as soon as stage st
+// is unpacked (after the barrier that follows the unpacking) and land while
+// stage st is computed, so the raw bytes need no second buffer.  Records use
+// two buffers (stage st in st % 2).  With DBUF the window words are
+// double-buffered (stage st in window buffer st % 2) and that barrier is the
+// only one per stage: it also certifies that every warp finished computing
+// stage st - 1, whose window and record buffers are the next ones reused.
+// Without DBUF a second barrier ends each stage.
 template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
   constexpr int kPairW = 32 * H;
-  constexpr int kRecBufs = DBUF ? 3 : 2;
+  constexpr int kRecBufs = 2;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int64_t t0 = tile * pat_tile_samples(KIND, H);
   const int n_st = (p.n_chan + NC - 1) / NC;
@@ -155,10 +156,10 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   auto issue = [&](int st, int32_t base) {
     unsigned char* dst = rec_buf(st % kRecBufs);
     if constexpr (PAIRS)
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid,
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, 0, t0, base, tid,
                             pair_chunk(p, blk, n_st, st), p.chunk_bytes, dst);
     else
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, st & 1, t0, base, tid, cr.src(st),
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, 0, t0, base, tid, cr.src(st),
                             cr.bytes(st), dst);
   };
   if (tid <= NC) {
@@ -166,14 +167,13 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     // by the copies: order those generic-proxy reads before them.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     issue(0, base_of(0));
-    if (n_st > 1) issue(1, base_of(1));
   }
-  int32_t next_base = base_of(2);
-  auto issue_next = [&](int st) {  // copies of stage st + 2 into the buffers stage st freed
-    if (tid <= NC && st + 2 < n_st) {
+  int32_t next_base = base_of(1);
+  auto issue_next = [&](int st) {  // copies of stage st + 1 once stage st is unpacked
+    if (tid <= NC && st + 1 < n_st) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(st + 2, next_base);
-      next_base = base_of(st + 3);
+      issue(st + 1, next_base);
+      next_base = base_of(st + 2);
     }
   };
 
@@ -190,13 +190,13 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
   for (int st = 0; st < n_st; ++st) {
     const int buf = st & 1;
-    const uint32_t parity = (st >> 1) & 1;
+    const uint32_t parity = st & 1;  // the one stage barrier completes a phase per stage
     const int nc = min(NC, p.n_chan - st * NC);
     uint32_t* pwb = sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
     auto unpack = [&]() {  // raw bytes of stage st into window words
       // Warp w takes channels w, w + NW, ...; its lanes take consecutive units
       // (conflict-free 16-byte stores).
-      const uint8_t* rawb = sm.raw + static_cast<size_t>(buf) * NC * p.lraw;
+      const uint8_t* rawb = sm.raw;
       for (int ch = w; ch < nc; ch += NW) {
         const uint8_t* raw_ch = rawb + static_cast<size_t>(ch) * p.lraw;
         uint32_t* dst = pwb + static_cast<size_t>(ch) * p.lp;
@@ -204,23 +204,17 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
           *reinterpret_cast<uint4*>(dst + 4 * q) = unpack_unit<KIND, kPairW>(raw_ch, q, p.bin);
       }
     };
-    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
-    if (DBUF && ok) unpack();
+    const bool ok = mbar_wait(sm.bar_base, parity);
+    if (ok) unpack();
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.err, kErrTimeout);
-        // Let copies still in flight land before the CTA exits (bounded).
-        mbar_wait(sm.bar_base + 8u * buf, parity);
-        if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
+        // Let the copies still in flight land before the CTA exits (bounded).
+        mbar_wait(sm.bar_base, parity);
       }
       return false;
     }
-    if constexpr (DBUF) {
-      issue_next(st);
-    } else {
-      unpack();
-      __syncthreads();
-    }
+    issue_next(st);
 
     // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
     // PTX labels, appear once per instantiation.
@@ -269,10 +263,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     }
     since += nc;
     rb = rb + 1 == kRecBufs ? 0 : rb + 1;
-    if constexpr (!DBUF) {
-      __syncthreads();  // window words, raw[buf] and recs[buf] are free
-      issue_next(st);
-    }
+    if constexpr (!DBUF) __syncthreads();  // the window words are free
     if (since + NC > p.flush || st == n_st - 1) {
       // The transpose tiles reuse this stage's window buffer: wait until every
       // warp has finished reading it.
@@ -280,6 +271,9 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
       first = false;
       since = 0;
+      // The next stage unpacks into this window buffer (single-buffered):
+      // wait until every warp has read its transpose tile back.
+      if constexpr (!DBUF) __syncthreads();
     }
   }
   return true;
