@@ -514,11 +514,85 @@ def run_stream(args):
                         "data_seconds_done": st["chunks"] * chunk_s,
                         "real_time_factor_aggregate": st["chunks"] * chunk_s / wall,
                         "dm_samples_per_s": st["chunks"] * dm_samples_per_chunk / wall})
+    sat = _stream_saturated(args, spec, pool, chunk, plan_cache)
     print(json.dumps({"metric": "p50/p99 chunk latency, real-time factor",
                       "workload": "stream: 64 beams u8 4096 ch, 1670 MHz top, 320 MHz band, "
                                   "64 us, chunks 65536 + overlap; DM 0-150/0.1 b1, 150-300/0.2 b2, "
                                   "300-1000/0.5 b4, 1000-2000/1.0 b8",
-                      "hbm_budget_gb": args.hbm_budget_gb, "results": results}))
+                      "hbm_budget_gb": args.hbm_budget_gb, "results": results,
+                      "saturated": sat}))
+
+
+def _stream_saturated(args, spec, pool, chunk, plan_cache):
+    """Server against the plain per-beam path on the same chunks, all queued at
+    once: the plain path runs every beam's chunks one after another on one
+    stream (copy in, dd_run, keep the overlap), the server launches them on
+    per-beam streams.  Both end with each beam's last window output, which
+    depends on every earlier chunk through the overlap; they must be equal."""
+    import torch
+    from paper_2311_05341_gb300 import stream as dds
+    from paper_2311_05341_gb300.batch import input_buffer
+
+    n_beams, per_beam = args.stream_sat_beams, args.stream_sat_chunks
+    srv = dds.StreamServer(chunk, int(args.hbm_budget_gb * 2**30), plan_cache=plan_cache)
+    plan = srv._plan(spec)
+    ov = dds.overlap_for(plan, spec.ranges)
+    n = ov + chunk
+    dm_samples_per_chunk = sum(
+        k * (chunk // r[3]) for k, r in zip(plan.info(0)["n_dm"], spec.ranges))
+    jobs = [(b, pool[(b + j) % len(pool)]) for j in range(per_beam) for b in range(n_beams)]
+
+    # Plain: one stream, beam after beam.
+    windows = [input_buffer(spec.dtype, len(spec.freqs), n, "cuda") for _ in range(n_beams)]
+    outs = [plan.empty_output(n) for _ in range(n_beams)]
+
+    def plain():
+        for b in range(n_beams):
+            for j in range(per_beam):
+                windows[b][:, ov:n].copy_(pool[(b + j) % len(pool)], non_blocking=True)
+                plan.run(windows[b], out=outs[b], n_samp=n)
+                tail = windows[b][:, chunk:n]
+                windows[b][:, :ov].copy_(tail.clone() if ov > chunk else tail)
+
+    def server():
+        for b in range(n_beams):
+            srv.request(b, spec)
+        for b, c in jobs:
+            srv.submit(b, c)
+        srv.drain()
+
+    for w in windows:
+        w.zero_()
+    plain()  # warm-up (plans, allocator)
+    torch.cuda.synchronize()
+    for w in windows:
+        w.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+
+    server()  # warm-up: the beams stay admitted; reset their windows
+    torch.cuda.synchronize()
+    for b in range(n_beams):
+        srv.beams[b].window.zero_()
+    srv.latencies.clear()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    server()
+    torch.cuda.synchronize()
+    t_srv = time.perf_counter() - t0
+    same = all(torch.equal(srv.beams[b].out, outs[b]) for b in range(n_beams))
+    total = len(jobs) * dm_samples_per_chunk
+    st = srv.stats()
+    return {"beams": n_beams, "chunks": len(jobs),
+            "server_dm_samples_per_s": total / t_srv, "server_s": t_srv,
+            "plain_per_beam_dm_samples_per_s": total / t_plain, "plain_s": t_plain,
+            "server_over_plain": t_plain / t_srv,
+            "real_time_factor_server": len(jobs) * chunk * spec.t_samp / t_srv,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "outputs_identical_to_plain": bool(same)}
 
 
 def run_frontend(args):
@@ -614,6 +688,8 @@ def main():
                              "stream", "frontend"])
     ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
     ap.add_argument("--stream-seconds", type=float, default=15.0)
+    ap.add_argument("--stream-sat-beams", type=int, default=16)
+    ap.add_argument("--stream-sat-chunks", type=int, default=4)
     ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-rows-reference", type=int, default=16)
