@@ -87,8 +87,9 @@ typedef struct {
   int64_t max_delay_raw;              /* max over ranges of (s_max+1)*bin - 1 raw samples */
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
-  int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane, or
-                                          DD_TILE_PATTERN (0: generic kernel) */
+  int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane,
+                                          DD_TILE_PATTERN or DD_TILE_MERGE
+                                          (0: generic kernel) */
 } dd_plan_info;
 
 /* Forward kernels a range can run on (dd_plan_info.kernel). */
@@ -97,10 +98,17 @@ typedef struct {
                                lanes); bins with bin * sample bytes dividing 16 */
 
 /* Tile code of the pattern family (dd_plan_set_tile, dd_plan_info.tile_dms):
- * 4 DMs per lane, one indexed branch per channel over the 27 patterns of
- * per-DM shift increments in {0, 1, 2}.  Plans whose shift of some channel
- * grows by more than 2 between consecutive trial DMs cannot use it. */
+ * 4 DMs per lane, one indexed branch per channel (or channel pair) over the
+ * 32 patterns of per-DM shift increments a or a + 1 between a lane's DMs,
+ * a = 0..3.  Plans whose shift of some channel grows by more than 4 between
+ * consecutive trial DMs cannot use it. */
 #define DD_TILE_PATTERN 0x104
+/* The pattern tile with channel classes (uint8 input at bin 1): per group of
+ * 16 consecutive trial DMs, channels whose shifts differ by constants over
+ * those DMs are summed once into one staged window, read at one channel's
+ * shifts.  Exact: the output is the same as channel by channel.  Only on
+ * request (the automatic choice does not take it). */
+#define DD_TILE_MERGE 0x105
 
 /*
  * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
@@ -151,7 +159,7 @@ dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_sa
 
 /*
  * Choose the tile of range `range`: `tile` is the offset tile's DM count per
- * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, or 0 = automatic.  Per-plan tile
+ * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, DD_TILE_MERGE, or 0 = automatic.  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
  * Rebuilds the plan's device tables, so it must be followed by
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.

@@ -140,9 +140,11 @@ class Plan:
         """Pick the register tile of range r and re-upload.
 
         tile: DMs per lane of the offset tile (8, 6, 4, 2, 1), "pattern"
-        (DD_TILE_PATTERN), or 0 for the automatic choice.
+        (DD_TILE_PATTERN), "merge" (DD_TILE_MERGE: the pattern tile with
+        channel classes), or 0 for the automatic choice.
         """
-        code = _lib.DD_TILE_PATTERN if tile == "pattern" else int(tile)
+        code = {"pattern": _lib.DD_TILE_PATTERN, "merge": _lib.DD_TILE_MERGE}.get(tile, tile)
+        code = int(code)
         check(self._lib.dd_plan_set_tile(self._h, int(r), code))
         if self.workspace is not None:
             self.upload(self.workspace.device if device is None else device)

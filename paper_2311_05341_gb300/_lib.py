@@ -20,6 +20,7 @@ DD_U8, DD_U16, DD_F32, DD_U4 = 1, 2, 3, 4
 DD_MAX_RANGES = 16
 DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 DD_TILE_PATTERN = 0x104
+DD_TILE_MERGE = 0x105
 
 
 class DDError(RuntimeError):

@@ -56,7 +56,10 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
-    o->tile_dms[i] = !rp.tile_ok ? 0 : (rp.tile_pattern ? DD_TILE_PATTERN : rp.tile_dr);
+    o->tile_dms[i] = !rp.tile_ok        ? 0
+                     : !rp.tile_pattern ? rp.tile_dr
+                     : tk::kPatShapes[rp.tile_shape].merge ? DD_TILE_MERGE
+                                                           : DD_TILE_PATTERN;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
     if (raw > o->max_delay_raw) o->max_delay_raw = raw;
   }
@@ -265,8 +268,9 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
     return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
-  if (tile != 0 && tile != DD_TILE_PATTERN && !tk::shape_for(tile))
-    return fail(DD_ERR_INVALID_ARG, "tile must be 0, 1, 2, 4, 6, 8 or DD_TILE_PATTERN");
+  if (tile != 0 && tile != DD_TILE_PATTERN && tile != DD_TILE_MERGE && !tk::shape_for(tile))
+    return fail(DD_ERR_INVALID_ARG,
+                "tile must be 0, 1, 2, 4, 6, 8, DD_TILE_PATTERN or DD_TILE_MERGE");
   bool ok;
   try {
     ok = retile_range(plan, static_cast<size_t>(range), tile);

@@ -123,7 +123,8 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
           if (g == b->groups.size()) b->groups.push_back({rp.tile_kind, rp.tile_shape});
           b->pjob_group.push_back(static_cast<int32_t>(g));
           b->groups[g].smem = std::max(
-              b->groups[g].smem, tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp));
+              b->groups[g].smem,
+              tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp, rp.tile_nv));
           ts = tk::pat_tile_samples(rp.tile_kind, ps.h);
           dms = static_cast<double>(ps.warps) * tk::kPatDr;
         } else {

@@ -48,6 +48,7 @@ struct RangePlan {
   int32_t tile_units_shift = 0;
   size_t tile_chunk_off = 0;    // pair tiles: byte offset of the pair chunks in tile_recs
   int32_t tile_chunk_bytes = 0; // pair tiles: bytes per (DM block, stage) chunk
+  int32_t tile_nv = 0;          // merged pattern tiles: window slots per round
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]

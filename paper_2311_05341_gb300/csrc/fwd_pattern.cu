@@ -13,30 +13,32 @@
 namespace dd {
 namespace tk {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   using namespace pattern;
-  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF>(smem, p.lraw);
+  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF, MERGE>(smem, p.lraw);
   if (threadIdx.x == 0) {
     mbar_init(sm.bar_base, NC + 1);
     mbar_init(sm.bar_base + 8, NC + 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blockIdx.x % p.n_blocks,
-                                               blockIdx.x / p.n_blocks + p.tile0);
+  const int blk = blockIdx.x % p.n_blocks;
+  const int64_t tile = blockIdx.x / p.n_blocks + p.tile0;
+  if constexpr (MERGE) pat_body_merge<H, NW, NC, AMAX>(p, sm, blk, tile);
+  else pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blk, tile);
 }
 
 }  // namespace tk
 
 namespace {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
-  const size_t smem =
-      tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX}, prm.lp);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX>;
+  const size_t smem = tk::pat_smem_bytes(
+      KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX, MERGE}, prm.lp, prm.nv);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX, MERGE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -50,8 +52,8 @@ int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t s
   if constexpr (!tk::pat_shape_serves(s, KIND)) {
     return static_cast<int>(cudaErrorInvalidValue);  // the planner never picks it
   } else {
-    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(prm, grid,
-                                                                                  st);
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax, s.merge>(
+        prm, grid, st);
   }
 }
 

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     if (it >= b.n_items) break;
     const BatchItem item = b.items[it];
     const TileParams p = b.jobs[item.job].p;
-    const pattern::PSmem sm = pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf>(smem, p.lraw);
+    const pattern::PSmem sm =
+        pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf, s.merge>(smem, p.lraw);
     __syncthreads();  // every thread has read item_slot; the previous item is done
     if (threadIdx.x == 0) {
       // Stage phases restart at 0 for every item: re-initialise the barriers
@@ -55,9 +56,13 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     }
     barriers_valid = true;
     __syncthreads();
-    if (!pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(p, sm, item.blk,
-                                                                            item.tile))
-      break;
+    bool ok;
+    if constexpr (s.merge)
+      ok = pattern::pat_body_merge<s.h, s.warps, s.nc, s.amax>(p, sm, item.blk, item.tile);
+    else
+      ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(p, sm, item.blk,
+                                                                               item.tile);
+    if (!ok) break;
   }
 }
 

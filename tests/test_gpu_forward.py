@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import paper_2311_05341_gb300 as dd
+from paper_2311_05341_gb300._lib import DD_TILE_MERGE as TILE_MERGE
 from paper_2311_05341_gb300._lib import DD_TILE_PATTERN as TILE_PATTERN
 from synth import workloads, channel_freqs, filterbank
 
@@ -133,12 +134,14 @@ def test_tiled_full_planes_every_shape(dtype, seed):
     ref_abs = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges, take_abs=True)
     xd = padded_device(x)
     # Steps of at most 1.7 samples keep every per-DM increment in {0, 1, 2}:
-    # the pattern tile serves all these plans too.
-    for dms in (8, 6, 4, 2, 1, "pattern"):
+    # the pattern tile serves all these plans too (uint8: also with channel
+    # classes).
+    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge",) if dtype == "u8" else ())
+    for dms in tiles:
         plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
         info = plan.info(b.n_samp)
-        code = TILE_PATTERN if dms == "pattern" else dms
+        code = {"pattern": TILE_PATTERN, "merge": TILE_MERGE}.get(dms, dms)
         assert info["kernel"] == ["tiled"] and info["tile_dms"] == [code]
         got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
         if dtype == "f32":
@@ -168,7 +171,7 @@ def test_pattern_steep_plans(dtype, seed):
     ref = oracle.forward(x, freqs, f_high, 64e-6, [r])[0]
     ref_abs = oracle.forward(x, freqs, f_high, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
-    for tile in ("pattern", 1):
+    for tile in ("pattern", 1) + (("merge",) if dtype == "u8" else ()):
         plan = dd.Plan(freqs, f_high, 64e-6, [r], dtype)
         plan.set_tile(0, tile)
         got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
@@ -194,7 +197,7 @@ def test_tiled_decimation_every_shape(dtype, b):
     ref_abs = oracle.forward(x, freqs, 1400.0, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
     ran = 0
-    for dms in (8, 6, 4, 2, 1, "pattern"):
+    for dms in (8, 6, 4, 2, 1, "pattern", "merge"):
         plan = dd.Plan(freqs, 1400.0, 64e-6, [r], dtype)
         try:
             plan.set_tile(0, dms)
@@ -281,9 +284,9 @@ def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
         np.testing.assert_array_equal(g, o)
 
 
-@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, 6),
-                                       (workloads.paper_u16, 0)],
-                         ids=["paper_u8", "paper_u8_offset6", "paper_u16"])
+@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, "pattern"),
+                                       (workloads.paper_u8, 6), (workloads.paper_u16, 0)],
+                         ids=["paper_u8", "paper_u8_pattern", "paper_u8_offset6", "paper_u16"])
 def test_paper_scale_sampled(make, tile):
     beam = make()
     x, tables, n_dm, n_out = oracle_input(beam)

@@ -191,8 +191,10 @@ def test_pattern_tile_selection():
     assert info["kernel"] == ["tiled"] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
     # Per-warp pair lists against 64-byte offset records: other table sizes.
     assert info["workspace_bytes"] != ws_offset
+    plan.set_tile(0, "merge")
+    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_MERGE]
     plan.set_tile(0, 6)
-    plan.set_tile(0, 0)  # automatic: the pattern tile again
+    plan.set_tile(0, 0)  # automatic: the pattern tile (channel classes only on request)
     assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
     tiny = workloads.tiny_u8()  # 8 samples per DM step at the lowest channel
     plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
@@ -201,8 +203,29 @@ def test_pattern_tile_selection():
     assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
     assert plan.info(tiny.n_samp)["tile_dms"] == [2]
     with pytest.raises(dd.DDError) as ei:
+        plan.set_tile(0, "merge")
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    with pytest.raises(dd.DDError) as ei:
         plan.set_tile(0, 3)
     assert ei.value.status == _lib.DD_ERR_INVALID_ARG
+
+
+def test_merge_tile_selection():
+    """Channel classes serve uint8 at bin 1 only; other kinds and bins keep the
+    pattern tile."""
+    paper = workloads.paper_u8()
+    for dtype in ("u16", "f32", "u4"):
+        plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, dtype,
+                       upload=False)
+        assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN], dtype
+        with pytest.raises(dd.DDError) as ei:
+            plan.set_tile(0, "merge")
+        assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    binned = [(0.0, 40.0, 0.2, 2)]
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, binned, "u8", upload=False)
+    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
+    with pytest.raises(dd.DDError):
+        plan.set_tile(0, "merge")
 
 
 def test_u4_plan_selection_and_refusals():
