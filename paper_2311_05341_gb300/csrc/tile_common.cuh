@@ -236,6 +236,12 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
   asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
+// Two adjacent int32 outputs (8-byte aligned) in one 64-bit reduction: exact
+// while both are non-negative sums below 2^32 (no carry crosses the halves).
+__device__ __forceinline__ void red_add_pair(int32_t* p, uint32_t lo, uint32_t hi) {
+  const unsigned long long v = static_cast<unsigned long long>(hi) << 32 | lo;
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // Transposed store tile of a register tile with H window words per lane.
 // Lane l holds positions p = H l + j (j < H); uint8 at bin 1 also holds
@@ -294,7 +300,26 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
         }
       }
       __syncwarp();
-      if (d < p.n_dm) {
+      bool paired = false;
+      if constexpr (!ST::kPad && KIND != kF32) {
+        // Later widenings of integer sums (non-negative) with the row 8-byte
+        // aligned: lane l adds positions 64 m + 2 l and + 1 in one 64-bit
+        // reduction (the tile holds position p at index p).
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        if (!first && d < p.n_dm && (reinterpret_cast<uintptr_t>(row) & 7u) == 0) {
+          constexpr int kPos = 32 * ST::kRows;
+#pragma unroll
+          for (int m = 0; m < (kPos + 63) / 64; ++m) {
+            const int pos = 64 * m + 2 * l;
+            if (pos >= kPos || pos >= lim) continue;
+            const uint2 v = *reinterpret_cast<const uint2*>(tr + pos);
+            if (pos + 1 < lim) red_add_pair(row + pos, v.x, v.y);
+            else red_add(row + pos, static_cast<int32_t>(v.x));
+          }
+          paired = true;
+        }
+      }
+      if (d < p.n_dm && !paired) {
         OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
         constexpr int kCh = (ST::kRows + 1) / 2;  // rows per half
 #pragma unroll
