@@ -430,7 +430,7 @@ __device__ __forceinline__ bool pat_body_merge(const TileParams& p, const PSmem&
     since += nc;
     rb = rb + 1 == kRecBufs ? 0 : rb + 1;
     if (since + NC > p.flush || st == n_st - 1) {
-      widen_store<KIND, kPatDr, NW, NC, H>(p, sm.pw, acc, blk, t0, first);
+      widen_store<KIND, kPatDr, NW, NC, H, false>(p, sm.pw, acc, blk, t0, first);
       first = false;
       since = 0;
       __syncthreads();  // transpose tiles read back before the next windows are built

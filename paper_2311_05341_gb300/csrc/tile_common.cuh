@@ -263,7 +263,7 @@ struct StoreTile {
 // into the output rows through the warp's transposed shared tile.  The tiles
 // live in the window buffer pw; when it cannot hold one per warp, the warps
 // take turns in `groups` rounds.  Called by every thread of the CTA.
-template <int KIND, int DR, int NW, int NC, int H>
+template <int KIND, int DR, int NW, int NC, int H, bool kPackedTile = true>
 __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
                                             AccT<KIND> (&acc)[DR][H], int blk, int64_t t0,
                                             bool first) {
@@ -284,6 +284,43 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
 #pragma unroll
     for (int i = 0; i < DR; ++i) {
       const int d = blk * (DR * NW) + w * DR + i;
+      if constexpr (kPackedTile && KIND == kU8 && !ST::kPad) {
+        // uint8 pairs (widened every 256 channels), row 8-byte aligned:
+        // packed words: the tile keeps each accumulator
+        // word whole (position p and p + 32H in its halves) and lane l takes
+        // words 64 m + 2 l and + 1, i.e. output pairs (p, p + 1) and
+        // (p + 32H, p + 32H + 1): one 64-bit store or reduction each.
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        if ((reinterpret_cast<uintptr_t>(row) & 7u) == 0) {
+#pragma unroll
+          for (int j = 0; j < H; ++j) {
+            tr[wbase + j] = acc[i][j];
+            acc[i][j] = 0u;
+          }
+          __syncwarp();
+          if (d < p.n_dm) {
+            auto put = [&](int pos, uint32_t a, uint32_t b) {
+              if (pos + 1 < lim) {
+                if (first) *reinterpret_cast<int2*>(row + pos) = make_int2(a, b);
+                else red_add_pair(row + pos, a, b);
+              } else if (pos < lim) {
+                if (first) row[pos] = static_cast<int32_t>(a);
+                else red_add(row + pos, static_cast<int32_t>(a));
+              }
+            };
+#pragma unroll
+            for (int m = 0; m < (ST::kPairW + 63) / 64; ++m) {
+              const int p0 = 64 * m + 2 * l;
+              if (p0 >= ST::kPairW) continue;
+              const uint2 v = *reinterpret_cast<const uint2*>(tr + p0);
+              put(p0, v.x & 0xffffu, v.y & 0xffffu);
+              put(p0 + ST::kPairW, v.x >> 16, v.y >> 16);
+            }
+          }
+          __syncwarp();
+          continue;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < H; ++j) {
         if constexpr (packed_pairs(KIND)) {
