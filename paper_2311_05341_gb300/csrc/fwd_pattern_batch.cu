@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     const int it = item_slot;
     if (it >= b.n_items) break;
     const BatchItem item = b.items[it];
-    const TileParams p = b.jobs[item.job].p;
+    // The job's parameters stay in global memory (read-only for the launch):
+    // a copy in registers would crowd out the accumulators.
+    const TileParams& p = static_cast<const PatBatchJob* __restrict__>(b.jobs)[item.job].p;
     const pattern::PSmem sm =
         pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf, s.merge>(smem, p.lraw);
     __syncthreads();  // every thread has read item_slot; the previous item is done

@@ -232,7 +232,8 @@ __device__ __forceinline__ uint32_t batch_item(const BatchJob* job, int blk, int
                                             uint32_t gstage, unsigned char* smem,
                                             int32_t max_lraw) {
   const Smem sm = smem_layout<NC>(smem, max_lraw);
-  const TileParams p = job->p;
+  // Parameters read from global memory as needed (read-only for the launch).
+  const TileParams& p = static_cast<const BatchJob* __restrict__>(job)->p;
   uint32_t g = gstage;
   return tile_body<KIND, DR, NW, NC>(p, sm, blk, tile, g) ? g : kStageError;
 }
