@@ -300,12 +300,57 @@ def run_ours(args):
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
     }
+    if beam.dtype == "f32":
+        line["adjoint"] = _adjoint_timing(args, plan, x, info, beam, stream)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(beam, x_host, info, args.cpu_rows)
         if beam.dtype in ("u8", "u16", "f32") and len(beam.ranges) == 1 and beam.ranges[0][3] == 1:
             line["cpu_baseline_tiled"] = cpu_tiled_baseline(beam, x_host, plan.shifts(0), info,
                                                             args.cpu_tiled_rows)
     print(json.dumps(line))
+
+
+def _adjoint_timing(args, plan, x, info, beam, stream):
+    """Float32 plans: the adjoint gather (dd_run_adjoint) alone, and one
+    training step through the autograd Function (forward, loss = sum Y * W,
+    backward to the filterbank), each timed with CUDA events."""
+    import torch
+    from paper_2311_05341_gb300 import autograd as ddg
+
+    n = beam.n_samp
+    g = torch.Generator(device="cuda").manual_seed(4)
+    w = torch.randn(info["out_elems"], device="cuda", generator=g)
+    xbar = torch.empty((beam.n_chan, (n + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+    xr = x[:, :n].clone().requires_grad_(True)
+
+    def adjoint():
+        plan.run_adjoint(w, n, xbar=xbar, stream=stream)
+
+    def step():
+        xr.grad = None
+        planes = ddg.dedisperse(xr, plan)
+        loss = sum((p.reshape(-1) * wp).sum() for p, wp in
+                   zip(planes, torch.split(w, [p.numel() for p in planes])))
+        loss.backward()
+
+    out = {}
+    for name, fn in (("adjoint", adjoint), ("train_step", step)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms": ms,
+                     "dm_samples_per_s": sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
+                     / (ms / 1e3)}
+    out["what"] = ("adjoint: dd_run_adjoint gather of a random cotangent; train_step: "
+                   "autograd forward + loss sum(Y W) + backward (forward, adjoint, elementwise)")
+    return out
 
 
 def cpu_baseline(beam, x_host, info, n_rows):

@@ -7,10 +7,11 @@
 // sample X[c][t] enters output Y_r[d][floor(t/b_r) - s_r(c,d)] with weight 1
 // (Eq. 3 with time binning), so this is exactly the derivative of Eq. 3 with
 // respect to X.  The paper has no adjoint; this mirrors its forward tiling with
-// the roles of channel and DM swapped: a CTA owns 8 channels x 256 raw
-// samples, and for each chunk of DMs it stages the needed window of each DM's
-// output row in shared memory, then every thread gathers from it at its
-// channel's offset.
+// the roles of channel and DM swapped: a CTA owns 64 channels x 256 raw
+// samples (8 warps x 8 channels, lane l: samples l + 32 k), and for each chunk
+// of DMs it stages the needed window of each DM's output row in shared memory
+// once for all 64 channels, then every thread gathers from it at each of its
+// channels' offsets.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,10 +22,13 @@ namespace dd {
 
 namespace {
 
-constexpr int kAdjChan = 8;        // channels per CTA (one per warp row)
+constexpr int kAdjWarpChan = 8;                 // channels per warp
+constexpr int kAdjWarps = 8;
+constexpr int kAdjChan = kAdjWarpChan * kAdjWarps;  // channels per CTA
+static_assert(kAdjChan == kAdjChanBlock, "adjoint span is planned for this block");
 constexpr int kAdjSampPerThread = 8;
 constexpr int kAdjTile = 32 * kAdjSampPerThread;  // raw samples per CTA
-constexpr int kAdjDmChunk = 32;
+constexpr int kAdjDmChunk = 32;  // DMs staged per step (fewer when the windows are wide)
 
 struct AdjRange {
   const int32_t* shifts;  // [n_dm][n_chan]
@@ -42,24 +46,26 @@ struct AdjParams {
   int64_t n_samp;
   int64_t stride;
   int32_t max_win;
+  int32_t dm_chunk;       // DMs staged per step (<= kAdjDmChunk)
 };
 
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams prm, float* __restrict__ xbar) {
   extern __shared__ unsigned char smem_raw[];
   float* win_buf = reinterpret_cast<float*>(smem_raw);                      // [chunk][max_win]
-  int32_t* sh_buf = reinterpret_cast<int32_t*>(win_buf + kAdjDmChunk * prm.max_win);  // [chunk][8]
-  int32_t* hi_buf = sh_buf + kAdjDmChunk * kAdjChan;                        // [chunk]
+  int32_t* sh_buf = reinterpret_cast<int32_t*>(win_buf + prm.dm_chunk * prm.max_win);  // [chunk][64]
+  int32_t* hi_buf = sh_buf + prm.dm_chunk * kAdjChan;                        // [chunk]
 
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int32_t n_cblk = (prm.n_chan + kAdjChan - 1) / kAdjChan;
   const int64_t tile = blockIdx.x / n_cblk;
   const int32_t c_first = (blockIdx.x % n_cblk) * kAdjChan;
-  const int32_t c = min(c_first + ty, prm.n_chan - 1);
   const int64_t t_raw0 = tile * kAdjTile;
 
-  float acc[kAdjSampPerThread];
+  float acc[kAdjWarpChan][kAdjSampPerThread];
 #pragma unroll
-  for (int k = 0; k < kAdjSampPerThread; ++k) acc[k] = 0.f;
+  for (int j = 0; j < kAdjWarpChan; ++j)
+#pragma unroll
+    for (int k = 0; k < kAdjSampPerThread; ++k) acc[j][k] = 0.f;
 
   for (int32_t ri = 0; ri < prm.n_ranges; ++ri) {
     const AdjRange rr = prm.r[ri];
@@ -69,22 +75,24 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams prm, float
     for (int k = 0; k < kAdjSampPerThread; ++k)
       rel[k] = static_cast<int32_t>((t_raw0 + tx + 32 * k) / rr.bin - u0);
 
-    for (int32_t d0 = 0; d0 < rr.n_dm; d0 += kAdjDmChunk) {
-      const int32_t nd = min(kAdjDmChunk, rr.n_dm - d0);
+    for (int32_t d0 = 0; d0 < rr.n_dm; d0 += prm.dm_chunk) {
+      const int32_t nd = min(prm.dm_chunk, rr.n_dm - d0);
       __syncthreads();
-      // Shifts of the chunk's DMs for the CTA's channels and their maximum.
-      for (int32_t dd = ty; dd < nd; dd += 8) {
-        const int32_t d = d0 + dd;
-        int32_t s = -0x7fffffff;
-        if (tx < kAdjChan) {
-          const int32_t cc = min(c_first + tx, prm.n_chan - 1);
-          s = rr.shifts[static_cast<int64_t>(d) * prm.n_chan + cc];
-          sh_buf[dd * kAdjChan + tx] = s;
-        }
-        const int32_t hi = __reduce_max_sync(0xffffffffu, s);
+      // Shifts of the chunk's DMs for the CTA's channels (channels past the
+      // last take its shifts; they are never written).
+      for (int32_t e = tid; e < nd * kAdjChan; e += kAdjWarps * 32) {
+        const int32_t dd = e / kAdjChan, cc = e % kAdjChan;
+        const int32_t c = min(c_first + cc, prm.n_chan - 1);
+        sh_buf[e] = rr.shifts[static_cast<int64_t>(d0 + dd) * prm.n_chan + c];
+      }
+      __syncthreads();
+      // Warp ty stages DMs ty, ty + 8, ...: the row window from the block's
+      // largest shift, ybar[d][u0 - hi + k], k < win (0 outside [0, n_out)).
+      for (int32_t dd = ty; dd < nd; dd += kAdjWarps) {
+        const int32_t hi = __reduce_max_sync(
+            0xffffffffu, max(sh_buf[dd * kAdjChan + tx], sh_buf[dd * kAdjChan + 32 + tx]));
         if (tx == 0) hi_buf[dd] = hi;
-        // Window of output row d: ybar[d][u0 - hi + k], k < win (0 outside [0, n_out)).
-        const float* yrow = rr.ybar + static_cast<int64_t>(d) * rr.n_out;
+        const float* yrow = rr.ybar + static_cast<int64_t>(d0 + dd) * rr.n_out;
         for (int32_t k = tx; k < rr.win; k += 32) {
           const int64_t u = u0 - hi + k;
           win_buf[dd * prm.max_win + k] = (u >= 0 && u < rr.n_out) ? yrow[u] : 0.f;
@@ -92,20 +100,28 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams prm, float
       }
       __syncthreads();
       for (int32_t dd = 0; dd < nd; ++dd) {
-        const int32_t off = hi_buf[dd] - sh_buf[dd * kAdjChan + ty];
-        const float* w = win_buf + dd * prm.max_win + off;
+        const int32_t hi = hi_buf[dd];
+        const float* w = win_buf + dd * prm.max_win + hi;
+        const int32_t* sh = sh_buf + dd * kAdjChan + ty * kAdjWarpChan;
 #pragma unroll
-        for (int k = 0; k < kAdjSampPerThread; ++k) acc[k] += w[rel[k]];
+        for (int j = 0; j < kAdjWarpChan; ++j) {
+          const float* wj = w - sh[j];
+#pragma unroll
+          for (int k = 0; k < kAdjSampPerThread; ++k) acc[j][k] += wj[rel[k]];
+        }
       }
     }
   }
 
-  if (c_first + ty < prm.n_chan) {
+#pragma unroll
+  for (int j = 0; j < kAdjWarpChan; ++j) {
+    const int32_t c = c_first + ty * kAdjWarpChan + j;
+    if (c >= prm.n_chan) continue;
     float* xrow = xbar + static_cast<int64_t>(c) * prm.stride;
 #pragma unroll
     for (int k = 0; k < kAdjSampPerThread; ++k) {
       const int64_t t = t_raw0 + tx + 32 * k;
-      if (t < prm.n_samp) xrow[t] = acc[k];
+      if (t < prm.n_samp) xrow[t] = acc[j][k];
     }
   }
 }
@@ -135,9 +151,11 @@ int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64
     max_win = std::max(max_win, a.win);
   }
   prm.max_win = max_win;
-  const size_t smem = static_cast<size_t>(kAdjDmChunk) * max_win * sizeof(float) +
-                      static_cast<size_t>(kAdjDmChunk) * (kAdjChan + 1) * sizeof(int32_t);
-  if (smem > 200 * 1024) return static_cast<int>(cudaErrorInvalidConfiguration);
+  const size_t per_dm = static_cast<size_t>(max_win) * sizeof(float) + (kAdjChan + 1) * sizeof(int32_t);
+  const size_t smem_max = 200 * 1024;
+  prm.dm_chunk = static_cast<int32_t>(std::min<size_t>(kAdjDmChunk, smem_max / per_dm));
+  if (prm.dm_chunk < 1) return static_cast<int>(cudaErrorInvalidConfiguration);
+  const size_t smem = static_cast<size_t>(prm.dm_chunk) * per_dm;
   cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -145,7 +163,7 @@ int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64
   const int64_t tiles = (n_samp + kAdjTile - 1) / kAdjTile;
   const int64_t grid = tiles * n_cblk;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
-  adjoint_kernel<<<static_cast<unsigned>(grid), dim3(32, 8), smem,
+  adjoint_kernel<<<static_cast<unsigned>(grid), dim3(32, kAdjWarps), smem,
                    static_cast<cudaStream_t>(stream)>>>(prm, d_xbar);
   return static_cast<int>(cudaGetLastError());
 }

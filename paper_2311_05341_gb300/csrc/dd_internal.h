@@ -19,6 +19,9 @@ constexpr double kDispersionConstant = 4148.808;
 constexpr int kGenDmPerThread = 2;
 constexpr int kGenSampPerThread = 8;
 constexpr int kGenDmPerCta = 8 * kGenDmPerThread;
+
+// Adjoint blocking (adjoint.cu): channels per CTA.
+constexpr int kAdjChanBlock = 64;
 constexpr int kGenSampPerCta = 32 * kGenSampPerThread;
 
 struct RangePlan {

@@ -643,15 +643,16 @@ dd_status build_plan(dd_plan_s* p) {
     rp.gen_n_blocks = static_cast<int32_t>((rp.n_dm + kGenDmPerCta - 1) / kGenDmPerCta);
     rp.gen_span = block_span(rp, n_chan, kGenDmPerCta);
 
-    // Adjoint: channel blocks of 8 (one warp row each), span over the block for
-    // each DM: s(last channel) - s(first channel) with shifts non-decreasing
-    // towards lower frequency; take the true max/min to allow any order.
+    // Adjoint: channel blocks of kAdjChanBlock (one CTA each), span over the
+    // block for each DM: s(last channel) - s(first channel) with shifts
+    // non-decreasing towards lower frequency; take the true max/min to allow
+    // any order.
     int32_t aspan = 0;
     for (int64_t d = 0; d < rp.n_dm; ++d) {
       const int32_t* row = &rp.shifts[static_cast<size_t>(d) * n_chan];
-      for (int32_t c0 = 0; c0 < n_chan; c0 += 8) {
+      for (int32_t c0 = 0; c0 < n_chan; c0 += kAdjChanBlock) {
         int32_t lo = row[c0], hi = row[c0];
-        for (int32_t c = c0; c < std::min(c0 + 8, n_chan); ++c) {
+        for (int32_t c = c0; c < std::min(c0 + kAdjChanBlock, n_chan); ++c) {
           lo = std::min(lo, row[c]);
           hi = std::max(hi, row[c]);
         }
