@@ -90,7 +90,15 @@ typedef struct {
   int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane,
                                           DD_TILE_PATTERN or DD_TILE_MERGE
                                           (0: generic kernel) */
+  int32_t adjoint_kernel;             /* float32 plans: DD_ADJOINT_* dd_run_adjoint
+                                          uses (0 for other dtypes) */
 } dd_plan_info;
+
+/* Adjoint kernels (dd_plan_info.adjoint_kernel). */
+#define DD_ADJOINT_GATHER 1  /* staged cotangent windows, gathered per channel */
+#define DD_ADJOINT_PATTERN 2 /* the forward pattern tile on the cotangent rows with
+                                the transposed shift table (channels as trials,
+                                shifts s_max - s(c, d)), then expanded over bins */
 
 /* Forward kernels a range can run on (dd_plan_info.kernel). */
 #define DD_KERNEL_GENERIC 1 /* shared-memory staged, any dtype and bin */

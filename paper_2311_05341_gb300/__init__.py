@@ -127,6 +127,7 @@ class Plan:
             "max_delay_raw": inf.max_delay_raw, "workspace_bytes": inf.workspace_bytes,
             "kernel": [{1: "generic", 2: "tiled"}[inf.kernel[i]] for i in range(n)],
             "tile_dms": [inf.tile_dms[i] for i in range(n)],
+            "adjoint_kernel": {0: None, 1: "gather", 2: "pattern"}[inf.adjoint_kernel],
         }
 
     def shifts(self, r: int = 0) -> np.ndarray:

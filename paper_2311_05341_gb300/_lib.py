@@ -21,6 +21,7 @@ DD_MAX_RANGES = 16
 DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 DD_TILE_PATTERN = 0x104
 DD_TILE_MERGE = 0x105
+DD_ADJOINT_GATHER, DD_ADJOINT_PATTERN = 1, 2
 
 
 class DDError(RuntimeError):
@@ -48,7 +49,8 @@ class PlanInfo(ctypes.Structure):
                 ("out_elems", ctypes.c_int64), ("max_delay_raw", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_size_t),
                 ("kernel", ctypes.c_int32 * DD_MAX_RANGES),
-                ("tile_dms", ctypes.c_int32 * DD_MAX_RANGES)]
+                ("tile_dms", ctypes.c_int32 * DD_MAX_RANGES),
+                ("adjoint_kernel", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes) for every exported entry point.

@@ -126,11 +126,111 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams prm, float
   }
 }
 
+// xbar[c][t] = sum_r z_r[n_chan - 1 - c][floor(t / b_r)]: the per-range
+// adjoints computed by the forward pattern kernel (rows in reverse channel
+// order, one sample per decimated sample) expanded over their time bins.
+struct ExpandRange {
+  const float* z;  // [n_chan][u_len]
+  int64_t u_len;
+  int32_t bin;
+};
+struct ExpandParams {
+  ExpandRange r[DD_MAX_RANGES];
+  int32_t n_ranges;
+  int32_t n_chan;
+  int64_t n_samp;
+  int64_t stride;
+};
+
+__global__ void __launch_bounds__(256) adjoint_expand_kernel(const ExpandParams prm,
+                                                             float* __restrict__ xbar) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x;
+  const int32_t c = blockIdx.y;
+  if (t >= prm.n_samp) return;
+  float v = 0.f;
+  for (int32_t i = 0; i < prm.n_ranges; ++i) {
+    const ExpandRange& r = prm.r[i];
+    v += r.z[static_cast<int64_t>(prm.n_chan - 1 - c) * r.u_len + t / r.bin];
+  }
+  xbar[static_cast<int64_t>(c) * prm.stride + t] = v;
+}
+
+constexpr int kAdjNotServed = -1;
+
+// The adjoint through the forward pattern kernel (plan.cpp, build_adjoint_range):
+// per range, the cotangent rows padded with s_max zeros on both sides (stream-
+// ordered scratch), the forward transform of them with the transposed shift
+// table, then the expansion.  kAdjNotServed when some range has no such tile.
+int launch_adjoint_pattern(const dd_plan_s* p, const float* d_ybar, float* d_xbar,
+                           int64_t n_samp, int64_t stride, const int64_t* n_out,
+                           const int64_t* out_off, void* stream) {
+  const size_t n_r = p->ranges.size();
+  if (p->adj.size() != n_r || n_r == 0 || p->n_chan > 65535) return kAdjNotServed;
+  for (const RangePlan& ar : p->adj)
+    if (!ar.tile_ok) return kAdjNotServed;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Scratch: one padded input buffer (the largest range's) and every range's output.
+  int64_t u_len[DD_MAX_RANGES], pad_stride[DD_MAX_RANGES];
+  size_t in_floats = 0, out_floats = 0;
+  for (size_t i = 0; i < n_r; ++i) {
+    const RangePlan& rp = p->ranges[i];
+    u_len[i] = (n_samp - 1) / rp.r.bin + 1;
+    pad_stride[i] = (u_len[i] + rp.s_max + 3) / 4 * 4;  // 16-byte rows for the copies
+    in_floats = std::max(in_floats, static_cast<size_t>(rp.n_dm) * pad_stride[i]);
+    out_floats += static_cast<size_t>(p->n_chan) * ((u_len[i] + 3) / 4 * 4);
+  }
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, (in_floats + out_floats) * sizeof(float), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return kAdjNotServed;
+  }
+  float* x_pad = static_cast<float*>(scratch);
+  float* z = x_pad + in_floats;
+  ExpandParams ep{};
+  ep.n_ranges = static_cast<int32_t>(n_r);
+  ep.n_chan = p->n_chan;
+  ep.n_samp = n_samp;
+  ep.stride = stride;
+  const unsigned char* ws = static_cast<const unsigned char*>(p->d_ws);
+  int32_t* err = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) + tk::kStatusOffset);
+  int rc = 0;
+  for (size_t i = 0; i < n_r && rc == 0; ++i) {
+    const RangePlan& rp = p->ranges[i];
+    const RangePlan& ar = p->adj[i];
+    const int64_t pad = rp.s_max;
+    e = cudaMemsetAsync(x_pad, 0, static_cast<size_t>(rp.n_dm) * pad_stride[i] * sizeof(float), st);
+    if (e == cudaSuccess && n_out[i] > 0)
+      e = cudaMemcpy2DAsync(x_pad + pad, pad_stride[i] * sizeof(float), d_ybar + out_off[i],
+                            n_out[i] * sizeof(float), n_out[i] * sizeof(float),
+                            static_cast<size_t>(rp.n_dm), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      rc = static_cast<int>(e);
+      break;
+    }
+    const int64_t z_stride = (u_len[i] + 3) / 4 * 4;
+    rc = launch_forward_tiled_with_tables(p, ar, ws + ar.off_tile_recs, err, x_pad, pad_stride[i],
+                                          z_stride, z, 0, u_len[i], stream);
+    ep.r[i] = ExpandRange{z, z_stride, rp.r.bin};
+    z += static_cast<size_t>(p->n_chan) * z_stride;
+  }
+  if (rc == 0) {
+    const dim3 grid(static_cast<unsigned>((n_samp + 255) / 256), static_cast<unsigned>(p->n_chan));
+    adjoint_expand_kernel<<<grid, 256, 0, st>>>(ep, d_xbar);
+    rc = static_cast<int>(cudaGetLastError());
+  }
+  e = cudaFreeAsync(scratch, st);
+  if (rc == 0 && e != cudaSuccess) rc = static_cast<int>(e);
+  return rc;
+}
+
 }  // namespace
 
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
                    void* stream) {
+  const int fast = launch_adjoint_pattern(p, d_ybar, d_xbar, n_samp, stride, n_out, out_off, stream);
+  if (fast != kAdjNotServed) return fast;
   AdjParams prm{};
   prm.n_ranges = static_cast<int32_t>(p->ranges.size());
   prm.n_chan = p->n_chan;

@@ -65,6 +65,12 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
   }
   o->out_elems = off;
   o->workspace_bytes = p->ws_bytes;
+  o->adjoint_kernel = 0;
+  if (p->dtype == DD_F32) {
+    bool all = !p->adj.empty();
+    for (const auto& ar : p->adj) all = all && ar.tile_ok;
+    o->adjoint_kernel = all && p->n_chan <= 65535 ? DD_ADJOINT_PATTERN : DD_ADJOINT_GATHER;
+  }
   return DD_OK;
 }
 

@@ -52,6 +52,7 @@ struct RangePlan {
   size_t tile_chunk_off = 0;    // pair tiles: byte offset of the pair chunks in tile_recs
   int32_t tile_chunk_bytes = 0; // pair tiles: bytes per (DM block, stage) chunk
   int32_t tile_nv = 0;          // merged pattern tiles: window slots per round
+  int32_t tile_n_chan = 0;      // rows of the tables' input when not the plan's channels
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
@@ -74,6 +75,9 @@ struct dd_plan_s {
   void* d_ws = nullptr;                // bound device workspace (caller-owned)
   size_t ws_bytes = 0;
   void* host_pipe = nullptr;           // streams/events of dd_run_host (api.cu)
+  // Float32 plans: per range, its adjoint as a forward transform (plan.cpp,
+  // build_adjoint_range; tile_ok false where the pattern tile cannot serve it).
+  std::vector<dd::RangePlan> adj;
 };
 
 namespace dd {

@@ -308,7 +308,7 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   tk::TileParams prm{};
   prm.x = d_in;
   prm.stride = stride;
-  prm.n_chan = p->n_chan;
+  prm.n_chan = rp.tile_n_chan > 0 ? rp.tile_n_chan : p->n_chan;
   prm.recs = recs;
   if (rp.tile_pattern && rp.tile_chunk_bytes > 0) {  // pair tiles: base table, then chunks
     prm.bases = static_cast<const int32_t*>(recs);

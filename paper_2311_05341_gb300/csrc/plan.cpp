@@ -538,9 +538,43 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
     if (try_tile_shape(rp, n_chan, kind, *tk::shape_for(dr))) return;
 }
 
+// The adjoint of range rp (float32) as a forward transform: with P = s_max,
+// xbar_r[c][u] = sum_d ybar[d][u - s(c, d)] = sum_d Z[d][u + P - s(c, d)] for
+// the cotangent rows Z[d] padded with P zeros on both sides, so it is Eq. 3 on
+// "channels" d (the range's trial DMs) at "trial DMs" c' = n_chan - 1 - c
+// (the channels in reverse order) with shifts P - s(c, d) >= 0.  Those grow
+// with c' by the delay differences of adjacent channels (small and
+// non-negative for channels ordered from high to low frequency), which the
+// pattern tiles serve when each warp's increments are a or a + 1.
+void build_adjoint_range(const RangePlan& rp, int32_t n_chan, RangePlan* ar) {
+  *ar = RangePlan{};
+  ar->r = rp.r;
+  ar->r.bin = 1;  // the cotangent rows are already at the range's time resolution
+  ar->n_dm = n_chan;
+  ar->tile_n_chan = static_cast<int32_t>(rp.n_dm);
+  const int32_t pad = rp.s_max;
+  const int64_t n_dm = rp.n_dm;
+  ar->shifts.resize(static_cast<size_t>(n_chan) * n_dm);
+  int32_t smax = 0;
+  for (int32_t cp = 0; cp < n_chan; ++cp) {
+    const int32_t c = n_chan - 1 - cp;
+    for (int64_t d = 0; d < n_dm; ++d) {
+      const int32_t sh = pad - rp.shifts[static_cast<size_t>(d) * n_chan + c];
+      ar->shifts[static_cast<size_t>(cp) * n_dm + d] = sh;
+      smax = std::max(smax, sh);
+    }
+  }
+  ar->s_max = smax;
+  if (n_dm > (int64_t{1} << 20)) return;
+  for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
+    if (!tk::kPatShapes[i].merge &&
+        try_pattern_shape(*ar, static_cast<int32_t>(n_dm), tk::kF32, i))
+      return;
+}
+
 void layout_workspace(dd_plan_s* p) {
   size_t ws = tk::kStatusBytes;  // device status word(s) first
-  for (auto& rp : p->ranges) {
+  auto place = [&](RangePlan& rp) {
     ws = align_up(ws, 256);
     rp.off_shifts = ws;
     ws += rp.shifts.size() * sizeof(int32_t);
@@ -549,15 +583,19 @@ void layout_workspace(dd_plan_s* p) {
       rp.off_tile_recs = ws;
       ws += rp.tile_recs.size();
     }
-  }
+  };
+  for (auto& rp : p->ranges) place(rp);
+  for (auto& ar : p->adj) place(ar);
   p->ws_bytes = align_up(ws, 256);
   p->host_ws.assign(p->ws_bytes, 0);
-  for (const auto& rp : p->ranges) {
+  auto copy = [&](const RangePlan& rp) {
     std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
                 rp.shifts.size() * sizeof(int32_t));
     if (rp.tile_ok)
       std::memcpy(p->host_ws.data() + rp.off_tile_recs, rp.tile_recs.data(), rp.tile_recs.size());
-  }
+  };
+  for (const auto& rp : p->ranges) copy(rp);
+  for (const auto& ar : p->adj) copy(ar);
 }
 
 }  // namespace
@@ -662,6 +700,12 @@ dd_status build_plan(dd_plan_s* p) {
     rp.adj_span = aspan;
 
     choose_tile(rp, n_chan, p->dtype);
+  }
+  p->adj.clear();
+  if (p->dtype == DD_F32) {
+    p->adj.resize(p->ranges.size());
+    for (size_t i = 0; i < p->ranges.size(); ++i)
+      build_adjoint_range(p->ranges[i], n_chan, &p->adj[i]);
   }
   layout_workspace(p);
   return DD_OK;

@@ -1,4 +1,6 @@
-"""Parity of the CUDA adjoint (re-dispersion gather) with the oracle transpose.
+"""Parity of the CUDA adjoint (re-dispersion) with the oracle transpose, on
+both of its kernels (the gather, and the forward pattern tile on the
+cotangent rows with the transposed shift table).
 
 Checks: full-plane parity with the FP64 oracle adjoint on multi-range,
 binned plans; the dot-product test <A X, W> = <X, A^T W> and central finite
@@ -85,3 +87,46 @@ def test_adjoint_rejects_integer_plan():
     with pytest.raises(dd.DDError) as ei:
         plan.run_adjoint(torch.zeros(1024, device="cuda"), 512)
     assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adjoint_both_kernels_vs_oracle(seed):
+    """Plans with narrow channels (the pattern path: channels as trials with
+    the transposed shift table, expanded over bins) and with wide channels
+    (the gather path), ragged channel counts and several binned ranges."""
+    rng = np.random.default_rng(70 + seed)
+    narrow = seed % 2 == 0
+    if narrow:  # adjacent channels' delays differ by at most ~1 sample
+        n_chan = int(rng.choice([33, 96, 130, 257]))
+        freqs = channel_freqs(1500.0, 0.02 * n_chan, n_chan)
+        n_dm = int(rng.choice([7, 64, 65, 130]))
+    else:  # few wide channels, many DMs: several samples between neighbours
+        n_chan = int(rng.choice([9, 17, 33]))
+        freqs = channel_freqs(1500.0, 600.0, n_chan)
+        n_dm = int(rng.choice([130, 200]))
+    k_low = oracle.delay_coeff(freqs[-1], 1500.0) / 64e-6
+    step = float(rng.uniform(0.3, 1.5)) / k_low
+    ranges = [(0.0, n_dm * step, step, 1)]
+    if rng.integers(0, 2):
+        ranges.append((n_dm * step, 2 * n_dm * step, 2 * step, int(rng.choice([2, 3, 4]))))
+    s_max = max(oracle.extent(freqs, 1500.0, 64e-6, r, 10 ** 9)[0] * r[3] for r in ranges)
+    n_samp = int(s_max + rng.integers(1, 3000))
+    plan = dd.Plan(freqs, 1500.0, 64e-6, ranges, "f32")
+    info = plan.info(n_samp)
+    assert info["adjoint_kernel"] == ("pattern" if narrow else "gather")
+    ybar = rng.standard_normal(info["out_elems"]).astype(np.float32)
+    parts = [ybar[o:o + a * b].reshape(a, b).astype(np.float64)
+             for o, a, b in zip(info["out_offset"], info["n_dm"], info["n_out"])]
+    ref = oracle.adjoint(parts, n_chan, n_samp, freqs, 1500.0, 64e-6, ranges)
+    ref_abs = oracle.adjoint([np.abs(p) for p in parts], n_chan, n_samp, freqs, 1500.0, 64e-6,
+                             ranges)
+    got = plan.run_adjoint(torch.from_numpy(ybar).cuda(), n_samp).cpu().numpy()
+    err = np.abs(got.astype(np.float64) - ref)
+    assert np.all(err <= 1e-5 * ref_abs + 1e-30)
+    assert np.all(got[ref_abs == 0] == 0)
+
+
+def test_adjoint_kernel_of_diff_workload():
+    beam = workloads.diff_f32()
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, "f32", upload=False)
+    assert plan.info(beam.n_samp)["adjoint_kernel"] == "pattern"
