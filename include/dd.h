@@ -214,6 +214,11 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
  * [n_chan][xbar_row_stride] float32, fully overwritten for t < n_samp (samples
  * no output reads get 0).  This operation is this library's own (the paper has
  * no adjoint); it is the derivative of Eq. 3 with respect to X.
+ * Kernel (dd_plan_info.adjoint_kernel): DD_ADJOINT_PATTERN takes stream-ordered
+ * device scratch (cudaMallocAsync / cudaFreeAsync on `stream`) of
+ * max_r n_dm_r x (ceil(n_samp/b_r) + s_max_r) + sum_r n_chan x ceil(n_samp/b_r)
+ * floats (rows rounded to 4), released when the call's work completes; if that
+ * allocation fails the gather kernel runs instead (no scratch).
  * Errors: DD_ERR_UNSUPPORTED for integer plans, otherwise as dd_run.
  */
 dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
