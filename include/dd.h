@@ -214,15 +214,36 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
  * [n_chan][xbar_row_stride] float32, fully overwritten for t < n_samp (samples
  * no output reads get 0).  This operation is this library's own (the paper has
  * no adjoint); it is the derivative of Eq. 3 with respect to X.
- * Kernel (dd_plan_info.adjoint_kernel): DD_ADJOINT_PATTERN takes stream-ordered
- * device scratch (cudaMallocAsync / cudaFreeAsync on `stream`) of
- * max_r n_dm_r x (ceil(n_samp/b_r) + s_max_r) + sum_r n_chan x ceil(n_samp/b_r)
- * floats (rows rounded to 4), released when the call's work completes; if that
- * allocation fails the gather kernel runs instead (no scratch).
+ * This call runs the gather kernel (DD_ADJOINT_GATHER) and needs no scratch;
+ * dd_run_adjoint_scratch runs the faster pattern kernel where the plan has it.
  * Errors: DD_ERR_UNSUPPORTED for integer plans, otherwise as dd_run.
  */
 dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
                          int64_t xbar_row_stride, void* stream);
+
+/*
+ * Device scratch bytes dd_run_adjoint_scratch needs for n_samp raw samples:
+ * max_r n_dm_r x (ceil(n_samp/b_r) + s_max_r) + sum_r n_chan x ceil(n_samp/b_r)
+ * floats (rows rounded up to 4 floats); 0 when the plan's adjoint kernel
+ * (dd_plan_info.adjoint_kernel) is the gather.  Host only.
+ * Errors: DD_ERR_INVALID_ARG for null pointers, DD_ERR_UNSUPPORTED for integer
+ * plans, DD_ERR_SHAPE for n_samp <= 0.
+ */
+dd_status dd_adjoint_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* bytes);
+
+/*
+ * dd_run_adjoint with caller-owned device scratch (16-byte aligned; the
+ * library allocates no device memory): with at least
+ * dd_adjoint_scratch_bytes bytes and a plan whose adjoint_kernel is
+ * DD_ADJOINT_PATTERN it runs the forward pattern tile on the cotangent rows
+ * (padded into the scratch) with the transposed shift table, then expands
+ * the result over each range's time bin; otherwise the gather.  The scratch
+ * is in use until the call's work on `stream` completes.
+ * Errors: as dd_run_adjoint; DD_ERR_SHAPE for a misaligned scratch.
+ */
+dd_status dd_run_adjoint_scratch(dd_plan plan, const float* d_ybar, float* d_xbar,
+                                 int64_t n_samp, int64_t xbar_row_stride, void* d_scratch,
+                                 size_t scratch_bytes, void* stream);
 
 /*
  * Device status of a plan's earlier runs: synchronises `stream`, then returns

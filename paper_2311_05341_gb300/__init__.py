@@ -202,8 +202,18 @@ class Plan:
             stride = (n_samp + 3) // 4 * 4
             xbar = torch.empty((self.n_chan, stride), dtype=torch.float32,
                                device=ybar_flat.device)
-        check(self._lib.dd_run_adjoint(self._h, ybar_flat.data_ptr(), xbar.data_ptr(), int(n_samp),
-                                       xbar.stride(0), _stream_ptr(stream)))
+        need = ctypes.c_size_t(0)
+        check(self._lib.dd_adjoint_scratch_bytes(self._h, int(n_samp), ctypes.byref(need)))
+        scratch = (torch.empty(int(need.value), dtype=torch.uint8, device=ybar_flat.device)
+                   if need.value else None)
+        check(self._lib.dd_run_adjoint_scratch(
+            self._h, ybar_flat.data_ptr(), xbar.data_ptr(), int(n_samp), xbar.stride(0),
+            None if scratch is None else scratch.data_ptr(), int(need.value),
+            _stream_ptr(stream)))
+        if scratch is not None:
+            # The scratch stays in use until the call's work on the stream ends.
+            scratch.record_stream(torch.cuda.current_stream(ybar_flat.device)
+                                  if stream is None else stream)
         return xbar[:, :n_samp]
 
     def run_host_tmajor(self, h_in, h_out, d_tm_stage, d_cm_stage, d_out_stage,

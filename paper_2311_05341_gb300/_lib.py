@@ -66,6 +66,8 @@ SIGNATURES = {
     "dd_plan_set_tile": (ctypes.c_int, [_VP, _I32, _I32]),
     "dd_run": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP]),
+    "dd_run_adjoint_scratch": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP, _SZ, _VP]),
+    "dd_adjoint_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
     "dd_run_u8_noalloc": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),

@@ -157,36 +157,47 @@ __global__ void __launch_bounds__(256) adjoint_expand_kernel(const ExpandParams 
 
 constexpr int kAdjNotServed = -1;
 
-// The adjoint through the forward pattern kernel (plan.cpp, build_adjoint_range):
-// per range, the cotangent rows padded with s_max zeros on both sides (stream-
-// ordered scratch), the forward transform of them with the transposed shift
-// table, then the expansion.  kAdjNotServed when some range has no such tile.
-int launch_adjoint_pattern(const dd_plan_s* p, const float* d_ybar, float* d_xbar,
-                           int64_t n_samp, int64_t stride, const int64_t* n_out,
-                           const int64_t* out_off, void* stream) {
-  const size_t n_r = p->ranges.size();
-  if (p->adj.size() != n_r || n_r == 0 || p->n_chan > 65535) return kAdjNotServed;
-  for (const RangePlan& ar : p->adj)
-    if (!ar.tile_ok) return kAdjNotServed;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Scratch: one padded input buffer (the largest range's) and every range's output.
-  int64_t u_len[DD_MAX_RANGES], pad_stride[DD_MAX_RANGES];
+// Per-range sizes of the pattern adjoint: decimated samples per row u_len,
+// padded cotangent row stride (16-byte rows), result row stride.
+struct AdjSizes {
+  int64_t u_len[DD_MAX_RANGES], pad_stride[DD_MAX_RANGES], z_stride[DD_MAX_RANGES];
   size_t in_floats = 0, out_floats = 0;
+};
+
+// Sizes, or false when some range has no pattern tables.
+bool adjoint_sizes(const dd_plan_s* p, int64_t n_samp, AdjSizes* z) {
+  const size_t n_r = p->ranges.size();
+  if (p->adj.size() != n_r || n_r == 0 || p->n_chan > 65535 || n_samp <= 0) return false;
+  for (const RangePlan& ar : p->adj)
+    if (!ar.tile_ok) return false;
   for (size_t i = 0; i < n_r; ++i) {
     const RangePlan& rp = p->ranges[i];
-    u_len[i] = (n_samp - 1) / rp.r.bin + 1;
-    pad_stride[i] = (u_len[i] + rp.s_max + 3) / 4 * 4;  // 16-byte rows for the copies
-    in_floats = std::max(in_floats, static_cast<size_t>(rp.n_dm) * pad_stride[i]);
-    out_floats += static_cast<size_t>(p->n_chan) * ((u_len[i] + 3) / 4 * 4);
+    z->u_len[i] = (n_samp - 1) / rp.r.bin + 1;
+    z->pad_stride[i] = (z->u_len[i] + rp.s_max + 3) / 4 * 4;
+    z->z_stride[i] = (z->u_len[i] + 3) / 4 * 4;
+    z->in_floats = std::max(z->in_floats, static_cast<size_t>(rp.n_dm) * z->pad_stride[i]);
+    z->out_floats += static_cast<size_t>(p->n_chan) * z->z_stride[i];
   }
-  void* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(&scratch, (in_floats + out_floats) * sizeof(float), st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
+  return true;
+}
+
+// The adjoint through the forward pattern kernel (plan.cpp, build_adjoint_range):
+// per range, the cotangent rows padded with s_max zeros on both sides (in the
+// caller's scratch), the forward transform of them with the transposed shift
+// table, then the expansion.  kAdjNotServed when some range has no such tables
+// or the scratch is too small.
+int launch_adjoint_pattern(const dd_plan_s* p, const float* d_ybar, float* d_xbar,
+                           int64_t n_samp, int64_t stride, const int64_t* n_out,
+                           const int64_t* out_off, void* d_scratch, size_t scratch_bytes,
+                           void* stream) {
+  AdjSizes zs;
+  if (!d_scratch || !adjoint_sizes(p, n_samp, &zs) ||
+      scratch_bytes < (zs.in_floats + zs.out_floats) * sizeof(float))
     return kAdjNotServed;
-  }
-  float* x_pad = static_cast<float*>(scratch);
-  float* z = x_pad + in_floats;
+  const size_t n_r = p->ranges.size();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* x_pad = static_cast<float*>(d_scratch);
+  float* z = x_pad + zs.in_floats;
   ExpandParams ep{};
   ep.n_ranges = static_cast<int32_t>(n_r);
   ep.n_chan = p->n_chan;
@@ -194,42 +205,41 @@ int launch_adjoint_pattern(const dd_plan_s* p, const float* d_ybar, float* d_xba
   ep.stride = stride;
   const unsigned char* ws = static_cast<const unsigned char*>(p->d_ws);
   int32_t* err = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) + tk::kStatusOffset);
-  int rc = 0;
-  for (size_t i = 0; i < n_r && rc == 0; ++i) {
+  for (size_t i = 0; i < n_r; ++i) {
     const RangePlan& rp = p->ranges[i];
     const RangePlan& ar = p->adj[i];
     const int64_t pad = rp.s_max;
-    e = cudaMemsetAsync(x_pad, 0, static_cast<size_t>(rp.n_dm) * pad_stride[i] * sizeof(float), st);
+    cudaError_t e = cudaMemsetAsync(
+        x_pad, 0, static_cast<size_t>(rp.n_dm) * zs.pad_stride[i] * sizeof(float), st);
     if (e == cudaSuccess && n_out[i] > 0)
-      e = cudaMemcpy2DAsync(x_pad + pad, pad_stride[i] * sizeof(float), d_ybar + out_off[i],
+      e = cudaMemcpy2DAsync(x_pad + pad, zs.pad_stride[i] * sizeof(float), d_ybar + out_off[i],
                             n_out[i] * sizeof(float), n_out[i] * sizeof(float),
                             static_cast<size_t>(rp.n_dm), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) {
-      rc = static_cast<int>(e);
-      break;
-    }
-    const int64_t z_stride = (u_len[i] + 3) / 4 * 4;
-    rc = launch_forward_tiled_with_tables(p, ar, ws + ar.off_tile_recs, err, x_pad, pad_stride[i],
-                                          z_stride, z, 0, u_len[i], stream);
-    ep.r[i] = ExpandRange{z, z_stride, rp.r.bin};
-    z += static_cast<size_t>(p->n_chan) * z_stride;
+    if (e != cudaSuccess) return static_cast<int>(e);
+    const int rc = launch_forward_tiled_with_tables(p, ar, ws + ar.off_tile_recs, err, x_pad,
+                                                    zs.pad_stride[i], zs.z_stride[i], z, 0,
+                                                    zs.u_len[i], stream);
+    if (rc != 0) return rc;
+    ep.r[i] = ExpandRange{z, zs.z_stride[i], rp.r.bin};
+    z += static_cast<size_t>(p->n_chan) * zs.z_stride[i];
   }
-  if (rc == 0) {
-    const dim3 grid(static_cast<unsigned>((n_samp + 255) / 256), static_cast<unsigned>(p->n_chan));
-    adjoint_expand_kernel<<<grid, 256, 0, st>>>(ep, d_xbar);
-    rc = static_cast<int>(cudaGetLastError());
-  }
-  e = cudaFreeAsync(scratch, st);
-  if (rc == 0 && e != cudaSuccess) rc = static_cast<int>(e);
-  return rc;
+  const dim3 grid(static_cast<unsigned>((n_samp + 255) / 256), static_cast<unsigned>(p->n_chan));
+  adjoint_expand_kernel<<<grid, 256, 0, st>>>(ep, d_xbar);
+  return static_cast<int>(cudaGetLastError());
 }
 
 }  // namespace
 
+size_t adjoint_scratch_bytes(const dd_plan_s* p, int64_t n_samp) {
+  AdjSizes zs;
+  return adjoint_sizes(p, n_samp, &zs) ? (zs.in_floats + zs.out_floats) * sizeof(float) : 0;
+}
+
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
-                   void* stream) {
-  const int fast = launch_adjoint_pattern(p, d_ybar, d_xbar, n_samp, stride, n_out, out_off, stream);
+                   void* d_scratch, size_t scratch_bytes, void* stream) {
+  const int fast = launch_adjoint_pattern(p, d_ybar, d_xbar, n_samp, stride, n_out, out_off,
+                                          d_scratch, scratch_bytes, stream);
   if (fast != kAdjNotServed) return fast;
   AdjParams prm{};
   prm.n_ranges = static_cast<int32_t>(p->ranges.size());

@@ -330,15 +330,32 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
   return DD_OK;
 }
 
-dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
-                         int64_t xbar_row_stride, void* stream) {
+dd_status dd_run_adjoint_scratch(dd_plan plan, const float* d_ybar, float* d_xbar,
+                                 int64_t n_samp, int64_t xbar_row_stride, void* d_scratch,
+                                 size_t scratch_bytes, void* stream) {
   if (plan && plan->dtype != DD_F32) return fail(DD_ERR_UNSUPPORTED, "adjoint needs a float32 plan");
+  if (d_scratch && reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
+    return fail(DD_ERR_SHAPE, "adjoint scratch must be 16-byte aligned");
   dd_plan_info info;
   dd_status st = check_run(plan, d_ybar, xbar_row_stride, n_samp, d_xbar, &info);
   if (st != DD_OK) return st;
   int e = launch_adjoint(plan, d_ybar, d_xbar, n_samp, xbar_row_stride, info.n_out,
-                         info.out_offset, stream);
+                         info.out_offset, d_scratch, scratch_bytes, stream);
   if (e != 0) return cuda_fail(e, "dd_run_adjoint launch");
+  return DD_OK;
+}
+
+dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64_t n_samp,
+                         int64_t xbar_row_stride, void* stream) {
+  return dd_run_adjoint_scratch(plan, d_ybar, d_xbar, n_samp, xbar_row_stride, nullptr, 0,
+                                stream);
+}
+
+dd_status dd_adjoint_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* bytes) {
+  if (!plan || !bytes) return fail(DD_ERR_INVALID_ARG, "plan or bytes is NULL");
+  if (plan->dtype != DD_F32) return fail(DD_ERR_UNSUPPORTED, "adjoint needs a float32 plan");
+  if (n_samp <= 0) return fail(DD_ERR_SHAPE, "n_samp must be positive");
+  *bytes = adjoint_scratch_bytes(plan, n_samp);
   return DD_OK;
 }
 

@@ -121,9 +121,14 @@ int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* 
 int launch_transpose(int elem_bytes, const void* d_in, int64_t in_row_stride, int32_t n_chan,
                      void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
                      void* stream);
+// Adjoint (adjoint.cu): with d_scratch of at least adjoint_scratch_bytes()
+// bytes the pattern kernel runs where the plan has its tables, else the gather.
 int launch_adjoint(const dd_plan_s* p, const float* d_ybar, float* d_xbar, int64_t n_samp,
                    int64_t stride, const int64_t* n_out, const int64_t* out_off,
-                   void* stream);
+                   void* d_scratch, size_t scratch_bytes, void* stream);
+// Scratch bytes of the pattern adjoint for n_samp raw samples (0: the plan's
+// adjoint is the gather).
+size_t adjoint_scratch_bytes(const dd_plan_s* p, int64_t n_samp);
 
 tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,

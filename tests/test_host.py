@@ -14,7 +14,7 @@ import pytest
 
 import paper_2311_05341_gb300 as dd
 from paper_2311_05341_gb300 import _lib
-from synth import workloads
+from synth import channel_freqs, workloads
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -240,3 +240,34 @@ def test_u4_plan_selection_and_refusals():
     lib = _lib.load()
     st = lib.dd_transpose(_lib.DD_U4, 16, 32, 1, 16, 32, 0, 1, None)
     assert st == _lib.DD_ERR_UNSUPPORTED
+
+
+def test_adjoint_scratch_bytes():
+    """dd_adjoint_scratch_bytes: the pattern adjoint's scratch by its formula,
+    0 where the plan's adjoint is the gather, errors for bad arguments."""
+    import ctypes
+    lib = _lib.load()
+    freqs = channel_freqs(1500.0, 2.6, 130)
+    ranges = [(0.0, 25.6, 0.4, 1), (25.6, 51.2, 0.8, 2)]
+    plan = dd.Plan(freqs, 1500.0, 64e-6, ranges, "f32", upload=False)
+    n_samp = 6001
+    info = plan.info(n_samp)
+    assert info["adjoint_kernel"] == "pattern"
+    got = ctypes.c_size_t(0)
+    assert lib.dd_adjoint_scratch_bytes(plan.handle, n_samp, ctypes.byref(got)) == _lib.DD_OK
+    r4 = lambda n: (n + 3) // 4 * 4
+    u = [(n_samp - 1) // r[3] + 1 for r in ranges]
+    pad_in = max(nd * r4(uu + s) for nd, uu, s in zip(info["n_dm"], u, info["s_max"]))
+    want = 4 * (pad_in + sum(130 * r4(uu) for uu in u))
+    assert got.value == want
+    wide = dd.Plan(channel_freqs(1500.0, 600.0, 17), 1500.0, 64e-6, [(0.0, 80.0, 0.4, 1)], "f32",
+                   upload=False)
+    assert wide.info(n_samp)["adjoint_kernel"] == "gather"
+    assert lib.dd_adjoint_scratch_bytes(wide.handle, n_samp, ctypes.byref(got)) == _lib.DD_OK
+    assert got.value == 0
+    u8 = dd.Plan(freqs, 1500.0, 64e-6, ranges, "u8", upload=False)
+    assert u8.info(n_samp)["adjoint_kernel"] is None
+    assert lib.dd_adjoint_scratch_bytes(u8.handle, n_samp, ctypes.byref(got)) == \
+        _lib.DD_ERR_UNSUPPORTED
+    assert lib.dd_adjoint_scratch_bytes(plan.handle, 0, ctypes.byref(got)) == _lib.DD_ERR_SHAPE
+    assert lib.dd_adjoint_scratch_bytes(plan.handle, n_samp, None) == _lib.DD_ERR_INVALID_ARG
