@@ -348,8 +348,9 @@ def _adjoint_timing(args, plan, x, info, beam, stream):
         out[name] = {"ms": ms,
                      "dm_samples_per_s": sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
                      / (ms / 1e3)}
-    out["what"] = ("adjoint: dd_run_adjoint gather of a random cotangent; train_step: "
-                   "autograd forward + loss sum(Y W) + backward (forward, adjoint, elementwise)")
+    out["what"] = ("adjoint: Plan.run_adjoint of a random cotangent (dd_run_adjoint_scratch: "
+                   "kernel %s); train_step: autograd forward + loss sum(Y W) + backward "
+                   "(forward, adjoint, elementwise)" % info.get("adjoint_kernel"))
     return out
 
 
