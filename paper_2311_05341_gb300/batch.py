@@ -133,7 +133,9 @@ class BatchRunner:
     """Owns per-beam device buffers and runs all beams as one persistent launch."""
 
     def __init__(self, beams, device="cuda", autotune: bool = True, graph: bool = True,
-                 tuner: Autotuner | None = None):
+                 tuner: Autotuner | None = None, tiles=None):
+        """tiles: optional per beam, a list of per-range tiles (as Plan.set_tile
+        takes them) used instead of the autotuner or the first feasible tile."""
         torch = _torch()
         self.device = torch.device(device)
         self.beams = list(beams)
@@ -144,7 +146,11 @@ class BatchRunner:
             plan = Plan(b.freqs, b.f_ref, b.t_samp, b.ranges, b.dtype, device=self.device)
             x = input_buffer(b.dtype, plan.n_chan, b.n_samp, self.device)
             out = plan.empty_output(b.n_samp, self.device)
-            if self.tuner is not None:
+            if tiles is not None:
+                for r, t in enumerate(tiles[len(self.plans)]):
+                    plan.set_tile(r, t)
+                self.shapes.append(list(tiles[len(self.plans)]))
+            elif self.tuner is not None:
                 self.shapes.append(self.tuner.choose(plan, b.n_samp, x, out))
             else:
                 shp = []

@@ -136,3 +136,28 @@ def test_batch_with_4bit_beams():
         assert torch.equal(bo, o), f"beam {i} differs between batch and alone"
     for i, b in enumerate(runner.beams):
         _check_oracle(b, hosts[i], runner.planes(i))
+
+
+def test_batch_with_channel_class_tiles():
+    """uint8 beams on the pattern tile with channel classes (opt-in) in one
+    batch with a plain pattern beam: the merged persistent kernel equals the
+    per-beam launch and the oracle."""
+    beams = [ddb.BeamSpec(channel_freqs(1520.0, 6.0, 300), 1520.0, 64e-6,
+                          [(0.0, 25.6, 0.1, 1)], "u8", 9000),
+             ddb.BeamSpec(channel_freqs(1670.0, 10.0, 257), 1670.0, 64e-6,
+                          [(0.0, 12.8, 0.1, 1), (12.8, 25.6, 0.2, 1)], "u8", 7001),
+             ddb.BeamSpec(channel_freqs(1400.0, 300.0, 96), 1400.0, 64e-6,
+                          [(0.0, 6.4, 0.05, 1)], "u8", 6000)]
+    runner = ddb.BatchRunner(beams, autotune=False, graph=True,
+                             tiles=[["merge"], ["merge", "merge"], ["pattern"]])
+    hosts = _fill(runner, 950)
+    runner.run()
+    torch.cuda.synchronize()
+    runner.status()
+    batched = [o.clone() for o in runner.outputs]
+    runner.run_per_beam()
+    torch.cuda.synchronize()
+    for i, (bo, o) in enumerate(zip(batched, runner.outputs)):
+        assert torch.equal(bo, o), f"beam {i} differs between batch and alone"
+    for i, b in enumerate(runner.beams):
+        _check_oracle(b, hosts[i], runner.planes(i))
