@@ -168,7 +168,8 @@ constexpr PatShape kPatShapes[] = {
     {23, 16, 32, true, false, 3, false},  {23, 16, 12, true, false, 3, false},
     {23, 16, 6, true, false, 3, false},   {19, 16, 32, false, false, 1, false},
     {19, 16, 12, false, false, 1, false}, {19, 16, 6, false, false, 1, false},
-    {19, 16, 12, false, false, 3, false}, {19, 16, 6, false, false, 3, false}};
+    {19, 16, 32, false, false, 3, false}, {19, 16, 12, false, false, 3, false},
+    {19, 16, 6, false, false, 3, false}};
 constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
 constexpr bool pat_shapes_fit_records() {
   for (const PatShape& s : kPatShapes)
