@@ -18,6 +18,7 @@ end-to-end (host buffers through the C ABI) number.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -181,8 +182,22 @@ def run_ours(args):
                    device=f"cuda:{local}")
     if args.tile != "auto":
         for r in range(len(beam.ranges)):
-            plan.set_tile(r, args.tile if args.tile == "pattern" else int(args.tile))
+            plan.set_tile(r, args.tile if args.tile in ("pattern", "merge", "packed")
+                          else int(args.tile))
+    elif beam.dtype == "u8":
+        # The fastest uint8 path: the packed tile where it serves (it needs the
+        # caller scratch allocated below, so dd_plan_create does not pick it).
+        for r in range(len(beam.ranges)):
+            try:
+                plan.set_tile(r, "packed")
+            except dd.DDError:
+                pass
     info = plan.info(beam.n_samp)
+    # Caller-owned scratch of the packed tile (allocated once, like the output).
+    need = ctypes.c_size_t(0)
+    _lib.check(lib.dd_plan_input_scratch_bytes(plan.handle, beam.n_samp, ctypes.byref(need)))
+    scratch = (torch.empty(int(need.value), dtype=torch.uint8, device=f"cuda:{local}")
+               if need.value else None)
     tables = {}
 
     def shift_rows(r, d):
@@ -202,7 +217,8 @@ def run_ours(args):
     sp = stream.cuda_stream
 
     def step():
-        plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp)
+        plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp,
+                     scratch=scratch)
 
     for _ in range(args.warmup):
         step()
@@ -210,7 +226,9 @@ def run_ours(args):
 
     dm_samples = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
     chan_adds = dm_samples * beam.n_chan
-    launches_per_step = len(beam.ranges)
+    # One transform launch per range, plus the packing launch when a range is
+    # on the packed tile.
+    launches_per_step = len(beam.ranges) + (1 if scratch is not None else 0)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -289,7 +307,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": _describe(beam), "n_dm": info["n_dm_total"],
                    "n_out": info["n_out"],
-                   "tile": ["pattern" if t == _lib.DD_TILE_PATTERN else t
+                   "tile": [{_lib.DD_TILE_PATTERN: "pattern", _lib.DD_TILE_MERGE: "merge",
+                             _lib.DD_TILE_PACKED: "packed"}.get(t, t)
                             for t in info["tile_dms"]],
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
@@ -744,8 +763,9 @@ def main():
                     help="raw samples per channel instead of the workload's (smaller "
                          "cases for profiler captures)")
     ap.add_argument("--tile", default="auto",
-                    help="register tile of every range: auto, pattern or the offset tile's "
-                         "DMs per lane (8, 6, 4, 2, 1)")
+                    help="register tile of every range: auto (uint8: packed where it "
+                         "serves), pattern, merge, packed or the offset tile's DMs per lane "
+                         "(8, 6, 4, 2, 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -88,8 +88,8 @@ typedef struct {
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
   int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane,
-                                          DD_TILE_PATTERN or DD_TILE_MERGE
-                                          (0: generic kernel) */
+                                          DD_TILE_PATTERN, DD_TILE_MERGE or
+                                          DD_TILE_PACKED (0: generic kernel) */
   int32_t adjoint_kernel;             /* float32 plans: DD_ADJOINT_* dd_run_adjoint
                                           uses (0 for other dtypes) */
 } dd_plan_info;
@@ -117,6 +117,12 @@ typedef struct {
  * shifts.  Exact: the output is the same as channel by channel.  Only on
  * request (the automatic choice does not take it). */
 #define DD_TILE_MERGE 0x105
+/* The pattern tile on a packed copy of uint8 input (bin 1): word t of each
+ * channel holds samples t and t + 32 H in its 16-bit halves, so the staged
+ * words are the window words (no unpacking, one barrier per stage).  dd_run
+ * writes the copy into caller scratch first: such plans run through
+ * dd_run_scratch (dd_plan_input_scratch_bytes sizes it). */
+#define DD_TILE_PACKED 0x106
 
 /*
  * Build a plan on the host (no device work).  freqs_mhz[n_chan] are channel
@@ -167,7 +173,8 @@ dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_sa
 
 /*
  * Choose the tile of range `range`: `tile` is the offset tile's DM count per
- * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, DD_TILE_MERGE, or 0 = automatic.  Per-plan tile
+ * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, DD_TILE_MERGE, DD_TILE_PACKED, or
+ * 0 = automatic.  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
  * Rebuilds the plan's device tables, so it must be followed by
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
@@ -205,6 +212,27 @@ dd_status dd_plan_upload(dd_plan plan, void* d_workspace, size_t bytes, void* st
  */
 dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
                  void* d_out, void* stream);
+
+/*
+ * Device scratch bytes dd_run_scratch needs for n_samp raw samples: the packed
+ * copy of the input, n_chan x ceil4(n_samp) 32-bit words, when some range is
+ * on DD_TILE_PACKED; 0 otherwise.  Host only.
+ * Errors: DD_ERR_INVALID_ARG for null pointers, DD_ERR_SHAPE for n_samp <= 0.
+ */
+dd_status dd_plan_input_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* bytes);
+
+/*
+ * dd_run with caller-owned device scratch (16-byte aligned, at least
+ * dd_plan_input_scratch_bytes; the library allocates no device memory): ranges
+ * on DD_TILE_PACKED read the packed copy written there first (one pass over
+ * the input, on `stream`), the others read d_in.  The scratch is in use until
+ * the call's work on `stream` completes.  dd_run on a plan with a packed
+ * range returns DD_ERR_UNSUPPORTED.
+ * Errors: as dd_run; DD_ERR_BUDGET if the scratch is missing or too small,
+ * DD_ERR_SHAPE if it is misaligned.
+ */
+dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                         void* d_out, void* d_scratch, size_t scratch_bytes, void* stream);
 
 /*
  * Adjoint (transpose) of dd_run for float32 plans: re-dispersion
@@ -295,6 +323,20 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
  */
 dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
                       void* h_out, void* d_in_stage, void* d_out_stage, void* stream);
+
+/*
+ * dd_run_host with caller-owned device scratch for ranges on DD_TILE_PACKED
+ * (16-byte aligned, at least dd_plan_input_scratch_bytes): each segment's
+ * columns are packed on an internal stream once the samples 32 H further on
+ * have arrived, and those ranges take the outputs whose packed words are
+ * complete.  dd_run_host (and dd_run_host_tmajor) return DD_ERR_UNSUPPORTED
+ * for such plans.
+ * Errors: as dd_run_host; DD_ERR_BUDGET for missing or too little scratch,
+ * DD_ERR_SHAPE for a misaligned one.
+ */
+dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_stride,
+                              int64_t n_samp, void* h_out, void* d_in_stage, void* d_out_stage,
+                              void* d_scratch, size_t scratch_bytes, void* stream);
 
 /*
  * Forward transform of a uint8 plan without any caller-provided workspace, for

@@ -142,9 +142,12 @@ class Plan:
 
         tile: DMs per lane of the offset tile (8, 6, 4, 2, 1), "pattern"
         (DD_TILE_PATTERN), "merge" (DD_TILE_MERGE: the pattern tile with
-        channel classes), or 0 for the automatic choice.
+        channel classes), "packed" (DD_TILE_PACKED: the pattern tile on a
+        packed copy of uint8 input, made in scratch by run()), or 0 for the
+        automatic choice.
         """
-        code = {"pattern": _lib.DD_TILE_PATTERN, "merge": _lib.DD_TILE_MERGE}.get(tile, tile)
+        code = {"pattern": _lib.DD_TILE_PATTERN, "merge": _lib.DD_TILE_MERGE,
+                "packed": _lib.DD_TILE_PACKED}.get(tile, tile)
         code = int(code)
         check(self._lib.dd_plan_set_tile(self._h, int(r), code))
         if self.workspace is not None:
@@ -187,13 +190,32 @@ class Plan:
         n = x.shape[1] * per if n_samp is None else int(n_samp)
         if out is None:
             out = self.empty_output(n, x.device)
-        check(self._lib.dd_run(self._h, x.data_ptr(), x.stride(0) * per, n, out.data_ptr(),
-                               _stream_ptr(stream)))
+        scratch = self._input_scratch(n, x.device)
+        check(self._lib.dd_run_scratch(
+            self._h, x.data_ptr(), x.stride(0) * per, n, out.data_ptr(),
+            None if scratch is None else scratch.data_ptr(),
+            0 if scratch is None else scratch.numel(), _stream_ptr(stream)))
+        if scratch is not None and stream is not None:
+            scratch.record_stream(stream)
         return self.split(out, n)
 
-    def run_raw(self, x_ptr: int, stride: int, n_samp: int, out_ptr: int, stream_ptr: int):
-        """Forward transform on raw device pointers (no checks beyond the library's)."""
-        check(self._lib.dd_run(self._h, x_ptr, stride, n_samp, out_ptr, stream_ptr))
+    def _input_scratch(self, n_samp: int, device):
+        """Device scratch for ranges on the packed tile (None when there are
+        none), from torch's caching allocator for each run."""
+        import torch
+        need = ctypes.c_size_t(0)
+        check(self._lib.dd_plan_input_scratch_bytes(self._h, int(n_samp), ctypes.byref(need)))
+        if need.value == 0:
+            return None
+        return torch.empty(int(need.value), dtype=torch.uint8, device=device)
+
+    def run_raw(self, x_ptr: int, stride: int, n_samp: int, out_ptr: int, stream_ptr: int,
+                scratch=None):
+        """Forward transform on raw device pointers (no checks beyond the
+        library's); scratch: a device uint8 tensor for packed-tile ranges."""
+        check(self._lib.dd_run_scratch(self._h, x_ptr, stride, n_samp, out_ptr,
+                                       None if scratch is None else scratch.data_ptr(),
+                                       0 if scratch is None else scratch.numel(), stream_ptr))
 
     def run_adjoint(self, ybar_flat, n_samp: int, xbar=None, stream=None):
         """Adjoint of run() for f32 plans: flat cotangent -> [n_chan][n_samp] float32."""
@@ -232,9 +254,14 @@ class Plan:
         """Host-to-host forward through pinned host buffers and device staging."""
         per = _samples_per_elem(self.dtype)
         n = h_in.shape[1] * per if n_samp is None else int(n_samp)
-        check(self._lib.dd_run_host(self._h, h_in.data_ptr(), h_in.stride(0) * per, n,
-                                    h_out.data_ptr(), d_in_stage.data_ptr(),
-                                    d_out_stage.data_ptr(), _stream_ptr(stream)))
+        scratch = self._input_scratch(n, d_in_stage.device)
+        check(self._lib.dd_run_host_scratch(
+            self._h, h_in.data_ptr(), h_in.stride(0) * per, n, h_out.data_ptr(),
+            d_in_stage.data_ptr(), d_out_stage.data_ptr(),
+            None if scratch is None else scratch.data_ptr(),
+            0 if scratch is None else scratch.numel(), _stream_ptr(stream)))
+        if scratch is not None and stream is not None:
+            scratch.record_stream(stream)
 
     def _check_input(self, x):
         import torch

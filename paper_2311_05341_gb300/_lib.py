@@ -21,6 +21,7 @@ DD_MAX_RANGES = 16
 DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 DD_TILE_PATTERN = 0x104
 DD_TILE_MERGE = 0x105
+DD_TILE_PACKED = 0x106
 DD_ADJOINT_GATHER, DD_ADJOINT_PATTERN = 1, 2
 
 
@@ -66,6 +67,9 @@ SIGNATURES = {
     "dd_plan_set_tile": (ctypes.c_int, [_VP, _I32, _I32]),
     "dd_run": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
     "dd_run_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP]),
+    "dd_run_scratch": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _SZ, _VP]),
+    "dd_run_host_scratch": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "dd_plan_input_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
     "dd_run_adjoint_scratch": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP, _SZ, _VP]),
     "dd_adjoint_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),

@@ -56,8 +56,9 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
-    o->tile_dms[i] = !rp.tile_ok        ? 0
-                     : !rp.tile_pattern ? rp.tile_dr
+    o->tile_dms[i] = !rp.tile_ok                          ? 0
+                     : !rp.tile_pattern                   ? rp.tile_dr
+                     : rp.tile_kind == tk::kU8P            ? DD_TILE_PACKED
                      : tk::kPatShapes[rp.tile_shape].merge ? DD_TILE_MERGE
                                                            : DD_TILE_PATTERN;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
@@ -148,6 +149,17 @@ void free_host_pipe(dd_plan_s* p) {
 namespace {
 
 // Outputs [t_begin, t_end) of one range on its kernel.
+// Bytes of the packed uint8 copy (kU8P ranges read it), 0 without such a range.
+size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
+  for (const auto& rp : p->ranges)
+    if (rp.tile_ok && rp.tile_kind == tk::kU8P)
+      return static_cast<size_t>(p->n_chan) * static_cast<size_t>((n_samp + 3) / 4 * 4) * 4;
+  return 0;
+}
+
+// Ranges on DD_TILE_PACKED need the packed copy, which only dd_run_scratch makes.
+bool has_packed_range(const dd_plan_s* p) { return packed_input_bytes(p, 1) > 0; }
+
 int launch_range(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
                  int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
                  void* stream) {
@@ -274,9 +286,10 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
     return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
-  if (tile != 0 && tile != DD_TILE_PATTERN && tile != DD_TILE_MERGE && !tk::shape_for(tile))
+  if (tile != 0 && tile != DD_TILE_PATTERN && tile != DD_TILE_MERGE && tile != DD_TILE_PACKED &&
+      !tk::shape_for(tile))
     return fail(DD_ERR_INVALID_ARG,
-                "tile must be 0, 1, 2, 4, 6, 8, DD_TILE_PATTERN or DD_TILE_MERGE");
+                "tile must be 0, 1, 2, 4, 6, 8, DD_TILE_PATTERN, DD_TILE_MERGE or DD_TILE_PACKED");
   bool ok;
   try {
     ok = retile_range(plan, static_cast<size_t>(range), tile);
@@ -314,19 +327,56 @@ static dd_status check_run(dd_plan plan, const void* d_in, int64_t stride, int64
   return DD_OK;
 }
 
-dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
-                 void* d_out, void* stream) {
+dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                         void* d_out, void* d_scratch, size_t scratch_bytes, void* stream) {
   dd_plan_info info;
   dd_status st = check_run(plan, d_in, in_row_stride, n_samp, d_out, &info);
   if (st != DD_OK) return st;
+  const size_t need = packed_input_bytes(plan, n_samp);
+  if (need > 0) {
+    if (!d_scratch)
+      return fail(DD_ERR_UNSUPPORTED,
+                  "a range is on DD_TILE_PACKED: run it with dd_run_scratch and scratch of "
+                  "dd_plan_input_scratch_bytes");
+    if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
+    if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
+      return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
+  }
+  const int64_t packed_stride = (n_samp + 3) / 4 * 4;
+  int32_t packed_pair = 0;  // pair distance of the packed copy now in the scratch
   const size_t osz = 4;
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
     void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
     const RangePlan& rp = plan->ranges[i];
-    int e = launch_range(plan, rp, d_in, in_row_stride, n_samp, info.n_out[i], o, 0,
-                         info.n_out[i], stream);
+    const void* src = d_in;
+    int64_t stride = in_row_stride;
+    if (rp.tile_ok && rp.tile_kind == tk::kU8P) {
+      const int32_t pair = 32 * rp.tile_h;
+      if (pair != packed_pair) {
+        int e = launch_pack_pairs(d_in, in_row_stride, plan->n_chan, n_samp, d_scratch,
+                                  packed_stride, pair, 0, packed_stride, stream);
+        if (e != 0) return cuda_fail(e, "dd_run packing");
+        packed_pair = pair;
+      }
+      src = d_scratch;
+      stride = packed_stride;
+    }
+    int e = launch_range(plan, rp, src, stride, n_samp, info.n_out[i], o, 0, info.n_out[i],
+                         stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
+  return DD_OK;
+}
+
+dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                 void* d_out, void* stream) {
+  return dd_run_scratch(plan, d_in, in_row_stride, n_samp, d_out, nullptr, 0, stream);
+}
+
+dd_status dd_plan_input_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* bytes) {
+  if (!plan || !bytes) return fail(DD_ERR_INVALID_ARG, "plan or bytes is NULL");
+  if (n_samp <= 0) return fail(DD_ERR_SHAPE, "n_samp must be positive");
+  *bytes = packed_input_bytes(plan, n_samp);
   return DD_OK;
 }
 
@@ -379,11 +429,15 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream) {
 // The segmented host pipeline of dd_run_host (tm == nullptr: h_in is
 // channel-major with row stride cm_stride, copied straight into d_cm) and
 // dd_run_host_tmajor (h_in is time-major with row stride tm_stride, copied
-// into d_tm and transposed into d_cm on its own stream).
+// into d_tm and transposed into d_cm on its own stream).  With d_packed
+// (ranges on DD_TILE_PACKED, channel-major input only), the packed copy of
+// each segment's columns is made on that stream too, `pair` samples behind the
+// copied ones (a packed word needs samples t and t + pair), and those ranges'
+// kernels take only outputs whose words are packed.
 static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const void* h_in,
                                    int64_t tm_stride, void* d_tm, int64_t n_samp, void* h_out,
                                    void* d_cm, int64_t cm_stride, void* d_out_stage,
-                                   void* stream) {
+                                   void* d_packed, void* stream) {
   // The plan's copy streams and events are shared: calls from several host
   // threads enqueue one after the other (each wait captures its own record).
   static std::mutex host_mu;
@@ -406,6 +460,11 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
   const int64_t seg = (n_samp + kHostSegments - 1) / kHostSegments;
   const int64_t seg_len = (seg + 255) / 256 * 256;
+  const int64_t packed_stride = (n_samp + 3) / 4 * 4;
+  int32_t pair = 0;
+  for (const auto& rp : plan->ranges)
+    if (d_packed && rp.tile_ok && rp.tile_kind == tk::kU8P) pair = 32 * rp.tile_h;
+  int64_t packed_done = 0;
   int64_t raw_done = 0;
   int64_t done[DD_MAX_RANGES] = {};
   for (int k = 0; k < kHostSegments; ++k) {
@@ -442,6 +501,21 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
       e = cudaEventRecord(hp->tr[k], hp->s_tr);
       if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
       ready = hp->tr[k];
+    } else if (pair > 0) {  // packed copy of the columns whose pair partner is in
+      e = cudaStreamWaitEvent(hp->s_tr, hp->in[k], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      const int64_t packed_end =
+          last ? packed_stride : std::max(packed_done, (raw_end - pair) / 16 * 16);
+      if (packed_end > packed_done) {
+        const int le = launch_pack_pairs(dcm, row_bytes(plan->dtype, cm_stride), plan->n_chan,
+                                         n_samp, d_packed, packed_stride, pair, packed_done,
+                                         packed_end, hp->s_tr);
+        if (le != 0) return cuda_fail(le, "dd_run_host packing");
+      }
+      packed_done = packed_end;
+      e = cudaEventRecord(hp->tr[k], hp->s_tr);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      ready = hp->tr[k];
     }
     raw_done = std::max(raw_done, raw_end);
     e = cudaStreamWaitEvent(sc, ready, 0);
@@ -451,16 +525,20 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
     int64_t lim[DD_MAX_RANGES];
     for (size_t r = 0; r < plan->ranges.size(); ++r) {
       const RangePlan& rp = plan->ranges[r];
+      const bool from_packed = pair > 0 && rp.tile_ok && rp.tile_kind == tk::kU8P;
       const int64_t n_out = info.n_out[r];
       int64_t l = n_out;
       if (!last) {
+        // Samples usable so far; a packed word t holds samples t and t + pair.
+        const int64_t avail = from_packed ? packed_done + pair : raw_end;
         const int64_t ts = range_tile_samples(rp);
-        l = std::min<int64_t>(n_out, raw_end / rp.r.bin - rp.s_max);
+        l = std::min<int64_t>(n_out, avail / rp.r.bin - rp.s_max);
         l = l < 0 ? 0 : l / ts * ts;
       }
       lim[r] = l;
       if (l > done[r]) {
-        const int le = launch_range(plan, rp, dcm, cm_stride, n_samp, n_out,
+        const int le = launch_range(plan, rp, from_packed ? d_packed : dcm,
+                                    from_packed ? packed_stride : cm_stride, n_samp, n_out,
                                     dout + info.out_offset[r] * 4, done[r], l, sc);
         if (le != 0) return cuda_fail(le, "dd_run_host forward launch");
       }
@@ -488,14 +566,38 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   return DD_OK;
 }
 
-dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
-                      void* h_out, void* d_in_stage, void* d_out_stage, void* stream) {
+dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_stride,
+                              int64_t n_samp, void* h_out, void* d_in_stage, void* d_out_stage,
+                              void* d_scratch, size_t scratch_bytes, void* stream) {
   if (!h_in || !h_out) return fail(DD_ERR_INVALID_ARG, "h_in or h_out is NULL");
   dd_plan_info info;
   dd_status st = check_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, &info);
   if (st != DD_OK) return st;
+  const size_t need = packed_input_bytes(plan, n_samp);
+  if (need > 0) {
+    if (!d_scratch)
+      return fail(DD_ERR_UNSUPPORTED,
+                  "a range is on DD_TILE_PACKED: run it with dd_run_host_scratch and scratch of "
+                  "dd_plan_input_scratch_bytes");
+    if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
+    if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
+      return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
+    int32_t pair = 0;
+    for (const auto& rp : plan->ranges)
+      if (rp.tile_ok && rp.tile_kind == tk::kU8P) {
+        if (pair != 0 && pair != 32 * rp.tile_h)
+          return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
+        pair = 32 * rp.tile_h;
+      }
+  }
   return run_host_pipeline(plan, info, h_in, 0, nullptr, n_samp, h_out, d_in_stage,
-                           in_row_stride, d_out_stage, stream);
+                           in_row_stride, d_out_stage, need > 0 ? d_scratch : nullptr, stream);
+}
+
+dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
+                      void* h_out, void* d_in_stage, void* d_out_stage, void* stream) {
+  return dd_run_host_scratch(plan, h_in, in_row_stride, n_samp, h_out, d_in_stage, d_out_stage,
+                             nullptr, 0, stream);
 }
 
 static dd_status check_transpose(size_t esz, const void* d_in, int64_t in_row_stride,
@@ -535,6 +637,8 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
                              int64_t n_samp, void* h_out, void* d_tm_stage, void* d_cm_stage,
                              int64_t cm_row_stride, void* d_out_stage, void* stream) {
   if (!h_in || !h_out || !d_tm_stage) return fail(DD_ERR_INVALID_ARG, "NULL buffer");
+  if (plan && has_packed_range(plan))
+    return fail(DD_ERR_UNSUPPORTED, "the host pipeline does not take DD_TILE_PACKED ranges");
   if (plan && plan->dtype == DD_U4)
     return fail(DD_ERR_UNSUPPORTED, "time-major input takes uint8, uint16 or float32 samples");
   dd_plan_info info;
@@ -544,7 +648,7 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
                        d_cm_stage, cm_row_stride, 0, n_samp);
   if (st != DD_OK) return st;
   return run_host_pipeline(plan, info, h_in, in_row_stride, d_tm_stage, n_samp, h_out,
-                           d_cm_stage, cm_row_stride, d_out_stage, stream);
+                           d_cm_stage, cm_row_stride, d_out_stage, nullptr, stream);
 }
 
 }  // extern "C"

@@ -18,11 +18,15 @@ namespace tk {
 // Window-word kinds of the tiled kernels: uint8 at time bin 1 and 4-bit input
 // at any bin pack two (decimated) samples per 32-bit word (16-bit lanes);
 // uint8 at a larger bin (kU8W), uint16 and float32 keep one (decimated) sample
-// per word.  Values 1-3 equal dd_dtype.
-enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5 };
+// per word.  kU8P: uint8 at bin 1 read from a packed copy of the input whose
+// 32-bit word t already holds samples t and t + pair in its 16-bit halves (the
+// pattern tiles stage it as window words directly).  Values 1-3 equal dd_dtype.
+enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6 };
 
 // Window words pair samples u and u + pair in their 16-bit halves.
-DD_HOST_DEVICE constexpr bool packed_pairs(int kind) { return kind == kU8 || kind == kU4; }
+DD_HOST_DEVICE constexpr bool packed_pairs(int kind) {
+  return kind == kU8 || kind == kU4 || kind == kU8P;
+}
 
 constexpr int kH = 20;               // window words per lane per DM (the register tile width)
 constexpr int kMaxOff = 15;          // largest in-window DM offset (4-bit field)
@@ -44,7 +48,8 @@ DD_HOST_DEVICE constexpr int tile_samples(int kind) { return 32 * kH * samples_p
 DD_HOST_DEVICE constexpr int elem_bytes(int kind) {
   return (kind == kU8 || kind == kU8W || kind == kU4) ? 1 : (kind == kU16 ? 2 : 4);
 }
-// Raw samples per 16 bytes (4-bit samples: two per byte).
+// Raw samples per 16 bytes (4-bit samples: two per byte; kU8P: positions of
+// the packed copy, one 4-byte word each).
 DD_HOST_DEVICE constexpr int samples_per_16b(int kind) {
   return kind == kU4 ? 32 : 16 / elem_bytes(kind);
 }
@@ -61,14 +66,14 @@ DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) {
 inline bool bin_supported(int kind, int bin) {
   const int per = samples_per_16b(kind);
   return bin >= 1 && bin <= per && per % bin == 0 && (kind != kU8 || bin == 1) &&
-         (kind != kU4 || bin <= 16);
+         (kind != kU8P || bin == 1) && (kind != kU4 || bin <= 16);
 }
 // Channels between widenings of the accumulators: uint8 pairs in 16-bit lanes
 // hold 255 * 256 < 2^16, 4-bit pairs 15 * bin per channel; one-sample words
 // stay below 2^31 for floor((2^31 - 1) / (max sample * bin)) channels; float
 // never needs one.
 inline int flush_channels(int kind, int bin) {
-  if (kind == kU8) return 256;
+  if (kind == kU8 || kind == kU8P) return 256;
   if (kind == kU4) return 65535 / (15 * bin);
   if (kind == kF32) return 1 << 30;
   const double max_sample = (kind == kU8W ? 255.0 : 65535.0) * bin;
@@ -183,7 +188,7 @@ static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its
 // The shape serves a kind: pairs take integer window words, single channels
 // float; channel classes are built from uint8 samples at bin 1.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
-  return s.pairs == (kind != kF32) && (!s.merge || kind == kU8);
+  return s.pairs == (kind != kF32) && (!s.merge || kind == kU8) && (kind != kU8P || !s.dbuf);
 }
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
@@ -289,7 +294,10 @@ DD_HOST_DEVICE constexpr int32_t pat_raw_bytes(int kind, int bin, const PatShape
   return raw_bytes(kind, bin, lp, 32 * s.h) + (s.merge ? kMergeHalo : 0);
 }
 // nv: window slots of a merged tile (else the nc staged channels' windows).
+// kU8P stages window words directly: two staging buffers and no window buffer.
 inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp, int nv = 0) {
+  if (kind == kU8P)
+    return pat_raw_offset(s) + 2 * static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp);
   const int windows = s.merge ? nv : s.nc;
   return pat_raw_offset(s) + static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp) +
          (s.dbuf ? 2 : 1) * static_cast<size_t>(windows) * lp * 4;

@@ -1,0 +1,79 @@
+// pack.cu -- the packed copy of a uint8 filterbank read by the kU8P pattern
+// tiles: word t of channel c holds samples t and t + pair in its 16-bit halves,
+//   W[c][t] = X[c][t] | X[c][t + pair] << 16   (0 where an index reaches n_samp),
+// so the tiles stage window words without unpacking.  HBM-bound: reads the
+// input twice (the second read mostly from L2) and writes four bytes per sample.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+constexpr int kPackPerThread = 16;  // samples per thread: one 16-byte load per half
+
+__device__ __forceinline__ uint32_t sample_at(const uint8_t* row, int64_t t, int64_t n) {
+  return t < n ? row[t] : 0u;
+}
+
+__global__ void __launch_bounds__(256) pack_pairs_kernel(const uint8_t* __restrict__ in,
+                                                         int64_t in_stride, int64_t n_samp,
+                                                         uint32_t* __restrict__ out,
+                                                         int64_t out_stride, int32_t pair,
+                                                         int64_t chunks_per_row, int32_t n_chan,
+                                                         int64_t t_begin, int64_t t_end) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c = gid / chunks_per_row;
+  const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
+  if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
+  const uint8_t* row = in + c * in_stride;
+  uint32_t* dst = out + c * out_stride + t;
+  uint32_t w[kPackPerThread];
+  if (t + pair + kPackPerThread <= n_samp) {
+    // Both halves inside the row: two aligned 16-byte loads (t, pair and the
+    // row stride are multiples of 16).
+    const uint4 a = *reinterpret_cast<const uint4*>(row + t);
+    const uint4 b = *reinterpret_cast<const uint4*>(row + t + pair);
+    const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      w[4 * k + 0] = __byte_perm(av[k], bv[k], 0x4440) & 0x00ff00ffu;
+      w[4 * k + 1] = __byte_perm(av[k], bv[k], 0x4541) & 0x00ff00ffu;
+      w[4 * k + 2] = __byte_perm(av[k], bv[k], 0x4642) & 0x00ff00ffu;
+      w[4 * k + 3] = __byte_perm(av[k], bv[k], 0x4743) & 0x00ff00ffu;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPackPerThread; ++k)
+      w[k] = sample_at(row, t + k, n_samp) | sample_at(row, t + k + pair, n_samp) << 16;
+  }
+  // t_end is a multiple of 4 words; the range's last chunk may be partial.
+#pragma unroll
+  for (int k = 0; k < kPackPerThread; k += 4)
+    if (t + k < t_end)
+      *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
+}
+
+}  // namespace
+
+int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
+                      void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
+                      int64_t t_end, void* stream) {
+  if (n_chan <= 0 || n_samp <= 0 || t_end <= t_begin) return 0;
+  if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_stride < n_samp ||
+      t_begin % 16 != 0 || t_begin < 0 || t_end % 4 != 0 || t_end > out_stride)
+    return static_cast<int>(cudaErrorInvalidValue);
+  const int64_t chunks = (t_end - t_begin + kPackPerThread - 1) / kPackPerThread;
+  const int64_t threads = chunks * n_chan;
+  const int64_t blocks = (threads + 255) / 256;
+  if (blocks > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  pack_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const uint8_t*>(d_in), in_stride, n_samp, static_cast<uint32_t*>(d_out),
+      out_stride, pair, chunks, n_chan, t_begin, t_end);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace dd

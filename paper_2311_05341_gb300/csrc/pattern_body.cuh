@@ -130,10 +130,18 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 // only one per stage: it also certifies that every warp finished computing
 // stage st - 1, whose window and record buffers are the next ones reused.
 // Without DBUF a second barrier ends each stage.
+//
+// kU8P (packed input) stages window words directly: two staging buffers
+// (stage st in st % 2, each with its own mbarrier), the copies of stage st + 1
+// issued at the top of stage st (its buffer was last read in stage st - 1,
+// which ended with a barrier), no unpacking, and one barrier per stage (it
+// also carries the bounded-wait status).
 template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
+  constexpr bool kDirect = KIND == kU8P;
+  static_assert(!kDirect || !DBUF, "packed input stages its window words directly");
   constexpr int kPairW = 32 * H;
   constexpr int kRecBufs = 2;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -155,11 +163,12 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   const ChannelRecs<NC, PRec> cr{my_recs, reinterpret_cast<PRec*>(sm.recs), p.n_chan};
   auto issue = [&](int st, int32_t base) {
     unsigned char* dst = rec_buf(st % kRecBufs);
+    const int sbuf = kDirect ? (st & 1) : 0;
     if constexpr (PAIRS)
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, 0, t0, base, tid,
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, sbuf, t0, base, tid,
                             pair_chunk(p, blk, n_st, st), p.chunk_bytes, dst);
     else
-      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, 0, t0, base, tid, cr.src(st),
+      issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, sbuf, t0, base, tid, cr.src(st),
                             cr.bytes(st), dst);
   };
   if (tid <= NC) {
@@ -190,31 +199,40 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 
   for (int st = 0; st < n_st; ++st) {
     const int buf = st & 1;
-    const uint32_t parity = st & 1;  // the one stage barrier completes a phase per stage
+    // One stage barrier completes a phase per stage; with kDirect each of the
+    // two completes one every other stage.
+    const uint32_t parity = kDirect ? (st >> 1) & 1 : st & 1;
+    const uint32_t bar = sm.bar_base + (kDirect ? 8u * buf : 0u);
     const int nc = min(NC, p.n_chan - st * NC);
-    uint32_t* pwb = sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
+    uint32_t* pwb = kDirect ? reinterpret_cast<uint32_t*>(sm.raw + static_cast<size_t>(buf) * NC * p.lraw)
+                            : sm.pw + (DBUF ? static_cast<size_t>(buf) * NC * p.lp : 0);
     auto unpack = [&]() {  // raw bytes of stage st into window words
       // Warp w takes channels w, w + NW, ...; its lanes take consecutive units
       // (conflict-free 16-byte stores).
-      const uint8_t* rawb = sm.raw;
-      for (int ch = w; ch < nc; ch += NW) {
-        const uint8_t* raw_ch = rawb + static_cast<size_t>(ch) * p.lraw;
-        uint32_t* dst = pwb + static_cast<size_t>(ch) * p.lp;
-        for (int q = l; q < units; q += 32)
-          *reinterpret_cast<uint4*>(dst + 4 * q) = unpack_unit<KIND, kPairW>(raw_ch, q, p.bin);
+      if constexpr (!kDirect) {
+        const uint8_t* rawb = sm.raw;
+        for (int ch = w; ch < nc; ch += NW) {
+          const uint8_t* raw_ch = rawb + static_cast<size_t>(ch) * p.lraw;
+          uint32_t* dst = pwb + static_cast<size_t>(ch) * p.lp;
+          for (int q = l; q < units; q += 32)
+            *reinterpret_cast<uint4*>(dst + 4 * q) = unpack_unit<KIND, kPairW>(raw_ch, q, p.bin);
+        }
       }
     };
-    const bool ok = mbar_wait(sm.bar_base, parity);
-    if (ok) unpack();
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(p.err, kErrTimeout);
-        // Let the copies still in flight land before the CTA exits (bounded).
-        mbar_wait(sm.bar_base, parity);
+    if constexpr (kDirect) issue_next(st);
+    const bool ok = mbar_wait(bar, parity);
+    if constexpr (!kDirect) {
+      if (ok) unpack();
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(p.err, kErrTimeout);
+          // Let the copies still in flight land before the CTA exits (bounded).
+          mbar_wait(bar, parity);
+        }
+        return false;
       }
-      return false;
+      issue_next(st);
     }
-    issue_next(st);
 
     // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
     // PTX labels, appear once per instantiation.
@@ -263,7 +281,21 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     }
     since += nc;
     rb = rb + 1 == kRecBufs ? 0 : rb + 1;
-    if constexpr (!DBUF) __syncthreads();  // the window words are free
+    if constexpr (kDirect) {
+      // The window words are free; a wait that gave up (its stage was added
+      // from stale words, never stored) ends the unit once the copies in
+      // flight have landed (bounded).
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(p.err, kErrTimeout);
+          mbar_wait(bar, parity);
+          if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
+        }
+        return false;
+      }
+    } else if constexpr (!DBUF) {
+      __syncthreads();  // the window words are free
+    }
     if (since + NC > p.flush || st == n_st - 1) {
       // The transpose tiles reuse this stage's window buffer: wait until every
       // warp has finished reading it.

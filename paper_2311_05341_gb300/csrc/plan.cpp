@@ -415,7 +415,8 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
 
 // Try one tile shape for a range; on success fill the range's tile fields.
 bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh) {
-  if (kind == tk::kU4) return false;  // 4-bit input runs on the pattern tiles only
+  // 4-bit and packed uint8 input run on the pattern tiles only.
+  if (kind == tk::kU4 || kind == tk::kU8P) return false;
   const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
   const int32_t lp = tk::window_words(kind, rp.r.bin, span);
   if (tk::smem_bytes(kind, rp.r.bin, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
@@ -515,10 +516,12 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_recs.clear();
   const int kind = dtype == DD_U4                      ? tk::kU4
                    : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
+                   : (dtype == DD_U8 && rp.tile_request == DD_TILE_PACKED) ? tk::kU8P
                                                       : static_cast<int>(dtype);
+  if (rp.tile_request == DD_TILE_PACKED && kind != tk::kU8P) return;
   if (!tk::bin_supported(kind, rp.r.bin)) return;
   if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == DD_TILE_MERGE ||
-      rp.tile_request == 0) {
+      rp.tile_request == DD_TILE_PACKED || rp.tile_request == 0) {
     // Channel classes only on request: on GB300 the paper-scale plan ran
     // 237 ms with them against 196 ms without (the window building costs more
     // than the channel adds it saves).

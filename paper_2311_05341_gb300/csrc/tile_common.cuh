@@ -284,7 +284,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
 #pragma unroll
     for (int i = 0; i < DR; ++i) {
       const int d = blk * (DR * NW) + w * DR + i;
-      if constexpr (kPackedTile && KIND == kU8 && !ST::kPad) {
+      if constexpr (kPackedTile && (KIND == kU8 || KIND == kU8P) && !ST::kPad) {
         // uint8 pairs (widened every 256 channels), row 8-byte aligned:
         // packed words: the tile keeps each accumulator
         // word whole (position p and p + 32H in its halves) and lane l takes

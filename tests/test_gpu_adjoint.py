@@ -109,7 +109,7 @@ def test_adjoint_both_kernels_vs_oracle(seed):
     ranges = [(0.0, n_dm * step, step, 1)]
     if rng.integers(0, 2):
         ranges.append((n_dm * step, 2 * n_dm * step, 2 * step, int(rng.choice([2, 3, 4]))))
-    s_max = max(oracle.extent(freqs, 1500.0, 64e-6, r, 10 ** 9)[0] * r[3] for r in ranges)
+    s_max = max((oracle.extent(freqs, 1500.0, 64e-6, r, 10 ** 9)[0] + 1) * r[3] for r in ranges)
     n_samp = int(s_max + rng.integers(1, 3000))
     plan = dd.Plan(freqs, 1500.0, 64e-6, ranges, "f32")
     info = plan.info(n_samp)

@@ -12,6 +12,7 @@ import pytest
 import oracle
 import paper_2311_05341_gb300 as dd
 from paper_2311_05341_gb300._lib import DD_TILE_MERGE as TILE_MERGE
+from paper_2311_05341_gb300._lib import DD_TILE_PACKED as TILE_PACKED
 from paper_2311_05341_gb300._lib import DD_TILE_PATTERN as TILE_PATTERN
 from synth import workloads, channel_freqs, filterbank
 
@@ -136,12 +137,12 @@ def test_tiled_full_planes_every_shape(dtype, seed):
     # Steps of at most 1.7 samples keep every per-DM increment in {0, 1, 2}:
     # the pattern tile serves all these plans too (uint8: also with channel
     # classes).
-    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge",) if dtype == "u8" else ())
+    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge", "packed") if dtype == "u8" else ())
     for dms in tiles:
         plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
         info = plan.info(b.n_samp)
-        code = {"pattern": TILE_PATTERN, "merge": TILE_MERGE}.get(dms, dms)
+        code = {"pattern": TILE_PATTERN, "merge": TILE_MERGE, "packed": TILE_PACKED}.get(dms, dms)
         assert info["kernel"] == ["tiled"] and info["tile_dms"] == [code]
         got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
         if dtype == "f32":
@@ -171,7 +172,7 @@ def test_pattern_steep_plans(dtype, seed):
     ref = oracle.forward(x, freqs, f_high, 64e-6, [r])[0]
     ref_abs = oracle.forward(x, freqs, f_high, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
-    for tile in ("pattern", 1) + (("merge",) if dtype == "u8" else ()):
+    for tile in ("pattern", 1) + (("merge", "packed") if dtype == "u8" else ()):
         plan = dd.Plan(freqs, f_high, 64e-6, [r], dtype)
         plan.set_tile(0, tile)
         got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
@@ -285,8 +286,10 @@ def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
 
 
 @pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, "pattern"),
-                                       (workloads.paper_u8, 6), (workloads.paper_u16, 0)],
-                         ids=["paper_u8", "paper_u8_pattern", "paper_u8_offset6", "paper_u16"])
+                                       (workloads.paper_u8, "packed"), (workloads.paper_u8, 6),
+                                       (workloads.paper_u16, 0)],
+                         ids=["paper_u8", "paper_u8_pattern", "paper_u8_packed", "paper_u8_offset6",
+                              "paper_u16"])
 def test_paper_scale_sampled(make, tile):
     beam = make()
     x, tables, n_dm, n_out = oracle_input(beam)
