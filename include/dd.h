@@ -117,7 +117,7 @@ typedef struct {
  * shifts.  Exact: the output is the same as channel by channel.  Only on
  * request (the automatic choice does not take it). */
 #define DD_TILE_MERGE 0x105
-/* The pattern tile on a packed copy of uint8 input (bin 1): word t of each
+/* The pattern tile on a packed copy of uint8 or 4-bit input (bin 1): word t of each
  * channel holds samples t and t + 32 H in its 16-bit halves, so the staged
  * words are the window words (no unpacking, one barrier per stage).  dd_run
  * writes the copy into caller scratch first: such plans run through

@@ -353,8 +353,9 @@ dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, 
     if (rp.tile_ok && rp.tile_kind == tk::kU8P) {
       const int32_t pair = 32 * rp.tile_h;
       if (pair != packed_pair) {
-        int e = launch_pack_pairs(d_in, in_row_stride, plan->n_chan, n_samp, d_scratch,
-                                  packed_stride, pair, 0, packed_stride, stream);
+        int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan,
+                                  n_samp, d_scratch, packed_stride, pair, 0, packed_stride,
+                                  plan->dtype == DD_U4, stream);
         if (e != 0) return cuda_fail(e, "dd_run packing");
         packed_pair = pair;
       }
@@ -509,7 +510,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
       if (packed_end > packed_done) {
         const int le = launch_pack_pairs(dcm, row_bytes(plan->dtype, cm_stride), plan->n_chan,
                                          n_samp, d_packed, packed_stride, pair, packed_done,
-                                         packed_end, hp->s_tr);
+                                         packed_end, plan->dtype == DD_U4, hp->s_tr);
         if (le != 0) return cuda_fail(le, "dd_run_host packing");
       }
       packed_done = packed_end;

@@ -120,10 +120,11 @@ int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* 
 // Packed uint8 copy for the kU8P tiles (pack.cu): out[c][t] = in[c][t] |
 // in[c][t + pair] << 16 for t in [t_begin, t_end) (0 past n_samp); strides in
 // bytes (in) and 32-bit words (out, a multiple of 4 and >= n_samp); pair and
-// t_begin multiples of 16, t_end of 4 and <= out_stride.
+// t_begin multiples of 16, t_end of 4 and <= out_stride.  four_bit: 4-bit
+// input, two samples per byte (the earlier in the low nibble).
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, void* stream);
+                      int64_t t_end, bool four_bit, void* stream);
 // Time-major [t][c] to channel-major [c][t] for t in [t_begin, t_end) (transpose.cu).
 int launch_transpose(int elem_bytes, const void* d_in, int64_t in_row_stride, int32_t n_chan,
                      void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,

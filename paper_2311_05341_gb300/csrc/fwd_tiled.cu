@@ -330,6 +330,8 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.units_shift = rp.tile_units_shift;
   prm.bin = rp.r.bin;
   prm.flush = tk::flush_channels(rp.tile_kind, rp.r.bin);
+  // Packed 4-bit input: at most 15 per sample in the 16-bit lanes.
+  if (rp.tile_kind == tk::kU8P && p->dtype == DD_U4) prm.flush = tk::flush_channels(tk::kU4, 1);
   prm.out = d_out;
   prm.err = err;
   return prm;

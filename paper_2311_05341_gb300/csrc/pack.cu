@@ -1,5 +1,5 @@
-// pack.cu -- the packed copy of a uint8 filterbank read by the kU8P pattern
-// tiles: word t of channel c holds samples t and t + pair in its 16-bit halves,
+// pack.cu -- the packed copy of a uint8 (or 4-bit) filterbank read by the
+// kU8P pattern tiles: word t of channel c holds samples t and t + pair in its 16-bit halves,
 //   W[c][t] = X[c][t] | X[c][t + pair] << 16   (0 where an index reaches n_samp),
 // so the tiles stage window words without unpacking.  HBM-bound: reads the
 // input twice (the second read mostly from L2) and writes four bytes per sample.
@@ -57,11 +57,52 @@ __global__ void __launch_bounds__(256) pack_pairs_kernel(const uint8_t* __restri
       *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
 }
 
+// The same packed words from 4-bit input (two samples per byte, the earlier
+// in the low nibble; in_stride in bytes).
+__device__ __forceinline__ uint32_t nibble_at(const uint8_t* row, int64_t t, int64_t n) {
+  return t < n ? (row[t >> 1] >> (4 * (t & 1))) & 0xfu : 0u;
+}
+
+__global__ void __launch_bounds__(256) pack_pairs4_kernel(const uint8_t* __restrict__ in,
+                                                          int64_t in_stride, int64_t n_samp,
+                                                          uint32_t* __restrict__ out,
+                                                          int64_t out_stride, int32_t pair,
+                                                          int64_t chunks_per_row, int32_t n_chan,
+                                                          int64_t t_begin, int64_t t_end) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c = gid / chunks_per_row;
+  const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
+  if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
+  const uint8_t* row = in + c * in_stride;
+  uint32_t* dst = out + c * out_stride + t;
+  uint32_t w[kPackPerThread];
+  if (t + pair + kPackPerThread <= n_samp) {
+    // Both halves inside the row: two aligned 8-byte loads (t, pair and the
+    // row stride in samples are multiples of 16).
+    const uint2 a = *reinterpret_cast<const uint2*>(row + (t >> 1));
+    const uint2 b = *reinterpret_cast<const uint2*>(row + ((t + pair) >> 1));
+    const uint32_t av[2] = {a.x, a.y}, bv[2] = {b.x, b.y};
+#pragma unroll
+    for (int k = 0; k < kPackPerThread; ++k) {
+      const int sh = 4 * (k & 7);
+      w[k] = ((av[k >> 3] >> sh) & 0xfu) | ((bv[k >> 3] >> sh) & 0xfu) << 16;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPackPerThread; ++k)
+      w[k] = nibble_at(row, t + k, n_samp) | nibble_at(row, t + k + pair, n_samp) << 16;
+  }
+#pragma unroll
+  for (int k = 0; k < kPackPerThread; k += 4)
+    if (t + k < t_end)
+      *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
+}
+
 }  // namespace
 
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, void* stream) {
+                      int64_t t_end, bool four_bit, void* stream) {
   if (n_chan <= 0 || n_samp <= 0 || t_end <= t_begin) return 0;
   if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_stride < n_samp ||
       t_begin % 16 != 0 || t_begin < 0 || t_end % 4 != 0 || t_end > out_stride)
@@ -70,9 +111,15 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
   const int64_t threads = chunks * n_chan;
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
-  pack_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const uint8_t*>(d_in), in_stride, n_samp, static_cast<uint32_t*>(d_out),
-      out_stride, pair, chunks, n_chan, t_begin, t_end);
+  const auto* in = static_cast<const uint8_t*>(d_in);
+  auto* out = static_cast<uint32_t*>(d_out);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (four_bit)
+    pack_pairs4_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end);
+  else
+    pack_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end);
   return static_cast<int>(cudaGetLastError());
 }
 

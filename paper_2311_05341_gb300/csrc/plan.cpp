@@ -514,9 +514,12 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_chunk_bytes = 0;
   rp.tile_nv = 0;
   rp.tile_recs.clear();
-  const int kind = dtype == DD_U4                      ? tk::kU4
+  // Packed input (uint8 or 4-bit at bin 1): the same packed word format.
+  const bool packed = rp.tile_request == DD_TILE_PACKED && (dtype == DD_U8 || dtype == DD_U4) &&
+                      rp.r.bin == 1;
+  const int kind = packed                             ? tk::kU8P
+                   : dtype == DD_U4                   ? tk::kU4
                    : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
-                   : (dtype == DD_U8 && rp.tile_request == DD_TILE_PACKED) ? tk::kU8P
                                                       : static_cast<int>(dtype);
   if (rp.tile_request == DD_TILE_PACKED && kind != tk::kU8P) return;
   if (!tk::bin_supported(kind, rp.r.bin)) return;

@@ -125,3 +125,33 @@ def test_u4_paper_scale_sampled():
                                   t_lo, t_hi)
         got = plane[torch.tensor(rows, device="cuda"), t_lo:t_hi].cpu().numpy()
         np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_u4_packed_tile(seed):
+    """4-bit input through the packed tile (the same packed words, nibbles
+    zero-extended; widened every 65535 / 15 channels), alone and beside a
+    binned range, against the oracle; saturated samples (15) on 4500
+    channels cross a widening."""
+    from paper_2311_05341_gb300._lib import DD_TILE_PACKED
+    rng = np.random.default_rng(6300 + seed)
+    n_chan = int(rng.choice([1, 17, 96, 257, 4500 if seed == 5 else 300]))
+    f_high = float(rng.uniform(800, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / 64e-6
+    step = float(rng.uniform(0.3, 2.9)) / k_low
+    n_dm = int(rng.choice([3, 64, 65, 130]))
+    ranges = [(0.0, n_dm * step, step, 1)]
+    if seed % 2:
+        ranges.append((n_dm * step, 2 * n_dm * step, 2 * step, 4))
+    s_max = max((oracle.extent(freqs, f_high, 64e-6, r, 10 ** 9)[0] + 1) * r[3] for r in ranges)
+    n_samp = int(s_max + rng.choice([1, 735, 1472, 2945]))
+    data = _packed(n_chan, n_samp, 6400 + seed, mean=15.0 if seed == 5 else 8.0,
+                   sd=0.0 if seed == 5 else 4.0)
+    plan = dd.Plan(freqs, f_high, 64e-6, ranges, "u4")
+    plan.set_tile(0, "packed")
+    assert plan.info(n_samp)["tile_dms"][0] == DD_TILE_PACKED
+    planes = plan.run(torch.from_numpy(data).cuda(), n_samp=n_samp)
+    ref = oracle.forward(oracle.Packed4(data, n_samp), freqs, f_high, 64e-6, ranges)
+    for r, (g, o) in enumerate(zip(planes, ref)):
+        np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")
