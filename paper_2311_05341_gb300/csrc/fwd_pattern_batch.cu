@@ -107,6 +107,7 @@ int launch_pattern_batch(int kind, int shape, const tk::PatBatchArgs& args, int3
     case tk::kU16: return launch_kind<tk::kU16>(shape, args, grid, smem, st, kShapes);
     case tk::kU4: return launch_kind<tk::kU4>(shape, args, grid, smem, st, kShapes);
     case tk::kF32: return launch_kind<tk::kF32>(shape, args, grid, smem, st, kShapes);
+    case tk::kF32D: return launch_kind<tk::kF32D>(shape, args, grid, smem, st, kShapes);
   }
   return static_cast<int>(cudaErrorInvalidValue);
 }

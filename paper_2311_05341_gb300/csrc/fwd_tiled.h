@@ -20,8 +20,14 @@ namespace tk {
 // uint8 at a larger bin (kU8W), uint16 and float32 keep one (decimated) sample
 // per word.  kU8P: uint8 at bin 1 read from a packed copy of the input whose
 // 32-bit word t already holds samples t and t + pair in its 16-bit halves (the
-// pattern tiles stage it as window words directly).  Values 1-3 equal dd_dtype.
-enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6 };
+// pattern tiles stage it as window words directly).  kF32D: float32 at bin 1
+// staged as window words directly (the input words are the window words).
+// Values 1-3 equal dd_dtype.
+enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6, kF32D = 7 };
+
+// Float window words; kinds whose staged words are the window words.
+DD_HOST_DEVICE constexpr bool float_kind(int kind) { return kind == kF32 || kind == kF32D; }
+DD_HOST_DEVICE constexpr bool direct_kind(int kind) { return kind == kU8P || kind == kF32D; }
 
 // Window words pair samples u and u + pair in their 16-bit halves.
 DD_HOST_DEVICE constexpr bool packed_pairs(int kind) {
@@ -66,7 +72,7 @@ DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) {
 inline bool bin_supported(int kind, int bin) {
   const int per = samples_per_16b(kind);
   return bin >= 1 && bin <= per && per % bin == 0 && (kind != kU8 || bin == 1) &&
-         (kind != kU8P || bin == 1) && (kind != kU4 || bin <= 16);
+         (!direct_kind(kind) || bin == 1) && (kind != kU4 || bin <= 16);
 }
 // Channels between widenings of the accumulators: uint8 pairs in 16-bit lanes
 // hold 255 * 256 < 2^16, 4-bit pairs 15 * bin per channel; one-sample words
@@ -75,7 +81,7 @@ inline bool bin_supported(int kind, int bin) {
 inline int flush_channels(int kind, int bin) {
   if (kind == kU8 || kind == kU8P) return 256;
   if (kind == kU4) return 65535 / (15 * bin);
-  if (kind == kF32) return 1 << 30;
+  if (float_kind(kind)) return 1 << 30;
   const double max_sample = (kind == kU8W ? 255.0 : 65535.0) * bin;
   const double n = 2147483647.0 / max_sample;
   return n > (1 << 30) ? (1 << 30) : static_cast<int>(n);
@@ -188,7 +194,8 @@ static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its
 // The shape serves a kind: pairs take integer window words, single channels
 // float; channel classes are built from uint8 samples at bin 1.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
-  return s.pairs == (kind != kF32) && (!s.merge || kind == kU8) && (kind != kU8P || !s.dbuf);
+  return s.pairs == !float_kind(kind) && (!s.merge || kind == kU8) &&
+         (!direct_kind(kind) || !s.dbuf);
 }
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
@@ -294,9 +301,9 @@ DD_HOST_DEVICE constexpr int32_t pat_raw_bytes(int kind, int bin, const PatShape
   return raw_bytes(kind, bin, lp, 32 * s.h) + (s.merge ? kMergeHalo : 0);
 }
 // nv: window slots of a merged tile (else the nc staged channels' windows).
-// kU8P stages window words directly: two staging buffers and no window buffer.
+// Direct kinds stage window words: two staging buffers and no window buffer.
 inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp, int nv = 0) {
-  if (kind == kU8P)
+  if (direct_kind(kind))
     return pat_raw_offset(s) + 2 * static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp);
   const int windows = s.merge ? nv : s.nc;
   return pat_raw_offset(s) + static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp) +

@@ -67,7 +67,7 @@ __device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32
                 "no generated pattern blocks for H");
 #define DD_PAT_CASE(HH)                                                  \
   if constexpr (H == HH) {                                               \
-    if constexpr (KIND == kF32) DD_PATL_CHANNEL_F32_##HH(acc, win, ix);  \
+    if constexpr (float_kind(KIND)) DD_PATL_CHANNEL_F32_##HH(acc, win, ix);  \
     else DD_PATL_CHANNEL_U32_##HH(acc, win, ix);                         \
   }
   DD_PAT_CASE(15)
@@ -87,7 +87,7 @@ __device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
                                                  uint32_t ix) {
 #define DD_PAT_CASE(HH)                                           \
   if constexpr (H == HH) {                                        \
-    if constexpr (KIND == kF32) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
+    if constexpr (float_kind(KIND)) DD_PAT_CHANNEL_F32_##HH(acc, R, ix); \
     else DD_PAT_CHANNEL_U32_##HH(acc, R, ix);                     \
   }
   DD_PAT_CASE(15)
@@ -131,7 +131,7 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 // stage st - 1, whose window and record buffers are the next ones reused.
 // Without DBUF a second barrier ends each stage.
 //
-// kU8P (packed input) stages window words directly: two staging buffers
+// Direct kinds (packed uint8 input, float32 at bin 1) stage window words: two staging buffers
 // (stage st in st % 2, each with its own mbarrier), the copies of stage st + 1
 // issued at the top of stage st (its buffer was last read in stage st - 1,
 // which ended with a barrier), no unpacking, and one barrier per stage (it
@@ -139,8 +139,8 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
-  static_assert(!PAIRS || KIND != kF32, "channel pairs need integer window words");
-  constexpr bool kDirect = KIND == kU8P;
+  static_assert(!PAIRS || !float_kind(KIND), "channel pairs need integer window words");
+  constexpr bool kDirect = direct_kind(KIND);
   static_assert(!kDirect || !DBUF, "packed input stages its window words directly");
   constexpr int kPairW = 32 * H;
   constexpr int kRecBufs = 2;
@@ -264,7 +264,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
         AccT<KIND> R[kR];
 #pragma unroll
         for (int k = 0; k < kR; ++k) {
-          if constexpr (KIND == kF32) R[k] = __uint_as_float(src[k]);
+          if constexpr (float_kind(KIND)) R[k] = __uint_as_float(src[k]);
           else R[k] = src[k];
         }
         pat_channel_regs<KIND, H>(acc, R, e >> kPatOffBits);

@@ -415,8 +415,8 @@ bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift)
 
 // Try one tile shape for a range; on success fill the range's tile fields.
 bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh) {
-  // 4-bit and packed uint8 input run on the pattern tiles only.
-  if (kind == tk::kU4 || kind == tk::kU8P) return false;
+  // 4-bit input and the direct kinds run on the pattern tiles only.
+  if (kind == tk::kU4 || tk::direct_kind(kind)) return false;
   const int32_t span = block_span(rp, n_chan, sh.dr * sh.warps);
   const int32_t lp = tk::window_words(kind, rp.r.bin, span);
   if (tk::smem_bytes(kind, rp.r.bin, sh, lp) > 227 * 1024) return false;  // one CTA per SM at worst
@@ -528,6 +528,11 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
     // Channel classes only on request: on GB300 the paper-scale plan ran
     // 237 ms with them against 196 ms without (the window building costs more
     // than the channel adds it saves).
+    // Float32 at bin 1 first tries the direct kind (the input words are the
+    // window words: no unpacking, two staging buffers).
+    if (kind == tk::kF32 && rp.r.bin == 1 && rp.tile_request != DD_TILE_MERGE)
+      for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
+        if (!tk::kPatShapes[i].merge && try_pattern_shape(rp, n_chan, tk::kF32D, i)) return;
     for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i) {
       const bool merge = tk::kPatShapes[i].merge;
       if (merge != (rp.tile_request == DD_TILE_MERGE)) continue;
@@ -572,10 +577,11 @@ void build_adjoint_range(const RangePlan& rp, int32_t n_chan, RangePlan* ar) {
   }
   ar->s_max = smax;
   if (n_dm > (int64_t{1} << 20)) return;
-  for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
-    if (!tk::kPatShapes[i].merge &&
-        try_pattern_shape(*ar, static_cast<int32_t>(n_dm), tk::kF32, i))
-      return;
+  for (int kind : {static_cast<int>(tk::kF32D), static_cast<int>(tk::kF32)})
+    for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
+      if (!tk::kPatShapes[i].merge &&
+          try_pattern_shape(*ar, static_cast<int32_t>(n_dm), kind, i))
+        return;
 }
 
 void layout_workspace(dd_plan_s* p) {

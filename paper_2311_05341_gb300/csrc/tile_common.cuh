@@ -53,9 +53,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Accumulator (window word) and output element of a kind.
 template <int KIND>
-using AccT = std::conditional_t<KIND == kF32, float, uint32_t>;
+using AccT = std::conditional_t<float_kind(KIND), float, uint32_t>;
 template <int KIND>
-using OutT = std::conditional_t<KIND == kF32, float, int32_t>;
+using OutT = std::conditional_t<float_kind(KIND), float, int32_t>;
 
 __device__ __forceinline__ uint32_t byte_sum4(uint32_t w) { return __dp4a(w, 0x01010101u, 0u); }
 __device__ __forceinline__ uint32_t half_sum2(uint32_t w) { return (w & 0xffffu) + (w >> 16); }
@@ -338,7 +338,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
       }
       __syncwarp();
       bool paired = false;
-      if constexpr (!ST::kPad && KIND != kF32) {
+      if constexpr (!ST::kPad && !float_kind(KIND)) {
         // Later widenings of integer sums (non-negative) with the row 8-byte
         // aligned: lane l adds positions 64 m + 2 l and + 1 in one 64-bit
         // reduction (the tile holds position p at index p).
@@ -367,13 +367,13 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
             const int kk = h * kCh + k;
             if (kk < ST::kRows) {
               const uint32_t bits = tr[ST::row(kk) + l];
-              if constexpr (KIND == kF32) v[k] = __uint_as_float(bits);
+              if constexpr (float_kind(KIND)) v[k] = __uint_as_float(bits);
               else v[k] = static_cast<int32_t>(bits);
             } else {
               v[k] = OutT<KIND>(0);
             }
           }
-          if (!first && KIND != kF32) {
+          if (!first && !float_kind(KIND)) {
             // Later widenings of integer sums: reductions at L2 (exact, any
             // order), so the warp does not wait for the row to come back.
 #pragma unroll
