@@ -185,10 +185,10 @@ def run_ours(args):
         for r in range(len(beam.ranges)):
             plan.set_tile(r, args.tile if args.tile in ("pattern", "merge", "packed")
                           else int(args.tile))
-    elif beam.dtype in ("u8", "u4"):
-        # The fastest 8- and 4-bit path: the packed tile where it serves (it
-        # needs the caller scratch allocated below, so dd_plan_create does not
-        # pick it).
+    elif beam.dtype in ("u8", "u4", "u16"):
+        # The fastest integer path: the packed tile where it serves (it needs
+        # the caller scratch allocated below, so dd_plan_create does not pick
+        # it).
         for r in range(len(beam.ranges)):
             try:
                 plan.set_tile(r, "packed")

@@ -117,9 +117,10 @@ typedef struct {
  * shifts.  Exact: the output is the same as channel by channel.  Only on
  * request (the automatic choice does not take it). */
 #define DD_TILE_MERGE 0x105
-/* The pattern tile on a packed copy of uint8 or 4-bit input (bin 1): word t of each
- * channel holds samples t and t + 32 H in its 16-bit halves, so the staged
- * words are the window words (no unpacking, one barrier per stage).  dd_run
+/* The pattern tile on a packed copy of uint8, 4-bit or uint16 input (bin 1):
+ * word t of each channel holds samples t and t + 32 H in its 16-bit halves
+ * (uint16: sample t widened to 32 bits), so the staged words are the window
+ * words (no unpacking, one barrier per stage).  dd_run
  * writes the copy into caller scratch first: such plans run through
  * dd_run_scratch (dd_plan_input_scratch_bytes sizes it). */
 #define DD_TILE_PACKED 0x106

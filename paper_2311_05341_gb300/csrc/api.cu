@@ -58,7 +58,7 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
     o->tile_dms[i] = !rp.tile_ok                          ? 0
                      : !rp.tile_pattern                   ? rp.tile_dr
-                     : rp.tile_kind == tk::kU8P            ? DD_TILE_PACKED
+                     : tk::packed_copy_kind(rp.tile_kind)  ? DD_TILE_PACKED
                      : tk::kPatShapes[rp.tile_shape].merge ? DD_TILE_MERGE
                                                            : DD_TILE_PATTERN;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
@@ -149,10 +149,10 @@ void free_host_pipe(dd_plan_s* p) {
 namespace {
 
 // Outputs [t_begin, t_end) of one range on its kernel.
-// Bytes of the packed uint8 copy (kU8P ranges read it), 0 without such a range.
+// Bytes of the packed copy (packed-copy kinds read it), 0 without such a range.
 size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
   for (const auto& rp : p->ranges)
-    if (rp.tile_ok && rp.tile_kind == tk::kU8P)
+    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))
       return static_cast<size_t>(p->n_chan) * static_cast<size_t>((n_samp + 3) / 4 * 4) * 4;
   return 0;
 }
@@ -343,19 +343,19 @@ dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, 
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
   }
   const int64_t packed_stride = (n_samp + 3) / 4 * 4;
-  int32_t packed_pair = 0;  // pair distance of the packed copy now in the scratch
+  int32_t packed_pair = -1;  // pair distance of the packed copy now in the scratch
   const size_t osz = 4;
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
     void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
     const RangePlan& rp = plan->ranges[i];
     const void* src = d_in;
     int64_t stride = in_row_stride;
-    if (rp.tile_ok && rp.tile_kind == tk::kU8P) {
-      const int32_t pair = 32 * rp.tile_h;
+    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {
+      const int32_t pair = pack_pair(rp);
       if (pair != packed_pair) {
         int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan,
                                   n_samp, d_scratch, packed_stride, pair, 0, packed_stride,
-                                  plan->dtype == DD_U4, stream);
+                                  pack_source(plan->dtype), stream);
         if (e != 0) return cuda_fail(e, "dd_run packing");
         packed_pair = pair;
       }
@@ -462,9 +462,9 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   const int64_t seg = (n_samp + kHostSegments - 1) / kHostSegments;
   const int64_t seg_len = (seg + 255) / 256 * 256;
   const int64_t packed_stride = (n_samp + 3) / 4 * 4;
-  int32_t pair = 0;
+  int32_t pair = -1;  // lag of the packed copy behind the copied samples (-1: none)
   for (const auto& rp : plan->ranges)
-    if (d_packed && rp.tile_ok && rp.tile_kind == tk::kU8P) pair = 32 * rp.tile_h;
+    if (d_packed && rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) pair = pack_pair(rp);
   int64_t packed_done = 0;
   int64_t raw_done = 0;
   int64_t done[DD_MAX_RANGES] = {};
@@ -502,7 +502,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
       e = cudaEventRecord(hp->tr[k], hp->s_tr);
       if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
       ready = hp->tr[k];
-    } else if (pair > 0) {  // packed copy of the columns whose pair partner is in
+    } else if (pair >= 0) {  // packed copy of the columns whose pair partner is in
       e = cudaStreamWaitEvent(hp->s_tr, hp->in[k], 0);
       if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
       const int64_t packed_end =
@@ -510,7 +510,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
       if (packed_end > packed_done) {
         const int le = launch_pack_pairs(dcm, row_bytes(plan->dtype, cm_stride), plan->n_chan,
                                          n_samp, d_packed, packed_stride, pair, packed_done,
-                                         packed_end, plan->dtype == DD_U4, hp->s_tr);
+                                         packed_end, pack_source(plan->dtype), hp->s_tr);
         if (le != 0) return cuda_fail(le, "dd_run_host packing");
       }
       packed_done = packed_end;
@@ -526,7 +526,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
     int64_t lim[DD_MAX_RANGES];
     for (size_t r = 0; r < plan->ranges.size(); ++r) {
       const RangePlan& rp = plan->ranges[r];
-      const bool from_packed = pair > 0 && rp.tile_ok && rp.tile_kind == tk::kU8P;
+      const bool from_packed = pair >= 0 && rp.tile_ok && tk::packed_copy_kind(rp.tile_kind);
       const int64_t n_out = info.n_out[r];
       int64_t l = n_out;
       if (!last) {
@@ -583,12 +583,12 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
     if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
     if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
-    int32_t pair = 0;
+    int32_t pair = -1;
     for (const auto& rp : plan->ranges)
-      if (rp.tile_ok && rp.tile_kind == tk::kU8P) {
-        if (pair != 0 && pair != 32 * rp.tile_h)
+      if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {
+        if (pair >= 0 && pair != pack_pair(rp))
           return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
-        pair = 32 * rp.tile_h;
+        pair = pack_pair(rp);
       }
   }
   return run_host_pipeline(plan, info, h_in, 0, nullptr, n_samp, h_out, d_in_stage,

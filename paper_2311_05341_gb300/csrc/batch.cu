@@ -95,7 +95,7 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       int64_t out_off = 0;
       for (size_t r = 0; r < p->ranges.size(); ++r) {
         const RangePlan& rp = p->ranges[r];
-        const bool pat = rp.tile_ok && rp.tile_pattern && rp.tile_kind != tk::kU8P;
+        const bool pat = rp.tile_ok && rp.tile_pattern && !tk::packed_copy_kind(rp.tile_kind);
         if (!rp.tile_ok || (rp.tile_pattern && !pat) ||
             (!pat && (rp.tile_pattern || !batch_shape(rp.tile_dr)))) {
           delete b;

@@ -120,11 +120,20 @@ int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* 
 // Packed uint8 copy for the kU8P tiles (pack.cu): out[c][t] = in[c][t] |
 // in[c][t + pair] << 16 for t in [t_begin, t_end) (0 past n_samp); strides in
 // bytes (in) and 32-bit words (out, a multiple of 4 and >= n_samp); pair and
-// t_begin multiples of 16, t_end of 4 and <= out_stride.  four_bit: 4-bit
-// input, two samples per byte (the earlier in the low nibble).
+// t_begin multiples of 16, t_end of 4 and <= out_stride.  Source kU4: 4-bit
+// input, two samples per byte (the earlier in the low nibble); kU16: uint16
+// input widened, out[c][t] = in[c][t] (pair unused).
+enum class PackSource { kU8, kU4, kU16 };
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, bool four_bit, void* stream);
+                      int64_t t_end, PackSource src, void* stream);
+// Pair distance and source of a range's packed copy.
+inline int32_t pack_pair(const RangePlan& rp) {
+  return rp.tile_kind == tk::kU8P ? 32 * rp.tile_h : 0;
+}
+inline PackSource pack_source(dd_dtype dtype) {
+  return dtype == DD_U16 ? PackSource::kU16 : dtype == DD_U4 ? PackSource::kU4 : PackSource::kU8;
+}
 // Time-major [t][c] to channel-major [c][t] for t in [t_begin, t_end) (transpose.cu).
 int launch_transpose(int elem_bytes, const void* d_in, int64_t in_row_stride, int32_t n_chan,
                      void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,

@@ -94,6 +94,7 @@ int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* 
     case tk::kU4: return launch_pattern_kind<tk::kU4>(rp.tile_shape, prm, grid, st);
     case tk::kU8P: return launch_pattern_kind<tk::kU8P>(rp.tile_shape, prm, grid, st);
     case tk::kF32D: return launch_pattern_kind<tk::kF32D>(rp.tile_shape, prm, grid, st);
+    case tk::kU16P: return launch_pattern_kind<tk::kU16P>(rp.tile_shape, prm, grid, st);
     case tk::kF32: return launch_pattern_kind<tk::kF32>(rp.tile_shape, prm, grid, st);
   }
   return static_cast<int>(cudaErrorInvalidValue);

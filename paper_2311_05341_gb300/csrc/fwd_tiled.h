@@ -22,12 +22,19 @@ namespace tk {
 // 32-bit word t already holds samples t and t + pair in its 16-bit halves (the
 // pattern tiles stage it as window words directly).  kF32D: float32 at bin 1
 // staged as window words directly (the input words are the window words).
+// kU16P: uint16 at bin 1 read from a copy widened to 32-bit words.
 // Values 1-3 equal dd_dtype.
-enum Kind : int { kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6, kF32D = 7 };
+enum Kind : int {
+  kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6, kF32D = 7, kU16P = 8
+};
 
-// Float window words; kinds whose staged words are the window words.
+// Float window words; kinds whose staged words are the window words; kinds
+// that read a packed copy of the input made in caller scratch.
 DD_HOST_DEVICE constexpr bool float_kind(int kind) { return kind == kF32 || kind == kF32D; }
-DD_HOST_DEVICE constexpr bool direct_kind(int kind) { return kind == kU8P || kind == kF32D; }
+DD_HOST_DEVICE constexpr bool packed_copy_kind(int kind) { return kind == kU8P || kind == kU16P; }
+DD_HOST_DEVICE constexpr bool direct_kind(int kind) {
+  return packed_copy_kind(kind) || kind == kF32D;
+}
 
 // Window words pair samples u and u + pair in their 16-bit halves.
 DD_HOST_DEVICE constexpr bool packed_pairs(int kind) {

@@ -1,5 +1,5 @@
 // pack.cu -- the packed copy of a uint8 (or 4-bit) filterbank read by the
-// kU8P pattern tiles: word t of channel c holds samples t and t + pair in its 16-bit halves,
+// kU8P pattern tiles (uint16: the copy widened to 32-bit words, kU16P): word t of channel c holds samples t and t + pair in its 16-bit halves,
 //   W[c][t] = X[c][t] | X[c][t + pair] << 16   (0 where an index reaches n_samp),
 // so the tiles stage window words without unpacking.  HBM-bound: reads the
 // input twice (the second read mostly from L2) and writes four bytes per sample.
@@ -98,11 +98,45 @@ __global__ void __launch_bounds__(256) pack_pairs4_kernel(const uint8_t* __restr
       *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
 }
 
+// uint16 input widened to one sample per 32-bit word (pair unused).
+__global__ void __launch_bounds__(256) widen16_kernel(const uint8_t* __restrict__ in,
+                                                      int64_t in_stride, int64_t n_samp,
+                                                      uint32_t* __restrict__ out,
+                                                      int64_t out_stride, int64_t chunks_per_row,
+                                                      int32_t n_chan, int64_t t_begin,
+                                                      int64_t t_end) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c = gid / chunks_per_row;
+  const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
+  if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
+  const uint16_t* row = reinterpret_cast<const uint16_t*>(in + c * in_stride);
+  uint32_t* dst = out + c * out_stride + t;
+  uint32_t w[kPackPerThread];
+  if (t + kPackPerThread <= n_samp) {
+    // Two aligned 16-byte loads (t is a multiple of 16, rows 16-byte aligned).
+    const uint4 a = *reinterpret_cast<const uint4*>(row + t);
+    const uint4 b = *reinterpret_cast<const uint4*>(row + t + 8);
+    const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      w[2 * k] = v[k] & 0xffffu;
+      w[2 * k + 1] = v[k] >> 16;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPackPerThread; ++k) w[k] = t + k < n_samp ? row[t + k] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kPackPerThread; k += 4)
+    if (t + k < t_end)
+      *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
+}
+
 }  // namespace
 
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, bool four_bit, void* stream) {
+                      int64_t t_end, PackSource src, void* stream) {
   if (n_chan <= 0 || n_samp <= 0 || t_end <= t_begin) return 0;
   if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_stride < n_samp ||
       t_begin % 16 != 0 || t_begin < 0 || t_end % 4 != 0 || t_end > out_stride)
@@ -114,7 +148,10 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
   const auto* in = static_cast<const uint8_t*>(d_in);
   auto* out = static_cast<uint32_t*>(d_out);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (four_bit)
+  if (src == PackSource::kU16)
+    widen16_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        in, in_stride, n_samp, out, out_stride, chunks, n_chan, t_begin, t_end);
+  else if (src == PackSource::kU4)
     pack_pairs4_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end);
   else

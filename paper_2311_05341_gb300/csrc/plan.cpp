@@ -514,14 +514,15 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_chunk_bytes = 0;
   rp.tile_nv = 0;
   rp.tile_recs.clear();
-  // Packed input (uint8 or 4-bit at bin 1): the same packed word format.
-  const bool packed = rp.tile_request == DD_TILE_PACKED && (dtype == DD_U8 || dtype == DD_U4) &&
-                      rp.r.bin == 1;
-  const int kind = packed                             ? tk::kU8P
+  // Packed input at bin 1: uint8 and 4-bit share the paired word format,
+  // uint16 is widened to one sample per word.
+  const bool packed = rp.tile_request == DD_TILE_PACKED &&
+                      (dtype == DD_U8 || dtype == DD_U4 || dtype == DD_U16) && rp.r.bin == 1;
+  const int kind = packed                             ? (dtype == DD_U16 ? tk::kU16P : tk::kU8P)
                    : dtype == DD_U4                   ? tk::kU4
                    : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
                                                       : static_cast<int>(dtype);
-  if (rp.tile_request == DD_TILE_PACKED && kind != tk::kU8P) return;
+  if (rp.tile_request == DD_TILE_PACKED && !tk::packed_copy_kind(kind)) return;
   if (!tk::bin_supported(kind, rp.r.bin)) return;
   if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == DD_TILE_MERGE ||
       rp.tile_request == DD_TILE_PACKED || rp.tile_request == 0) {

@@ -69,7 +69,7 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
   // Every range must run on the tiled kernel, and all tables must fit.
   size_t need = tk::kStatusBytes;
   for (const RangePlan& rp : plan->ranges) {
-    if (!rp.tile_ok || rp.tile_kind == tk::kU8P)
+    if (!rp.tile_ok || tk::packed_copy_kind(rp.tile_kind))
       return fail(DD_ERR_UNSUPPORTED,
                   "dd_run_u8_noalloc needs every range on the tiled kernel, not DD_TILE_PACKED");
     if (range_n_out(plan, rp, n_samp) <= 0)

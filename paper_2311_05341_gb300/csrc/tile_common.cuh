@@ -328,7 +328,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
           tr[wbase + j] = v & 0xffffu;
           tr[wbase + j + kHiOff] = v >> 16;
           acc[i][j] = 0u;
-        } else if constexpr (KIND == kU16 || KIND == kU8W) {
+        } else if constexpr (KIND == kU16 || KIND == kU8W || KIND == kU16P) {
           tr[wbase + j] = acc[i][j];
           acc[i][j] = 0u;
         } else {

@@ -122,3 +122,37 @@ def test_packed_host_pipeline():
     ref = oracle.forward(np.ascontiguousarray(x[:, :n_samp]), freqs, 1500.0, 64e-6, ranges)
     for r, (g, o) in enumerate(zip(plan.split(h_out, n_samp), ref)):
         np.testing.assert_array_equal(g.numpy(), o, err_msg=f"range {r}")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_packed_uint16(seed):
+    """uint16 through the packed tile (the input widened to 32-bit words),
+    beside a binned range, on the device and through the host pipeline."""
+    rng = np.random.default_rng(5400 + seed)
+    n_chan = int(rng.choice([1, 33, 257]))
+    f_high = float(rng.uniform(900, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / 64e-6
+    step = float(rng.uniform(0.2, 2.9)) / k_low
+    n_dm = int(rng.choice([7, 64, 130]))
+    ranges = [(0.0, n_dm * step, step, 1), (n_dm * step, 2 * n_dm * step, 2 * step, 2)]
+    s_max = max((oracle.extent(freqs, f_high, 64e-6, r, 10 ** 9)[0] + 1) * r[3] for r in ranges)
+    n_samp = int(s_max + rng.choice([1, 1471, 30001]))
+    stride = (n_samp + 7) // 8 * 8
+    x = filterbank(np.uint16, n_chan, n_samp, 5500 + seed, 40000, 12000, row_stride=stride)
+    x[:, n_samp:] = 65535
+    ref = oracle.forward(np.ascontiguousarray(x[:, :n_samp]), freqs, f_high, 64e-6, ranges)
+    plan = dd.Plan(freqs, f_high, 64e-6, ranges, "u16")
+    plan.set_tile(0, "packed")
+    info = plan.info(n_samp)
+    assert info["tile_dms"][0] == _lib.DD_TILE_PACKED
+    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
+    for r, (g, o) in enumerate(zip(got, ref)):
+        np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.full((info["out_elems"],), -5, dtype=torch.int32).pin_memory()
+    plan.run_host(h_in, h_out, torch.empty_like(h_in, device="cuda"), plan.empty_output(n_samp),
+                  n_samp=n_samp)
+    torch.cuda.synchronize()
+    for r, (g, o) in enumerate(zip(plan.split(h_out, n_samp), ref)):
+        np.testing.assert_array_equal(g.numpy(), o, err_msg=f"host range {r}")
