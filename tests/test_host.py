@@ -271,3 +271,38 @@ def test_adjoint_scratch_bytes():
         _lib.DD_ERR_UNSUPPORTED
     assert lib.dd_adjoint_scratch_bytes(plan.handle, 0, ctypes.byref(got)) == _lib.DD_ERR_SHAPE
     assert lib.dd_adjoint_scratch_bytes(plan.handle, n_samp, None) == _lib.DD_ERR_INVALID_ARG
+
+
+def test_packed_tile_selection_and_scratch_bytes():
+    """DD_TILE_PACKED serves uint8, 4-bit and uint16 ranges at bin 1 only (not
+    float32, not binned ranges); it is never the automatic choice; the input
+    scratch is n_chan x ceil4(n_samp) 32-bit words when some range is packed."""
+    lib = _lib.load()
+    paper = workloads.paper_u8()
+    # The paper band and DM step on fewer channels and DMs (quick to plan).
+    paper.n_chan, paper.ranges = 1024, [(0.0, 51.2, 0.1, 1)]
+    need = ctypes.c_size_t(0)
+    for dtype in ("u8", "u4", "u16"):
+        plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, dtype,
+                       upload=False)
+        assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN], dtype
+        assert lib.dd_plan_input_scratch_bytes(plan.handle, 1001, ctypes.byref(need)) == \
+            _lib.DD_OK
+        assert need.value == 0
+        plan.set_tile(0, "packed")
+        assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PACKED], dtype
+        assert lib.dd_plan_input_scratch_bytes(plan.handle, 1001, ctypes.byref(need)) == \
+            _lib.DD_OK
+        assert need.value == paper.n_chan * 1004 * 4
+    f32 = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "f32", upload=False)
+    with pytest.raises(dd.DDError) as ei:
+        f32.set_tile(0, "packed")
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    binned = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, [(0.0, 40.0, 0.2, 2)], "u8",
+                     upload=False)
+    with pytest.raises(dd.DDError):
+        binned.set_tile(0, "packed")
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
+    assert lib.dd_plan_input_scratch_bytes(plan.handle, 0, ctypes.byref(need)) == \
+        _lib.DD_ERR_SHAPE
+    assert lib.dd_plan_input_scratch_bytes(plan.handle, 10, None) == _lib.DD_ERR_INVALID_ARG
