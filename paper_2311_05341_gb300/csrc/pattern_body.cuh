@@ -235,8 +235,12 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     }
 
     // Shift-and-sum.  The loops stay rolled so the dispatch blocks, and their
-    // PTX labels, appear once per instantiation.
-    if constexpr (PAIRS) {
+    // PTX labels, appear once per instantiation.  A direct-kind thread whose
+    // wait gave up skips it: its records may not have landed (the stage ends
+    // with the barrier that reports the timeout; no barrier lies in between).
+    if (kDirect && !ok) {
+      // nothing to add
+    } else if constexpr (PAIRS) {
       const uint32_t lane_win = smem_u32(pwb + H * l);
       const unsigned char* ck = rec_buf(rb);
       const int n_pairs = ck[w], n_items = n_pairs + ck[kPairMaxWarps + w];
