@@ -37,8 +37,7 @@ HBM_GBS = 6644.1      # measured copy bandwidth of the GB300s
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu), keyed by
 # workload, raw samples and tile; valid only for the kernel build it was taken
 # on (profiles/fwd_pattern_u8_8192ch.md).
-TRAFFIC = {("paper_u8", 262144, (0x104,)): 13.41e9 + 63.07e9,
-           ("paper_u8", 262144, (0x106,)): 34.25e9 + 65.51e9}
+TRAFFIC = {("paper_u8", 262144, (0x104,)): 13.41e9 + 63.07e9}
 UNIT = "DM*samples/s"
 
 
