@@ -468,3 +468,40 @@ def test_packed4_equals_unpacked_u8(oracle_mod, synth_mod):
     b = oracle_mod.forward(np.ascontiguousarray(vals[:, :n]), freqs, 1500.0, 64e-6, ranges)
     for pa, pb in zip(a, b):
         np.testing.assert_array_equal(pa, pb)
+
+
+def test_adjoint_is_a_forward_transform_of_padded_rows(oracle_mod, synth_mod):
+    """The identity the CUDA adjoint is built on, checked in FP64 against the
+    oracle transpose: per range, with P = s_max and the cotangent rows padded
+    with P zeros on both sides, xbar_r[c][u] = sum_d Z[d][u + P - s(c, d)] --
+    Eq. 3 on "channels" d at shifts P - s(c, d) for the channels taken in
+    reverse order (shifts that grow with the reversed index) -- and the raw
+    samples take the decimated sample floor(t / b)."""
+    freqs = synth_mod.channel_freqs(1400.0, 300.0, 24)
+    ranges = [(0.0, 30.0, 0.5, 1), (30.0, 60.0, 1.0, 2)]
+    t_samp, n_samp = 1e-4, 1500
+    rng = np.random.default_rng(12)
+    want_planes = oracle_mod.forward(np.zeros((24, n_samp), np.float32), freqs, 1400.0, t_samp,
+                                     ranges)
+    ys = [rng.standard_normal(p.shape) for p in want_planes]
+    want = oracle_mod.adjoint(ys, 24, n_samp, freqs, 1400.0, t_samp, ranges)
+    got = np.zeros((24, n_samp))
+    for r, y in zip(ranges, ys):
+        s = oracle_mod.shift_table(freqs, 1400.0, t_samp, r).astype(np.int64)  # [d][c]
+        n_dm, n_out = y.shape
+        b = r[3]
+        u_len = (n_samp - 1) // b + 1
+        pad = int(s.max())
+        z = np.zeros((n_dm, u_len + pad))
+        z[:, pad:pad + n_out] = y
+        # Reversed channel order: trial c' = n_chan - 1 - c, shifts pad - s.
+        shifts_t = pad - s[:, ::-1]  # [d][c']
+        assert np.all(shifts_t >= 0)
+        # Increments along c' are the adjacent channels' delay differences (>= 0).
+        assert np.all(np.diff(shifts_t, axis=1) >= 0)
+        zc = np.zeros((24, u_len))
+        for cp in range(24):
+            for d in range(n_dm):
+                zc[cp] += z[d, shifts_t[d, cp]:shifts_t[d, cp] + u_len]
+        got += zc[::-1][:, np.arange(n_samp) // b]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
