@@ -184,7 +184,7 @@ def run_ours(args):
         for r in range(len(beam.ranges)):
             plan.set_tile(r, args.tile if args.tile in ("pattern", "merge", "packed")
                           else int(args.tile))
-    elif beam.dtype in ("u8", "u4", "u16"):
+    elif beam.dtype in ("u8", "u4", "u16", "f32"):
         # The fastest integer path: the packed tile where it serves (it needs
         # the caller scratch allocated below, so dd_plan_create does not pick
         # it).
@@ -217,9 +217,20 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    def step():
-        plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp,
-                     scratch=scratch)
+    def step(ev_mid=None):
+        """One pass: the packing launch (packed ranges) and the transform; with
+        ev_mid, an event between them so the transform is timed alone."""
+        if scratch is None:
+            if ev_mid is not None:
+                ev_mid.record(stream)
+            plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp)
+            return
+        _lib.check(lib.dd_pack_input(plan.handle, x.data_ptr(), x.stride(0) * spe, beam.n_samp,
+                                     scratch.data_ptr(), scratch.numel(), sp))
+        if ev_mid is not None:
+            ev_mid.record(stream)
+        _lib.check(lib.dd_run_packed(plan.handle, x.data_ptr(), x.stride(0) * spe, beam.n_samp,
+                                     out.data_ptr(), scratch.data_ptr(), scratch.numel(), sp))
 
     for _ in range(args.warmup):
         step()
@@ -237,20 +248,24 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     evs[0].record(stream)
     for i in range(args.steps):
-        step()
+        step(mids[i])
         evs[i + 1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
+    # The dominant kernel alone: the transform launches between mids[i] and evs[i + 1].
+    kern = sum(mids[i].elapsed_time(evs[i + 1]) for i in range(args.steps)) / 1e3 / args.steps
     value, total = replica_throughput(dm_samples * args.steps, sum(per), "cuda")
     ms_per_step = total / args.steps * 1e3
 
     # End to end through the C ABI: pinned host in -> device -> pinned host out.
     e2e = None
+    e2e_buffers = None
     if not args.no_e2e:
         h_in = torch.from_numpy(x_host).pin_memory()
         h_out = torch.empty(info["out_elems"], dtype=plan.out_dtype()).pin_memory()
@@ -268,6 +283,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
                "ms_per_step": sec * 1e3}
+        e2e_buffers = (h_in, h_out)
 
     peaks = measure_alu_peak(torch, lib)
     if rank != 0:
@@ -276,7 +292,7 @@ def run_ours(args):
     # against the add rate derived from the SM's integer units and clock (a
     # three-input add retires on the 16-lane integer pipe of each of the 4 SM
     # sub-partitions; float adds on both 16-lane float pipes).
-    sample_adds_per_s = chan_adds / (total / args.steps)
+    sample_adds_per_s = chan_adds / kern  # the transform kernel's own launch time
     sms = peaks["sm_count"]
     per_lane = {"u8": 4, "u4": 4, "u16": 2, "f32": 1}[beam.dtype]
     lanes = 128 if beam.dtype == "f32" else 64  # lane-ops per clock per SM
@@ -288,6 +304,8 @@ def run_ours(args):
         "bound": "alu", "achieved": sample_adds_per_s / 1e12, "peak": peak_adds / 1e12,
         "unit": "Tadd/s", "frac": sample_adds_per_s / peak_adds,
         "traffic": traffic,
+        "kernel_ms": kern * 1e3,
+        "frac_whole_step": chan_adds / (total / args.steps) / peak_adds,
         "peak_source": ("%d lane-ops/clk/SM x %d SMs x %g MHz x %d sample-adds per lane-op"
                         % (lanes, sms, SM_MAX_MHZ, per_lane)),
         "alu_microbench": {k: v for k, v in peaks.items()},
@@ -327,6 +345,17 @@ def run_ours(args):
         if beam.dtype in ("u8", "u16", "f32") and len(beam.ranges) == 1 and beam.ranges[0][3] == 1:
             line["cpu_baseline_tiled"] = cpu_tiled_baseline(beam, x_host, plan.shifts(0), info,
                                                             args.cpu_tiled_rows)
+    if ws == 1 and args.workload == "paper_u8" and not args.no_extras:
+        # The rest of the headline metric on the same GPU: batched vs plain
+        # (config 3), streamed vs plain with p50/p99 latency and the real-time
+        # factor over an arrival-rate sweep (config 5), and the float32
+        # forward / adjoint / training step (config 4).  Each carries its own
+        # clock record.
+        del x, out, scratch, e2e_buffers
+        torch.cuda.empty_cache()
+        line["batched"] = batched_result(args)
+        line["stream"] = stream_result(args)
+        line["diff_f32"] = diff_result(args)
     print(json.dumps(line))
 
 
@@ -449,163 +478,195 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_batched(args):
-    """Config 3: 24 u8 + 8 u16 + 4 f32 beams, persistent launches (one per tile
-    family, CUDA graph) against the plain path (one dd_run per beam, each
-    plan's automatic tile)."""
+def _timed(fn, steps, warmup, stream=None):
+    """Mean seconds per call of fn over `steps` calls after `warmup` calls
+    (CUDA events on the current stream)."""
     import torch
-    import paper_2311_05341_gb300 as dd
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps / 1e3
+
+
+def batched_result(args):
+    """Config 3: 24 u8 + 8 u16 + 4 f32 beams in persistent launches (one per
+    tile variant, autotuned tiles, CUDA graph) against the plain path (one
+    dd_run per beam on each plan's tuned tile), same inputs, same outputs."""
+    import torch
     from paper_2311_05341_gb300 import batch as ddb
     from synth import workloads
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
     beams = workloads.batched()
     specs = [ddb.BeamSpec(b.freqs, b.f_high, b.t_samp, b.ranges, b.dtype, b.n_samp) for b in beams]
+    t_setup = time.perf_counter()
     runner = ddb.BatchRunner(specs, autotune=True, graph=True)
     for b, x in zip(beams, runner.inputs):
         h = workloads.make_input(b, lambda r, d, b=b: _plan_shifts_cache(b)[r][d], *_sizes(b))
         x[:, : b.n_samp].copy_(torch.from_numpy(h).to(x.device))
     torch.cuda.synchronize()
-    plain = [dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, b.dtype) for b in beams]
-    plain_out = [p.empty_output(b.n_samp) for p, b in zip(plain, beams)]
-    units = sum(sum(a * c for a, c in zip(p.info(b.n_samp)["n_dm"], p.info(b.n_samp)["n_out"]))
-                for p, b in zip(plain, beams))
-    adds = sum(sum(a * c for a, c in zip(p.info(b.n_samp)["n_dm"], p.info(b.n_samp)["n_out"]))
-               * b.n_chan for p, b in zip(plain, beams))
+    t_setup = time.perf_counter() - t_setup
+    infos = [p.info(b.n_samp) for p, b in zip(runner.plans, beams)]
+    units = sum(sum(a * c for a, c in zip(i["n_dm"], i["n_out"])) for i in infos)
+    adds = sum(sum(a * c for a, c in zip(i["n_dm"], i["n_out"])) * b.n_chan
+               for i, b in zip(infos, beams))
+    plain_out = [torch.empty_like(o) for o in runner.outputs]
 
     def plain_step():
-        for p, x, o, b in zip(plain, runner.inputs, plain_out, beams):
+        for p, x, o, b in zip(runner.plans, runner.inputs, plain_out, beams):
             p.run(x, out=o, n_samp=b.n_samp)
 
-    def time(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps / 1e3
-
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    t_plain = time(plain_step)
-    t_batch = time(runner.run)
+    t_plain = _timed(plain_step, args.steps, args.warmup)
+    t_batch = _timed(runner.run, args.steps, args.warmup)
     clk = clocks.stop()
     runner.status()
     same = all(torch.equal(a, c) for a, c in zip(plain_out, runner.outputs))
-    line = {
-        "metric": METRIC, "value": units / t_batch, "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
-        "data": "synthetic",
-        "config": {"workload": "batched: 24 x u8 1024 ch x 131072 (2048 DMs step 0.1), "
-                               "8 x u16 4096 ch x 65536 at 54.6 us (3072 DMs step 0.2), "
-                               "4 x f32 336 ch x 32768 at 327.68 us (1024 DMs step 0.2)",
-                   "beams": len(beams), "work_items": runner.n_items,
-                   "tiles": runner.shapes[0] + runner.shapes[24] + runner.shapes[32]},
+    tiles = {}
+    for b, shp in zip(beams, runner.shapes):
+        tiles.setdefault(b.dtype, str(shp[0]))
+    res = {
+        "workload": "24 x u8 1024 ch x 131072 (2048 DMs step 0.1), 8 x u16 4096 ch x 65536 "
+                    "at 54.6 us (3072 DMs step 0.2), 4 x f32 336 ch x 32768 at 327.68 us "
+                    "(1024 DMs step 0.2)",
+        "value": units / t_batch, "unit": UNIT, "ms_per_step": t_batch * 1e3,
         "channel_adds_per_s": adds / t_batch,
         "plain_per_beam": {"value": units / t_plain, "ms_per_step": t_plain * 1e3},
         "batched_over_plain": t_plain / t_batch,
         "outputs_identical_to_plain": bool(same),
-        "gpu_launches": args.steps * runner.n_launches,
-        "clocks": clk,
+        "beams": len(beams), "work_items": runner.n_items, "tiles": tiles,
+        "launches_per_step": runner.n_launches, "setup_s": t_setup, "clocks": clk,
     }
+    del runner, plain_out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(args):
+    res = batched_result(args)
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+            "data": "synthetic", "config": {"workload": "batched: " + res["workload"]},
+            "gpu_launches": args.steps * res["launches_per_step"], "clocks": res["clocks"],
+            "batched": res}
     print(json.dumps(line))
 
 
-def run_stream(args):
-    """Config 5: 64 u8 beams of 4096 channels, chunks of 65536 samples, Poisson
-    arrivals at m x real time, 4-range decimated plan, HBM-budget admission."""
+def stream_result(args):
+    """Config 5: 64 u8 beams of 4096 channels, chunks of 65536 samples, the
+    4-range decimated plan.  (1) Saturated: the server (windowed outputs,
+    packed tile, one stream per beam) against the plain per-beam path (dd_run
+    over the whole overlap + chunk window, one stream), on the same chunks,
+    with identical outputs.  (2) Poisson arrivals at each rate (multiples of
+    real time): p50/p99 chunk latency and the aggregate real-time factor
+    (Sec. 5.4's R); the knee is the highest rate whose p99 stays within one
+    chunk's duration."""
     import torch
     from paper_2311_05341_gb300 import stream as dds
-    from synth import poisson_arrivals, workloads, filterbank
+    from synth import filterbank, poisson_arrivals, workloads
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
     chunk, n_beams = 65536, 64
     beam0 = workloads.stream_beam(0, chunk)
     spec = dds.StreamSpec(beam0.freqs, beam0.f_high, beam0.t_samp, beam0.ranges, "u8")
     pool = [torch.from_numpy(filterbank(np.uint8, beam0.n_chan, chunk, 5000 + i, 128, 16))
             .pin_memory() for i in range(4)]
     chunk_s = chunk * beam0.t_samp
-    results = []
+    budget = int(args.hbm_budget_gb * 2**30)
     plan_cache = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    sat = _stream_saturated(args, spec, pool, chunk, plan_cache)
+    sweep = []
     for m in args.stream_rates:
-        srv = dds.StreamServer(chunk, int(args.hbm_budget_gb * 2**30), plan_cache=plan_cache)
-        need = srv.beam_bytes(spec)
+        srv = dds.StreamServer(chunk, budget, plan_cache=plan_cache)
         rng = np.random.default_rng(int(m * 1000))
         n_chunks = rng.integers(2, 6, n_beams)
         sched = []
         for b in range(n_beams):
             ts = poisson_arrivals(7000 + b + int(m * 100), m / chunk_s, int(n_chunks[b]))
-            sched += [(float(t), b) for t in ts]
+            sched += [(float(t), b) for t in ts if t < args.stream_seconds]
         sched.sort()
+        last = {}
+        for k, (_, b) in enumerate(sched):
+            last[b] = k  # a beam's stream ends with its last scheduled chunk
         for b in range(n_beams):
             srv.request(b, spec)
-        sent = {b: 0 for b in range(n_beams)}
-        pending_release = set()
         t0 = time.perf_counter()
         i = 0
-        while True:
+        ended = set()
+        while i < len(sched) or srv.queue or srv.inflight:
             now = time.perf_counter() - t0
-            if now > args.stream_seconds:
-                break
             while i < len(sched) and sched[i][0] <= now:
                 _, b = sched[i]
-                srv.submit(b, pool[(b + sent[b]) % len(pool)], arrival=t0 + sched[i][0])
-                sent[b] += 1
-                if sent[b] == n_chunks[b]:
-                    pending_release.add(b)
+                srv.submit(b, pool[(b + i) % len(pool)], arrival=t0 + sched[i][0])
+                if last[b] == i:
+                    ended.add(b)
                 i += 1
             srv.pump()
-            for b in list(pending_release):
-                if srv.is_admitted(b) and not any(j.beam == b for j in list(srv.queue) +
-                                                  srv.inflight):
+            for b in list(ended):  # streams that ended leave and free their memory
+                if srv.is_admitted(b) and not srv.has_work(b):
                     srv.release(b)
-                    pending_release.discard(b)
-            if i >= len(sched) and not srv.queue and not srv.inflight and not pending_release:
-                break
+                    ended.discard(b)
+            if now > 4 * args.stream_seconds:
+                break  # far over capacity: stop waiting
             time.sleep(0.0005)
+        srv.drain()
         wall = time.perf_counter() - t0
-        torch.cuda.synchronize()
         st = srv.stats()
         dm_samples_per_chunk = sum(
             n * (chunk // r[3]) for n, r in zip(srv._plan(spec).info(0)["n_dm"], spec.ranges))
-        results.append({"rate_x_realtime": m, "wall_s": wall, **st,
-                        "beam_bytes": need,
-                        "data_seconds_done": st["chunks"] * chunk_s,
-                        "real_time_factor_aggregate": st["chunks"] * chunk_s / wall,
-                        "dm_samples_per_s": st["chunks"] * dm_samples_per_chunk / wall})
-    sat = _stream_saturated(args, spec, pool, chunk, plan_cache)
-    print(json.dumps({"metric": "p50/p99 chunk latency, real-time factor",
-                      "workload": "stream: 64 beams u8 4096 ch, 1670 MHz top, 320 MHz band, "
-                                  "64 us, chunks 65536 + overlap; DM 0-150/0.1 b1, 150-300/0.2 b2, "
-                                  "300-1000/0.5 b4, 1000-2000/1.0 b8",
-                      "hbm_budget_gb": args.hbm_budget_gb, "results": results,
-                      "saturated": sat}))
+        sweep.append({"rate_x_realtime": m, "chunks": st["chunks"], "p50_ms": st["p50_ms"],
+                      "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "wall_s": wall,
+                      "admitted": st["admitted"], "waiting": st["waiting"],
+                      "real_time_factor_aggregate": st["chunks"] * chunk_s / wall,
+                      "dm_samples_per_s": st["chunks"] * dm_samples_per_chunk / wall})
+        del srv
+    clk = clocks.stop()
+    ok = [r["rate_x_realtime"] for r in sweep if r["p99_ms"] <= chunk_s * 1e3]
+    res = {"workload": "64 beams u8 4096 ch, 1670 MHz top, 320 MHz band, 64 us, chunks 65536 "
+                       "+ overlap; DM 0-150/0.1 b1, 150-300/0.2 b2, 300-1000/0.5 b4, "
+                       "1000-2000/1.0 b8",
+           "chunk_s": chunk_s, "hbm_budget_gb": args.hbm_budget_gb,
+           "saturated": sat, "sweep": sweep,
+           "knee_x_realtime": max(ok) if ok else None,
+           "knee_rule": "highest swept rate with p99 chunk latency <= one chunk (4.19 s)",
+           "clocks": clk}
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_stream(args):
+    res = stream_result(args)
+    print(json.dumps({"metric": "p50/p99 chunk latency, real-time factor", **res}))
 
 
 def _stream_saturated(args, spec, pool, chunk, plan_cache):
     """Server against the plain per-beam path on the same chunks, all queued at
     once: the plain path runs every beam's chunks one after another on one
-    stream (copy in, dd_run, keep the overlap), the server launches them on
-    per-beam streams.  Both end with each beam's last window output, which
-    depends on every earlier chunk through the overlap; they must be equal."""
+    stream (copy in, dd_run of the whole window on the plan's automatic tiles,
+    keep the overlap); the server launches them on per-beam streams and
+    computes each range's chunk / bin new outputs only (dd_run_window).  Both
+    end with each beam's last window outputs, which depend on every earlier
+    chunk through the overlap; they must be equal."""
     import torch
+    import paper_2311_05341_gb300 as dd
     from paper_2311_05341_gb300 import stream as dds
     from paper_2311_05341_gb300.batch import input_buffer
 
     n_beams, per_beam = args.stream_sat_beams, args.stream_sat_chunks
     srv = dds.StreamServer(chunk, int(args.hbm_budget_gb * 2**30), plan_cache=plan_cache)
-    plan = srv._plan(spec)
+    plan = dd.Plan(spec.freqs, spec.f_ref, spec.t_samp, spec.ranges, spec.dtype)
     ov = dds.overlap_for(plan, spec.ranges)
     n = ov + chunk
-    dm_samples_per_chunk = sum(
-        k * (chunk // r[3]) for k, r in zip(plan.info(0)["n_dm"], spec.ranges))
+    keep = srv.keep_counts(spec)
+    dm_samples_per_chunk = sum(k * c for k, c in zip(plan.info(0)["n_dm"], keep))
     jobs = [(b, pool[(b + j) % len(pool)]) for j in range(per_beam) for b in range(n_beams)]
 
     # Plain: one stream, beam after beam.
@@ -649,16 +710,66 @@ def _stream_saturated(args, spec, pool, chunk, plan_cache):
     server()
     torch.cuda.synchronize()
     t_srv = time.perf_counter() - t0
-    same = all(torch.equal(srv.beams[b].out, outs[b]) for b in range(n_beams))
+    same = True
+    for b in range(n_beams):
+        for k, p_srv, p_plain in zip(keep, srv.planes(srv.beams[b]), plan.split(outs[b], n)):
+            same = same and torch.equal(p_srv, p_plain[:, :k])
     total = len(jobs) * dm_samples_per_chunk
     st = srv.stats()
-    return {"beams": n_beams, "chunks": len(jobs),
-            "server_dm_samples_per_s": total / t_srv, "server_s": t_srv,
-            "plain_per_beam_dm_samples_per_s": total / t_plain, "plain_s": t_plain,
-            "server_over_plain": t_plain / t_srv,
-            "real_time_factor_server": len(jobs) * chunk * spec.t_samp / t_srv,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "outputs_identical_to_plain": bool(same)}
+    res = {"beams": n_beams, "chunks": len(jobs),
+           "server_dm_samples_per_s": total / t_srv, "server_s": t_srv,
+           "plain_per_beam_dm_samples_per_s": total / t_plain, "plain_s": t_plain,
+           "server_over_plain": t_plain / t_srv,
+           "real_time_factor_server": len(jobs) * chunk * spec.t_samp / t_srv,
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+           "outputs_identical_to_plain": bool(same)}
+    for b in list(srv.beams):
+        srv.release(b)
+    del windows, outs, srv
+    return res
+
+
+def diff_result(args):
+    """Config 4: float32 1024 ch x 65536 at 128 us, 1024 DMs: forward,
+    adjoint and one training step (forward, loss sum(Y W), backward through
+    the autograd Function), CUDA events, against the float add roofline."""
+    import torch
+    import paper_2311_05341_gb300 as dd
+    from synth import workloads
+
+    beam = _workload("diff_f32")
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
+    plan.set_tile(0, "packed")  # float pairs: two adds per instruction
+    info = plan.info(beam.n_samp)
+    x_host = workloads.make_input(beam, lambda r, d: plan.shifts(r)[d], info["n_dm"],
+                                  info["n_out"], row_stride=(beam.n_samp + 3) // 4 * 4)
+    x = torch.from_numpy(x_host).cuda()
+    out = plan.empty_output(beam.n_samp)
+    scratch = torch.empty(plan.input_scratch_bytes(beam.n_samp), dtype=torch.uint8, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_fwd = _timed(lambda: plan.run_raw(x.data_ptr(), x.stride(0), beam.n_samp, out.data_ptr(),
+                                        sp, scratch=scratch), args.steps, args.warmup)
+    adj = _adjoint_timing(args, plan, x, info, beam, torch.cuda.current_stream())
+    clk = clocks.stop()
+    dm_samples = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = 128 * sms * SM_MAX_MHZ * 1e6  # FP32 add lanes per clock per SM x SMs x clock
+    adds = dm_samples * beam.n_chan
+    res = {"workload": _describe(beam), "tile": "packed (float pairs)",
+           "forward": {"ms": t_fwd * 1e3, "dm_samples_per_s": dm_samples / t_fwd,
+                       "adds_per_s": adds / t_fwd, "frac": adds / t_fwd / peak},
+           "adjoint": {**adj["adjoint"], "frac": adds / (adj["adjoint"]["ms"] / 1e3) / peak,
+                       "kernel": info["adjoint_kernel"]},
+           "train_step": adj["train_step"],
+           "adjoint_over_forward": adj["adjoint"]["ms"] / (t_fwd * 1e3),
+           "peak": {"value": peak / 1e12, "unit": "Tadd/s",
+                    "source": "128 FP32 lanes/clk/SM x %d SMs x %g MHz" % (sms, SM_MAX_MHZ)},
+           "clocks": clk}
+    del x, out, plan, scratch
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_frontend(args):
@@ -752,11 +863,12 @@ def main():
     ap.add_argument("--workload", default="paper_u8",
                     choices=["paper_u8", "paper_u16", "paper_u4", "tiny_u8", "diff_f32", "batched",
                              "stream", "frontend"])
-    ap.add_argument("--stream-rates", type=float, nargs="+", default=[1.0, 4.0])
-    ap.add_argument("--stream-seconds", type=float, default=15.0)
+    ap.add_argument("--stream-rates", type=float, nargs="+",
+                    default=[1.0, 1.25, 1.5, 2.0, 3.0, 4.0])
+    ap.add_argument("--stream-seconds", type=float, default=8.0)
     ap.add_argument("--stream-sat-beams", type=int, default=16)
     ap.add_argument("--stream-sat-chunks", type=int, default=4)
-    ap.add_argument("--hbm-budget-gb", type=float, default=100.0)
+    ap.add_argument("--hbm-budget-gb", type=float, default=170.0)
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-rows-reference", type=int, default=16)
     ap.add_argument("--cpu-tiled-rows", type=int, default=256)
@@ -769,6 +881,9 @@ def main():
                          "(8, 6, 4, 2, 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="paper_u8 only: skip the batched, streaming and float32 results "
+                         "that the default line carries")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -181,7 +181,7 @@ dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_sa
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
  * Errors: DD_ERR_INVALID_ARG for another code; DD_ERR_UNSUPPORTED if that
  * tile cannot serve the range (unsupported bin, DM offsets or increments too
- * wide for it, window too large for shared memory); the previous choice is
+ * wide for it, window too large for shared memory); the previous choice (and its workspace binding) is
  * kept.
  */
 dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile);
@@ -236,6 +236,41 @@ dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, 
                          void* d_out, void* d_scratch, size_t scratch_bytes, void* stream);
 
 /*
+ * The two halves of dd_run_scratch, for callers that reuse one packed copy
+ * (several plans over the same input) or time the transform alone.
+ * dd_pack_input writes the packed copy of d_in that the plan's DD_TILE_PACKED
+ * ranges read into d_scratch (sizes and rules as dd_run_scratch; nothing is
+ * written when the plan has no such range).  dd_run_packed is dd_run_scratch
+ * without the packing pass: d_scratch must hold the packed copy of the same
+ * d_in and n_samp, made by dd_pack_input (or an earlier dd_run_scratch) with
+ * a plan of the same channels and tile.
+ * Errors: as dd_run_scratch; dd_pack_input: DD_ERR_UNSUPPORTED if the plan's
+ * packed ranges need different copies.
+ */
+dd_status dd_pack_input(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        void* d_scratch, size_t scratch_bytes, void* stream);
+dd_status dd_run_packed(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        void* d_out, const void* d_scratch, size_t scratch_bytes, void* stream);
+
+/*
+ * dd_run_scratch restricted to a window of outputs: the first n_keep[r]
+ * outputs of each range r (1 <= n_keep[r] <= n_out_r), t in [0, n_keep[r]),
+ * each equal to that output of dd_run (Eq. 3 evaluated at those t only).
+ * d_out receives, for each range in order, n_dm_r rows of n_keep[r] samples
+ * (row d at element offset sum_{q<r} n_dm_q n_keep[q] + d n_keep[r]); int32
+ * or float32 as dd_run.  The work is proportional to sum_r n_dm_r n_keep[r]:
+ * a streaming caller whose window holds the max-delay overlap plus a new
+ * chunk asks each range for the chunk's chunk / b_r new outputs only (the
+ * real-time processing of Sec. 5.4 done incrementally).  Scratch rules as
+ * dd_run_scratch.  n_keep is host memory, read during the call.
+ * Errors: as dd_run_scratch; DD_ERR_INVALID_ARG for a NULL n_keep,
+ * DD_ERR_SHAPE for an n_keep[r] outside [1, n_out_r].
+ */
+dd_status dd_run_window(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        const int64_t* n_keep, void* d_out, void* d_scratch, size_t scratch_bytes,
+                        void* stream);
+
+/*
  * Adjoint (transpose) of dd_run for float32 plans: re-dispersion
  *   xbar[c][t] = sum_r sum_d ybar_r[d][floor(t/b_r) - s_r(c, d)]
  * over terms with 0 <= floor(t/b_r) - s_r(c,d) < n_out_r, computed as a gather
@@ -252,9 +287,13 @@ dd_status dd_run_adjoint(dd_plan plan, const float* d_ybar, float* d_xbar, int64
 
 /*
  * Device scratch bytes dd_run_adjoint_scratch needs for n_samp raw samples:
- * max_r n_dm_r x (ceil(n_samp/b_r) + s_max_r) + sum_r n_chan x ceil(n_samp/b_r)
- * floats (rows rounded up to 4 floats); 0 when the plan's adjoint kernel
- * (dd_plan_info.adjoint_kernel) is the gather.  Host only.
+ * the padded cotangent rows, max_r 2 n_dm_r x (ceil(n_samp/b_r) + s_max_r)
+ * floats (as float pairs; n_dm_r x ... floats where a range's adjoint tile
+ * stages single floats), plus the per-range results, sum_r n_chan x
+ * ceil(n_samp/b_r) floats, except for a plan of one range at bin 1, whose
+ * result goes straight into xbar (rows rounded up to 4 elements); 0 when the
+ * plan's adjoint kernel (dd_plan_info.adjoint_kernel) is the gather.  Host
+ * only.
  * Errors: DD_ERR_INVALID_ARG for null pointers, DD_ERR_UNSUPPORTED for integer
  * plans, DD_ERR_SHAPE for n_samp <= 0.
  */
@@ -281,6 +320,22 @@ dd_status dd_run_adjoint_scratch(dd_plan plan, const float* d_ybar, float* d_xba
  * spin forever; a timeout leaves that run's output undefined.
  */
 dd_status dd_plan_device_status(dd_plan plan, void* stream);
+
+/*
+ * Bound of the plan's device waits.  Every kernel stage waits for its copies
+ * with at most max_polls polls of the mbarrier (max_polls <= 0: the default,
+ * 2^22); a wait that runs out makes the kernel record DD_ERR_TIMEOUT for
+ * dd_plan_device_status (or dd_batch_status, or dd_run_u8_noalloc_status),
+ * let its issued copies land and return, leaving that run's output undefined;
+ * the context stays usable.  hold_stage >= 0 is a test hook for that path: the
+ * copies of channel stage hold_stage (of every CTA of the register-tiled
+ * kernels) are never issued, so the first wait on it runs out; -1 turns it
+ * off.  Host only; takes effect at the next launch (batches: at the next
+ * dd_batch_bind).  The paper has no counterpart: the kernels' waits are this
+ * library's own.
+ * Errors: DD_ERR_INVALID_ARG for a NULL plan or hold_stage < -1.
+ */
+dd_status dd_plan_set_wait_limit(dd_plan plan, int32_t max_polls, int32_t hold_stage);
 
 /*
  * Front end: time-major samples d_in[t][c] (the order a receiver or a SIGPROC
@@ -349,21 +404,35 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
  *     device memory (every GPU that loads the library reserves it until the
  *     process exits).  Plans whose tables exceed it get DD_ERR_BUDGET.
  *   - Every range must run on the tiled kernel (dd_plan_query's kernel is
- *     DD_KERNEL_TILED), otherwise DD_ERR_UNSUPPORTED.
+ *     DD_KERNEL_TILED) and not on DD_TILE_PACKED, otherwise
+ *     DD_ERR_UNSUPPORTED.
  *   - d_in / in_row_stride / n_samp / d_out follow dd_run; the plan needs no
  *     dd_plan_upload.  The call allocates nothing and frees nothing.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any CUDA
- *     stream capture.
+ *     stream capture.  The address is cached for the life of the process:
+ *     cudaDeviceReset between calls is not supported.
  *   - All calls share the one array, which keeps the last call's contents;
- *     each call first clears the status word and copies its tables in, on
- *     `stream`.  Calls that overlap on the GPU (different streams, or host
- *     threads) race on the array and give undefined results: serialise them.
- *   - A bounded device wait that gives up leaves this call's output undefined;
- *     it is not reported here (dd_run with dd_plan_device_status reports it).
+ *     each call copies its tables in on `stream` first.  Calls that overlap on
+ *     the GPU (different streams, or host threads) race on the array and give
+ *     undefined results: serialise them.
+ *   - The array starts with a status word, zero when the library loads; a
+ *     bounded device wait that gives up sets it (and leaves that call's output
+ *     undefined) and dd_run_u8_noalloc_status reads and clears it.
  */
 dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t in_row_stride,
                             int64_t n_samp, void* d_out, void* stream);
+
+/*
+ * Wait status of the dd_run_u8_noalloc calls on the current device since the
+ * last check: synchronises `stream`, returns DD_ERR_TIMEOUT (and clears the
+ * status word) if a bounded device wait of one of them gave up, DD_OK
+ * otherwise.  Reads the word in the fixed array through the address cached by
+ * the first dd_run_u8_noalloc call (DD_OK if there was none); allocates
+ * nothing.  The paper has no counterpart.
+ * Errors: DD_ERR_CUDA if the copy or the synchronisation fails.
+ */
+dd_status dd_run_u8_noalloc_status(void* stream);
 
 /* ---------------------------------------------------------------------------
  * Persistent batches: many beams (plans of different channel counts, dtypes,

@@ -209,6 +209,53 @@ class Plan:
             return None
         return torch.empty(int(need.value), dtype=torch.uint8, device=device)
 
+    def run_window(self, x, n_keep, out=None, n_samp: int | None = None, stream=None,
+                   scratch=None):
+        """The first n_keep[r] outputs of every range r (dd_run_window): a list of
+        [n_dm_r][n_keep[r]] planes in one flat buffer `out` (allocated if None).
+        scratch: device uint8 tensor for packed-tile ranges (allocated per call
+        from torch's caching allocator if None and the plan needs it)."""
+        import torch
+        self._check_input(x)
+        per = _samples_per_elem(self.dtype)
+        n = x.shape[1] * per if n_samp is None else int(n_samp)
+        keep = [int(k) for k in n_keep]
+        n_dm = self.info(0)["n_dm"]
+        total = sum(a * b for a, b in zip(n_dm, keep))
+        if out is None:
+            out = torch.empty(max(total, 4), dtype=self.out_dtype(), device=x.device)
+        if scratch is None:
+            scratch = self._input_scratch(n, x.device)
+        arr = (ctypes.c_int64 * len(keep))(*keep)
+        check(self._lib.dd_run_window(
+            self._h, x.data_ptr(), x.stride(0) * per, n, arr, out.data_ptr(),
+            None if scratch is None else scratch.data_ptr(),
+            0 if scratch is None else scratch.numel(), _stream_ptr(stream)))
+        if scratch is not None and stream is not None:
+            scratch.record_stream(stream)
+        planes, off = [], 0
+        for a, b in zip(n_dm, keep):
+            planes.append(out[off:off + a * b].view(a, b))
+            off += a * b
+        return planes
+
+    def input_scratch_bytes(self, n_samp: int) -> int:
+        """Device scratch bytes of the packed-tile ranges (0 without any)."""
+        need = ctypes.c_size_t(0)
+        check(self._lib.dd_plan_input_scratch_bytes(self._h, int(n_samp), ctypes.byref(need)))
+        return int(need.value)
+
+    def set_wait_limit(self, max_polls: int = 0, hold_stage: int = -1):
+        """Bound of the kernels' pipeline waits (0: default) and the timeout
+        test hook (dd_plan_set_wait_limit)."""
+        check(self._lib.dd_plan_set_wait_limit(self._h, int(max_polls), int(hold_stage)))
+        return self
+
+    def device_status(self, stream=None):
+        """Raises DDError(DD_ERR_TIMEOUT) if a bounded device wait of an earlier
+        run gave up (dd_plan_device_status); synchronises the stream."""
+        check(self._lib.dd_plan_device_status(self._h, _stream_ptr(stream)))
+
     def run_raw(self, x_ptr: int, stride: int, n_samp: int, out_ptr: int, stream_ptr: int,
                 scratch=None):
         """Forward transform on raw device pointers (no checks beyond the

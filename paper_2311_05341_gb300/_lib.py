@@ -74,6 +74,12 @@ SIGNATURES = {
     "dd_adjoint_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),
     "dd_run_u8_noalloc": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP]),
+    "dd_run_u8_noalloc_status": (ctypes.c_int, [_VP]),
+    "dd_run_window": (ctypes.c_int, [_VP, _VP, _I64, _I64, ctypes.POINTER(_I64), _VP, _VP, _SZ,
+                                     _VP]),
+    "dd_plan_set_wait_limit": (ctypes.c_int, [_VP, _I32, _I32]),
+    "dd_pack_input": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _SZ, _VP]),
+    "dd_run_packed": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _SZ, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
     "dd_run_host_tmajor": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _I64, _VP, _VP]),
     "dd_transpose": (ctypes.c_int, [ctypes.c_int, _VP, _I64, _I32, _VP, _I64, _I64, _I64, _VP]),

@@ -179,11 +179,7 @@ class BatchRunner:
         self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         check(lib.dd_batch_upload(h, self.workspace.data_ptr(), self.workspace.numel(), stream))
-        d_in = (ctypes.c_void_p * n)(*[x.data_ptr() for x in self.inputs])
-        strides = (ctypes.c_int64 * n)(*[x.stride(0) * (2 if b.dtype == "u4" else 1)
-                                         for x, b in zip(self.inputs, self.beams)])
-        d_out = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outputs])
-        check(lib.dd_batch_bind(h, d_in, strides, d_out, stream))
+        self.bind()
         n_items, n_jobs = ctypes.c_int64(), ctypes.c_int32()
         check(lib.dd_batch_info(h, ctypes.byref(n_items), ctypes.byref(n_jobs)))
         self.n_items, self.n_jobs = n_items.value, n_jobs.value
@@ -193,6 +189,18 @@ class BatchRunner:
         self.graph = None
         if graph:
             self._capture()
+
+    def bind(self):
+        """Upload the job table (buffers and each plan's launch parameters,
+        dd_batch_bind); again after a plan's wait limit changes."""
+        torch = _torch()
+        n = len(self.plans)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        d_in = (ctypes.c_void_p * n)(*[x.data_ptr() for x in self.inputs])
+        strides = (ctypes.c_int64 * n)(*[x.stride(0) * (2 if b.dtype == "u4" else 1)
+                                         for x, b in zip(self.inputs, self.beams)])
+        d_out = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outputs])
+        check(self._lib.dd_batch_bind(self._h, d_in, strides, d_out, stream))
 
     def _launch(self):
         torch = _torch()

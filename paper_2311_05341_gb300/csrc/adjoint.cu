@@ -155,13 +155,37 @@ __global__ void __launch_bounds__(256) adjoint_expand_kernel(const ExpandParams 
   xbar[static_cast<int64_t>(c) * prm.stride + t] = v;
 }
 
+// The padded cotangent rows of one range as the float-pair words the kF32P
+// pattern tile reads: word u of row d is (Z[d][u], Z[d][u + pair]) with
+// Z[d][u] = ybar[d][u - pad] for 0 <= u - pad < n_out and 0 elsewhere (the
+// rows padded with pad = s_max zeros on both sides), u < stride.  Each thread
+// writes 4 words.
+__global__ void __launch_bounds__(256) adjoint_pack_kernel(const float* __restrict__ ybar,
+                                                           int64_t n_out, int32_t pad,
+                                                           int32_t pair, int64_t stride,
+                                                           int64_t chunks_per_row, int64_t n_dm,
+                                                           float2* __restrict__ w) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t d = gid / chunks_per_row;
+  const int64_t u = (gid - d * chunks_per_row) * 4;
+  if (d >= n_dm || u >= stride) return;
+  const float* row = ybar + d * n_out;
+  auto z = [&](int64_t v) { return v >= pad && v - pad < n_out ? row[v - pad] : 0.f; };
+  float4* dst = reinterpret_cast<float4*>(w + d * stride + u);
+  dst[0] = make_float4(z(u), z(u + pair), z(u + 1), z(u + 1 + pair));
+  dst[1] = make_float4(z(u + 2), z(u + 2 + pair), z(u + 3), z(u + 3 + pair));
+}
+
 constexpr int kAdjNotServed = -1;
 
 // Per-range sizes of the pattern adjoint: decimated samples per row u_len,
-// padded cotangent row stride (16-byte rows), result row stride.
+// padded cotangent row stride (in the tile's staged elements: floats, or
+// float-pair words), result row stride; scratch in floats.  A plan of one
+// range at bin 1 writes its result straight into xbar (no result buffer).
 struct AdjSizes {
   int64_t u_len[DD_MAX_RANGES], pad_stride[DD_MAX_RANGES], z_stride[DD_MAX_RANGES];
   size_t in_floats = 0, out_floats = 0;
+  bool direct_out = false;
 };
 
 // Sizes, or false when some range has no pattern tables.
@@ -170,13 +194,15 @@ bool adjoint_sizes(const dd_plan_s* p, int64_t n_samp, AdjSizes* z) {
   if (p->adj.size() != n_r || n_r == 0 || p->n_chan > 65535 || n_samp <= 0) return false;
   for (const RangePlan& ar : p->adj)
     if (!ar.tile_ok) return false;
+  z->direct_out = n_r == 1 && p->ranges[0].r.bin == 1;
   for (size_t i = 0; i < n_r; ++i) {
     const RangePlan& rp = p->ranges[i];
+    const size_t per = tk::float_pairs(p->adj[i].tile_kind) ? 2 : 1;  // floats per element
     z->u_len[i] = (n_samp - 1) / rp.r.bin + 1;
     z->pad_stride[i] = (z->u_len[i] + rp.s_max + 3) / 4 * 4;
     z->z_stride[i] = (z->u_len[i] + 3) / 4 * 4;
-    z->in_floats = std::max(z->in_floats, static_cast<size_t>(rp.n_dm) * z->pad_stride[i]);
-    z->out_floats += static_cast<size_t>(p->n_chan) * z->z_stride[i];
+    z->in_floats = std::max(z->in_floats, per * static_cast<size_t>(rp.n_dm) * z->pad_stride[i]);
+    if (!z->direct_out) z->out_floats += static_cast<size_t>(p->n_chan) * z->z_stride[i];
   }
   return true;
 }
@@ -209,13 +235,33 @@ int launch_adjoint_pattern(const dd_plan_s* p, const float* d_ybar, float* d_xba
     const RangePlan& rp = p->ranges[i];
     const RangePlan& ar = p->adj[i];
     const int64_t pad = rp.s_max;
-    cudaError_t e = cudaMemsetAsync(
-        x_pad, 0, static_cast<size_t>(rp.n_dm) * zs.pad_stride[i] * sizeof(float), st);
-    if (e == cudaSuccess && n_out[i] > 0)
-      e = cudaMemcpy2DAsync(x_pad + pad, zs.pad_stride[i] * sizeof(float), d_ybar + out_off[i],
-                            n_out[i] * sizeof(float), n_out[i] * sizeof(float),
-                            static_cast<size_t>(rp.n_dm), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return static_cast<int>(e);
+    if (tk::float_pairs(ar.tile_kind)) {
+      // Padding and pair packing in one pass.
+      const int64_t chunks = zs.pad_stride[i] / 4;
+      const int64_t blocks = (chunks * rp.n_dm + 255) / 256;
+      if (blocks > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+      adjoint_pack_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+          d_ybar + out_off[i], n_out[i], static_cast<int32_t>(pad), pack_pair(ar),
+          zs.pad_stride[i], chunks, rp.n_dm, reinterpret_cast<float2*>(x_pad));
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return static_cast<int>(e);
+    } else {
+      cudaError_t e = cudaMemsetAsync(
+          x_pad, 0, static_cast<size_t>(rp.n_dm) * zs.pad_stride[i] * sizeof(float), st);
+      if (e == cudaSuccess && n_out[i] > 0)
+        e = cudaMemcpy2DAsync(x_pad + pad, zs.pad_stride[i] * sizeof(float), d_ybar + out_off[i],
+                              n_out[i] * sizeof(float), n_out[i] * sizeof(float),
+                              static_cast<size_t>(rp.n_dm), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return static_cast<int>(e);
+    }
+    if (zs.direct_out && ar.tile_pattern) {
+      // One range at bin 1: result row c' is xbar's row n_chan - 1 - c'.
+      const int rc = launch_forward_pattern(p, ar, ws + ar.off_tile_recs, err, x_pad,
+                                            zs.pad_stride[i], zs.u_len[i],
+                                            d_xbar + static_cast<int64_t>(p->n_chan - 1) * stride,
+                                            0, zs.u_len[i], stream, -stride);
+      return rc;
+    }
     const int rc = launch_forward_tiled_with_tables(p, ar, ws + ar.off_tile_recs, err, x_pad,
                                                     zs.pad_stride[i], zs.z_stride[i], z, 0,
                                                     zs.u_len[i], stream);

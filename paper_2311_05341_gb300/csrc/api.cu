@@ -153,7 +153,8 @@ namespace {
 size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
   for (const auto& rp : p->ranges)
     if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))
-      return static_cast<size_t>(p->n_chan) * static_cast<size_t>((n_samp + 3) / 4 * 4) * 4;
+      return static_cast<size_t>(p->n_chan) * static_cast<size_t>((n_samp + 3) / 4 * 4) *
+             packed_word_bytes(p->dtype);
   return 0;
 }
 
@@ -296,8 +297,18 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   } catch (const std::bad_alloc&) {
     return fail(DD_ERR_INVALID_ARG, "host allocation failed while retiling");
   }
-  plan->d_ws = nullptr;  // tables changed: upload again
+  // A refused tile leaves the previous tables (rebuilt identically) and the
+  // workspace binding as they were; a new tile needs dd_plan_upload.
   if (!ok) return fail(DD_ERR_UNSUPPORTED, "tile cannot serve this range");
+  plan->d_ws = nullptr;
+  return DD_OK;
+}
+
+dd_status dd_plan_set_wait_limit(dd_plan plan, int32_t max_polls, int32_t hold_stage) {
+  if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
+  if (hold_stage < -1) return fail(DD_ERR_INVALID_ARG, "hold_stage must be -1 or a stage index");
+  plan->wait_iters = max_polls > 0 ? max_polls : tk::kWaitIters;
+  plan->hold_stage = hold_stage;
   return DD_OK;
 }
 
@@ -327,11 +338,21 @@ static dd_status check_run(dd_plan plan, const void* d_in, int64_t stride, int64
   return DD_OK;
 }
 
-dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
-                         void* d_out, void* d_scratch, size_t scratch_bytes, void* stream) {
+// The forward transform of every range.  n_keep == nullptr: all n_out_r
+// outputs of each range, at dd_plan_query's offsets.  Otherwise the first
+// n_keep[r] outputs of range r, as rows of n_keep[r] samples, concatenated.
+// pack == false: the packed copy is already in d_scratch (dd_pack_input).
+static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stride,
+                             int64_t n_samp, const int64_t* n_keep, void* d_out, void* d_scratch,
+                             size_t scratch_bytes, void* stream, bool pack = true) {
   dd_plan_info info;
   dd_status st = check_run(plan, d_in, in_row_stride, n_samp, d_out, &info);
   if (st != DD_OK) return st;
+  if (n_keep) {
+    for (int32_t i = 0; i < info.n_ranges; ++i)
+      if (n_keep[i] < 1 || n_keep[i] > info.n_out[i])
+        return fail(DD_ERR_SHAPE, "n_keep[r] must be in [1, n_out_r]");
+  }
   const size_t need = packed_input_bytes(plan, n_samp);
   if (need > 0) {
     if (!d_scratch)
@@ -345,28 +366,77 @@ dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, 
   const int64_t packed_stride = (n_samp + 3) / 4 * 4;
   int32_t packed_pair = -1;  // pair distance of the packed copy now in the scratch
   const size_t osz = 4;
+  int64_t off = 0;           // element offset of the range's rows in d_out
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
-    void* o = static_cast<unsigned char*>(d_out) + info.out_offset[i] * osz;
     const RangePlan& rp = plan->ranges[i];
+    const int64_t row = n_keep ? n_keep[i] : info.n_out[i];
+    void* o = static_cast<unsigned char*>(d_out) + (n_keep ? off : info.out_offset[i]) * osz;
+    off += rp.n_dm * row;
     const void* src = d_in;
     int64_t stride = in_row_stride;
     if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {
       const int32_t pair = pack_pair(rp);
-      if (pair != packed_pair) {
+      if (!pack && packed_pair != -1 && pair != packed_pair)
+        return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
+      if (pair != packed_pair && pack) {
         int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan,
                                   n_samp, d_scratch, packed_stride, pair, 0, packed_stride,
                                   pack_source(plan->dtype), stream);
         if (e != 0) return cuda_fail(e, "dd_run packing");
-        packed_pair = pair;
       }
+      packed_pair = pair;
       src = d_scratch;
       stride = packed_stride;
     }
-    int e = launch_range(plan, rp, src, stride, n_samp, info.n_out[i], o, 0, info.n_out[i],
-                         stream);
+    int e = launch_range(plan, rp, src, stride, n_samp, row, o, 0, row, stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
   return DD_OK;
+}
+
+dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                         void* d_out, void* d_scratch, size_t scratch_bytes, void* stream) {
+  return run_forward(plan, d_in, in_row_stride, n_samp, nullptr, d_out, d_scratch, scratch_bytes,
+                     stream);
+}
+
+dd_status dd_pack_input(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        void* d_scratch, size_t scratch_bytes, void* stream) {
+  dd_plan_info info;
+  if (!d_scratch) return fail(DD_ERR_INVALID_ARG, "d_scratch is NULL");
+  dd_status st = check_run(plan, d_in, in_row_stride, n_samp, d_scratch, &info);
+  if (st != DD_OK) return st;
+  const size_t need = packed_input_bytes(plan, n_samp);
+  if (need == 0) return DD_OK;  // no range reads a packed copy
+  if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
+  const int64_t packed_stride = (n_samp + 3) / 4 * 4;
+  int32_t packed_pair = -1;
+  for (const RangePlan& rp : plan->ranges) {
+    if (!(rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))) continue;
+    const int32_t pair = pack_pair(rp);
+    if (packed_pair != -1 && pair != packed_pair)
+      return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
+    packed_pair = pair;
+  }
+  int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan, n_samp,
+                            d_scratch, packed_stride, packed_pair, 0, packed_stride,
+                            pack_source(plan->dtype), stream);
+  if (e != 0) return cuda_fail(e, "dd_pack_input");
+  return DD_OK;
+}
+
+dd_status dd_run_packed(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        void* d_out, const void* d_scratch, size_t scratch_bytes, void* stream) {
+  return run_forward(plan, d_in, in_row_stride, n_samp, nullptr, d_out,
+                     const_cast<void*>(d_scratch), scratch_bytes, stream, false);
+}
+
+dd_status dd_run_window(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
+                        const int64_t* n_keep, void* d_out, void* d_scratch, size_t scratch_bytes,
+                        void* stream) {
+  if (!n_keep) return fail(DD_ERR_INVALID_ARG, "n_keep is NULL");
+  return run_forward(plan, d_in, in_row_stride, n_samp, n_keep, d_out, d_scratch, scratch_bytes,
+                     stream);
 }
 
 dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,

@@ -78,6 +78,10 @@ struct dd_plan_s {
   // Float32 plans: per range, its adjoint as a forward transform (plan.cpp,
   // build_adjoint_range; tile_ok false where the pattern tile cannot serve it).
   std::vector<dd::RangePlan> adj;
+  // Bounded device waits (dd_plan_set_wait_limit): polls before a pipeline
+  // wait gives up, and the channel stage whose copies are withheld (-1: none).
+  int32_t wait_iters = dd::tk::kWaitIters;
+  int32_t hold_stage = -1;
 };
 
 namespace dd {
@@ -113,27 +117,37 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
                                      void* stream);
-// The pattern kernel (fwd_pattern.cu), same arguments.
+// The pattern kernel (fwd_pattern.cu), same arguments; output row d + 1
+// starts out_stride elements after row d (n_out for the output layout of
+// dd_run; negative for rows written in reverse order).
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                           void* d_out, int64_t t_begin, int64_t t_end, void* stream);
+                           void* d_out, int64_t t_begin, int64_t t_end, void* stream,
+                           int64_t out_stride);
 // Packed uint8 copy for the kU8P tiles (pack.cu): out[c][t] = in[c][t] |
 // in[c][t + pair] << 16 for t in [t_begin, t_end) (0 past n_samp); strides in
 // bytes (in) and 32-bit words (out, a multiple of 4 and >= n_samp); pair and
 // t_begin multiples of 16, t_end of 4 and <= out_stride.  Source kU4: 4-bit
 // input, two samples per byte (the earlier in the low nibble); kU16: uint16
-// input widened, out[c][t] = in[c][t] (pair unused).
-enum class PackSource { kU8, kU4, kU16 };
+// input widened, out[c][t] = in[c][t] (pair unused); kF32: float32 input,
+// 64-bit words out[c][t] = (in[c][t], in[c][t + pair]) (out_stride in those
+// words).
+enum class PackSource { kU8, kU4, kU16, kF32 };
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
                       int64_t t_end, PackSource src, void* stream);
 // Pair distance and source of a range's packed copy.
 inline int32_t pack_pair(const RangePlan& rp) {
-  return rp.tile_kind == tk::kU8P ? 32 * rp.tile_h : 0;
+  return rp.tile_kind == tk::kU8P || rp.tile_kind == tk::kF32P ? 32 * rp.tile_h : 0;
 }
 inline PackSource pack_source(dd_dtype dtype) {
-  return dtype == DD_U16 ? PackSource::kU16 : dtype == DD_U4 ? PackSource::kU4 : PackSource::kU8;
+  return dtype == DD_U16   ? PackSource::kU16
+         : dtype == DD_U4  ? PackSource::kU4
+         : dtype == DD_F32 ? PackSource::kF32
+                           : PackSource::kU8;
 }
+// Bytes of one word of a plan's packed copy.
+inline size_t packed_word_bytes(dd_dtype dtype) { return dtype == DD_F32 ? 8 : 4; }
 // Time-major [t][c] to channel-major [c][t] for t in [t_begin, t_end) (transpose.cu).
 int launch_transpose(int elem_bytes, const void* d_in, int64_t in_row_stride, int32_t n_chan,
                      void* d_out, int64_t out_row_stride, int64_t t_begin, int64_t t_end,
@@ -151,6 +165,15 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                             void* d_out);
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
+// Per-kind launchers of the pattern kernels (fwd_pattern_k*.cu): the
+// one-unit-per-CTA kernel and the persistent batch kernel of kPatShapes[shape].
+#define DD_PATTERN_KINDS(X) X(kU8) X(kU8W) X(kU8P) X(kU4) X(kU16) X(kU16P) X(kF32) X(kF32D) X(kF32P)
+#define DD_DECLARE_PATTERN_KIND(K)                                                            \
+  int pattern_forward_##K(int shape, const tk::TileParams& prm, int64_t grid, void* stream); \
+  int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem,  \
+                        void* stream);
+DD_PATTERN_KINDS(DD_DECLARE_PATTERN_KIND)
+#undef DD_DECLARE_PATTERN_KIND
 // Persistent pattern-tile launch of one variant (kind, tk::kPatShapes index).
 int launch_pattern_batch(int kind, int shape, const tk::PatBatchArgs& args, int32_t grid,
                          size_t smem, void* stream);

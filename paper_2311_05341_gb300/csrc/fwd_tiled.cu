@@ -130,13 +130,14 @@ __device__ __forceinline__ bool tile_body(const TileParams& p, const Smem& sm, i
     const uint32_t g = gstage + st;
     const int buf = g & 1;
     const uint32_t parity = (g >> 1) & 1;
-    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity);
+    const bool ok = mbar_wait(sm.bar_base + 8u * buf, parity, p.wait_iters);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.err, kErrTimeout);
         // Let copies still in flight land before the CTA exits (bounded).
-        mbar_wait(sm.bar_base + 8u * buf, parity);
-        if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((g + 1) >> 1) & 1);
+        if (st != p.hold_stage) mbar_wait(sm.bar_base + 8u * buf, parity);
+        if (st + 1 < n_st && st + 1 != p.hold_stage)
+          mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((g + 1) >> 1) & 1);
       }
       return false;
     }
@@ -318,6 +319,7 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.n_dm = static_cast<int32_t>(rp.n_dm);
   prm.n_blocks = rp.tile_n_blocks;
   prm.n_out = n_out;
+  prm.out_stride = n_out;
   prm.tile0 = 0;
   prm.t_end = n_out;
   prm.lp = rp.tile_lp;
@@ -334,6 +336,8 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   if (rp.tile_kind == tk::kU8P && p->dtype == DD_U4) prm.flush = tk::flush_channels(tk::kU4, 1);
   prm.out = d_out;
   prm.err = err;
+  prm.wait_iters = p->wait_iters;
+  prm.hold_stage = p->hold_stage;
   return prm;
 }
 
@@ -349,7 +353,7 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
                                      void* stream) {
   if (rp.tile_pattern)
     return launch_forward_pattern(p, rp, recs, err, d_in, stride, n_out, d_out, t_begin, t_end,
-                                  stream);
+                                  stream, n_out);
   tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
   const int ts = tk::tile_samples(rp.tile_kind);
   if (t_begin % ts != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)

@@ -22,16 +22,22 @@ namespace tk {
 // 32-bit word t already holds samples t and t + pair in its 16-bit halves (the
 // pattern tiles stage it as window words directly).  kF32D: float32 at bin 1
 // staged as window words directly (the input words are the window words).
-// kU16P: uint16 at bin 1 read from a copy widened to 32-bit words.
+// kU16P: uint16 at bin 1 read from a copy widened to 32-bit words.  kF32P:
+// float32 at bin 1 read from a packed copy of 64-bit words, word t holding
+// samples t and t + pair as two floats, added two at a time (add.f32x2).
 // Values 1-3 equal dd_dtype.
 enum Kind : int {
-  kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6, kF32D = 7, kU16P = 8
+  kU8 = 1, kU16 = 2, kF32 = 3, kU8W = 4, kU4 = 5, kU8P = 6, kF32D = 7, kU16P = 8, kF32P = 9
 };
 
 // Float window words; kinds whose staged words are the window words; kinds
 // that read a packed copy of the input made in caller scratch.
-DD_HOST_DEVICE constexpr bool float_kind(int kind) { return kind == kF32 || kind == kF32D; }
-DD_HOST_DEVICE constexpr bool packed_copy_kind(int kind) { return kind == kU8P || kind == kU16P; }
+DD_HOST_DEVICE constexpr bool float_kind(int kind) {
+  return kind == kF32 || kind == kF32D || kind == kF32P;
+}
+DD_HOST_DEVICE constexpr bool packed_copy_kind(int kind) {
+  return kind == kU8P || kind == kU16P || kind == kF32P;
+}
 DD_HOST_DEVICE constexpr bool direct_kind(int kind) {
   return packed_copy_kind(kind) || kind == kF32D;
 }
@@ -49,17 +55,29 @@ constexpr int kPair = 32 * kH;       // uint8: word u packs samples u and u + kP
 // positions plus the p / 160 padding, rounded up.
 DD_HOST_DEVICE constexpr int flush_words(int kind) { return kind == 1 ? 1288 : 648; }
 constexpr int kMaxWarps = 12;
-constexpr int kWaitIters = 1 << 22;  // bound on every mbarrier wait loop
+constexpr int kWaitIters = 1 << 22;  // default bound on the polls of an mbarrier wait
 constexpr int kErrTimeout = 1;       // device status bit: a bounded wait gave up
 constexpr size_t kStatusOffset = 0;  // status word at the start of the plan workspace
 constexpr size_t kStatusBytes = 256;
 
-// Samples held by one 32-bit window word: two for the packed-pair kinds.
-DD_HOST_DEVICE constexpr int samples_per_word(int kind) { return packed_pairs(kind) ? 2 : 1; }
+// Window words of two floats (samples u and u + pair), 8 bytes each.
+DD_HOST_DEVICE constexpr bool float_pairs(int kind) { return kind == kF32P; }
+// Bytes of one window word.
+DD_HOST_DEVICE constexpr int word_bytes(int kind) { return float_pairs(kind) ? 8 : 4; }
+
+// Samples held by one window word: two for the packed-pair kinds.
+DD_HOST_DEVICE constexpr int samples_per_word(int kind) {
+  return packed_pairs(kind) || float_pairs(kind) ? 2 : 1;
+}
 // Output samples per CTA tile: 32 lanes x kH words x samples per word.
 DD_HOST_DEVICE constexpr int tile_samples(int kind) { return 32 * kH * samples_per_word(kind); }
+// Bytes of one element of the rows a kind stages (kF32P: a 64-bit word of
+// its packed copy).
 DD_HOST_DEVICE constexpr int elem_bytes(int kind) {
-  return (kind == kU8 || kind == kU8W || kind == kU4) ? 1 : (kind == kU16 ? 2 : 4);
+  return (kind == kU8 || kind == kU8W || kind == kU4) ? 1
+         : kind == kU16                              ? 2
+         : kind == kF32P                             ? 8
+                                                     : 4;
 }
 // Raw samples per 16 bytes (4-bit samples: two per byte; kU8P: positions of
 // the packed copy, one 4-byte word each).
@@ -184,13 +202,16 @@ struct PatShape {
 // 32 channels per stage with loads inside the pattern blocks measured 12 %
 // faster at H = 23 than H = 19 with loads before the branch (1024-channel
 // float32 plan, 3.85 against 4.38 ms).
+// Float pairs (kF32P, 64-bit words of two floats): H = 11 words of 2
+// samples, the accumulators of 4 DMs in 88 registers.
 constexpr PatShape kPatShapes[] = {
     {23, 16, 32, true, false, 3, true},
     {23, 16, 32, true, false, 3, false},  {23, 16, 12, true, false, 3, false},
     {23, 16, 6, true, false, 3, false},   {23, 16, 32, false, false, 3, false},
     {19, 16, 32, false, false, 3, false}, {19, 16, 12, false, false, 1, false},
     {19, 16, 6, false, false, 1, false},  {19, 16, 12, false, false, 3, false},
-    {19, 16, 6, false, false, 3, false}};
+    {19, 16, 6, false, false, 3, false},  {11, 16, 24, false, false, 3, false},
+    {11, 16, 16, false, false, 3, false}, {11, 16, 8, false, false, 3, false}};
 constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
 constexpr bool pat_shapes_fit_records() {
   for (const PatShape& s : kPatShapes)
@@ -200,9 +221,10 @@ constexpr bool pat_shapes_fit_records() {
 static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its records hold");
 // The shape serves a kind: pairs take integer window words, single channels
 // float; channel classes are built from uint8 samples at bin 1.
+// Float-pair shapes (H < 15) serve kF32P only.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
   return s.pairs == !float_kind(kind) && (!s.merge || kind == kU8) &&
-         (!direct_kind(kind) || !s.dbuf);
+         (!direct_kind(kind) || !s.dbuf) && ((s.h < 15) == float_pairs(kind));
 }
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
@@ -340,6 +362,7 @@ struct TileParams {
   int32_t n_dm;
   int32_t n_blocks;
   int64_t n_out;        // output row length
+  int64_t out_stride;   // elements from output row d to row d + 1 (n_out, or negative)
   int64_t tile0;        // first time tile of the launch
   int64_t t_end;        // outputs t >= t_end are not written (<= n_out)
   int32_t lp;           // window words per staged channel
@@ -351,6 +374,8 @@ struct TileParams {
   int32_t nv;           // merged pattern tiles: window slots per round
   void* out;            // [n_dm][n_out] int32 or float32
   int32_t* err;
+  int32_t wait_iters;   // polls before a pipeline wait gives up (kWaitIters by default)
+  int32_t hold_stage;   // channel stage whose copies are never issued (timeout test; -1: none)
 };
 
 // Persistent batch execution: one work list of (job, DM block, time tile)

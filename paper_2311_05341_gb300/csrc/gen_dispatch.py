@@ -95,7 +95,13 @@ PAIR_H = (15, 17, 19, 21, 23, 25)  # window words per lane of the channel-pair p
 LOAD_AHEAD = 4
 
 
-LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32")}
+LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32"),
+        "F2": ("ld.shared.b64", ".b64")}
+# Float pairs: 64-bit window words of two floats (samples u and u + 32 H),
+# added two at a time.
+OPS_F2 = ("add.rn.f32x2", "l")
+WORD_BYTES = {"U32": 4, "F32": 4, "F2": 8}
+F2_H = (11,)  # window words per lane of the float-pair pattern tiles
 
 
 PATTERNS = 32  # 8 base increments a = 0..3 x the 8 patterns of +0/+1 on top
@@ -118,9 +124,9 @@ def pattern_load_macro(op, h, pair):
     offsets (0, o_1, o_2, o_3) touch, then DM i adds words o_i .. o_i + h
     into A[i][0 .. h).
     """
-    instr = OPS[op][0]
+    instr, cons = OPS_F2 if op == "F2" else OPS[op]
     ld, ty = LOAD[op]
-    cons = OPS[op][1]
+    wb = WORD_BYTES[op]
     tag = f"ddl{'q' if pair else op.lower()}{h}"
     nacc = PATTERN_DR * h
     win = h + max(_pattern_offsets(p)[3] for p in range(PATTERNS))
@@ -138,9 +144,9 @@ def pattern_load_macro(op, h, pair):
         lines.append(f'"{tag}_p{p}:\\n\\t"')
 
         def load(k):
-            lines.append(f'"{ld} t{k}, [%{s1}+{4 * k}];\\n\\t"')
+            lines.append(f'"{ld} t{k}, [%{s1}+{wb * k}];\\n\\t"')
             if pair:
-                lines.append(f'"{ld} u{k}, [%{s2}+{4 * k}];\\n\\t"')
+                lines.append(f'"{ld} u{k}, [%{s2}+{wb * k}];\\n\\t"')
 
         def add(i, j):
             a = i * h + j
@@ -192,6 +198,9 @@ def generate(path):
             out.append("")
     for h in PAIR_H:
         out += pattern_load_macro("U32", h, True)
+        out.append("")
+    for h in F2_H:
+        out += pattern_load_macro("F2", h, False)
         out.append("")
     text = "\n".join(out) + "\n"
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -1,5 +1,6 @@
 // pack.cu -- the packed copy of a uint8 (or 4-bit) filterbank read by the
-// kU8P pattern tiles (uint16: the copy widened to 32-bit words, kU16P): word t of channel c holds samples t and t + pair in its 16-bit halves,
+// kU8P pattern tiles (uint16: the copy widened to 32-bit words, kU16P; float32:
+// 64-bit words of two floats, kF32P): word t of channel c holds samples t and t + pair in its 16-bit halves,
 //   W[c][t] = X[c][t] | X[c][t + pair] << 16   (0 where an index reaches n_samp),
 // so the tiles stage window words without unpacking.  HBM-bound: reads the
 // input twice (the second read mostly from L2) and writes four bytes per sample.
@@ -132,6 +133,41 @@ __global__ void __launch_bounds__(256) widen16_kernel(const uint8_t* __restrict_
       *reinterpret_cast<uint4*>(dst + k) = make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
 }
 
+// float32 pairs: 64-bit word t = (X[t], X[t + pair]) as two floats (0 past
+// n_samp); out_stride counts 64-bit words.  Each thread writes 4 words.
+__global__ void __launch_bounds__(256) pack_f32_pairs_kernel(const float* __restrict__ in,
+                                                             int64_t in_stride, int64_t n_samp,
+                                                             float2* __restrict__ out,
+                                                             int64_t out_stride, int32_t pair,
+                                                             int64_t chunks_per_row,
+                                                             int32_t n_chan, int64_t t_begin,
+                                                             int64_t t_end) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c = gid / chunks_per_row;
+  const int64_t t = t_begin + (gid - c * chunks_per_row) * 4;
+  if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
+  const float* row = in + c * in_stride;
+  float2* dst = out + c * out_stride + t;
+  float a[4], b[4];
+  if (t + pair + 4 <= n_samp) {
+    // Both halves inside the row: two aligned 16-byte loads (t, pair and the
+    // row stride are multiples of 4 floats).
+    const float4 va = *reinterpret_cast<const float4*>(row + t);
+    const float4 vb = *reinterpret_cast<const float4*>(row + t + pair);
+    a[0] = va.x; a[1] = va.y; a[2] = va.z; a[3] = va.w;
+    b[0] = vb.x; b[1] = vb.y; b[2] = vb.z; b[3] = vb.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = t + k < n_samp ? row[t + k] : 0.f;
+      b[k] = t + k + pair < n_samp ? row[t + k + pair] : 0.f;
+    }
+  }
+  // t_end is a multiple of 4 words, so a thread's 4 words are all in range.
+  reinterpret_cast<float4*>(dst)[0] = make_float4(a[0], b[0], a[1], b[1]);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(a[2], b[2], a[3], b[3]);
+}
+
 }  // namespace
 
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
@@ -141,6 +177,16 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
   if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_stride < n_samp ||
       t_begin % 16 != 0 || t_begin < 0 || t_end % 4 != 0 || t_end > out_stride)
     return static_cast<int>(cudaErrorInvalidValue);
+  if (src == PackSource::kF32) {
+    const int64_t chunks = (t_end - t_begin) / 4;
+    const int64_t blocks = (chunks * n_chan + 255) / 256;
+    if (blocks > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+    pack_f32_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0,
+                            static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float*>(d_in), in_stride / 4, n_samp, static_cast<float2*>(d_out),
+        out_stride, pair, chunks, n_chan, t_begin, t_end);
+    return static_cast<int>(cudaGetLastError());
+  }
   const int64_t chunks = (t_end - t_begin + kPackPerThread - 1) / kPackPerThread;
   const int64_t threads = chunks * n_chan;
   const int64_t blocks = (threads + 255) / 256;

@@ -63,6 +63,11 @@ __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
 template <int KIND, int H>
 __device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
                                             uint32_t ix) {
+  if constexpr (float_pairs(KIND)) {
+    static_assert(H == 11, "no generated float-pair blocks for H");
+    DD_PATL_CHANNEL_F2_11(acc, win, ix);
+    return;
+  } else {
   static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pattern blocks for H");
 #define DD_PAT_CASE(HH)                                                  \
@@ -77,6 +82,7 @@ __device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32
   DD_PAT_CASE(23)
   DD_PAT_CASE(25)
 #undef DD_PAT_CASE
+  }
 }
 
 // The same with the window words already in registers R (H + 6 of them): the
@@ -141,6 +147,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
                                          int64_t tile) {
   static_assert(!PAIRS || !float_kind(KIND), "channel pairs need integer window words");
   constexpr bool kDirect = direct_kind(KIND);
+  constexpr uint32_t kWB = word_bytes(KIND);  // bytes per window word
   static_assert(!kDirect || !DBUF, "packed input stages its window words directly");
   constexpr int kPairW = 32 * H;
   constexpr int kRecBufs = 2;
@@ -220,14 +227,14 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       }
     };
     if constexpr (kDirect) issue_next(st);
-    const bool ok = mbar_wait(bar, parity);
+    const bool ok = mbar_wait(bar, parity, p.wait_iters);
     if constexpr (!kDirect) {
       if (ok) unpack();
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
           atomicOr(p.err, kErrTimeout);
           // Let the copies still in flight land before the CTA exits (bounded).
-          mbar_wait(bar, parity);
+          if (st != p.hold_stage) mbar_wait(bar, parity);
         }
         return false;
       }
@@ -241,7 +248,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     if (kDirect && !ok) {
       // nothing to add
     } else if constexpr (PAIRS) {
-      const uint32_t lane_win = smem_u32(pwb + H * l);
+      const uint32_t lane_win = smem_u32(pwb) + kWB * H * l;
       const unsigned char* ck = rec_buf(rb);
       const int n_pairs = ck[w], n_items = n_pairs + ck[kPairMaxWarps + w];
       const PairItem* items = reinterpret_cast<const PairItem*>(ck + kPairCountBytes) + w * NC;
@@ -275,11 +282,11 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       }
     } else {
       const PRec* rs = reinterpret_cast<const PRec*>(rec_buf(rb));
-      const uint32_t lane_win = smem_u32(pwb + H * l);
+      const uint32_t lane_win = smem_u32(pwb) + kWB * H * l;
 #pragma unroll 1
       for (int ch = 0; ch < nc; ++ch) {
         const uint32_t e = rs[ch].w[w];
-        pat_channel<KIND, H>(acc, lane_win + 4u * (ch * p.lp + (e & kPatOffMask)),
+        pat_channel<KIND, H>(acc, lane_win + kWB * (ch * p.lp + (e & kPatOffMask)),
                              e >> kPatOffBits);
       }
     }
@@ -292,8 +299,9 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
           atomicOr(p.err, kErrTimeout);
-          mbar_wait(bar, parity);
-          if (st + 1 < n_st) mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
+          if (st != p.hold_stage) mbar_wait(bar, parity);
+          if (st + 1 < n_st && st + 1 != p.hold_stage)
+            mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
         }
         return false;
       }
@@ -386,7 +394,7 @@ __device__ __forceinline__ bool pat_body_merge(const TileParams& p, const PSmem&
   for (int st = 0; st < n_st; ++st) {
     const uint32_t parity = st & 1;
     const int nc = min(NC, p.n_chan - st * NC);
-    const bool ok = mbar_wait(sm.bar_base, parity);
+    const bool ok = mbar_wait(sm.bar_base, parity, p.wait_iters);
     const unsigned char* ck = rec_buf(rb);
     const int n_rounds = ok ? ck[0] : 0;
     const uint16_t* wins = reinterpret_cast<const uint16_t*>(ck + kMergeWinOff);
@@ -433,7 +441,7 @@ __device__ __forceinline__ bool pat_body_merge(const TileParams& p, const PSmem&
         if (__syncthreads_or(!ok)) {
           if (tid == 0) {
             atomicOr(p.err, kErrTimeout);
-            mbar_wait(sm.bar_base, parity);
+            if (st != p.hold_stage) mbar_wait(sm.bar_base, parity);
           }
           return false;
         }

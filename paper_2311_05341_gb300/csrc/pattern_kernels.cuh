@@ -1,0 +1,178 @@
+// pattern_kernels.cuh -- the pattern-tile kernels (pattern_body.cuh) and their
+// launch templates: the one-unit-per-CTA kernel of dd_run and the persistent
+// kernel of dd_batch_run, for every tk::kPatShapes entry that serves a kind.
+// Included only by the per-kind translation units fwd_pattern_k*.cu, each of
+// which defines the launchers of its kind with DD_PATTERN_KIND, so that the
+// kinds compile in parallel; fwd_pattern.cu and fwd_pattern_batch.cu
+// dispatch on the kind.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <iterator>
+#include <utility>
+
+#include "dd_internal.h"
+#include "pattern_body.cuh"
+
+namespace dd {
+namespace tk {
+
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
+__global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using namespace pattern;
+  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF, MERGE>(smem, p.lraw);
+  if (threadIdx.x == 0) {
+    mbar_init(sm.bar_base, NC + 1);
+    mbar_init(sm.bar_base + 8, NC + 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int blk = blockIdx.x % p.n_blocks;
+  const int64_t tile = blockIdx.x / p.n_blocks + p.tile0;
+  if constexpr (MERGE) pat_body_merge<H, NW, NC, AMAX>(p, sm, blk, tile);
+  else pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blk, tile);
+}
+
+}  // namespace tk
+
+namespace pattern_launch {
+
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
+int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  const size_t smem = tk::pat_smem_bytes(
+      KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX, MERGE}, prm.lp, prm.nv);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX, MERGE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<static_cast<unsigned>(grid), NW * 32, smem, st>>>(prm);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <int KIND, int I>
+int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  constexpr tk::PatShape s = tk::kPatShapes[I];
+  if constexpr (!tk::pat_shape_serves(s, KIND)) {
+    return static_cast<int>(cudaErrorInvalidValue);  // the planner never picks it
+  } else {
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax, s.merge>(
+        prm, grid, st);
+  }
+}
+
+template <int KIND, size_t... I>
+int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cudaStream_t st,
+                        std::index_sequence<I...>) {
+  int rc = static_cast<int>(cudaErrorInvalidValue);
+  ((shape == static_cast<int>(I) ? (rc = launch_pattern_index<KIND, I>(prm, grid, st), 0) : 0),
+   ...);
+  return rc;
+}
+
+template <int KIND>
+int launch_pattern_kind(int shape, const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  return launch_pattern_kind<KIND>(
+      shape, prm, grid, st, std::make_index_sequence<std::size(tk::kPatShapes)>{});
+}
+
+}  // namespace pattern_launch
+
+namespace tk {
+
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent kernel of one variant (KIND, kPatShapes[I]): the jobs of a batch
+// are grouped by variant and each group is one launch, so every launch has
+// the register allocation of its own variant.
+template <int KIND, int I>
+__global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
+    fwd_pattern_batch_kernel(const PatBatchArgs b) {
+  constexpr PatShape s = kPatShapes[I];
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int item_slot;
+  bool barriers_valid = false;
+  for (;;) {
+    if (threadIdx.x == 0) item_slot = static_cast<int>(atomicAdd(b.counter, 1u));
+    __syncthreads();
+    const int it = item_slot;
+    if (it >= b.n_items) break;
+    const BatchItem item = b.items[it];
+    // The job's parameters stay in global memory (read-only for the launch):
+    // a copy in registers would crowd out the accumulators.
+    const TileParams& p = static_cast<const PatBatchJob* __restrict__>(b.jobs)[item.job].p;
+    const pattern::PSmem sm =
+        pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf, s.merge>(smem, p.lraw);
+    __syncthreads();  // every thread has read item_slot; the previous item is done
+    if (threadIdx.x == 0) {
+      // Stage phases restart at 0 for every item: re-initialise the barriers
+      // (all copies of the previous item have landed and been waited for).
+      if (barriers_valid) {
+        mbar_inval(sm.bar_base);
+        mbar_inval(sm.bar_base + 8);
+      }
+      mbar_init(sm.bar_base, s.nc + 1);
+      mbar_init(sm.bar_base + 8, s.nc + 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    barriers_valid = true;
+    __syncthreads();
+    bool ok;
+    if constexpr (s.merge)
+      ok = pattern::pat_body_merge<s.h, s.warps, s.nc, s.amax>(p, sm, item.blk, item.tile);
+    else
+      ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(p, sm, item.blk,
+                                                                               item.tile);
+    if (!ok) break;
+  }
+}
+
+}  // namespace tk
+
+namespace pattern_launch {
+
+template <int KIND, int I>
+int launch_variant(const tk::PatBatchArgs& args, int32_t grid, size_t smem, cudaStream_t st) {
+  if constexpr (!tk::pat_shape_serves(tk::kPatShapes[I], KIND)) {
+    return static_cast<int>(cudaErrorInvalidValue);  // never grouped by the host
+  } else {
+    auto kern = tk::fwd_pattern_batch_kernel<KIND, I>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return static_cast<int>(e);
+    kern<<<grid, tk::kPatShapes[I].warps * 32, smem, st>>>(args);
+    return static_cast<int>(cudaGetLastError());
+  }
+}
+
+template <int KIND, size_t... I>
+int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem,
+                cudaStream_t st, std::index_sequence<I...>) {
+  int rc = static_cast<int>(cudaErrorInvalidValue);
+  ((shape == static_cast<int>(I) ? (rc = launch_variant<KIND, I>(args, grid, smem, st), 0) : 0),
+   ...);
+  return rc;
+}
+
+}  // namespace pattern_launch
+
+}  // namespace dd
+
+// The launchers of one kind (declared in dd_internal.h).
+#define DD_PATTERN_KIND(K)                                                                  \
+  namespace dd {                                                                            \
+  int pattern_forward_##K(int shape, const tk::TileParams& prm, int64_t grid, void* st) {   \
+    return pattern_launch::launch_pattern_kind<tk::K>(shape, prm, grid,                    \
+                                                      static_cast<cudaStream_t>(st));       \
+  }                                                                                         \
+  int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem, \
+                        void* st) {                                                         \
+    return pattern_launch::launch_kind<tk::K>(                                              \
+        shape, args, grid, smem, static_cast<cudaStream_t>(st),                             \
+        std::make_index_sequence<tk::kNumPatShapes>{});                                     \
+  }                                                                                         \
+  }

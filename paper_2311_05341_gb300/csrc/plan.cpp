@@ -397,6 +397,9 @@ bool build_merge_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk:
 bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift) {
   int32_t s = 0;
   while ((2u << s) <= d) ++s;  // s = floor(log2(d))
+  // One lower first: a power of two d = 2^s needs m = 2^31 at shift s - 1
+  // (2^32 at shift s does not fit 32 bits).  Every candidate is verified.
+  if (s > 0) --s;
   for (; s < 32; ++s) {
     const uint64_t m = ((uint64_t{1} << (32 + s)) + d - 1) / d;
     if (m > 0xffffffffull) break;
@@ -517,8 +520,11 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   // Packed input at bin 1: uint8 and 4-bit share the paired word format,
   // uint16 is widened to one sample per word.
   const bool packed = rp.tile_request == DD_TILE_PACKED &&
-                      (dtype == DD_U8 || dtype == DD_U4 || dtype == DD_U16) && rp.r.bin == 1;
-  const int kind = packed                             ? (dtype == DD_U16 ? tk::kU16P : tk::kU8P)
+                      (dtype == DD_U8 || dtype == DD_U4 || dtype == DD_U16 || dtype == DD_F32) &&
+                      rp.r.bin == 1;
+  const int kind = packed ? (dtype == DD_U16   ? tk::kU16P
+                             : dtype == DD_F32 ? tk::kF32P
+                                               : tk::kU8P)
                    : dtype == DD_U4                   ? tk::kU4
                    : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
                                                       : static_cast<int>(dtype);
@@ -578,7 +584,10 @@ void build_adjoint_range(const RangePlan& rp, int32_t n_chan, RangePlan* ar) {
   }
   ar->s_max = smax;
   if (n_dm > (int64_t{1} << 20)) return;
-  for (int kind : {static_cast<int>(tk::kF32D), static_cast<int>(tk::kF32)})
+  // Float pairs first (two adds per instruction; the adjoint packs its padded
+  // cotangent rows into pairs anyway), then plain floats.
+  for (int kind : {static_cast<int>(tk::kF32P), static_cast<int>(tk::kF32D),
+                   static_cast<int>(tk::kF32)})
     for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
       if (!tk::kPatShapes[i].merge &&
           try_pattern_shape(*ar, static_cast<int32_t>(n_dm), kind, i))

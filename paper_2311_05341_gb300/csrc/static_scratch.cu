@@ -29,6 +29,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
+// Device address of the array per device, looked up once with that device
+// current and kept for the life of the process (a cudaDeviceReset between
+// calls would leave it stale; that is documented as unsupported).
 void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -86,9 +89,11 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
   if (st != DD_OK) return st;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The status word is zero when the library loads; kernels only set bits in
+  // it and dd_run_u8_noalloc_status clears it, so it collects every call's
+  // timeouts until it is read.
   int32_t* err = reinterpret_cast<int32_t*>(scratch + tk::kStatusOffset);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, tk::kStatusBytes, s);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc: clear status");
+  cudaError_t e = cudaSuccess;
   size_t off = tk::kStatusBytes;
   int64_t out_off = 0;
   for (const RangePlan& rp : plan->ranges) {
@@ -105,4 +110,26 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
     out_off += rp.n_dm * n_out;
   }
   return DD_OK;
+}
+
+extern "C" dd_status dd_run_u8_noalloc_status(void* stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc_status: cudaGetDevice");
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (dev >= 0 && dev < kMaxDevices) scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  }
+  if (!scratch) return DD_OK;  // no call has run on this device
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t word = 0;
+  e = cudaMemcpyAsync(&word, scratch + tk::kStatusOffset, sizeof(word), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc_status: read status");
+  if (word == 0) return DD_OK;
+  e = cudaMemsetAsync(scratch + tk::kStatusOffset, 0, sizeof(word), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run_u8_noalloc_status: clear status");
+  return fail(DD_ERR_TIMEOUT, "a bounded device wait of an earlier dd_run_u8_noalloc call gave up");
 }

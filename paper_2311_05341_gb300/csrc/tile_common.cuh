@@ -35,9 +35,12 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitIters; ++it) {
+// Bounded wait for phase `parity` of an mbarrier: at most `limit` polls.
+// Returns false on timeout.  Pipeline waits take the plan's bound
+// (TileParams::wait_iters); the waits that let issued copies land before a
+// timed-out CTA exits keep the default.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = kWaitIters) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -51,9 +54,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// Accumulator (window word) and output element of a kind.
+// Accumulator (window word) and output element of a kind.  Float pairs keep
+// two float accumulators (samples u and u + 32 H) in one 64-bit register pair.
 template <int KIND>
-using AccT = std::conditional_t<float_kind(KIND), float, uint32_t>;
+using AccT = std::conditional_t<float_pairs(KIND), unsigned long long,
+                                std::conditional_t<float_kind(KIND), float, uint32_t>>;
 template <int KIND>
 using OutT = std::conditional_t<float_kind(KIND), float, int32_t>;
 
@@ -185,12 +190,15 @@ __device__ __forceinline__ uint4 unpack_unit(const uint8_t* raw_ch, int q, int b
 // bar_base + 8 buf).  Threads 0..NC-1 copy one channel's raw window each: it
 // starts at the 16-byte aligned decimated sample at or before t0 + base and is
 // clipped at the end of the row.  Thread NC copies rec_bytes of the stage's
-// records from rec_src to rec_dst.
+// records from rec_src to rec_dst.  Nothing is issued (and nobody arrives)
+// for the stage p.hold_stage, so the wait on it runs out: the hook that tests
+// the timeout path.
 template <int KIND, int NC>
 __device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_base, uint8_t* raw,
                                             int st, int buf, int64_t t0, int32_t base, int tid,
                                             const void* rec_src, uint32_t rec_bytes,
                                             void* rec_dst) {
+  if (st == p.hold_stage) return;
   const uint32_t bar = bar_base + 8u * buf;
   if (tid < NC) {
     const int c = st * NC + tid;
@@ -269,10 +277,11 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
                                             bool first) {
   using ST = StoreTile<KIND, H>;
   constexpr int kFw = ST::kWords;
+  constexpr int kWw = word_bytes(KIND) / 4;  // 32-bit words per window word
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-  // Window buffers hold at least 32 H + 16 words per channel.
-  constexpr bool kAllFit = NC * (32 * H + 16) >= NW * kFw;
-  const int fit = (NC * p.lp) / kFw;  // tiles that fit the window buffer
+  // Window buffers hold at least 32 H + 16 window words per channel.
+  constexpr bool kAllFit = NC * (32 * H + 16) * kWw >= NW * kFw;
+  const int fit = (NC * p.lp * kWw) / kFw;  // tiles that fit the window buffer
   const int groups = kAllFit ? 1 : (NW + fit - 1) / fit;
   uint32_t* tr = pw + (w / groups) * kFw;
   const int wbase = H * l + (ST::kPad ? (l >> 3) : 0);
@@ -290,7 +299,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
         // word whole (position p and p + 32H in its halves) and lane l takes
         // words 64 m + 2 l and + 1, i.e. output pairs (p, p + 1) and
         // (p + 32H, p + 32H + 1): one 64-bit store or reduction each.
-        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.out_stride + t0;
         if ((reinterpret_cast<uintptr_t>(row) & 7u) == 0) {
 #pragma unroll
           for (int j = 0; j < H; ++j) {
@@ -328,6 +337,11 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
           tr[wbase + j] = v & 0xffffu;
           tr[wbase + j + kHiOff] = v >> 16;
           acc[i][j] = 0u;
+        } else if constexpr (float_pairs(KIND)) {
+          // Low float: position H l + j; high float: that + 32 H.
+          tr[wbase + j] = static_cast<uint32_t>(acc[i][j]);
+          tr[wbase + j + kHiOff] = static_cast<uint32_t>(acc[i][j] >> 32);
+          acc[i][j] = 0ull;
         } else if constexpr (KIND == kU16 || KIND == kU8W || KIND == kU16P) {
           tr[wbase + j] = acc[i][j];
           acc[i][j] = 0u;
@@ -342,7 +356,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
         // Later widenings of integer sums (non-negative) with the row 8-byte
         // aligned: lane l adds positions 64 m + 2 l and + 1 in one 64-bit
         // reduction (the tile holds position p at index p).
-        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.out_stride + t0;
         if (!first && d < p.n_dm && (reinterpret_cast<uintptr_t>(row) & 7u) == 0) {
           constexpr int kPos = 32 * ST::kRows;
 #pragma unroll
@@ -357,7 +371,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
         }
       }
       if (d < p.n_dm && !paired) {
-        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.n_out + t0;
+        OutT<KIND>* row = static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.out_stride + t0;
         constexpr int kCh = (ST::kRows + 1) / 2;  // rows per half
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

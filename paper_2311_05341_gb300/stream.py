@@ -2,18 +2,23 @@
 
 Each admitted beam keeps a device window of `overlap + chunk` raw samples per
 channel.  A new chunk is copied into the window behind the overlap (the last
-`overlap` samples of the previous step, kept on the device), the window is
-dedispersed with dd_run, and the window's tail becomes the next overlap.  With
-overlap >= max_r bin_r * S_max_r every step emits the next `chunk / bin_r`
-output samples of every DM range, equal to the same samples of a one-shot
+`overlap` samples of the previous step, kept on the device), and the window is
+dedispersed with dd_run_window for the first `chunk / bin_r` outputs of every
+DM range r only: with overlap >= max_r bin_r * S_max_r those are the next
+`chunk / bin_r` outputs of the stream, equal to the same samples of a one-shot
 transform of the concatenated stream (the paper's real-time processing,
-Sec. 5.4, done incrementally).
+Sec. 5.4, done incrementally), and no output is computed twice.  The window's
+tail becomes the next overlap.  Ranges that the packed-input tile serves run
+on it, from a per-beam packed copy of the window in scratch that the budget
+counts.
 
 Serving is continuous batching: each beam has its own CUDA stream, chunks are
 launched as soon as they arrive, so work of different beams overlaps on the
-device; beams are admitted while their device memory (window, output planes)
-fits an HBM budget and wait otherwise until another beam leaves.  Latency is
-measured from a chunk's arrival to its outputs being ready on the device.
+device; beams are admitted while their device memory (window, packed copy,
+output planes) fits an HBM budget and wait otherwise until another beam
+leaves.  Latency is measured from a chunk's arrival to its outputs being ready
+on the device.  snapshot() / restore() carry a beam's stream state (its
+overlap and position) across a server restart.
 """
 from __future__ import annotations
 
@@ -23,7 +28,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Plan
+from . import DDError, Plan
 
 
 def _torch():
@@ -47,8 +52,9 @@ class _Beam:
     spec: StreamSpec
     plan: Plan
     window: object          # device [n_chan][overlap + chunk]
-    out: object             # device flat output of one window
+    out: object             # device: per range [n_dm_r][chunk / bin_r], concatenated
     stream: object          # torch.cuda.Stream
+    scratch: object = None  # device packed copy of the window (packed-tile ranges)
     n_chunks: int = 0
     kept: list = field(default_factory=list)  # host copies of kept outputs per chunk
     bytes: int = 0
@@ -77,13 +83,16 @@ class StreamServer:
     """Admits beams under an HBM budget and dedisperses their chunks as they arrive."""
 
     def __init__(self, chunk: int, hbm_budget_bytes: int, device="cuda", keep_outputs=False,
-                 plan_cache: dict | None = None):
+                 plan_cache: dict | None = None, packed: bool = True):
+        """chunk: raw samples per chunk (a multiple of 16 and of every range's
+        bin); packed: run the ranges the packed-input tile serves on it."""
         torch = _torch()
         self.device = torch.device(device)
         self.chunk = int(chunk)
         self.budget = int(hbm_budget_bytes)
         self.used = 0
         self.keep_outputs = keep_outputs
+        self.packed = packed
         self.beams: dict[int, _Beam] = {}
         self.waiting: collections.deque = collections.deque()  # (beam_id, spec) not yet admitted
         self.queue: collections.deque = collections.deque()    # jobs of admitted beams
@@ -96,18 +105,38 @@ class StreamServer:
     # -- admission ---------------------------------------------------------
     def _plan(self, spec: StreamSpec) -> Plan:
         key = (spec.freqs.tobytes(), spec.f_ref, spec.t_samp, tuple(map(tuple, spec.ranges)),
-               spec.dtype)
+               spec.dtype, self.packed)
         if key not in self.plan_cache:
-            self.plan_cache[key] = Plan(spec.freqs, spec.f_ref, spec.t_samp, spec.ranges,
-                                        spec.dtype, device=self.device)
+            plan = Plan(spec.freqs, spec.f_ref, spec.t_samp, spec.ranges, spec.dtype,
+                        device=self.device)
+            if self.packed:
+                for r in range(len(spec.ranges)):
+                    try:
+                        plan.set_tile(r, "packed")
+                    except DDError:
+                        pass  # this range stays on the plan's automatic tile
+            self.plan_cache[key] = plan
         return self.plan_cache[key]
 
-    def beam_bytes(self, spec: StreamSpec) -> int:
+    def keep_counts(self, spec: StreamSpec) -> list:
+        """New outputs per range per chunk: chunk / bin_r."""
+        for r in spec.ranges:
+            if self.chunk % int(r[3]):
+                raise ValueError("the chunk must be a multiple of every range's bin")
+        return [self.chunk // int(r[3]) for r in spec.ranges]
+
+    def _sizes(self, spec: StreamSpec):
         plan = self._plan(spec)
         ov = overlap_for(plan, spec.ranges)
         n = ov + self.chunk
+        out_elems = sum(a * b for a, b in zip(plan.info(0)["n_dm"], self.keep_counts(spec)))
+        return plan, ov, n, out_elems, plan.input_scratch_bytes(n)
+
+    def beam_bytes(self, spec: StreamSpec) -> int:
+        """Device bytes of one admitted beam: window, packed copy, outputs."""
+        plan, ov, n, out_elems, scratch = self._sizes(spec)
         in_bytes = (n + 1) // 2 if spec.dtype == "u4" else n * {"u8": 1, "u16": 2, "f32": 4}[spec.dtype]
-        return len(spec.freqs) * in_bytes + plan.info(n)["out_elems"] * 4
+        return len(spec.freqs) * in_bytes + out_elems * 4 + scratch
 
     def request(self, beam_id: int, spec: StreamSpec) -> bool:
         """Admit a beam now if its memory fits the budget, else queue it."""
@@ -126,13 +155,12 @@ class StreamServer:
     def _admit(self, beam_id: int, spec: StreamSpec, need: int):
         torch = _torch()
         from .batch import input_buffer
-        plan = self._plan(spec)
-        ov = overlap_for(plan, spec.ranges)
-        n = ov + self.chunk
+        plan, ov, n, out_elems, scratch = self._sizes(spec)
         window = input_buffer(spec.dtype, len(spec.freqs), n, self.device)
-        out = plan.empty_output(n, self.device)
+        out = torch.empty(max(out_elems, 4), dtype=plan.out_dtype(), device=self.device)
+        sc = torch.empty(scratch, dtype=torch.uint8, device=self.device) if scratch else None
         self.beams[beam_id] = _Beam(spec, plan, window, out, torch.cuda.Stream(self.device),
-                                    bytes=need)
+                                    scratch=sc, bytes=need)
         self.used += need
 
     def release(self, beam_id: int):
@@ -168,9 +196,10 @@ class StreamServer:
         spe = 2 if beam.spec.dtype == "u4" else 1
         with torch.cuda.stream(beam.stream):
             beam.window[:, ov // spe:n // spe].copy_(job.chunk, non_blocking=True)
-            plan.run(beam.window, out=beam.out, n_samp=n, stream=beam.stream)
+            plan.run_window(beam.window, self.keep_counts(beam.spec), out=beam.out, n_samp=n,
+                            stream=beam.stream, scratch=beam.scratch)
             if self.keep_outputs:
-                beam.kept.append(self._kept(beam, n, ov))
+                beam.kept.append(self._kept(beam, ov))
             # The tail of this window is the next step's overlap.
             tail = beam.window[:, self.chunk // spe:n // spe]
             beam.window[:, :ov // spe].copy_(tail.clone() if ov > self.chunk else tail)
@@ -180,15 +209,54 @@ class StreamServer:
         beam.n_chunks += 1
         self.inflight.append(job)
 
-    def _kept(self, beam: _Beam, n: int, ov: int):
-        """Host copies of this step's new outputs: chunk / bin samples per range."""
-        planes = beam.plan.split(beam.out, n)
+    def planes(self, beam: _Beam):
+        """Views of a beam's last window outputs: per range [n_dm_r][chunk / bin_r]."""
+        n_dm = beam.plan.info(0)["n_dm"]
+        out, off = [], 0
+        for a, b in zip(n_dm, self.keep_counts(beam.spec)):
+            out.append(beam.out[off:off + a * b].view(a, b))
+            off += a * b
+        return out
+
+    def _kept(self, beam: _Beam, ov: int):
+        """Host copies of this step's new outputs: chunk / bin samples per range.
+        Output t of the k-th window is decimated sample (k chunk - ov) / bin + t
+        of the stream; those before the stream's start read the zeroed overlap
+        and are dropped."""
         kept = []
-        for (lo, hi, step, b), p in zip(beam.spec.ranges, planes):
-            first = beam.n_chunks == 0
-            start = ov // b if first else 0
-            kept.append(p[:, start:self.chunk // b].cpu())
+        for (lo, hi, step, b), p in zip(beam.spec.ranges, self.planes(beam)):
+            start = max(0, (ov - beam.n_chunks * self.chunk) // b)
+            kept.append(p[:, start:].cpu())
         return kept
+
+    # -- checkpoint / resume -------------------------------------------------
+    def snapshot(self, beam_id: int) -> dict:
+        """State of an admitted beam between chunks, on the host: its spec, the
+        overlap samples of its window and the number of chunks done.  A server
+        that restores it continues the stream exactly where this one stopped."""
+        beam = self.beams[beam_id]
+        beam.stream.synchronize()
+        ov = overlap_for(beam.plan, beam.spec.ranges)
+        spe = 2 if beam.spec.dtype == "u4" else 1
+        return {"spec": beam.spec, "chunk": self.chunk, "n_chunks": beam.n_chunks,
+                "overlap": beam.window[:, :ov // spe].cpu()}
+
+    def restore(self, beam_id: int, state: dict) -> bool:
+        """Admit a beam from snapshot() state (same chunk size); False if the
+        budget does not admit it now (then it is not queued)."""
+        if state["chunk"] != self.chunk:
+            raise ValueError("snapshot taken with another chunk size")
+        spec = state["spec"]
+        need = self.beam_bytes(spec)
+        if beam_id in self.beams or self.used + need > self.budget:
+            return False
+        self._admit(beam_id, spec, need)
+        beam = self.beams[beam_id]
+        ov = overlap_for(beam.plan, spec.ranges)
+        spe = 2 if spec.dtype == "u4" else 1
+        beam.window[:, :ov // spe].copy_(state["overlap"].to(self.device))
+        beam.n_chunks = int(state["n_chunks"])
+        return True
 
     def pump(self, block: bool = False):
         """Launch queued chunks of admitted beams; retire finished ones."""
@@ -215,8 +283,15 @@ class StreamServer:
                 now_list.append(job)
         self.inflight = now_list
 
+    def has_work(self, beam_id: int) -> bool:
+        """A chunk of the beam is queued or on the device."""
+        return any(j.beam == beam_id for j in self.queue) or any(
+            j.beam == beam_id for j in self.inflight)
+
     def drain(self):
-        while self.queue or self.inflight:
+        """Run every queued chunk of admitted beams to completion (chunks of
+        beams still waiting for admission stay queued)."""
+        while self.inflight or any(j.beam in self.beams for j in self.queue):
             self.pump(block=True)
 
     def stats(self) -> dict:

@@ -6,6 +6,8 @@ CTA tiles, ragged tails, odd channel counts, bins, several ranges); the
 paper-scale workloads compare sampled rows and windows plus properties that
 hold at any size.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -137,7 +139,8 @@ def test_tiled_full_planes_every_shape(dtype, seed):
     # Steps of at most 1.7 samples keep every per-DM increment in {0, 1, 2}:
     # the pattern tile serves all these plans too (uint8: also with channel
     # classes).
-    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge", "packed") if dtype == "u8" else ())
+    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge", "packed") if dtype == "u8" else
+                                           ("packed",) if dtype == "f32" else ())
     for dms in tiles:
         plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
@@ -172,7 +175,8 @@ def test_pattern_steep_plans(dtype, seed):
     ref = oracle.forward(x, freqs, f_high, 64e-6, [r])[0]
     ref_abs = oracle.forward(x, freqs, f_high, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
-    for tile in ("pattern", 1) + (("merge", "packed") if dtype == "u8" else ()):
+    for tile in ("pattern", 1) + (("merge", "packed") if dtype == "u8" else
+                                  ("packed",) if dtype == "f32" else ()):
         plan = dd.Plan(freqs, f_high, 64e-6, [r], dtype)
         plan.set_tile(0, tile)
         got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
@@ -267,21 +271,39 @@ def test_too_short_input_raises():
     assert ei.value.status == 3  # DD_ERR_SHAPE
 
 
-def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows, rng):
+# Oracle rows of the paper-scale workloads, computed once per workload and
+# shared by the tile variants that run the same input.
+_PAPER_REF = {}
+
+
+def _paper_reference(beam, x, n_dm, n_out, pulse_rows):
+    """Every 16th DM row (plus the last and the pulse rows) at full length, and
+    96 random rows on three windows (the first, a random and the ragged last
+    tile), from the oracle."""
+    if beam.name not in _PAPER_REF:
+        r = 0
+        rows_full = sorted(set(range(0, n_dm[r], 16)) | {n_dm[r] - 1} | set(pulse_rows))
+        full = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[r],
+                                   rows_full)
+        rng = np.random.default_rng(9)
+        rows = rng.integers(0, n_dm[r], 96)
+        wins = []
+        for t_lo in [0, int(rng.integers(0, n_out[r] - 2048)), n_out[r] - 1500]:
+            t_hi = min(t_lo + 2048, n_out[r])
+            wins.append((t_lo, t_hi, oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp,
+                                                         beam.ranges[r], rows, t_lo, t_hi)))
+        _PAPER_REF.clear()  # one workload's rows at a time (host memory)
+        _PAPER_REF[beam.name] = (rows_full, full, rows, wins)
+    return _PAPER_REF[beam.name]
+
+
+def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows):
     """Compare sampled full rows and windows of a large plane with the oracle."""
-    r = 0
-    rows_full = sorted(set(list(range(0, n_dm[r], 256)) + [n_dm[r] - 1] + pulse_rows))
-    got = planes_gpu[r][torch.tensor(rows_full, device="cuda")].cpu().numpy()
-    ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[r],
-                              rows_full)
-    np.testing.assert_array_equal(got, ref)
-    # Random rows on windows (including the ragged last tile).
-    rows = rng.integers(0, n_dm[r], 96)
-    for t_lo in [0, int(rng.integers(0, n_out[r] - 2048)), n_out[r] - 1500]:
-        t_hi = min(t_lo + 2048, n_out[r])
-        g = planes_gpu[r][torch.tensor(rows, device="cuda"), t_lo:t_hi].cpu().numpy()
-        o = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[r], rows,
-                                t_lo, t_hi)
+    rows_full, full, rows, wins = _paper_reference(beam, x, n_dm, n_out, pulse_rows)
+    got = planes_gpu[0][torch.tensor(rows_full, device="cuda")].cpu().numpy()
+    np.testing.assert_array_equal(got, full)
+    for t_lo, t_hi, o in wins:
+        g = planes_gpu[0][torch.tensor(rows, device="cuda"), t_lo:t_hi].cpu().numpy()
         np.testing.assert_array_equal(g, o)
 
 
@@ -301,8 +323,7 @@ def test_paper_scale_sampled(make, tile):
     torch.cuda.synchronize()
     assert planes[0].shape == (n_dm[0], n_out[0])
     pulses = workloads.resolve_pulses(beam, n_dm, n_out)
-    _sampled_parity(beam, x, planes, n_dm, n_out, [p[1] for p in pulses],
-                    np.random.default_rng(9))
+    _sampled_parity(beam, x, planes, n_dm, n_out, [p[1] for p in pulses])
     # DM 0 is the plain channel sum at any size.
     dm0 = xt.to(torch.int64).sum(0)[: n_out[0]].to(torch.int32)
     assert torch.equal(planes[0][0], dm0)
@@ -311,3 +332,29 @@ def test_paper_scale_sampled(make, tile):
         lo, hi = max(d - 20, 0), min(d + 21, n_dm[0])
         seg = planes[0][lo:hi, t0:t0 + w].to(torch.int64).sum(1)
         assert int(torch.argmax(seg)) + lo == d
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("DD_FULL_PLANE") != "1",
+                    reason="the full paper-scale comparison takes minutes of oracle time; "
+                           "set DD_FULL_PLANE=1 to run it")
+def test_paper_u8_full_plane():
+    """Every output of the paper-scale uint8 plane (4096 x 257097) against the
+    oracle, on the automatic tile and on the packed tile the benchmark runs."""
+    beam = workloads.paper_u8()
+    x, _, n_dm, n_out = oracle_input(beam)
+    xt = torch.from_numpy(x).cuda()
+    plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
+    auto = plan.run(xt)[0]
+    plan.set_tile(0, "packed")
+    packed = plan.run(xt)[0]
+    torch.cuda.synchronize()
+    assert auto.shape == (n_dm[0], n_out[0]) == packed.shape
+    block = 256
+    for d0 in range(0, n_dm[0], block):
+        rows = list(range(d0, min(d0 + block, n_dm[0])))
+        ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
+        np.testing.assert_array_equal(auto[d0:d0 + len(rows)].cpu().numpy(), ref,
+                                      err_msg=f"automatic tile, rows {d0}..")
+        np.testing.assert_array_equal(packed[d0:d0 + len(rows)].cpu().numpy(), ref,
+                                      err_msg=f"packed tile, rows {d0}..")

@@ -156,3 +156,41 @@ def test_packed_uint16(seed):
     torch.cuda.synchronize()
     for r, (g, o) in enumerate(zip(plan.split(h_out, n_samp), ref)):
         np.testing.assert_array_equal(g.numpy(), o, err_msg=f"host range {r}")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_packed_float32(seed):
+    """float32 through the packed tile (64-bit words of two floats, added two
+    at a time with add.f32x2), beside a binned range, on the device and
+    through the host pipeline, against the FP64 oracle within 1e-5 sum |X|."""
+    from gpu_util import assert_float_parity
+    rng = np.random.default_rng(5600 + seed)
+    n_chan = int(rng.choice([1, 33, 257, 300]))
+    f_high = float(rng.uniform(900, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / 64e-6
+    step = float(rng.uniform(0.2, 2.9)) / k_low
+    n_dm = int(rng.choice([7, 64, 130]))
+    ranges = [(0.0, n_dm * step, step, 1), (n_dm * step, 2 * n_dm * step, 2 * step, 2)]
+    s_max = max((oracle.extent(freqs, f_high, 64e-6, r, 10 ** 9)[0] + 1) * r[3] for r in ranges)
+    n_samp = int(s_max + rng.choice([1, 703, 704, 705, 30001]))
+    stride = (n_samp + 3) // 4 * 4
+    x = filterbank(np.float32, n_chan, n_samp, 5700 + seed, 0.0, 1.0, row_stride=stride)
+    x[:, n_samp:] = 1e30  # padding the transform must not read
+    xs = np.ascontiguousarray(x[:, :n_samp])
+    ref = oracle.forward(xs, freqs, f_high, 64e-6, ranges)
+    ref_abs = oracle.forward(xs, freqs, f_high, 64e-6, ranges, take_abs=True)
+    plan = dd.Plan(freqs, f_high, 64e-6, ranges, "f32")
+    plan.set_tile(0, "packed")
+    info = plan.info(n_samp)
+    assert info["tile_dms"][0] == _lib.DD_TILE_PACKED
+    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
+    for r, (g, o, a) in enumerate(zip(got, ref, ref_abs)):
+        assert_float_parity(g.cpu().numpy(), o, a, f"range {r}")
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.full((info["out_elems"],), -5.0, dtype=torch.float32).pin_memory()
+    plan.run_host(h_in, h_out, torch.empty_like(h_in, device="cuda"), plan.empty_output(n_samp),
+                  n_samp=n_samp)
+    torch.cuda.synchronize()
+    for r, (g, o, a) in enumerate(zip(plan.split(h_out, n_samp), ref, ref_abs)):
+        assert_float_parity(g.numpy(), o, a, f"host range {r}")

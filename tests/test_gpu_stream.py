@@ -132,3 +132,53 @@ def test_chunked_4bit_equals_one_shot():
     o = oracle.forward_rows(oracle.Packed4(x, CHUNK * N_CHUNKS), spec.freqs, spec.f_ref,
                             spec.t_samp, RANGES[0], rows, 0, got[0].shape[1])
     np.testing.assert_array_equal(got[0][rows], o)
+
+
+def test_snapshot_restore_equals_uninterrupted():
+    """A beam checkpointed between chunks and resumed on a new server gives the
+    same outputs as the uninterrupted stream (and the one-shot transform)."""
+    spec = _spec(192)
+    x = _stream_data(650, 192)
+    chunks = _chunks(x)
+    whole, _ = _run_server({0: (spec, chunks)}, 1 << 34, [0] * N_CHUNKS)
+    first = dds.StreamServer(CHUNK, 1 << 34, keep_outputs=True)
+    assert first.request(0, spec)
+    for k in range(2):
+        first.submit(0, chunks[k])
+    first.drain()
+    state = first.snapshot(0)
+    part1 = first.outputs(first.release(0))
+    second = dds.StreamServer(CHUNK, 1 << 34, keep_outputs=True)
+    assert second.restore(0, state)
+    for k in range(2, N_CHUNKS):
+        second.submit(0, chunks[k])
+    second.drain()
+    part2 = second.outputs(second.beams[0])
+    for r in range(len(RANGES)):
+        resumed = np.concatenate([part1[r], part2[r]], axis=1)
+        np.testing.assert_array_equal(resumed, whole[0][r], err_msg=f"range {r}")
+    ref, _ = _one_shot(spec, x)
+    for r, (g, o) in enumerate(zip(whole[0], ref)):
+        np.testing.assert_array_equal(g, o[:, : g.shape[1]], err_msg=f"range {r}")
+
+
+def test_window_outputs_equal_full_run():
+    """dd_run_window's first n_keep outputs of every range equal dd_run's (the
+    packed tile and the plain tiles alike)."""
+    spec = _spec(256)
+    x = _stream_data(660)
+    n = x.shape[1]
+    for packed in (False, True):
+        plan = dd.Plan(spec.freqs, spec.f_ref, spec.t_samp, spec.ranges, "u8")
+        if packed:
+            plan.set_tile(0, "packed")
+        xd = torch.from_numpy(x).cuda()
+        full = [p.cpu().numpy() for p in plan.run(xd)]
+        keep = [max(1, f.shape[1] // 3 + 5 * r) for r, f in enumerate(full)]
+        win = [p.cpu().numpy() for p in plan.run_window(xd, keep)]
+        for r, (f, w) in enumerate(zip(full, win)):
+            assert w.shape == (f.shape[0], keep[r])
+            np.testing.assert_array_equal(w, f[:, : keep[r]], err_msg=f"range {r}")
+        with pytest.raises(dd.DDError):
+            plan.run_window(xd, [f.shape[1] + 1 for f in full])
+    assert n > 0

@@ -8,6 +8,8 @@ import oracle
 import paper_2311_05341_gb300 as dd
 from synth import channel_freqs, filterbank
 
+from gpu_util import assert_float_parity
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
@@ -73,8 +75,14 @@ def test_time_major_host_pipeline(dtype):
     d_out = plan.empty_output(n_samp)
     plan.run_host_tmajor(h_in, h_out, d_tm, d_cm, d_out, n_samp=n_samp)
     torch.cuda.synchronize()
-    x_cm = np.zeros((77, d_cm.shape[1]), x_tm.dtype)
-    x_cm[:, :n_samp] = oracle.transpose(x_tm[:, :77])
-    ref = torch.cat([p.reshape(-1) for p in plan.run(torch.from_numpy(x_cm).cuda(),
-                                                     n_samp=n_samp)]).cpu()
-    assert torch.equal(h_out, ref)
+    # The oracle's transform of the oracle's transpose of the same samples.
+    x_cm = np.ascontiguousarray(oracle.transpose(x_tm[:, :77]))
+    ref = oracle.forward(x_cm, freqs, 1500.0, 64e-6, ranges)
+    got = plan.split(h_out, n_samp)
+    for r, (g, o) in enumerate(zip(got, ref)):
+        g = g.numpy()
+        if dtype == "f32":
+            ab = oracle.forward(x_cm, freqs, 1500.0, 64e-6, ranges, take_abs=True)[r]
+            assert_float_parity(g, o, ab, f"range {r}")
+        else:
+            np.testing.assert_array_equal(g, o, err_msg=f"range {r}")

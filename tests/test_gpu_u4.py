@@ -108,23 +108,25 @@ def test_u4_host_path_equals_device_path():
 
 
 def test_u4_paper_scale_sampled():
-    """8192 channels x 262144 samples (1 GB packed), 4096 DMs: sampled rows."""
+    """8192 channels x 262144 samples (1 GB packed), 4096 DMs: every 16th DM
+    row at full length, on the plain pattern tile and on the packed tile."""
     beam = workloads.paper_u8()
     n_samp = beam.n_samp
     data = _packed(beam.n_chan, n_samp, 6500)
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, "u4")
     assert plan.info(n_samp)["tile_dms"] == [TILE_PATTERN]
-    plane = plan.run(torch.from_numpy(data).cuda(), n_samp=n_samp)[0]
+    xd = torch.from_numpy(data).cuda()
+    plane = plan.run(xd, n_samp=n_samp)[0]
+    plan.set_tile(0, "packed")
+    plane_packed = plan.run(xd, n_samp=n_samp)[0]
     torch.cuda.synchronize()
     x = oracle.Packed4(data, n_samp)
-    rows = [0, 1, 1000, 2047, 3333, 4095]
-    n_out = plane.shape[1]
-    for t_lo in (0, n_out // 2, n_out - 1500):
-        t_hi = min(t_lo + 2048, n_out)
-        ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows,
-                                  t_lo, t_hi)
-        got = plane[torch.tensor(rows, device="cuda"), t_lo:t_hi].cpu().numpy()
-        np.testing.assert_array_equal(got, ref)
+    n_dm = plane.shape[0]
+    rows = sorted(set(range(0, n_dm, 16)) | {n_dm - 1, 1, 3333})
+    ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
+    idx = torch.tensor(rows, device="cuda")
+    np.testing.assert_array_equal(plane[idx].cpu().numpy(), ref)
+    np.testing.assert_array_equal(plane_packed[idx].cpu().numpy(), ref)
 
 
 @pytest.mark.parametrize("seed", range(6))

@@ -243,8 +243,10 @@ def test_u4_plan_selection_and_refusals():
 
 
 def test_adjoint_scratch_bytes():
-    """dd_adjoint_scratch_bytes: the pattern adjoint's scratch by its formula,
-    0 where the plan's adjoint is the gather, errors for bad arguments."""
+    """dd_adjoint_scratch_bytes: the pattern adjoint's scratch by its formula
+    (padded cotangent rows as float pairs, per-range results; no result
+    buffer for one range at bin 1), 0 where the plan's adjoint is the gather,
+    errors for bad arguments."""
     import ctypes
     lib = _lib.load()
     freqs = channel_freqs(1500.0, 2.6, 130)
@@ -257,9 +259,13 @@ def test_adjoint_scratch_bytes():
     assert lib.dd_adjoint_scratch_bytes(plan.handle, n_samp, ctypes.byref(got)) == _lib.DD_OK
     r4 = lambda n: (n + 3) // 4 * 4
     u = [(n_samp - 1) // r[3] + 1 for r in ranges]
-    pad_in = max(nd * r4(uu + s) for nd, uu, s in zip(info["n_dm"], u, info["s_max"]))
+    pad_in = max(2 * nd * r4(uu + s) for nd, uu, s in zip(info["n_dm"], u, info["s_max"]))
     want = 4 * (pad_in + sum(130 * r4(uu) for uu in u))
     assert got.value == want
+    one = dd.Plan(freqs, 1500.0, 64e-6, ranges[:1], "f32", upload=False)
+    i1 = one.info(n_samp)
+    assert lib.dd_adjoint_scratch_bytes(one.handle, n_samp, ctypes.byref(got)) == _lib.DD_OK
+    assert got.value == 4 * 2 * i1["n_dm"][0] * r4(n_samp + i1["s_max"][0])
     wide = dd.Plan(channel_freqs(1500.0, 600.0, 17), 1500.0, 64e-6, [(0.0, 80.0, 0.4, 1)], "f32",
                    upload=False)
     assert wide.info(n_samp)["adjoint_kernel"] == "gather"
@@ -274,9 +280,10 @@ def test_adjoint_scratch_bytes():
 
 
 def test_packed_tile_selection_and_scratch_bytes():
-    """DD_TILE_PACKED serves uint8, 4-bit and uint16 ranges at bin 1 only (not
-    float32, not binned ranges); it is never the automatic choice; the input
-    scratch is n_chan x ceil4(n_samp) 32-bit words when some range is packed."""
+    """DD_TILE_PACKED serves uint8, 4-bit, uint16 and float32 ranges at bin 1
+    only (not binned ranges); it is never the automatic choice; the input
+    scratch is n_chan x ceil4(n_samp) words (32-bit; float32: 64-bit pairs)
+    when some range is packed."""
     lib = _lib.load()
     paper = workloads.paper_u8()
     # The paper band and DM step on fewer channels and DMs (quick to plan).
@@ -295,9 +302,11 @@ def test_packed_tile_selection_and_scratch_bytes():
             _lib.DD_OK
         assert need.value == paper.n_chan * 1004 * 4
     f32 = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "f32", upload=False)
-    with pytest.raises(dd.DDError) as ei:
-        f32.set_tile(0, "packed")
-    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    assert f32.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
+    f32.set_tile(0, "packed")
+    assert f32.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PACKED]
+    assert lib.dd_plan_input_scratch_bytes(f32.handle, 1001, ctypes.byref(need)) == _lib.DD_OK
+    assert need.value == paper.n_chan * 1004 * 8
     binned = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, [(0.0, 40.0, 0.2, 2)], "u8",
                      upload=False)
     with pytest.raises(dd.DDError):
