@@ -88,10 +88,12 @@ typedef struct {
   size_t workspace_bytes;             /* device workspace dd_plan_upload needs */
   int32_t kernel[DD_MAX_RANGES];      /* forward kernel per range: DD_KERNEL_* */
   int32_t tile_dms[DD_MAX_RANGES];    /* tile of the tiled kernel: DMs per lane,
-                                          DD_TILE_PATTERN, DD_TILE_MERGE or
-                                          DD_TILE_PACKED (0: generic kernel) */
+                                          DD_TILE_PATTERN or DD_TILE_PACKED
+                                          (0: generic kernel) */
   int32_t adjoint_kernel;             /* float32 plans: DD_ADJOINT_* dd_run_adjoint
                                           uses (0 for other dtypes) */
+  int32_t tile_shape[DD_MAX_RANGES];  /* pattern-tile ranges: the dd_tile_shapes index
+                                          in use; -1 for other ranges */
 } dd_plan_info;
 
 /* Adjoint kernels (dd_plan_info.adjoint_kernel). */
@@ -111,16 +113,11 @@ typedef struct {
  * a = 0..3.  Plans whose shift of some channel grows by more than 4 between
  * consecutive trial DMs cannot use it. */
 #define DD_TILE_PATTERN 0x104
-/* The pattern tile with channel classes (uint8 input at bin 1): per group of
- * 16 consecutive trial DMs, channels whose shifts differ by constants over
- * those DMs are summed once into one staged window, read at one channel's
- * shifts.  Exact: the output is the same as channel by channel.  Only on
- * request (the automatic choice does not take it). */
-#define DD_TILE_MERGE 0x105
-/* The pattern tile on a packed copy of uint8, 4-bit or uint16 input (bin 1):
- * word t of each channel holds samples t and t + 32 H in its 16-bit halves
- * (uint16: sample t widened to 32 bits), so the staged words are the window
- * words (no unpacking, one barrier per stage).  dd_run
+/* The pattern tile on a packed copy of uint8, 4-bit, uint16 or float32 input
+ * (bin 1): word t of each channel holds samples t and t + 32 H in its 16-bit
+ * halves (uint16: sample t widened to 32 bits; float32: a 64-bit word of the
+ * two floats, added two at a time), so the staged words are the window words
+ * (no unpacking, one barrier per stage).  dd_run
  * writes the copy into caller scratch first: such plans run through
  * dd_run_scratch (dd_plan_input_scratch_bytes sizes it). */
 #define DD_TILE_PACKED 0x106
@@ -174,8 +171,7 @@ dd_status dd_plan_dm_ranges(const double* freqs_mhz, int32_t n_chan, double t_sa
 
 /*
  * Choose the tile of range `range`: `tile` is the offset tile's DM count per
- * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, DD_TILE_MERGE, DD_TILE_PACKED, or
- * 0 = automatic.  Per-plan tile
+ * lane (8, 6, 4, 2 or 1), DD_TILE_PATTERN, DD_TILE_PACKED, or 0 = automatic.  Per-plan tile
  * choice follows the paper's per-telescope tuning of D_dm / N_REG (Sec. 4.1).
  * Rebuilds the plan's device tables, so it must be followed by
  * dd_plan_upload (workspace_bytes may change); the plan is unbound until then.
@@ -322,6 +318,41 @@ dd_status dd_run_adjoint_scratch(dd_plan plan, const float* d_ybar, float* d_xba
 dd_status dd_plan_device_status(dd_plan plan, void* stream);
 
 /*
+ * Shapes of the pattern tiles, the tuning space of DD_TILE_PATTERN and
+ * DD_TILE_PACKED ranges.  The paper tunes its kernel's tile parameters per
+ * telescope and plan (Sec. 4.1: the register tile D_dm x D_t and the channels
+ * staged per step); these are the same parameters of this library's tiles.
+ */
+typedef struct {
+  int32_t words_per_lane;     /* H: window words a lane holds per trial DM (a
+                                 word holds two samples for uint8, 4-bit and
+                                 float pairs) */
+  int32_t dms_per_lane;       /* trial DMs per lane (4) */
+  int32_t warps;              /* warps per CTA */
+  int32_t channels_per_stage; /* channels staged per pipeline step */
+  int32_t channel_pairs;      /* 1: two channels per add (integer samples) */
+  int32_t float_pairs;        /* 1: 64-bit words of two floats (float32 packed tile) */
+  int32_t automatic;          /* 1: the automatic choice may take it (else only
+                                 dd_plan_set_tile_shape does) */
+} dd_tile_shape;
+
+/* Copy up to max_shapes entries of the shape table to out and set *n_shapes
+ * to its length (host only; out may be NULL when max_shapes is 0).
+ * Errors: DD_ERR_INVALID_ARG for NULL pointers. */
+dd_status dd_tile_shapes(dd_tile_shape* out, int32_t max_shapes, int32_t* n_shapes);
+
+/*
+ * dd_plan_set_tile for DD_TILE_PATTERN or DD_TILE_PACKED with one explicit
+ * shape (an index of dd_tile_shapes; -1: the automatic shape), the
+ * autotuner's knob.  Rebuilds the tables (dd_plan_upload
+ * follows, as for dd_plan_set_tile).
+ * Errors: DD_ERR_INVALID_ARG for another tile or index; DD_ERR_UNSUPPORTED if
+ * the shape cannot serve the range (its kind, window or increments), the
+ * previous choice and its binding kept.
+ */
+dd_status dd_plan_set_tile_shape(dd_plan plan, int32_t range, int32_t tile, int32_t shape);
+
+/*
  * Bound of the plan's device waits.  Every kernel stage waits for its copies
  * with at most max_polls polls of the mbarrier (max_polls <= 0: the default,
  * 2^22); a wait that runs out makes the kernel record DD_ERR_TIMEOUT for
@@ -448,8 +479,9 @@ dd_status dd_run_u8_noalloc_status(void* stream);
 typedef struct dd_batch_s* dd_batch;
 
 /* Build the work lists for n_plans plans and their raw sample counts.  Every
- * range must be on the tiled kernel, on the pattern tile or an offset tile
- * with 4, 2 or 1 DMs per lane, else DD_ERR_UNSUPPORTED; DD_ERR_BUDGET if the plans' windows together exceed the
+ * range must be on the tiled kernel, on the pattern tile (DD_TILE_PACKED
+ * included) or an offset tile with 4, 2 or 1 DMs per lane, else
+ * DD_ERR_UNSUPPORTED; DD_ERR_BUDGET if the plans' windows together exceed the
  * persistent kernel's shared memory; DD_ERR_SHAPE if an input is shorter than
  * a range's maximum delay. */
 dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n_plans,
@@ -460,19 +492,38 @@ dd_status dd_batch_workspace_bytes(dd_batch batch, size_t* bytes);
 /* Number of work items and jobs (plan ranges) of the batch. */
 dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs);
 /* Kernel launches one dd_batch_run makes (one per pattern-tile variant present,
- * plus one if any range is on an offset tile). */
+ * one if any range is on an offset tile, and one packing launch per plan with
+ * a DD_TILE_PACKED range). */
 dd_status dd_batch_launches(dd_batch batch, int32_t* n_launches);
 /* Copy the work list into caller device memory (256-byte aligned, >= the
  * workspace bytes) and bind it; synchronises `stream`. */
 dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void* stream);
 /* Bind the input/output buffers of every plan (d_in[i], in_row_stride[i],
  * d_out[i] follow dd_run's rules for plan i) by uploading the job table;
- * synchronises `stream`.  Rebind whenever a buffer address changes. */
+ * synchronises `stream`.  Rebind whenever a buffer address changes.
+ * Errors: DD_ERR_UNSUPPORTED if a plan has a DD_TILE_PACKED range (bind it with
+ * dd_batch_bind_scratch). */
 dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
                         void* const* d_out, void* stream);
-/* Persistent launches over all items of a bound batch (a counter reset and one
- * kernel launch per tile family present, in order on `stream`; all can be
- * captured in a CUDA graph). */
+/* Device scratch bytes plan `plan` of the batch needs for its packed copy
+ * (dd_plan_input_scratch_bytes at the batch's sample count; 0 without a
+ * DD_TILE_PACKED range).  Host only. */
+dd_status dd_batch_plan_scratch_bytes(dd_batch batch, int32_t plan, size_t* bytes);
+/* dd_batch_bind with caller-owned scratch per plan (d_scratch[i] of
+ * scratch_bytes[i] >= dd_batch_plan_scratch_bytes, 16-byte aligned; NULL
+ * arrays or entries for plans without a packed range): each dd_batch_run then
+ * first writes the packed copies (one packing launch per such plan), and the
+ * persistent launches read them.  The scratch is in use while runs are.
+ * Errors: as dd_batch_bind; DD_ERR_UNSUPPORTED for missing scratch,
+ * DD_ERR_BUDGET for too little, DD_ERR_SHAPE for a misaligned one. */
+dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
+                                const int64_t* in_row_stride, void* const* d_out,
+                                void* const* d_scratch, const size_t* scratch_bytes,
+                                void* stream);
+/* Persistent launches over all items of a bound batch (a counter reset, the
+ * packing launches of plans bound with scratch, and one kernel launch per tile
+ * family present, in order on `stream`; all can be captured in a CUDA
+ * graph). */
 dd_status dd_batch_run(dd_batch batch, void* stream);
 /* DD_ERR_TIMEOUT if a bounded device wait of any batch plan gave up since the
  * last check (clears the flags); synchronises `stream`. */

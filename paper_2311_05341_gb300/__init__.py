@@ -68,6 +68,16 @@ def dm_ranges(freqs, t_samp: float, dm_max: float, tol: float = 1.25, width: flo
     return [(arr[i].dm_lo, arr[i].dm_hi, arr[i].dm_step, arr[i].bin) for i in range(n.value)]
 
 
+def tile_shapes() -> list:
+    """The pattern-tile shape table (dd_tile_shapes) as dicts, by index."""
+    lib = _lib.load()
+    n = ctypes.c_int32()
+    check(lib.dd_tile_shapes(None, 0, ctypes.byref(n)))
+    arr = (_lib.TileShape * n.value)()
+    check(lib.dd_tile_shapes(ctypes.cast(arr, ctypes.c_void_p), n.value, ctypes.byref(n)))
+    return [{f: getattr(a, f) for f, _ in _lib.TileShape._fields_} for a in arr]
+
+
 def _stream_ptr(stream) -> int:
     import torch
     if stream is None:
@@ -128,6 +138,7 @@ class Plan:
             "kernel": [{1: "generic", 2: "tiled"}[inf.kernel[i]] for i in range(n)],
             "tile_dms": [inf.tile_dms[i] for i in range(n)],
             "adjoint_kernel": {0: None, 1: "gather", 2: "pattern"}[inf.adjoint_kernel],
+            "tile_shape": [inf.tile_shape[i] for i in range(n)],
         }
 
     def shifts(self, r: int = 0) -> np.ndarray:
@@ -141,15 +152,23 @@ class Plan:
         """Pick the register tile of range r and re-upload.
 
         tile: DMs per lane of the offset tile (8, 6, 4, 2, 1), "pattern"
-        (DD_TILE_PATTERN), "merge" (DD_TILE_MERGE: the pattern tile with
-        channel classes), "packed" (DD_TILE_PACKED: the pattern tile on a
-        packed copy of uint8 input, made in scratch by run()), or 0 for the
+        (DD_TILE_PATTERN), "packed" (DD_TILE_PACKED: the pattern tile on a
+        packed copy of the input, made in scratch by run()), or 0 for the
         automatic choice.
         """
-        code = {"pattern": _lib.DD_TILE_PATTERN, "merge": _lib.DD_TILE_MERGE,
-                "packed": _lib.DD_TILE_PACKED}.get(tile, tile)
+        code = {"pattern": _lib.DD_TILE_PATTERN, "packed": _lib.DD_TILE_PACKED}.get(tile, tile)
         code = int(code)
         check(self._lib.dd_plan_set_tile(self._h, int(r), code))
+        if self.workspace is not None:
+            self.upload(self.workspace.device if device is None else device)
+        return self
+
+    def set_tile_shape(self, r: int, tile, shape: int, device=None):
+        """Range r on the pattern tile ("pattern") or the packed tile
+        ("packed") with one explicit shape of tile_shapes() (-1: automatic);
+        re-uploads."""
+        code = {"pattern": _lib.DD_TILE_PATTERN, "packed": _lib.DD_TILE_PACKED}[tile]
+        check(self._lib.dd_plan_set_tile_shape(self._h, int(r), code, int(shape)))
         if self.workspace is not None:
             self.upload(self.workspace.device if device is None else device)
         return self

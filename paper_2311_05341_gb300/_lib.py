@@ -20,7 +20,6 @@ DD_U8, DD_U16, DD_F32, DD_U4 = 1, 2, 3, 4
 DD_MAX_RANGES = 16
 DD_KERNEL_GENERIC, DD_KERNEL_TILED = 1, 2
 DD_TILE_PATTERN = 0x104
-DD_TILE_MERGE = 0x105
 DD_TILE_PACKED = 0x106
 DD_ADJOINT_GATHER, DD_ADJOINT_PATTERN = 1, 2
 
@@ -51,7 +50,15 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t),
                 ("kernel", ctypes.c_int32 * DD_MAX_RANGES),
                 ("tile_dms", ctypes.c_int32 * DD_MAX_RANGES),
-                ("adjoint_kernel", ctypes.c_int32)]
+                ("adjoint_kernel", ctypes.c_int32),
+                ("tile_shape", ctypes.c_int32 * DD_MAX_RANGES)]
+
+
+class TileShape(ctypes.Structure):
+    _fields_ = [("words_per_lane", ctypes.c_int32), ("dms_per_lane", ctypes.c_int32),
+                ("warps", ctypes.c_int32), ("channels_per_stage", ctypes.c_int32),
+                ("channel_pairs", ctypes.c_int32), ("float_pairs", ctypes.c_int32),
+                ("automatic", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes) for every exported entry point.
@@ -78,6 +85,8 @@ SIGNATURES = {
     "dd_run_window": (ctypes.c_int, [_VP, _VP, _I64, _I64, ctypes.POINTER(_I64), _VP, _VP, _SZ,
                                      _VP]),
     "dd_plan_set_wait_limit": (ctypes.c_int, [_VP, _I32, _I32]),
+    "dd_tile_shapes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I32)]),
+    "dd_plan_set_tile_shape": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
     "dd_pack_input": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _SZ, _VP]),
     "dd_run_packed": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _SZ, _VP]),
     "dd_run_host": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP]),
@@ -96,6 +105,10 @@ SIGNATURES = {
     "dd_batch_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I64),
                                      ctypes.POINTER(_VP), _VP]),
     "dd_batch_run": (ctypes.c_int, [_VP, _VP]),
+    "dd_batch_plan_scratch_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_SZ)]),
+    "dd_batch_bind_scratch": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I64),
+                                             ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                             ctypes.POINTER(_SZ), _VP]),
     "dd_batch_status": (ctypes.c_int, [_VP, _VP]),
     "dd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dd_last_error_detail": (ctypes.c_char_p, []),

@@ -1,13 +1,16 @@
 """Batched dedispersion of many beams in one persistent launch (dd_batch_*).
 
 Beams may differ in channel count, dtype, sampling time and DM plan.  Each
-beam's plan gets a register tile (the pattern tile, or the offset tile with
-4, 2 or 1 DMs per lane) chosen by the autotuner, which times the feasible
-tiles on the beam's own shapes and caches the winner by plan signature -- the
-per-telescope tuning of the paper's tile parameters (Sec. 4.1) done
-automatically.  The batch then runs as persistent launches (one per tile
-family) over (beam range, DM block, time tile) work lists, optionally
-captured once in a CUDA graph and replayed.
+beam's plan gets a register tile chosen by the autotuner, which times every
+feasible candidate on the beam's own shapes and caches the winner by plan
+signature -- the per-telescope tuning of the paper's tile parameters
+(Sec. 4.1) done automatically.  The candidates are the pattern tile and the
+packed-input tile in each shape of the shape table (window words per lane H,
+warps per CTA, channels per stage; dd_tile_shapes) and the offset tile with
+4, 2 or 1 DMs per lane.  The batch then runs as persistent launches (one per
+tile variant, after the packing launches of packed-tile beams) over
+(beam range, DM block, time tile) work lists, optionally captured once in a
+CUDA graph and replayed.
 """
 from __future__ import annotations
 
@@ -22,7 +25,45 @@ import numpy as np
 from . import Plan, _lib
 from ._lib import check
 
-BATCH_SHAPES = ("pattern", 4, 2, 1)  # tiles the persistent kernels serve
+BATCH_SHAPES = ("pattern", 4, 2, 1)  # tile families the persistent kernels serve
+
+
+def tile_candidates(plan: Plan, r: int, packed: bool = True):
+    """Every (tile, shape) the batch can run range r of the plan on: the
+    pattern tile (and, for bin-1 ranges of packable dtypes, the packed tile)
+    in each shape that serves it, then the offset tiles.  Leaves the range on
+    its automatic tile."""
+    from . import tile_shapes
+    out = []
+    tiles = ["pattern"] + (["packed"] if packed and plan.dtype in ("u8", "u4", "u16", "f32")
+                           and int(plan.ranges[r][3]) == 1 else [])
+    for tile in tiles:
+        for i, sh in enumerate(tile_shapes()):
+            try:
+                plan.set_tile_shape(r, tile, i)
+                out.append((tile, i))
+            except _lib.DDError:
+                pass
+    for dr in (4, 2, 1):
+        try:
+            plan.set_tile(r, dr)
+            out.append((dr, -1))
+        except _lib.DDError:
+            pass
+    plan.set_tile(r, 0)
+    return out
+
+
+def apply_tile(plan: Plan, r: int, cand):
+    """Put range r on a candidate of tile_candidates ((tile, shape) or a bare
+    tile as Plan.set_tile takes it)."""
+    if isinstance(cand, (list, tuple)):
+        tile, shape = cand
+        if tile in ("pattern", "packed"):
+            plan.set_tile_shape(r, tile, int(shape))
+            return
+        cand = tile
+    plan.set_tile(r, cand)
 
 
 @dataclass
@@ -65,11 +106,14 @@ def plan_signature(plan: Plan, n_samp: int) -> str:
 
 
 class Autotuner:
-    """Times every feasible tile shape of a plan and keeps the fastest."""
+    """Times every feasible (tile, shape) of each range of a plan and keeps the
+    fastest (each candidate timed with its own packing pass, if any)."""
 
-    def __init__(self, shapes=BATCH_SHAPES, reps: int = 3, cache_path: str | None = None):
-        self.shapes = tuple(shapes)
+    def __init__(self, shapes=None, reps: int = 3, cache_path: str | None = None,
+                 packed: bool = True):
+        self.shapes = None if shapes is None else tuple(shapes)  # restrict to these tiles
         self.reps = reps
+        self.packed = packed
         self.cache_path = cache_path or os.environ.get("DD_AUTOTUNE_CACHE")
         self.cache = {}
         if self.cache_path and os.path.exists(self.cache_path):
@@ -78,34 +122,30 @@ class Autotuner:
         self.log = []
 
     def _feasible(self, plan: Plan, r: int):
-        ok = []
-        for dr in self.shapes:
-            try:
-                plan.set_tile(r, dr)
-                ok.append(dr)
-            except _lib.DDError:
-                pass
-        return ok
+        cands = tile_candidates(plan, r, packed=self.packed)
+        if self.shapes is not None:
+            cands = [c for c in cands if c[0] in self.shapes]
+        return cands
 
     def choose(self, plan: Plan, n_samp: int, x, out):
-        """Pick and set a shape for every range of the plan; returns them."""
+        """Pick and set a (tile, shape) for every range of the plan; returns them."""
         torch = _torch()
-        key = plan_signature(plan, n_samp)
+        key = plan_signature(plan, n_samp) + ("|packed" if self.packed else "")
         if key in self.cache:
-            choice = self.cache[key]
-            for r, dr in enumerate(choice):
-                plan.set_tile(r, dr)
+            choice = [tuple(c) if isinstance(c, list) else c for c in self.cache[key]]
+            for r, c in enumerate(choice):
+                apply_tile(plan, r, c)
             return choice
         choice = []
         for r in range(len(plan.ranges)):
             feas = self._feasible(plan, r)
             if not feas:
                 raise _lib.DDError(_lib.DD_ERR_UNSUPPORTED,
-                                   f"range {r} fits none of the batch tile shapes")
+                                   f"range {r} fits none of the batch tiles")
             best, best_ms = feas[0], float("inf")
             if len(feas) > 1:
-                for dr in feas:
-                    plan.set_tile(r, dr)
+                for cand in feas:
+                    apply_tile(plan, r, cand)
                     plan.run(x, out=out, n_samp=n_samp)
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
@@ -115,10 +155,10 @@ class Autotuner:
                     e1.record()
                     torch.cuda.synchronize()
                     ms = e0.elapsed_time(e1) / self.reps
-                    self.log.append((key, r, dr, ms))
+                    self.log.append((key, r, cand, ms))
                     if ms < best_ms:
-                        best, best_ms = dr, ms
-            plan.set_tile(r, best)
+                        best, best_ms = cand, ms
+            apply_tile(plan, r, best)
             choice.append(best)
         self.cache[key] = choice
         if self.cache_path:
@@ -147,8 +187,6 @@ class BatchRunner:
             x = input_buffer(b.dtype, plan.n_chan, b.n_samp, self.device)
             out = plan.empty_output(b.n_samp, self.device)
             if tiles is not None:
-                for r, t in enumerate(tiles[len(self.plans)]):
-                    plan.set_tile(r, t)
                 self.shapes.append(list(tiles[len(self.plans)]))
             elif self.tuner is not None:
                 self.shapes.append(self.tuner.choose(plan, b.n_samp, x, out))
@@ -163,6 +201,9 @@ class BatchRunner:
                         except _lib.DDError:
                             continue
                 self.shapes.append(shp)
+            if tiles is not None:
+                for r, t in enumerate(tiles[len(self.plans)]):
+                    apply_tile(plan, r, t)
             self.plans.append(plan)
             self.inputs.append(x)
             self.outputs.append(out)
@@ -174,6 +215,13 @@ class BatchRunner:
         check(lib.dd_batch_create(handles, n_samp, n, ctypes.byref(h)))
         self._h = h
         self._lib = lib
+        # Per-beam scratch of packed-tile beams (their packed copies).
+        self.scratch = []
+        for i in range(n):
+            need = ctypes.c_size_t()
+            check(lib.dd_batch_plan_scratch_bytes(h, i, ctypes.byref(need)))
+            self.scratch.append(torch.empty(need.value, dtype=torch.uint8, device=self.device)
+                                if need.value else None)
         nbytes = ctypes.c_size_t()
         check(lib.dd_batch_workspace_bytes(h, ctypes.byref(nbytes)))
         self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
@@ -200,7 +248,9 @@ class BatchRunner:
         strides = (ctypes.c_int64 * n)(*[x.stride(0) * (2 if b.dtype == "u4" else 1)
                                          for x, b in zip(self.inputs, self.beams)])
         d_out = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outputs])
-        check(self._lib.dd_batch_bind(self._h, d_in, strides, d_out, stream))
+        d_sc = (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in self.scratch])
+        n_sc = (ctypes.c_size_t * n)(*[0 if t is None else t.numel() for t in self.scratch])
+        check(self._lib.dd_batch_bind_scratch(self._h, d_in, strides, d_out, d_sc, n_sc, stream))
 
     def _launch(self):
         torch = _torch()

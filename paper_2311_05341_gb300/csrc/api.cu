@@ -56,10 +56,10 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     if (o->n_out[i] > 0) off += rp.n_dm * o->n_out[i];
     o->n_dm_total += rp.n_dm;
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
+    o->tile_shape[i] = rp.tile_ok && rp.tile_pattern ? rp.tile_shape : -1;
     o->tile_dms[i] = !rp.tile_ok                          ? 0
                      : !rp.tile_pattern                   ? rp.tile_dr
                      : tk::packed_copy_kind(rp.tile_kind)  ? DD_TILE_PACKED
-                     : tk::kPatShapes[rp.tile_shape].merge ? DD_TILE_MERGE
                                                            : DD_TILE_PATTERN;
     int64_t raw = (static_cast<int64_t>(rp.s_max) + 1) * rp.r.bin - 1;
     if (raw > o->max_delay_raw) o->max_delay_raw = raw;
@@ -287,19 +287,53 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile) {
   if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
   if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
     return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
-  if (tile != 0 && tile != DD_TILE_PATTERN && tile != DD_TILE_MERGE && tile != DD_TILE_PACKED &&
-      !tk::shape_for(tile))
-    return fail(DD_ERR_INVALID_ARG,
-                "tile must be 0, 1, 2, 4, 6, 8, DD_TILE_PATTERN, DD_TILE_MERGE or DD_TILE_PACKED");
+  if (tile != 0 && tile != DD_TILE_PATTERN && tile != DD_TILE_PACKED && !tk::shape_for(tile))
+    return fail(DD_ERR_INVALID_ARG, "tile must be 0, 1, 2, 4, 6, 8, DD_TILE_PATTERN or DD_TILE_PACKED");
   bool ok;
   try {
-    ok = retile_range(plan, static_cast<size_t>(range), tile);
+    ok = retile_range(plan, static_cast<size_t>(range), tile, -1);
   } catch (const std::bad_alloc&) {
     return fail(DD_ERR_INVALID_ARG, "host allocation failed while retiling");
   }
   // A refused tile leaves the previous tables (rebuilt identically) and the
   // workspace binding as they were; a new tile needs dd_plan_upload.
   if (!ok) return fail(DD_ERR_UNSUPPORTED, "tile cannot serve this range");
+  plan->d_ws = nullptr;
+  return DD_OK;
+}
+
+dd_status dd_tile_shapes(dd_tile_shape* out, int32_t max_shapes, int32_t* n_shapes) {
+  if (!n_shapes || (max_shapes > 0 && !out)) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+  const int32_t n = tk::kNumPatShapes;
+  *n_shapes = n;
+  for (int32_t i = 0; i < n && i < max_shapes; ++i) {
+    const tk::PatShape& s = tk::kPatShapes[i];
+    out[i].words_per_lane = s.h;
+    out[i].dms_per_lane = tk::kPatDr;
+    out[i].warps = s.warps;
+    out[i].channels_per_stage = s.nc;
+    out[i].channel_pairs = s.pairs ? 1 : 0;
+    out[i].float_pairs = s.h < 15 ? 1 : 0;
+    out[i].automatic = i < tk::kPatTuneFirst ? 1 : 0;
+  }
+  return DD_OK;
+}
+
+dd_status dd_plan_set_tile_shape(dd_plan plan, int32_t range, int32_t tile, int32_t shape) {
+  if (!plan) return fail(DD_ERR_INVALID_ARG, "plan is NULL");
+  if (range < 0 || range >= static_cast<int32_t>(plan->ranges.size()))
+    return fail(DD_ERR_INVALID_ARG, "range index out of bounds");
+  if (tile != DD_TILE_PATTERN && tile != DD_TILE_PACKED)
+    return fail(DD_ERR_INVALID_ARG, "tile must be DD_TILE_PATTERN or DD_TILE_PACKED");
+  if (shape < -1 || shape >= tk::kNumPatShapes)
+    return fail(DD_ERR_INVALID_ARG, "shape must be -1 or a dd_tile_shapes index");
+  bool ok;
+  try {
+    ok = retile_range(plan, static_cast<size_t>(range), tile, shape);
+  } catch (const std::bad_alloc&) {
+    return fail(DD_ERR_INVALID_ARG, "host allocation failed while retiling");
+  }
+  if (!ok) return fail(DD_ERR_UNSUPPORTED, "that shape cannot serve this range");
   plan->d_ws = nullptr;
   return DD_OK;
 }

@@ -53,6 +53,15 @@ struct dd_batch_s {
   unsigned char* d_ws = nullptr;
   bool bound = false;
   int32_t sm_count = 0;
+  // Plans with ranges on DD_TILE_PACKED: the packing pass each run makes
+  // before the persistent launches (bound by dd_batch_bind_scratch).
+  struct Pack {
+    int32_t plan;
+    const void* in = nullptr;
+    int64_t in_stride = 0;  // bytes
+    void* scratch = nullptr;
+  };
+  std::vector<Pack> packs;
 };
 
 namespace {
@@ -95,14 +104,17 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       int64_t out_off = 0;
       for (size_t r = 0; r < p->ranges.size(); ++r) {
         const RangePlan& rp = p->ranges[r];
-        const bool pat = rp.tile_ok && rp.tile_pattern && !tk::packed_copy_kind(rp.tile_kind);
+        const bool pat = rp.tile_ok && rp.tile_pattern;
+        if (pat && tk::packed_copy_kind(rp.tile_kind) &&
+            (b->packs.empty() || b->packs.back().plan != i))
+          b->packs.push_back({i});
         if (!rp.tile_ok || (rp.tile_pattern && !pat) ||
             (!pat && (rp.tile_pattern || !batch_shape(rp.tile_dr)))) {
           delete b;
           return fail(DD_ERR_UNSUPPORTED,
                       "batch plan " + std::to_string(i) + " range " + std::to_string(r) +
-                          " is not on a batch tile (the pattern tile, or the offset tile with "
-                          "4/2/1 DMs per lane; see dd_plan_set_tile)");
+                          " is not on a batch tile (the pattern or packed tile, or the offset "
+                          "tile with 4/2/1 DMs per lane; see dd_plan_set_tile)");
         }
         const int64_t n_out = range_n_out(p, rp, n_samp[i]);
         if (n_out <= 0) {
@@ -125,7 +137,7 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
           b->pjob_group.push_back(static_cast<int32_t>(g));
           b->groups[g].smem = std::max(
               b->groups[g].smem,
-              tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp, rp.tile_nv));
+              tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp));
           ts = tk::pat_tile_samples(rp.tile_kind, ps.h);
           dms = static_cast<double>(ps.warps) * tk::kPatDr;
         } else {
@@ -216,7 +228,7 @@ dd_status dd_batch_info(dd_batch batch, int64_t* n_items, int32_t* n_jobs) {
 
 dd_status dd_batch_launches(dd_batch batch, int32_t* n_launches) {
   if (!batch || !n_launches) return fail(DD_ERR_INVALID_ARG, "NULL argument");
-  int32_t n = batch->items.empty() ? 0 : 1;
+  int32_t n = (batch->items.empty() ? 0 : 1) + static_cast<int32_t>(batch->packs.size());
   for (const auto& g : batch->groups) n += g.items.empty() ? 0 : 1;
   *n_launches = n;
   return DD_OK;
@@ -249,18 +261,42 @@ dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void*
   return DD_OK;
 }
 
-dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
-                        void* const* d_out, void* stream) {
+dd_status dd_batch_plan_scratch_bytes(dd_batch batch, int32_t plan, size_t* bytes) {
+  if (!batch || !bytes) return fail(DD_ERR_INVALID_ARG, "batch or bytes is NULL");
+  if (plan < 0 || plan >= static_cast<int32_t>(batch->plans.size()))
+    return fail(DD_ERR_INVALID_ARG, "plan index out of bounds");
+  return dd_plan_input_scratch_bytes(batch->plans[plan], batch->n_samp[plan], bytes);
+}
+
+dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
+                                const int64_t* in_row_stride, void* const* d_out,
+                                void* const* d_scratch, const size_t* scratch_bytes,
+                                void* stream) {
   if (!batch || !d_in || !in_row_stride || !d_out)
     return fail(DD_ERR_INVALID_ARG, "NULL argument");
   if (!batch->d_ws) return fail(DD_ERR_INVALID_ARG, "batch has no uploaded workspace");
+  batch->bound = false;
+  for (auto& pk : batch->packs) {
+    const dd_plan p = batch->plans[pk.plan];
+    size_t need = 0;
+    dd_plan_input_scratch_bytes(p, batch->n_samp[pk.plan], &need);
+    if (!d_scratch || !scratch_bytes || !d_scratch[pk.plan])
+      return fail(DD_ERR_UNSUPPORTED, "batch plan " + std::to_string(pk.plan) +
+                                          " has a packed-tile range: bind it with scratch");
+    if (scratch_bytes[pk.plan] < need) return fail(DD_ERR_BUDGET, "batch plan scratch too small");
+    if (reinterpret_cast<uintptr_t>(d_scratch[pk.plan]) & 15u)
+      return fail(DD_ERR_SHAPE, "batch plan scratch must be 16-byte aligned");
+    pk.in = d_in[pk.plan];
+    pk.in_stride = static_cast<int64_t>(dtype_row_bytes(p->dtype, in_row_stride[pk.plan]));
+    pk.scratch = d_scratch[pk.plan];
+  }
   for (size_t j = 0; j < batch->jobs.size(); ++j) {
     const auto& jr = batch->jobs[j];
     const dd_plan p = batch->plans[jr.plan];
     if (!p->d_ws) return fail(DD_ERR_INVALID_ARG, "a batch plan has no uploaded workspace");
     const void* x = d_in[jr.plan];
     void* o = d_out[jr.plan];
-    const int64_t stride = in_row_stride[jr.plan];
+    int64_t stride = in_row_stride[jr.plan];
     const int64_t n = batch->n_samp[jr.plan];
     const int64_t stride_bytes = p->dtype == DD_U4 ? stride / 2
                                  : stride * (p->dtype == DD_U8 ? 1 : (p->dtype == DD_U16 ? 2 : 4));
@@ -269,6 +305,10 @@ dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* 
         stride < n || stride_bytes % 16 != 0 || (p->dtype == DD_U4 && stride % 2 != 0))
       return fail(DD_ERR_SHAPE, "batch input/output alignment or stride");
     const RangePlan& rp = p->ranges[jr.range];
+    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {  // reads the packed copy
+      x = d_scratch[jr.plan];
+      stride = (n + 3) / 4 * 4;
+    }
     const tk::TileParams prm =
         tiled_params(p, rp, static_cast<unsigned char*>(p->d_ws) + rp.off_tile_recs,
                      reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p->d_ws) +
@@ -302,6 +342,11 @@ dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* 
   return DD_OK;
 }
 
+dd_status dd_batch_bind(dd_batch batch, const void* const* d_in, const int64_t* in_row_stride,
+                        void* const* d_out, void* stream) {
+  return dd_batch_bind_scratch(batch, d_in, in_row_stride, d_out, nullptr, nullptr, stream);
+}
+
 dd_status dd_batch_run(dd_batch batch, void* stream) {
   if (!batch) return fail(DD_ERR_INVALID_ARG, "batch is NULL");
   if (!batch->bound) return fail(DD_ERR_INVALID_ARG, "batch is not bound (dd_batch_bind)");
@@ -309,6 +354,17 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
   cudaError_t e =
       cudaMemsetAsync(batch->d_ws, 0, (1 + batch->groups.size()) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run counter reset");
+  for (const auto& pk : batch->packs) {  // the packed copies the persistent launches read
+    const dd_plan p = batch->plans[pk.plan];
+    int32_t pair = 0;
+    for (const auto& rp : p->ranges)
+      if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) pair = pack_pair(rp);
+    const int64_t n = batch->n_samp[pk.plan];
+    const int64_t packed_stride = (n + 3) / 4 * 4;
+    const int le = launch_pack_pairs(pk.in, pk.in_stride, p->n_chan, n, pk.scratch, packed_stride,
+                                     pair, 0, packed_stride, pack_source(p->dtype), stream);
+    if (le != 0) return cuda_fail(le, "dd_batch_run packing");
+  }
   for (size_t gi = 0; gi < batch->groups.size(); ++gi) {
     const auto& g = batch->groups[gi];
     if (g.items.empty()) continue;

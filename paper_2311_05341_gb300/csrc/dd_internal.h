@@ -45,13 +45,13 @@ struct RangePlan {
   int32_t tile_shape = 0;       // index into tk::kPatShapes (pattern tiles)
   int32_t tile_kind = 0;        // window-word kind (tk::Kind)
   int32_t tile_request = 0;     // tile requested by dd_plan_set_tile (0 = automatic)
+  int32_t shape_request = -1;   // pattern shape requested (dd_plan_set_tile_shape; -1: first fit)
   int32_t tile_n_blocks = 0;    // DM blocks of tile_dr * warps DMs
   int32_t tile_lp = 0;          // window words per staged channel
   uint32_t tile_units_magic = 0;  // division by tile_lp / 4 (see fwd_tiled.h)
   int32_t tile_units_shift = 0;
   size_t tile_chunk_off = 0;    // pair tiles: byte offset of the pair chunks in tile_recs
   int32_t tile_chunk_bytes = 0; // pair tiles: bytes per (DM block, stage) chunk
-  int32_t tile_nv = 0;          // merged pattern tiles: window slots per round
   int32_t tile_n_chan = 0;      // rows of the tables' input when not the plan's channels
 
   // Byte offsets of the device tables inside the workspace.
@@ -94,7 +94,7 @@ dd_status cuda_fail(int err, const char* what);
 dd_status build_plan(dd_plan_s* p);
 // (Re)choose the uint8 tile of one range (request 0 = automatic) and rebuild
 // the workspace image.  Returns false if the requested tile does not fit.
-bool retile_range(dd_plan_s* p, size_t range, int32_t request);
+bool retile_range(dd_plan_s* p, size_t range, int32_t request, int32_t shape_request = -1);
 int64_t range_n_out(const dd_plan_s* p, const RangePlan& rp, int64_t n_samp);
 // DM ranges from a smearing tolerance (dd_plan_dm_ranges); returns their count.
 int32_t dm_plan_ranges(const double* freqs, int32_t n_chan, double t_samp, double dm_max,
@@ -145,6 +145,13 @@ inline PackSource pack_source(dd_dtype dtype) {
          : dtype == DD_U4  ? PackSource::kU4
          : dtype == DD_F32 ? PackSource::kF32
                            : PackSource::kU8;
+}
+// Bytes of n samples of a dtype (4-bit: two per byte, rounded up).
+inline size_t dtype_row_bytes(dd_dtype t, int64_t n) {
+  return t == DD_U4    ? static_cast<size_t>((n + 1) / 2)
+         : t == DD_U8  ? static_cast<size_t>(n)
+         : t == DD_U16 ? static_cast<size_t>(n) * 2
+                       : static_cast<size_t>(n) * 4;
 }
 // Bytes of one word of a plan's packed copy.
 inline size_t packed_word_bytes(dd_dtype dtype) { return dtype == DD_F32 ? 8 : 4; }

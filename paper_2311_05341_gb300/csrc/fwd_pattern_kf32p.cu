@@ -1,5 +1,5 @@
-// fwd_pattern_kf32p.cu -- the pattern-tile kernels and launchers of kind
+// fwd_pattern_kf32p.cu -- the one-unit-per-CTA pattern kernels and launcher of kind
 // kF32P: float32 pairs (64-bit words of two floats, add.f32x2) from the packed copy.
 #include "pattern_kernels.cuh"
 
-DD_PATTERN_KIND(kF32P)
+DD_PATTERN_KIND_FORWARD(kF32P)

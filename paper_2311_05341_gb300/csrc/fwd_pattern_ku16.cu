@@ -1,5 +1,5 @@
-// fwd_pattern_ku16.cu -- the pattern-tile kernels and launchers of kind
+// fwd_pattern_ku16.cu -- the one-unit-per-CTA pattern kernels and launcher of kind
 // kU16: uint16 (one sample per word, unpacked).
 #include "pattern_kernels.cuh"
 
-DD_PATTERN_KIND(kU16)
+DD_PATTERN_KIND_FORWARD(kU16)

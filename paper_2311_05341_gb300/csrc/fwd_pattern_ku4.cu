@@ -1,5 +1,5 @@
-// fwd_pattern_ku4.cu -- the pattern-tile kernels and launchers of kind
+// fwd_pattern_ku4.cu -- the one-unit-per-CTA pattern kernels and launcher of kind
 // kU4: 4-bit samples (pairs in 16-bit lanes, unpacked from staged nibbles).
 #include "pattern_kernels.cuh"
 
-DD_PATTERN_KIND(kU4)
+DD_PATTERN_KIND_FORWARD(kU4)

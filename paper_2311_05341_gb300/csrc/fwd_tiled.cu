@@ -327,7 +327,6 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
                  ? tk::pat_raw_bytes(rp.tile_kind, rp.r.bin, tk::kPatShapes[rp.tile_shape],
                                      rp.tile_lp)
                  : tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp);
-  prm.nv = rp.tile_nv;
   prm.units_magic = rp.tile_units_magic;
   prm.units_shift = rp.tile_units_shift;
   prm.bin = rp.r.bin;

@@ -196,22 +196,27 @@ struct PatShape {
   bool pairs;
   bool dbuf;
   int amax;
-  bool merge;  // channel classes (uint8 at bin 1; see below)
 };
 // Fewer channels per stage fit the wider raw windows of larger bins.  Float:
 // 32 channels per stage with loads inside the pattern blocks measured 12 %
 // faster at H = 23 than H = 19 with loads before the branch (1024-channel
 // float32 plan, 3.85 against 4.38 ms).
 // Float pairs (kF32P, 64-bit words of two floats): H = 11 words of 2
-// samples, the accumulators of 4 DMs in 88 registers.
+// samples, the accumulators of 4 DMs in 88 registers (H = 13 with 12 warps).
+// The automatic choice takes the first entry that serves and fits; the
+// entries from index kPatTuneFirst on are reached only through an explicit
+// shape (dd_plan_set_tile_shape), for the autotuner: other window widths,
+// warp counts and channels per stage.
 constexpr PatShape kPatShapes[] = {
-    {23, 16, 32, true, false, 3, true},
-    {23, 16, 32, true, false, 3, false},  {23, 16, 12, true, false, 3, false},
-    {23, 16, 6, true, false, 3, false},   {23, 16, 32, false, false, 3, false},
-    {19, 16, 32, false, false, 3, false}, {19, 16, 12, false, false, 1, false},
-    {19, 16, 6, false, false, 1, false},  {19, 16, 12, false, false, 3, false},
-    {19, 16, 6, false, false, 3, false},  {11, 16, 24, false, false, 3, false},
-    {11, 16, 16, false, false, 3, false}, {11, 16, 8, false, false, 3, false}};
+    {23, 16, 32, true, false, 3},  {23, 16, 12, true, false, 3},  {23, 16, 6, true, false, 3},
+    {23, 16, 32, false, false, 3}, {19, 16, 32, false, false, 3}, {19, 16, 12, false, false, 1},
+    {19, 16, 6, false, false, 1},  {19, 16, 12, false, false, 3}, {19, 16, 6, false, false, 3},
+    {11, 16, 24, false, false, 3}, {11, 16, 16, false, false, 3}, {11, 16, 8, false, false, 3},
+    // Tuning entries.
+    {21, 16, 32, true, false, 3},  {19, 16, 32, true, false, 3},  {25, 12, 32, true, false, 3},
+    {23, 12, 32, true, false, 3},  {23, 16, 24, true, false, 3},  {21, 16, 32, false, false, 3},
+    {13, 12, 16, false, false, 3}, {11, 12, 24, false, false, 3}};
+constexpr int kPatTuneFirst = 12;
 constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
 constexpr bool pat_shapes_fit_records() {
   for (const PatShape& s : kPatShapes)
@@ -220,65 +225,18 @@ constexpr bool pat_shapes_fit_records() {
 }
 static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its records hold");
 // The shape serves a kind: pairs take integer window words, single channels
-// float; channel classes are built from uint8 samples at bin 1.
-// Float-pair shapes (H < 15) serve kF32P only.
+// float; float-pair shapes (H < 15) serve kF32P only.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
-  return s.pairs == !float_kind(kind) && (!s.merge || kind == kU8) &&
-         (!direct_kind(kind) || !s.dbuf) && ((s.h < 15) == float_pairs(kind));
+  return s.pairs == !float_kind(kind) && (!direct_kind(kind) || !s.dbuf) &&
+         ((s.h < 15) == float_pairs(kind));
 }
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {
   return kPairCountBytes + warps * nc * static_cast<int>(sizeof(PairItem));
 }
 
-// Channel classes (merged pattern tiles).  A sub-block is kMergeSubWarps
-// warps, i.e. kMergeSubWarps * kPatDr consecutive trial DMs.  Channels c of a
-// stage whose shifts differ from those of a reference channel r by the same
-// amount at every DM of the sub-block, s(c, d) - s(r, d) = const, form a
-// class: the sum over the class of X_c[t + s(c, d)] is one read of the summed
-// window V[u] = sum_c W_c[u + delta_c] at the reference channel's shifts
-// (W_c = channel c's staged window words, delta_c = c's window offset minus
-// r's, 0 <= delta_c <= kMergeMaxDelta).  The sums are exact (integers), so the
-// output is that of the channel-by-channel sum.  Per stage each sub-block's
-// warps walk the classes of their sub-block as channel pairs and singles; the
-// stage's windows are built in rounds of at most `nv` windows (a plan value
-// set by shared memory), so a stage with more classes than fit takes more
-// than one round.
-//
-// Chunk of one (DM block, stage), merge_chunk_bytes(warps, nc) bytes:
-//   [0]                 number of rounds
-//   [16 + r]            windows of round r
-//   [32 + 64 r + w]     pairs of warp w in round r
-//   [64 + 64 r + w]     singles of warp w in round r
-//   kMergeWinOff        uint16 per (round, window slot): first member | count << 8
-//   kMergeMemOff        uint32 per member: byte offset in the raw buffer of the
-//                       4-byte word holding sample delta of its staged channel
-//                       (delta rounded down to 4) | byte-permute selector of
-//                       the 4 samples from delta on, << 16
-//   kMergeItemOff       PairItem per (warp, nc): warp w's items, round by round,
-//                       a = window slot * lp + offset of the reference channel
-constexpr int kMergeSubWarps = 4;
-constexpr int kMergeMaxRounds = 4;
-constexpr int kMergeMaxNv = 64;       // window slots per round
-constexpr int kMergeMinNv = 32;
-constexpr int kMergeMaxDelta = 60;    // member window offset (raw bytes fetched: + kMergeHalo)
-constexpr int kMergeHalo = 64;
-constexpr int kMergeCntOff = 32;
-constexpr int kMergeWinOff = kMergeCntOff + kMergeMaxRounds * kPairCountBytes;
-constexpr int kMergeMemOff = kMergeWinOff + 2 * kMergeMaxRounds * kMergeMaxNv;
-DD_HOST_DEVICE constexpr int merge_max_members(int warps, int nc) {
-  return nc * (warps / kMergeSubWarps);
-}
-DD_HOST_DEVICE constexpr int merge_item_off(int warps, int nc) {
-  return (kMergeMemOff + 4 * merge_max_members(warps, nc) + 15) / 16 * 16;
-}
-DD_HOST_DEVICE constexpr int merge_chunk_bytes(int warps, int nc) {
-  return merge_item_off(warps, nc) + warps * nc * static_cast<int>(sizeof(PairItem));
-}
 DD_HOST_DEVICE constexpr int pat_chunk_bytes(const PatShape& s) {
-  return s.merge   ? merge_chunk_bytes(s.warps, s.nc)
-         : s.pairs ? pair_chunk_bytes(s.warps, s.nc)
-                   : 0;
+  return s.pairs ? pair_chunk_bytes(s.warps, s.nc) : 0;
 }
 
 
@@ -324,26 +282,16 @@ DD_HOST_DEVICE constexpr size_t pat_raw_offset(const PatShape& s) {
                                           : s.nc * static_cast<int>(sizeof(PRec))) +
           127) / 128 * 128;
 }
-// Raw bytes staged per channel (merged tiles: kMergeHalo more for the members'
-// window offsets).
+// Raw bytes staged per channel.
 DD_HOST_DEVICE constexpr int32_t pat_raw_bytes(int kind, int bin, const PatShape& s, int32_t lp) {
-  return raw_bytes(kind, bin, lp, 32 * s.h) + (s.merge ? kMergeHalo : 0);
+  return raw_bytes(kind, bin, lp, 32 * s.h);
 }
-// nv: window slots of a merged tile (else the nc staged channels' windows).
 // Direct kinds stage window words: two staging buffers and no window buffer.
-inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp, int nv = 0) {
+inline size_t pat_smem_bytes(int kind, int bin, const PatShape& s, int32_t lp) {
   if (direct_kind(kind))
     return pat_raw_offset(s) + 2 * static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp);
-  const int windows = s.merge ? nv : s.nc;
   return pat_raw_offset(s) + static_cast<size_t>(s.nc) * pat_raw_bytes(kind, bin, s, lp) +
-         (s.dbuf ? 2 : 1) * static_cast<size_t>(windows) * lp * 4;
-}
-// Window slots of a merged tile that fit beside its raw and record buffers.
-inline int pat_merge_nv(int kind, int bin, const PatShape& s, int32_t lp, size_t smem_max) {
-  const size_t fixed = pat_smem_bytes(kind, bin, s, lp, 0);
-  if (fixed >= smem_max) return 0;
-  const size_t nv = (smem_max - fixed) / (static_cast<size_t>(lp) * 4);
-  return static_cast<int>(nv < static_cast<size_t>(kMergeMaxNv) ? nv : kMergeMaxNv);
+         (s.dbuf ? 2 : 1) * static_cast<size_t>(s.nc) * lp * 4;
 }
 
 inline size_t smem_bytes(int kind, int bin, const Shape& s, int32_t lp) {
@@ -371,7 +319,6 @@ struct TileParams {
   int32_t units_shift;
   int32_t bin;          // time decimation of the range (raw samples per window word)
   int32_t flush;        // channels between accumulator widenings
-  int32_t nv;           // merged pattern tiles: window slots per round
   void* out;            // [n_dm][n_out] int32 or float32
   int32_t* err;
   int32_t wait_iters;   // polls before a pipeline wait gives up (kWaitIters by default)

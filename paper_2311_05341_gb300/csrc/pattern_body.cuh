@@ -45,9 +45,9 @@ struct PSmem {
   uint32_t* pw;       // [1 or 2][NC][lp] window words
 };
 
-template <int NW, int NC, bool PAIRS, bool DBUF, bool MERGE = false>
+template <int NW, int NC, bool PAIRS, bool DBUF>
 __device__ __forceinline__ PSmem pat_layout(unsigned char* smem, int32_t lraw) {
-  constexpr size_t kRawOff = pat_raw_offset(PatShape{0, NW, NC, PAIRS, DBUF, 0, MERGE});
+  constexpr size_t kRawOff = pat_raw_offset(PatShape{0, NW, NC, PAIRS, DBUF, 0});
   PSmem sm;
   sm.bar_base = smem_u32(smem);
   sm.recs = smem + kRecOffset;
@@ -64,8 +64,9 @@ template <int KIND, int H>
 __device__ __forceinline__ void pat_channel(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
                                             uint32_t ix) {
   if constexpr (float_pairs(KIND)) {
-    static_assert(H == 11, "no generated float-pair blocks for H");
-    DD_PATL_CHANNEL_F2_11(acc, win, ix);
+    static_assert(H == 11 || H == 13, "no generated float-pair blocks for H");
+    if constexpr (H == 11) DD_PATL_CHANNEL_F2_11(acc, win, ix);
+    else DD_PATL_CHANNEL_F2_13(acc, win, ix);
     return;
   } else {
   static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
@@ -318,166 +319,6 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       // The next stage unpacks into this window buffer (single-buffered):
       // wait until every warp has read its transpose tile back.
       if constexpr (!DBUF) __syncthreads();
-    }
-  }
-  return true;
-}
-
-// Words u..u+3 of a class window (low 16-bit lanes: samples u.., high lanes:
-// samples u + 32H ..): the sum over the members of their staged uint8 samples
-// at u + delta.  Even and odd samples are summed apart in 16-bit lanes (at
-// most NC members x 255 < 2^16), then interleaved.
-struct MergeSum {
-  uint32_t e_lo = 0, o_lo = 0, e_hi = 0, o_hi = 0;
-  __device__ __forceinline__ void add(uint32_t lo, uint32_t hi) {
-    e_lo += lo & 0x00ff00ffu;
-    o_lo += __byte_perm(lo, 0u, 0x4341);
-    e_hi += hi & 0x00ff00ffu;
-    o_hi += __byte_perm(hi, 0u, 0x4341);
-  }
-  __device__ __forceinline__ uint4 words() const {
-    return make_uint4(__byte_perm(e_lo, e_hi, 0x5410), __byte_perm(o_lo, o_hi, 0x5410),
-                      __byte_perm(e_lo, e_hi, 0x7632), __byte_perm(o_lo, o_hi, 0x7632));
-  }
-};
-
-// Four raw bytes of a member from word K of `src` on: two aligned loads and a
-// byte funnel (selector 0x3210 when the member's offset is a multiple of 4).
-template <int K>
-__device__ __forceinline__ uint32_t member_word(const uint32_t* src, uint32_t sel) {
-  return __byte_perm(src[K], src[K + 1], sel);
-}
-
-// Merged pattern tile (uint8 at bin 1): one (DM block, time tile) work unit.
-// The pipeline is that of pat_body without double-buffered windows; per
-// stage the classes' windows are built from the staged raw bytes in one or
-// more rounds (fwd_tiled.h), each followed by the warps' pair/single walk
-// over the round's windows.  The next stage's copies are issued once the last
-// round's windows are built.  Returns false after a bounded wait gave up.
-template <int H, int NW, int NC, int AMAX>
-__device__ __forceinline__ bool pat_body_merge(const TileParams& p, const PSmem& sm, int blk,
-                                               int64_t tile) {
-  constexpr int KIND = kU8;
-  constexpr int kPairW = 32 * H;
-  constexpr int kRecBufs = 2;
-  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-  const int64_t t0 = tile * pat_tile_samples(KIND, H);
-  const int n_st = (p.n_chan + NC - 1) / NC;
-  const int32_t* my_bases = p.bases + static_cast<int64_t>(blk) * p.n_chan;
-  auto base_of = [&](int st) -> int32_t {
-    const int c = st * NC + tid;
-    return (tid < NC && st < n_st && c < p.n_chan) ? my_bases[c] : 0;
-  };
-  auto rec_buf = [&](int rb) -> unsigned char* { return sm.recs + rb * p.chunk_bytes; };
-  auto issue = [&](int st, int32_t base) {
-    issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, 0, t0, base, tid,
-                          pair_chunk(p, blk, n_st, st), p.chunk_bytes, rec_buf(st % kRecBufs));
-  };
-  if (tid <= NC) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(0, base_of(0));
-  }
-  int32_t next_base = base_of(1);
-
-  uint32_t acc[kPatDr][H];
-#pragma unroll
-  for (int i = 0; i < kPatDr; ++i)
-#pragma unroll
-    for (int j = 0; j < H; ++j) acc[i][j] = 0u;
-
-  bool first = true;
-  int since = 0;
-  const int units = p.lp >> 2;
-  const int item_off = merge_item_off(NW, NC);
-  int rb = 0;
-
-  for (int st = 0; st < n_st; ++st) {
-    const uint32_t parity = st & 1;
-    const int nc = min(NC, p.n_chan - st * NC);
-    const bool ok = mbar_wait(sm.bar_base, parity, p.wait_iters);
-    const unsigned char* ck = rec_buf(rb);
-    const int n_rounds = ok ? ck[0] : 0;
-    const uint16_t* wins = reinterpret_cast<const uint16_t*>(ck + kMergeWinOff);
-    const uint32_t* mem = reinterpret_cast<const uint32_t*>(ck + kMergeMemOff);
-    const PairItem* items = reinterpret_cast<const PairItem*>(ck + item_off) + w * NC;
-    int k0 = 0;  // this warp's first item of the round
-    for (int r = 0; r < n_rounds || r == 0; ++r) {
-      // Build the round's class windows.  A task is 64 units (4 window words
-      // each) of one window; warp w takes tasks w, w + NW, ...; lane l sums
-      // units qb + l and qb + 32 + l over the window's members, two members
-      // per step.  Lanes past the window's end read words up to 64 units
-      // further (inside the raw buffer or the window buffer that follows it)
-      // and store nothing.
-      if (ok) {
-        const int tpw = (units + 63) >> 6;
-        const uint32_t recip = (65536u + tpw - 1) / tpw;  // t / tpw for t < 2^16 / tpw^2
-        const int n_tasks = ck[16 + r] * tpw;
-        for (int t = w; t < n_tasks; t += NW) {
-          const int v = static_cast<int>((static_cast<uint32_t>(t) * recip) >> 16);
-          const int q0 = ((t - v * tpw) << 6) + l;
-          const uint32_t e = wins[r * kMergeMaxNv + v];
-          const int m0 = e & 0xffu, m1 = m0 + (e >> 8);
-          const uint8_t* lane_raw = sm.raw + 4 * q0;
-          MergeSum a, b;
-          auto member = [&](uint32_t me) {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(lane_raw + (me & 0xffffu));
-            const uint32_t sel = me >> 16;
-            a.add(member_word<0>(src, sel), member_word<kPairW / 4>(src, sel));
-            b.add(member_word<32>(src, sel), member_word<32 + kPairW / 4>(src, sel));
-          };
-          int m = m0;
-          for (; m + 1 < m1; m += 2) {
-            const uint32_t e0 = mem[m], e1 = mem[m + 1];
-            member(e0);
-            member(e1);
-          }
-          if (m < m1) member(mem[m]);
-          uint32_t* dst = sm.pw + static_cast<size_t>(v) * p.lp + 4 * q0;
-          if (q0 < units) *reinterpret_cast<uint4*>(dst) = a.words();
-          if (q0 + 32 < units) *reinterpret_cast<uint4*>(dst + 128) = b.words();
-        }
-      }
-      if (r == 0) {
-        if (__syncthreads_or(!ok)) {
-          if (tid == 0) {
-            atomicOr(p.err, kErrTimeout);
-            if (st != p.hold_stage) mbar_wait(sm.bar_base, parity);
-          }
-          return false;
-        }
-      } else {
-        __syncthreads();
-      }
-      if (r + 1 >= n_rounds && tid <= NC && st + 1 < n_st) {
-        // The raw bytes are consumed: stage st + 1's copies land meanwhile.
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(st + 1, next_base);
-        next_base = base_of(st + 2);
-      }
-      // Shift-and-sum over the round's windows (pairs of equal pattern, then singles).
-      const uint32_t lane_win = smem_u32(sm.pw + H * l);
-      const int n_pairs = ck[kMergeCntOff + r * kPairCountBytes + w];
-      const int n_items = n_pairs + ck[kMergeCntOff + r * kPairCountBytes + kPairMaxWarps + w];
-#pragma unroll 1
-      for (int k = 0; k < n_pairs; ++k) {
-        const PairItem it = items[k0 + k];
-        pat_pair<H>(acc, lane_win + 4u * (it.a & 0xffffu), lane_win + 4u * (it.a >> 16), it.pat);
-      }
-#pragma unroll 1
-      for (int k = n_pairs; k < n_items; ++k) {
-        const PairItem it = items[k0 + k];
-        pat_channel<KIND, H>(acc, lane_win + 4u * it.a, it.pat);
-      }
-      k0 += n_items;
-      __syncthreads();  // the windows are free
-    }
-    since += nc;
-    rb = rb + 1 == kRecBufs ? 0 : rb + 1;
-    if (since + NC > p.flush || st == n_st - 1) {
-      widen_store<KIND, kPatDr, NW, NC, H, false>(p, sm.pw, acc, blk, t0, first);
-      first = false;
-      since = 0;
-      __syncthreads();  // transpose tiles read back before the next windows are built
     }
   }
   return true;

@@ -1,10 +1,10 @@
 // pattern_kernels.cuh -- the pattern-tile kernels (pattern_body.cuh) and their
 // launch templates: the one-unit-per-CTA kernel of dd_run and the persistent
 // kernel of dd_batch_run, for every tk::kPatShapes entry that serves a kind.
-// Included only by the per-kind translation units fwd_pattern_k*.cu, each of
-// which defines the launchers of its kind with DD_PATTERN_KIND, so that the
-// kinds compile in parallel; fwd_pattern.cu and fwd_pattern_batch.cu
-// dispatch on the kind.
+// Included only by the per-kind translation units fwd_pattern_k*.cu (one-unit
+// kernels) and fwd_pattern_batch_k*.cu (persistent kernels), each of which
+// defines one kind's launcher, so that they compile in parallel;
+// fwd_pattern.cu and fwd_pattern_batch.cu dispatch on the kind.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,11 +19,11 @@
 namespace dd {
 namespace tk {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   using namespace pattern;
-  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF, MERGE>(smem, p.lraw);
+  const PSmem sm = pat_layout<NW, NC, PAIRS, DBUF>(smem, p.lraw);
   if (threadIdx.x == 0) {
     mbar_init(sm.bar_base, NC + 1);
     mbar_init(sm.bar_base + 8, NC + 1);
@@ -32,19 +32,18 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
   __syncthreads();
   const int blk = blockIdx.x % p.n_blocks;
   const int64_t tile = blockIdx.x / p.n_blocks + p.tile0;
-  if constexpr (MERGE) pat_body_merge<H, NW, NC, AMAX>(p, sm, blk, tile);
-  else pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blk, tile);
+  pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blk, tile);
 }
 
 }  // namespace tk
 
 namespace pattern_launch {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool MERGE>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
-  const size_t smem = tk::pat_smem_bytes(
-      KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX, MERGE}, prm.lp, prm.nv);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX, MERGE>;
+  const size_t smem =
+      tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX}, prm.lp);
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -58,7 +57,7 @@ int launch_pattern_index(const tk::TileParams& prm, int64_t grid, cudaStream_t s
   if constexpr (!tk::pat_shape_serves(s, KIND)) {
     return static_cast<int>(cudaErrorInvalidValue);  // the planner never picks it
   } else {
-    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax, s.merge>(
+    return launch_pattern_shape<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(
         prm, grid, st);
   }
 }
@@ -106,7 +105,7 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     // a copy in registers would crowd out the accumulators.
     const TileParams& p = static_cast<const PatBatchJob* __restrict__>(b.jobs)[item.job].p;
     const pattern::PSmem sm =
-        pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf, s.merge>(smem, p.lraw);
+        pattern::pat_layout<s.warps, s.nc, s.pairs, s.dbuf>(smem, p.lraw);
     __syncthreads();  // every thread has read item_slot; the previous item is done
     if (threadIdx.x == 0) {
       // Stage phases restart at 0 for every item: re-initialise the barriers
@@ -121,12 +120,8 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     }
     barriers_valid = true;
     __syncthreads();
-    bool ok;
-    if constexpr (s.merge)
-      ok = pattern::pat_body_merge<s.h, s.warps, s.nc, s.amax>(p, sm, item.blk, item.tile);
-    else
-      ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(p, sm, item.blk,
-                                                                               item.tile);
+    const bool ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(
+        p, sm, item.blk, item.tile);
     if (!ok) break;
   }
 }
@@ -162,13 +157,18 @@ int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t sm
 
 }  // namespace dd
 
-// The launchers of one kind (declared in dd_internal.h).
-#define DD_PATTERN_KIND(K)                                                                  \
+// The launchers of one kind (declared in dd_internal.h): the one-unit kernel
+// (DD_PATTERN_KIND_FORWARD) and the persistent batch kernel
+// (DD_PATTERN_KIND_BATCH), each in a translation unit of its own.
+#define DD_PATTERN_KIND_FORWARD(K)                                                          \
   namespace dd {                                                                            \
   int pattern_forward_##K(int shape, const tk::TileParams& prm, int64_t grid, void* st) {   \
     return pattern_launch::launch_pattern_kind<tk::K>(shape, prm, grid,                    \
                                                       static_cast<cudaStream_t>(st));       \
   }                                                                                         \
+  }
+#define DD_PATTERN_KIND_BATCH(K)                                                            \
+  namespace dd {                                                                            \
   int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem, \
                         void* st) {                                                         \
     return pattern_launch::launch_kind<tk::K>(                                              \

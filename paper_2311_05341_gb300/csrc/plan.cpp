@@ -225,174 +225,6 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
   return true;
 }
 
-// Channel-class tables of the merged pattern tile (layout in fwd_tiled.h): the
-// base shifts s(c, d0) as for the pair tiles, then one chunk per (DM block,
-// stage).  Per sub-block, the stage's channels are grouped by their shift
-// increments over the sub-block's DMs (DMs past the range's end clamped to
-// its last, as everywhere); a class's reference channel is its member with
-// the smallest window offset at the sub-block's first DM, and members more
-// than kMergeMaxDelta words beyond it start classes of their own.  The
-// classes of the sub-blocks are spread over rounds of at most nv windows,
-// each sub-block's share divided evenly among the rounds.  Each warp lists
-// the reference channels of its sub-block's classes of each round as pairs of
-// equal pattern and singles (entries as in build_pair_tables).  Returns false
-// if some offset, increment or count does not fit.
-bool build_merge_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::PatShape& ps,
-                        int32_t lp, int nv, std::vector<unsigned char>& out, size_t* chunk_off,
-                        int32_t* n_blocks_out) {
-  using namespace tk;
-  const int dm_cta = kPatDr * ps.warps;
-  const int sub_dm = kPatDr * kMergeSubWarps;
-  const int n_sub = ps.warps / kMergeSubWarps;
-  const int32_t align = align_samples(kind, rp.r.bin);
-  const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
-  const int n_st = (n_chan + ps.nc - 1) / ps.nc;
-  const size_t cb = static_cast<size_t>(merge_chunk_bytes(ps.warps, ps.nc));
-  const int item_off = merge_item_off(ps.warps, ps.nc);
-  const size_t bases_bytes = align_up(static_cast<size_t>(n_blocks) * n_chan * 4, 256);
-  const int32_t lraw = pat_raw_bytes(kind, rp.r.bin, ps, lp);
-  if (ps.warps % kMergeSubWarps != 0 || ps.warps > kPairMaxWarps) return false;
-  out.assign(bases_bytes + static_cast<size_t>(n_blocks) * n_st * cb, 0);
-  auto shift = [&](int64_t d, int32_t c) {
-    d = std::min<int64_t>(d, rp.n_dm - 1);
-    return rp.shifts[static_cast<size_t>(d) * n_chan + c];
-  };
-  struct Cls {
-    int ref;                               // staged channel
-    std::vector<std::pair<int, int>> mem;  // (staged channel, delta)
-  };
-  std::vector<std::vector<Cls>> cls(n_sub);
-  std::vector<std::vector<uint32_t>> by_pat(kPatterns);
-  std::map<std::vector<int32_t>, std::vector<int>> groups;
-  std::vector<int32_t> key(sub_dm - 1);
-  std::vector<int> order;
-  for (int64_t b = 0; b < n_blocks; ++b) {
-    const int64_t d0 = b * dm_cta;
-    int32_t* bases = reinterpret_cast<int32_t*>(out.data()) + b * n_chan;
-    for (int32_t c = 0; c < n_chan; ++c) bases[c] = shift(d0, c);
-    auto offset = [&](int64_t d, int32_t c) { return shift(d, c) - bases[c] + bases[c] % align; };
-    for (int st = 0; st < n_st; ++st) {
-      unsigned char* chunk = out.data() + bases_bytes + (static_cast<size_t>(b) * n_st + st) * cb;
-      const int c0 = st * ps.nc, nc = std::min(ps.nc, n_chan - c0);
-      int total = 0;
-      for (int j = 0; j < n_sub; ++j) {
-        const int64_t dj = d0 + static_cast<int64_t>(j) * sub_dm;
-        groups.clear();
-        order.clear();
-        for (int k = 0; k < nc; ++k) {
-          const int32_t c = c0 + k;
-          for (int i = 1; i < sub_dm; ++i) key[i - 1] = shift(dj + i, c) - shift(dj, c);
-          auto& g = groups[key];
-          if (g.empty()) order.push_back(k);
-          g.push_back(k);
-        }
-        cls[j].clear();
-        for (int k_first : order) {
-          const int32_t c = c0 + k_first;
-          for (int i = 1; i < sub_dm; ++i) key[i - 1] = shift(dj + i, c) - shift(dj, c);
-          std::vector<int> ks = groups[key];
-          std::stable_sort(ks.begin(), ks.end(), [&](int x, int y) {
-            return offset(dj, c0 + x) < offset(dj, c0 + y);
-          });
-          size_t i = 0;
-          while (i < ks.size()) {
-            Cls cl;
-            cl.ref = ks[i];
-            const int32_t o_ref = offset(dj, c0 + ks[i]);
-            for (; i < ks.size(); ++i) {
-              const int32_t delta = offset(dj, c0 + ks[i]) - o_ref;
-              if (delta > kMergeMaxDelta) break;
-              cl.mem.push_back({ks[i], delta});
-            }
-            cls[j].push_back(std::move(cl));
-          }
-        }
-        total += static_cast<int>(cls[j].size());
-      }
-      // Rounds: the fewest whose even split of every sub-block fits nv slots.
-      int rounds = (total + nv - 1) / nv;
-      auto lo_of = [&](int j, int r, int R) {
-        return static_cast<int>(cls[j].size()) * r / R;
-      };
-      for (;; ++rounds) {
-        if (rounds > kMergeMaxRounds) return false;
-        bool fits = true;
-        for (int r = 0; r < rounds && fits; ++r) {
-          int v = 0;
-          for (int j = 0; j < n_sub; ++j) v += lo_of(j, r + 1, rounds) - lo_of(j, r, rounds);
-          fits = v <= nv;
-        }
-        if (fits) break;
-      }
-      chunk[0] = static_cast<unsigned char>(rounds);
-      uint16_t* wins = reinterpret_cast<uint16_t*>(chunk + kMergeWinOff);
-      uint32_t* mem = reinterpret_cast<uint32_t*>(chunk + kMergeMemOff);
-      PairItem* items = reinterpret_cast<PairItem*>(chunk + item_off);
-      int n_mem = 0;
-      std::vector<int> item_n(ps.warps, 0);
-      for (int r = 0; r < rounds; ++r) {
-        int v = 0;
-        for (int j = 0; j < n_sub; ++j) {
-          const int lo = lo_of(j, r, rounds), hi = lo_of(j, r + 1, rounds);
-          const int v_first = v;
-          for (int i = lo; i < hi; ++i, ++v) {
-            const Cls& cl = cls[j][i];
-            if (n_mem + static_cast<int>(cl.mem.size()) > merge_max_members(ps.warps, ps.nc))
-              return false;
-            wins[r * kMergeMaxNv + v] =
-                static_cast<uint16_t>(n_mem | static_cast<int>(cl.mem.size()) << 8);
-            for (const auto& m : cl.mem) {
-              const uint32_t off = static_cast<uint32_t>(m.first) * static_cast<uint32_t>(lraw) +
-                                   (static_cast<uint32_t>(m.second) & ~3u);
-              if (off > 0xffffu) return false;
-              const uint32_t sel = 0x3210u + 0x1111u * (static_cast<uint32_t>(m.second) & 3u);
-              mem[n_mem++] = off | sel << 16;
-            }
-          }
-          // The sub-block's warps: pairs of equal pattern, then singles.
-          for (int w = j * kMergeSubWarps; w < (j + 1) * kMergeSubWarps; ++w) {
-            for (auto& q : by_pat) q.clear();
-            const int64_t dw = d0 + static_cast<int64_t>(kPatDr) * w;
-            const int n_real = static_cast<int>(std::min<int64_t>(kPatDr, rp.n_dm - dw));
-            for (int i = lo; i < hi; ++i) {
-              const int32_t c = c0 + cls[j][i].ref;
-              const int32_t off = offset(dw, c);
-              if (off < 0 || off > static_cast<int32_t>(kPatOffMask)) return false;
-              int32_t s_dm[kPatDr];
-              for (int t = 0; t < kPatDr; ++t) s_dm[t] = shift(dw + t, c);
-              uint32_t pat = 0;
-              if (!pattern_of(s_dm, n_real, ps.amax, &pat)) return false;
-              const uint32_t a = static_cast<uint32_t>(v_first + i - lo) * lp +
-                                 static_cast<uint32_t>(off);
-              if (a > 0xffffu) return false;
-              by_pat[pat].push_back(a);
-            }
-            PairItem* wi = items + static_cast<size_t>(w) * ps.nc;
-            int& n = item_n[w];
-            const int n0 = n;
-            for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat) {
-              const auto& q = by_pat[pat];
-              for (size_t i = 0; i + 1 < q.size(); i += 2)
-                wi[n++] = PairItem{q[i] | q[i + 1] << 16, pat};
-            }
-            const int n_pairs = n - n0;
-            for (uint32_t pat = 0; pat < static_cast<uint32_t>(kPatterns); ++pat)
-              if (by_pat[pat].size() % 2) wi[n++] = PairItem{by_pat[pat].back(), pat};
-            if (n > ps.nc) return false;
-            chunk[kMergeCntOff + r * kPairCountBytes + w] = static_cast<unsigned char>(n_pairs);
-            chunk[kMergeCntOff + r * kPairCountBytes + kPairMaxWarps + w] =
-                static_cast<unsigned char>(n - n0 - n_pairs);
-          }
-        }
-        chunk[16 + r] = static_cast<unsigned char>(v);
-      }
-    }
-  }
-  *chunk_off = bases_bytes;
-  *n_blocks_out = static_cast<int32_t>(n_blocks);
-  return true;
-}
-
 // Multiply-high constants for exact u / d with u < limit (verified exhaustively).
 bool division_magic(uint32_t d, uint32_t limit, uint32_t* magic, int32_t* shift) {
   int32_t s = 0;
@@ -438,7 +270,6 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
   rp.tile_shape = 0;
   rp.tile_chunk_off = 0;
   rp.tile_chunk_bytes = 0;
-  rp.tile_nv = 0;
   rp.tile_kind = kind;
   rp.tile_n_blocks = n_blocks;
   rp.tile_lp = lp;
@@ -453,26 +284,18 @@ bool try_tile_shape(RangePlan& rp, int32_t n_chan, int kind, const tk::Shape& sh
 bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   const tk::PatShape& ps = tk::kPatShapes[shape];
   if (!tk::pat_shape_serves(ps, kind)) return false;
-  if (ps.merge && rp.r.bin != 1) return false;
   const int32_t span = block_span(rp, n_chan, tk::kPatDr * ps.warps);
   const int32_t lp = tk::pat_window_words(kind, rp.r.bin, ps.h, span);
-  const int nv = ps.merge ? tk::pat_merge_nv(kind, rp.r.bin, ps, lp, 227 * 1024) : 0;
-  if (ps.merge && nv < tk::kMergeMinNv) return false;
-  if (tk::pat_smem_bytes(kind, rp.r.bin, ps, lp, nv) > 227 * 1024) return false;
+  if (tk::pat_smem_bytes(kind, rp.r.bin, ps, lp) > 227 * 1024) return false;
   uint32_t magic = 0;
   int32_t shift = 0;
-  // Merged tiles divide by lp / 4 over a round's window units (up to nv windows).
-  const int32_t div_windows = std::max(ps.nc, nv);
-  if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(div_windows * lp / 4),
+  if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(ps.nc * lp / 4),
                       &magic, &shift))
     return false;
   std::vector<unsigned char> tables;
   int32_t n_blocks = 0;
   size_t chunk_off = 0;
-  if (ps.merge) {
-    if (!build_merge_tables(rp, n_chan, kind, ps, lp, nv, tables, &chunk_off, &n_blocks))
-      return false;
-  } else if (ps.pairs) {
+  if (ps.pairs) {
     if (!build_pair_tables(rp, n_chan, kind, ps, lp, tables, &chunk_off, &n_blocks)) return false;
   } else {
     std::vector<tk::PRec> recs;
@@ -492,7 +315,6 @@ bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   rp.tile_units_shift = shift;
   rp.tile_chunk_off = chunk_off;
   rp.tile_chunk_bytes = tk::pat_chunk_bytes(ps);
-  rp.tile_nv = nv;
   rp.tile_recs = std::move(tables);
   return true;
 }
@@ -515,7 +337,6 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_kind = 0;
   rp.tile_chunk_off = 0;
   rp.tile_chunk_bytes = 0;
-  rp.tile_nv = 0;
   rp.tile_recs.clear();
   // Packed input at bin 1: uint8 and 4-bit share the paired word format,
   // uint16 is widened to one sample per word.
@@ -530,21 +351,20 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
                                                       : static_cast<int>(dtype);
   if (rp.tile_request == DD_TILE_PACKED && !tk::packed_copy_kind(kind)) return;
   if (!tk::bin_supported(kind, rp.r.bin)) return;
-  if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == DD_TILE_MERGE ||
-      rp.tile_request == DD_TILE_PACKED || rp.tile_request == 0) {
-    // Channel classes only on request: on GB300 the paper-scale plan ran
-    // 237 ms with them against 196 ms without (the window building costs more
-    // than the channel adds it saves).
+  if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == DD_TILE_PACKED ||
+      rp.tile_request == 0) {
     // Float32 at bin 1 first tries the direct kind (the input words are the
-    // window words: no unpacking, two staging buffers).
-    if (kind == tk::kF32 && rp.r.bin == 1 && rp.tile_request != DD_TILE_MERGE)
-      for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
-        if (!tk::kPatShapes[i].merge && try_pattern_shape(rp, n_chan, tk::kF32D, i)) return;
-    for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i) {
-      const bool merge = tk::kPatShapes[i].merge;
-      if (merge != (rp.tile_request == DD_TILE_MERGE)) continue;
-      if (try_pattern_shape(rp, n_chan, kind, i)) return;
-    }
+    // window words: no unpacking, two staging buffers).  An explicit shape
+    // (the autotuner's) is the only one tried; otherwise the first entry
+    // before the tuning entries that serves and fits.
+    auto candidate = [&](int i) {
+      return rp.shape_request >= 0 ? i == rp.shape_request : i < tk::kPatTuneFirst;
+    };
+    if (kind == tk::kF32 && rp.r.bin == 1)
+      for (int i = 0; i < tk::kNumPatShapes; ++i)
+        if (candidate(i) && try_pattern_shape(rp, n_chan, tk::kF32D, i)) return;
+    for (int i = 0; i < tk::kNumPatShapes; ++i)
+      if (candidate(i) && try_pattern_shape(rp, n_chan, kind, i)) return;
     if (rp.tile_request != 0) return;
   }
   if (rp.tile_request > 0) {
@@ -588,10 +408,8 @@ void build_adjoint_range(const RangePlan& rp, int32_t n_chan, RangePlan* ar) {
   // cotangent rows into pairs anyway), then plain floats.
   for (int kind : {static_cast<int>(tk::kF32P), static_cast<int>(tk::kF32D),
                    static_cast<int>(tk::kF32)})
-    for (int i = 0; i < static_cast<int>(std::size(tk::kPatShapes)); ++i)
-      if (!tk::kPatShapes[i].merge &&
-          try_pattern_shape(*ar, static_cast<int32_t>(n_dm), kind, i))
-        return;
+    for (int i = 0; i < tk::kNumPatShapes; ++i)
+      if (try_pattern_shape(*ar, static_cast<int32_t>(n_dm), kind, i)) return;
 }
 
 void layout_workspace(dd_plan_s* p) {
@@ -733,13 +551,15 @@ dd_status build_plan(dd_plan_s* p) {
   return DD_OK;
 }
 
-bool retile_range(dd_plan_s* p, size_t range, int32_t request) {
+bool retile_range(dd_plan_s* p, size_t range, int32_t request, int32_t shape_request) {
   RangePlan& rp = p->ranges[range];
-  const int32_t old = rp.tile_request;
+  const int32_t old = rp.tile_request, old_shape = rp.shape_request;
   rp.tile_request = request;
+  rp.shape_request = shape_request;
   choose_tile(rp, p->n_chan, p->dtype);
-  if (request > 0 && !rp.tile_ok) {
+  if ((request > 0 || shape_request >= 0) && !rp.tile_ok) {
     rp.tile_request = old;
+    rp.shape_request = old_shape;
     choose_tile(rp, p->n_chan, p->dtype);
     layout_workspace(p);
     return false;

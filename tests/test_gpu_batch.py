@@ -70,7 +70,13 @@ def _check_oracle(b, host, planes):
 def test_batch_equals_alone_and_oracle(autotune):
     runner = ddb.BatchRunner(_beams(), autotune=autotune, graph=True)
     assert runner.n_jobs == 6
-    assert all(dr in ddb.BATCH_SHAPES for shp in runner.shapes for dr in shp)
+    if autotune:
+        # (tile, shape) per range: the pattern or packed tile in a table shape,
+        # or an offset tile.
+        assert all(t[0] in ("pattern", "packed", 4, 2, 1) for shp in runner.shapes
+                   for t in shp)
+    else:
+        assert all(dr in ddb.BATCH_SHAPES for shp in runner.shapes for dr in shp)
     if not autotune:
         # The first feasible tile: the pattern tile, except for the steep
         # 96-channel float beam (offset tile): both persistent families run.
@@ -138,19 +144,27 @@ def test_batch_with_4bit_beams():
         _check_oracle(b, hosts[i], runner.planes(i))
 
 
-def test_batch_with_channel_class_tiles():
-    """uint8 beams on the pattern tile with channel classes (opt-in) in one
-    batch with a plain pattern beam: the merged persistent kernel equals the
-    per-beam launch and the oracle."""
-    beams = [ddb.BeamSpec(channel_freqs(1520.0, 6.0, 300), 1520.0, 64e-6,
+def test_batch_packed_and_shape_tiles():
+    """Beams on the packed tile (uint8, uint16 and float pairs, each packed by
+    the batch run) and on explicit pattern shapes of the tuning table, in one
+    batch: batch == alone == oracle."""
+    from paper_2311_05341_gb300 import tile_shapes
+    shapes = tile_shapes()
+    tune = [i for i, s in enumerate(shapes) if not s["automatic"] and s["channel_pairs"]]
+    f2 = [i for i, s in enumerate(shapes) if s["float_pairs"]]
+    beams = [ddb.BeamSpec(channel_freqs(1520.0, 310.0, 256), 1520.0, 64e-6,
                           [(0.0, 25.6, 0.1, 1)], "u8", 9000),
-             ddb.BeamSpec(channel_freqs(1670.0, 10.0, 257), 1670.0, 64e-6,
-                          [(0.0, 12.8, 0.1, 1), (12.8, 25.6, 0.2, 1)], "u8", 7001),
-             ddb.BeamSpec(channel_freqs(1400.0, 300.0, 96), 1400.0, 64e-6,
-                          [(0.0, 6.4, 0.05, 1)], "u8", 6000)]
-    runner = ddb.BatchRunner(beams, autotune=False, graph=True,
-                             tiles=[["merge"], ["merge", "merge"], ["pattern"]])
-    hosts = _fill(runner, 950)
+             ddb.BeamSpec(channel_freqs(1670.0, 320.0, 300), 1670.0, 54.6e-6,
+                          [(0.0, 19.2, 0.2, 1)], "u16", 7001),
+             ddb.BeamSpec(channel_freqs(400.0, 100.0, 96), 400.0, 327.68e-6,
+                          [(0.0, 3.2, 0.05, 1)], "f32", 5000),
+             ddb.BeamSpec(channel_freqs(1400.0, 300.0, 130), 1400.0, 64e-6,
+                          [(0.0, 6.4, 0.05, 1), (6.4, 12.8, 0.1, 2)], "u8", 6000)]
+    tiles = [[("packed", -1)], [("packed", tune[0])], [("packed", f2[-1])],
+             [("pattern", tune[1]), ("pattern", -1)]]
+    runner = ddb.BatchRunner(beams, autotune=False, graph=True, tiles=tiles)
+    assert runner.n_launches >= 3 + 3  # three packing launches and the persistent ones
+    hosts = _fill(runner, 990)
     runner.run()
     torch.cuda.synchronize()
     runner.status()

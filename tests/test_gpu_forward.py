@@ -13,7 +13,6 @@ import pytest
 
 import oracle
 import paper_2311_05341_gb300 as dd
-from paper_2311_05341_gb300._lib import DD_TILE_MERGE as TILE_MERGE
 from paper_2311_05341_gb300._lib import DD_TILE_PACKED as TILE_PACKED
 from paper_2311_05341_gb300._lib import DD_TILE_PATTERN as TILE_PATTERN
 from synth import workloads, channel_freqs, filterbank
@@ -137,15 +136,14 @@ def test_tiled_full_planes_every_shape(dtype, seed):
     ref_abs = oracle.forward(x, b.freqs, b.f_high, b.t_samp, b.ranges, take_abs=True)
     xd = padded_device(x)
     # Steps of at most 1.7 samples keep every per-DM increment in {0, 1, 2}:
-    # the pattern tile serves all these plans too (uint8: also with channel
-    # classes).
-    tiles = (8, 6, 4, 2, 1, "pattern") + (("merge", "packed") if dtype == "u8" else
-                                           ("packed",) if dtype == "f32" else ())
+    # the pattern tile serves all these plans too (uint8 and float32: also on
+    # the packed copy).
+    tiles = (8, 6, 4, 2, 1, "pattern") + (("packed",) if dtype in ("u8", "f32") else ())
     for dms in tiles:
         plan = dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, dtype)
         plan.set_tile(0, dms)
         info = plan.info(b.n_samp)
-        code = {"pattern": TILE_PATTERN, "merge": TILE_MERGE, "packed": TILE_PACKED}.get(dms, dms)
+        code = {"pattern": TILE_PATTERN, "packed": TILE_PACKED}.get(dms, dms)
         assert info["kernel"] == ["tiled"] and info["tile_dms"] == [code]
         got = plan.run(xd, n_samp=b.n_samp)[0].cpu().numpy()
         if dtype == "f32":
@@ -175,8 +173,7 @@ def test_pattern_steep_plans(dtype, seed):
     ref = oracle.forward(x, freqs, f_high, 64e-6, [r])[0]
     ref_abs = oracle.forward(x, freqs, f_high, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
-    for tile in ("pattern", 1) + (("merge", "packed") if dtype == "u8" else
-                                  ("packed",) if dtype == "f32" else ()):
+    for tile in ("pattern", 1) + (("packed",) if dtype in ("u8", "f32") else ()):
         plan = dd.Plan(freqs, f_high, 64e-6, [r], dtype)
         plan.set_tile(0, tile)
         got = plan.run(xd, n_samp=n_samp)[0].cpu().numpy()
@@ -202,7 +199,7 @@ def test_tiled_decimation_every_shape(dtype, b):
     ref_abs = oracle.forward(x, freqs, 1400.0, 64e-6, [r], take_abs=True)[0]
     xd = padded_device(x)
     ran = 0
-    for dms in (8, 6, 4, 2, 1, "pattern", "merge"):
+    for dms in (8, 6, 4, 2, 1, "pattern"):
         plan = dd.Plan(freqs, 1400.0, 64e-6, [r], dtype)
         try:
             plan.set_tile(0, dms)

@@ -191,10 +191,8 @@ def test_pattern_tile_selection():
     assert info["kernel"] == ["tiled"] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
     # Per-warp pair lists against 64-byte offset records: other table sizes.
     assert info["workspace_bytes"] != ws_offset
-    plan.set_tile(0, "merge")
-    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_MERGE]
     plan.set_tile(0, 6)
-    plan.set_tile(0, 0)  # automatic: the pattern tile (channel classes only on request)
+    plan.set_tile(0, 0)  # automatic: the pattern tile
     assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
     tiny = workloads.tiny_u8()  # 8 samples per DM step at the lowest channel
     plan = dd.Plan(tiny.freqs, tiny.f_high, tiny.t_samp, tiny.ranges, "u8", upload=False)
@@ -203,29 +201,53 @@ def test_pattern_tile_selection():
     assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
     assert plan.info(tiny.n_samp)["tile_dms"] == [2]
     with pytest.raises(dd.DDError) as ei:
-        plan.set_tile(0, "merge")
-    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
-    with pytest.raises(dd.DDError) as ei:
         plan.set_tile(0, 3)
     assert ei.value.status == _lib.DD_ERR_INVALID_ARG
 
 
-def test_merge_tile_selection():
-    """Channel classes serve uint8 at bin 1 only; other kinds and bins keep the
-    pattern tile."""
+def test_tile_shape_table_and_explicit_shapes():
+    """dd_tile_shapes lists the pattern shapes (the automatic ones first, then
+    the tuning entries); dd_plan_set_tile_shape puts a range on one of them,
+    refuses shapes that cannot serve it (keeping the previous choice) and bad
+    arguments; dd_plan_info reports the shape in use."""
+    shapes = dd.tile_shapes()
+    assert len(shapes) >= 12
+    auto = [s["automatic"] for s in shapes]
+    assert auto == sorted(auto, reverse=True) and 0 in auto and 1 in auto
+    assert all(s["dms_per_lane"] == 4 and s["words_per_lane"] % 2 == 1 for s in shapes)
     paper = workloads.paper_u8()
-    for dtype in ("u16", "f32", "u4"):
-        plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, dtype,
-                       upload=False)
-        assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN], dtype
-        with pytest.raises(dd.DDError) as ei:
-            plan.set_tile(0, "merge")
-        assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
-    binned = [(0.0, 40.0, 0.2, 2)]
-    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, binned, "u8", upload=False)
-    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PATTERN]
-    with pytest.raises(dd.DDError):
-        plan.set_tile(0, "merge")
+    paper.n_chan, paper.ranges = 512, [(0.0, 51.2, 0.1, 1)]
+    plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
+    first = plan.info(paper.n_samp)["tile_shape"][0]
+    assert shapes[first]["automatic"] and shapes[first]["channel_pairs"]
+    served = 0
+    for i, sh in enumerate(shapes):
+        if sh["channel_pairs"] and not sh["float_pairs"]:
+            plan.set_tile_shape(0, "pattern", i)
+            info = plan.info(paper.n_samp)
+            assert info["tile_shape"] == [i] and info["tile_dms"] == [_lib.DD_TILE_PATTERN]
+            served += 1
+        else:
+            with pytest.raises(dd.DDError) as ei:
+                plan.set_tile_shape(0, "pattern", i)
+            assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+            assert plan.info(paper.n_samp)["tile_shape"] != [i]
+    assert served >= 5
+    plan.set_tile_shape(0, "packed", -1)
+    assert plan.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PACKED]
+    f2 = [i for i, s in enumerate(shapes) if s["float_pairs"]]
+    f32 = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "f32", upload=False)
+    for i in f2:
+        f32.set_tile_shape(0, "packed", i)
+        assert f32.info(paper.n_samp)["tile_shape"] == [i]
+    lib = _lib.load()
+    assert lib.dd_plan_set_tile_shape(plan.handle, 0, 6, 0) == _lib.DD_ERR_INVALID_ARG
+    assert lib.dd_plan_set_tile_shape(plan.handle, 0, _lib.DD_TILE_PATTERN, len(shapes)) == \
+        _lib.DD_ERR_INVALID_ARG
+    assert lib.dd_plan_set_tile_shape(plan.handle, 5, _lib.DD_TILE_PATTERN, 0) == \
+        _lib.DD_ERR_INVALID_ARG
+    plan.set_tile(0, 6)
+    assert plan.info(paper.n_samp)["tile_shape"] == [-1]
 
 
 def test_u4_plan_selection_and_refusals():
