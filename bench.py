@@ -33,11 +33,21 @@ import numpy as np  # noqa: E402
 
 METRIC = "DM-trials x samples / s"
 SM_MAX_MHZ = 2070.0   # GB300 maximum SM clock
-HBM_GBS = 6644.1      # measured copy bandwidth of the GB300s
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu), keyed by
-# workload, raw samples and tile; valid only for the kernel build it was taken
-# on (profiles/fwd_pattern_u8_8192ch.md).
-TRAFFIC = {("paper_u8", 262144, (0x104,)): 13.41e9 + 63.07e9}
+def _measured_hbm_gbs(default=6800.0):
+    """The machine's measured HBM copy bandwidth (MEASURED_PEAKS.json beside this
+    file, written per machine pool), else the recipe's 6.8 TB/s fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return default
+
+
+HBM_GBS = _measured_hbm_gbs()
+# dram__bytes_read.sum + dram__bytes_write.sum of one transform launch (ncu),
+# keyed by workload, raw samples and tile; valid only for the kernel build it
+# was taken on (profiles/fwd_pattern_u8_8192ch.md).
+TRAFFIC = {("paper_u8", 262144, (0x106,)): 34.73e9 + 66.41e9}
 UNIT = "DM*samples/s"
 
 
@@ -763,6 +773,7 @@ def diff_result(args):
     the autograd Function), CUDA events, against the float add roofline."""
     import torch
     import paper_2311_05341_gb300 as dd
+    from paper_2311_05341_gb300 import _lib
     from synth import workloads
 
     beam = _workload("diff_f32")
@@ -775,10 +786,31 @@ def diff_result(args):
     out = plan.empty_output(beam.n_samp)
     scratch = torch.empty(plan.input_scratch_bytes(beam.n_samp), dtype=torch.uint8, device="cuda")
     sp = torch.cuda.current_stream().cuda_stream
+    lib = plan._lib
+    stream = torch.cuda.current_stream()
+
+    def pack():
+        _lib.check(lib.dd_pack_input(plan.handle, x.data_ptr(), x.stride(0), beam.n_samp,
+                                     scratch.data_ptr(), scratch.numel(), sp))
+
+    def transform():
+        _lib.check(lib.dd_run_packed(plan.handle, x.data_ptr(), x.stride(0), beam.n_samp,
+                                     out.data_ptr(), scratch.data_ptr(), scratch.numel(), sp))
+
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    t_fwd = _timed(lambda: plan.run_raw(x.data_ptr(), x.stride(0), beam.n_samp, out.data_ptr(),
-                                        sp, scratch=scratch), args.steps, args.warmup)
+    t_fwd = _timed(lambda: (pack(), transform()), args.steps, args.warmup)
+    # The transform launch alone (CUDA events around it, the packing outside).
+    ks = []
+    for _ in range(args.steps):
+        pack()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        transform()
+        e1.record(stream)
+        ks.append((e0, e1))
+    torch.cuda.synchronize()
+    t_kern = sum(a.elapsed_time(b) for a, b in ks) / len(ks) / 1e3
     adj = _adjoint_timing(args, plan, x, info, beam, torch.cuda.current_stream())
     clk = clocks.stop()
     dm_samples = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
@@ -787,7 +819,8 @@ def diff_result(args):
     adds = dm_samples * beam.n_chan
     res = {"workload": _describe(beam), "tile": "packed (float pairs)",
            "forward": {"ms": t_fwd * 1e3, "dm_samples_per_s": dm_samples / t_fwd,
-                       "adds_per_s": adds / t_fwd, "frac": adds / t_fwd / peak},
+                       "adds_per_s": adds / t_fwd, "frac_with_packing": adds / t_fwd / peak,
+                       "kernel_ms": t_kern * 1e3, "frac": adds / t_kern / peak},
            "adjoint": {**adj["adjoint"], "frac": adds / (adj["adjoint"]["ms"] / 1e3) / peak,
                        "kernel": info["adjoint_kernel"]},
            "train_step": adj["train_step"],

@@ -520,10 +520,12 @@ dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
                                 const int64_t* in_row_stride, void* const* d_out,
                                 void* const* d_scratch, const size_t* scratch_bytes,
                                 void* stream);
-/* Persistent launches over all items of a bound batch (a counter reset, the
+/* Persistent launches over all items of a bound batch: a counter reset, the
  * packing launches of plans bound with scratch, and one kernel launch per tile
- * family present, in order on `stream`; all can be captured in a CUDA
- * graph). */
+ * family present.  The families run on concurrent lanes (the batch's own
+ * streams, created by dd_batch_upload, forked from `stream` after the reset
+ * and joined into it at the end), each lane packing the inputs it reads
+ * first; all of it can be captured in a CUDA graph from `stream`. */
 dd_status dd_batch_run(dd_batch batch, void* stream);
 /* DD_ERR_TIMEOUT if a bounded device wait of any batch plan gave up since the
  * last check (clears the flags); synchronises `stream`. */

@@ -30,6 +30,49 @@ dd_status cuda_fail(int err, const char* what) {
   return DD_ERR_CUDA;
 }
 
+std::vector<PackedCopy> packed_copies(const dd_plan_s* p, int64_t n_samp,
+                                      std::vector<int32_t>* range_copy) {
+  std::vector<PackedCopy> copies;
+  if (range_copy) range_copy->assign(p->ranges.size(), -1);
+  size_t off = 0;
+  for (size_t r = 0; r < p->ranges.size(); ++r) {
+    const RangePlan& rp = p->ranges[r];
+    if (!(rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))) continue;
+    const int32_t pair = pack_pair(rp), bin = rp.r.bin;
+    size_t k = 0;
+    while (k < copies.size() && !(copies[k].pair == pair && copies[k].bin == bin)) ++k;
+    if (k == copies.size()) {
+      PackedCopy pc{};
+      pc.pair = pair;
+      pc.bin = bin;
+      pc.stride = (std::max<int64_t>(n_samp / bin, 1) + 3) / 4 * 4;
+      pc.offset = off;
+      pc.bytes = static_cast<size_t>(p->n_chan) * static_cast<size_t>(pc.stride) *
+                 packed_word_bytes(p->dtype);
+      off = (off + pc.bytes + 255) / 256 * 256;
+      copies.push_back(pc);
+    }
+    if (range_copy) (*range_copy)[r] = static_cast<int32_t>(k);
+  }
+  return copies;
+}
+
+size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
+  const auto copies = packed_copies(p, n_samp, nullptr);
+  return copies.empty() ? 0 : copies.back().offset + copies.back().bytes;
+}
+
+int launch_pack_copy(const dd_plan_s* p, const PackedCopy& pc, const void* d_in, int64_t in_stride,
+                     int64_t n_samp, void* d_scratch, void* stream) {
+  unsigned char* dst = static_cast<unsigned char*>(d_scratch) + pc.offset;
+  const int64_t in_bytes = static_cast<int64_t>(dtype_row_bytes(p->dtype, in_stride));
+  if (pc.bin > 1)
+    return launch_pack_pairs_binned(d_in, in_bytes, p->n_chan, n_samp, pc.bin, dst, pc.stride,
+                                    pc.pair, stream);
+  return launch_pack_pairs(d_in, in_bytes, p->n_chan, n_samp, dst, pc.stride, pc.pair, 0,
+                           pc.stride, pack_source(p->dtype), stream);
+}
+
 namespace {
 
 size_t elem_size(dd_dtype t) { return (t == DD_U8 || t == DD_U4) ? 1 : (t == DD_U16 ? 2 : 4); }
@@ -148,18 +191,6 @@ void free_host_pipe(dd_plan_s* p) {
 
 namespace {
 
-// Outputs [t_begin, t_end) of one range on its kernel.
-// Bytes of the packed copy (packed-copy kinds read it), 0 without such a range.
-size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
-  for (const auto& rp : p->ranges)
-    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))
-      return static_cast<size_t>(p->n_chan) * static_cast<size_t>((n_samp + 3) / 4 * 4) *
-             packed_word_bytes(p->dtype);
-  return 0;
-}
-
-// Ranges on DD_TILE_PACKED need the packed copy, which only dd_run_scratch makes.
-bool has_packed_range(const dd_plan_s* p) { return packed_input_bytes(p, 1) > 0; }
 
 int launch_range(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
                  int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
@@ -397,8 +428,13 @@ static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stri
     if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
   }
-  const int64_t packed_stride = (n_samp + 3) / 4 * 4;
-  int32_t packed_pair = -1;  // pair distance of the packed copy now in the scratch
+  std::vector<int32_t> range_copy;
+  const std::vector<PackedCopy> copies = packed_copies(plan, n_samp, &range_copy);
+  if (pack)
+    for (const PackedCopy& pc : copies) {
+      const int e = launch_pack_copy(plan, pc, d_in, in_row_stride, n_samp, d_scratch, stream);
+      if (e != 0) return cuda_fail(e, "dd_run packing");
+    }
   const size_t osz = 4;
   int64_t off = 0;           // element offset of the range's rows in d_out
   for (size_t i = 0; i < plan->ranges.size(); ++i) {
@@ -408,19 +444,10 @@ static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stri
     off += rp.n_dm * row;
     const void* src = d_in;
     int64_t stride = in_row_stride;
-    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {
-      const int32_t pair = pack_pair(rp);
-      if (!pack && packed_pair != -1 && pair != packed_pair)
-        return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
-      if (pair != packed_pair && pack) {
-        int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan,
-                                  n_samp, d_scratch, packed_stride, pair, 0, packed_stride,
-                                  pack_source(plan->dtype), stream);
-        if (e != 0) return cuda_fail(e, "dd_run packing");
-      }
-      packed_pair = pair;
-      src = d_scratch;
-      stride = packed_stride;
+    if (range_copy[i] >= 0) {  // reads its packed copy
+      const PackedCopy& pc = copies[range_copy[i]];
+      src = static_cast<unsigned char*>(d_scratch) + pc.offset;
+      stride = pc.stride;
     }
     int e = launch_range(plan, rp, src, stride, n_samp, row, o, 0, row, stream);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
@@ -443,19 +470,12 @@ dd_status dd_pack_input(dd_plan plan, const void* d_in, int64_t in_row_stride, i
   const size_t need = packed_input_bytes(plan, n_samp);
   if (need == 0) return DD_OK;  // no range reads a packed copy
   if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
-  const int64_t packed_stride = (n_samp + 3) / 4 * 4;
-  int32_t packed_pair = -1;
-  for (const RangePlan& rp : plan->ranges) {
-    if (!(rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))) continue;
-    const int32_t pair = pack_pair(rp);
-    if (packed_pair != -1 && pair != packed_pair)
-      return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
-    packed_pair = pair;
+  if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
+    return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
+  for (const PackedCopy& pc : packed_copies(plan, n_samp, nullptr)) {
+    const int e = launch_pack_copy(plan, pc, d_in, in_row_stride, n_samp, d_scratch, stream);
+    if (e != 0) return cuda_fail(e, "dd_pack_input");
   }
-  int e = launch_pack_pairs(d_in, row_bytes(plan->dtype, in_row_stride), plan->n_chan, n_samp,
-                            d_scratch, packed_stride, packed_pair, 0, packed_stride,
-                            pack_source(plan->dtype), stream);
-  if (e != 0) return cuda_fail(e, "dd_pack_input");
   return DD_OK;
 }
 
@@ -687,13 +707,11 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
     if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
     if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
-    int32_t pair = -1;
-    for (const auto& rp : plan->ranges)
-      if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {
-        if (pair >= 0 && pair != pack_pair(rp))
-          return fail(DD_ERR_UNSUPPORTED, "packed ranges with different pair distances");
-        pair = pack_pair(rp);
-      }
+    const auto copies = packed_copies(plan, n_samp, nullptr);
+    if (copies.size() != 1 || copies[0].bin != 1)
+      return fail(DD_ERR_UNSUPPORTED,
+                  "the host pipeline packs one copy at bin 1: binned packed ranges run "
+                  "through dd_run_scratch");
   }
   return run_host_pipeline(plan, info, h_in, 0, nullptr, n_samp, h_out, d_in_stage,
                            in_row_stride, d_out_stage, need > 0 ? d_scratch : nullptr, stream);
@@ -742,7 +760,7 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
                              int64_t n_samp, void* h_out, void* d_tm_stage, void* d_cm_stage,
                              int64_t cm_row_stride, void* d_out_stage, void* stream) {
   if (!h_in || !h_out || !d_tm_stage) return fail(DD_ERR_INVALID_ARG, "NULL buffer");
-  if (plan && has_packed_range(plan))
+  if (plan && packed_input_bytes(plan, 1) > 0)
     return fail(DD_ERR_UNSUPPORTED, "the host pipeline does not take DD_TILE_PACKED ranges");
   if (plan && plan->dtype == DD_U4)
     return fail(DD_ERR_UNSUPPORTED, "time-major input takes uint8, uint16 or float32 samples");

@@ -10,7 +10,10 @@
 // x tile work), DM blocks of a time tile consecutive so their shared input
 // window stays in L2.  dd_batch_bind uploads the per-job pointers once;
 // dd_batch_run is then a counter reset and up to two launches, which a CUDA
-// graph can capture and replay.
+// graph can capture and replay.  The launches run on lanes: one per pattern
+// group and one for the offset family, each lane a stream (the first the
+// caller's) that packs its beams' inputs and then runs its persistent launch,
+// so packing overlaps other lanes' compute and the lanes' tails overlap.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,11 +60,31 @@ struct dd_batch_s {
   // before the persistent launches (bound by dd_batch_bind_scratch).
   struct Pack {
     int32_t plan;
+    dd::PackedCopy copy{};  // one packed copy of the plan's input (api.cu)
+    int32_t copy_index = 0;
     const void* in = nullptr;
-    int64_t in_stride = 0;  // bytes
+    int64_t in_stride = 0;  // samples
     void* scratch = nullptr;
+    int32_t lane = 0;       // launch lane that packs it (the first lane reading it)
   };
   std::vector<Pack> packs;
+  // Launch lanes: one per pattern group, then the offset-tile family.  Each
+  // lane runs its packing launches and then its persistent launch on a stream
+  // of its own (the first lane on the caller's), so that packing overlaps the
+  // other lanes' compute and one lane's tail overlaps the next lane's start.
+  std::vector<std::vector<int32_t>> lane_packs;  // packs each lane reads
+  std::vector<cudaStream_t> lane_streams;        // [n_lanes]; [0] unused (caller's)
+  std::vector<cudaEvent_t> pack_done, lane_done;
+  cudaEvent_t start = nullptr;
+  ~dd_batch_s() {
+    for (cudaStream_t st : lane_streams)
+      if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : pack_done)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : lane_done)
+      if (e) cudaEventDestroy(e);
+    if (start) cudaEventDestroy(start);
+  }
 };
 
 namespace {
@@ -105,9 +128,15 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
       for (size_t r = 0; r < p->ranges.size(); ++r) {
         const RangePlan& rp = p->ranges[r];
         const bool pat = rp.tile_ok && rp.tile_pattern;
-        if (pat && tk::packed_copy_kind(rp.tile_kind) &&
-            (b->packs.empty() || b->packs.back().plan != i))
-          b->packs.push_back({i});
+        if (r == 0) {  // the plan's packed copies (one per distinct pair distance and bin)
+          const auto copies = packed_copies(p, n_samp[i], nullptr);
+          for (size_t k = 0; k < copies.size(); ++k) {
+            dd_batch_s::Pack pk{i};
+            pk.copy = copies[k];
+            pk.copy_index = static_cast<int32_t>(k);
+            b->packs.push_back(pk);
+          }
+        }
         if (!rp.tile_ok || (rp.tile_pattern && !pat) ||
             (!pat && (rp.tile_pattern || !batch_shape(rp.tile_dr)))) {
           delete b;
@@ -137,7 +166,8 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
           b->pjob_group.push_back(static_cast<int32_t>(g));
           b->groups[g].smem = std::max(
               b->groups[g].smem,
-              tk::pat_smem_bytes(rp.tile_kind, rp.r.bin, ps, rp.tile_lp));
+              tk::pat_smem_bytes(rp.tile_kind, tk::staged_bin(rp.tile_kind, rp.r.bin), ps,
+                                 rp.tile_lp));
           ts = tk::pat_tile_samples(rp.tile_kind, ps.h);
           dms = static_cast<double>(ps.warps) * tk::kPatDr;
         } else {
@@ -197,6 +227,23 @@ dd_status dd_batch_create(const dd_plan* plans, const int64_t* n_samp, int32_t n
     if (too_big) {
       delete b;
       return fail(DD_ERR_BUDGET, "batch shared-memory layout exceeds 227 KB");
+    }
+    // Lanes that read each plan's packed copy (offset tiles never do).
+    b->lane_packs.assign(b->groups.size() + 1, {});
+    for (size_t k = 0; k < b->packs.size(); ++k) {
+      int32_t first = -1;
+      std::vector<int32_t> range_copy;
+      packed_copies(b->plans[b->packs[k].plan], b->n_samp[b->packs[k].plan], &range_copy);
+      for (const auto& j : b->jobs) {
+        if (j.plan != b->packs[k].plan || !j.pattern) continue;
+        if (range_copy[j.range] != b->packs[k].copy_index) continue;
+        const int32_t lane = b->pjob_group[j.index];
+        auto& lp = b->lane_packs[lane];
+        if (std::find(lp.begin(), lp.end(), static_cast<int32_t>(k)) == lp.end())
+          lp.push_back(static_cast<int32_t>(k));
+        if (first < 0) first = lane;
+      }
+      b->packs[k].lane = first < 0 ? 0 : first;
     }
   } catch (const std::bad_alloc&) {
     delete b;
@@ -258,6 +305,20 @@ dd_status dd_batch_upload(dd_batch batch, void* d_workspace, size_t bytes, void*
   batch->sm_count = sms;
   batch->d_ws = ws;
   batch->bound = false;
+  if (batch->lane_streams.empty()) {  // the launch lanes' streams and events (dd_batch_run)
+    const size_t n_lanes = batch->groups.size() + 1;
+    batch->lane_streams.assign(n_lanes, nullptr);
+    batch->lane_done.assign(n_lanes, nullptr);
+    batch->pack_done.assign(batch->packs.size(), nullptr);
+    for (size_t i = 1; i < n_lanes && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithFlags(&batch->lane_streams[i], cudaStreamNonBlocking);
+    for (size_t i = 0; i < n_lanes && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&batch->lane_done[i], cudaEventDisableTiming);
+    for (size_t i = 0; i < batch->packs.size() && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&batch->pack_done[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&batch->start, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_batch_upload streams");
+  }
   return DD_OK;
 }
 
@@ -287,7 +348,7 @@ dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
     if (reinterpret_cast<uintptr_t>(d_scratch[pk.plan]) & 15u)
       return fail(DD_ERR_SHAPE, "batch plan scratch must be 16-byte aligned");
     pk.in = d_in[pk.plan];
-    pk.in_stride = static_cast<int64_t>(dtype_row_bytes(p->dtype, in_row_stride[pk.plan]));
+    pk.in_stride = in_row_stride[pk.plan];
     pk.scratch = d_scratch[pk.plan];
   }
   for (size_t j = 0; j < batch->jobs.size(); ++j) {
@@ -305,9 +366,12 @@ dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
         stride < n || stride_bytes % 16 != 0 || (p->dtype == DD_U4 && stride % 2 != 0))
       return fail(DD_ERR_SHAPE, "batch input/output alignment or stride");
     const RangePlan& rp = p->ranges[jr.range];
-    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {  // reads the packed copy
-      x = d_scratch[jr.plan];
-      stride = (n + 3) / 4 * 4;
+    if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) {  // reads its packed copy
+      std::vector<int32_t> range_copy;
+      const auto copies = packed_copies(p, n, &range_copy);
+      const PackedCopy& pc = copies[range_copy[jr.range]];
+      x = static_cast<unsigned char*>(d_scratch[jr.plan]) + pc.offset;
+      stride = pc.stride;
     }
     const tk::TileParams prm =
         tiled_params(p, rp, static_cast<unsigned char*>(p->d_ws) + rp.off_tile_recs,
@@ -354,20 +418,40 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
   cudaError_t e =
       cudaMemsetAsync(batch->d_ws, 0, (1 + batch->groups.size()) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run counter reset");
-  for (const auto& pk : batch->packs) {  // the packed copies the persistent launches read
-    const dd_plan p = batch->plans[pk.plan];
-    int32_t pair = 0;
-    for (const auto& rp : p->ranges)
-      if (rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) pair = pack_pair(rp);
-    const int64_t n = batch->n_samp[pk.plan];
-    const int64_t packed_stride = (n + 3) / 4 * 4;
-    const int le = launch_pack_pairs(pk.in, pk.in_stride, p->n_chan, n, pk.scratch, packed_stride,
-                                     pair, 0, packed_stride, pack_source(p->dtype), stream);
+  // Lanes: pattern groups 0..G-1, then the offset family (lane G).  Lane 0
+  // runs on the caller's stream, the others on the batch's own streams, which
+  // start after the counter reset and end before the caller's stream goes on.
+  const size_t n_lanes = batch->groups.size() + 1;
+  std::vector<bool> used(n_lanes, false);
+  for (size_t gi = 0; gi < batch->groups.size(); ++gi) used[gi] = !batch->groups[gi].items.empty();
+  used[n_lanes - 1] = !batch->items.empty();
+  if (batch->lane_streams.size() != n_lanes) return fail(DD_ERR_INVALID_ARG, "batch not uploaded");
+  auto lane_stream = [&](size_t lane) {
+    return lane == 0 ? s : batch->lane_streams[lane];
+  };
+  e = cudaEventRecord(batch->start, s);
+  for (size_t i = 1; i < n_lanes && e == cudaSuccess; ++i)
+    if (used[i]) e = cudaStreamWaitEvent(batch->lane_streams[i], batch->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run ordering");
+  // Packing launches, each on the first lane that reads its copy.
+  for (size_t k = 0; k < batch->packs.size(); ++k) {
+    const auto& pk = batch->packs[k];
+    cudaStream_t ls = lane_stream(pk.lane);
+    const int le = launch_pack_copy(batch->plans[pk.plan], pk.copy, pk.in, pk.in_stride,
+                                    batch->n_samp[pk.plan], pk.scratch, ls);
     if (le != 0) return cuda_fail(le, "dd_batch_run packing");
+    e = cudaEventRecord(batch->pack_done[k], ls);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run ordering");
   }
   for (size_t gi = 0; gi < batch->groups.size(); ++gi) {
     const auto& g = batch->groups[gi];
     if (g.items.empty()) continue;
+    cudaStream_t ls = lane_stream(gi);
+    for (int32_t k : batch->lane_packs[gi])  // copies packed on another lane
+      if (batch->packs[k].lane != static_cast<int32_t>(gi)) {
+        e = cudaStreamWaitEvent(ls, batch->pack_done[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run ordering");
+      }
     tk::PatBatchArgs args{};
     args.jobs = reinterpret_cast<const tk::PatBatchJob*>(batch->d_ws + batch->off_pjobs);
     args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + g.off_items);
@@ -376,10 +460,11 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(g.items.size()),
                                            static_cast<int64_t>(batch->sm_count));
     int le = launch_pattern_batch(g.kind, g.shape, args,
-                                  static_cast<int32_t>(std::max<int64_t>(grid, 1)), g.smem, stream);
+                                  static_cast<int32_t>(std::max<int64_t>(grid, 1)), g.smem, ls);
     if (le != 0) return cuda_fail(le, "dd_batch_run pattern launch");
   }
   if (!batch->items.empty()) {
+    cudaStream_t ls = lane_stream(n_lanes - 1);
     tk::BatchArgs args{};
     args.jobs = reinterpret_cast<const tk::BatchJob*>(batch->d_ws + batch->off_jobs);
     args.items = reinterpret_cast<const tk::BatchItem*>(batch->d_ws + batch->off_items);
@@ -389,8 +474,16 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
     const size_t smem = tk::batch_smem_bytes(batch->max_lraw, batch->max_lp);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(batch->items.size()),
                                            static_cast<int64_t>(batch->sm_count));
-    int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, stream);
+    int le = launch_batch(args, static_cast<int32_t>(std::max<int64_t>(grid, 1)), smem, ls);
     if (le != 0) return cuda_fail(le, "dd_batch_run launch");
+  }
+  // The caller's stream goes on once every lane is done (packs only run on
+  // lanes with items: the lanes that read them).
+  for (size_t i = 1; i < n_lanes; ++i) {
+    if (!used[i]) continue;
+    e = cudaEventRecord(batch->lane_done[i], batch->lane_streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, batch->lane_done[i], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_batch_run ordering");
   }
   return DD_OK;
 }

@@ -136,6 +136,13 @@ enum class PackSource { kU8, kU4, kU16, kF32 };
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
                       int64_t t_end, PackSource src, void* stream);
+// uint8 decimated by bin (2, 4, 8) into packed pair words of decimated samples
+// (pack.cu): out[c][t] = D[c][t] | D[c][t + pair] << 16, D the sums of bin
+// consecutive samples, t < out_stride (a multiple of 4, >= n_samp / bin), 0
+// past n_samp / bin; in_stride in bytes.
+int launch_pack_pairs_binned(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
+                             int32_t bin, void* d_out, int64_t out_stride, int32_t pair,
+                             void* stream);
 // Pair distance and source of a range's packed copy.
 inline int32_t pack_pair(const RangePlan& rp) {
   return rp.tile_kind == tk::kU8P || rp.tile_kind == tk::kF32P ? 32 * rp.tile_h : 0;
@@ -146,6 +153,24 @@ inline PackSource pack_source(dd_dtype dtype) {
          : dtype == DD_F32 ? PackSource::kF32
                            : PackSource::kU8;
 }
+// The packed copies a plan's DD_TILE_PACKED ranges read (api.cu): one per
+// distinct (pair distance, bin), in range order, at 256-byte aligned offsets
+// of the caller's scratch; each copy has `stride` words per channel row.
+struct PackedCopy {
+  int32_t pair;
+  int32_t bin;
+  int64_t stride;  // words per row: ceil4(n_samp / bin)
+  size_t offset;   // bytes into the scratch
+  size_t bytes;
+};
+// The copies, and for each range its copy (-1: reads the input itself).
+std::vector<PackedCopy> packed_copies(const dd_plan_s* p, int64_t n_samp,
+                                      std::vector<int32_t>* range_copy);
+// Bytes all copies take (0 without a packed range).
+size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp);
+// Write one copy of the input (in_stride in samples) into scratch.
+int launch_pack_copy(const dd_plan_s* p, const PackedCopy& pc, const void* d_in, int64_t in_stride,
+                     int64_t n_samp, void* d_scratch, void* stream);
 // Bytes of n samples of a dtype (4-bit: two per byte, rounded up).
 inline size_t dtype_row_bytes(dd_dtype t, int64_t n) {
   return t == DD_U4    ? static_cast<size_t>((n + 1) / 2)

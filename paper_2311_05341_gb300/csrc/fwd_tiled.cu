@@ -323,13 +323,13 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.tile0 = 0;
   prm.t_end = n_out;
   prm.lp = rp.tile_lp;
+  const int sb = tk::staged_bin(rp.tile_kind, rp.r.bin);  // packed copies: already decimated
   prm.lraw = rp.tile_pattern
-                 ? tk::pat_raw_bytes(rp.tile_kind, rp.r.bin, tk::kPatShapes[rp.tile_shape],
-                                     rp.tile_lp)
-                 : tk::raw_bytes(rp.tile_kind, rp.r.bin, rp.tile_lp);
+                 ? tk::pat_raw_bytes(rp.tile_kind, sb, tk::kPatShapes[rp.tile_shape], rp.tile_lp)
+                 : tk::raw_bytes(rp.tile_kind, sb, rp.tile_lp);
   prm.units_magic = rp.tile_units_magic;
   prm.units_shift = rp.tile_units_shift;
-  prm.bin = rp.r.bin;
+  prm.bin = sb;
   prm.flush = tk::flush_channels(rp.tile_kind, rp.r.bin);
   // Packed 4-bit input: at most 15 per sample in the 16-bit lanes.
   if (rp.tile_kind == tk::kU8P && p->dtype == DD_U4) prm.flush = tk::flush_channels(tk::kU4, 1);

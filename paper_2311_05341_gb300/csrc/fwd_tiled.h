@@ -94,17 +94,23 @@ DD_HOST_DEVICE constexpr int64_t sample_bytes(int kind, int64_t n) {
 DD_HOST_DEVICE constexpr int align_samples(int kind, int bin) {
   return samples_per_16b(kind) / bin;
 }
+// The bin the staged rows are at: packed copies are already decimated.
+DD_HOST_DEVICE constexpr int staged_bin(int kind, int bin) {
+  return packed_copy_kind(kind) ? 1 : bin;
+}
 inline bool bin_supported(int kind, int bin) {
   const int per = samples_per_16b(kind);
   return bin >= 1 && bin <= per && per % bin == 0 && (kind != kU8 || bin == 1) &&
          (!direct_kind(kind) || bin == 1) && (kind != kU4 || bin <= 16);
 }
 // Channels between widenings of the accumulators: uint8 pairs in 16-bit lanes
-// hold 255 * 256 < 2^16, 4-bit pairs 15 * bin per channel; one-sample words
+// hold 255 * 256 < 2^16 (packed copies of uint8 decimated by b: 65535 /
+// (255 b) channels), 4-bit pairs 15 * bin per channel; one-sample words
 // stay below 2^31 for floor((2^31 - 1) / (max sample * bin)) channels; float
 // never needs one.
 inline int flush_channels(int kind, int bin) {
-  if (kind == kU8 || kind == kU8P) return 256;
+  if (kind == kU8) return 256;
+  if (kind == kU8P) return 65535 / (255 * bin);  // decimated uint8 sums (bin 1: 256)
   if (kind == kU4) return 65535 / (15 * bin);
   if (float_kind(kind)) return 1 << 30;
   const double max_sample = (kind == kU8W ? 255.0 : 65535.0) * bin;
@@ -202,21 +208,26 @@ struct PatShape {
 // faster at H = 23 than H = 19 with loads before the branch (1024-channel
 // float32 plan, 3.85 against 4.38 ms).
 // Float pairs (kF32P, 64-bit words of two floats): H = 11 words of 2
-// samples, the accumulators of 4 DMs in 88 registers (H = 13 with 12 warps).
+// samples, the accumulators of 4 DMs in 88 registers (H = 13 with 12 warps),
+// channel pairs (two add.f32x2 per accumulator) or single channels.
 // The automatic choice takes the first entry that serves and fits; the
 // entries from index kPatTuneFirst on are reached only through an explicit
 // shape (dd_plan_set_tile_shape), for the autotuner: other window widths,
 // warp counts and channels per stage.
+// Float pairs take channel pairs first (two channels per indexed branch: the
+// 1024-channel plan ran 2.94 ms against 3.07 ms with single channels).
 constexpr PatShape kPatShapes[] = {
     {23, 16, 32, true, false, 3},  {23, 16, 12, true, false, 3},  {23, 16, 6, true, false, 3},
     {23, 16, 32, false, false, 3}, {19, 16, 32, false, false, 3}, {19, 16, 12, false, false, 1},
     {19, 16, 6, false, false, 1},  {19, 16, 12, false, false, 3}, {19, 16, 6, false, false, 3},
-    {11, 16, 24, false, false, 3}, {11, 16, 16, false, false, 3}, {11, 16, 8, false, false, 3},
+    {11, 16, 24, true, false, 3},  {11, 16, 16, true, false, 3},  {11, 16, 24, false, false, 3},
+    {11, 16, 16, false, false, 3}, {11, 16, 8, false, false, 3},
     // Tuning entries.
     {21, 16, 32, true, false, 3},  {19, 16, 32, true, false, 3},  {25, 12, 32, true, false, 3},
     {23, 12, 32, true, false, 3},  {23, 16, 24, true, false, 3},  {21, 16, 32, false, false, 3},
-    {13, 12, 16, false, false, 3}, {11, 12, 24, false, false, 3}};
-constexpr int kPatTuneFirst = 12;
+    {13, 12, 16, false, false, 3}, {11, 12, 24, false, false, 3}, {13, 12, 16, true, false, 3},
+    {11, 12, 24, true, false, 3}};
+constexpr int kPatTuneFirst = 14;
 constexpr int kNumPatShapes = static_cast<int>(sizeof(kPatShapes) / sizeof(kPatShapes[0]));
 constexpr bool pat_shapes_fit_records() {
   for (const PatShape& s : kPatShapes)
@@ -224,11 +235,13 @@ constexpr bool pat_shapes_fit_records() {
   return true;
 }
 static_assert(pat_shapes_fit_records(), "a pattern shape has more warps than its records hold");
-// The shape serves a kind: pairs take integer window words, single channels
-// float; float-pair shapes (H < 15) serve kF32P only.
+// The shape serves a kind: float-pair shapes (H < 15) serve kF32P only, with
+// channel pairs or single channels; the others pair integer window words or
+// take float words one channel at a time.
 DD_HOST_DEVICE constexpr bool pat_shape_serves(const PatShape& s, int kind) {
-  return s.pairs == !float_kind(kind) && (!direct_kind(kind) || !s.dbuf) &&
-         ((s.h < 15) == float_pairs(kind));
+  return ((s.h < 15) == float_pairs(kind)) &&
+         (s.pairs ? !float_kind(kind) || float_pairs(kind) : float_kind(kind)) &&
+         (!direct_kind(kind) || !s.dbuf);
 }
 
 DD_HOST_DEVICE constexpr int pair_chunk_bytes(int warps, int nc) {

@@ -129,7 +129,7 @@ def pattern_load_macro(op, h, pair):
     instr, cons = OPS_F2 if op == "F2" else OPS[op]
     ld, ty = LOAD[op]
     wb = WORD_BYTES[op]
-    tag = f"ddl{'q' if pair else op.lower()}{h}"
+    tag = f"ddl{('q' if op == 'U32' else 'q' + op.lower()) if pair else op.lower()}{h}"
     nacc = PATTERN_DR * h
     win = h + max(_pattern_offsets(p)[3] for p in range(PATTERNS))
     s1 = nacc
@@ -177,7 +177,8 @@ def pattern_load_macro(op, h, pair):
     lines.append(f'"{tag}_end:\\n\\t}}"')
     outs = ", ".join(f'"+{cons}"(A[{i}][{j}])' for i in range(PATTERN_DR) for j in range(h))
     ins = '"r"(S), "r"(S2), "r"(IX)' if pair else '"r"(S), "r"(IX)'
-    name = f"DD_PATL2_CHANNEL_U32_{h}(A, S, S2, IX)" if pair else f"DD_PATL_CHANNEL_{op}_{h}(A, S, IX)"
+    name = (f"DD_PATL2_CHANNEL_{op}_{h}(A, S, S2, IX)" if pair
+            else f"DD_PATL_CHANNEL_{op}_{h}(A, S, IX)")
     out = [f"#define {name} \\", "  asm volatile( \\"]
     out += [f"      {ln} \\" for ln in lines]
     out.append(f"      : {outs} \\")
@@ -204,6 +205,8 @@ def generate(path):
         out.append("")
     for h in F2_H:
         out += pattern_load_macro("F2", h, False)
+        out.append("")
+        out += pattern_load_macro("F2", h, True)
         out.append("")
     text = "\n".join(out) + "\n"
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -168,7 +168,94 @@ __global__ void __launch_bounds__(256) pack_f32_pairs_kernel(const float* __rest
   reinterpret_cast<float4*>(dst)[1] = make_float4(a[2], b[2], a[3], b[3]);
 }
 
+// uint8 decimated by a time bin b (2, 4 or 8) into the packed pair words:
+// word t = D[t] | D[t + pair] << 16 with D[t] = sum_{j < b} X[b t + j], the
+// decimated sample (Sec. 5.3's binning), for t < n_dec = floor(n_samp / b), 0
+// past it.  Each thread writes 4 words (out_stride and the output length are
+// multiples of 4).
+template <int B>
+__device__ __forceinline__ uint32_t dec_at(const uint8_t* row, int64_t t, int64_t n_dec) {
+  if (t >= n_dec) return 0u;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < B; ++j) s += row[B * t + j];
+  return s;
+}
+
+template <int B>
+__device__ __forceinline__ void dec4(const uint8_t* row, int64_t t, uint32_t (&d)[4]) {
+  // 4 decimated samples from 4 B aligned bytes (B = 2: 8, 4: 16, 8: 32 bytes).
+  if constexpr (B == 2) {
+    const uint2 a = *reinterpret_cast<const uint2*>(row + 2 * t);
+    const uint32_t s0 = (a.x & 0x00ff00ffu) + ((a.x >> 8) & 0x00ff00ffu);
+    const uint32_t s1 = (a.y & 0x00ff00ffu) + ((a.y >> 8) & 0x00ff00ffu);
+    d[0] = s0 & 0xffffu; d[1] = s0 >> 16; d[2] = s1 & 0xffffu; d[3] = s1 >> 16;
+  } else if constexpr (B == 4) {
+    const uint4 a = *reinterpret_cast<const uint4*>(row + 4 * t);
+    d[0] = __dp4a(a.x, 0x01010101u, 0u); d[1] = __dp4a(a.y, 0x01010101u, 0u);
+    d[2] = __dp4a(a.z, 0x01010101u, 0u); d[3] = __dp4a(a.w, 0x01010101u, 0u);
+  } else {
+    const uint4 a = *reinterpret_cast<const uint4*>(row + 8 * t);
+    const uint4 b = *reinterpret_cast<const uint4*>(row + 8 * t + 16);
+    d[0] = __dp4a(a.y, 0x01010101u, __dp4a(a.x, 0x01010101u, 0u));
+    d[1] = __dp4a(a.w, 0x01010101u, __dp4a(a.z, 0x01010101u, 0u));
+    d[2] = __dp4a(b.y, 0x01010101u, __dp4a(b.x, 0x01010101u, 0u));
+    d[3] = __dp4a(b.w, 0x01010101u, __dp4a(b.z, 0x01010101u, 0u));
+  }
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) pack_pairs_binned_kernel(
+    const uint8_t* __restrict__ in, int64_t in_stride, int64_t n_samp, uint32_t* __restrict__ out,
+    int64_t out_stride, int32_t pair, int64_t chunks_per_row, int32_t n_chan) {
+  const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c = gid / chunks_per_row;
+  const int64_t t = (gid - c * chunks_per_row) * 4;
+  if (c >= n_chan) return;  // the last block's spare threads
+  const uint8_t* row = in + c * in_stride;
+  const int64_t n_dec = n_samp / B;
+  uint32_t lo[4], hi[4];
+  if (t + pair + 4 <= n_dec) {
+    dec4<B>(row, t, lo);
+    dec4<B>(row, t + pair, hi);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      lo[k] = dec_at<B>(row, t + k, n_dec);
+      hi[k] = dec_at<B>(row, t + k + pair, n_dec);
+    }
+  }
+  *reinterpret_cast<uint4*>(out + c * out_stride + t) =
+      make_uint4(lo[0] | hi[0] << 16, lo[1] | hi[1] << 16, lo[2] | hi[2] << 16, lo[3] | hi[3] << 16);
+}
+
 }  // namespace
+
+int launch_pack_pairs_binned(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
+                             int32_t bin, void* d_out, int64_t out_stride, int32_t pair,
+                             void* stream) {
+  if (n_chan <= 0 || n_samp <= 0) return 0;
+  if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 ||
+      out_stride < n_samp / bin || (bin != 2 && bin != 4 && bin != 8))
+    return static_cast<int>(cudaErrorInvalidValue);
+  const int64_t chunks = out_stride / 4;
+  const int64_t blocks = (chunks * n_chan + 255) / 256;
+  if (blocks > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
+  const auto* in = static_cast<const uint8_t*>(d_in);
+  auto* out = static_cast<uint32_t*>(d_out);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned g = static_cast<unsigned>(blocks);
+  if (bin == 2)
+    pack_pairs_binned_kernel<2><<<g, 256, 0, st>>>(in, in_stride, n_samp, out, out_stride, pair,
+                                                   chunks, n_chan);
+  else if (bin == 4)
+    pack_pairs_binned_kernel<4><<<g, 256, 0, st>>>(in, in_stride, n_samp, out, out_stride, pair,
+                                                   chunks, n_chan);
+  else
+    pack_pairs_binned_kernel<8><<<g, 256, 0, st>>>(in, in_stride, n_samp, out, out_stride, pair,
+                                                   chunks, n_chan);
+  return static_cast<int>(cudaGetLastError());
+}
 
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,

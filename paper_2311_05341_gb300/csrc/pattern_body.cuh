@@ -106,9 +106,15 @@ __device__ __forceinline__ void pat_channel_regs(AccT<KIND> (&acc)[kPatDr][H],
 #undef DD_PAT_CASE
 }
 
-template <int H>
-__device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t win, uint32_t win2,
-                                         uint32_t ix) {
+template <int KIND, int H>
+__device__ __forceinline__ void pat_pair(AccT<KIND> (&acc)[kPatDr][H], uint32_t win,
+                                         uint32_t win2, uint32_t ix) {
+  if constexpr (float_pairs(KIND)) {
+    static_assert(H == 11 || H == 13, "no generated float-pair pair blocks for H");
+    if constexpr (H == 11) DD_PATL2_CHANNEL_F2_11(acc, win, win2, ix);
+    else DD_PATL2_CHANNEL_F2_13(acc, win, win2, ix);
+    return;
+  } else {
   static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pair blocks for H");
   if constexpr (H == 15) DD_PATL2_CHANNEL_U32_15(acc, win, win2, ix);
@@ -117,6 +123,7 @@ __device__ __forceinline__ void pat_pair(uint32_t (&acc)[kPatDr][H], uint32_t wi
   else if constexpr (H == 21) DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
   else if constexpr (H == 23) DD_PATL2_CHANNEL_U32_23(acc, win, win2, ix);
   else DD_PATL2_CHANNEL_U32_25(acc, win, win2, ix);
+  }
 }
 
 // Pair chunk of one (DM block, stage) in global memory.
@@ -146,7 +153,8 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
-  static_assert(!PAIRS || !float_kind(KIND), "channel pairs need integer window words");
+  static_assert(!PAIRS || !float_kind(KIND) || float_pairs(KIND),
+                "channel pairs need integer window words or float pairs");
   constexpr bool kDirect = direct_kind(KIND);
   constexpr uint32_t kWB = word_bytes(KIND);  // bytes per window word
   static_assert(!kDirect || !DBUF, "packed input stages its window words directly");
@@ -256,12 +264,13 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
 #pragma unroll 1
       for (int k = 0; k < n_pairs; ++k) {
         const PairItem it = items[k];
-        pat_pair<H>(acc, lane_win + 4u * (it.a & 0xffffu), lane_win + 4u * (it.a >> 16), it.pat);
+        pat_pair<KIND, H>(acc, lane_win + kWB * (it.a & 0xffffu), lane_win + kWB * (it.a >> 16),
+                          it.pat);
       }
 #pragma unroll 1
       for (int k = n_pairs; k < n_items; ++k) {
         const PairItem it = items[k];
-        pat_channel<KIND, H>(acc, lane_win + 4u * it.a, it.pat);
+        pat_channel<KIND, H>(acc, lane_win + kWB * it.a, it.pat);
       }
     } else if constexpr (AMAX <= 1) {
       // Base increments 0 and 1 only: the lane's H + 6 window words are loaded

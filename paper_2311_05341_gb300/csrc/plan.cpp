@@ -60,7 +60,7 @@ bool build_tile_records(const RangePlan& rp, int32_t n_chan, int kind, const tk:
                         std::vector<tk::Rec>& recs, int32_t* n_blocks_out) {
   using namespace tk;
   const int dm_cta = sh.dr * sh.warps;
-  const int32_t align = align_samples(kind, rp.r.bin);
+  const int32_t align = align_samples(kind, tk::staged_bin(kind, rp.r.bin));
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   recs.assign(static_cast<size_t>(n_blocks) * n_chan, tk::Rec{});
   for (int64_t b = 0; b < n_blocks; ++b) {
@@ -128,7 +128,7 @@ bool build_pattern_records(const RangePlan& rp, int32_t n_chan, int kind, const 
                            std::vector<tk::PRec>& recs, int32_t* n_blocks_out) {
   using namespace tk;
   const int dm_cta = kPatDr * ps.warps;
-  const int32_t align = align_samples(kind, rp.r.bin);
+  const int32_t align = align_samples(kind, tk::staged_bin(kind, rp.r.bin));
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   recs.assign(static_cast<size_t>(n_blocks) * n_chan, tk::PRec{});
   auto shift = [&](int64_t d, int32_t c) {
@@ -170,7 +170,7 @@ bool build_pair_tables(const RangePlan& rp, int32_t n_chan, int kind, const tk::
                        int32_t* n_blocks_out) {
   using namespace tk;
   const int dm_cta = kPatDr * ps.warps;
-  const int32_t align = align_samples(kind, rp.r.bin);
+  const int32_t align = align_samples(kind, tk::staged_bin(kind, rp.r.bin));
   const int64_t n_blocks = (rp.n_dm + dm_cta - 1) / dm_cta;
   const int n_st = (n_chan + ps.nc - 1) / ps.nc;
   const size_t cb = static_cast<size_t>(pair_chunk_bytes(ps.warps, ps.nc));
@@ -285,8 +285,9 @@ bool try_pattern_shape(RangePlan& rp, int32_t n_chan, int kind, int shape) {
   const tk::PatShape& ps = tk::kPatShapes[shape];
   if (!tk::pat_shape_serves(ps, kind)) return false;
   const int32_t span = block_span(rp, n_chan, tk::kPatDr * ps.warps);
-  const int32_t lp = tk::pat_window_words(kind, rp.r.bin, ps.h, span);
-  if (tk::pat_smem_bytes(kind, rp.r.bin, ps, lp) > 227 * 1024) return false;
+  const int sb = tk::staged_bin(kind, rp.r.bin);
+  const int32_t lp = tk::pat_window_words(kind, sb, ps.h, span);
+  if (tk::pat_smem_bytes(kind, sb, ps, lp) > 227 * 1024) return false;
   uint32_t magic = 0;
   int32_t shift = 0;
   if (!division_magic(static_cast<uint32_t>(lp / 4), static_cast<uint32_t>(ps.nc * lp / 4),
@@ -340,9 +341,13 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_recs.clear();
   // Packed input at bin 1: uint8 and 4-bit share the paired word format,
   // uint16 is widened to one sample per word.
+  // Packed copies: uint8, 4-bit, uint16 and float32 at bin 1; uint8 also
+  // decimated by 2, 4 or 8 (sums of at most 2040 keep 32 or more channels in
+  // a 16-bit lane).
+  const int b = rp.r.bin;
   const bool packed = rp.tile_request == DD_TILE_PACKED &&
                       (dtype == DD_U8 || dtype == DD_U4 || dtype == DD_U16 || dtype == DD_F32) &&
-                      rp.r.bin == 1;
+                      (b == 1 || (dtype == DD_U8 && (b == 2 || b == 4 || b == 8)));
   const int kind = packed ? (dtype == DD_U16   ? tk::kU16P
                              : dtype == DD_F32 ? tk::kF32P
                                                : tk::kU8P)
@@ -350,7 +355,7 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
                    : (dtype == DD_U8 && rp.r.bin > 1) ? tk::kU8W
                                                       : static_cast<int>(dtype);
   if (rp.tile_request == DD_TILE_PACKED && !tk::packed_copy_kind(kind)) return;
-  if (!tk::bin_supported(kind, rp.r.bin)) return;
+  if (!tk::bin_supported(kind, tk::staged_bin(kind, rp.r.bin))) return;
   if (rp.tile_request == DD_TILE_PATTERN || rp.tile_request == DD_TILE_PACKED ||
       rp.tile_request == 0) {
     // Float32 at bin 1 first tries the direct kind (the input words are the

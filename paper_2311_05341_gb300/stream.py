@@ -9,8 +9,10 @@ DM range r only: with overlap >= max_r bin_r * S_max_r those are the next
 transform of the concatenated stream (the paper's real-time processing,
 Sec. 5.4, done incrementally), and no output is computed twice.  The window's
 tail becomes the next overlap.  Ranges that the packed-input tile serves run
-on it, from a per-beam packed copy of the window in scratch that the budget
-counts.
+on it (uint8 at bins 1, 2, 4 and 8), from a packed copy of the window made in
+one of a few scratch slots the server shares among its beams (a slot is
+reused once the launch that last used it is done); the budget counts the
+slots once and each beam's window and outputs.
 
 Serving is continuous batching: each beam has its own CUDA stream, chunks are
 launched as soon as they arrive, so work of different beams overlaps on the
@@ -54,7 +56,6 @@ class _Beam:
     window: object          # device [n_chan][overlap + chunk]
     out: object             # device: per range [n_dm_r][chunk / bin_r], concatenated
     stream: object          # torch.cuda.Stream
-    scratch: object = None  # device packed copy of the window (packed-tile ranges)
     n_chunks: int = 0
     kept: list = field(default_factory=list)  # host copies of kept outputs per chunk
     bytes: int = 0
@@ -83,11 +84,16 @@ class StreamServer:
     """Admits beams under an HBM budget and dedisperses their chunks as they arrive."""
 
     def __init__(self, chunk: int, hbm_budget_bytes: int, device="cuda", keep_outputs=False,
-                 plan_cache: dict | None = None, packed: bool = True):
+                 plan_cache: dict | None = None, packed: bool = True, scratch_slots: int = 4):
         """chunk: raw samples per chunk (a multiple of 16 and of every range's
-        bin); packed: run the ranges the packed-input tile serves on it."""
+        bin); packed: run the ranges the packed-input tile serves on it, with
+        `scratch_slots` shared scratch buffers for the packed copies."""
         torch = _torch()
         self.device = torch.device(device)
+        self.n_slots = max(1, int(scratch_slots))
+        self.slots = []          # [buffer, event of its last use]
+        self.slot_bytes = 0
+        self._next_slot = 0
         self.chunk = int(chunk)
         self.budget = int(hbm_budget_bytes)
         self.used = 0
@@ -133,20 +139,45 @@ class StreamServer:
         return plan, ov, n, out_elems, plan.input_scratch_bytes(n)
 
     def beam_bytes(self, spec: StreamSpec) -> int:
-        """Device bytes of one admitted beam: window, packed copy, outputs."""
+        """Device bytes of one admitted beam: window and outputs (the packed
+        copies live in the server's shared scratch slots)."""
         plan, ov, n, out_elems, scratch = self._sizes(spec)
         in_bytes = (n + 1) // 2 if spec.dtype == "u4" else n * {"u8": 1, "u16": 2, "f32": 4}[spec.dtype]
-        return len(spec.freqs) * in_bytes + out_elems * 4 + scratch
+        return len(spec.freqs) * in_bytes + out_elems * 4
+
+    def slots_bytes(self, spec: StreamSpec) -> int:
+        """Device bytes of the shared scratch slots a beam of `spec` needs
+        (counted once for all beams)."""
+        return self.n_slots * self._sizes(spec)[4]
+
+    def _ensure_slots(self, scratch: int) -> bool:
+        """Grow the shared scratch slots to `scratch` bytes each if the budget
+        allows (with nothing in flight); False if it does not."""
+        torch = _torch()
+        if scratch <= self.slot_bytes:
+            return True
+        extra = self.n_slots * (scratch - self.slot_bytes)
+        if self.used + extra > self.budget:
+            return False
+        for job in self.inflight:
+            job.event.synchronize()
+        self.slots = [[torch.empty(scratch, dtype=torch.uint8, device=self.device), None]
+                      for _ in range(self.n_slots)]
+        self.used += extra
+        self.slot_bytes = scratch
+        return True
 
     def request(self, beam_id: int, spec: StreamSpec) -> bool:
         """Admit a beam now if its memory fits the budget, else queue it."""
         if beam_id in self.beams:
             return True
         need = self.beam_bytes(spec)
-        if need > self.budget:
+        scratch = self._sizes(spec)[4]
+        if need + self.n_slots * max(scratch, self.slot_bytes) > self.budget:
             self.rejected += 1
             return False
-        if self.used + need <= self.budget and not self.waiting:
+        if (self.used + need <= self.budget and not self.waiting and
+                self._ensure_slots(scratch) and self.used + need <= self.budget):
             self._admit(beam_id, spec, need)
             return True
         self.waiting.append((beam_id, spec))
@@ -158,9 +189,8 @@ class StreamServer:
         plan, ov, n, out_elems, scratch = self._sizes(spec)
         window = input_buffer(spec.dtype, len(spec.freqs), n, self.device)
         out = torch.empty(max(out_elems, 4), dtype=plan.out_dtype(), device=self.device)
-        sc = torch.empty(scratch, dtype=torch.uint8, device=self.device) if scratch else None
         self.beams[beam_id] = _Beam(spec, plan, window, out, torch.cuda.Stream(self.device),
-                                    scratch=sc, bytes=need)
+                                    bytes=need)
         self.used += need
 
     def release(self, beam_id: int):
@@ -171,7 +201,8 @@ class StreamServer:
         while self.waiting:
             bid, spec = self.waiting[0]
             need = self.beam_bytes(spec)
-            if self.used + need > self.budget:
+            if (self.used + need > self.budget or not self._ensure_slots(self._sizes(spec)[4])
+                    or self.used + need > self.budget):
                 break
             self.waiting.popleft()
             self._admit(bid, spec, need)
@@ -194,10 +225,19 @@ class StreamServer:
         # Column indices of the window buffer ("u4" packs two samples per byte;
         # the overlap and the chunk are even).
         spe = 2 if beam.spec.dtype == "u4" else 1
+        slot = None
+        if plan.input_scratch_bytes(n):
+            slot = self.slots[self._next_slot]
+            self._next_slot = (self._next_slot + 1) % self.n_slots
         with torch.cuda.stream(beam.stream):
             beam.window[:, ov // spe:n // spe].copy_(job.chunk, non_blocking=True)
+            if slot is not None and slot[1] is not None:
+                beam.stream.wait_event(slot[1])  # the slot's last user is done with it
             plan.run_window(beam.window, self.keep_counts(beam.spec), out=beam.out, n_samp=n,
-                            stream=beam.stream, scratch=beam.scratch)
+                            stream=beam.stream, scratch=None if slot is None else slot[0])
+            if slot is not None:
+                slot[1] = torch.cuda.Event()
+                slot[1].record(beam.stream)
             if self.keep_outputs:
                 beam.kept.append(self._kept(beam, ov))
             # The tail of this window is the next step's overlap.
@@ -248,7 +288,8 @@ class StreamServer:
             raise ValueError("snapshot taken with another chunk size")
         spec = state["spec"]
         need = self.beam_bytes(spec)
-        if beam_id in self.beams or self.used + need > self.budget:
+        if (beam_id in self.beams or self.used + need > self.budget or
+                not self._ensure_slots(self._sizes(spec)[4]) or self.used + need > self.budget):
             return False
         self._admit(beam_id, spec, need)
         beam = self.beams[beam_id]

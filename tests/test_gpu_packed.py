@@ -181,12 +181,25 @@ def test_packed_float32(seed):
     ref = oracle.forward(xs, freqs, f_high, 64e-6, ranges)
     ref_abs = oracle.forward(xs, freqs, f_high, 64e-6, ranges, take_abs=True)
     plan = dd.Plan(freqs, f_high, 64e-6, ranges, "f32")
+    xd = torch.from_numpy(x).cuda()
+    # Every float-pair shape (single channels and channel pairs, 16 and 12
+    # warps) that fits the plan.
+    ran = 0
+    for i, sh in enumerate(dd.tile_shapes()):
+        if not sh["float_pairs"]:
+            continue
+        try:
+            plan.set_tile_shape(0, "packed", i)
+        except dd.DDError:
+            continue
+        ran += 1
+        got = plan.run(xd, n_samp=n_samp)
+        for r, (g, o, a) in enumerate(zip(got, ref, ref_abs)):
+            assert_float_parity(g.cpu().numpy(), o, a, f"shape {i} range {r}")
+    assert ran >= 3
     plan.set_tile(0, "packed")
     info = plan.info(n_samp)
     assert info["tile_dms"][0] == _lib.DD_TILE_PACKED
-    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
-    for r, (g, o, a) in enumerate(zip(got, ref, ref_abs)):
-        assert_float_parity(g.cpu().numpy(), o, a, f"range {r}")
     h_in = torch.from_numpy(x).pin_memory()
     h_out = torch.full((info["out_elems"],), -5.0, dtype=torch.float32).pin_memory()
     plan.run_host(h_in, h_out, torch.empty_like(h_in, device="cuda"), plan.empty_output(n_samp),
@@ -194,3 +207,47 @@ def test_packed_float32(seed):
     torch.cuda.synchronize()
     for r, (g, o, a) in enumerate(zip(plan.split(h_out, n_samp), ref, ref_abs)):
         assert_float_parity(g.numpy(), o, a, f"host range {r}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_packed_binned_uint8(seed):
+    """uint8 ranges at bins 2, 4 and 8 on the packed tile (copies of decimated
+    pair words, widened every 65535 / (255 bin) channels) beside a bin-1 packed
+    range and a plain range, against the oracle; saturated samples (255) on
+    every channel cross every widening at its lane bound."""
+    rng = np.random.default_rng(5800 + seed)
+    n_chan = int(rng.choice([33, 96, 257, 300]))
+    f_high = float(rng.uniform(900, 1700))
+    freqs = channel_freqs(f_high, float(rng.uniform(0.05, 0.25)) * f_high, n_chan)
+    k_low = oracle.delay_coeff(freqs[-1], f_high) / 64e-6
+    step = float(rng.uniform(0.2, 1.5)) / k_low
+    n_dm = int(rng.choice([7, 64, 130]))
+    ranges, lo, tiles = [], 0.0, []
+    for b in (1, 2, 4, 8, 3):
+        ranges.append((lo, lo + n_dm * step * b, step * b, b))
+        lo += n_dm * step * b
+        tiles.append("packed" if b != 3 else 0)
+    s_max = max((oracle.extent(freqs, f_high, 64e-6, r, 10 ** 9)[0] + 1) * r[3] for r in ranges)
+    n_samp = int(s_max + rng.choice([1, 1471, 12001]))
+    stride = (n_samp + 15) // 16 * 16
+    saturated = seed == 0
+    if saturated:
+        x = np.zeros((n_chan, stride), np.uint8)
+        x[:, :n_samp] = 255
+    else:
+        x = filterbank(np.uint8, n_chan, n_samp, 5900 + seed, 200, 80, row_stride=stride)
+    x[:, n_samp:] = 255
+    ref = oracle.forward(np.ascontiguousarray(x[:, :n_samp]), freqs, f_high, 64e-6, ranges)
+    plan = dd.Plan(freqs, f_high, 64e-6, ranges, "u8")
+    for r, t in enumerate(tiles):
+        plan.set_tile(r, t)
+    info = plan.info(n_samp)
+    assert info["tile_dms"][:4] == [_lib.DD_TILE_PACKED] * 4
+    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
+    for r, (g, o) in enumerate(zip(got, ref)):
+        np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")
+    # The same through a windowed run (the streaming server's call).
+    keep = [max(1, o.shape[1] // 2) for o in ref]
+    win = plan.run_window(torch.from_numpy(x).cuda(), keep, n_samp=n_samp)
+    for r, (w, o) in enumerate(zip(win, ref)):
+        np.testing.assert_array_equal(w.cpu().numpy(), o[:, : keep[r]], err_msg=f"window {r}")

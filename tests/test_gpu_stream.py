@@ -95,7 +95,8 @@ def test_alone_equals_mixed_with_admission():
     alone, _ = _run_server({0: streams[0]}, 1 << 34, [0] * N_CHUNKS)
     probe = dds.StreamServer(CHUNK, 1 << 34)
     need = [probe.beam_bytes(specs[b]) for b in specs]
-    budget = need[0] + need[1] + need[2] // 2  # the third beam must wait
+    slots = max(probe.slots_bytes(specs[b]) for b in specs)  # shared packed-copy scratch
+    budget = slots + need[0] + need[1] + need[2] // 2  # the third beam must wait
     srv = dds.StreamServer(CHUNK, budget, keep_outputs=True)
     assert srv.request(0, specs[0]) and srv.request(1, specs[1])
     assert not srv.request(2, specs[2]) and not srv.is_admitted(2)

@@ -303,9 +303,9 @@ def test_adjoint_scratch_bytes():
 
 def test_packed_tile_selection_and_scratch_bytes():
     """DD_TILE_PACKED serves uint8, 4-bit, uint16 and float32 ranges at bin 1
-    only (not binned ranges); it is never the automatic choice; the input
-    scratch is n_chan x ceil4(n_samp) words (32-bit; float32: 64-bit pairs)
-    when some range is packed."""
+    and uint8 at bins 2, 4 and 8; it is never the automatic choice; the input
+    scratch is n_chan x ceil4(n_samp / bin) words (32-bit; float32: 64-bit
+    pairs) per distinct packed copy."""
     lib = _lib.load()
     paper = workloads.paper_u8()
     # The paper band and DM step on fewer channels and DMs (quick to plan).
@@ -329,10 +329,23 @@ def test_packed_tile_selection_and_scratch_bytes():
     assert f32.info(paper.n_samp)["tile_dms"] == [_lib.DD_TILE_PACKED]
     assert lib.dd_plan_input_scratch_bytes(f32.handle, 1001, ctypes.byref(need)) == _lib.DD_OK
     assert need.value == paper.n_chan * 1004 * 8
-    binned = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, [(0.0, 40.0, 0.2, 2)], "u8",
+    # uint8 decimated by 2, 4 or 8: a packed copy of decimated pair words (one
+    # per distinct bin); other bins and other dtypes at bin > 1 are refused.
+    binned = dd.Plan(paper.freqs, paper.f_high, paper.t_samp,
+                     [(0.0, 40.0, 0.2, 2), (40.0, 80.0, 0.4, 4), (80.0, 120.0, 0.8, 3)], "u8",
                      upload=False)
+    binned.set_tile(0, "packed")
+    binned.set_tile(1, "packed")
     with pytest.raises(dd.DDError):
-        binned.set_tile(0, "packed")
+        binned.set_tile(2, "packed")
+    assert lib.dd_plan_input_scratch_bytes(binned.handle, 1001, ctypes.byref(need)) == _lib.DD_OK
+    copy2 = paper.n_chan * ((1001 // 2 + 3) // 4 * 4) * 4
+    copy4 = paper.n_chan * ((1001 // 4 + 3) // 4 * 4) * 4
+    assert need.value == (copy2 + 255) // 256 * 256 + copy4
+    u16b = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, [(0.0, 40.0, 0.2, 2)], "u16",
+                   upload=False)
+    with pytest.raises(dd.DDError):
+        u16b.set_tile(0, "packed")
     plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "u8", upload=False)
     assert lib.dd_plan_input_scratch_bytes(plan.handle, 0, ctypes.byref(need)) == \
         _lib.DD_ERR_SHAPE
