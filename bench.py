@@ -44,10 +44,11 @@ def _measured_hbm_gbs(default=6800.0):
 
 
 HBM_GBS = _measured_hbm_gbs()
-# dram__bytes_read.sum + dram__bytes_write.sum of one transform launch (ncu),
-# keyed by workload, raw samples and tile; valid only for the kernel build it
-# was taken on (profiles/fwd_pattern_u8_8192ch.md).
-TRAFFIC = {("paper_u8", 262144, (0x106,)): 34.73e9 + 66.41e9}
+# dram__bytes_read.sum + dram__bytes_write.sum of the transform launches the
+# roofline times (ncu), keyed by workload, raw samples, tiles, input mode and
+# segments; valid only for the kernel build it was taken on
+# (profiles/fwd_pattern_u8_8192ch.md).
+TRAFFIC = {}
 UNIT = "DM*samples/s"
 
 
@@ -194,21 +195,30 @@ def run_ours(args):
         for r in range(len(beam.ranges)):
             plan.set_tile(r, args.tile if args.tile in ("pattern", "packed")
                           else int(args.tile))
-    elif beam.dtype in ("u8", "u4", "u16", "f32"):
-        # The fastest integer path: the packed tile where it serves (it needs
-        # the caller scratch allocated below, so dd_plan_create does not pick
-        # it).
+    elif beam.dtype == "f32":
+        # Float32's fastest tile (float pairs) reads a packed copy with other
+        # tables than the automatic tile's, so it is asked for explicitly.
         for r in range(len(beam.ranges)):
             try:
                 plan.set_tile(r, "packed")
             except dd.DDError:
                 pass
     info = plan.info(beam.n_samp)
-    # Caller-owned scratch of the packed tile (allocated once, like the output).
-    need = ctypes.c_size_t(0)
-    _lib.check(lib.dd_plan_input_scratch_bytes(plan.handle, beam.n_samp, ctypes.byref(need)))
-    scratch = (torch.empty(int(need.value), dtype=torch.uint8, device=f"cuda:{local}")
-               if need.value else None)
+    # Caller-owned scratch (allocated once, like the output): the packed ring
+    # of `segments` time segments for the ranges with a packed copy (the
+    # automatic uint8 / 4-bit / uint16 tiles), the full copies for
+    # --segments 1, none for 0.
+    need = plan.input_scratch_bytes(beam.n_samp)
+    mode = "input read directly"
+    if any(info["packed_copy"]) and args.segments > 0:
+        try:
+            need = max(need, plan.packed_scratch_bytes(beam.n_samp, args.segments))
+            mode = "packed ring" if args.segments > 1 else "packed full copy"
+        except dd.DDError:
+            need = max(need, plan.packed_scratch_bytes(beam.n_samp, 1))
+            mode = "packed full copy"
+    scratch = (torch.empty(int(need), dtype=torch.uint8, device=f"cuda:{local}")
+               if need else None)
     tables = {}
 
     def shift_rows(r, d):
@@ -227,20 +237,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    def step(ev_mid=None):
-        """One pass: the packing launch (packed ranges) and the transform; with
-        ev_mid, an event between them so the transform is timed alone."""
-        if scratch is None:
-            if ev_mid is not None:
-                ev_mid.record(stream)
-            plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp)
-            return
-        _lib.check(lib.dd_pack_input(plan.handle, x.data_ptr(), x.stride(0) * spe, beam.n_samp,
-                                     scratch.data_ptr(), scratch.numel(), sp))
-        if ev_mid is not None:
-            ev_mid.record(stream)
-        _lib.check(lib.dd_run_packed(plan.handle, x.data_ptr(), x.stride(0) * spe, beam.n_samp,
-                                     out.data_ptr(), scratch.data_ptr(), scratch.numel(), sp))
+    def step():
+        """One pass: dd_run_scratch over the whole input (in ring mode it packs
+        segment k + 1 while the kernels of segment k run, on the plan's side
+        streams joined back into this one)."""
+        plan.run_raw(x.data_ptr(), x.stride(0) * spe, beam.n_samp, out.data_ptr(), sp,
+                     scratch=scratch)
 
     for _ in range(args.warmup):
         step()
@@ -248,9 +250,7 @@ def run_ours(args):
 
     dm_samples = sum(a * b for a, b in zip(info["n_dm"], info["n_out"]))
     chan_adds = dm_samples * beam.n_chan
-    # One transform launch per range, plus the packing launch when a range is
-    # on the packed tile.
-    launches_per_step = len(beam.ranges) + (1 if scratch is not None else 0)
+    launches_per_step = _launches_per_step(plan, info, mode, args.segments)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -258,20 +258,27 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     evs[0].record(stream)
     for i in range(args.steps):
-        step(mids[i])
+        step()
         evs[i + 1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
-    # The dominant kernel alone: the transform launches between mids[i] and evs[i + 1].
-    kern = sum(mids[i].elapsed_time(evs[i + 1]) for i in range(args.steps)) / 1e3 / args.steps
     value, total = replica_throughput(dm_samples * args.steps, sum(per), "cuda")
     ms_per_step = total / args.steps * 1e3
+    # The same tables in one transform launch from the full packed copy (the
+    # copy made first, outside the launch's events), and the unpacking kernel
+    # without scratch: the dominant kernel timed alone, the ncu launch list's
+    # per-launch figure.
+    single = _single_launch_times(torch, lib, plan, info, x, spe, beam.n_samp, out, stream, args)
+    # In ring mode the step's transform launches overlap each other and the
+    # packing, so the roofline takes the whole step (a lower bound on the
+    # kernels' own rate); with one launch per range the launch time.
+    kern = (total / args.steps if mode != "packed full copy" or single is None
+            else single["kernel_ms"] / 1e3)
 
     # End to end through the C ABI: pinned host in -> device -> pinned host out.
     e2e = None
@@ -302,19 +309,23 @@ def run_ours(args):
     # against the add rate derived from the SM's integer units and clock (a
     # three-input add retires on the 16-lane integer pipe of each of the 4 SM
     # sub-partitions; float adds on both 16-lane float pipes).
-    sample_adds_per_s = chan_adds / kern  # the transform kernel's own launch time
+    sample_adds_per_s = chan_adds / kern
     sms = peaks["sm_count"]
     per_lane = {"u8": 4, "u4": 4, "u16": 2, "f32": 1}[beam.dtype]
     lanes = 128 if beam.dtype == "f32" else 64  # lane-ops per clock per SM
     peak_adds = lanes * sms * SM_MAX_MHZ * 1e6 * per_lane
     algo_bytes = (beam.n_chan * beam.n_samp * np.dtype(beam.np_dtype).itemsize // spe
                   + info["out_elems"] * 4)
-    traffic = TRAFFIC.get((args.workload, beam.n_samp, tuple(info["tile_dms"])))
+    traffic = TRAFFIC.get((args.workload, beam.n_samp, tuple(info["tile_dms"]), mode,
+                           args.segments))
     roofline = {
         "bound": "alu", "achieved": sample_adds_per_s / 1e12, "peak": peak_adds / 1e12,
         "unit": "Tadd/s", "frac": sample_adds_per_s / peak_adds,
         "traffic": traffic,
         "kernel_ms": kern * 1e3,
+        "timed": ("the whole step: %d transform launches on two streams with the packing "
+                  "overlapped" % launches_per_step["transform"]) if mode == "packed ring"
+                 else "the transform launch alone",
         "frac_whole_step": chan_adds / (total / args.steps) / peak_adds,
         "peak_source": ("%d lane-ops/clk/SM x %d SMs x %g MHz x %d sample-adds per lane-op"
                         % (lanes, sms, SM_MAX_MHZ, per_lane)),
@@ -339,15 +350,23 @@ def run_ours(args):
                    "tile": [{_lib.DD_TILE_PATTERN: "pattern",
                              _lib.DD_TILE_PACKED: "packed"}.get(t, t)
                             for t in info["tile_dms"]],
+                   "input": mode + (f" ({args.segments} segments, "
+                                    f"{need / 1e9:.2f} GB scratch)" if mode == "packed ring"
+                                    else f" ({need / 1e9:.2f} GB scratch)" if need else ""),
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
         "channel_adds_per_s": chan_adds * args.steps * ws / total,
         "real_time_factor": t_obs / (ms_per_step / 1e3),
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": args.steps * launches_per_step,
+        "gpu_launches": args.steps * launches_per_step["total"],
         "clocks": clk,
     }
+    if single is not None:
+        single["frac"] = chan_adds / (single["kernel_ms"] / 1e3) / peak_adds
+        if "unpacked_ms" in single:
+            single["frac_unpacked_kernel"] = chan_adds / (single["unpacked_ms"] / 1e3) / peak_adds
+        line["single_launch"] = single
     if beam.dtype == "f32":
         line["adjoint"] = _adjoint_timing(args, plan, x, info, beam, stream)
     if ws == 1 and not args.no_cpu_baseline:
@@ -367,6 +386,72 @@ def run_ours(args):
         line["stream"] = stream_result(args)
         line["diff_f32"] = diff_result(args)
     print(json.dumps(line))
+
+
+def _launches_per_step(plan, info, mode, segments):
+    """Kernel launches of one dd_run_scratch: per range one transform launch
+    (plus one packing launch per copy); in ring mode one packing launch and
+    one launch per ring range for every segment with outputs (the library's
+    segment rule: boundaries k * ceil(n / segments) rounded down to each
+    range's time tiles, n the longest ring range's outputs)."""
+    shapes = None
+    n_ranges = len(info["n_out"])
+    if mode == "packed full copy":
+        return {"transform": n_ranges, "total": n_ranges + 1}
+    if mode != "packed ring":
+        return {"transform": n_ranges, "total": n_ranges + (1 if plan.input_scratch_bytes(
+            info["n_samp"]) else 0)}
+    import paper_2311_05341_gb300 as dd
+    shapes = dd.tile_shapes()
+    ring = [r for r in range(n_ranges) if info["packed_copy"][r]]
+    n_max = max(info["n_out"][r] for r in ring)
+    seg = -(-n_max // segments)
+    transform, packs = n_ranges - len(ring), 0
+    for k in range(segments):
+        busy = 0
+        for r in ring:
+            sh = shapes[info["tile_shape"][r]]
+            ts = 32 * sh["words_per_lane"] * (1 if plan.dtype == "u16" else 2)
+            n_out = info["n_out"][r]
+            lo = min(n_out, k * seg // ts * ts)
+            hi = n_out if k == segments - 1 else min(n_out, (k + 1) * seg // ts * ts)
+            busy += hi > lo
+        transform += busy
+        packs += busy > 0
+    return {"transform": transform, "total": transform + packs}
+
+
+def _single_launch_times(torch, lib, plan, info, x, spe, n_samp, out, stream, args):
+    """Ranges with a packed copy: the full copies (dd_pack_input), then one
+    transform launch per range from them (dd_run_packed) timed alone with
+    CUDA events; and dd_run without scratch (the automatic tiles unpacking
+    the input themselves).  None without such a range."""
+    if not any(info["packed_copy"]):
+        return None
+    from paper_2311_05341_gb300 import _lib
+    full = plan.packed_scratch_bytes(n_samp, 1)
+    sc = torch.empty(full, dtype=torch.uint8, device=x.device)
+    sp = stream.cuda_stream
+    args_in = (plan.handle, x.data_ptr(), x.stride(0) * spe, n_samp)
+
+    def pack():
+        _lib.check(lib.dd_pack_input(*args_in, sc.data_ptr(), full, sp))
+
+    def run():
+        _lib.check(lib.dd_run_packed(*args_in, out.data_ptr(), sc.data_ptr(), full, sp))
+
+    pack_s = _timed(pack, args.steps, args.warmup, stream)
+    pack()
+    run_s = _timed(run, args.steps, args.warmup, stream)
+    del sc
+    res = {"what": "full packed copy (dd_pack_input), then the transform launch alone "
+                   "(dd_run_packed)", "pack_ms": pack_s * 1e3, "kernel_ms": run_s * 1e3}
+    if plan.input_scratch_bytes(n_samp) == 0:
+        def unpacked():
+            plan.run_raw(x.data_ptr(), x.stride(0) * spe, n_samp, out.data_ptr(), sp)
+        res["unpacked_ms"] = _timed(unpacked, args.steps, args.warmup, stream) * 1e3
+    torch.cuda.empty_cache()
+    return res
 
 
 def _adjoint_timing(args, plan, x, info, beam, stream):
@@ -527,13 +612,20 @@ def batched_result(args):
     adds = sum(sum(a * c for a, c in zip(i["n_dm"], i["n_out"])) * b.n_chan
                for i, b in zip(infos, beams))
     # The plain per-beam path: one dd_run per beam on the plan's automatic
-    # tile (what dd_plan_create gives), one after another on one stream.
+    # tile (what dd_plan_create gives, no scratch), one after another on one
+    # stream; and Plan.run's default per beam (the automatic tiles from a
+    # packed ring where they have a packed copy).
     plain = [dd.Plan(b.freqs, b.f_high, b.t_samp, b.ranges, b.dtype) for b in beams]
     plain_out = [p.empty_output(b.n_samp) for p, b in zip(plain, beams)]
     tuned_out = [torch.empty_like(o) for o in runner.outputs]
+    ring_out = [torch.empty_like(o) for o in runner.outputs]
 
     def plain_step():
         for p, x, o, b in zip(plain, runner.inputs, plain_out, beams):
+            p.run(x, out=o, n_samp=b.n_samp, segments=0)
+
+    def ring_step():
+        for p, x, o, b in zip(plain, runner.inputs, ring_out, beams):
             p.run(x, out=o, n_samp=b.n_samp)
 
     def tuned_step():  # per beam again, on the batch's tuned tiles
@@ -544,12 +636,14 @@ def batched_result(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     t_plain = _timed(plain_step, args.steps, args.warmup)
+    t_ring = _timed(ring_step, args.steps, args.warmup)
     t_tuned = _timed(tuned_step, args.steps, args.warmup)
     t_batch = _timed(runner.run, args.steps, args.warmup)
     clk = clocks.stop()
     runner.status()
     same = all(torch.equal(a, c) for a, c in zip(plain_out, runner.outputs))
     same_tuned = all(torch.equal(a, c) for a, c in zip(tuned_out, runner.outputs))
+    same_ring = all(torch.equal(a, c) for a, c in zip(ring_out, runner.outputs))
     tiles = {}
     for b, shp in zip(beams, runner.shapes):
         tiles.setdefault(b.dtype, [str(t) for t in shp])
@@ -563,6 +657,11 @@ def batched_result(args):
                            "what": "one dd_run per beam, automatic tiles, one stream"},
         "batched_over_plain": t_plain / t_batch,
         "outputs_identical_to_plain": bool(same),
+        "per_beam_ring": {"value": units / t_ring, "ms_per_step": t_ring * 1e3,
+                          "what": "Plan.run per beam (automatic tiles from a 8-segment "
+                                  "packed ring where they have a packed copy), one stream",
+                          "outputs_identical": bool(same_ring)},
+        "batched_over_per_beam_ring": t_ring / t_batch,
         "per_beam_same_tiles": {"value": units / t_tuned, "ms_per_step": t_tuned * 1e3,
                                 "what": "one run per beam on the batch's tuned tiles"},
         "batched_over_same_tiles": t_tuned / t_batch,
@@ -570,7 +669,7 @@ def batched_result(args):
         "beams": len(beams), "work_items": runner.n_items, "tiles": tiles,
         "launches_per_step": runner.n_launches, "setup_s": t_setup, "clocks": clk,
     }
-    del runner, plain_out, tuned_out, plain
+    del runner, plain_out, tuned_out, ring_out, plain
     torch.cuda.empty_cache()
     return res
 
@@ -688,8 +787,8 @@ def run_stream(args):
 def _stream_saturated(args, spec, pool, chunk, plan_cache):
     """Server against the plain per-beam path on the same chunks, all queued at
     once: the plain path runs every beam's chunks one after another on one
-    stream (copy in, dd_run of the whole window on the plan's automatic tiles,
-    keep the overlap); the server launches them on per-beam streams and
+    stream (copy in, dd_run of the whole window on the plan's automatic tiles
+    without scratch, keep the overlap); the server launches them on per-beam streams and
     computes each range's chunk / bin new outputs only (dd_run_window).  Both
     end with each beam's last window outputs, which depend on every earlier
     chunk through the overlap; they must be equal."""
@@ -715,7 +814,7 @@ def _stream_saturated(args, spec, pool, chunk, plan_cache):
         for b in range(n_beams):
             for j in range(per_beam):
                 windows[b][:, ov:n].copy_(pool[(b + j) % len(pool)], non_blocking=True)
-                plan.run(windows[b], out=outs[b], n_samp=n)
+                plan.run(windows[b], out=outs[b], n_samp=n, segments=0)
                 tail = windows[b][:, chunk:n]
                 windows[b][:, :ov].copy_(tail.clone() if ov > chunk else tail)
 
@@ -940,6 +1039,9 @@ def main():
                     help="register tile of every range: auto (packed where it serves), "
                          "pattern, packed or the offset tile's DMs per lane "
                          "(8, 6, 4, 2, 1)")
+    ap.add_argument("--segments", type=int, default=8,
+                    help="ranges with a packed copy: time segments of the packed ring "
+                         "(1: the full copy, 0: no packed copy)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

@@ -94,6 +94,12 @@ typedef struct {
                                           uses (0 for other dtypes) */
   int32_t tile_shape[DD_MAX_RANGES];  /* pattern-tile ranges: the dd_tile_shapes index
                                           in use; -1 for other ranges */
+  int32_t packed_copy[DD_MAX_RANGES]; /* 1: the range can run from a packed copy of
+                                          the input (DD_TILE_PACKED, or the automatic
+                                          pattern tile of uint8, 4-bit or uint16 input
+                                          at bin 1, whose tables the packed kernel
+                                          also runs) given the scratch of
+                                          dd_plan_packed_scratch_bytes; 0 otherwise */
 } dd_plan_info;
 
 /* Adjoint kernels (dd_plan_info.adjoint_kernel). */
@@ -119,7 +125,11 @@ typedef struct {
  * two floats, added two at a time), so the staged words are the window words
  * (no unpacking, one barrier per stage).  dd_run
  * writes the copy into caller scratch first: such plans run through
- * dd_run_scratch (dd_plan_input_scratch_bytes sizes it). */
+ * dd_run_scratch (dd_plan_input_scratch_bytes sizes it).  The automatic
+ * pattern tile of uint8, 4-bit and uint16 input at bin 1 runs the same
+ * packed kernel whenever dd_run_scratch is given the scratch of
+ * dd_plan_packed_scratch_bytes (full copies or a ring), and the unpacking
+ * kernel otherwise. */
 #define DD_TILE_PACKED 0x106
 
 /*
@@ -219,27 +229,56 @@ dd_status dd_run(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t 
 dd_status dd_plan_input_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* bytes);
 
 /*
- * dd_run with caller-owned device scratch (16-byte aligned, at least
- * dd_plan_input_scratch_bytes; the library allocates no device memory): ranges
- * on DD_TILE_PACKED read the packed copy written there first (one pass over
- * the input, on `stream`), the others read d_in.  The scratch is in use until
- * the call's work on `stream` completes.  dd_run on a plan with a packed
- * range returns DD_ERR_UNSUPPORTED.
- * Errors: as dd_run; DD_ERR_BUDGET if the scratch is missing or too small,
- * DD_ERR_SHAPE if it is misaligned.
+ * Device scratch bytes with which dd_run_scratch runs every range that has a
+ * packed copy (dd_plan_info.packed_copy) from packed words, for n_samp raw
+ * samples.  n_segments = 1: the full copies (one pass packs the whole input,
+ * then the ranges' kernels run).  n_segments in [2, 256]: a ring of two
+ * slots, each the packed words of one of n_segments time segments of the
+ * outputs plus the ranges' largest delay (about 2 (n_out / n_segments +
+ * s_max) words per channel): segment k is packed while the kernels of
+ * segment k - 1 run, so packing overlaps the transform and the scratch is a
+ * fraction of the input's packed size.  0 if no range has a packed copy.
+ * Host only.
+ * Errors: DD_ERR_INVALID_ARG for null pointers or n_segments outside
+ * [1, 256], DD_ERR_SHAPE for n_samp <= 0 or an input shorter than a range's
+ * delay, DD_ERR_UNSUPPORTED (n_segments > 1) when the packed ranges need
+ * more than one copy or one at a bin above 1 (no ring: give n_segments = 1).
+ */
+dd_status dd_plan_packed_scratch_bytes(dd_plan plan, int64_t n_samp, int32_t n_segments,
+                                       size_t* bytes);
+
+/*
+ * dd_run with caller-owned device scratch (16-byte aligned; the library
+ * allocates no device memory).  With at least dd_plan_packed_scratch_bytes(1)
+ * every range with a packed copy reads the copy written there first (one
+ * pass over the input, on `stream`).  With less, but at least the ring of
+ * some segment count in [2, 256] (dd_plan_packed_scratch_bytes), those
+ * ranges run from the ring with the fewest segments that fits, packing and
+ * the segments' kernels overlapped on the plan's own side streams (a
+ * high-priority packing stream and a second compute stream, created at the
+ * first such call, joined back into `stream`); the other ranges read d_in.
+ * With less still, ranges on DD_TILE_PACKED read their full copies (at least
+ * dd_plan_input_scratch_bytes) and the others d_in.  The results are the
+ * same in every case.  The scratch is in use until the call's work on
+ * `stream` completes.  dd_run on a plan with a DD_TILE_PACKED range returns
+ * DD_ERR_UNSUPPORTED.
+ * Errors: as dd_run; DD_ERR_BUDGET if the scratch is missing or too small
+ * for the DD_TILE_PACKED ranges, DD_ERR_SHAPE if it is misaligned.
  */
 dd_status dd_run_scratch(dd_plan plan, const void* d_in, int64_t in_row_stride, int64_t n_samp,
                          void* d_out, void* d_scratch, size_t scratch_bytes, void* stream);
 
 /*
- * The two halves of dd_run_scratch, for callers that reuse one packed copy
- * (several plans over the same input) or time the transform alone.
- * dd_pack_input writes the packed copy of d_in that the plan's DD_TILE_PACKED
- * ranges read into d_scratch (sizes and rules as dd_run_scratch; nothing is
- * written when the plan has no such range).  dd_run_packed is dd_run_scratch
- * without the packing pass: d_scratch must hold the packed copy of the same
- * d_in and n_samp, made by dd_pack_input (or an earlier dd_run_scratch) with
- * a plan of the same channels and tile.
+ * The two halves of dd_run_scratch with full copies, for callers that reuse
+ * one packed copy (several plans over the same input) or time the transform
+ * alone.  dd_pack_input writes the packed copies of d_in into d_scratch:
+ * those of every range with a packed copy when scratch_bytes is at least
+ * dd_plan_packed_scratch_bytes(1), else those of the DD_TILE_PACKED ranges
+ * (sizes and rules as dd_run_scratch; nothing is written when no range reads
+ * a copy).  dd_run_packed is dd_run_scratch without the packing pass and
+ * never takes the ring: d_scratch (the same scratch_bytes) must hold the
+ * copies of the same d_in and n_samp, made by dd_pack_input with a plan of
+ * the same channels and tiles.
  * Errors: as dd_run_scratch; dd_pack_input: DD_ERR_UNSUPPORTED if the plan's
  * packed ranges need different copies.
  */

@@ -139,6 +139,7 @@ class Plan:
             "tile_dms": [inf.tile_dms[i] for i in range(n)],
             "adjoint_kernel": {0: None, 1: "gather", 2: "pattern"}[inf.adjoint_kernel],
             "tile_shape": [inf.tile_shape[i] for i in range(n)],
+            "packed_copy": [bool(inf.packed_copy[i]) for i in range(n)],
         }
 
     def shifts(self, r: int = 0) -> np.ndarray:
@@ -200,16 +201,21 @@ class Plan:
         return [flat[o:o + nd * no].view(nd, no)
                 for o, nd, no in zip(inf["out_offset"], inf["n_dm"], inf["n_out"])]
 
-    def run(self, x, out=None, n_samp: int | None = None, stream=None):
+    def run(self, x, out=None, n_samp: int | None = None, stream=None, segments: int = 8):
         """Forward transform of a cuda tensor x [n_chan][stride] -> list of planes.
 
-        For "u4" plans x holds packed bytes [n_chan][stride / 2]."""
+        For "u4" plans x holds packed bytes [n_chan][stride / 2].  Ranges with a
+        packed copy (info()["packed_copy"]) run from packed words in scratch
+        from torch's caching allocator: a ring of `segments` time segments
+        (dd_plan_packed_scratch_bytes; about 2 / segments of the full copy),
+        1 for the full copy, 0 for none (the automatic tiles then unpack the
+        input themselves; DD_TILE_PACKED ranges always get their copies)."""
         self._check_input(x)
         per = _samples_per_elem(self.dtype)
         n = x.shape[1] * per if n_samp is None else int(n_samp)
         if out is None:
             out = self.empty_output(n, x.device)
-        scratch = self._input_scratch(n, x.device)
+        scratch = self._input_scratch(n, x.device, segments)
         check(self._lib.dd_run_scratch(
             self._h, x.data_ptr(), x.stride(0) * per, n, out.data_ptr(),
             None if scratch is None else scratch.data_ptr(),
@@ -218,15 +224,30 @@ class Plan:
             scratch.record_stream(stream)
         return self.split(out, n)
 
-    def _input_scratch(self, n_samp: int, device):
-        """Device scratch for ranges on the packed tile (None when there are
-        none), from torch's caching allocator for each run."""
+    def _input_scratch(self, n_samp: int, device, segments: int = 0):
+        """Device scratch for the packed copies of a run (None when it needs
+        none), from torch's caching allocator for each run: the DD_TILE_PACKED
+        ranges' copies, and with segments > 0 the ring (or, where the plan has
+        no ring, the full copies) of every range with a packed copy."""
         import torch
-        need = ctypes.c_size_t(0)
-        check(self._lib.dd_plan_input_scratch_bytes(self._h, int(n_samp), ctypes.byref(need)))
-        if need.value == 0:
+        need = self.input_scratch_bytes(n_samp)
+        if segments > 0 and any(self.info(n_samp)["packed_copy"]):
+            try:
+                need = max(need, self.packed_scratch_bytes(n_samp, segments))
+            except DDError:
+                need = max(need, self.packed_scratch_bytes(n_samp, 1))
+        if need == 0:
             return None
-        return torch.empty(int(need.value), dtype=torch.uint8, device=device)
+        return torch.empty(int(need), dtype=torch.uint8, device=device)
+
+    def packed_scratch_bytes(self, n_samp: int, segments: int = 16) -> int:
+        """Scratch bytes with which every range with a packed copy runs from
+        packed words: a ring of `segments` time segments, or the full copies
+        for segments == 1 (dd_plan_packed_scratch_bytes)."""
+        need = ctypes.c_size_t(0)
+        check(self._lib.dd_plan_packed_scratch_bytes(self._h, int(n_samp), int(segments),
+                                                     ctypes.byref(need)))
+        return int(need.value)
 
     def run_window(self, x, n_keep, out=None, n_samp: int | None = None, stream=None,
                    scratch=None):
@@ -316,11 +337,14 @@ class Plan:
                                            d_out_stage.data_ptr(), _stream_ptr(stream)))
 
     def run_host(self, h_in, h_out, d_in_stage, d_out_stage, n_samp: int | None = None,
-                 stream=None):
-        """Host-to-host forward through pinned host buffers and device staging."""
+                 stream=None, packed: bool = True):
+        """Host-to-host forward through pinned host buffers and device staging.
+        packed: the automatic tiles with a packed copy read it too (scratch of
+        the full copy, packed as the input arrives); DD_TILE_PACKED ranges
+        always do."""
         per = _samples_per_elem(self.dtype)
         n = h_in.shape[1] * per if n_samp is None else int(n_samp)
-        scratch = self._input_scratch(n, d_in_stage.device)
+        scratch = self._input_scratch(n, d_in_stage.device, 1 if packed else 0)
         check(self._lib.dd_run_host_scratch(
             self._h, h_in.data_ptr(), h_in.stride(0) * per, n, h_out.data_ptr(),
             d_in_stage.data_ptr(), d_out_stage.data_ptr(),

@@ -51,7 +51,8 @@ class PlanInfo(ctypes.Structure):
                 ("kernel", ctypes.c_int32 * DD_MAX_RANGES),
                 ("tile_dms", ctypes.c_int32 * DD_MAX_RANGES),
                 ("adjoint_kernel", ctypes.c_int32),
-                ("tile_shape", ctypes.c_int32 * DD_MAX_RANGES)]
+                ("tile_shape", ctypes.c_int32 * DD_MAX_RANGES),
+                ("packed_copy", ctypes.c_int32 * DD_MAX_RANGES)]
 
 
 class TileShape(ctypes.Structure):
@@ -77,6 +78,7 @@ SIGNATURES = {
     "dd_run_scratch": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _SZ, _VP]),
     "dd_run_host_scratch": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "dd_plan_input_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
+    "dd_plan_packed_scratch_bytes": (ctypes.c_int, [_VP, _I64, _I32, ctypes.POINTER(_SZ)]),
     "dd_run_adjoint_scratch": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP, _SZ, _VP]),
     "dd_adjoint_scratch_bytes": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_SZ)]),
     "dd_plan_device_status": (ctypes.c_int, [_VP, _VP]),

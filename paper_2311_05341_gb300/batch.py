@@ -146,12 +146,13 @@ class Autotuner:
             if len(feas) > 1:
                 for cand in feas:
                     apply_tile(plan, r, cand)
-                    plan.run(x, out=out, n_samp=n_samp)
+                    # Full copies for packed candidates, as the batch runs them.
+                    plan.run(x, out=out, n_samp=n_samp, segments=0)
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record()
                     for _ in range(self.reps):
-                        plan.run(x, out=out, n_samp=n_samp)
+                        plan.run(x, out=out, n_samp=n_samp, segments=0)
                     e1.record()
                     torch.cuda.synchronize()
                     ms = e0.elapsed_time(e1) / self.reps
@@ -283,9 +284,10 @@ class BatchRunner:
         return self.plans[i].split(self.outputs[i], self.beams[i].n_samp)
 
     def run_per_beam(self):
-        """The plain path: one dd_run per beam, in order, on the current stream."""
+        """The plain path: one dd_run per beam (dd_run_scratch with the full
+        copies of its packed ranges), in order, on the current stream."""
         for p, x, o, b in zip(self.plans, self.inputs, self.outputs, self.beams):
-            p.run(x, out=o, n_samp=b.n_samp)
+            p.run(x, out=o, n_samp=b.n_samp, segments=0)
 
     def close(self):
         if getattr(self, "_h", None):

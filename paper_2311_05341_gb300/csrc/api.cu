@@ -31,14 +31,15 @@ dd_status cuda_fail(int err, const char* what) {
 }
 
 std::vector<PackedCopy> packed_copies(const dd_plan_s* p, int64_t n_samp,
-                                      std::vector<int32_t>* range_copy) {
+                                      std::vector<int32_t>* range_copy, bool with_auto) {
   std::vector<PackedCopy> copies;
   if (range_copy) range_copy->assign(p->ranges.size(), -1);
   size_t off = 0;
   for (size_t r = 0; r < p->ranges.size(); ++r) {
     const RangePlan& rp = p->ranges[r];
-    if (!(rp.tile_ok && tk::packed_copy_kind(rp.tile_kind))) continue;
-    const int32_t pair = pack_pair(rp), bin = rp.r.bin;
+    const int kind = copy_kind(rp, with_auto);
+    if (kind == 0) continue;
+    const int32_t pair = pack_pair(rp, kind), bin = rp.r.bin;
     size_t k = 0;
     while (k < copies.size() && !(copies[k].pair == pair && copies[k].bin == bin)) ++k;
     if (k == copies.size()) {
@@ -57,8 +58,8 @@ std::vector<PackedCopy> packed_copies(const dd_plan_s* p, int64_t n_samp,
   return copies;
 }
 
-size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp) {
-  const auto copies = packed_copies(p, n_samp, nullptr);
+size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp, bool with_auto) {
+  const auto copies = packed_copies(p, n_samp, nullptr, with_auto);
   return copies.empty() ? 0 : copies.back().offset + copies.back().bytes;
 }
 
@@ -100,6 +101,7 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
     o->n_dm_total += rp.n_dm;
     o->kernel[i] = rp.tile_ok ? DD_KERNEL_TILED : DD_KERNEL_GENERIC;
     o->tile_shape[i] = rp.tile_ok && rp.tile_pattern ? rp.tile_shape : -1;
+    o->packed_copy[i] = copy_kind(rp, true) != 0 ? 1 : 0;
     o->tile_dms[i] = !rp.tile_ok                          ? 0
                      : !rp.tile_pattern                   ? rp.tile_dr
                      : tk::packed_copy_kind(rp.tile_kind)  ? DD_TILE_PACKED
@@ -125,20 +127,38 @@ dd_status fill_info(const dd_plan_s* p, int64_t n_samp, dd_plan_info* o) {
 // internal one) so that one segment's last CTAs overlap the next one's first.
 constexpr int kHostSegments = 16;
 
+// Slots of the packed ring (dd_run_scratch with less scratch than the full
+// packed copies): segment k is packed into slot k % kRingSlots while the
+// kernels of segment k - 1 run.
+constexpr int kRingSlots = 2;
+constexpr int kRingMaxSegments = 256;
+
 struct HostPipe {
   int device = -1;
   cudaStream_t s_in = nullptr, s_out = nullptr, s_comp = nullptr, s_tr = nullptr;
+  cudaStream_t s_pack = nullptr;  // ring packing, at the highest stream priority
   cudaEvent_t start = nullptr, done = nullptr;
   cudaEvent_t in[kHostSegments] = {}, comp[kHostSegments] = {}, tr[kHostSegments] = {};
+  cudaEvent_t packed[kRingSlots] = {}, freed[kRingSlots] = {};
 };
+
+// The plans' side streams and events are shared by every call on a plan:
+// calls from several host threads enqueue one after the other (each wait
+// captures the record of its own call).
+std::mutex g_pipe_mu;
 
 void destroy_pipe(HostPipe* hp) {
   if (hp->s_in) cudaStreamDestroy(hp->s_in);
   if (hp->s_out) cudaStreamDestroy(hp->s_out);
   if (hp->s_comp) cudaStreamDestroy(hp->s_comp);
   if (hp->s_tr) cudaStreamDestroy(hp->s_tr);
+  if (hp->s_pack) cudaStreamDestroy(hp->s_pack);
   for (cudaEvent_t e : {hp->start, hp->done})
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < kRingSlots; ++k) {
+    if (hp->packed[k]) cudaEventDestroy(hp->packed[k]);
+    if (hp->freed[k]) cudaEventDestroy(hp->freed[k]);
+  }
   for (int k = 0; k < kHostSegments; ++k) {
     if (hp->in[k]) cudaEventDestroy(hp->in[k]);
     if (hp->comp[k]) cudaEventDestroy(hp->comp[k]);
@@ -166,8 +186,16 @@ cudaError_t host_pipe(dd_plan_s* p, HostPipe** out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->s_tr, cudaStreamNonBlocking);
+  int prio_least = 0, prio_greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&hp->s_pack, cudaStreamNonBlocking, prio_greatest);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->done, cudaEventDisableTiming);
+  for (int k = 0; k < kRingSlots && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&hp->packed[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->freed[k], cudaEventDisableTiming);
+  }
   for (int k = 0; k < kHostSegments && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&hp->in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->comp[k], cudaEventDisableTiming);
@@ -192,13 +220,108 @@ void free_host_pipe(dd_plan_s* p) {
 namespace {
 
 
+// Outputs [t_begin, t_end) of range rp.  kind > 0: the pattern tables run
+// by that packed-copy kernel (copy_kind) on packed words, element 0 of each
+// row holding word x_origin.
 int launch_range(const dd_plan_s* p, const RangePlan& rp, const void* d_in, int64_t stride,
                  int64_t n_samp, int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
-                 void* stream) {
+                 void* stream, int kind = 0, int64_t x_origin = 0) {
+  if (kind > 0) {
+    unsigned char* ws = static_cast<unsigned char*>(p->d_ws);
+    return launch_forward_pattern(p, rp, ws + rp.off_tile_recs,
+                                  reinterpret_cast<int32_t*>(ws + tk::kStatusOffset), d_in,
+                                  stride, n_out, d_out, t_begin, t_end, stream, n_out, kind,
+                                  x_origin);
+  }
   return rp.tile_ok ? launch_forward_tiled(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
                                            t_end, stream)
                     : launch_forward_generic(p, rp, d_in, stride, n_samp, n_out, d_out, t_begin,
                                              t_end, stream);
+}
+
+// The full packed copies a run reads: those of every range with a copy
+// kind, automatic tiles included, when the scratch holds them all (and
+// they add to the DD_TILE_PACKED ranges' copies); else the DD_TILE_PACKED
+// ranges' only.
+bool full_with_auto(const dd_plan_s* p, int64_t n_samp, const void* d_scratch, size_t bytes) {
+  if (!d_scratch) return false;
+  const size_t all = packed_input_bytes(p, n_samp, true);
+  return all > packed_input_bytes(p, n_samp, false) && bytes >= all;
+}
+
+// One time segment of the ring: packed words [origin, end) in its slot, and
+// the outputs [lo_r, hi_r) each ring range computes from them.
+struct RingSeg {
+  int64_t origin = 0;
+  int64_t end = 0;
+  int64_t lo[DD_MAX_RANGES] = {};
+  int64_t hi[DD_MAX_RANGES] = {};
+};
+struct RingLayout {
+  int32_t pair = 0;
+  int64_t slot_words = 0;     // words per channel row of a slot
+  size_t slot_bytes = 0;      // a slot, 256-byte aligned
+  bool ring[DD_MAX_RANGES] = {};  // the range runs from the ring
+  std::vector<RingSeg> segs;  // the segments with work
+  size_t bytes() const { return kRingSlots * slot_bytes; }
+};
+
+// The ring for n_seg segments of the longest ring range's outputs, each
+// range's boundaries rounded down to its time tiles.  False when the ranges
+// with a copy kind need more than one copy, or one at a bin above 1 (those
+// need the full copies), or there are none.
+bool ring_layout(const dd_plan_s* p, const dd_plan_info& info, int64_t n_samp, int n_seg,
+                 RingLayout* L) {
+  std::vector<int32_t> rc;
+  const std::vector<PackedCopy> copies = packed_copies(p, n_samp, &rc, true);
+  if (copies.size() != 1 || copies[0].bin != 1 || n_seg < 2) return false;
+  *L = RingLayout{};
+  L->pair = copies[0].pair;
+  int64_t n_max = 0;
+  for (size_t r = 0; r < p->ranges.size(); ++r)
+    if (rc[r] >= 0) {
+      L->ring[r] = true;
+      n_max = std::max(n_max, info.n_out[r]);
+    }
+  const int64_t seg = (n_max + n_seg - 1) / n_seg;
+  int64_t words = 0;
+  for (int k = 0; k < n_seg; ++k) {
+    RingSeg sg;
+    int64_t lo_min = -1, need = 0;
+    for (size_t r = 0; r < p->ranges.size(); ++r) {
+      if (!L->ring[r]) continue;
+      const RangePlan& rp = p->ranges[r];
+      const int64_t ts = range_tile_samples(rp), n_out = info.n_out[r];
+      const int64_t lo = std::min(n_out, k * seg / ts * ts);
+      const int64_t hi = k == n_seg - 1 ? n_out : std::min(n_out, (k + 1) * seg / ts * ts);
+      sg.lo[r] = lo;
+      sg.hi[r] = hi;
+      if (hi <= lo) continue;
+      lo_min = lo_min < 0 ? lo : std::min(lo_min, lo);
+      // Output t reads packed words t' <= t + s_max (a packed word t' holds
+      // samples t' and t' + pair).
+      need = std::max(need, hi + static_cast<int64_t>(rp.s_max));
+    }
+    if (lo_min < 0) continue;
+    sg.origin = lo_min / 32 * 32;  // a multiple of every tables' window alignment
+    sg.end = std::min(copies[0].stride, (need + 15) / 16 * 16);
+    words = std::max(words, sg.end - sg.origin);
+    L->segs.push_back(sg);
+  }
+  L->slot_words = (words + 15) / 16 * 16;
+  L->slot_bytes = (static_cast<size_t>(p->n_chan) * static_cast<size_t>(L->slot_words) *
+                       packed_word_bytes(p->dtype) + 255) / 256 * 256;
+  return !L->segs.empty();
+}
+
+// The fewest segments (at least 2) whose ring fits `bytes`.
+bool pick_ring(const dd_plan_s* p, const dd_plan_info& info, int64_t n_samp, size_t bytes,
+               RingLayout* L) {
+  for (int n = 2; n <= kRingMaxSegments; ++n) {
+    if (!ring_layout(p, info, n_samp, n, L)) return false;
+    if (L->bytes() <= bytes) return true;
+  }
+  return false;
 }
 
 }  // namespace
@@ -403,10 +526,75 @@ static dd_status check_run(dd_plan plan, const void* d_in, int64_t stride, int64
   return DD_OK;
 }
 
+// The ring: the ranges with a copy kind run in time segments from a ring of
+// kRingSlots packed slots.  Segment k is packed (on the plan's high-priority
+// packing stream) into slot k % kRingSlots once the kernels of segment
+// k - kRingSlots have read it, and its kernels run on the caller's stream
+// (k even) or the plan's second compute stream (k odd), so that packing
+// overlaps the kernels and one segment's last CTAs overlap the next one's
+// first.  The other ranges read the input on the caller's stream.  The
+// caller's stream waits for all of it.
+static dd_status run_ring(dd_plan plan, const dd_plan_info& info, const void* d_in,
+                          int64_t in_row_stride, int64_t n_samp, void* d_out, void* d_scratch,
+                          const RingLayout& L, void* stream) {
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe* hp = nullptr;
+  cudaError_t e = host_pipe(plan, &hp);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run ring streams");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  e = cudaEventRecord(hp->start, s);
+  for (cudaStream_t o : {hp->s_pack, hp->s_comp})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(o, hp->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+  unsigned char* out = static_cast<unsigned char*>(d_out);
+  for (size_t r = 0; r < plan->ranges.size(); ++r) {
+    if (L.ring[r]) continue;
+    const int le = launch_range(plan, plan->ranges[r], d_in, in_row_stride, n_samp, info.n_out[r],
+                                out + info.out_offset[r] * 4, 0, info.n_out[r], s);
+    if (le != 0) return cuda_fail(le, "dd_run forward launch");
+  }
+  const size_t in_bytes = dtype_row_bytes(plan->dtype, in_row_stride);
+  for (size_t k = 0; k < L.segs.size(); ++k) {
+    const RingSeg& sg = L.segs[k];
+    const int slot = static_cast<int>(k % kRingSlots);
+    unsigned char* buf = static_cast<unsigned char*>(d_scratch) + slot * L.slot_bytes;
+    if (k >= static_cast<size_t>(kRingSlots)) {
+      e = cudaStreamWaitEvent(hp->s_pack, hp->freed[slot], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+    }
+    int le = launch_pack_pairs(d_in, static_cast<int64_t>(in_bytes), plan->n_chan, n_samp, buf,
+                               L.slot_words, L.pair, sg.origin, sg.end,
+                               pack_source(plan->dtype), hp->s_pack, sg.origin);
+    if (le != 0) return cuda_fail(le, "dd_run ring packing");
+    cudaStream_t sc = (k & 1) ? hp->s_comp : s;
+    e = cudaEventRecord(hp->packed[slot], hp->s_pack);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, hp->packed[slot], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+    for (size_t r = 0; r < plan->ranges.size(); ++r) {
+      if (!L.ring[r] || sg.hi[r] <= sg.lo[r]) continue;
+      const RangePlan& rp = plan->ranges[r];
+      le = launch_range(plan, rp, buf, L.slot_words, n_samp, info.n_out[r],
+                        out + info.out_offset[r] * 4, sg.lo[r], sg.hi[r], sc,
+                        copy_kind(rp, true), sg.origin);
+      if (le != 0) return cuda_fail(le, "dd_run ring forward launch");
+    }
+    e = cudaEventRecord(hp->freed[slot], sc);
+    if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+  }
+  e = cudaEventRecord(hp->done, hp->s_comp);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+  return DD_OK;
+}
+
 // The forward transform of every range.  n_keep == nullptr: all n_out_r
 // outputs of each range, at dd_plan_query's offsets.  Otherwise the first
 // n_keep[r] outputs of range r, as rows of n_keep[r] samples, concatenated.
 // pack == false: the packed copy is already in d_scratch (dd_pack_input).
+// Scratch that holds the full copies of every range with a copy kind runs
+// them all from packed copies; less scratch runs them from the ring when it
+// fits (whole outputs, packing here); else only the DD_TILE_PACKED ranges
+// read packed copies.
 static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stride,
                              int64_t n_samp, const int64_t* n_keep, void* d_out, void* d_scratch,
                              size_t scratch_bytes, void* stream, bool pack = true) {
@@ -418,7 +606,15 @@ static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stri
       if (n_keep[i] < 1 || n_keep[i] > info.n_out[i])
         return fail(DD_ERR_SHAPE, "n_keep[r] must be in [1, n_out_r]");
   }
-  const size_t need = packed_input_bytes(plan, n_samp);
+  if (d_scratch && reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
+    return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
+  const bool with_auto = full_with_auto(plan, n_samp, d_scratch, scratch_bytes);
+  if (!n_keep && pack && d_scratch && scratch_bytes < packed_input_bytes(plan, n_samp, true)) {
+    RingLayout L;
+    if (pick_ring(plan, info, n_samp, scratch_bytes, &L))
+      return run_ring(plan, info, d_in, in_row_stride, n_samp, d_out, d_scratch, L, stream);
+  }
+  const size_t need = packed_input_bytes(plan, n_samp, with_auto);
   if (need > 0) {
     if (!d_scratch)
       return fail(DD_ERR_UNSUPPORTED,
@@ -429,7 +625,7 @@ static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stri
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
   }
   std::vector<int32_t> range_copy;
-  const std::vector<PackedCopy> copies = packed_copies(plan, n_samp, &range_copy);
+  const std::vector<PackedCopy> copies = packed_copies(plan, n_samp, &range_copy, with_auto);
   if (pack)
     for (const PackedCopy& pc : copies) {
       const int e = launch_pack_copy(plan, pc, d_in, in_row_stride, n_samp, d_scratch, stream);
@@ -444,12 +640,14 @@ static dd_status run_forward(dd_plan plan, const void* d_in, int64_t in_row_stri
     off += rp.n_dm * row;
     const void* src = d_in;
     int64_t stride = in_row_stride;
+    int kind = 0;
     if (range_copy[i] >= 0) {  // reads its packed copy
       const PackedCopy& pc = copies[range_copy[i]];
       src = static_cast<unsigned char*>(d_scratch) + pc.offset;
       stride = pc.stride;
+      kind = copy_kind(rp, with_auto);
     }
-    int e = launch_range(plan, rp, src, stride, n_samp, row, o, 0, row, stream);
+    int e = launch_range(plan, rp, src, stride, n_samp, row, o, 0, row, stream, kind);
     if (e != 0) return cuda_fail(e, "dd_run forward launch");
   }
   return DD_OK;
@@ -467,12 +665,13 @@ dd_status dd_pack_input(dd_plan plan, const void* d_in, int64_t in_row_stride, i
   if (!d_scratch) return fail(DD_ERR_INVALID_ARG, "d_scratch is NULL");
   dd_status st = check_run(plan, d_in, in_row_stride, n_samp, d_scratch, &info);
   if (st != DD_OK) return st;
-  const size_t need = packed_input_bytes(plan, n_samp);
+  const bool with_auto = full_with_auto(plan, n_samp, d_scratch, scratch_bytes);
+  const size_t need = packed_input_bytes(plan, n_samp, with_auto);
   if (need == 0) return DD_OK;  // no range reads a packed copy
   if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
   if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
     return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
-  for (const PackedCopy& pc : packed_copies(plan, n_samp, nullptr)) {
+  for (const PackedCopy& pc : packed_copies(plan, n_samp, nullptr, with_auto)) {
     const int e = launch_pack_copy(plan, pc, d_in, in_row_stride, n_samp, d_scratch, stream);
     if (e != 0) return cuda_fail(e, "dd_pack_input");
   }
@@ -502,6 +701,32 @@ dd_status dd_plan_input_scratch_bytes(dd_plan plan, int64_t n_samp, size_t* byte
   if (!plan || !bytes) return fail(DD_ERR_INVALID_ARG, "plan or bytes is NULL");
   if (n_samp <= 0) return fail(DD_ERR_SHAPE, "n_samp must be positive");
   *bytes = packed_input_bytes(plan, n_samp);
+  return DD_OK;
+}
+
+dd_status dd_plan_packed_scratch_bytes(dd_plan plan, int64_t n_samp, int32_t n_segments,
+                                       size_t* bytes) {
+  if (!plan || !bytes) return fail(DD_ERR_INVALID_ARG, "plan or bytes is NULL");
+  if (n_samp <= 0) return fail(DD_ERR_SHAPE, "n_samp must be positive");
+  if (n_segments < 1 || n_segments > kRingMaxSegments)
+    return fail(DD_ERR_INVALID_ARG, "n_segments must be in [1, 256]");
+  *bytes = 0;
+  const size_t full = packed_input_bytes(plan, n_samp, true);
+  if (full == 0 || n_segments == 1) {
+    *bytes = full;
+    return DD_OK;
+  }
+  dd_plan_info info;
+  fill_info(plan, n_samp, &info);
+  for (int32_t i = 0; i < info.n_ranges; ++i)
+    if (info.n_out[i] <= 0) return fail(DD_ERR_SHAPE, "input shorter than a range's maximum delay");
+  RingLayout L;
+  if (!ring_layout(plan, info, n_samp, n_segments, &L))
+    return fail(DD_ERR_UNSUPPORTED,
+                "the packed ranges need copies at a bin above 1 or at two pair distances: "
+                "no ring (n_segments = 1 gives the full copies)");
+  // At least the full copies' size, the run takes those instead.
+  *bytes = L.bytes();
   return DD_OK;
 }
 
@@ -562,11 +787,8 @@ dd_status dd_plan_device_status(dd_plan plan, void* stream) {
 static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const void* h_in,
                                    int64_t tm_stride, void* d_tm, int64_t n_samp, void* h_out,
                                    void* d_cm, int64_t cm_stride, void* d_out_stage,
-                                   void* d_packed, void* stream) {
-  // The plan's copy streams and events are shared: calls from several host
-  // threads enqueue one after the other (each wait captures its own record).
-  static std::mutex host_mu;
-  std::lock_guard<std::mutex> lock(host_mu);
+                                   void* d_packed, bool with_auto, void* stream) {
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
   HostPipe* hp = nullptr;
   cudaError_t e = host_pipe(plan, &hp);
   if (e != cudaSuccess) return cuda_fail(e, "dd_run_host streams");
@@ -588,7 +810,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   const int64_t packed_stride = (n_samp + 3) / 4 * 4;
   int32_t pair = -1;  // lag of the packed copy behind the copied samples (-1: none)
   for (const auto& rp : plan->ranges)
-    if (d_packed && rp.tile_ok && tk::packed_copy_kind(rp.tile_kind)) pair = pack_pair(rp);
+    if (d_packed && copy_kind(rp, with_auto)) pair = pack_pair(rp, copy_kind(rp, with_auto));
   int64_t packed_done = 0;
   int64_t raw_done = 0;
   int64_t done[DD_MAX_RANGES] = {};
@@ -650,7 +872,8 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
     int64_t lim[DD_MAX_RANGES];
     for (size_t r = 0; r < plan->ranges.size(); ++r) {
       const RangePlan& rp = plan->ranges[r];
-      const bool from_packed = pair >= 0 && rp.tile_ok && tk::packed_copy_kind(rp.tile_kind);
+      const int kind = pair >= 0 ? copy_kind(rp, with_auto) : 0;
+      const bool from_packed = kind != 0;
       const int64_t n_out = info.n_out[r];
       int64_t l = n_out;
       if (!last) {
@@ -664,7 +887,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
       if (l > done[r]) {
         const int le = launch_range(plan, rp, from_packed ? d_packed : dcm,
                                     from_packed ? packed_stride : cm_stride, n_samp, n_out,
-                                    dout + info.out_offset[r] * 4, done[r], l, sc);
+                                    dout + info.out_offset[r] * 4, done[r], l, sc, kind);
         if (le != 0) return cuda_fail(le, "dd_run_host forward launch");
       }
     }
@@ -698,7 +921,14 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
   dd_plan_info info;
   dd_status st = check_run(plan, d_in_stage, in_row_stride, n_samp, d_out_stage, &info);
   if (st != DD_OK) return st;
-  const size_t need = packed_input_bytes(plan, n_samp);
+  // Automatic tiles with a copy kind read the packed copy too when the
+  // scratch holds it and it is the one bin-1 copy the pipeline makes.
+  bool with_auto = full_with_auto(plan, n_samp, d_scratch, scratch_bytes);
+  if (with_auto) {
+    const auto all = packed_copies(plan, n_samp, nullptr, true);
+    with_auto = all.size() == 1 && all[0].bin == 1;
+  }
+  const size_t need = packed_input_bytes(plan, n_samp, with_auto);
   if (need > 0) {
     if (!d_scratch)
       return fail(DD_ERR_UNSUPPORTED,
@@ -707,14 +937,15 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
     if (scratch_bytes < need) return fail(DD_ERR_BUDGET, "input scratch too small");
     if (reinterpret_cast<uintptr_t>(d_scratch) % 16 != 0)
       return fail(DD_ERR_SHAPE, "input scratch must be 16-byte aligned");
-    const auto copies = packed_copies(plan, n_samp, nullptr);
+    const auto copies = packed_copies(plan, n_samp, nullptr, with_auto);
     if (copies.size() != 1 || copies[0].bin != 1)
       return fail(DD_ERR_UNSUPPORTED,
                   "the host pipeline packs one copy at bin 1: binned packed ranges run "
                   "through dd_run_scratch");
   }
   return run_host_pipeline(plan, info, h_in, 0, nullptr, n_samp, h_out, d_in_stage,
-                           in_row_stride, d_out_stage, need > 0 ? d_scratch : nullptr, stream);
+                           in_row_stride, d_out_stage, need > 0 ? d_scratch : nullptr,
+                           with_auto, stream);
 }
 
 dd_status dd_run_host(dd_plan plan, const void* h_in, int64_t in_row_stride, int64_t n_samp,
@@ -771,7 +1002,7 @@ dd_status dd_run_host_tmajor(dd_plan plan, const void* h_in, int64_t in_row_stri
                        d_cm_stage, cm_row_stride, 0, n_samp);
   if (st != DD_OK) return st;
   return run_host_pipeline(plan, info, h_in, in_row_stride, d_tm_stage, n_samp, h_out,
-                           d_cm_stage, cm_row_stride, d_out_stage, nullptr, stream);
+                           d_cm_stage, cm_row_stride, d_out_stage, nullptr, false, stream);
 }
 
 }  // extern "C"

@@ -53,6 +53,11 @@ struct RangePlan {
   size_t tile_chunk_off = 0;    // pair tiles: byte offset of the pair chunks in tile_recs
   int32_t tile_chunk_bytes = 0; // pair tiles: bytes per (DM block, stage) chunk
   int32_t tile_n_chan = 0;      // rows of the tables' input when not the plan's channels
+  // Automatic pattern tiles of uint8, 4-bit and uint16 input at time bin 1:
+  // the packed-copy kind (kU8P, kU16P) whose kernel runs the same tables
+  // from a packed copy of the input (the tables are planned at the plain
+  // kind's window alignment, a multiple of the packed kind's); 0 if none.
+  int32_t alt_kind = 0;
 
   // Byte offsets of the device tables inside the workspace.
   size_t off_shifts = 0;        // int32 [n_dm][n_chan]
@@ -120,22 +125,29 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
 // The pattern kernel (fwd_pattern.cu), same arguments; output row d + 1
 // starts out_stride elements after row d (n_out for the output layout of
 // dd_run; negative for rows written in reverse order).
+// `kind` > 0 runs the tables with that kernel kind (a packed-copy kind the
+// range's copy_kind allows) and `x_origin` is the sample held by element 0
+// of each input row (a time segment's packed words in a ring slot; a
+// multiple of the tables' window alignment).
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                            void* d_out, int64_t t_begin, int64_t t_end, void* stream,
-                           int64_t out_stride);
+                           int64_t out_stride, int kind = 0, int64_t x_origin = 0);
 // Packed uint8 copy for the kU8P tiles (pack.cu): out[c][t] = in[c][t] |
 // in[c][t + pair] << 16 for t in [t_begin, t_end) (0 past n_samp); strides in
-// bytes (in) and 32-bit words (out, a multiple of 4 and >= n_samp); pair and
-// t_begin multiples of 16, t_end of 4 and <= out_stride.  Source kU4: 4-bit
+// bytes (in) and 32-bit words (out, a multiple of 4); pair and t_begin
+// multiples of 16, t_end of 4.  Source kU4: 4-bit
 // input, two samples per byte (the earlier in the low nibble); kU16: uint16
 // input widened, out[c][t] = in[c][t] (pair unused); kF32: float32 input,
 // 64-bit words out[c][t] = (in[c][t], in[c][t + pair]) (out_stride in those
 // words).
 enum class PackSource { kU8, kU4, kU16, kF32 };
+// out_origin: the word held by element 0 of each output row (a ring slot
+// holding words [out_origin, out_origin + out_stride)); t_begin >= out_origin,
+// t_end <= out_origin + out_stride, out_origin a multiple of 16.
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, PackSource src, void* stream);
+                      int64_t t_end, PackSource src, void* stream, int64_t out_origin = 0);
 // uint8 decimated by bin (2, 4, 8) into packed pair words of decimated samples
 // (pack.cu): out[c][t] = D[c][t] | D[c][t + pair] << 16, D the sums of bin
 // consecutive samples, t < out_stride (a multiple of 4, >= n_samp / bin), 0
@@ -143,10 +155,20 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
 int launch_pack_pairs_binned(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                              int32_t bin, void* d_out, int64_t out_stride, int32_t pair,
                              void* stream);
-// Pair distance and source of a range's packed copy.
-inline int32_t pack_pair(const RangePlan& rp) {
-  return rp.tile_kind == tk::kU8P || rp.tile_kind == tk::kF32P ? 32 * rp.tile_h : 0;
+// The kernel kind that runs range rp from a packed copy of the input: its
+// own kind on DD_TILE_PACKED, the alternative kind of an automatic pattern
+// tile when `with_auto` (the caller's scratch holds copies for those too),
+// else 0 (the range reads the input itself).
+inline int copy_kind(const RangePlan& rp, bool with_auto) {
+  if (!rp.tile_ok || !rp.tile_pattern) return 0;
+  if (tk::packed_copy_kind(rp.tile_kind)) return rp.tile_kind;
+  return with_auto ? rp.alt_kind : 0;
 }
+// Pair distance of the packed copy a range reads with kernel kind `kind`.
+inline int32_t pack_pair(const RangePlan& rp, int kind) {
+  return kind == tk::kU8P || kind == tk::kF32P ? 32 * rp.tile_h : 0;
+}
+inline int32_t pack_pair(const RangePlan& rp) { return pack_pair(rp, rp.tile_kind); }
 inline PackSource pack_source(dd_dtype dtype) {
   return dtype == DD_U16   ? PackSource::kU16
          : dtype == DD_U4  ? PackSource::kU4
@@ -163,11 +185,12 @@ struct PackedCopy {
   size_t offset;   // bytes into the scratch
   size_t bytes;
 };
-// The copies, and for each range its copy (-1: reads the input itself).
+// The copies, and for each range its copy (-1: reads the input itself);
+// with_auto: also the copies of the automatic tiles with an alt_kind.
 std::vector<PackedCopy> packed_copies(const dd_plan_s* p, int64_t n_samp,
-                                      std::vector<int32_t>* range_copy);
+                                      std::vector<int32_t>* range_copy, bool with_auto = false);
 // Bytes all copies take (0 without a packed range).
-size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp);
+size_t packed_input_bytes(const dd_plan_s* p, int64_t n_samp, bool with_auto = false);
 // Write one copy of the input (in_stride in samples) into scratch.
 int launch_pack_copy(const dd_plan_s* p, const PackedCopy& pc, const void* d_in, int64_t in_stride,
                      int64_t n_samp, void* d_scratch, void* stream);
@@ -195,7 +218,7 @@ size_t adjoint_scratch_bytes(const dd_plan_s* p, int64_t n_samp);
 
 tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                            void* d_out);
+                            void* d_out, int kind = 0);
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
 // Per-kind launchers of the pattern kernels (fwd_pattern_k*.cu): the
 // one-unit-per-CTA kernel and the persistent batch kernel of kPatShapes[shape].

@@ -12,10 +12,13 @@ namespace dd {
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                            void* d_out, int64_t t_begin, int64_t t_end, void* stream,
-                           int64_t out_stride) {
-  tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
+                           int64_t out_stride, int kind, int64_t x_origin) {
+  if (kind <= 0) kind = rp.tile_kind;
+  tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out, kind);
   prm.out_stride = out_stride;
-  const int ts = tk::pat_tile_samples(rp.tile_kind, rp.tile_h);
+  prm.x_origin = x_origin;
+  if (x_origin < 0 || x_origin % prm.align != 0) return static_cast<int>(cudaErrorInvalidValue);
+  const int ts = tk::pat_tile_samples(kind, rp.tile_h);
   if (t_begin % ts != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)
     return static_cast<int>(cudaErrorInvalidValue);
   prm.tile0 = t_begin / ts;
@@ -24,7 +27,7 @@ int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* 
   const int64_t grid = tiles * rp.tile_n_blocks;
   if (grid <= 0 || grid > 0x7fffffffLL) return static_cast<int>(cudaErrorInvalidConfiguration);
   const int shape = rp.tile_shape;
-  switch (rp.tile_kind) {
+  switch (kind) {
 #define DD_CASE(K) \
   case tk::K: return pattern_forward_##K(shape, prm, grid, stream);
     DD_PATTERN_KINDS(DD_CASE)

@@ -305,10 +305,15 @@ int launch_kind(int dr, const tk::TileParams& prm, int64_t grid, cudaStream_t st
 
 tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                            void* d_out) {
+                            void* d_out, int kind) {
+  // The tables were built for rp.tile_kind; `kind` (a packed-copy kind, see
+  // copy_kind) may run them from a packed copy of the input.
+  if (kind <= 0) kind = rp.tile_kind;
   tk::TileParams prm{};
   prm.x = d_in;
   prm.stride = stride;
+  prm.x_origin = 0;
+  prm.align = tk::align_samples(rp.tile_kind, tk::staged_bin(rp.tile_kind, rp.r.bin));
   prm.n_chan = rp.tile_n_chan > 0 ? rp.tile_n_chan : p->n_chan;
   prm.recs = recs;
   if (rp.tile_pattern && rp.tile_chunk_bytes > 0) {  // pair tiles: base table, then chunks
@@ -323,16 +328,16 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.tile0 = 0;
   prm.t_end = n_out;
   prm.lp = rp.tile_lp;
-  const int sb = tk::staged_bin(rp.tile_kind, rp.r.bin);  // packed copies: already decimated
+  const int sb = tk::staged_bin(kind, rp.r.bin);  // packed copies: already decimated
   prm.lraw = rp.tile_pattern
-                 ? tk::pat_raw_bytes(rp.tile_kind, sb, tk::kPatShapes[rp.tile_shape], rp.tile_lp)
-                 : tk::raw_bytes(rp.tile_kind, sb, rp.tile_lp);
+                 ? tk::pat_raw_bytes(kind, sb, tk::kPatShapes[rp.tile_shape], rp.tile_lp)
+                 : tk::raw_bytes(kind, sb, rp.tile_lp);
   prm.units_magic = rp.tile_units_magic;
   prm.units_shift = rp.tile_units_shift;
   prm.bin = sb;
-  prm.flush = tk::flush_channels(rp.tile_kind, rp.r.bin);
+  prm.flush = tk::flush_channels(kind, rp.r.bin);
   // Packed 4-bit input: at most 15 per sample in the 16-bit lanes.
-  if (rp.tile_kind == tk::kU8P && p->dtype == DD_U4) prm.flush = tk::flush_channels(tk::kU4, 1);
+  if (kind == tk::kU8P && p->dtype == DD_U4) prm.flush = tk::flush_channels(tk::kU4, 1);
   prm.out = d_out;
   prm.err = err;
   prm.wait_iters = p->wait_iters;

@@ -315,7 +315,10 @@ inline size_t smem_bytes(int kind, int bin, const Shape& s, int32_t lp) {
 // One (DM block, time tile) work unit of one range.
 struct TileParams {
   const void* x;        // channel-major input rows
-  int64_t stride;       // elements between channel rows
+  int64_t stride;       // elements between channel rows (and the rows' length)
+  int64_t x_origin;     // staged sample held by element 0 of each row (0, or a
+                        // time segment's first word in a ring slot)
+  int32_t align;        // window starts: multiples of this many staged samples
   int32_t n_chan;
   const void* recs;     // [n_blocks][n_chan] Rec or PRec; pair chunks [n_blocks][stages]
   const int32_t* bases; // pair tiles: s(c, first DM of block) [n_blocks][n_chan]

@@ -25,13 +25,14 @@ __global__ void __launch_bounds__(256) pack_pairs_kernel(const uint8_t* __restri
                                                          uint32_t* __restrict__ out,
                                                          int64_t out_stride, int32_t pair,
                                                          int64_t chunks_per_row, int32_t n_chan,
-                                                         int64_t t_begin, int64_t t_end) {
+                                                         int64_t t_begin, int64_t t_end,
+                                                         int64_t origin) {
   const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t c = gid / chunks_per_row;
   const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
   if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
   const uint8_t* row = in + c * in_stride;
-  uint32_t* dst = out + c * out_stride + t;
+  uint32_t* dst = out + c * out_stride + (t - origin);
   uint32_t w[kPackPerThread];
   if (t + pair + kPackPerThread <= n_samp) {
     // Both halves inside the row: two aligned 16-byte loads (t, pair and the
@@ -69,13 +70,13 @@ __global__ void __launch_bounds__(256) pack_pairs4_kernel(const uint8_t* __restr
                                                           uint32_t* __restrict__ out,
                                                           int64_t out_stride, int32_t pair,
                                                           int64_t chunks_per_row, int32_t n_chan,
-                                                          int64_t t_begin, int64_t t_end) {
+                                                          int64_t t_begin, int64_t t_end, int64_t origin) {
   const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t c = gid / chunks_per_row;
   const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
   if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
   const uint8_t* row = in + c * in_stride;
-  uint32_t* dst = out + c * out_stride + t;
+  uint32_t* dst = out + c * out_stride + (t - origin);
   uint32_t w[kPackPerThread];
   if (t + pair + kPackPerThread <= n_samp) {
     // Both halves inside the row: two aligned 8-byte loads (t, pair and the
@@ -105,13 +106,13 @@ __global__ void __launch_bounds__(256) widen16_kernel(const uint8_t* __restrict_
                                                       uint32_t* __restrict__ out,
                                                       int64_t out_stride, int64_t chunks_per_row,
                                                       int32_t n_chan, int64_t t_begin,
-                                                      int64_t t_end) {
+                                                      int64_t t_end, int64_t origin) {
   const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t c = gid / chunks_per_row;
   const int64_t t = t_begin + (gid - c * chunks_per_row) * kPackPerThread;
   if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
   const uint16_t* row = reinterpret_cast<const uint16_t*>(in + c * in_stride);
-  uint32_t* dst = out + c * out_stride + t;
+  uint32_t* dst = out + c * out_stride + (t - origin);
   uint32_t w[kPackPerThread];
   if (t + kPackPerThread <= n_samp) {
     // Two aligned 16-byte loads (t is a multiple of 16, rows 16-byte aligned).
@@ -141,13 +142,13 @@ __global__ void __launch_bounds__(256) pack_f32_pairs_kernel(const float* __rest
                                                              int64_t out_stride, int32_t pair,
                                                              int64_t chunks_per_row,
                                                              int32_t n_chan, int64_t t_begin,
-                                                             int64_t t_end) {
+                                                             int64_t t_end, int64_t origin) {
   const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t c = gid / chunks_per_row;
   const int64_t t = t_begin + (gid - c * chunks_per_row) * 4;
   if (c >= n_chan || t >= t_end) return;  // the last block's spare threads
   const float* row = in + c * in_stride;
-  float2* dst = out + c * out_stride + t;
+  float2* dst = out + c * out_stride + (t - origin);
   float a[4], b[4];
   if (t + pair + 4 <= n_samp) {
     // Both halves inside the row: two aligned 16-byte loads (t, pair and the
@@ -259,10 +260,11 @@ int launch_pack_pairs_binned(const void* d_in, int64_t in_stride, int32_t n_chan
 
 int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64_t n_samp,
                       void* d_out, int64_t out_stride, int32_t pair, int64_t t_begin,
-                      int64_t t_end, PackSource src, void* stream) {
+                      int64_t t_end, PackSource src, void* stream, int64_t out_origin) {
   if (n_chan <= 0 || n_samp <= 0 || t_end <= t_begin) return 0;
-  if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_stride < n_samp ||
-      t_begin % 16 != 0 || t_begin < 0 || t_end % 4 != 0 || t_end > out_stride)
+  if (pair % 16 != 0 || in_stride % 16 != 0 || out_stride % 4 != 0 || out_origin < 0 ||
+      out_origin % 16 != 0 || t_begin % 16 != 0 || t_begin < out_origin || t_end % 4 != 0 ||
+      t_end > out_origin + out_stride)
     return static_cast<int>(cudaErrorInvalidValue);
   if (src == PackSource::kF32) {
     const int64_t chunks = (t_end - t_begin) / 4;
@@ -271,7 +273,7 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
     pack_f32_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0,
                             static_cast<cudaStream_t>(stream)>>>(
         static_cast<const float*>(d_in), in_stride / 4, n_samp, static_cast<float2*>(d_out),
-        out_stride, pair, chunks, n_chan, t_begin, t_end);
+        out_stride, pair, chunks, n_chan, t_begin, t_end, out_origin);
     return static_cast<int>(cudaGetLastError());
   }
   const int64_t chunks = (t_end - t_begin + kPackPerThread - 1) / kPackPerThread;
@@ -283,13 +285,13 @@ int launch_pack_pairs(const void* d_in, int64_t in_stride, int32_t n_chan, int64
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (src == PackSource::kU16)
     widen16_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        in, in_stride, n_samp, out, out_stride, chunks, n_chan, t_begin, t_end);
+        in, in_stride, n_samp, out, out_stride, chunks, n_chan, t_begin, t_end, out_origin);
   else if (src == PackSource::kU4)
     pack_pairs4_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end);
+        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end, out_origin);
   else
     pack_pairs_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end);
+        in, in_stride, n_samp, out, out_stride, pair, chunks, n_chan, t_begin, t_end, out_origin);
   return static_cast<int>(cudaGetLastError());
 }
 

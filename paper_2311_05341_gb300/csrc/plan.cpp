@@ -338,6 +338,7 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
   rp.tile_kind = 0;
   rp.tile_chunk_off = 0;
   rp.tile_chunk_bytes = 0;
+  rp.alt_kind = 0;
   rp.tile_recs.clear();
   // Packed input at bin 1: uint8 and 4-bit share the paired word format,
   // uint16 is widened to one sample per word.
@@ -369,7 +370,21 @@ void choose_tile(RangePlan& rp, int32_t n_chan, dd_dtype dtype) {
       for (int i = 0; i < tk::kNumPatShapes; ++i)
         if (candidate(i) && try_pattern_shape(rp, n_chan, tk::kF32D, i)) return;
     for (int i = 0; i < tk::kNumPatShapes; ++i)
-      if (candidate(i) && try_pattern_shape(rp, n_chan, kind, i)) return;
+      if (candidate(i) && try_pattern_shape(rp, n_chan, kind, i)) {
+        // The automatic tile of uint8, 4-bit or uint16 input at bin 1 can
+        // also run from a packed copy (dd_run_scratch with the scratch of
+        // dd_plan_packed_scratch_bytes): same tables, the packed kernel's
+        // two staging buffers must fit shared memory too.
+        const int alt = kind == tk::kU16 ? static_cast<int>(tk::kU16P)
+                                         : static_cast<int>(tk::kU8P);
+        const tk::PatShape& ps = tk::kPatShapes[i];
+        if (rp.tile_request == 0 && rp.shape_request < 0 && b == 1 &&
+            (kind == tk::kU8 || kind == tk::kU4 || kind == tk::kU16) &&
+            tk::pat_shape_serves(ps, alt) &&
+            tk::pat_smem_bytes(alt, 1, ps, rp.tile_lp) <= 227 * 1024)
+          rp.alt_kind = alt;
+        return;
+      }
     if (rp.tile_request != 0) return;
   }
   if (rp.tile_request > 0) {

@@ -205,9 +205,12 @@ __device__ __forceinline__ void issue_stage(const TileParams& p, uint32_t bar_ba
     uint32_t bytes = 0;
     const uint8_t* src = nullptr;
     if (c < p.n_chan) {
-      const int64_t align = align_samples(KIND, p.bin);              // decimated samples, 2^k
-      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin;      // raw samples
-      if (ua < p.stride) {
+      // Window start: the planner's alignment (a power of two, decimated
+      // samples, a multiple of the 16 bytes a copy starts on), as raw
+      // samples from element 0 of the row.
+      const int64_t align = p.align;
+      const int64_t ua = ((t0 + base) & ~(align - 1)) * p.bin - p.x_origin;
+      if (ua >= 0 && ua < p.stride) {
         const int64_t room = sample_bytes(KIND, p.stride - ua);
         bytes = static_cast<uint32_t>(room < p.lraw ? room : p.lraw);
         src = static_cast<const uint8_t*>(p.x) +

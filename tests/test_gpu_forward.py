@@ -304,19 +304,23 @@ def _sampled_parity(beam, x, planes_gpu, n_dm, n_out, pulse_rows):
         np.testing.assert_array_equal(g, o)
 
 
-@pytest.mark.parametrize("make,tile", [(workloads.paper_u8, 0), (workloads.paper_u8, "pattern"),
-                                       (workloads.paper_u8, "packed"), (workloads.paper_u8, 6),
-                                       (workloads.paper_u16, 0)],
-                         ids=["paper_u8", "paper_u8_pattern", "paper_u8_packed", "paper_u8_offset6",
-                              "paper_u16"])
-def test_paper_scale_sampled(make, tile):
+# (workload, tile, segments): the automatic tile from the packed ring (the
+# default of Plan.run) and unpacking the input itself (no scratch), the
+# explicit pattern tile, the packed tile from its full copy, an offset tile.
+@pytest.mark.parametrize("make,tile,segments",
+                         [(workloads.paper_u8, 0, 8), (workloads.paper_u8, 0, 0),
+                          (workloads.paper_u8, "pattern", 16), (workloads.paper_u8, "packed", 1),
+                          (workloads.paper_u8, 6, 16), (workloads.paper_u16, 0, 16)],
+                         ids=["paper_u8_ring", "paper_u8_unpacked", "paper_u8_pattern",
+                              "paper_u8_packed_full", "paper_u8_offset6", "paper_u16_ring"])
+def test_paper_scale_sampled(make, tile, segments):
     beam = make()
     x, tables, n_dm, n_out = oracle_input(beam)
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
     if tile:
         plan.set_tile(0, tile)
     xt = torch.from_numpy(x).cuda()
-    planes = plan.run(xt)
+    planes = plan.run(xt, segments=segments)
     torch.cuda.synchronize()
     assert planes[0].shape == (n_dm[0], n_out[0])
     pulses = workloads.resolve_pulses(beam, n_dm, n_out)
@@ -337,21 +341,22 @@ def test_paper_scale_sampled(make, tile):
                            "set DD_FULL_PLANE=1 to run it")
 def test_paper_u8_full_plane():
     """Every output of the paper-scale uint8 plane (4096 x 257097) against the
-    oracle, on the automatic tile and on the packed tile the benchmark runs."""
+    oracle: the automatic tile from the packed ring (what the benchmark runs)
+    and unpacking the input itself, and the packed tile from its full copy."""
     beam = workloads.paper_u8()
     x, _, n_dm, n_out = oracle_input(beam)
     xt = torch.from_numpy(x).cuda()
     plan = dd.Plan(beam.freqs, beam.f_high, beam.t_samp, beam.ranges, beam.dtype)
-    auto = plan.run(xt)[0]
+    planes = {"ring": plan.run(xt, segments=8)[0], "unpacked": plan.run(xt, segments=0)[0]}
     plan.set_tile(0, "packed")
-    packed = plan.run(xt)[0]
+    planes["packed full copy"] = plan.run(xt, segments=1)[0]
     torch.cuda.synchronize()
-    assert auto.shape == (n_dm[0], n_out[0]) == packed.shape
+    for p in planes.values():
+        assert p.shape == (n_dm[0], n_out[0])
     block = 256
     for d0 in range(0, n_dm[0], block):
         rows = list(range(d0, min(d0 + block, n_dm[0])))
         ref = oracle.forward_rows(x, beam.freqs, beam.f_high, beam.t_samp, beam.ranges[0], rows)
-        np.testing.assert_array_equal(auto[d0:d0 + len(rows)].cpu().numpy(), ref,
-                                      err_msg=f"automatic tile, rows {d0}..")
-        np.testing.assert_array_equal(packed[d0:d0 + len(rows)].cpu().numpy(), ref,
-                                      err_msg=f"packed tile, rows {d0}..")
+        for name, p in planes.items():
+            np.testing.assert_array_equal(p[d0:d0 + len(rows)].cpu().numpy(), ref,
+                                          err_msg=f"{name}, rows {d0}..")

@@ -24,7 +24,7 @@ _NP = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32}
 _NOISE = {"u8": (128, 30), "u16": (32768, 3000), "f32": (0.0, 1.0)}
 
 
-def _host_vs_device(freqs, f_ref, t_samp, ranges, dtype, n_samp, seed):
+def _host_vs_device(freqs, f_ref, t_samp, ranges, dtype, n_samp, seed, packed=True):
     plan = dd.Plan(freqs, f_ref, t_samp, ranges, dtype)
     per = 16 // np.dtype(_NP[dtype]).itemsize
     stride = (n_samp + per - 1) // per * per
@@ -36,7 +36,7 @@ def _host_vs_device(freqs, f_ref, t_samp, ranges, dtype, n_samp, seed):
     h_out = torch.full((info["out_elems"],), -5, dtype=out_dt).pin_memory()
     d_in = torch.empty_like(h_in, device="cuda")
     d_out = plan.empty_output(n_samp)
-    plan.run_host(h_in, h_out, d_in, d_out, n_samp=n_samp)
+    plan.run_host(h_in, h_out, d_in, d_out, n_samp=n_samp, packed=packed)
     torch.cuda.synchronize()
     ref_dev = plan.run(h_in.cuda(), n_samp=n_samp)
     flat = torch.cat([p.reshape(-1) for p in ref_dev]).cpu()
@@ -44,15 +44,19 @@ def _host_vs_device(freqs, f_ref, t_samp, ranges, dtype, n_samp, seed):
     return plan, x, h_out, info
 
 
-@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
-def test_host_path_equals_device_path_and_oracle(dtype):
+# packed: the automatic uint8 and uint16 tiles at bin 1 read the packed copy
+# the pipeline makes as the input arrives, or unpack the input themselves.
+@pytest.mark.parametrize("dtype,packed", [("u8", True), ("u8", False), ("u16", True),
+                                          ("u16", False), ("f32", True)])
+def test_host_path_equals_device_path_and_oracle(dtype, packed):
     freqs = channel_freqs(1500.0, 300.0, 97)
     # Four ranges: pattern and offset tiles, decimation, and a time bin (3)
     # that only the generic kernel takes.
     ranges = [(0.0, 6.0, 0.05, 1), (6.0, 12.0, 0.1, 2), (12.0, 30.0, 0.3, 3),
               (30.0, 60.0, 1.0, 4)]
     n_samp = 40001
-    plan, x, h_out, info = _host_vs_device(freqs, 1500.0, 64e-6, ranges, dtype, n_samp, 11)
+    plan, x, h_out, info = _host_vs_device(freqs, 1500.0, 64e-6, ranges, dtype, n_samp, 11,
+                                           packed)
     ref = oracle.forward(x[:, :n_samp], freqs, 1500.0, 64e-6, ranges)
     planes = plan.split(h_out, n_samp)
     for r, (g, o) in enumerate(zip(planes, ref)):

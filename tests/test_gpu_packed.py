@@ -28,8 +28,9 @@ def _plan(freqs, f_high, ranges, tiles):
     return plan
 
 
+@pytest.mark.parametrize("segments", [1, 16])
 @pytest.mark.parametrize("seed", range(8))
-def test_packed_random_plans(seed):
+def test_packed_random_plans(seed, segments):
     """Ragged channel counts, DM counts and lengths (the last packed words of
     a row pair a sample with zeros past n_samp), mixed with a plain range."""
     rng = np.random.default_rng(5200 + seed)
@@ -52,7 +53,8 @@ def test_packed_random_plans(seed):
     ref = oracle.forward(np.ascontiguousarray(x[:, :n_samp]), freqs, f_high, 64e-6, ranges)
     plan = _plan(freqs, f_high, ranges, tiles)
     assert plan.info(n_samp)["tile_dms"][0] == _lib.DD_TILE_PACKED
-    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
+    # The full copy, or the ring of 16 time segments.
+    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp, segments=segments)
     for r, (g, o) in enumerate(zip(got, ref)):
         np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")
 
@@ -146,7 +148,8 @@ def test_packed_uint16(seed):
     plan.set_tile(0, "packed")
     info = plan.info(n_samp)
     assert info["tile_dms"][0] == _lib.DD_TILE_PACKED
-    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
+    # The full copy (odd seeds) or the ring of 16 time segments.
+    got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp, segments=1 if seed % 2 else 16)
     for r, (g, o) in enumerate(zip(got, ref)):
         np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")
     h_in = torch.from_numpy(x).pin_memory()
@@ -243,6 +246,7 @@ def test_packed_binned_uint8(seed):
         plan.set_tile(r, t)
     info = plan.info(n_samp)
     assert info["tile_dms"][:4] == [_lib.DD_TILE_PACKED] * 4
+    # Binned copies have no ring: the full copies.
     got = plan.run(torch.from_numpy(x).cuda(), n_samp=n_samp)
     for r, (g, o) in enumerate(zip(got, ref)):
         np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"range {r}")

@@ -238,7 +238,13 @@ def test_tile_shape_table_and_explicit_shapes():
     f2 = [i for i, s in enumerate(shapes) if s["float_pairs"]]
     f32 = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "f32", upload=False)
     for i in f2:
-        f32.set_tile_shape(0, "packed", i)
+        # A window that does not fit shared memory (32 channels of float-pair
+        # words on this plan) is refused; the automatic shapes all fit.
+        try:
+            f32.set_tile_shape(0, "packed", i)
+        except dd.DDError as e:
+            assert e.status == _lib.DD_ERR_UNSUPPORTED and not shapes[i]["automatic"]
+            continue
         assert f32.info(paper.n_samp)["tile_shape"] == [i]
     lib = _lib.load()
     assert lib.dd_plan_set_tile_shape(plan.handle, 0, 6, 0) == _lib.DD_ERR_INVALID_ARG
@@ -350,3 +356,55 @@ def test_packed_tile_selection_and_scratch_bytes():
     assert lib.dd_plan_input_scratch_bytes(plan.handle, 0, ctypes.byref(need)) == \
         _lib.DD_ERR_SHAPE
     assert lib.dd_plan_input_scratch_bytes(plan.handle, 10, None) == _lib.DD_ERR_INVALID_ARG
+
+
+def test_packed_copy_flags_and_ring_sizes():
+    """The automatic pattern tile of uint8, 4-bit and uint16 input at bin 1 can
+    run from a packed copy (float32's automatic tile, binned uint8 and offset
+    tiles cannot); the full copies are n_chan x ceil4(n_samp) words and a ring
+    of n segments holds two slots of about n_out / n + the largest delay words
+    per channel (plus a time tile and alignment)."""
+    paper = workloads.paper_u8()
+    n_samp = paper.n_samp
+    for dtype in ("u8", "u4", "u16"):
+        plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, dtype,
+                       upload=False)
+        info = plan.info(n_samp)
+        assert info["packed_copy"] == [True], dtype
+        assert plan.input_scratch_bytes(n_samp) == 0  # nothing is required
+        full = plan.packed_scratch_bytes(n_samp, 1)
+        assert full == paper.n_chan * n_samp * 4
+        n_out, s_max = info["n_out"][0], info["s_max"][0]
+        ts = 2 * 32 * 23 if dtype != "u16" else 32 * 23  # samples per time tile
+        prev = 2 * full  # two slots of half the outputs each exceed the full copy
+        for n in (2, 4, 16, 64):
+            ring = plan.packed_scratch_bytes(n_samp, n)
+            lo = 2 * paper.n_chan * 4 * (n_out // n + s_max - ts)
+            hi = 2 * paper.n_chan * 4 * (-(-n_out // n) + ts + s_max + 64) + 512
+            assert lo <= ring <= hi, (dtype, n, lo, ring, hi)
+            assert ring <= prev
+            prev = ring
+        assert plan.packed_scratch_bytes(n_samp, 16) < full / 4
+    f32 = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, "f32", upload=False)
+    assert f32.info(n_samp)["packed_copy"] == [False]
+    assert f32.packed_scratch_bytes(n_samp, 16) == 0
+    # Binned uint8 and an explicit pattern or offset tile: no packed copy (nor
+    # a tile whose packed kernel's two staging buffers would not fit).
+    multi = dd.Plan(paper.freqs, paper.f_high, paper.t_samp,
+                    [(0.0, 40.0, 0.1, 1), (40.0, 80.0, 0.2, 2), (80.0, 120.0, 0.1, 1)], "u8",
+                    upload=False)
+    assert multi.info(n_samp)["packed_copy"] == [True, False, True]
+    multi.set_tile(2, "pattern")
+    assert multi.info(n_samp)["packed_copy"] == [True, False, False]
+    multi.set_tile(2, 4)
+    assert multi.info(n_samp)["packed_copy"] == [True, False, False]
+    multi.set_tile(2, 0)
+    assert multi.info(n_samp)["packed_copy"] == [True, False, True]
+    # Two pair distances would need two copies: no ring, full copies only.
+    mixed = dd.Plan(paper.freqs, paper.f_high, paper.t_samp,
+                    [(0.0, 40.0, 0.1, 1), (40.0, 80.0, 0.1, 1)], "u8", upload=False)
+    mixed.set_tile_shape(1, "packed", 15)  # H = 19: pair distance 608
+    with pytest.raises(dd.DDError) as ei:
+        mixed.packed_scratch_bytes(n_samp, 8)
+    assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
+    assert mixed.packed_scratch_bytes(n_samp, 1) > 0
