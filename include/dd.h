@@ -479,9 +479,8 @@ dd_status dd_run_host_scratch(dd_plan plan, const void* h_in, int64_t in_row_str
  *   - d_in / in_row_stride / n_samp / d_out follow dd_run; the plan needs no
  *     dd_plan_upload.  The call allocates nothing and frees nothing.
  *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any CUDA
- *     stream capture.  The address is cached for the life of the process:
- *     cudaDeviceReset between calls is not supported.
+ *     device, with that device current).  The address is cached for the life
+ *     of the process: cudaDeviceReset between calls is not supported.
  *   - All calls share the one array, which keeps the last call's contents;
  *     each call copies its tables in on `stream` first.  Calls that overlap on
  *     the GPU (different streams, or host threads) race on the array and give
