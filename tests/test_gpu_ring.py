@@ -155,3 +155,33 @@ def test_ring_scratch_query_and_refusals():
     st = lib.dd_run_scratch(plan.handle, xd.data_ptr(), xd.stride(0), 20000, out.data_ptr(),
                             small.data_ptr(), small.numel(), None)
     assert st == _lib.DD_ERR_BUDGET
+
+
+def test_two_copies_fall_back_to_full_copy_and_unpacking():
+    """An explicit packed range at another pair distance (H = 19) beside an
+    automatic range (H = 23) needs two copies, so no ring: scratch for the
+    explicit copy alone runs that range packed and the automatic one unpacking
+    the input; scratch for both copies runs both packed.  Every output against
+    the oracle."""
+    freqs = channel_freqs(1500.0, 300.0, 160)
+    ranges = [(0.0, 6.4, 0.05, 1), (6.4, 12.8, 0.05, 1)]
+    n_samp = 30000
+    x, xd = _input("u8", 160, n_samp, 6700)
+    ref = oracle.forward(x, freqs, 1500.0, 64e-6, ranges)
+    plan = dd.Plan(freqs, 1500.0, 64e-6, ranges, "u8")
+    shapes = dd.tile_shapes()
+    h19 = [i for i, s in enumerate(shapes) if s["words_per_lane"] == 19 and s["channel_pairs"]
+           and not s["float_pairs"]][0]
+    plan.set_tile_shape(1, "packed", h19)
+    assert plan.info(n_samp)["packed_copy"] == [True, True]
+    with pytest.raises(dd.DDError):
+        plan.packed_scratch_bytes(n_samp, 8)
+    lib = _lib.load()
+    out = plan.empty_output(n_samp)
+    for nbytes in (plan.input_scratch_bytes(n_samp), plan.packed_scratch_bytes(n_samp, 1)):
+        sc = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        _lib.check(lib.dd_run_scratch(plan.handle, xd.data_ptr(), xd.stride(0), n_samp,
+                                      out.data_ptr(), sc.data_ptr(), nbytes, None))
+        torch.cuda.synchronize()
+        for r, (g, o) in enumerate(zip(plan.split(out, n_samp), ref)):
+            np.testing.assert_array_equal(g.cpu().numpy(), o, err_msg=f"{nbytes} B, range {r}")
