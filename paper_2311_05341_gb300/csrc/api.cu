@@ -504,7 +504,8 @@ dd_status dd_plan_upload(dd_plan plan, void* d_workspace, size_t bytes, void* st
   if (!plan || !d_workspace) return fail(DD_ERR_INVALID_ARG, "plan or workspace is NULL");
   if (bytes < plan->ws_bytes) return fail(DD_ERR_BUDGET, "workspace smaller than workspace_bytes");
   if (!aligned16(d_workspace)) return fail(DD_ERR_SHAPE, "workspace must be 16-byte aligned");
-  cudaError_t e = cudaMemcpyAsync(d_workspace, plan->host_ws.data(), plan->ws_bytes,
+  // The image ends before the widening slots, which need no contents.
+  cudaError_t e = cudaMemcpyAsync(d_workspace, plan->host_ws.data(), plan->host_ws.size(),
                                   cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dd_plan_upload");
   plan->d_ws = d_workspace;

@@ -87,6 +87,13 @@ struct dd_plan_s {
   // wait gives up, and the channel stage whose copies are withheld (-1: none).
   int32_t wait_iters = dd::tk::kWaitIters;
   int32_t hold_stage = -1;
+  // Widening slots in the workspace (plan.cpp, layout_workspace): 64-bit
+  // words per slot (0: none) and byte offsets of the slot flags and slots.
+  // The workspace image (host_ws) ends before the slots: they need no
+  // initial contents.
+  int32_t wslot_words = 0;
+  size_t off_wflags = 0;
+  size_t off_wslots = 0;
 };
 
 namespace dd {
@@ -118,10 +125,12 @@ int launch_forward_tiled(const dd_plan_s* p, const RangePlan& rp, const void* d_
                          int64_t t_begin, int64_t t_end, void* stream);
 // The tiled kernel with its record table and status word at explicit device
 // addresses (used by the no-allocation entry point and the batch runtime).
+// widen_slots = false: the widening never uses the plan workspace's slots
+// (the no-allocation entry point, whose plan may have no workspace).
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
-                                     void* stream);
+                                     void* stream, bool widen_slots = true);
 // The pattern kernel (fwd_pattern.cu), same arguments; output row d + 1
 // starts out_stride elements after row d (n_out for the output layout of
 // dd_run; negative for rows written in reverse order).
@@ -132,7 +141,8 @@ int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, co
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                            void* d_out, int64_t t_begin, int64_t t_end, void* stream,
-                           int64_t out_stride, int kind = 0, int64_t x_origin = 0);
+                           int64_t out_stride, int kind = 0, int64_t x_origin = 0,
+                           bool widen_slots = true);
 // Packed uint8 copy for the kU8P tiles (pack.cu): out[c][t] = in[c][t] |
 // in[c][t + pair] << 16 for t in [t_begin, t_end) (0 past n_samp); strides in
 // bytes (in) and 32-bit words (out, a multiple of 4); pair and t_begin
@@ -218,7 +228,7 @@ size_t adjoint_scratch_bytes(const dd_plan_s* p, int64_t n_samp);
 
 tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                            void* d_out, int kind = 0);
+                            void* d_out, int kind = 0, bool widen_slots = true);
 int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* stream);
 // Per-kind launchers of the pattern kernels (fwd_pattern_k*.cu): the
 // one-unit-per-CTA kernel and the persistent batch kernel of kPatShapes[shape].

@@ -12,9 +12,10 @@ namespace dd {
 int launch_forward_pattern(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                            int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
                            void* d_out, int64_t t_begin, int64_t t_end, void* stream,
-                           int64_t out_stride, int kind, int64_t x_origin) {
+                           int64_t out_stride, int kind, int64_t x_origin, bool widen_slots) {
   if (kind <= 0) kind = rp.tile_kind;
-  tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out, kind);
+  tk::TileParams prm =
+      tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out, kind, widen_slots);
   prm.out_stride = out_stride;
   prm.x_origin = x_origin;
   if (x_origin < 0 || x_origin % prm.align != 0) return static_cast<int>(cudaErrorInvalidValue);

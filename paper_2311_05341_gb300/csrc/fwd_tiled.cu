@@ -305,7 +305,7 @@ int launch_kind(int dr, const tk::TileParams& prm, int64_t grid, cudaStream_t st
 
 tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                             int32_t* err, const void* d_in, int64_t stride, int64_t n_out,
-                            void* d_out, int kind) {
+                            void* d_out, int kind, bool widen_slots) {
   // The tables were built for rp.tile_kind; `kind` (a packed-copy kind, see
   // copy_kind) may run them from a packed copy of the input.
   if (kind <= 0) kind = rp.tile_kind;
@@ -342,6 +342,23 @@ tk::TileParams tiled_params(const dd_plan_s* p, const RangePlan& rp, const void*
   prm.err = err;
   prm.wait_iters = p->wait_iters;
   prm.hold_stage = p->hold_stage;
+  // Pattern tiles with 16-bit lanes widen into the workspace's slots when the
+  // plan has a bound workspace with them (the no-allocation entry point's
+  // tables live elsewhere and widen into the output rows).
+  prm.wslots = nullptr;
+  prm.wflags = nullptr;
+  prm.n_wslots = 0;
+  prm.wslot_words = 0;
+  const int32_t need = tk::kPatDr * (rp.tile_pattern ? tk::kPatShapes[rp.tile_shape].warps : 0) *
+                       32 * rp.tile_h;
+  if (widen_slots && rp.tile_pattern && tk::packed_pairs(kind) && p->d_ws &&
+      p->wslot_words >= need) {
+    unsigned char* ws = static_cast<unsigned char*>(p->d_ws);
+    prm.wslots = reinterpret_cast<unsigned long long*>(ws + p->off_wslots);
+    prm.wflags = reinterpret_cast<int32_t*>(ws + p->off_wflags);
+    prm.n_wslots = tk::kWidenSlots;
+    prm.wslot_words = p->wslot_words;
+  }
   return prm;
 }
 
@@ -354,10 +371,10 @@ int64_t range_tile_samples(const RangePlan& rp) {
 int launch_forward_tiled_with_tables(const dd_plan_s* p, const RangePlan& rp, const void* recs,
                                      int32_t* err, const void* d_in, int64_t stride,
                                      int64_t n_out, void* d_out, int64_t t_begin, int64_t t_end,
-                                     void* stream) {
+                                     void* stream, bool widen_slots) {
   if (rp.tile_pattern)
     return launch_forward_pattern(p, rp, recs, err, d_in, stride, n_out, d_out, t_begin, t_end,
-                                  stream, n_out);
+                                  stream, n_out, 0, 0, widen_slots);
   tk::TileParams prm = tiled_params(p, rp, recs, err, d_in, stride, n_out, d_out);
   const int ts = tk::tile_samples(rp.tile_kind);
   if (t_begin % ts != 0 || t_begin < 0 || t_end > n_out || t_end <= t_begin)

@@ -339,7 +339,22 @@ struct TileParams {
   int32_t* err;
   int32_t wait_iters;   // polls before a pipeline wait gives up (kWaitIters by default)
   int32_t hold_stage;   // channel stage whose copies are never issued (timeout test; -1: none)
+  // Widening slots of the pattern tiles with 16-bit lanes (nullptr: widen
+  // into the output rows).  A CTA holds one slot for the duration of a unit:
+  // each warp widens its lanes into its own part of the slot (64-bit words
+  // of the sums for samples u and u + 32 H) whenever its lanes are full, and
+  // the unit's last stage adds the slot to the lanes and stores each output
+  // once.  The slots live in the plan workspace; wflags[s] is 1 while slot s
+  // is held.
+  unsigned long long* wslots;
+  int32_t* wflags;
+  int32_t n_wslots;
+  int32_t wslot_words;  // 64-bit words per slot
 };
+// Widening slots in a plan workspace: two per SM of the largest GB300-class
+// part (1 CTA per SM for the 16-warp pattern tiles, whose 128 registers per
+// thread fill the register file; the second half covers smaller tiles).
+constexpr int kWidenSlots = 320;
 
 // Persistent batch execution: one work list of (job, DM block, time tile)
 // items over many jobs (plan ranges with their input/output pointers).

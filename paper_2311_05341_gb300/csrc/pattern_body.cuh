@@ -213,6 +213,38 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   const int units = p.lp >> 2;
   int rb = 0;     // st % kRecBufs
 
+  // 16-bit lanes with widening slots: each warp widens into its part of the
+  // CTA's slot on its own schedule (staggered over the warps so that their
+  // reductions spread over the stages), with no barrier; the last stage
+  // stores each output once.  Without a slot (none configured, or none
+  // free) the CTA widens into the output rows together.  The slot index
+  // stays in shared memory (s_wslot, -1: none) and `since` / `first` count
+  // per warp in slot mode, for the CTA otherwise.
+  __shared__ int s_wslot;
+  if constexpr (packed_pairs(KIND)) {
+    if (tid == 0) s_wslot = p.wslots != nullptr ? acquire_wslot(p) : -1;
+    __syncthreads();
+    if (s_wslot >= 0) {
+      constexpr int kStagger = NW < 8 ? NW : 8;
+      since = ((w % kStagger) * p.flush) / kStagger;
+    }
+  }
+  auto warp_slot = [&]() {
+    return p.wslots + static_cast<int64_t>(s_wslot) * p.wslot_words +
+           static_cast<int64_t>(w) * kPatDr * 32 * H;
+  };
+  // Timeout exit with a slot held: every thread's slot writes are ordered
+  // before thread 0 frees it.
+  auto drop_slot = [&]() {
+    if constexpr (packed_pairs(KIND)) {
+      if (s_wslot >= 0) {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) release_wslot(p, s_wslot);
+      }
+    }
+  };
+
   for (int st = 0; st < n_st; ++st) {
     const int buf = st & 1;
     // One stage barrier completes a phase per stage; with kDirect each of the
@@ -245,6 +277,7 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
           // Let the copies still in flight land before the CTA exits (bounded).
           if (st != p.hold_stage) mbar_wait(bar, parity);
         }
+        drop_slot();
         return false;
       }
       issue_next(st);
@@ -302,6 +335,18 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     }
     since += nc;
     rb = rb + 1 == kRecBufs ? 0 : rb + 1;
+    const bool last = st == n_st - 1;
+    bool in_slot = false;
+    if constexpr (packed_pairs(KIND)) {
+      in_slot = s_wslot >= 0;
+      // A warp whose lanes could not take the next stage widens into the slot
+      // now, before the stage barrier (registers to global memory only).
+      if (in_slot && !last && since + NC > p.flush) {
+        widen_to_slot<kPatDr, H>(warp_slot(), acc, first);
+        first = false;
+        since = 0;
+      }
+    }
     if constexpr (kDirect) {
       // The window words are free; a wait that gave up (its stage was added
       // from stale words, never stored) ends the unit once the copies in
@@ -313,21 +358,37 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
           if (st + 1 < n_st && st + 1 != p.hold_stage)
             mbar_wait(sm.bar_base + 8u * (buf ^ 1), ((st + 1) >> 1) & 1);
         }
+        drop_slot();
         return false;
       }
     } else if constexpr (!DBUF) {
       __syncthreads();  // the window words are free
     }
-    if (since + NC > p.flush || st == n_st - 1) {
+    if (in_slot ? last : since + NC > p.flush || last) {
       // The transpose tiles reuse this stage's window buffer: wait until every
       // warp has finished reading it.
       if constexpr (DBUF) __syncthreads();
-      widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
+      if constexpr (packed_pairs(KIND)) {
+        if (in_slot)
+          store_from_slot<KIND, kPatDr, NW, NC, H>(p, pwb, acc, warp_slot(), first, blk, t0);
+        else
+          widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
+      } else {
+        widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
+      }
       first = false;
       since = 0;
       // The next stage unpacks into this window buffer (single-buffered):
       // wait until every warp has read its transpose tile back.
       if constexpr (!DBUF) __syncthreads();
+    }
+  }
+  if constexpr (packed_pairs(KIND)) {
+    if (s_wslot >= 0) {
+      // Every warp has read its part of the slot back (store_from_slot).
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) release_wslot(p, s_wslot);
     }
   }
   return true;

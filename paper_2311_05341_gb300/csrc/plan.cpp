@@ -446,8 +446,25 @@ void layout_workspace(dd_plan_s* p) {
   };
   for (auto& rp : p->ranges) place(rp);
   for (auto& ar : p->adj) place(ar);
-  p->ws_bytes = align_up(ws, 256);
-  p->host_ws.assign(p->ws_bytes, 0);
+  // Widening slots for the pattern tiles whose lanes hold 16-bit sums (uint8
+  // and 4-bit, from the input or a packed copy): flags (zero: free) in the
+  // uploaded image, the slots after it.
+  p->wslot_words = 0;
+  for (const auto& rp : p->ranges)
+    if (rp.tile_ok && rp.tile_pattern && tk::packed_pairs(rp.tile_kind))
+      p->wslot_words = std::max<int32_t>(
+          p->wslot_words, tk::kPatDr * tk::kPatShapes[rp.tile_shape].warps * 32 * rp.tile_h);
+  size_t image = align_up(ws, 256);
+  if (p->wslot_words > 0) {
+    p->off_wflags = image;
+    image = align_up(image + tk::kWidenSlots * sizeof(int32_t), 256);
+    p->off_wslots = image;
+    p->ws_bytes = image + static_cast<size_t>(tk::kWidenSlots) * p->wslot_words * 8;
+  } else {
+    p->off_wflags = p->off_wslots = 0;
+    p->ws_bytes = image;
+  }
+  p->host_ws.assign(image, 0);
   auto copy = [&](const RangePlan& rp) {
     std::memcpy(p->host_ws.data() + rp.off_shifts, rp.shifts.data(),
                 rp.shifts.size() * sizeof(int32_t));

@@ -104,7 +104,7 @@ extern "C" dd_status dd_run_u8_noalloc(dd_plan plan, const void* d_in, int64_t i
     const int64_t n_out = range_n_out(plan, rp, n_samp);
     int32_t* o = static_cast<int32_t*>(d_out) + out_off;
     int le = launch_forward_tiled_with_tables(plan, rp, scratch + off, err, d_in, in_row_stride,
-                                              n_out, o, 0, n_out, stream);
+                                              n_out, o, 0, n_out, stream, false);
     if (le != 0) return cuda_fail(le, "dd_run_u8_noalloc launch");
     off += rp.tile_recs.size();
     out_off += rp.n_dm * n_out;

@@ -425,5 +425,114 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
   }
 }
 
+
+// Widening slots (TileParams::wslots): one slot per CTA and unit, acquired
+// from the plan's flags by thread 0 (the SM id is the first probe), released
+// after the unit's last reads of it.  Returns -1 if every slot stayed held
+// through the probes (the unit then widens into the output rows).
+__device__ __forceinline__ int acquire_wslot(const TileParams& p) {
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  for (int probe = 0; probe < 4 * p.n_wslots; ++probe) {
+    const int s = static_cast<int>((smid + static_cast<unsigned>(probe)) %
+                                   static_cast<unsigned>(p.n_wslots));
+    if (atomicCAS(p.wflags + s, 0, 1) == 0) {
+      __threadfence();  // the slot's earlier holder is done with it
+      return s;
+    }
+  }
+  return -1;
+}
+__device__ __forceinline__ void release_wslot(const TileParams& p, int slot) {
+  __threadfence();
+  atomicExch(p.wflags + slot, 0);
+}
+
+// One warp widens its 16-bit lanes into its part of the slot: accumulator
+// word (i, j) of lane l (samples at positions H l + j and H l + j + 32 H)
+// adds its halves into 64-bit word (i H + j) 32 + l as two 32-bit sums (each
+// below 2^32: no carry crosses them).  The first widening of a unit stores.
+// Lanes are zeroed.  Coalesced: a warp's 32 words are 256 contiguous bytes.
+template <int DR, int H>
+__device__ __forceinline__ void widen_to_slot(unsigned long long* warp_slot,
+                                              uint32_t (&acc)[DR][H], bool first) {
+  const int l = threadIdx.x & 31;
+  unsigned long long* q = warp_slot + l;
+#pragma unroll
+  for (int i = 0; i < DR; ++i)
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const uint32_t a = acc[i][j];
+      const unsigned long long v =
+          static_cast<unsigned long long>(a & 0xffffu) |
+          static_cast<unsigned long long>(a >> 16) << 32;
+      unsigned long long* w = q + (i * H + j) * 32;
+      if (first)
+        asm volatile("st.global.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
+      else
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
+      acc[i][j] = 0u;
+    }
+}
+
+// The unit's outputs from a slot: each warp adds its lanes to the sums its
+// earlier widenings left in its part of the slot (none if `fresh`), writes
+// the 32-bit totals of its DMs into its transposed shared tile (position
+// H l + j and that + 32 H, as widen_store) and stores every output row of the
+// tile once.  Called by every thread of the CTA (the tiles take turns in
+// `groups` rounds when the window buffer cannot hold one per warp).
+template <int KIND, int DR, int NW, int NC, int H>
+__device__ __forceinline__ void store_from_slot(const TileParams& p, uint32_t* pw,
+                                                uint32_t (&acc)[DR][H],
+                                                const unsigned long long* warp_slot,
+                                                bool fresh, int blk, int64_t t0) {
+  static_assert(H % 2 == 1, "the transposed tile needs an odd lane stride");
+  constexpr int kPairW = 32 * H;
+  constexpr int kRows = 2 * H;            // rows of 32 positions
+  constexpr int kFw = 32 * kRows;         // per-warp tile
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  constexpr bool kAllFit = NC * (32 * H + 16) >= NW * kFw;
+  const int fit = (NC * p.lp) / kFw;
+  const int groups = kAllFit ? 1 : (NW + fit - 1) / fit;
+  uint32_t* tr = pw + (w / groups) * kFw;
+  const int wbase = H * l;
+  const int64_t lim = p.t_end - t0;
+  // This thread's reductions into its words of the slot are performed before
+  // it reads them back.
+  if (!fresh) __threadfence();
+  for (int gi = 0; gi < groups; ++gi) {
+    if (gi > 0) __syncthreads();
+    if (w % groups != gi) continue;
+#pragma unroll
+    for (int i = 0; i < DR; ++i) {
+      const int d = blk * (DR * NW) + w * DR + i;
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const uint32_t a = acc[i][j];
+        uint32_t lo = a & 0xffffu, hi = a >> 16;
+        if (!fresh) {
+          const unsigned long long v = __ldcg(warp_slot + (i * H + j) * 32 + l);
+          lo += static_cast<uint32_t>(v);
+          hi += static_cast<uint32_t>(v >> 32);
+        }
+        tr[wbase + j] = lo;
+        tr[wbase + j + kPairW] = hi;
+        acc[i][j] = 0u;
+      }
+      __syncwarp();
+      if (d < p.n_dm) {
+        OutT<KIND>* row =
+            static_cast<OutT<KIND>*>(p.out) + static_cast<int64_t>(d) * p.out_stride + t0;
+#pragma unroll 4
+        for (int k = 0; k < kRows; ++k) {
+          const int pos = 32 * k + l;
+          if (pos < lim) row[pos] = static_cast<int32_t>(tr[pos]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace tk
 }  // namespace dd
