@@ -408,3 +408,20 @@ def test_packed_copy_flags_and_ring_sizes():
         mixed.packed_scratch_bytes(n_samp, 8)
     assert ei.value.status == _lib.DD_ERR_UNSUPPORTED
     assert mixed.packed_scratch_bytes(n_samp, 1) > 0
+
+
+def test_workspace_holds_widening_slots():
+    """Plans with uint8 or 4-bit pattern tiles reserve 320 widening slots of
+    DMs-per-CTA x 32 H 64-bit words after their tables (slot flags uploaded,
+    slots not); uint16 plans, whose 32-bit lanes never widen, none."""
+    paper = workloads.paper_u8()
+    slot = 4 * 16 * 32 * 23 * 8  # 4 DMs x 16 warps, H = 23, 8 bytes
+    sizes = {}
+    for dtype in ("u8", "u4", "u16"):
+        plan = dd.Plan(paper.freqs, paper.f_high, paper.t_samp, paper.ranges, dtype,
+                       upload=False)
+        sizes[dtype] = plan.info(paper.n_samp)["workspace_bytes"]
+    tables = sizes["u16"]  # same shape of tables, no slots
+    for dtype in ("u8", "u4"):
+        extra = sizes[dtype] - tables
+        assert 320 * slot <= extra <= 320 * slot + 320 * 4 + 512, (dtype, extra)
