@@ -150,7 +150,7 @@ __device__ __forceinline__ const unsigned char* pair_chunk(const TileParams& p, 
 // issued at the top of stage st (its buffer was last read in stage st - 1,
 // which ended with a barrier), no unpacking, and one barrier per stage (it
 // also carries the bounded-wait status).
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool SLOTS>
 __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, int blk,
                                          int64_t tile) {
   static_assert(!PAIRS || !float_kind(KIND) || float_pairs(KIND),
@@ -187,6 +187,41 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       issue_stage<KIND, NC>(p, sm.bar_base, sm.raw, st, sbuf, t0, base, tid, cr.src(st),
                             cr.bytes(st), dst);
   };
+  // SLOTS (16-bit lanes, the plan's workspace has widening slots): each warp
+  // widens into its part of the CTA's slot when its lanes are full, before
+  // the stage barrier, with no shared-memory transpose and no barrier of its
+  // own; the last stage stores each output once.  All warps widen at the
+  // same stage: staggering them over the stages (two warps per stage) ran
+  // 1.3 % slower, every stage then waiting at its barrier for the warps that
+  // widen.  Otherwise the CTA widens into the output rows together.  The
+  // slot index stays in shared memory.  The slot is taken before the unit
+  // issues any copy: if none comes free within the probes (at most one CTA
+  // of these tiles runs per SM and the workspace has twice as many slots as
+  // a GB300 has SMs), the unit reports kErrTimeout and computes nothing.
+  static_assert(!SLOTS || packed_pairs(KIND), "widening slots serve 16-bit lanes");
+  __shared__ int s_wslot;
+  if constexpr (SLOTS) {
+    if (tid == 0) {
+      s_wslot = acquire_wslot(p);
+      if (s_wslot < 0) atomicOr(p.err, kErrTimeout);
+    }
+    __syncthreads();
+    if (s_wslot < 0) return false;
+  }
+  auto warp_slot = [&]() {
+    return p.wslots + static_cast<int64_t>(s_wslot) * p.wslot_words +
+           static_cast<int64_t>(w) * kPatDr * 32 * H;
+  };
+  // Timeout exit with a slot held: every thread's slot writes are ordered
+  // before thread 0 frees it.
+  auto drop_slot = [&]() {
+    if constexpr (SLOTS) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) release_wslot(p, s_wslot);
+    }
+  };
+
   if (tid <= NC) {
     // Shared memory read by an earlier unit of a persistent CTA is rewritten
     // by the copies: order those generic-proxy reads before them.
@@ -212,35 +247,6 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   int since = 0;  // channels accumulated since the last widen
   const int units = p.lp >> 2;
   int rb = 0;     // st % kRecBufs
-
-  // 16-bit lanes with widening slots: each warp widens into its part of the
-  // CTA's slot when its lanes are full, before the stage barrier, with no
-  // shared-memory transpose and no barrier of its own; the last stage stores
-  // each output once.  All warps widen at the same stage: staggering them
-  // over the stages (two warps per stage) ran 1.3 % slower, every stage then
-  // waiting at its barrier for the warps that widen.  Without a slot (none
-  // configured, or none free) the CTA widens into the output rows together.
-  // The slot index stays in shared memory (s_wslot, -1: none).
-  __shared__ int s_wslot;
-  if constexpr (packed_pairs(KIND)) {
-    if (tid == 0) s_wslot = p.wslots != nullptr ? acquire_wslot(p) : -1;
-    __syncthreads();
-  }
-  auto warp_slot = [&]() {
-    return p.wslots + static_cast<int64_t>(s_wslot) * p.wslot_words +
-           static_cast<int64_t>(w) * kPatDr * 32 * H;
-  };
-  // Timeout exit with a slot held: every thread's slot writes are ordered
-  // before thread 0 frees it.
-  auto drop_slot = [&]() {
-    if constexpr (packed_pairs(KIND)) {
-      if (s_wslot >= 0) {
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) release_wslot(p, s_wslot);
-      }
-    }
-  };
 
   for (int st = 0; st < n_st; ++st) {
     const int buf = st & 1;
@@ -333,12 +339,10 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     since += nc;
     rb = rb + 1 == kRecBufs ? 0 : rb + 1;
     const bool last = st == n_st - 1;
-    bool in_slot = false;
-    if constexpr (packed_pairs(KIND)) {
-      in_slot = s_wslot >= 0;
+    if constexpr (SLOTS) {
       // A warp whose lanes could not take the next stage widens into the slot
       // now, before the stage barrier (registers to global memory only).
-      if (in_slot && !last && since + NC > p.flush) {
+      if (!last && since + NC > p.flush) {
         widen_to_slot<kPatDr, H>(warp_slot(), acc, first);
         first = false;
         since = 0;
@@ -361,18 +365,14 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
     } else if constexpr (!DBUF) {
       __syncthreads();  // the window words are free
     }
-    if (in_slot ? last : since + NC > p.flush || last) {
+    if (SLOTS ? last : since + NC > p.flush || last) {
       // The transpose tiles reuse this stage's window buffer: wait until every
       // warp has finished reading it.
       if constexpr (DBUF) __syncthreads();
-      if constexpr (packed_pairs(KIND)) {
-        if (in_slot)
-          store_from_slot<KIND, kPatDr, NW, NC, H>(p, pwb, acc, warp_slot(), first, blk, t0);
-        else
-          widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
-      } else {
+      if constexpr (SLOTS)
+        store_from_slot<KIND, kPatDr, NW, NC, H>(p, pwb, acc, warp_slot(), first, blk, t0);
+      else
         widen_store<KIND, kPatDr, NW, NC, H>(p, pwb, acc, blk, t0, first);
-      }
       first = false;
       since = 0;
       // The next stage unpacks into this window buffer (single-buffered):
@@ -380,13 +380,11 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
       if constexpr (!DBUF) __syncthreads();
     }
   }
-  if constexpr (packed_pairs(KIND)) {
-    if (s_wslot >= 0) {
-      // Every warp has read its part of the slot back (store_from_slot).
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) release_wslot(p, s_wslot);
-    }
+  if constexpr (SLOTS) {
+    // Every warp has read its part of the slot back (store_from_slot).
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) release_wslot(p, s_wslot);
   }
   return true;
 }

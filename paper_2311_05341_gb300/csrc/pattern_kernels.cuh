@@ -19,7 +19,7 @@
 namespace dd {
 namespace tk {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool SLOTS>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   using namespace pattern;
@@ -32,23 +32,35 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
   __syncthreads();
   const int blk = blockIdx.x % p.n_blocks;
   const int64_t tile = blockIdx.x / p.n_blocks + p.tile0;
-  pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX>(p, sm, blk, tile);
+  pat_body<KIND, H, NW, NC, PAIRS, DBUF, AMAX, SLOTS>(p, sm, blk, tile);
 }
 
 }  // namespace tk
 
 namespace pattern_launch {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
-int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool SLOTS>
+int launch_pattern_mode(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   const size_t smem =
       tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX}, prm.lp);
-  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX>;
+  auto kern = tk::fwd_pattern_kernel<KIND, H, NW, NC, PAIRS, DBUF, AMAX, SLOTS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
   kern<<<static_cast<unsigned>(grid), NW * 32, smem, st>>>(prm);
   return static_cast<int>(cudaGetLastError());
+}
+
+// 16-bit lanes widen into the workspace's slots when the parameters carry
+// them (a kernel without the row widening at all: 3 % faster on the paper
+// plan than one that can take either), else into the output rows.
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
+int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
+  if constexpr (tk::packed_pairs(KIND)) {
+    if (prm.wslots != nullptr)
+      return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, true>(prm, grid, st);
+  }
+  return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, false>(prm, grid, st);
 }
 
 template <int KIND, int I>
@@ -88,7 +100,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar) {
 // Persistent kernel of one variant (KIND, kPatShapes[I]): the jobs of a batch
 // are grouped by variant and each group is one launch, so every launch has
 // the register allocation of its own variant.
-template <int KIND, int I>
+template <int KIND, int I, bool SLOTS>
 __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     fwd_pattern_batch_kernel(const PatBatchArgs b) {
   constexpr PatShape s = kPatShapes[I];
@@ -120,7 +132,7 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     }
     barriers_valid = true;
     __syncthreads();
-    const bool ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax>(
+    const bool ok = pattern::pat_body<KIND, s.h, s.warps, s.nc, s.pairs, s.dbuf, s.amax, SLOTS>(
         p, sm, item.blk, item.tile);
     if (!ok) break;
   }
@@ -130,25 +142,38 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
 
 namespace pattern_launch {
 
+template <int KIND, int I, bool SLOTS>
+int launch_variant_mode(const tk::PatBatchArgs& args, int32_t grid, size_t smem,
+                        cudaStream_t st) {
+  auto kern = tk::fwd_pattern_batch_kernel<KIND, I, SLOTS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  kern<<<grid, tk::kPatShapes[I].warps * 32, smem, st>>>(args);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// slots: every job of the launch carries widening slots (16-bit lanes only).
 template <int KIND, int I>
-int launch_variant(const tk::PatBatchArgs& args, int32_t grid, size_t smem, cudaStream_t st) {
+int launch_variant(const tk::PatBatchArgs& args, int32_t grid, size_t smem, cudaStream_t st,
+                   bool slots) {
   if constexpr (!tk::pat_shape_serves(tk::kPatShapes[I], KIND)) {
     return static_cast<int>(cudaErrorInvalidValue);  // never grouped by the host
   } else {
-    auto kern = tk::fwd_pattern_batch_kernel<KIND, I>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return static_cast<int>(e);
-    kern<<<grid, tk::kPatShapes[I].warps * 32, smem, st>>>(args);
-    return static_cast<int>(cudaGetLastError());
+    if constexpr (tk::packed_pairs(KIND)) {
+      if (slots) return launch_variant_mode<KIND, I, true>(args, grid, smem, st);
+    }
+    return launch_variant_mode<KIND, I, false>(args, grid, smem, st);
   }
 }
 
 template <int KIND, size_t... I>
 int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem,
-                cudaStream_t st, std::index_sequence<I...>) {
+                cudaStream_t st, bool slots, std::index_sequence<I...>) {
   int rc = static_cast<int>(cudaErrorInvalidValue);
-  ((shape == static_cast<int>(I) ? (rc = launch_variant<KIND, I>(args, grid, smem, st), 0) : 0),
+  ((shape == static_cast<int>(I)
+        ? (rc = launch_variant<KIND, I>(args, grid, smem, st, slots), 0)
+        : 0),
    ...);
   return rc;
 }
@@ -170,9 +195,9 @@ int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t sm
 #define DD_PATTERN_KIND_BATCH(K)                                                            \
   namespace dd {                                                                            \
   int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem, \
-                        void* st) {                                                         \
+                        void* st, bool slots) {                                             \
     return pattern_launch::launch_kind<tk::K>(                                              \
-        shape, args, grid, smem, static_cast<cudaStream_t>(st),                             \
+        shape, args, grid, smem, static_cast<cudaStream_t>(st), slots,                      \
         std::make_index_sequence<tk::kNumPatShapes>{});                                     \
   }                                                                                         \
   }

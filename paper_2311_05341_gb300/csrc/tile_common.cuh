@@ -429,7 +429,7 @@ __device__ __forceinline__ void widen_store(const TileParams& p, uint32_t* pw,
 // Widening slots (TileParams::wslots): one slot per CTA and unit, acquired
 // from the plan's flags by thread 0 (the SM id is the first probe), released
 // after the unit's last reads of it.  Returns -1 if every slot stayed held
-// through the probes (the unit then widens into the output rows).
+// through the probes (the unit then reports kErrTimeout).
 __device__ __forceinline__ int acquire_wslot(const TileParams& p) {
   unsigned smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
