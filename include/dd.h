@@ -198,7 +198,12 @@ dd_status dd_plan_set_tile(dd_plan plan, int32_t range, int32_t tile);
  * `stream`, and bind that workspace to the plan.  The workspace must stay
  * alive and unmodified while runs are in flight.  The host staging copy lives
  * in the plan, so the plan must outlive the copy (synchronise the stream
- * before destroying a plan whose upload may still be running).
+ * before destroying a plan whose upload may still be running).  Plans with
+ * uint8 or 4-bit pattern tiles also keep their kernels' widening slots in
+ * the workspace (320 slots after the tables, 121 MB for 64-DM blocks at
+ * H = 23: each CTA widens its 16-bit partial sums into a slot it takes for
+ * the duration of a work unit, so runs of one plan on several streams may
+ * overlap); only the tables and the slots' flags are copied.
  * Errors: DD_ERR_BUDGET if bytes is too small, DD_ERR_SHAPE if misaligned,
  * DD_ERR_CUDA if the copy cannot be enqueued.
  */
