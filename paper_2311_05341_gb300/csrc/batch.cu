@@ -44,7 +44,7 @@ struct dd_batch_s {
   struct PatGroup {
     int32_t kind;
     int32_t shape;
-    bool slots = false;  // every job widens into its plan's slots (set when bound)
+    int mode = 0;  // widening mode every job takes (tk::widen_mode; set when bound)
     size_t smem = 0;
     size_t off_items = 0;
     std::vector<dd::tk::BatchItem> items;
@@ -352,7 +352,7 @@ dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
     pk.in_stride = in_row_stride[pk.plan];
     pk.scratch = d_scratch[pk.plan];
   }
-  for (auto& g : batch->groups) g.slots = tk::packed_pairs(g.kind);
+  for (auto& g : batch->groups) g.mode = -1;  // none seen yet
   for (size_t j = 0; j < batch->jobs.size(); ++j) {
     const auto& jr = batch->jobs[j];
     const dd_plan p = batch->plans[jr.plan];
@@ -383,7 +383,10 @@ dd_status dd_batch_bind_scratch(dd_batch batch, const void* const* d_in,
     if (jr.pattern) {
       tk::PatBatchJob& bj = batch->host_pjobs[jr.index];
       auto& grp = batch->groups[batch->pjob_group[jr.index]];
-      if (prm.wslots == nullptr) grp.slots = false;
+      const int m = tk::widen_mode(rp.tile_kind, tk::kPatShapes[rp.tile_shape].nc,
+                                   prm.wslots != nullptr, prm.flush);
+      // A group whose jobs would take different modes widens into the rows.
+      grp.mode = grp.mode < 0 || grp.mode == m ? m : 0;
       bj.p = prm;
       bj.kind = rp.tile_kind;
       bj.shape = rp.tile_shape;
@@ -465,7 +468,7 @@ dd_status dd_batch_run(dd_batch batch, void* stream) {
                                            static_cast<int64_t>(batch->sm_count));
     int le = launch_pattern_batch(g.kind, g.shape, args,
                                   static_cast<int32_t>(std::max<int64_t>(grid, 1)), g.smem, ls,
-                                  g.slots);
+                                  g.mode < 0 ? 0 : g.mode);
     if (le != 0) return cuda_fail(le, "dd_batch_run pattern launch");
   }
   if (!batch->items.empty()) {

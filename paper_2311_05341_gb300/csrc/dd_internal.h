@@ -236,12 +236,12 @@ int launch_batch(const tk::BatchArgs& args, int32_t grid, size_t smem, void* str
 #define DD_DECLARE_PATTERN_KIND(K)                                                            \
   int pattern_forward_##K(int shape, const tk::TileParams& prm, int64_t grid, void* stream); \
   int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem,  \
-                        void* stream, bool slots);
+                        void* stream, int mode);
 DD_PATTERN_KINDS(DD_DECLARE_PATTERN_KIND)
 #undef DD_DECLARE_PATTERN_KIND
 // Persistent pattern-tile launch of one variant (kind, tk::kPatShapes index);
-// slots: every job carries widening slots (TileParams::wslots).
+// mode: the widening mode (tk::widen_mode) every job of the launch takes.
 int launch_pattern_batch(int kind, int shape, const tk::PatBatchArgs& args, int32_t grid,
-                         size_t smem, void* stream, bool slots);
+                         size_t smem, void* stream, int mode);
 
 }  // namespace dd

@@ -15,10 +15,10 @@
 namespace dd {
 
 int launch_pattern_batch(int kind, int shape, const tk::PatBatchArgs& args, int32_t grid,
-                         size_t smem, void* stream, bool slots) {
+                         size_t smem, void* stream, int mode) {
   switch (kind) {
 #define DD_CASE(K) \
-  case tk::K: return pattern_batch_##K(shape, args, grid, smem, stream, slots);
+  case tk::K: return pattern_batch_##K(shape, args, grid, smem, stream, mode);
     DD_PATTERN_KINDS(DD_CASE)
 #undef DD_CASE
   }

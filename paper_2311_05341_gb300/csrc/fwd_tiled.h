@@ -351,6 +351,15 @@ struct TileParams {
   int32_t n_wslots;
   int32_t wslot_words;  // 64-bit words per slot
 };
+// Widening mode of a pattern-tile launch (a template argument of its
+// kernel): 0 into the output rows, 1 into slots (every word when the lanes
+// are full), 2 into slots by phases (the lanes take exactly 8 stages of nc
+// channels: 1 / 8 of the words after every stage).  Separate kernels: one
+// that could take either of 0 and 1 at run time was 3 % slower on the paper
+// plan.
+DD_HOST_DEVICE constexpr int widen_mode(int kind, int nc, bool slots, int32_t flush) {
+  return !packed_pairs(kind) || !slots ? 0 : flush / nc == 8 ? 2 : 1;
+}
 // Widening slots in a plan workspace: two per SM of the largest GB300-class
 // part (1 CTA per SM for the 16-warp pattern tiles, whose 128 registers per
 // thread fill the register file; the second half covers smaller tiles).

@@ -19,7 +19,7 @@
 namespace dd {
 namespace tk {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool SLOTS>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, int SLOTS>
 __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   using namespace pattern;
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fwd_pattern_kernel(const TileParam
 
 namespace pattern_launch {
 
-template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, bool SLOTS>
+template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX, int SLOTS>
 int launch_pattern_mode(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   const size_t smem =
       tk::pat_smem_bytes(KIND, prm.bin, tk::PatShape{H, NW, NC, PAIRS, DBUF, AMAX}, prm.lp);
@@ -51,16 +51,16 @@ int launch_pattern_mode(const tk::TileParams& prm, int64_t grid, cudaStream_t st
   return static_cast<int>(cudaGetLastError());
 }
 
-// 16-bit lanes widen into the workspace's slots when the parameters carry
-// them (a kernel without the row widening at all: 3 % faster on the paper
-// plan than one that can take either), else into the output rows.
 template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   if constexpr (tk::packed_pairs(KIND)) {
-    if (prm.wslots != nullptr)
-      return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, true>(prm, grid, st);
+    switch (tk::widen_mode(KIND, NC, prm.wslots != nullptr, prm.flush)) {
+      case 2: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 2>(prm, grid, st);
+      case 1: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 1>(prm, grid, st);
+      default: break;
+    }
   }
-  return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, false>(prm, grid, st);
+  return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 0>(prm, grid, st);
 }
 
 template <int KIND, int I>
@@ -100,7 +100,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar) {
 // Persistent kernel of one variant (KIND, kPatShapes[I]): the jobs of a batch
 // are grouped by variant and each group is one launch, so every launch has
 // the register allocation of its own variant.
-template <int KIND, int I, bool SLOTS>
+template <int KIND, int I, int SLOTS>
 __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
     fwd_pattern_batch_kernel(const PatBatchArgs b) {
   constexpr PatShape s = kPatShapes[I];
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kPatShapes[I].warps * 32, 1)
 
 namespace pattern_launch {
 
-template <int KIND, int I, bool SLOTS>
+template <int KIND, int I, int SLOTS>
 int launch_variant_mode(const tk::PatBatchArgs& args, int32_t grid, size_t smem,
                         cudaStream_t st) {
   auto kern = tk::fwd_pattern_batch_kernel<KIND, I, SLOTS>;
@@ -153,26 +153,27 @@ int launch_variant_mode(const tk::PatBatchArgs& args, int32_t grid, size_t smem,
   return static_cast<int>(cudaGetLastError());
 }
 
-// slots: every job of the launch carries widening slots (16-bit lanes only).
+// mode: the widening mode every job of the launch takes (tk::widen_mode).
 template <int KIND, int I>
 int launch_variant(const tk::PatBatchArgs& args, int32_t grid, size_t smem, cudaStream_t st,
-                   bool slots) {
+                   int mode) {
   if constexpr (!tk::pat_shape_serves(tk::kPatShapes[I], KIND)) {
     return static_cast<int>(cudaErrorInvalidValue);  // never grouped by the host
   } else {
     if constexpr (tk::packed_pairs(KIND)) {
-      if (slots) return launch_variant_mode<KIND, I, true>(args, grid, smem, st);
+      if (mode == 2) return launch_variant_mode<KIND, I, 2>(args, grid, smem, st);
+      if (mode == 1) return launch_variant_mode<KIND, I, 1>(args, grid, smem, st);
     }
-    return launch_variant_mode<KIND, I, false>(args, grid, smem, st);
+    return launch_variant_mode<KIND, I, 0>(args, grid, smem, st);
   }
 }
 
 template <int KIND, size_t... I>
 int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem,
-                cudaStream_t st, bool slots, std::index_sequence<I...>) {
+                cudaStream_t st, int mode, std::index_sequence<I...>) {
   int rc = static_cast<int>(cudaErrorInvalidValue);
   ((shape == static_cast<int>(I)
-        ? (rc = launch_variant<KIND, I>(args, grid, smem, st, slots), 0)
+        ? (rc = launch_variant<KIND, I>(args, grid, smem, st, mode), 0)
         : 0),
    ...);
   return rc;
@@ -195,9 +196,9 @@ int launch_kind(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t sm
 #define DD_PATTERN_KIND_BATCH(K)                                                            \
   namespace dd {                                                                            \
   int pattern_batch_##K(int shape, const tk::PatBatchArgs& args, int32_t grid, size_t smem, \
-                        void* st, bool slots) {                                             \
+                        void* st, int mode) {                                               \
     return pattern_launch::launch_kind<tk::K>(                                              \
-        shape, args, grid, smem, static_cast<cudaStream_t>(st), slots,                      \
+        shape, args, grid, smem, static_cast<cudaStream_t>(st), mode,                       \
         std::make_index_sequence<tk::kNumPatShapes>{});                                     \
   }                                                                                         \
   }

@@ -475,8 +475,50 @@ __device__ __forceinline__ void widen_to_slot(unsigned long long* warp_slot,
     }
 }
 
+// Widening by phases: word k = i H + j of the lanes belongs to phase k mod G;
+// at the end of stage st a warp widens the words of phase st mod G only, so
+// each word is widened every G stages (G NC channels, within the lanes'
+// bound when G NC <= the flush interval) and a stage carries 1 / G of the
+// widening instead of every G-th stage all of it.  Stores in the first G
+// stages (each word's first widening), reductions after.
+template <int DR, int H, int G, int C>
+__device__ __forceinline__ void widen_words(unsigned long long* q, uint32_t (&acc)[DR][H],
+                                            bool first) {
+#pragma unroll
+  for (int k = C; k < DR * H; k += G) {
+    const int i = k / H, j = k % H;
+    const uint32_t a = acc[i][j];
+    const unsigned long long v = static_cast<unsigned long long>(a & 0xffffu) |
+                                 static_cast<unsigned long long>(a >> 16) << 32;
+    unsigned long long* w = q + k * 32;
+    if (first)
+      asm volatile("st.global.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
+    else
+      asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
+    acc[i][j] = 0u;
+  }
+}
+template <int DR, int H, int G>
+__device__ __forceinline__ void widen_phase(unsigned long long* warp_slot,
+                                            uint32_t (&acc)[DR][H], int phase, bool first) {
+  static_assert(G == 8, "phases are generated for G = 8");
+  unsigned long long* q = warp_slot + (threadIdx.x & 31);
+  switch (phase) {
+    case 0: widen_words<DR, H, G, 0>(q, acc, first); break;
+    case 1: widen_words<DR, H, G, 1>(q, acc, first); break;
+    case 2: widen_words<DR, H, G, 2>(q, acc, first); break;
+    case 3: widen_words<DR, H, G, 3>(q, acc, first); break;
+    case 4: widen_words<DR, H, G, 4>(q, acc, first); break;
+    case 5: widen_words<DR, H, G, 5>(q, acc, first); break;
+    case 6: widen_words<DR, H, G, 6>(q, acc, first); break;
+    default: widen_words<DR, H, G, 7>(q, acc, first); break;
+  }
+}
+
 // The unit's outputs from a slot: each warp adds its lanes to the sums its
-// earlier widenings left in its part of the slot (none if `fresh`), writes
+// earlier widenings left in its part of the slot (for word k = i H + j only
+// if k mod G < done: the phases widened at least once; G = 1 with done = 0
+// or 1 when every word is widened together), writes
 // the 32-bit totals of its DMs into its transposed shared tile (position
 // H l + j and that + 32 H, as widen_store) and stores every output row of the
 // tile once.  Called by every thread of the CTA (the tiles take turns in
@@ -484,8 +526,8 @@ __device__ __forceinline__ void widen_to_slot(unsigned long long* warp_slot,
 template <int KIND, int DR, int NW, int NC, int H>
 __device__ __forceinline__ void store_from_slot(const TileParams& p, uint32_t* pw,
                                                 uint32_t (&acc)[DR][H],
-                                                const unsigned long long* warp_slot,
-                                                bool fresh, int blk, int64_t t0) {
+                                                const unsigned long long* warp_slot, int G,
+                                                int done, int blk, int64_t t0) {
   static_assert(H % 2 == 1, "the transposed tile needs an odd lane stride");
   constexpr int kPairW = 32 * H;
   constexpr int kRows = 2 * H;            // rows of 32 positions
@@ -499,7 +541,7 @@ __device__ __forceinline__ void store_from_slot(const TileParams& p, uint32_t* p
   const int64_t lim = p.t_end - t0;
   // This thread's reductions into its words of the slot are performed before
   // it reads them back.
-  if (!fresh) __threadfence();
+  if (done > 0) __threadfence();
   for (int gi = 0; gi < groups; ++gi) {
     if (gi > 0) __syncthreads();
     if (w % groups != gi) continue;
@@ -510,7 +552,7 @@ __device__ __forceinline__ void store_from_slot(const TileParams& p, uint32_t* p
       for (int j = 0; j < H; ++j) {
         const uint32_t a = acc[i][j];
         uint32_t lo = a & 0xffffu, hi = a >> 16;
-        if (!fresh) {
+        if ((i * H + j) % G < done) {
           const unsigned long long v = __ldcg(warp_slot + (i * H + j) * 32 + l);
           lo += static_cast<uint32_t>(v);
           hi += static_cast<uint32_t>(v >> 32);
