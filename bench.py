@@ -48,7 +48,7 @@ HBM_GBS = _measured_hbm_gbs()
 # roofline times (ncu), keyed by workload, raw samples, tiles, input mode and
 # segments; valid only for the kernel build it was taken on
 # (profiles/fwd_pattern_u8_8192ch.md).
-TRAFFIC = {}
+TRAFFIC = {("paper_u8", 262144, (0x104,), "packed ring", 8): 18.33e9 + 13.44e9}
 UNIT = "DM*samples/s"
 
 
