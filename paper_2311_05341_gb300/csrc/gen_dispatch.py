@@ -97,6 +97,11 @@ PAIR_H = (15, 17, 19, 21, 23, 25)  # window words per lane of the channel-pair p
 LOAD_AHEAD = {"U32": 8, "F32": 4, "F2": 4}
 
 
+# Channel pairs whose two window words are summed once per word (t_k + u_k)
+# before the four DMs add that sum: (h + o_3) + 4 h adds per pair instead of
+# 8 h.  Float pairs only (integer pairs already add both channels in one
+# three-input add per accumulator).
+PRESUM = {"F2"}
 LOAD = {"U32": ("ld.shared.b32", ".b32"), "F32": ("ld.shared.f32", ".f32"),
         "F2": ("ld.shared.b64", ".b64")}
 # Float pairs: 64-bit window words of two floats (samples u and u + 32 H),
@@ -150,13 +155,16 @@ def pattern_load_macro(op, h, pair):
             if pair:
                 lines.append(f'"{ld} u{k}, [%{s2}+{wb * k}];\\n\\t"')
 
+        presum = pair and op in PRESUM
+
         def add(i, j):
             a = i * h + j
             lines.append(f'"{instr} %{a}, %{a}, t{offs[i] + j};\\n\\t"')
-            if pair:
+            if pair and not presum:
                 lines.append(f'"{instr} %{a}, %{a}, u{offs[i] + j};\\n\\t"')
 
         ahead = LOAD_AHEAD[op]
+        assert ahead is not None or not presum
         if ahead is None:
             for k in range(n):
                 load(k)
@@ -167,6 +175,8 @@ def pattern_load_macro(op, h, pair):
             for k in range(min(ahead, n)):
                 load(k)
             for k in range(n):  # adds consuming word k, then the next load
+                if presum:  # every word k < h + o_3 is read by some DM
+                    lines.append(f'"{instr} t{k}, t{k}, u{k};\\n\\t"')
                 for i in range(PATTERN_DR):
                     if 0 <= k - offs[i] < h:
                         add(i, k - offs[i])
