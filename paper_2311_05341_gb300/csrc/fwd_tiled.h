@@ -353,12 +353,15 @@ struct TileParams {
 };
 // Widening mode of a pattern-tile launch (a template argument of its
 // kernel): 0 into the output rows, 1 into slots (every word when the lanes
-// are full), 2 into slots by phases (the lanes take exactly 8 stages of nc
-// channels: 1 / 8 of the words after every stage).  Separate kernels: one
-// that could take either of 0 and 1 at run time was 3 % slower on the paper
-// plan.
+// are full), G = 8 (and for packed copies of binned uint8, G = 4 or 2) into
+// slots by G phases: the lanes take exactly G stages of nc channels, and 1 / G
+// of the words widen after every stage.  Separate kernels: one that could
+// take either of 0 and 1 at run time was 3 % slower on the paper plan.
 DD_HOST_DEVICE constexpr int widen_mode(int kind, int nc, bool slots, int32_t flush) {
-  return !packed_pairs(kind) || !slots ? 0 : flush / nc == 8 ? 2 : 1;
+  return !packed_pairs(kind) || !slots                      ? 0
+         : flush / nc == 8                                  ? 8
+         : kind == kU8P && (flush / nc == 4 || flush / nc == 2) ? flush / nc
+                                                                : 1;
 }
 // Widening slots in a plan workspace: two per SM of the largest GB300-class
 // part (1 CTA per SM for the 16-warp pattern tiles, whose 128 registers per

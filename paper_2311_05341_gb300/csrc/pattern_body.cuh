@@ -3,9 +3,10 @@
 // tile) work unit, shared by the one-unit-per-CTA kernel and the persistent
 // batch kernel (fwd_pattern_batch.cu).
 //
-// Computes Eq. 3 (Algorithm 1) with the output partition, staging, binning and
-// widen/store of the offset tiles (fwd_tiled.cu); only the register tile and
-// its per-channel dispatch differ:
+// Computes Eq. 3 (Algorithm 1) with the output partition, staging and
+// binning of the offset tiles (fwd_tiled.cu); the register tile, its
+// per-channel dispatch and the widening of 16-bit lanes into per-CTA slots
+// differ:
 //
 //  * Every lane owns kPatDr = 4 consecutive DMs x H window words, H odd
 //    (uint8: 2H samples, pairing samples u and u + 32H in 16-bit lanes).
@@ -19,7 +20,10 @@
 //    block (gen_dispatch.py) that loads the window words its offsets touch
 //    (scalar shared loads, conflict-free at any offset because the lane
 //    stride H is odd) and adds both channels' samples with three-input adds.
-//    Float: one channel per branch.
+//    Float pairs: the same, the two channels' words summed once per word
+//    before the four DMs add the sum.  Single floats: one channel per branch.
+//  * 16-bit lanes (uint8, 4-bit) widen into a slot of the plan workspace
+//    (widening modes, tk::widen_mode), or without one into the output rows.
 //
 // Against the 4-bit-offset tiles this is one indexed branch per four DMs and
 // two channels instead of one per DM.  Every mbarrier wait is bounded; on
@@ -198,13 +202,14 @@ __device__ __forceinline__ bool pat_body(const TileParams& p, const PSmem& sm, i
   // issues any copy: if none comes free within the probes (at most one CTA
   // of these tiles runs per SM and the workspace has twice as many slots as
   // a GB300 has SMs), the unit reports kErrTimeout and computes nothing.
-  // SLOTS 2 widens by phases (widen_phase: 1 / 8 of the words at the end of
-  // every stage; the launch picks it when the lanes take exactly 8 stages):
-  // 4 % faster on the paper plan than every word every 8th stage (SLOTS 1),
-  // whose stage barrier waited for all warps' widenings at once.
+  // SLOTS = G >= 2 widens by G phases (widen_phase: 1 / G of the words at
+  // the end of every stage; the launch picks it when the lanes take exactly G
+  // stages): 4 % faster on the paper plan (G = 8) than every word every 8th
+  // stage (SLOTS 1), whose stage barrier waited for all warps' widenings at
+  // once.
   static_assert(!SLOTS || packed_pairs(KIND), "widening slots serve 16-bit lanes");
-  constexpr bool kPhased = SLOTS == 2;
-  constexpr int kPhases = 8;
+  constexpr bool kPhased = SLOTS >= 2;
+  constexpr int kPhases = kPhased ? SLOTS : 1;
   __shared__ int s_wslot;
   if constexpr (SLOTS) {
     if (tid == 0) {

@@ -55,9 +55,16 @@ template <int KIND, int H, int NW, int NC, bool PAIRS, bool DBUF, int AMAX>
 int launch_pattern_shape(const tk::TileParams& prm, int64_t grid, cudaStream_t st) {
   if constexpr (tk::packed_pairs(KIND)) {
     switch (tk::widen_mode(KIND, NC, prm.wslots != nullptr, prm.flush)) {
-      case 2: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 2>(prm, grid, st);
+      case 8: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 8>(prm, grid, st);
       case 1: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 1>(prm, grid, st);
       default: break;
+    }
+    if constexpr (KIND == tk::kU8P) {
+      switch (tk::widen_mode(KIND, NC, prm.wslots != nullptr, prm.flush)) {
+        case 4: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 4>(prm, grid, st);
+        case 2: return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 2>(prm, grid, st);
+        default: break;
+      }
     }
   }
   return launch_pattern_mode<KIND, H, NW, NC, PAIRS, DBUF, AMAX, 0>(prm, grid, st);
@@ -161,8 +168,12 @@ int launch_variant(const tk::PatBatchArgs& args, int32_t grid, size_t smem, cuda
     return static_cast<int>(cudaErrorInvalidValue);  // never grouped by the host
   } else {
     if constexpr (tk::packed_pairs(KIND)) {
-      if (mode == 2) return launch_variant_mode<KIND, I, 2>(args, grid, smem, st);
+      if (mode == 8) return launch_variant_mode<KIND, I, 8>(args, grid, smem, st);
       if (mode == 1) return launch_variant_mode<KIND, I, 1>(args, grid, smem, st);
+    }
+    if constexpr (KIND == tk::kU8P) {
+      if (mode == 4) return launch_variant_mode<KIND, I, 4>(args, grid, smem, st);
+      if (mode == 2) return launch_variant_mode<KIND, I, 2>(args, grid, smem, st);
     }
     return launch_variant_mode<KIND, I, 0>(args, grid, smem, st);
   }

@@ -501,17 +501,29 @@ __device__ __forceinline__ void widen_words(unsigned long long* q, uint32_t (&ac
 template <int DR, int H, int G>
 __device__ __forceinline__ void widen_phase(unsigned long long* warp_slot,
                                             uint32_t (&acc)[DR][H], int phase, bool first) {
-  static_assert(G == 8, "phases are generated for G = 8");
+  static_assert(G == 2 || G == 4 || G == 8, "phases are generated for G = 2, 4, 8");
   unsigned long long* q = warp_slot + (threadIdx.x & 31);
-  switch (phase) {
-    case 0: widen_words<DR, H, G, 0>(q, acc, first); break;
-    case 1: widen_words<DR, H, G, 1>(q, acc, first); break;
-    case 2: widen_words<DR, H, G, 2>(q, acc, first); break;
-    case 3: widen_words<DR, H, G, 3>(q, acc, first); break;
-    case 4: widen_words<DR, H, G, 4>(q, acc, first); break;
-    case 5: widen_words<DR, H, G, 5>(q, acc, first); break;
-    case 6: widen_words<DR, H, G, 6>(q, acc, first); break;
-    default: widen_words<DR, H, G, 7>(q, acc, first); break;
+  if constexpr (G == 2) {
+    if (phase == 0) widen_words<DR, H, G, 0>(q, acc, first);
+    else widen_words<DR, H, G, 1>(q, acc, first);
+  } else if constexpr (G == 4) {
+    switch (phase) {
+      case 0: widen_words<DR, H, G, 0>(q, acc, first); break;
+      case 1: widen_words<DR, H, G, 1>(q, acc, first); break;
+      case 2: widen_words<DR, H, G, 2>(q, acc, first); break;
+      default: widen_words<DR, H, G, 3>(q, acc, first); break;
+    }
+  } else {
+    switch (phase) {
+      case 0: widen_words<DR, H, G, 0>(q, acc, first); break;
+      case 1: widen_words<DR, H, G, 1>(q, acc, first); break;
+      case 2: widen_words<DR, H, G, 2>(q, acc, first); break;
+      case 3: widen_words<DR, H, G, 3>(q, acc, first); break;
+      case 4: widen_words<DR, H, G, 4>(q, acc, first); break;
+      case 5: widen_words<DR, H, G, 5>(q, acc, first); break;
+      case 6: widen_words<DR, H, G, 6>(q, acc, first); break;
+      default: widen_words<DR, H, G, 7>(q, acc, first); break;
+    }
   }
 }
 
