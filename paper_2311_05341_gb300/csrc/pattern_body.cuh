@@ -121,12 +121,19 @@ __device__ __forceinline__ void pat_pair(AccT<KIND> (&acc)[kPatDr][H], uint32_t 
   } else {
   static_assert(H == 15 || H == 17 || H == 19 || H == 21 || H == 23 || H == 25,
                 "no generated pair blocks for H");
-  if constexpr (H == 15) DD_PATL2_CHANNEL_U32_15(acc, win, win2, ix);
-  else if constexpr (H == 17) DD_PATL2_CHANNEL_U32_17(acc, win, win2, ix);
-  else if constexpr (H == 19) DD_PATL2_CHANNEL_U32_19(acc, win, win2, ix);
-  else if constexpr (H == 21) DD_PATL2_CHANNEL_U32_21(acc, win, win2, ix);
-  else if constexpr (H == 23) DD_PATL2_CHANNEL_U32_23(acc, win, win2, ix);
-  else DD_PATL2_CHANNEL_U32_25(acc, win, win2, ix);
+  // Packed uint8 / 4-bit copies take the blocks that load 7 words ahead.
+#define DD_PAIR_CASE(HH)                                                         \
+  if constexpr (H == HH) {                                                       \
+    if constexpr (KIND == kU8P) DD_PATL2_CHANNEL_U32P_##HH(acc, win, win2, ix);  \
+    else DD_PATL2_CHANNEL_U32_##HH(acc, win, win2, ix);                          \
+  }
+  DD_PAIR_CASE(15)
+  DD_PAIR_CASE(17)
+  DD_PAIR_CASE(19)
+  DD_PAIR_CASE(21)
+  DD_PAIR_CASE(23)
+  DD_PAIR_CASE(25)
+#undef DD_PAIR_CASE
   }
 }
 
