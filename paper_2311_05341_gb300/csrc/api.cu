@@ -210,6 +210,16 @@ cudaError_t host_pipe(dd_plan_s* p, HostPipe** out) {
   return cudaSuccess;
 }
 
+// A failure after the side streams were forked from the caller's stream:
+// the caller's stream still waits for whatever they already hold (as far as
+// the calls still succeed), so that the caller's next use of its buffers
+// cannot overtake copies or kernels queued there.
+dd_status fail_joined(HostPipe* hp, cudaStream_t s, int err, const char* what) {
+  for (cudaStream_t o : {hp->s_in, hp->s_out, hp->s_comp, hp->s_tr, hp->s_pack})
+    if (cudaEventRecord(hp->done, o) == cudaSuccess) cudaStreamWaitEvent(s, hp->done, 0);
+  return cuda_fail(err, what);
+}
+
 }  // namespace
 
 void free_host_pipe(dd_plan_s* p) {
@@ -546,13 +556,13 @@ static dd_status run_ring(dd_plan plan, const dd_plan_info& info, const void* d_
   e = cudaEventRecord(hp->start, s);
   for (cudaStream_t o : {hp->s_pack, hp->s_comp})
     if (e == cudaSuccess) e = cudaStreamWaitEvent(o, hp->start, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+  if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run ring ordering");
   unsigned char* out = static_cast<unsigned char*>(d_out);
   for (size_t r = 0; r < plan->ranges.size(); ++r) {
     if (L.ring[r]) continue;
     const int le = launch_range(plan, plan->ranges[r], d_in, in_row_stride, n_samp, info.n_out[r],
                                 out + info.out_offset[r] * 4, 0, info.n_out[r], s);
-    if (le != 0) return cuda_fail(le, "dd_run forward launch");
+    if (le != 0) return fail_joined(hp, s, le, "dd_run forward launch");
   }
   const size_t in_bytes = dtype_row_bytes(plan->dtype, in_row_stride);
   for (size_t k = 0; k < L.segs.size(); ++k) {
@@ -561,30 +571,30 @@ static dd_status run_ring(dd_plan plan, const dd_plan_info& info, const void* d_
     unsigned char* buf = static_cast<unsigned char*>(d_scratch) + slot * L.slot_bytes;
     if (k >= static_cast<size_t>(kRingSlots)) {
       e = cudaStreamWaitEvent(hp->s_pack, hp->freed[slot], 0);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run ring ordering");
     }
     int le = launch_pack_pairs(d_in, static_cast<int64_t>(in_bytes), plan->n_chan, n_samp, buf,
                                L.slot_words, L.pair, sg.origin, sg.end,
                                pack_source(plan->dtype), hp->s_pack, sg.origin);
-    if (le != 0) return cuda_fail(le, "dd_run ring packing");
+    if (le != 0) return fail_joined(hp, s, le, "dd_run ring packing");
     cudaStream_t sc = (k & 1) ? hp->s_comp : s;
     e = cudaEventRecord(hp->packed[slot], hp->s_pack);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, hp->packed[slot], 0);
-    if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+    if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run ring ordering");
     for (size_t r = 0; r < plan->ranges.size(); ++r) {
       if (!L.ring[r] || sg.hi[r] <= sg.lo[r]) continue;
       const RangePlan& rp = plan->ranges[r];
       le = launch_range(plan, rp, buf, L.slot_words, n_samp, info.n_out[r],
                         out + info.out_offset[r] * 4, sg.lo[r], sg.hi[r], sc,
                         copy_kind(rp, true), sg.origin);
-      if (le != 0) return cuda_fail(le, "dd_run ring forward launch");
+      if (le != 0) return fail_joined(hp, s, le, "dd_run ring forward launch");
     }
     e = cudaEventRecord(hp->freed[slot], sc);
-    if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+    if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run ring ordering");
   }
   e = cudaEventRecord(hp->done, hp->s_comp);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run ring ordering");
+  if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run ring ordering");
   return DD_OK;
 }
 
@@ -805,7 +815,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   e = cudaEventRecord(hp->start, s);
   for (cudaStream_t o : {hp->s_in, hp->s_out, hp->s_comp, hp->s_tr})
     if (e == cudaSuccess) e = cudaStreamWaitEvent(o, hp->start, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+  if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
   const int64_t seg = (n_samp + kHostSegments - 1) / kHostSegments;
   const int64_t seg_len = (seg + 255) / 256 * 256;
   const int64_t packed_stride = (n_samp + 3) / 4 * 4;
@@ -834,40 +844,40 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
                               row_bytes(plan->dtype, raw_end) - b0, plan->n_chan,
                               cudaMemcpyHostToDevice, hp->s_in);
       }
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host input copy");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host input copy");
     }
     e = cudaEventRecord(hp->in[k], hp->s_in);
-    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
     if (tmajor) {  // transposes run in order on one stream
       e = cudaStreamWaitEvent(hp->s_tr, hp->in[k], 0);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
       if (raw_end > raw_done) {
         const int le = launch_transpose(static_cast<int>(esz), dtm, tm_stride, plan->n_chan, dcm,
                                         cm_stride, raw_done, raw_end, hp->s_tr);
-        if (le != 0) return cuda_fail(le, "dd_run_host transpose");
+        if (le != 0) return fail_joined(hp, s, le, "dd_run_host transpose");
       }
       e = cudaEventRecord(hp->tr[k], hp->s_tr);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
       ready = hp->tr[k];
     } else if (pair >= 0) {  // packed copy of the columns whose pair partner is in
       e = cudaStreamWaitEvent(hp->s_tr, hp->in[k], 0);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
       const int64_t packed_end =
           last ? packed_stride : std::max(packed_done, (raw_end - pair) / 16 * 16);
       if (packed_end > packed_done) {
         const int le = launch_pack_pairs(dcm, row_bytes(plan->dtype, cm_stride), plan->n_chan,
                                          n_samp, d_packed, packed_stride, pair, packed_done,
                                          packed_end, pack_source(plan->dtype), hp->s_tr);
-        if (le != 0) return cuda_fail(le, "dd_run_host packing");
+        if (le != 0) return fail_joined(hp, s, le, "dd_run_host packing");
       }
       packed_done = packed_end;
       e = cudaEventRecord(hp->tr[k], hp->s_tr);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
       ready = hp->tr[k];
     }
     raw_done = std::max(raw_done, raw_end);
     e = cudaStreamWaitEvent(sc, ready, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
     // Every output whose dispersion track ends inside the samples copied so
     // far: t + S_max < raw_end / bin, whole time tiles except at the end.
     int64_t lim[DD_MAX_RANGES];
@@ -889,12 +899,12 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
         const int le = launch_range(plan, rp, from_packed ? d_packed : dcm,
                                     from_packed ? packed_stride : cm_stride, n_samp, n_out,
                                     dout + info.out_offset[r] * 4, done[r], l, sc, kind);
-        if (le != 0) return cuda_fail(le, "dd_run_host forward launch");
+        if (le != 0) return fail_joined(hp, s, le, "dd_run_host forward launch");
       }
     }
     e = cudaEventRecord(hp->comp[k], sc);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->s_out, hp->comp[k], 0);
-    if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+    if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
     for (size_t r = 0; r < plan->ranges.size(); ++r) {
       if (lim[r] <= done[r]) continue;
       const size_t pitch_out = static_cast<size_t>(info.n_out[r]) * 4;
@@ -903,7 +913,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
                             static_cast<size_t>(lim[r] - done[r]) * 4,
                             static_cast<size_t>(info.n_dm[r]), cudaMemcpyDeviceToHost,
                             hp->s_out);
-      if (e != cudaSuccess) return cuda_fail(e, "dd_run_host output copy");
+      if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host output copy");
       done[r] = lim[r];
     }
   }
@@ -911,7 +921,7 @@ static dd_status run_host_pipeline(dd_plan plan, const dd_plan_info& info, const
   // every segment's kernels on both compute streams.
   e = cudaEventRecord(hp->done, hp->s_out);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "dd_run_host ordering");
+  if (e != cudaSuccess) return fail_joined(hp, s, e, "dd_run_host ordering");
   return DD_OK;
 }
 
