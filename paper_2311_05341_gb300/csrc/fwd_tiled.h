@@ -364,8 +364,10 @@ DD_HOST_DEVICE constexpr int widen_mode(int kind, int nc, bool slots, int32_t fl
                                                                 : 1;
 }
 // Widening slots in a plan workspace: two per SM of the largest GB300-class
-// part (1 CTA per SM for the 16-warp pattern tiles, whose 128 registers per
-// thread fill the register file; the second half covers smaller tiles).
+// part.  Every kernel that takes slots holds at most one CTA per SM (16 warps
+// at 128 registers per thread, or 12 warps at up to 168, fill the register
+// file), so the CTAs of all launches of a plan in flight at once, on any
+// streams, find a free slot; the second half is margin.
 constexpr int kWidenSlots = 320;
 
 // Persistent batch execution: one work list of (job, DM block, time tile)
