@@ -545,7 +545,6 @@ def run_reference(args):
     x = workloads.make_input(beam, lambda r, d: tables[r][d], n_dm, n_out)
     if beam.dtype == "u4":
         x = oracle.Packed4(x, beam.n_samp)
-    info = {"n_dm": n_dm, "n_out": n_out}
     n_rows = args.cpu_rows_reference
     rows = np.linspace(0, n_dm[0] - 1, n_rows).astype(np.int64)
 
@@ -570,7 +569,6 @@ def run_reference(args):
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    del info
     print(json.dumps(line))
 
 
