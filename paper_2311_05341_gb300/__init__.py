@@ -234,7 +234,9 @@ class Plan:
         if segments > 0 and any(self.info(n_samp)["packed_copy"]):
             try:
                 need = max(need, self.packed_scratch_bytes(n_samp, segments))
-            except DDError:
+            except DDError as err:  # no ring for this plan: the full copies
+                if err.status != _lib.DD_ERR_UNSUPPORTED:
+                    raise
                 need = max(need, self.packed_scratch_bytes(n_samp, 1))
         if need == 0:
             return None

@@ -425,3 +425,31 @@ def test_workspace_holds_widening_slots():
     for dtype in ("u8", "u4"):
         extra = sizes[dtype] - tables
         assert 320 * slot <= extra <= 320 * slot + 320 * 4 + 512, (dtype, extra)
+
+
+def test_run_scratch_choice():
+    """Plan.run's scratch for the packed copies: the ring of `segments`, the
+    full copies for segments == 1 (and where the plan has no ring), none for
+    segments == 0; a segment count outside [1, 256] is an error, not a silent
+    fall back to the full copies."""
+    pytest.importorskip("torch")
+    freqs = channel_freqs(1500.0, 300.0, 64)
+    n = 20000
+    plan = dd.Plan(freqs, 1500.0, 64e-6, [(0.0, 6.4, 0.1, 1)], "u8", upload=False)
+    assert plan.info(n)["packed_copy"] == [True]
+    full = plan.packed_scratch_bytes(n, 1)
+    ring = plan.packed_scratch_bytes(n, 8)
+    assert 0 < ring < full
+    assert plan._input_scratch(n, "cpu", 8).numel() == ring
+    assert plan._input_scratch(n, "cpu", 1).numel() == full
+    assert plan._input_scratch(n, "cpu", 0) is None
+    with pytest.raises(dd.DDError) as err:
+        plan._input_scratch(n, "cpu", 300)
+    assert err.value.status == _lib.DD_ERR_INVALID_ARG
+    # A binned packed copy has no ring: the full copy it needs anyway.
+    binned = dd.Plan(freqs, 1500.0, 64e-6, [(0.0, 6.4, 0.1, 2)], "u8", upload=False)
+    binned.set_tile(0, "packed")
+    with pytest.raises(dd.DDError) as err:
+        binned.packed_scratch_bytes(n, 8)
+    assert err.value.status == _lib.DD_ERR_UNSUPPORTED
+    assert binned._input_scratch(n, "cpu", 8).numel() == binned.input_scratch_bytes(n) > 0
