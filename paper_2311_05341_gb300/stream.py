@@ -273,7 +273,12 @@ class StreamServer:
     def snapshot(self, beam_id: int) -> dict:
         """State of an admitted beam between chunks, on the host: its spec, the
         overlap samples of its window and the number of chunks done.  A server
-        that restores it continues the stream exactly where this one stopped."""
+        that restores it continues the stream exactly where this one stopped.
+        Chunks of the beam still queued here would be in neither, so they are
+        refused: pump() or drain() first."""
+        if any(j.beam == beam_id for j in self.queue):
+            raise RuntimeError(f"beam {beam_id} has queued chunks: pump() or drain() before "
+                               "snapshot()")
         beam = self.beams[beam_id]
         beam.stream.synchronize()
         ov = overlap_for(beam.plan, beam.spec.ranges)

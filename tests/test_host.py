@@ -453,3 +453,15 @@ def test_run_scratch_choice():
         binned.packed_scratch_bytes(n, 8)
     assert err.value.status == _lib.DD_ERR_UNSUPPORTED
     assert binned._input_scratch(n, "cpu", 8).numel() == binned.input_scratch_bytes(n) > 0
+
+
+def test_stream_snapshot_refuses_queued_chunks():
+    """A snapshot holds the overlap and the chunks already launched; a chunk
+    still queued for the beam would be lost between the two servers, so
+    snapshot() refuses until it has run (host logic, no device call)."""
+    torch = pytest.importorskip("torch")
+    from paper_2311_05341_gb300 import stream as dds
+    server = dds.StreamServer(4096, 1 << 30)
+    server.submit(3, torch.zeros((8, 4096), dtype=torch.uint8))
+    with pytest.raises(RuntimeError, match="queued chunks"):
+        server.snapshot(3)
