@@ -131,6 +131,8 @@ class Autotuner:
         """Pick and set a (tile, shape) for every range of the plan; returns them."""
         torch = _torch()
         key = plan_signature(plan, n_samp) + ("|packed" if self.packed else "")
+        if self.shapes is not None:  # a restricted tuner keeps its own entries
+            key += "|tiles=" + json.dumps(list(self.shapes), default=str)
         if key in self.cache:
             choice = [tuple(c) if isinstance(c, list) else c for c in self.cache[key]]
             for r, c in enumerate(choice):

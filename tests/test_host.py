@@ -6,6 +6,7 @@ arguments with the documented status codes.
 """
 import ctypes
 import glob
+import json
 import os
 import re
 
@@ -465,3 +466,26 @@ def test_stream_snapshot_refuses_queued_chunks():
     server.submit(3, torch.zeros((8, 4096), dtype=torch.uint8))
     with pytest.raises(RuntimeError, match="queued chunks"):
         server.snapshot(3)
+
+
+def test_autotune_cache_keeps_restricted_tuners_apart(tmp_path):
+    """A tuner restricted to some tiles never takes a cached choice made
+    without that restriction (or the other way round): the cache key names
+    the restriction.  A one-candidate tuner times nothing, so this runs on
+    the CPU."""
+    pytest.importorskip("torch")
+    from paper_2311_05341_gb300 import batch
+    freqs = channel_freqs(1500.0, 300.0, 64)
+    plan = dd.Plan(freqs, 1500.0, 64e-6, [(0.0, 6.4, 0.1, 1)], "u8", upload=False)
+    n = 20000
+    cache = tmp_path / "tune.json"
+    free_key = batch.plan_signature(plan, n) + "|packed"
+    cache.write_text(json.dumps({free_key: [["pattern", 0]]}))
+    restricted = batch.Autotuner(shapes=[4], cache_path=str(cache))
+    assert restricted.choose(plan, n, None, None) == [(4, -1)]
+    assert plan.info(n)["tile_dms"] == [4]
+    stored = json.loads(cache.read_text())
+    assert stored[free_key] == [["pattern", 0]] and len(stored) == 2
+    free = batch.Autotuner(cache_path=str(cache))
+    assert free.choose(plan, n, None, None) == [("pattern", 0)]
+    assert plan.info(n)["tile_dms"] == [_lib.DD_TILE_PATTERN]
